@@ -1,0 +1,183 @@
+/*
+ * sppc.h - C ABI of the GB300 (sm_103a) SPPC eigensolver library (libsppc.so).
+ *
+ * SPPC (Subspace Projection with Perturbative Corrections) computes the k lowest
+ * eigenpairs of a large sparse symmetric matrix H split as H = H0 + V with
+ * H0 = diag(H0_hat, 0), H0_hat the leading n1 x n1 block (the small configuration
+ * space) and V = H - H0 (paper Sec. 2, Eqs. split/split2; Algorithm 2).  Each order
+ * p adds k perturbative correction vectors Psi^(p) (Eq. exp_seq2), computed from
+ * small shifted solves in the leading block (Eqs. bl_diag, sm_first, sm_lin_proj),
+ * to an orthonormal basis Q (Eqs. blkGS, QR, Qp) and extracts Ritz pairs from the
+ * projected matrix Q^T H Q (Eqs. tilde_H, proj), costing k products with H per
+ * order (Sec. 4.3, Eqs. avoid_SpMV2, HPsip).
+ *
+ * Conventions (every entry point):
+ *  - Returns an sppc_status; never aborts.  On failure sppc_last_error(h) (or
+ *    sppc_last_error(NULL) for failures before a handle exists) gives a message.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; calls that return host results synchronise it.
+ *  - Device buffers passed in are owned by the caller and only read or written
+ *    during the call.  Host buffers likewise.  The library owns everything it
+ *    allocates (matrix copy, basis Q, W = HQ, scratch) and frees it in
+ *    sppc_destroy.
+ *  - Dense blocks are row-major n x ncols with a leading dimension (elements).
+ *  - All values crossing the ABI are IEEE FP64.  Internally the library stores
+ *    matrix values and vectors as double-float pairs (two fp32 whose sum carries
+ *    ~48 significant bits) and computes with error-free fp32 transformations,
+ *    because native FP64 throughput on this GPU is ~1/70 of FP32.
+ *  - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef SPPC_H_
+#define SPPC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sppc_ctx* sppc_handle;
+
+typedef enum {
+  SPPC_OK = 0,
+  SPPC_ERR_ARG = 1,           /* bad argument (null pointer, size, k range, ...) */
+  SPPC_ERR_NOT_SYMMETRIC = 2, /* H != H^T (only when opts.check_symmetry) */
+  SPPC_ERR_LEVELS = 3,        /* level_offsets malformed or n1 not a level boundary */
+  SPPC_ERR_OOM = 4,           /* device or host allocation failed */
+  SPPC_ERR_CUDA = 5,          /* a CUDA call failed (message has the CUDA error) */
+  SPPC_ERR_BREAKDOWN = 6,     /* Cholesky breakdown / rank loss in orthogonalisation */
+  SPPC_ERR_MINRES = 7,        /* a small solve hit its iteration limit */
+  SPPC_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up */
+  SPPC_NOT_CONVERGED = 9,     /* p_max reached; outputs hold the last order's pairs */
+  SPPC_ERR_STATE = 10,        /* call out of sequence (e.g. correct before start) */
+  SPPC_ERR_NAN = 11           /* a NaN/Inf appeared in the input or iteration */
+} sppc_status;
+
+/* Caller-owned CSR matrix, only read by sppc_create.  Rows must have strictly
+ * increasing column indices; the diagonal may be stored or absent. */
+typedef struct {
+  int64_t n;              /* rows = columns */
+  int64_t nnz;            /* stored entries */
+  const int64_t* row_ptr; /* n+1 offsets, row_ptr[0] = 0, row_ptr[n] = nnz */
+  const int32_t* col;     /* nnz column indices in [0, n) */
+  const double* val;      /* nnz values */
+  int32_t on_device;      /* 0: host pointers, 1: device pointers */
+} sppc_csr;
+
+typedef struct {
+  int32_t p_max;          /* maximum correction order (default 15; paper Sec. 4.3, 6) */
+  double tol;             /* scaled residual ||Hz - theta z|| / |theta| (Eq. rrn), default 1e-6 */
+  double minres_tol;      /* small solve: stop at ||r|| <= minres_tol ||b1|| (default 1e-12) */
+  int32_t minres_maxit;   /* small solve iteration cap (default 20*n1, at most 200000) */
+  double small_tol;       /* small eigensolve residual tolerance, relative to ||H0_hat|| (1e-12) */
+  int32_t small_block;    /* vectors in the small eigensolve (default 2k, >= k+1) */
+  double degeneracy_tol;  /* psi_hat_j also deflated for column k if |E_j - E_k| <= tol*||H0_hat|| (1e-10) */
+  int32_t check_symmetry; /* 1: verify H == H^T bit for bit at create (default 0) */
+  uint64_t seed;          /* seed of the small eigensolve's start block (default 0) */
+  int32_t timing;         /* 1: time kernels with CUDA events into sppc_stats (default 0) */
+} sppc_opts;
+
+typedef struct {
+  int32_t orders;            /* correction orders run (p of the last Rayleigh-Ritz) */
+  int32_t converged;         /* 1 if every scaled residual <= tol */
+  int64_t spmv_h;            /* products of H with one vector (k per order, k(P+1) total) */
+  int64_t spmv_h11;          /* products of H0_hat with one vector (small eigensolve + MINRES) */
+  int64_t minres_iters;      /* total MINRES iterations (max over the k columns, summed over orders) */
+  int64_t small_eig_iters;   /* Chebyshev filter degree summed over outer iterations */
+  int32_t spmm_launches;     /* launches of the big SpMM kernel */
+  double spmm_ms;            /* summed CUDA-event time of the big SpMM launches (timing=1) */
+  double minres_ms;          /* small solves (timing=1) */
+  double small_eig_ms;       /* small eigensolve (timing=1) */
+  double dense_ms;           /* Gram / orthogonalisation / Rayleigh-Ritz kernels (timing=1) */
+  double total_ms;           /* whole call (timing=1) */
+} sppc_stats;
+
+/* Fill `o` with the defaults listed above. */
+void sppc_default_opts(sppc_opts* o);
+
+/* Build a handle for H (paper Sec. 2: H0_hat = leading n1 x n1 block).
+ *  level_offsets[0..n_levels]: 0 = off_0 < off_1 < ... < off_n = n, the row ranges
+ *    of the hierarchy levels (Sec. 1: leading submatrix = smaller N_max space);
+ *  n1 must equal level_offsets[j] for some j >= 1 (Sec. 6.1: H0_hat is the whole
+ *    smaller configuration space), else SPPC_ERR_LEVELS;
+ *  1 <= k <= 8 eigenpairs, k < n1.
+ * Copies and reformats H into library-owned device memory (level-blocked SELL-32
+ * layout plus a separate copy of H0_hat).  Allocates the basis for opts.p_max
+ * orders up front (SPPC_ERR_OOM if it does not fit).  opts may be NULL. */
+sppc_status sppc_create(const sppc_csr* H, const int64_t* level_offsets, int32_t n_levels, int64_t n1,
+                        int32_t k, const sppc_opts* opts, void* stream, sppc_handle* out);
+
+/* Y = H X for ncols <= 8 columns (the SpMM of Sec. 4.2, "k SpMVs in Hq^(p)").
+ * X, Y: caller-owned DEVICE buffers, row-major n x ncols, leading dims ldx, ldy
+ * (>= ncols).  X and Y must not overlap. */
+sppc_status sppc_spmm(sppc_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t ncols,
+                      void* stream);
+
+/* Same product with HOST buffers: copies X to the device, multiplies, copies Y back
+ * (synchronises the stream). */
+sppc_status sppc_spmm_host(sppc_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t ncols,
+                           void* stream);
+
+/* Algorithm 2 steps 1-4: the k lowest eigenpairs (E^(0), psi_hat) of H0_hat
+ * (Eq. EP_small), Q^(0) = Psi^(0), W = H Q^(0), projected matrix and Ritz pairs.
+ * theta, resid: optional host arrays of k (NULL to skip). */
+sppc_status sppc_start(sppc_handle h, double* theta, double* resid, void* stream);
+
+/* One correction order p -> p+1 (Alg. 2 loop body, first half): right-hand side
+ * of Eq. exp_seq2 from the recycled H Psi^(p-1) (Eqs. avoid_SpMV2, HPsip), the
+ * correction energies E^(p) (Eq. exp_seq), x2 = -b2/E^(0) (Eq. sm_first), the k
+ * deflated small solves by MINRES (Eq. sm_lin_proj), block Gram-Schmidt twice
+ * (Eq. blkGS) and CholeskyQR2 (Eq. QR), appending q^(p) to Q (Eq. Qp). */
+sppc_status sppc_correct(sppc_handle h, void* stream);
+
+/* Rayleigh-Ritz after sppc_correct (second half of the loop body): W_p = H q^(p)
+ * (the k SpMVs of the order), bordered projected matrix (Eq. proj), its k lowest
+ * eigenpairs, Ritz vectors and scaled residuals (Eq. rrn).  theta, resid: optional
+ * host arrays of k. */
+sppc_status sppc_rayleigh_ritz(sppc_handle h, double* theta, double* resid, void* stream);
+
+/* Algorithm 2 end to end: start, then correct + rayleigh_ritz until every scaled
+ * residual <= tol or p_max orders.  Outputs (any may be NULL):
+ *   theta[k], resid[k]: host arrays;
+ *   Z: caller-owned DEVICE buffer n x k (ldz >= k), the Ritz vectors;
+ *   stats: host struct.
+ * tol <= 0 or p_max < 0 take the handle's options.  Returns SPPC_NOT_CONVERGED
+ * (with the last order's pairs filled in) when p_max is reached first. */
+sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, double* Z, int64_t ldz,
+                       double* resid, sppc_stats* stats, void* stream);
+
+/* Per-order record of the last solve: E^(p) (k values), sine of the angle between
+ * Psi_j^(p) and M^(p-1) after orthogonalisation (k values; Sec. 6.2), Ritz values
+ * and scaled residuals after order p (k values each), MINRES iterations per column.
+ * Any output may be NULL.  p in [0, orders]. */
+sppc_status sppc_order_info(sppc_handle h, int32_t p, double* E, double* angle, double* theta, double* resid,
+                            int32_t* minres_iters);
+
+/* Current statistics of the handle (cumulative since sppc_start). */
+sppc_status sppc_get_stats(sppc_handle h, sppc_stats* stats);
+
+/* Copies of internal state for tests (host buffers, FP64):
+ *   which = 0: psi_hat, n1 x k;   1: Q, n x m (m = k * (orders+1));   2: W = H Q, n x m;
+ *           3: projected matrix, m x m;   4: Psi^(p) of the last order, n x k;
+ *           5: E^(0), k.
+ * `count` is the number of doubles the buffer holds; returns SPPC_ERR_ARG if too small. */
+sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t count);
+
+/* Integer layout of the device matrix copy, for bit-exact checks.  Host buffers:
+ *   slice_ptr[n_slices+1] (int64), slice_rows[32*n_slices] (int32, -1 = padding lane),
+ *   h11 same for the leading block.  Query sizes with NULL buffers. */
+sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr, int32_t* slice_rows,
+                            int64_t* n11_slices, int64_t* h11_slice_ptr, int32_t* h11_slice_rows);
+
+/* Release everything the handle owns.  NULL is a no-op. */
+sppc_status sppc_destroy(sppc_handle h);
+
+/* Last error message of h (or of the calling thread's last failed create when
+ * h == NULL).  The string is owned by the library and valid until the next call. */
+const char* sppc_last_error(sppc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPPC_H_ */

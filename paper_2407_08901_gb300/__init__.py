@@ -1,0 +1,228 @@
+"""GB300 (sm_103a) SPPC eigensolver: thin Python binding of libsppc.so.
+
+Every function here has the name of the C entry point it wraps (declared in
+include/sppc.h) and only marshals arguments: all computation runs in the CUDA
+kernels of the library.  Importing the package loads libsppc.so and raises
+ImportError if it has not been built (``__graft_entry__.build()``); there is no
+fallback.  PyTorch is used only for device buffers and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+__all__ = [
+    "SppcError", "sppc_default_opts", "sppc_create", "sppc_spmm", "sppc_spmm_host", "sppc_start", "sppc_correct",
+    "sppc_rayleigh_ritz", "sppc_solve", "sppc_order_info", "sppc_get_stats", "sppc_get_state", "sppc_get_layout",
+    "sppc_destroy", "sppc_last_error", "EXPORTED_SYMBOLS", "STATUS",
+]
+
+STATUS = {0: "SPPC_OK", 1: "SPPC_ERR_ARG", 2: "SPPC_ERR_NOT_SYMMETRIC", 3: "SPPC_ERR_LEVELS", 4: "SPPC_ERR_OOM",
+          5: "SPPC_ERR_CUDA", 6: "SPPC_ERR_BREAKDOWN", 7: "SPPC_ERR_MINRES", 8: "SPPC_ERR_TIMEOUT",
+          9: "SPPC_NOT_CONVERGED", 10: "SPPC_ERR_STATE", 11: "SPPC_ERR_NAN"}
+SPPC_OK = 0
+SPPC_NOT_CONVERGED = 9
+
+
+class SppcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("p_max", ctypes.c_int32), ("tol", ctypes.c_double), ("minres_tol", ctypes.c_double),
+                ("minres_maxit", ctypes.c_int32), ("small_tol", ctypes.c_double), ("small_block", ctypes.c_int32),
+                ("degeneracy_tol", ctypes.c_double), ("check_symmetry", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("timing", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("orders", ctypes.c_int32), ("converged", ctypes.c_int32), ("spmv_h", ctypes.c_int64),
+                ("spmv_h11", ctypes.c_int64), ("minres_iters", ctypes.c_int64), ("small_eig_iters", ctypes.c_int64),
+                ("spmm_launches", ctypes.c_int32), ("spmm_ms", ctypes.c_double), ("minres_ms", ctypes.c_double),
+                ("small_eig_ms", ctypes.c_double), ("dense_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_VP = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "sppc_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "sppc_create": (_I32, [ctypes.POINTER(Csr), _VP, _I32, _I64, _I32, ctypes.POINTER(Opts), _VP,
+                           ctypes.POINTER(_VP)]),
+    "sppc_spmm": (_I32, [_VP, _VP, _I64, _VP, _I64, _I32, _VP]),
+    "sppc_spmm_host": (_I32, [_VP, _VP, _I64, _VP, _I64, _I32, _VP]),
+    "sppc_start": (_I32, [_VP, _VP, _VP, _VP]),
+    "sppc_correct": (_I32, [_VP, _VP]),
+    "sppc_rayleigh_ritz": (_I32, [_VP, _VP, _VP, _VP]),
+    "sppc_solve": (_I32, [_VP, _D, _I32, _VP, _VP, _I64, _VP, ctypes.POINTER(Stats), _VP]),
+    "sppc_order_info": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "sppc_get_stats": (_I32, [_VP, ctypes.POINTER(Stats)]),
+    "sppc_get_state": (_I32, [_VP, _I32, _VP, _I64]),
+    "sppc_get_layout": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sppc_destroy": (_I32, [_VP]),
+    "sppc_last_error": (ctypes.c_char_p, [_VP]),
+}
+EXPORTED_SYMBOLS = tuple(_SIGS)
+
+
+def _load():
+    if not os.path.exists(LIB):
+        raise ImportError(f"{LIB} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (contiguity is the caller's duty)."""
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(h, st: int, allow=(SPPC_OK,)):
+    if st not in allow:
+        msg = _lib.sppc_last_error(h)
+        raise SppcError(st, msg.decode() if msg else "")
+    return st
+
+
+def sppc_last_error(h=None) -> str:
+    m = _lib.sppc_last_error(h)
+    return m.decode() if m else ""
+
+
+def sppc_default_opts(**overrides) -> Opts:
+    o = Opts()
+    _lib.sppc_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def sppc_create(row_ptr, col, val, level_offsets, n1: int, k: int, opts: Opts | None = None, stream=None,
+                on_device: bool = False):
+    """Create a handle for the CSR matrix (int64 row_ptr, int32 col, float64 val).
+
+    Host numpy arrays (on_device=False) or torch CUDA tensors (on_device=True)."""
+    n = int(row_ptr.shape[0]) - 1
+    csr = Csr(n, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val), 1 if on_device else 0)
+    lev = np.ascontiguousarray(level_offsets, dtype=np.int64)
+    h = ctypes.c_void_p()
+    st = _lib.sppc_create(ctypes.byref(csr), lev.ctypes.data, len(lev) - 1, int(n1), int(k),
+                          ctypes.byref(opts) if opts is not None else None, _stream(stream), ctypes.byref(h))
+    _check(None, st)
+    return h
+
+
+def sppc_spmm(h, X, Y, stream=None) -> None:
+    """Y = H X for torch CUDA float64 tensors X, Y of shape (n, ncols), ncols <= 8."""
+    assert X.dtype == Y.dtype and X.is_cuda and Y.is_cuda and X.stride(1) == 1 and Y.stride(1) == 1
+    _check(h, _lib.sppc_spmm(h, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), X.shape[1], _stream(stream)))
+
+
+def sppc_spmm_host(h, X: np.ndarray, Y: np.ndarray, stream=None) -> None:
+    """Y = H X for host float64 arrays (copies inside the call)."""
+    assert X.flags.c_contiguous and Y.flags.c_contiguous
+    _check(h, _lib.sppc_spmm_host(h, _ptr(X), X.shape[1], _ptr(Y), Y.shape[1], X.shape[1], _stream(stream)))
+
+
+def sppc_start(h, k: int, stream=None):
+    th, rs = np.zeros(k), np.zeros(k)
+    _check(h, _lib.sppc_start(h, th.ctypes.data, rs.ctypes.data, _stream(stream)))
+    return th, rs
+
+
+def sppc_correct(h, stream=None) -> None:
+    _check(h, _lib.sppc_correct(h, _stream(stream)))
+
+
+def sppc_rayleigh_ritz(h, k: int, stream=None):
+    th, rs = np.zeros(k), np.zeros(k)
+    _check(h, _lib.sppc_rayleigh_ritz(h, th.ctypes.data, rs.ctypes.data, _stream(stream)))
+    return th, rs
+
+
+def sppc_solve(h, k: int, tol: float = -1.0, p_max: int = -1, Z=None, stream=None):
+    """Algorithm 2 end to end.  Z: optional torch CUDA float64 tensor (n, >=k).
+
+    Returns (converged, theta, resid, stats dict)."""
+    th, rs = np.zeros(k), np.zeros(k)
+    stats = Stats()
+    ldz = Z.stride(0) if Z is not None else 0
+    st = _lib.sppc_solve(h, float(tol), int(p_max), th.ctypes.data, _ptr(Z), ldz, rs.ctypes.data,
+                         ctypes.byref(stats), _stream(stream))
+    _check(h, st, allow=(SPPC_OK, SPPC_NOT_CONVERGED))
+    return st == SPPC_OK, th, rs, stats.as_dict()
+
+
+def sppc_order_info(h, p: int, k: int) -> dict:
+    E, ang, th, rs = (np.zeros(k) for _ in range(4))
+    it = np.zeros(k, dtype=np.int32)
+    _check(h, _lib.sppc_order_info(h, int(p), E.ctypes.data, ang.ctypes.data, th.ctypes.data, rs.ctypes.data,
+                                   it.ctypes.data))
+    return {"E": E, "angle": ang, "theta": th, "resid": rs, "minres_iters": it}
+
+
+def sppc_get_stats(h) -> dict:
+    s = Stats()
+    _check(h, _lib.sppc_get_stats(h, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def sppc_get_state(h, which: int, shape) -> np.ndarray:
+    out = np.zeros(shape)
+    _check(h, _lib.sppc_get_state(h, int(which), out.ctypes.data, out.size))
+    return out
+
+
+def sppc_get_layout(h) -> dict:
+    ns, n11 = ctypes.c_int64(), ctypes.c_int64()
+    _check(h, _lib.sppc_get_layout(h, ctypes.byref(ns), None, None, ctypes.byref(n11), None, None))
+    sp = np.zeros(ns.value + 1, dtype=np.int64)
+    sr = np.zeros(32 * ns.value, dtype=np.int32)
+    sp11 = np.zeros(n11.value + 1, dtype=np.int64)
+    sr11 = np.zeros(32 * n11.value, dtype=np.int32)
+    _check(h, _lib.sppc_get_layout(h, None, sp.ctypes.data, sr.ctypes.data, None, sp11.ctypes.data,
+                                   sr11.ctypes.data))
+    return {"slice_ptr": sp, "slice_rows": sr, "h11_slice_ptr": sp11, "h11_slice_rows": sr11}
+
+
+def sppc_destroy(h) -> None:
+    if h:
+        _lib.sppc_destroy(h)

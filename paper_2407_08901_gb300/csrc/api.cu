@@ -1,0 +1,1449 @@
+// C ABI and host driver of the SPPC eigensolver (Algorithm 2 of the paper).
+//
+// The driver owns all device memory and sequences the kernels of k_spmm.cu,
+// k_dense.cu and k_small.cu on the caller's stream.  Host work is limited to
+// argument checks, building the SELL-32 layout once in sppc_create, scalar
+// bookkeeping and one small device->host copy per correction order (the
+// convergence test of Alg. 2) or per few MINRES iterations.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "df.cuh"
+#include "sppc.h"
+#include "sppc_internal.h"
+
+using namespace sppc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct OrderRec {
+  std::vector<double> E, angle, theta, resid;
+  std::vector<int32_t> iters;
+};
+
+// Device scratch for small coefficient arrays (double-float) and FP64 scalars.
+enum CoefSlot : int {
+  kOnes = 0,         // 16
+  kNegOnes = 16,     // 16
+  kShiftNegE = 32,   // -E0 per column (MINRES operator shift)
+  kInvE0 = 48,       // 1/E0
+  kRhsBig = 64,      // (kMaxBlocks) x 8: -E^(p-l)/E0
+  kRhsSmall = 384,   // (kMaxBlocks) x 8
+  kDefl = 704,       // 8
+  kMinA = 720,       // 24: {-s, -beta, -alpha} for {psi_hat, v_prev, v}
+  kMinWAlpha = 744,  // 8: 1/rho1
+  kMinW = 752,       // 16: {-rho3/rho1, -rho2/rho1}
+  kMinX = 768,       // 8: c*eta
+  kMinV = 776,       // 8: 1/beta'
+  kCheb = 784,       // 3 x 16: alpha, beta, gamma of the Chebyshev filter
+  kTheta = 832,      // 16
+  kCoefEnd = 848
+};
+
+struct MinresState {
+  double beta, c_prev, c_cur, s_prev, s_cur, eta, rnorm, beta1, alpha;
+  int done, it;
+};
+
+}  // namespace
+
+struct sppc_ctx {
+  int64_t n = 0, nnz = 0, n1 = 0;
+  int k = 0, kp = 0, pmax = 0, mmax = 0;
+  std::vector<int64_t> lev;
+  sppc_opts opt{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+
+  // matrix (device)
+  SellDev H, H11;
+  std::vector<void*> allocs;
+  int64_t h_slices = 0, h11_slices = 0;
+  std::vector<int64_t> h_slice_ptr, h11_slice_ptr;  // host copies for sppc_get_layout
+  std::vector<int32_t> h_slice_rows, h11_slice_rows;
+  double h11_lo = 0, h11_hi = 0, h11_norm = 1;
+
+  // blocks (double-float, row-major n x kp)
+  float2 *Q = nullptr, *W = nullptr, *Psi = nullptr, *HPsi = nullptr, *T1 = nullptr, *T2 = nullptr;
+  // small-space vectors (n1 x kp)
+  float2 *psi_hat = nullptr, *vps = nullptr, *b1 = nullptr;
+  float2 *mv = nullptr, *mvprev = nullptr, *mp = nullptr, *my = nullptr, *mw1 = nullptr, *mw2 = nullptr,
+         *mx = nullptr;
+  // small eigensolve (n1 x 8 blocks, up to 2 per set; 3 filter sets + X + AX + tmp)
+  float2* se[12] = {nullptr};
+  // FP64 scalars / small matrices
+  double *dE = nullptr, *dHt = nullptr, *dGram = nullptr, *dC1 = nullptr, *dC2 = nullptr, *dR1 = nullptr,
+         *dR2 = nullptr, *dTheta = nullptr, *dV = nullptr, *dDots = nullptr, *dS = nullptr;
+  float2 *dCoef = nullptr, *dRinv = nullptr, *dRecycle = nullptr, *dY = nullptr, *dCoefBig = nullptr;
+  MinresState* dMin = nullptr;
+  int* dStatus = nullptr;
+  float2* partials = nullptr;
+  int64_t partial_cap = 0;
+  double *stageX = nullptr, *stageY = nullptr;  // sppc_spmm_host staging (n x 8 each)
+
+  // state
+  bool started = false, corrected = false;
+  int p = 0;
+  std::vector<double> E0, theta, resid;
+  std::vector<OrderRec> rec;
+  sppc_stats stats{};
+  std::vector<cudaEvent_t> evpool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // big-SpMM timing pairs
+  int evnext = 0;
+};
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+sppc_status fail(sppc_ctx* h, sppc_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h)
+    h->err = buf;
+  else
+    g_create_error = buf;
+  return st;
+}
+
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? SPPC_ERR_OOM : SPPC_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                                 \
+  } while (0)
+
+#define CKS(expr)                      \
+  do {                                 \
+    sppc_status s_ = (expr);           \
+    if (s_ != SPPC_OK) return s_;      \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(sppc_ctx* h, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+inline float2* blk(float2* base, int64_t n, int kp, int a) { return base + static_cast<int64_t>(a) * n * kp; }
+
+BlockList blocks(float2* base, int64_t n, int kp, int a0, int a1) {
+  BlockList L;
+  L.n = a1 - a0;
+  for (int a = a0; a < a1; ++a) L.p[a - a0] = blk(base, n, kp, a);
+  return L;
+}
+
+BlockList one(const float2* p) {
+  BlockList L;
+  L.n = 1;
+  L.p[0] = p;
+  return L;
+}
+
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------ tiny kernels
+__global__ void k_set_consts(float2* c) {
+  const int t = threadIdx.x;
+  if (t < 16) {
+    c[kOnes + t] = make_float2(1.f, 0.f);
+    c[kNegOnes + t] = make_float2(-1.f, 0.f);
+  }
+}
+
+__global__ void k_set_e0(const double* E0, int k, int kp, float2* c) {
+  const int j = threadIdx.x;
+  if (j >= kp) return;
+  c[kShiftNegE + j] = (j < k) ? df_from_double(-E0[j]) : make_float2(0.f, 0.f);
+  c[kInvE0 + j] = (j < k) ? df_from_double(1.0 / E0[j]) : make_float2(0.f, 0.f);
+}
+
+// Coefficients of the right-hand side of Eq. exp_seq2 at order p:
+//  big rows:   Psi^(p)_2 = (1/E0) H Psi^(p-1)_2 - sum_{l=1}^{p-2} (E^(p-l)/E0) Psi^(l)_2
+//  small rows: b1 = -V Psi^(p-1)_1 + E^(p) psi_hat + sum_{l=1}^{p-2} E^(p-l) Psi^(l)_1
+// E is stored as dE[q*kp + j] = E^(q)_j.
+__global__ void k_rhs_coefs(const double* dE, int p, int k, int kp, float2* c) {
+  const int j = threadIdx.x;
+  if (j >= kp) return;
+  const double e0 = dE[j];
+  for (int l = 1; l <= p - 2; ++l) {
+    const double el = (j < k) ? dE[(p - l) * kp + j] : 0.0;
+    c[kRhsBig + (l - 1) * 8 + j] = (j < k) ? df_from_double(-el / e0) : make_float2(0.f, 0.f);
+    c[kRhsSmall + l * 8 + j] = (j < k) ? df_from_double(el) : make_float2(0.f, 0.f);
+  }
+  c[kRhsSmall + j] = (j < k) ? df_from_double(dE[p * kp + j]) : make_float2(0.f, 0.f);
+}
+
+__global__ void k_neg_dots_to_coef(const double* d, int k, int kp, float2* out) {
+  const int j = threadIdx.x;
+  if (j < kp) out[j] = (j < k) ? df_from_double(-d[j]) : make_float2(0.f, 0.f);
+}
+
+// Coefficient matrix for X - A C given C (FP64, (na*kp) x kp): writes -C as double-float.
+__global__ void k_negmat(const double* C, int count, float2* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = df_from_double(-C[i]);
+}
+
+__global__ void k_addmat(const double* A, const double* B, int count, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = A[i] + B[i];
+}
+
+// R = R2 * R1 (kp x kp upper triangular FP64), stored as double-float rows
+// [dst + p*kp*kp ...] of the recycle coefficient matrix; Cacc (p*kp x kp) goes first.
+__global__ void k_recycle_coefs(const double* Cacc, int p, int kp, const double* R2, const double* R1, float2* dst) {
+  const int t = threadIdx.x;
+  for (int i = t; i < p * kp * kp; i += blockDim.x) dst[i] = df_from_double(Cacc[i]);
+  for (int e = t; e < kp * kp; e += blockDim.x) {
+    const int i = e / kp, j = e % kp;
+    double s = 0.0;
+    for (int l = 0; l < kp; ++l) s += R2[i * kp + l] * R1[l * kp + j];
+    dst[p * kp * kp + e] = df_from_double(s);
+  }
+}
+
+// Border of the projected matrix (Eq. proj): B = Q_{0..p}^T W_p in padded layout
+// ((p+1)*kp x kp).  Writes the compact m x m matrix (ld mmax), symmetrising the new
+// diagonal block and mirroring the border.
+__global__ void k_assemble_ht(const double* B, int p, int k, int kp, double* Ht, int ld) {
+  const int t = threadIdx.x;
+  const int rows = (p + 1) * k;
+  for (int e = t; e < rows * k; e += blockDim.x) {
+    const int r = e / k, j = e % k;
+    const int a = r / k, i = r % k;
+    const double v = B[(a * kp + i) * kp + j];
+    const int R = a * k + i, Cc = p * k + j;
+    if (a < p) {
+      Ht[R * ld + Cc] = v;
+      Ht[Cc * ld + R] = v;
+    } else {
+      const double w = B[(a * kp + j) * kp + i];
+      Ht[R * ld + Cc] = 0.5 * (v + w);
+    }
+  }
+}
+
+// Ritz coefficients Y (compact m x k, ld k) -> padded double-float ((p+1)*kp x kp);
+// theta -> double-float per column.
+__global__ void k_expand_y(const double* V, int p, int k, int kp, const double* th, float2* Y, float2* thdf) {
+  const int t = threadIdx.x;
+  const int rows = (p + 1) * kp;
+  for (int e = t; e < rows * kp; e += blockDim.x) {
+    const int r = e / kp, j = e % kp;
+    const int a = r / kp, i = r % kp;
+    Y[e] = (i < k && j < k) ? df_from_double(V[(a * k + i) * k + j]) : make_float2(0.f, 0.f);
+  }
+  if (t < kp) thdf[t] = (t < k) ? df_from_double(th[t]) : make_float2(0.f, 0.f);
+}
+
+// Coefficient sub-block for block updates of multi-block sets: out[(a*8+i)*8+j] =
+// src[(a*8+i)*lds + ob*8 + j] for a < na.
+__global__ void k_subblock(const float2* src, int lds, int na, int ob, float2* out) {
+  const int t = threadIdx.x;
+  for (int e = t; e < na * 64; e += blockDim.x) {
+    const int r = e / 8, j = e % 8;
+    out[e] = src[r * lds + ob * 8 + j];
+  }
+}
+
+// V (m x nev FP64, ld nev) -> double-float rotation coefficients (m x m padded to 16x16 ld 16)
+__global__ void k_vmat_df(const double* V, int m, int nev, int ldv, float2* out) {
+  const int t = threadIdx.x;
+  for (int e = t; e < 256; e += blockDim.x) {
+    const int i = e / 16, j = e % 16;
+    out[e] = (i < m && j < nev) ? df_from_double(V[i * ldv + j]) : make_float2(0.f, 0.f);
+  }
+}
+
+__global__ void k_minres_init(const double* bb, int k, int kp, MinresState* st, float2* coef) {
+  const int j = threadIdx.x;
+  if (j >= kp) return;
+  MinresState s{};
+  const double b1 = (j < k) ? sqrt(bb[j]) : 0.0;
+  s.beta = b1;
+  s.beta1 = b1;
+  s.eta = b1;
+  s.rnorm = b1;
+  s.c_prev = s.c_cur = 1.0;
+  s.s_prev = s.s_cur = 0.0;
+  s.done = (b1 > 0.0) ? 0 : 1;
+  s.it = 0;
+  st[j] = s;
+  coef[kMinV + j] = s.done ? make_float2(0.f, 0.f) : df_from_double(1.0 / b1);
+}
+
+// Lanczos step on the projected operator P (H11 - E) P, P = I - psi psi^T, in the
+// order of the oracle: with y = (H11 - E) v and the dots (v,y), (psi,y), (v,psi),
+// (v,v_prev) from one pass, s = psi^T y, alpha = v^T (P y - beta v_prev) and
+// p = P y - beta v_prev - alpha v.
+__global__ void k_minres_a(const double* dots, int kp, MinresState* st, float2* coef) {
+  const int j = threadIdx.x;
+  if (j >= kp) return;
+  MinresState& s = st[j];
+  double a = 0.0, sp = 0.0, be = 0.0;
+  if (!s.done) {
+    sp = dots[kp + j];
+    be = s.beta;
+    a = dots[j] - sp * dots[2 * kp + j] - be * dots[3 * kp + j];
+  }
+  s.alpha = a;
+  coef[kMinA + j] = df_from_double(-sp);
+  coef[kMinA + 8 + j] = df_from_double(s.it == 0 ? 0.0 : -be);
+  coef[kMinA + 16 + j] = df_from_double(-a);
+}
+
+// Lanczos norm beta' = ||p||, Givens rotation and solution update coefficients
+// (MINRES, Paige and Saunders 1975).
+__global__ void k_minres_b(const double* pp, int kp, double tol, MinresState* st, float2* coef, int* flags) {
+  const int j = threadIdx.x;
+  if (j >= kp) return;
+  MinresState& s = st[j];
+  const float2 z = make_float2(0.f, 0.f);
+  if (s.done) {
+    coef[kMinWAlpha + j] = z;
+    coef[kMinW + j] = z;
+    coef[kMinW + 8 + j] = z;
+    coef[kMinX + j] = z;
+    coef[kMinV + j] = z;
+    flags[j] = 1;
+    return;
+  }
+  const double bn = sqrt(fmax(pp[j], 0.0));
+  const double delta = s.c_cur * s.alpha - s.c_prev * s.s_cur * s.beta;
+  const double rho1 = hypot(delta, bn);
+  const double rho2 = s.s_cur * s.alpha + s.c_prev * s.c_cur * s.beta;
+  const double rho3 = s.s_prev * s.beta;
+  s.it += 1;
+  if (rho1 == 0.0) {
+    s.done = 1;
+    coef[kMinWAlpha + j] = z;
+    coef[kMinW + j] = z;
+    coef[kMinW + 8 + j] = z;
+    coef[kMinX + j] = z;
+    coef[kMinV + j] = z;
+    flags[j] = 1;
+    return;
+  }
+  const double cn = delta / rho1, sn = bn / rho1;
+  coef[kMinWAlpha + j] = df_from_double(1.0 / rho1);
+  coef[kMinW + j] = df_from_double(-rho3 / rho1);
+  coef[kMinW + 8 + j] = df_from_double(-rho2 / rho1);
+  coef[kMinX + j] = df_from_double(cn * s.eta);
+  s.rnorm = fabs(sn) * s.rnorm;
+  s.eta = -sn * s.eta;
+  s.c_prev = s.c_cur;
+  s.c_cur = cn;
+  s.s_prev = s.s_cur;
+  s.s_cur = sn;
+  const bool conv = (s.rnorm <= tol * s.beta1) || (bn == 0.0);
+  if (conv) {
+    s.done = 1;
+    coef[kMinV + j] = z;
+  } else {
+    coef[kMinV + j] = df_from_double(1.0 / bn);
+  }
+  s.beta = bn;
+  flags[j] = s.done;
+}
+
+__global__ void k_minres_iters(const MinresState* st, int kp, int* out) {
+  const int j = threadIdx.x;
+  if (j < kp) out[j] = st[j].it;
+}
+
+// ------------------------------------------------------------ SELL builder
+struct SellHost {
+  int64_t nslices = 0;
+  std::vector<int64_t> slice_ptr;
+  std::vector<int32_t> rows, col;
+  std::vector<float2> val;
+};
+
+void split_df(double x, float2& out) {
+  const float h = static_cast<float>(x);
+  out.x = h;
+  out.y = static_cast<float>(x - static_cast<double>(h));
+}
+
+// Rows [0, nrows) keeping only columns < col_limit.  `seg` are segment (level)
+// boundaries within [0, nrows]; rows are sorted by decreasing length inside windows
+// of `sigma` rows that never cross a segment, and cut into slices of 32 rows.
+void build_sell(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t col_limit,
+                const std::vector<int64_t>& seg, int64_t sigma, SellHost& S) {
+  std::vector<int64_t> len(nrows);
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nrows; ++r) {
+    const int32_t* b = ci + rp[r];
+    const int32_t* e = ci + rp[r + 1];
+    len[r] = (col_limit >= (int64_t)1 << 31) ? (e - b) : (std::lower_bound(b, e, (int32_t)col_limit) - b);
+  }
+  std::vector<int32_t> order(nrows);
+  for (int64_t r = 0; r < nrows; ++r) order[r] = (int32_t)r;
+  std::vector<std::pair<int64_t, int64_t>> windows;
+  std::vector<int64_t> slice_first;  // first position in `order` of each slice
+  std::vector<int32_t> slice_count;
+  for (size_t sgi = 0; sgi + 1 < seg.size(); ++sgi) {
+    const int64_t a = seg[sgi], b = seg[sgi + 1];
+    for (int64_t w = a; w < b; w += sigma) windows.push_back({w, std::min(w + sigma, b)});
+    for (int64_t s = a; s < b; s += 32) {
+      slice_first.push_back(s);
+      slice_count.push_back((int32_t)std::min<int64_t>(32, b - s));
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t wi = 0; wi < (int64_t)windows.size(); ++wi) {
+    std::stable_sort(order.begin() + windows[wi].first, order.begin() + windows[wi].second,
+                     [&](int32_t x, int32_t y) { return len[x] > len[y]; });
+  }
+  const int64_t ns = (int64_t)slice_first.size();
+  S.nslices = ns;
+  S.slice_ptr.assign(ns + 1, 0);
+  S.rows.assign(ns * 32, -1);
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t w = 0;
+    for (int l = 0; l < slice_count[s]; ++l) {
+      const int32_t r = order[slice_first[s] + l];
+      S.rows[s * 32 + l] = r;
+      w = std::max(w, len[r]);
+    }
+    S.slice_ptr[s + 1] = S.slice_ptr[s] + 32 * w;
+  }
+  S.col.assign(S.slice_ptr[ns], 0);
+  S.val.assign(S.slice_ptr[ns], make_float2(0.f, 0.f));
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t s = 0; s < ns; ++s) {
+    const int64_t base = S.slice_ptr[s];
+    const int64_t w = (S.slice_ptr[s + 1] - base) / 32;
+    for (int l = 0; l < 32; ++l) {
+      const int32_t r = S.rows[s * 32 + l];
+      const int64_t lr = (r >= 0) ? len[r] : 0;
+      for (int64_t t = 0; t < w; ++t) {
+        const int64_t o = base + 32 * t + l;
+        if (t < lr) {
+          S.col[o] = ci[rp[r] + t];
+          split_df(va[rp[r] + t], S.val[o]);
+        } else {
+          S.col[o] = (r >= 0) ? r : 0;
+        }
+      }
+    }
+  }
+}
+
+sppc_status upload_sell(sppc_ctx* h, const SellHost& S, SellDev& D, int64_t nrows) {
+  int64_t* sp;
+  int32_t *rows, *col;
+  float2* val;
+  CK(dalloc(h, &sp, S.slice_ptr.size()));
+  CK(dalloc(h, &rows, S.rows.size()));
+  CK(dalloc(h, &col, S.col.size()));
+  CK(dalloc(h, &val, S.val.size()));
+  CK(cudaMemcpyAsync(sp, S.slice_ptr.data(), sizeof(int64_t) * S.slice_ptr.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(rows, S.rows.data(), sizeof(int32_t) * S.rows.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(col, S.col.data(), sizeof(int32_t) * S.col.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(val, S.val.data(), sizeof(float2) * S.val.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  D.nslices = S.nslices;
+  D.nrows = nrows;
+  D.slice_ptr = sp;
+  D.slice_rows = rows;
+  D.col = col;
+  D.val = val;
+  return SPPC_OK;
+}
+
+// ---------------------------------------------------------- timing helpers
+cudaEvent_t next_event(sppc_ctx* h) {
+  if (h->evnext >= (int)h->evpool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->evpool.push_back(e);
+  }
+  return h->evpool[h->evnext++];
+}
+
+sppc_status collect_timing(sppc_ctx* h) {
+  for (auto& pr : h->pending) {
+    float ms = 0.f;
+    CK(cudaEventSynchronize(pr.second));
+    CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    h->stats.spmm_ms += ms;
+  }
+  h->pending.clear();
+  h->evnext = 0;
+  return SPPC_OK;
+}
+
+// The big SpMM W_p = H q^(p) (k SpMVs of the order), timed when opts.timing.
+sppc_status big_spmm(sppc_ctx* h, const float2* X, float2* Y, int kp) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->opt.timing) {
+    a = next_event(h);
+    b = next_event(h);
+    CK(cudaEventRecord(a, h->stream));
+  }
+  CK(spmm(h->H, kp, X, Y, Epi{}, h->stream));
+  if (h->opt.timing) {
+    CK(cudaEventRecord(b, h->stream));
+    h->pending.push_back({a, b});
+  }
+  h->stats.spmm_launches += 1;
+  return SPPC_OK;
+}
+
+}  // namespace
+
+// The multi-block helpers below need the full context type.
+namespace {
+
+// ---------------------------------------------------- small-space eigensolve
+// Chebyshev-filtered subspace iteration (Zhou and Saad, 2007) on H0_hat:
+// filter the block with T_d of the interval [cut, upper] mapped to [-1, 1]
+// (damps the unwanted upper spectrum), orthonormalise (shifted CholeskyQR then
+// CholeskyQR2), Rayleigh-Ritz on the block; stop when the k lowest residuals are
+// <= small_tol * ||H0_hat||.  Products with H0_hat use the same SpMM kernel.
+
+// G (b x b, ld 16) = X^T Z for block sets X, Z of nb blocks (8 columns each).
+sppc_status gram_set(sppc_ctx* h, float2** X, float2** Z, int nb, double* G16) {
+  cudaStream_t s = h->stream;
+  BlockList L;
+  L.n = nb;
+  for (int a = 0; a < nb; ++a) L.p[a] = X[a];
+  for (int ob = 0; ob < nb; ++ob) {
+    // out[(a*8+i)*8 + j] for column block ob
+    CK(gram(L, Z[ob], 8, 0, h->n1, h->dGram, h->partials, h->partial_cap, s));
+    // scatter into G16[(a*8+i)*16 + ob*8 + j]
+    for (int a = 0; a < nb; ++a)
+      CK(cudaMemcpy2DAsync(G16 + (a * 8) * 16 + ob * 8, 16 * sizeof(double), h->dGram + a * 64, 8 * sizeof(double),
+                           8 * sizeof(double), 8, cudaMemcpyDeviceToDevice, s));
+  }
+  return SPPC_OK;
+}
+
+// Y_set = X_set * M (M: 16 x 16 double-float, ld 16)
+sppc_status rotate_set(sppc_ctx* h, float2** X, float2** Y, int nb, const float2* M16) {
+  cudaStream_t s = h->stream;
+  BlockList L;
+  L.n = nb;
+  for (int a = 0; a < nb; ++a) L.p[a] = X[a];
+  for (int ob = 0; ob < nb; ++ob) {
+    k_subblock<<<1, 128, 0, s>>>(M16, 16, nb, ob, h->dCoefBig);
+    CK(cudaGetLastError());
+    CK(update(Y[ob], nullptr, nullptr, L, h->dCoefBig, 8, 0, h->n1, s));
+  }
+  return SPPC_OK;
+}
+
+sppc_status ortho_set(sppc_ctx* h, float2** X, float2** Tmp, int nb, int b) {
+  // shifted CholeskyQR, then CholeskyQR twice (result back in X)
+  for (int pass = 0; pass < 3; ++pass) {
+    CKS(gram_set(h, X, X, nb, h->dS));
+    const double shift = (pass == 0) ? 1e-12 : 0.0;
+    CK(chol_rinv(h->dS, 16, b, 16, shift, h->dR1, h->dRinv, h->dStatus, h->stream));
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, h->dStatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (st != 0) return fail(h, SPPC_ERR_BREAKDOWN, "small eigensolve: Cholesky breakdown at column %d", st - 1);
+    CKS(rotate_set(h, X, Tmp, nb, h->dRinv));
+    for (int a = 0; a < nb; ++a) std::swap(X[a], Tmp[a]);
+  }
+  return SPPC_OK;
+}
+
+sppc_status small_eigensolve(sppc_ctx* h) {
+  cudaStream_t s = h->stream;
+  const int64_t n1 = h->n1;
+  const int k = h->k;
+  int b = h->opt.small_block;
+  if (b <= 0) b = std::min(16, std::max(k + 2, 2 * k));
+  b = std::max(b, k + 1);
+  b = std::min<int64_t>(std::min(b, 16), n1);
+  const int nb = (b + 7) / 8;
+  float2* X[2] = {h->se[0], h->se[1]};
+  float2* AX[2] = {h->se[2], h->se[3]};
+  float2* Y0[2] = {h->se[4], h->se[5]};
+  float2* Y1[2] = {h->se[6], h->se[7]};
+  float2* Tmp[2] = {h->se[8], h->se[9]};
+  // seeded normal start block (columns >= b are zero)
+  {
+    std::vector<float2> host((size_t)n1 * 8 * nb, make_float2(0.f, 0.f));
+    const uint64_t seed = h->opt.seed;
+    for (int64_t r = 0; r < n1; ++r)
+      for (int c = 0; c < b; ++c) {
+        const uint64_t idx = (uint64_t)r * 16 + c;
+        const double u1 = ((mix64(seed + (2 * idx + 1) * 0x9E3779B97F4A7C15ULL) >> 11) + 1) * 0x1.0p-53;
+        const double u2 = (mix64(seed + (2 * idx + 2) * 0x9E3779B97F4A7C15ULL) >> 11) * 0x1.0p-53;
+        const double g = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+        split_df(g, host[(size_t)(c / 8) * n1 * 8 + (size_t)r * 8 + (c % 8)]);
+      }
+    for (int a = 0; a < nb; ++a)
+      CK(cudaMemcpyAsync(X[a], host.data() + (size_t)a * n1 * 8, sizeof(float2) * n1 * 8, cudaMemcpyHostToDevice, s));
+  }
+  CKS(ortho_set(h, X, Tmp, nb, b));
+  const double upper = h->h11_hi;
+  std::vector<double> th(16), res(16);
+  const int degree = 12;
+  int outer = 0;
+  for (; outer < 400; ++outer) {
+    // Rayleigh-Ritz on the block
+    for (int a = 0; a < nb; ++a) CK(spmm(h->H11, 8, X[a], AX[a], Epi{}, s));
+    h->stats.spmv_h11 += 8 * nb;
+    CKS(gram_set(h, X, AX, nb, h->dS));
+    CK(syev_lowest(h->dS, 16, b, b, h->dTheta, h->dV, b, s));
+    k_vmat_df<<<1, 256, 0, s>>>(h->dV, b, b, b, h->dRinv);
+    CK(cudaGetLastError());
+    CKS(rotate_set(h, X, Tmp, nb, h->dRinv));
+    for (int a = 0; a < nb; ++a) std::swap(X[a], Tmp[a]);
+    CKS(rotate_set(h, AX, Tmp, nb, h->dRinv));
+    for (int a = 0; a < nb; ++a) std::swap(AX[a], Tmp[a]);
+    CK(cudaMemcpyAsync(th.data(), h->dTheta, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // residuals of the k lowest: D = AX - X theta (block 0 holds columns 0..7)
+    std::vector<float2> thdf(8);
+    for (int c = 0; c < 8; ++c) {
+      const double v = (c < b) ? -th[c] : 0.0;
+      thdf[c].x = (float)v;
+      thdf[c].y = (float)(v - (double)thdf[c].x);
+    }
+    CK(cudaMemcpyAsync(h->dCoef + kTheta, thdf.data(), sizeof(float2) * 8, cudaMemcpyHostToDevice, s));
+    CK(combine_diag(Tmp[0], AX[0], h->dCoef + kOnes, one(X[0]), h->dCoef + kTheta, 8, 0, n1, s));
+    const float2* A1[1] = {Tmp[0]};
+    const float2* B1[1] = {Tmp[0]};
+    CK(coldots(A1, B1, 1, 8, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    CK(cudaMemcpyAsync(res.data(), h->dDots, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double worst = 0.0;
+    for (int c = 0; c < k; ++c) worst = std::max(worst, std::sqrt(std::max(res[c], 0.0)));
+    if (worst <= h->opt.small_tol * h->h11_norm) break;
+    // Chebyshev filter on [cut, upper]
+    const double cut = th[b - 1];
+    if (!(upper > cut)) return fail(h, SPPC_ERR_BREAKDOWN, "small eigensolve: empty filter interval");
+    const double e = 0.5 * (upper - cut), c = 0.5 * (upper + cut);
+    auto put3 = [&](double al, double be, double ga) -> sppc_status {
+      std::vector<float2> v(48);
+      for (int j = 0; j < 16; ++j) {
+        split_df(al, v[j]);
+        split_df(be, v[16 + j]);
+        split_df(ga, v[32 + j]);
+      }
+      CK(cudaMemcpyAsync(h->dCoef + kCheb, v.data(), sizeof(float2) * 48, cudaMemcpyHostToDevice, s));
+      return SPPC_OK;
+    };
+    // Y1 = (A X - c X)/e
+    CKS(put3(1.0 / e, -c / e, 0.0));
+    Epi e1;
+    e1.alpha = h->dCoef + kCheb;
+    e1.beta = h->dCoef + kCheb + 16;
+    for (int a = 0; a < nb; ++a) CK(spmm(h->H11, 8, X[a], Y1[a], e1, s));
+    CKS(put3(2.0 / e, -2.0 * c / e, -1.0));
+    float2* setA[2] = {X[0], X[1]};
+    float2* setB[2] = {Y1[0], Y1[1]};
+    float2* setC[2] = {Y0[0], Y0[1]};
+    for (int dgi = 2; dgi <= degree; ++dgi) {
+      Epi e2;
+      e2.alpha = h->dCoef + kCheb;
+      e2.beta = h->dCoef + kCheb + 16;
+      e2.gamma = h->dCoef + kCheb + 32;
+      for (int a = 0; a < nb; ++a) {
+        e2.Z = setA[a];
+        CK(spmm(h->H11, 8, setB[a], setC[a], e2, s));
+      }
+      for (int a = 0; a < nb; ++a) {
+        float2* t0 = setA[a];
+        setA[a] = setB[a];
+        setB[a] = setC[a];
+        setC[a] = t0;
+      }
+    }
+    h->stats.spmv_h11 += (int64_t)8 * nb * degree;
+    h->stats.small_eig_iters += degree;
+    // new X = setB (the last filtered block); keep the buffers distinct
+    for (int a = 0; a < nb; ++a) {
+      X[a] = setB[a];
+      // the remaining two buffers become AX / Tmp / filter scratch
+    }
+    {
+      // re-assign scratch buffers so that none aliases X
+      std::vector<float2*> pool;
+      for (int i = 0; i < 10; ++i) pool.push_back(h->se[i]);
+      std::vector<float2*> freeb;
+      for (float2* q : pool) {
+        bool used = false;
+        for (int a = 0; a < nb; ++a) used |= (q == X[a]);
+        if (!used) freeb.push_back(q);
+      }
+      int fi = 0;
+      for (int a = 0; a < nb; ++a) AX[a] = freeb[fi++];
+      for (int a = 0; a < nb; ++a) Y0[a] = freeb[fi++];
+      for (int a = 0; a < nb; ++a) Y1[a] = freeb[fi++];
+      for (int a = 0; a < nb; ++a) Tmp[a] = freeb[fi++];
+    }
+    CKS(ortho_set(h, X, Tmp, nb, b));
+  }
+  if (outer >= 400) return fail(h, SPPC_ERR_BREAKDOWN, "small eigensolve did not converge");
+  // psi_hat = first k columns (block 0), padded to kp
+  h->E0.assign(th.begin(), th.begin() + k);
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < j; ++i)
+      if (std::fabs(h->E0[i] - h->E0[j]) <= h->opt.degeneracy_tol * h->h11_norm)
+        return fail(h, SPPC_ERR_ARG, "degenerate small-space eigenvalues E_%d ~ E_%d are not supported", i, j);
+  if (b > k && std::fabs(th[k] - h->E0[k - 1]) <= h->opt.degeneracy_tol * h->h11_norm)
+    return fail(h, SPPC_ERR_ARG, "E_k of the small space is degenerate with E_(k+1)");
+  for (int j = 0; j < k; ++j)
+    if (std::fabs(h->E0[j]) <= 1e-8 * h->h11_norm)
+      return fail(h, SPPC_ERR_ARG, "E^(0)_%d is zero: x2 = -b2/E^(0) is undefined", j);
+  // copy columns 0..k-1 of X[0] (n1 x 8) into psi_hat (n1 x kp)
+  CK(cudaMemcpy2DAsync(h->psi_hat, sizeof(float2) * h->kp, X[0], sizeof(float2) * 8, sizeof(float2) * h->kp, n1,
+                       cudaMemcpyDeviceToDevice, s));
+  if (k < h->kp) {
+    // zero the padding columns
+    std::vector<float2> z((size_t)(h->kp - k), make_float2(0.f, 0.f));
+    CK(cudaMemset2DAsync(h->psi_hat + k, sizeof(float2) * h->kp, 0, sizeof(float2) * (h->kp - k), n1, s));
+  }
+  std::vector<double> e0p(h->kp, 0.0);
+  for (int j = 0; j < k; ++j) e0p[j] = h->E0[j];
+  CK(cudaMemcpyAsync(h->dE, e0p.data(), sizeof(double) * h->kp, cudaMemcpyHostToDevice, s));
+  k_set_e0<<<1, 32, 0, s>>>(h->dE, k, h->kp, h->dCoef);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return SPPC_OK;
+}
+
+// ----------------------------------------------------------------- MINRES
+// Solves (H0_hat - E_k) x = b1 for the k columns at once on the complement of
+// psi_hat_k (Eq. sm_lin_proj): the right-hand side is already deflated and every
+// new Lanczos vector is projected against psi_hat_k, so the singular direction
+// never enters the Krylov space.  x0 = 0; stop at ||r|| <= minres_tol ||b1||.
+sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
+  cudaStream_t s = h->stream;
+  const int kp = h->kp;
+  const int64_t n1 = h->n1;
+  float2* c = h->dCoef;
+  {
+    const float2* A[1] = {h->b1};
+    const float2* B[1] = {h->b1};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+  }
+  k_minres_init<<<1, 32, 0, s>>>(h->dDots, h->k, kp, h->dMin, c);
+  CK(cudaGetLastError());
+  float2 *v = h->mv, *vprev = h->mvprev, *p = h->mp, *y = h->my, *w1 = h->mw1, *w2 = h->mw2, *x = h->mx;
+  CK(combine_diag(v, h->b1, c + kMinV, BlockList{}, c, kp, 0, n1, s));
+  CK(fill_zero(vprev, n1 * kp, s));
+  CK(fill_zero(w1, n1 * kp, s));
+  CK(fill_zero(w2, n1 * kp, s));
+  CK(fill_zero(x, n1 * kp, s));
+  int maxit = h->opt.minres_maxit;
+  if (maxit <= 0) maxit = (int)std::min<int64_t>(200000, 20 * n1);
+  std::vector<int> flags(kp, 0);
+  int* dflags = h->dStatus + 4;
+  int it = 0;
+  bool all_done = false;
+  for (it = 1; it <= maxit; ++it) {
+    Epi e;
+    e.beta = c + kShiftNegE;
+    CK(spmm(h->H11, kp, v, y, e, s));
+    {
+      const float2* A[4] = {v, h->psi_hat, v, v};
+      const float2* B[4] = {y, y, h->psi_hat, vprev};
+      CK(coldots(A, B, 4, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    }
+    k_minres_a<<<1, 32, 0, s>>>(h->dDots, kp, h->dMin, c);
+    CK(cudaGetLastError());
+    {
+      BlockList L;
+      L.n = 3;
+      L.p[0] = h->psi_hat;
+      L.p[1] = vprev;
+      L.p[2] = v;
+      CK(combine_diag(p, y, c + kOnes, L, c + kMinA, kp, 0, n1, s));
+    }
+    {
+      const float2* A[1] = {p};
+      const float2* B[1] = {p};
+      CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    }
+    k_minres_b<<<1, 32, 0, s>>>(h->dDots, kp, h->opt.minres_tol, h->dMin, c, dflags);
+    CK(cudaGetLastError());
+    {
+      BlockList L;
+      L.n = 2;
+      L.p[0] = w2;
+      L.p[1] = w1;
+      CK(combine_diag(w2, v, c + kMinWAlpha, L, c + kMinW, kp, 0, n1, s));  // w_new into w2's buffer
+      std::swap(w1, w2);                                                    // w1 = w_new, w2 = old w1
+      CK(combine_diag(x, x, c + kOnes, one(w1), c + kMinX, kp, 0, n1, s));
+      CK(combine_diag(vprev, p, c + kMinV, BlockList{}, c, kp, 0, n1, s));  // v_next into vprev's buffer
+      std::swap(v, vprev);                                                   // v = v_next, vprev = old v
+    }
+    h->stats.spmv_h11 += h->k;
+    if ((it & 7) == 0 || it == maxit) {
+      CK(cudaMemcpyAsync(flags.data(), dflags, sizeof(int) * kp, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      all_done = true;
+      for (int j = 0; j < h->k; ++j) all_done &= (flags[j] != 0);
+      if (all_done) break;
+    }
+  }
+  // x -= psi_hat (psi_hat^T x): keep the solution on the complement of psi_hat_k
+  {
+    const float2* A[1] = {h->psi_hat};
+    const float2* B[1] = {x};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, h->k, kp, c + kDefl);
+    CK(cudaGetLastError());
+    CK(combine_diag(x, x, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
+  }
+  std::vector<int> its(kp, 0);
+  k_minres_iters<<<1, 32, 0, s>>>(h->dMin, kp, h->dStatus + 16);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(its.data(), h->dStatus + 16, sizeof(int) * kp, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  iters.assign(h->k, 0);
+  int mx = 0;
+  for (int j = 0; j < h->k; ++j) {
+    iters[j] = its[j];
+    mx = std::max(mx, its[j]);
+  }
+  h->stats.minres_iters += mx;
+  if (!all_done) return fail(h, SPPC_ERR_MINRES, "MINRES reached %d iterations without meeting the tolerance", maxit);
+  // copy x into the leading n1 rows of Psi^(p)
+  return SPPC_OK;
+}
+
+// ------------------------------------------------------- Rayleigh-Ritz core
+sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz) {
+  cudaStream_t s = h->stream;
+  const int k = h->k, kp = h->kp;
+  const int64_t n = h->n;
+  // border B = Q_{0..p}^T W_p (Eq. proj)
+  CK(gram(blocks(h->Q, n, kp, 0, p + 1), blk(h->W, n, kp, p), kp, 0, n, h->dGram, h->partials, h->partial_cap, s));
+  k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, p, k, kp, h->dHt, h->mmax);
+  CK(cudaGetLastError());
+  const int m = (p + 1) * k;
+  CK(syev_lowest(h->dHt, h->mmax, m, k, h->dTheta, h->dV, k, s));
+  k_expand_y<<<1, 256, 0, s>>>(h->dV, p, k, kp, h->dTheta, h->dY, h->dCoef + kTheta);
+  CK(cudaGetLastError());
+  CK(ritz_resid(blocks(h->Q, n, kp, 0, p + 1), blocks(h->W, n, kp, 0, p + 1), h->dY, h->dCoef + kTheta, kp, n,
+                h->dDots, h->partials, h->partial_cap, want_z ? Z : nullptr, ldz, k, s));
+  std::vector<double> th(k), r2(kp);
+  CK(cudaMemcpyAsync(th.data(), h->dTheta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(r2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->theta = th;
+  h->resid.assign(k, 0.0);
+  for (int j = 0; j < k; ++j) h->resid[j] = std::sqrt(std::max(r2[j], 0.0)) / std::fabs(th[j]);
+  return SPPC_OK;
+}
+
+bool all_converged(const sppc_ctx* h, double tol) {
+  for (double r : h->resid)
+    if (!(r <= tol)) return false;
+  return true;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void sppc_default_opts(sppc_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->p_max = 15;
+  o->tol = 1e-6;
+  o->minres_tol = 1e-12;
+  o->minres_maxit = 0;
+  o->small_tol = 1e-12;
+  o->small_block = 0;
+  o->degeneracy_tol = 1e-10;
+  o->check_symmetry = 0;
+  o->seed = 0;
+  o->timing = 0;
+}
+
+const char* sppc_last_error(sppc_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+sppc_status sppc_destroy(sppc_handle h) {
+  if (!h) return SPPC_OK;
+  for (void* p : h->allocs) cudaFree(p);
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  delete h;
+  return SPPC_OK;
+}
+
+sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_t n_levels, int64_t n1, int32_t k,
+                        const sppc_opts* opts, void* stream, sppc_handle* out) {
+  sppc_ctx* h = nullptr;
+  if (!out) return fail(nullptr, SPPC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!Hc || !level_offsets) return fail(nullptr, SPPC_ERR_ARG, "H or level_offsets is NULL");
+  if (Hc->n <= 0 || Hc->nnz < 0 || !Hc->row_ptr || (Hc->nnz > 0 && (!Hc->col || !Hc->val)))
+    return fail(nullptr, SPPC_ERR_ARG, "malformed CSR descriptor");
+  if (Hc->n >= ((int64_t)1 << 31) - 64) return fail(nullptr, SPPC_ERR_ARG, "n must be below 2^31");
+  if (k < 1 || k > 8) return fail(nullptr, SPPC_ERR_ARG, "k must be in [1, 8], got %d", k);
+  if (n_levels < 1) return fail(nullptr, SPPC_ERR_LEVELS, "n_levels must be >= 1");
+  const int64_t n = Hc->n;
+  if (level_offsets[0] != 0 || level_offsets[n_levels] != n)
+    return fail(nullptr, SPPC_ERR_LEVELS, "level_offsets must run from 0 to n");
+  bool n1_ok = false;
+  for (int i = 0; i < n_levels; ++i) {
+    if (level_offsets[i + 1] <= level_offsets[i]) return fail(nullptr, SPPC_ERR_LEVELS, "level_offsets not increasing");
+    if (level_offsets[i + 1] == n1) n1_ok = true;
+  }
+  if (!n1_ok) return fail(nullptr, SPPC_ERR_LEVELS, "n1 = %lld is not a level boundary", (long long)n1);
+  if (k >= n1) return fail(nullptr, SPPC_ERR_ARG, "k must be smaller than n1");
+  sppc_opts opt;
+  sppc_default_opts(&opt);
+  if (opts) opt = *opts;
+  if (opt.p_max < 0 || opt.p_max > kMaxBlocks - 2 || (int64_t)k * (opt.p_max + 1) > 144)
+    return fail(nullptr, SPPC_ERR_ARG, "p_max out of range (k*(p_max+1) must be <= 144)");
+
+  h = new sppc_ctx();
+  h->opt = opt;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->n = n;
+  h->nnz = Hc->nnz;
+  h->n1 = n1;
+  h->k = k;
+  h->kp = (k + 1) / 2 * 2;
+  h->pmax = opt.p_max;
+  h->mmax = k * (opt.p_max + 1);
+  h->lev.assign(level_offsets, level_offsets + n_levels + 1);
+  auto bail = [&](sppc_status st) {
+    g_create_error = h->err;
+    sppc_destroy(h);
+    return st;
+  };
+  // host copy of the CSR if needed
+  std::vector<int64_t> rp_h;
+  std::vector<int32_t> ci_h;
+  std::vector<double> va_h;
+  const int64_t* rp = Hc->row_ptr;
+  const int32_t* ci = Hc->col;
+  const double* va = Hc->val;
+  if (Hc->on_device) {
+    rp_h.resize(n + 1);
+    ci_h.resize(Hc->nnz);
+    va_h.resize(Hc->nnz);
+    if (cudaMemcpy(rp_h.data(), rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(ci_h.data(), ci, sizeof(int32_t) * Hc->nnz, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(va_h.data(), va, sizeof(double) * Hc->nnz, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bail(fail(h, SPPC_ERR_CUDA, "copying the device CSR to the host failed"));
+    rp = rp_h.data();
+    ci = ci_h.data();
+    va = va_h.data();
+  }
+  // validation
+  if (rp[0] != 0 || rp[n] != Hc->nnz) return bail(fail(h, SPPC_ERR_ARG, "row_ptr[0] must be 0 and row_ptr[n] = nnz"));
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int64_t r = 0; r < n; ++r) {
+    if (rp[r + 1] < rp[r]) {
+      bad |= 1;
+      continue;
+    }
+    for (int64_t t = rp[r]; t < rp[r + 1]; ++t) {
+      if (ci[t] < 0 || ci[t] >= n) bad |= 2;
+      if (t > rp[r] && ci[t] <= ci[t - 1]) bad |= 4;
+      if (!std::isfinite(va[t])) bad |= 8;
+    }
+  }
+  if (bad & 1) return bail(fail(h, SPPC_ERR_ARG, "row_ptr is not monotone"));
+  if (bad & 2) return bail(fail(h, SPPC_ERR_ARG, "column index out of range"));
+  if (bad & 4) return bail(fail(h, SPPC_ERR_ARG, "column indices must increase strictly within a row"));
+  if (bad & 8) return bail(fail(h, SPPC_ERR_NAN, "H holds a NaN or Inf"));
+  if (opt.check_symmetry) {
+    int asym = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(| : asym)
+    for (int64_t r = 0; r < n; ++r) {
+      for (int64_t t = rp[r]; t < rp[r + 1]; ++t) {
+        const int32_t c = ci[t];
+        const int32_t* b = ci + rp[c];
+        const int32_t* e = ci + rp[c + 1];
+        const int32_t* f = std::lower_bound(b, e, (int32_t)r);
+        if (f == e || *f != r || va[rp[c] + (f - b)] != va[t]) asym = 1;
+      }
+    }
+    if (asym) return bail(fail(h, SPPC_ERR_NOT_SYMMETRIC, "H is not symmetric"));
+  }
+  // Gershgorin interval of H0_hat
+  {
+    double lo = 1e300, hi = -1e300;
+#pragma omp parallel for reduction(min : lo) reduction(max : hi)
+    for (int64_t r = 0; r < n1; ++r) {
+      double dg = 0.0, off = 0.0;
+      for (int64_t t = rp[r]; t < rp[r + 1] && ci[t] < n1; ++t) {
+        if (ci[t] == r)
+          dg = va[t];
+        else
+          off += std::fabs(va[t]);
+      }
+      lo = std::min(lo, dg - off);
+      hi = std::max(hi, dg + off);
+    }
+    h->h11_lo = lo;
+    h->h11_hi = hi;
+    h->h11_norm = std::max(std::fabs(lo), std::fabs(hi));
+  }
+  // layouts
+  {
+    SellHost S;
+    std::vector<int64_t> seg(h->lev.begin(), h->lev.end());
+    build_sell(n, rp, ci, va, (int64_t)1 << 31, seg, 1024, S);
+    sppc_status st = upload_sell(h, S, h->H, n);
+    if (st != SPPC_OK) return bail(st);
+    h->h_slices = S.nslices;
+    h->h_slice_ptr = std::move(S.slice_ptr);
+    h->h_slice_rows = std::move(S.rows);
+  }
+  {
+    SellHost S;
+    std::vector<int64_t> seg = {0, n1};
+    build_sell(n1, rp, ci, va, n1, seg, 1024, S);
+    sppc_status st = upload_sell(h, S, h->H11, n1);
+    if (st != SPPC_OK) return bail(st);
+    h->h11_slices = S.nslices;
+    h->h11_slice_ptr = std::move(S.slice_ptr);
+    h->h11_slice_rows = std::move(S.rows);
+  }
+  // work buffers
+  {
+    const int kp = h->kp;
+    const int64_t nb = (int64_t)(h->pmax + 1) * n * kp;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](float2** p, size_t c) {
+      if (e == cudaSuccess) e = dalloc(h, p, c);
+    };
+    auto D = [&](double** p, size_t c) {
+      if (e == cudaSuccess) e = dalloc(h, p, c);
+    };
+    A(&h->Q, nb);
+    A(&h->W, nb);
+    A(&h->Psi, nb);
+    A(&h->HPsi, (size_t)n * kp);
+    A(&h->T1, (size_t)n * 8);
+    A(&h->T2, (size_t)n * 8);
+    for (float2** q : {&h->psi_hat, &h->vps, &h->b1, &h->mv, &h->mvprev, &h->mp, &h->my, &h->mw1, &h->mw2, &h->mx})
+      A(q, (size_t)n1 * kp);
+    for (int i = 0; i < 12; ++i) A(&h->se[i], (size_t)n1 * 8);
+    D(&h->dE, (size_t)(kMaxBlocks + 2) * 8);
+    D(&h->dHt, (size_t)h->mmax * h->mmax);
+    D(&h->dGram, (size_t)kMaxBlocks * 64);
+    D(&h->dC1, (size_t)kMaxBlocks * 64);
+    D(&h->dC2, (size_t)kMaxBlocks * 64);
+    D(&h->dR1, 256);
+    D(&h->dR2, 256);
+    D(&h->dTheta, 16);
+    D(&h->dV, 144 * 16);
+    D(&h->dDots, 64);
+    D(&h->dS, 256);
+    A(&h->dCoef, kCoefEnd);
+    A(&h->dRinv, 256);
+    A(&h->dRecycle, (size_t)kMaxBlocks * 64);
+    A(&h->dY, (size_t)kMaxBlocks * 64);
+    A(&h->dCoefBig, (size_t)kMaxBlocks * 64);
+    if (e == cudaSuccess) e = dalloc(h, &h->dMin, 16);
+    if (e == cudaSuccess) e = dalloc(h, &h->dStatus, 64);
+    h->partial_cap = ((n + 2047) / 2048 + 1) * (int64_t)kMaxBlocks * 64;
+    A(&h->partials, (size_t)h->partial_cap);
+    if (e != cudaSuccess)
+      return bail(fail(h, e == cudaErrorMemoryAllocation ? SPPC_ERR_OOM : SPPC_ERR_CUDA, "allocation failed: %s",
+                       cudaGetErrorString(e)));
+    k_set_consts<<<1, 32, 0, h->stream>>>(h->dCoef);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dHt, 0, sizeof(double) * h->mmax * h->mmax, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_CUDA, "init failed: %s", cudaGetErrorString(e)));
+  }
+  *out = h;
+  return SPPC_OK;
+}
+
+sppc_status sppc_spmm(sppc_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t ncols,
+                      void* stream) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (!X || !Y || ncols < 1 || ncols > 8 || ldx < ncols || ldy < ncols)
+    return fail(h, SPPC_ERR_ARG, "sppc_spmm: bad arguments (ncols in [1,8], ld >= ncols)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->stream = s;
+  const int kp = (ncols + 1) / 2 * 2;
+  CK(f64_to_df(X, ldx, ncols, h->T1, kp, 0, h->n, s));
+  CKS(big_spmm(h, h->T1, h->T2, kp));
+  CK(df_to_f64(h->T2, kp, Y, ldy, ncols, 0, h->n, s));
+  return SPPC_OK;
+}
+
+sppc_status sppc_spmm_host(sppc_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t ncols,
+                           void* stream) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (!X || !Y || ncols < 1 || ncols > 8 || ldx < ncols || ldy < ncols)
+    return fail(h, SPPC_ERR_ARG, "sppc_spmm_host: bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->stream = s;
+  if (!h->stageX) {
+    CK(dalloc(h, &h->stageX, (size_t)h->n * 8));
+    CK(dalloc(h, &h->stageY, (size_t)h->n * 8));
+  }
+  double* dX = h->stageX;
+  double* dY = h->stageY;
+  CK(cudaMemcpy2DAsync(dX, sizeof(double) * ncols, X, sizeof(double) * ldx, sizeof(double) * ncols, h->n,
+                       cudaMemcpyHostToDevice, s));
+  CKS(sppc_spmm(h, dX, ncols, dY, ncols, ncols, stream));
+  CK(cudaMemcpy2DAsync(Y, sizeof(double) * ldy, dY, sizeof(double) * ncols, sizeof(double) * ncols, h->n,
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SPPC_OK;
+}
+
+sppc_status sppc_start(sppc_handle h, double* theta, double* resid, void* stream) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->stream = s;
+  h->stats = sppc_stats{};
+  h->rec.clear();
+  h->p = 0;
+  h->started = false;
+  h->corrected = false;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (h->opt.timing) {
+    t0 = next_event(h);
+    t1 = next_event(h);
+    CK(cudaEventRecord(t0, s));
+  }
+  CKS(small_eigensolve(h));
+  if (h->opt.timing) {
+    CK(cudaEventRecord(t1, s));
+    CK(cudaEventSynchronize(t1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, t0, t1));
+    h->stats.small_eig_ms += ms;
+    h->evnext = 0;
+  }
+  const int kp = h->kp;
+  const int64_t n = h->n;
+  // Q^(0) = Psi^(0) = [psi_hat; 0] (Eq. EP_small), W_0 = H Q^(0)
+  CK(fill_zero(h->Q, n * kp, s));
+  CK(cudaMemcpyAsync(h->Q, h->psi_hat, sizeof(float2) * h->n1 * kp, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->Psi, h->Q, sizeof(float2) * n * kp, cudaMemcpyDeviceToDevice, s));
+  CKS(big_spmm(h, h->Q, h->W, kp));
+  h->stats.spmv_h += h->k;
+  CKS(rr_core(h, 0, false, nullptr, 0));
+  // H Psi^(0) = W_0
+  CK(cudaMemcpyAsync(h->HPsi, h->W, sizeof(float2) * n * kp, cudaMemcpyDeviceToDevice, s));
+  OrderRec r;
+  r.E = h->E0;
+  r.theta = h->theta;
+  r.resid = h->resid;
+  h->rec.push_back(r);
+  if (h->opt.timing) CKS(collect_timing(h));
+  h->started = true;
+  if (theta) std::copy(h->theta.begin(), h->theta.end(), theta);
+  if (resid) std::copy(h->resid.begin(), h->resid.end(), resid);
+  return SPPC_OK;
+}
+
+sppc_status sppc_correct(sppc_handle h, void* stream) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (!h->started || h->corrected) return fail(h, SPPC_ERR_STATE, "sppc_correct needs sppc_start / rayleigh_ritz first");
+  if (h->p + 1 > h->pmax) return fail(h, SPPC_ERR_STATE, "p_max orders already done");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->stream = s;
+  const int p = h->p + 1;
+  const int k = h->k, kp = h->kp;
+  const int64_t n = h->n, n1 = h->n1;
+  float2* c = h->dCoef;
+  float2* Psip = blk(h->Psi, n, kp, p);
+  float2* Psim1 = blk(h->Psi, n, kp, p - 1);
+  OrderRec rec;
+  // coefficients of Eq. exp_seq2 need E^(p); compute the small-space part first
+  // V Psi^(p-1)_1 = (H Psi^(p-1))_1 - H0_hat Psi^(p-1)_1  (Eq. avoid_SpMV2)
+  {
+    Epi e;
+    e.alpha = c + kNegOnes;
+    e.gamma = c + kOnes;
+    e.Z = h->HPsi;
+    CK(spmm(h->H11, kp, Psim1, h->vps, e, s));
+    h->stats.spmv_h11 += k;
+  }
+  // E^(p) = psi_hat^T (V Psi^(p-1))_1 = (Psi^(p-1))^T V Psi^(0) (Eq. exp_seq, V symmetric)
+  {
+    const float2* A[1] = {h->psi_hat};
+    const float2* B[1] = {h->vps};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dE + (size_t)p * kp, h->partials, h->partial_cap, s));
+  }
+  k_rhs_coefs<<<1, 32, 0, s>>>(h->dE, p, k, kp, c);
+  CK(cudaGetLastError());
+  // rows >= n1: Psi^(p)_2 = -b2 / E^(0) (Eq. sm_first)
+  {
+    BlockList L;
+    L.n = 0;
+    for (int l = 1; l <= p - 2; ++l) L.p[L.n++] = blk(h->Psi, n, kp, l);
+    CK(combine_diag(Psip, h->HPsi, c + kInvE0, L, c + kRhsBig, kp, n1, n, s));
+  }
+  // rows < n1: b1 = -V Psi^(p-1)_1 + E^(p) psi_hat + sum_{l=1}^{p-2} E^(p-l) Psi^(l)_1
+  {
+    BlockList L;
+    L.n = 0;
+    L.p[L.n++] = h->psi_hat;
+    for (int l = 1; l <= p - 2; ++l) L.p[L.n++] = blk(h->Psi, n, kp, l);
+    CK(combine_diag(h->b1, h->vps, c + kNegOnes, L, c + kRhsSmall, kp, 0, n1, s));
+  }
+  // deflate psi_hat_k (Eq. sm_lin_proj)
+  {
+    const float2* A[1] = {h->psi_hat};
+    const float2* B[1] = {h->b1};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl);
+    CK(cudaGetLastError());
+    CK(combine_diag(h->b1, h->b1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
+  }
+  // small solves (H0_hat - E_k^(0)) x1 = b1; at p = 1 b1 = 0 since V11 = 0 (Eq. first_PC)
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (h->opt.timing) {
+    t0 = next_event(h);
+    t1 = next_event(h);
+    CK(cudaEventRecord(t0, s));
+  }
+  if (p == 1) {
+    CK(fill_zero(Psip, n1 * kp, s));
+    rec.iters.assign(k, 0);
+  } else {
+    CKS(minres(h, rec.iters));
+    CK(cudaMemcpyAsync(Psip, h->mx, sizeof(float2) * n1 * kp, cudaMemcpyDeviceToDevice, s));
+  }
+  if (h->opt.timing) {
+    CK(cudaEventRecord(t1, s));
+    CK(cudaEventSynchronize(t1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, t0, t1));
+    h->stats.minres_ms += ms;
+  }
+  // block Gram-Schmidt, projector applied twice (Eq. blkGS)
+  BlockList Qs = blocks(h->Q, n, kp, 0, p);
+  const int nc = p * kp * kp;
+  CK(gram(Qs, Psip, kp, 0, n, h->dC1, h->partials, h->partial_cap, s));
+  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig);
+  CK(cudaGetLastError());
+  CK(update(h->T1, Psip, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
+  CK(gram(Qs, h->T1, kp, 0, n, h->dC2, h->partials, h->partial_cap, s));
+  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig);
+  CK(cudaGetLastError());
+  CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
+  k_addmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, h->dC2, nc, h->dC1);  // C = C1 + C2
+  CK(cudaGetLastError());
+  // angle diagnostics ||Phi_j|| / ||Psi_j^(p)||
+  {
+    const float2* A[2] = {Psip, h->T1};
+    const float2* B[2] = {Psip, h->T1};
+    CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+  }
+  std::vector<double> dd(2 * kp);
+  CK(cudaMemcpyAsync(dd.data(), h->dDots, sizeof(double) * 2 * kp, cudaMemcpyDeviceToHost, s));
+  // CholeskyQR2: Phi = q R (Eq. QR)
+  float2* q = blk(h->Q, n, kp, p);
+  CK(gram(one(h->T1), h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
+  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR1, h->dRinv, h->dStatus, s));
+  CK(update(h->T2, nullptr, nullptr, one(h->T1), h->dRinv, kp, 0, n, s));
+  CK(gram(one(h->T2), h->T2, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
+  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR2, h->dRinv, h->dStatus + 1, s));
+  CK(update(q, nullptr, nullptr, one(h->T2), h->dRinv, kp, 0, n, s));
+  // recycle coefficients [C; R2 R1] for H Psi^(p) (Eq. HPsip)
+  k_recycle_coefs<<<1, 256, 0, s>>>(h->dC1, p, kp, h->dR2, h->dR1, h->dRecycle);
+  CK(cudaGetLastError());
+  int st[2] = {0, 0};
+  CK(cudaMemcpyAsync(st, h->dStatus, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  std::vector<double> ep(kp);
+  CK(cudaMemcpyAsync(ep.data(), h->dE + (size_t)p * kp, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st[0] || st[1])
+    return fail(h, SPPC_ERR_BREAKDOWN, "CholeskyQR breakdown at order %d (rank-deficient correction block)", p);
+  rec.E.assign(ep.begin(), ep.begin() + k);
+  rec.angle.resize(k);
+  for (int j = 0; j < k; ++j) rec.angle[j] = std::sqrt(std::max(dd[kp + j], 0.0) / std::max(dd[j], 1e-300));
+  h->rec.push_back(rec);
+  h->p = p;
+  h->corrected = true;
+  return SPPC_OK;
+}
+
+sppc_status sppc_rayleigh_ritz(sppc_handle h, double* theta, double* resid, void* stream) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (!h->corrected) return fail(h, SPPC_ERR_STATE, "sppc_rayleigh_ritz needs sppc_correct first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->stream = s;
+  const int p = h->p, kp = h->kp;
+  const int64_t n = h->n;
+  // W_p = H q^(p): the k SpMVs of the order
+  CKS(big_spmm(h, blk(h->Q, n, kp, p), blk(h->W, n, kp, p), kp));
+  h->stats.spmv_h += h->k;
+  CKS(rr_core(h, p, false, nullptr, 0));
+  // H Psi^(p) = W_{0..p-1} C + W_p R (Eq. HPsip)
+  CK(update(h->HPsi, nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dRecycle, kp, 0, n, s));
+  OrderRec& r = h->rec.back();
+  r.theta = h->theta;
+  r.resid = h->resid;
+  h->corrected = false;
+  h->stats.orders = p;
+  if (h->opt.timing) CKS(collect_timing(h));
+  if (theta) std::copy(h->theta.begin(), h->theta.end(), theta);
+  if (resid) std::copy(h->resid.begin(), h->resid.end(), resid);
+  return SPPC_OK;
+}
+
+sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, double* Z, int64_t ldz,
+                       double* resid, sppc_stats* stats, void* stream) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (tol <= 0) tol = h->opt.tol;
+  if (p_max < 0) p_max = h->pmax;
+  if (p_max > h->pmax) return fail(h, SPPC_ERR_ARG, "p_max exceeds the p_max given at create");
+  if (Z && ldz < h->k) return fail(h, SPPC_ERR_ARG, "ldz < k");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (h->opt.timing) {
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventRecord(t0, s);
+  }
+  CKS(sppc_start(h, nullptr, nullptr, stream));
+  bool conv = all_converged(h, tol);
+  while (!conv && h->p < p_max) {
+    CKS(sppc_correct(h, stream));
+    CKS(sppc_rayleigh_ritz(h, nullptr, nullptr, stream));
+    conv = all_converged(h, tol);
+  }
+  if (Z) CKS(rr_core(h, h->p, true, Z, ldz));
+  h->stats.converged = conv ? 1 : 0;
+  h->stats.orders = h->p;
+  if (h->opt.timing) {
+    cudaEventRecord(t1, s);
+    cudaEventSynchronize(t1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    h->stats.total_ms = ms;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    h->stats.dense_ms = h->stats.total_ms - h->stats.spmm_ms - h->stats.minres_ms - h->stats.small_eig_ms;
+  }
+  if (theta) std::copy(h->theta.begin(), h->theta.end(), theta);
+  if (resid) std::copy(h->resid.begin(), h->resid.end(), resid);
+  if (stats) *stats = h->stats;
+  return conv ? SPPC_OK : SPPC_NOT_CONVERGED;
+}
+
+sppc_status sppc_order_info(sppc_handle h, int32_t p, double* E, double* angle, double* theta, double* resid,
+                            int32_t* minres_iters) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (p < 0 || p >= (int)h->rec.size()) return fail(h, SPPC_ERR_ARG, "order %d not available", p);
+  const OrderRec& r = h->rec[p];
+  const int k = h->k;
+  auto cp = [&](const std::vector<double>& v, double* o) {
+    if (!o) return;
+    for (int j = 0; j < k; ++j) o[j] = j < (int)v.size() ? v[j] : 0.0;
+  };
+  cp(r.E, E);
+  cp(r.angle, angle);
+  cp(r.theta, theta);
+  cp(r.resid, resid);
+  if (minres_iters)
+    for (int j = 0; j < k; ++j) minres_iters[j] = j < (int)r.iters.size() ? r.iters[j] : 0;
+  return SPPC_OK;
+}
+
+sppc_status sppc_get_stats(sppc_handle h, sppc_stats* stats) {
+  if (!h || !stats) return fail(h, SPPC_ERR_ARG, "NULL argument");
+  *stats = h->stats;
+  return SPPC_OK;
+}
+
+sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t count) {
+  if (!h || !out) return fail(h, SPPC_ERR_ARG, "NULL argument");
+  const int k = h->k, kp = h->kp;
+  const int64_t n = h->n, n1 = h->n1;
+  cudaStream_t s = h->stream;
+  const int nbk = h->p + 1;
+  auto dl = [&](const float2* src, int64_t rows, int ncols, double* dst, int64_t ld) -> sppc_status {
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, sizeof(double) * rows * ncols));
+    CK(df_to_f64(src, kp, tmp, ncols, ncols, 0, rows, s));
+    std::vector<double> hbuf((size_t)rows * ncols);
+    CK(cudaMemcpyAsync(hbuf.data(), tmp, sizeof(double) * rows * ncols, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cudaFree(tmp);
+    for (int64_t r = 0; r < rows; ++r)
+      for (int c2 = 0; c2 < ncols; ++c2) dst[r * ld + c2] = hbuf[(size_t)r * ncols + c2];
+    return SPPC_OK;
+  };
+  switch (which) {
+    case 0:
+      if (count < n1 * k) return fail(h, SPPC_ERR_ARG, "buffer too small");
+      return dl(h->psi_hat, n1, k, out, k);
+    case 1:
+    case 2: {
+      const int64_t m = (int64_t)k * nbk;
+      if (count < n * m) return fail(h, SPPC_ERR_ARG, "buffer too small");
+      for (int a = 0; a < nbk; ++a) {
+        std::vector<double> tmp((size_t)n * k);
+        CKS(dl(blk(which == 1 ? h->Q : h->W, n, kp, a), n, k, tmp.data(), k));
+        for (int64_t r = 0; r < n; ++r)
+          for (int j = 0; j < k; ++j) out[r * m + a * k + j] = tmp[(size_t)r * k + j];
+      }
+      return SPPC_OK;
+    }
+    case 3: {
+      const int m = k * nbk;
+      if (count < (int64_t)m * m) return fail(h, SPPC_ERR_ARG, "buffer too small");
+      std::vector<double> hbuf((size_t)h->mmax * h->mmax);
+      CK(cudaMemcpyAsync(hbuf.data(), h->dHt, sizeof(double) * hbuf.size(), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) out[i * m + j] = hbuf[(size_t)i * h->mmax + j];
+      return SPPC_OK;
+    }
+    case 4:
+      if (count < n * k) return fail(h, SPPC_ERR_ARG, "buffer too small");
+      return dl(blk(h->Psi, n, kp, h->p), n, k, out, k);
+    case 5:
+      if (count < k) return fail(h, SPPC_ERR_ARG, "buffer too small");
+      for (int j = 0; j < k; ++j) out[j] = j < (int)h->E0.size() ? h->E0[j] : 0.0;
+      return SPPC_OK;
+    default:
+      return fail(h, SPPC_ERR_ARG, "unknown state id %d", which);
+  }
+}
+
+sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr, int32_t* slice_rows,
+                            int64_t* n11_slices, int64_t* h11_slice_ptr, int32_t* h11_slice_rows) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (n_slices) *n_slices = h->h_slices;
+  if (n11_slices) *n11_slices = h->h11_slices;
+  if (slice_ptr) std::copy(h->h_slice_ptr.begin(), h->h_slice_ptr.end(), slice_ptr);
+  if (slice_rows) std::copy(h->h_slice_rows.begin(), h->h_slice_rows.end(), slice_rows);
+  if (h11_slice_ptr) std::copy(h->h11_slice_ptr.begin(), h->h11_slice_ptr.end(), h11_slice_ptr);
+  if (h11_slice_rows) std::copy(h->h11_slice_rows.begin(), h->h11_slice_rows.end(), h11_slice_rows);
+  return SPPC_OK;
+}
+
+}  // extern "C"

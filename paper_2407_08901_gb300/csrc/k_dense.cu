@@ -1,0 +1,379 @@
+// Tall-skinny dense kernels on row-major n x kp double-float blocks:
+// Gram products A^T B (block Gram-Schmidt Eq. blkGS, CholeskyQR Eq. QR, the
+// border of the projected matrix Eq. proj), block updates X - A C (blkGS, the
+// recycled H Psi of Eq. HPsip, Ritz vectors), diagonal combinations (right-hand
+// side of Eq. exp_seq2) and the Ritz residual norms of Eq. rrn.
+//
+// Reductions over rows are two-stage and deterministic: each CTA writes its
+// partial sums, a finishing kernel adds the partials in a fixed order.
+#include "df.cuh"
+#include "sppc_internal.h"
+
+namespace sppc {
+
+namespace {
+
+constexpr int kChunk = 2048;  // rows per CTA in the reductions
+
+__global__ void k_finish(const float2* __restrict__ partials, int64_t nchunks, int nout, double* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  float sh = 0.f, sl = 0.f;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    acc_add(sh, sl, partials[c * nout + o]);
+    acc_norm(sh, sl);
+  }
+  out[o] = (double)sh + (double)sl;
+}
+
+// One CTA = KP warps and kChunk rows; warp i owns column i of each A block,
+// lanes stride over rows.  B rows are shared through L1.
+template <int KP>
+__global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restrict__ B, int64_t r0, int64_t r1,
+                                              float2* __restrict__ partials) {
+  const int lane = threadIdx.x & 31;
+  const int i = threadIdx.x >> 5;
+  const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * kChunk;
+  const int64_t c1 = min(c0 + kChunk, r1);
+  const int nout = A.n * KP * KP;
+  for (int a = 0; a < A.n; ++a) {
+    const float2* __restrict__ Aa = A.p[a];
+    float sh[KP], sl[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) sh[j] = sl[j] = 0.f;
+    int cnt = 0;
+    for (int64_t r = c0 + lane; r < c1; r += 32) {
+      const float2 av = Aa[r * KP + i];
+      const float4* br = reinterpret_cast<const float4*>(B + r * KP);
+#pragma unroll
+      for (int q = 0; q < KP / 2; ++q) {
+        const float4 b = br[q];
+        acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b.x, b.y));
+        acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b.z, b.w));
+      }
+      if (((++cnt) & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const float2 t = warp_sum_df(acc_get(sh[j], sl[j]));
+      if (lane == 0) partials[static_cast<int64_t>(blockIdx.x) * nout + (a * KP + i) * KP + j] = t;
+    }
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) k_update(float2* Y, const float2* X, const float2* __restrict__ alpha,
+                                                BlockList A, const float2* __restrict__ coef, int64_t r0, int64_t r1) {
+  extern __shared__ float2 scoef[];
+  const int ncoef = A.n * KP * KP;
+  for (int t = threadIdx.x; t < ncoef; t += blockDim.x) scoef[t] = coef[t];
+  __shared__ float2 salpha[8];
+  if (threadIdx.x < KP) salpha[threadIdx.x] = alpha ? alpha[threadIdx.x] : make_float2(0.f, 0.f);
+  __syncthreads();
+  const int64_t r = r0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= r1) return;
+  float sh[KP], sl[KP];
+#pragma unroll
+  for (int j = 0; j < KP; ++j) sh[j] = sl[j] = 0.f;
+  if (X && alpha) {
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const float2 t = df_mul(salpha[j], X[r * KP + j]);
+      sh[j] = t.x;
+      sl[j] = t.y;
+    }
+  }
+  for (int a = 0; a < A.n; ++a) {
+    const float4* ar = reinterpret_cast<const float4*>(A.p[a] + r * KP);
+    float2 av[KP];
+#pragma unroll
+    for (int q = 0; q < KP / 2; ++q) {
+      const float4 t = ar[q];
+      av[2 * q] = make_float2(t.x, t.y);
+      av[2 * q + 1] = make_float2(t.z, t.w);
+    }
+    const float2* ca = scoef + a * KP * KP;
+#pragma unroll
+    for (int i = 0; i < KP; ++i) {
+#pragma unroll
+      for (int j = 0; j < KP; ++j) acc_mac(sh[j], sl[j], av[i], ca[i * KP + j]);
+    }
+#pragma unroll
+    for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < KP; ++j) Y[r * KP + j] = acc_get(sh[j], sl[j]);
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) k_combine_diag(float2* Y, const float2* X, const float2* __restrict__ alpha,
+                                                      BlockList A, const float2* __restrict__ coef, int64_t r0,
+                                                      int64_t r1) {
+  __shared__ float2 sc[kMaxBlocks * 8];
+  __shared__ float2 salpha[8];
+  for (int t = threadIdx.x; t < A.n * 8; t += blockDim.x) sc[t] = coef[t];
+  if (threadIdx.x < KP) salpha[threadIdx.x] = alpha ? alpha[threadIdx.x] : make_float2(0.f, 0.f);
+  __syncthreads();
+  const int64_t r = r0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= r1) return;
+  float sh[KP], sl[KP];
+#pragma unroll
+  for (int j = 0; j < KP; ++j) {
+    sh[j] = sl[j] = 0.f;
+    if (X && alpha) {
+      const float2 t = df_mul(salpha[j], X[r * KP + j]);
+      sh[j] = t.x;
+      sl[j] = t.y;
+    }
+  }
+  for (int b = 0; b < A.n; ++b) {
+    const float2* ab = A.p[b] + r * KP;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) acc_mac(sh[j], sl[j], sc[b * 8 + j], ab[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < KP; ++j) Y[r * KP + j] = acc_get(sh[j], sl[j]);
+}
+
+struct Pairs {
+  const float2* a[4];
+  const float2* b[4];
+};
+
+template <int KP>
+__global__ void __launch_bounds__(256) k_coldots(Pairs P, int nq, int64_t r0, int64_t r1, float2* partials) {
+  __shared__ float2 red[8][4 * 8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * kChunk;
+  const int64_t c1 = min(c0 + kChunk, r1);
+  float sh[4 * KP], sl[4 * KP];
+#pragma unroll
+  for (int t = 0; t < 4 * KP; ++t) sh[t] = sl[t] = 0.f;
+  for (int64_t r = c0 + threadIdx.x; r < c1; r += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q < nq) {
+#pragma unroll
+        for (int j = 0; j < KP; ++j) acc_mac(sh[q * KP + j], sl[q * KP + j], P.a[q][r * KP + j], P.b[q][r * KP + j]);
+      }
+    }
+  }
+  const int nout = nq * KP;
+#pragma unroll
+  for (int t = 0; t < 4 * KP; ++t) {
+    if (t < nout) {
+      const float2 v = warp_sum_df(acc_get(sh[t], sl[t]));
+      if (lane == 0) red[warp][t] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nout) {
+    float2 s = red[0][threadIdx.x];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = df_add(s, red[w][threadIdx.x]);
+    partials[static_cast<int64_t>(blockIdx.x) * nout + threadIdx.x] = s;
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, const float2* __restrict__ Y,
+                                                    const float2* __restrict__ theta, int64_t n, float2* partials,
+                                                    double* Zout, int64_t ldz, int ncols) {
+  extern __shared__ float2 sy[];
+  const int ny = Q.n * KP * KP;
+  for (int t = threadIdx.x; t < ny; t += blockDim.x) sy[t] = Y[t];
+  __shared__ float2 sth[8];
+  __shared__ float2 red[8][8];
+  if (threadIdx.x < KP) sth[threadIdx.x] = theta[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float rh[KP], rl[KP];
+#pragma unroll
+  for (int j = 0; j < KP; ++j) rh[j] = rl[j] = 0.f;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kChunk;
+  const int64_t c1 = min(c0 + kChunk, n);
+  for (int64_t r = c0 + threadIdx.x; r < c1; r += blockDim.x) {
+    float zh[KP], zl[KP], hh[KP], hl[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) zh[j] = zl[j] = hh[j] = hl[j] = 0.f;
+    for (int a = 0; a < Q.n; ++a) {
+      const float2* qa = Q.p[a] + r * KP;
+      const float2* wa = Wb.p[a] + r * KP;
+      const float2* ya = sy + a * KP * KP;
+#pragma unroll
+      for (int i = 0; i < KP; ++i) {
+        const float2 qv = qa[i], wv = wa[i];
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+          acc_mac(zh[j], zl[j], qv, ya[i * KP + j]);
+          acc_mac(hh[j], hl[j], wv, ya[i * KP + j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < KP; ++j) {
+        acc_norm(zh[j], zl[j]);
+        acc_norm(hh[j], hl[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const float2 z = acc_get(zh[j], zl[j]);
+      const float2 d = df_sub(acc_get(hh[j], hl[j]), df_mul(sth[j], z));
+      acc_mac(rh[j], rl[j], d, d);
+      if (Zout && j < ncols) Zout[r * ldz + j] = df_to_double(z);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KP; ++j) {
+    const float2 v = warp_sum_df(acc_get(rh[j], rl[j]));
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < KP) {
+    float2 s = red[0][threadIdx.x];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = df_add(s, red[w][threadIdx.x]);
+    partials[static_cast<int64_t>(blockIdx.x) * KP + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_f64_to_df(const double* __restrict__ X, int64_t ldx, int ncols, float2* __restrict__ Y, int kp,
+                            int64_t r0, int64_t r1) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t r = r0 + t / kp;
+  const int c = static_cast<int>(t % kp);
+  if (r >= r1) return;
+  Y[r * kp + c] = (c < ncols) ? df_from_double(X[r * ldx + c]) : make_float2(0.f, 0.f);
+}
+
+__global__ void k_df_to_f64(const float2* __restrict__ X, int kp, double* __restrict__ Y, int64_t ldy, int ncols,
+                            int64_t r0, int64_t r1) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t r = r0 + t / ncols;
+  const int c = static_cast<int>(t % ncols);
+  if (r >= r1) return;
+  Y[r * ldy + c] = df_to_double(X[r * kp + c]);
+}
+
+__global__ void k_zero(float2* Y, int64_t count) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < count) Y[t] = make_float2(0.f, 0.f);
+}
+
+inline unsigned nblk(int64_t work, int threads) { return static_cast<unsigned>((work + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_t r1, double* out,
+                 float2* partials, int64_t partial_cap, cudaStream_t s) {
+  const int nout = A.n * kp * kp;
+  if (r1 <= r0 || A.n == 0) {
+    return cudaMemsetAsync(out, 0, sizeof(double) * nout, s);
+  }
+  const int64_t nchunks = (r1 - r0 + kChunk - 1) / kChunk;
+  if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
+  const unsigned g = static_cast<unsigned>(nchunks);
+  switch (kp) {
+    case 2: k_gram<2><<<g, 64, 0, s>>>(A, B, r0, r1, partials); break;
+    case 4: k_gram<4><<<g, 128, 0, s>>>(A, B, r0, r1, partials); break;
+    case 6: k_gram<6><<<g, 192, 0, s>>>(A, B, r0, r1, partials); break;
+    case 8: k_gram<8><<<g, 256, 0, s>>>(A, B, r0, r1, partials); break;
+    default: return cudaErrorInvalidValue;
+  }
+  k_finish<<<nblk(nout, 256), 256, 0, s>>>(partials, nchunks, nout, out);
+  return cudaGetLastError();
+}
+
+cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef, int kp,
+                   int64_t r0, int64_t r1, cudaStream_t s) {
+  if (r1 <= r0) return cudaSuccess;
+  const size_t smem = sizeof(float2) * (size_t)(A.n > 0 ? A.n : 1) * kp * kp;
+  const unsigned g = nblk(r1 - r0, 256);
+  switch (kp) {
+    case 2: k_update<2><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    case 4: k_update<4><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    case 6: k_update<6><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    case 8: k_update<8><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t combine_diag(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef,
+                         int kp, int64_t r0, int64_t r1, cudaStream_t s) {
+  if (r1 <= r0) return cudaSuccess;
+  const unsigned g = nblk(r1 - r0, 256);
+  switch (kp) {
+    case 2: k_combine_diag<2><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    case 4: k_combine_diag<4><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    case 6: k_combine_diag<6><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    case 8: k_combine_diag<8><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int kp, int64_t r0, int64_t r1,
+                    double* out, float2* partials, int64_t partial_cap, cudaStream_t s) {
+  if (nq < 1 || nq > 4) return cudaErrorInvalidValue;
+  const int nout = nq * kp;
+  if (r1 <= r0) return cudaMemsetAsync(out, 0, sizeof(double) * nout, s);
+  Pairs P{};
+  for (int q = 0; q < nq; ++q) {
+    P.a[q] = A[q];
+    P.b[q] = B[q];
+  }
+  const int64_t nchunks = (r1 - r0 + kChunk - 1) / kChunk;
+  if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
+  const unsigned g = static_cast<unsigned>(nchunks);
+  switch (kp) {
+    case 2: k_coldots<2><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); break;
+    case 4: k_coldots<4><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); break;
+    case 6: k_coldots<6><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); break;
+    case 8: k_coldots<8><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); break;
+    default: return cudaErrorInvalidValue;
+  }
+  k_finish<<<nblk(nout, 256), 256, 0, s>>>(partials, nchunks, nout, out);
+  return cudaGetLastError();
+}
+
+cudaError_t ritz_resid(const BlockList& Q, const BlockList& Wb, const float2* Y, const float2* theta, int kp,
+                       int64_t n, double* out, float2* partials, int64_t partial_cap, double* Zout, int64_t ldz,
+                       int ncols, cudaStream_t s) {
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  if (nchunks * kp > partial_cap) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * (size_t)Q.n * kp * kp;
+  const unsigned g = static_cast<unsigned>(nchunks);
+  switch (kp) {
+    case 2: k_ritz_resid<2><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols); break;
+    case 4: k_ritz_resid<4><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols); break;
+    case 6: k_ritz_resid<6><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols); break;
+    case 8: k_ritz_resid<8><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols); break;
+    default: return cudaErrorInvalidValue;
+  }
+  k_finish<<<1, 32, 0, s>>>(partials, nchunks, kp, out);
+  return cudaGetLastError();
+}
+
+cudaError_t f64_to_df(const double* X, int64_t ldx, int ncols, float2* Y, int kp, int64_t r0, int64_t r1,
+                      cudaStream_t s) {
+  if (r1 <= r0) return cudaSuccess;
+  k_f64_to_df<<<nblk((r1 - r0) * kp, 256), 256, 0, s>>>(X, ldx, ncols, Y, kp, r0, r1);
+  return cudaGetLastError();
+}
+
+cudaError_t df_to_f64(const float2* X, int kp, double* Y, int64_t ldy, int ncols, int64_t r0, int64_t r1,
+                      cudaStream_t s) {
+  if (r1 <= r0 || ncols <= 0) return cudaSuccess;
+  k_df_to_f64<<<nblk((r1 - r0) * ncols, 256), 256, 0, s>>>(X, kp, Y, ldy, ncols, r0, r1);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_zero(float2* Y, int64_t count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_zero<<<nblk(count, 256), 256, 0, s>>>(Y, count);
+  return cudaGetLastError();
+}
+
+}  // namespace sppc

@@ -1,0 +1,71 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and rejects malformed input before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT, make_matrix
+
+
+def _header_symbols():
+    src = open(os.path.join(ROOT, "include", "sppc.h")).read()
+    return set(re.findall(r"^\s*(?:sppc_status|void|const char\*)\s+(sppc_\w+)\s*\(", src, re.M))
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+    import paper_2407_08901_gb300 as S
+    lib = ctypes.CDLL(S.LIB)
+    declared = _header_symbols()
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(S.EXPORTED_SYMBOLS)
+
+
+def test_default_opts():
+    import paper_2407_08901_gb300 as S
+    o = S.sppc_default_opts()
+    assert o.p_max == 15 and o.tol == 1e-6 and o.minres_tol == 1e-12 and o.check_symmetry == 0
+
+
+def _small():
+    w, rp, c, v = make_matrix("small")
+    return w, rp.copy(), c.copy(), v.copy()
+
+
+@pytest.mark.parametrize("case,status", [
+    ("n1_not_level", 3), ("k_zero", 1), ("k_nine", 1), ("levels_bad", 3), ("unsorted", 1), ("col_range", 1),
+    ("nan", 11), ("asym", 2), ("rowptr", 1),
+])
+def test_create_rejects_bad_input(case, status):
+    import paper_2407_08901_gb300 as S
+    w, rp, c, v = _small()
+    lev = w.level_offsets.copy()
+    n1, k = w.small_dim, w.k
+    opts = S.sppc_default_opts(check_symmetry=1)
+    if case == "n1_not_level":
+        n1 = n1 + 1
+    elif case == "k_zero":
+        k = 0
+    elif case == "k_nine":
+        k = 9
+    elif case == "levels_bad":
+        lev[2] = lev[1]
+    elif case == "unsorted":
+        lo = rp[5]
+        c[lo], c[lo + 1] = c[lo + 1], c[lo]
+    elif case == "col_range":
+        c[10] = w.n + 3
+    elif case == "nan":
+        v[7] = np.nan
+    elif case == "asym":
+        v[3] += 1e-3
+    elif case == "rowptr":
+        rp[-1] += 1
+    with pytest.raises(S.SppcError) as ei:
+        S.sppc_create(rp, c, v, lev, n1, k, opts)
+    assert ei.value.status == status, str(ei.value)
+    assert S.sppc_last_error(None)

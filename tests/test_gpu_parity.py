@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.  GPU only.
+
+Tolerances: the library computes in double-float (two fp32, ~48-bit
+significand, error-free transformations).  An SpMM row sum of m terms carries
+an error below ~m * 2^-46 * sum_j |H_ij x_j| (accumulation bound of the lazily
+renormalised accumulator), so entries are compared against 1e-12 times that
+row magnitude.  Eigenvalues must match the oracle to 1e-10 relative at the same
+order (the target of the FP64 path); scaled residuals (a difference of nearly
+equal vectors) to 1e-6 relative plus 1e-12 absolute.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from conftest import make_matrix
+from oracle.spmm import csr_spmm
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _lib():
+    import paper_2407_08901_gb300 as S
+    return S
+
+
+def _abs_spmm(rp, c, v, X):
+    return csr_spmm(rp, c, np.abs(v), np.abs(X))
+
+
+def _create(name_or_w, opts=None, **kw):
+    S = _lib()
+    w, rp, c, v = make_matrix(name_or_w)
+    o = opts or S.sppc_default_opts(**kw)
+    h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, o)
+    return S, w, rp, c, v, h
+
+
+@pytest.mark.parametrize("name", ["small", "c1"])
+@pytest.mark.parametrize("ncols", [1, 2, 5, 8])
+def test_spmm_matches_oracle(name, ncols):
+    S, w, rp, c, v, h = _create(name)
+    try:
+        X = W.random_block(w.n, ncols, 11 + ncols)
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.empty_like(Xd)
+        S.sppc_spmm(h, Xd, Yd)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().numpy()
+        ref = csr_spmm(rp, c, v, X)
+        mag = _abs_spmm(rp, c, v, X)
+        assert np.all(np.abs(Y - ref) <= 1e-12 * mag + 1e-300), np.max(np.abs(Y - ref) / mag)
+        # host-buffer entry point gives the same bytes
+        Yh = np.zeros_like(X)
+        S.sppc_spmm_host(h, np.ascontiguousarray(X), Yh)
+        assert np.array_equal(Yh, Y)
+    finally:
+        S.sppc_destroy(h)
+
+
+def test_spmm_empty_and_ragged_rows():
+    """A matrix with empty rows (no stored entry at all) and a level whose size is
+    not a multiple of the 32-row slice."""
+    S = _lib()
+    n = 203
+    rng = np.random.Generator(np.random.PCG64(9))
+    A = np.zeros((n, n))
+    for i in range(n):
+        if i % 7 == 3:
+            continue
+        js = rng.integers(0, n, 5)
+        A[i, js] = rng.standard_normal(5)
+    A = A + A.T
+    for i in range(n):
+        if i % 7 == 3:
+            A[i, :] = 0
+            A[:, i] = 0
+    rows, cols = np.nonzero(A)
+    rp = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))]).astype(np.int64)
+    c = cols.astype(np.int32)
+    v = A[rows, cols]
+    lev = np.array([0, 37, 101, n], dtype=np.int64)
+    h = S.sppc_create(rp, c, v, lev, 37, 2)
+    try:
+        X = W.random_block(n, 3, 1)
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.full_like(Xd, 7.0)
+        S.sppc_spmm(h, Xd, Yd)
+        Y = Yd.cpu().numpy()
+        ref = A @ X
+        assert np.allclose(Y, ref, rtol=0, atol=1e-12 * (np.abs(A) @ np.abs(X)).max() + 1e-300)
+        assert np.all(Y[3::7] == 0.0)
+    finally:
+        S.sppc_destroy(h)
+
+
+def _sell_reference(rp, c, n1_limit, seg, sigma=1024):
+    """The SELL-32 row order: inside each level, windows of 1024 rows sorted by
+    decreasing row length (stable), cut into slices of 32 rows."""
+    nrows = seg[-1]
+    lens = np.array([np.count_nonzero(c[rp[r]:rp[r + 1]] < n1_limit) for r in range(nrows)])
+    order = np.arange(nrows)
+    slice_rows, slice_ptr = [], [0]
+    for a, b in zip(seg[:-1], seg[1:]):
+        for w0 in range(a, b, sigma):
+            w1 = min(w0 + sigma, b)
+            idx = np.arange(w0, w1)
+            order[w0:w1] = idx[np.argsort(-lens[idx], kind="stable")]
+        for s0 in range(a, b, 32):
+            rows = order[s0:min(s0 + 32, b)]
+            pad = np.full(32, -1)
+            pad[: len(rows)] = rows
+            slice_rows.append(pad)
+            slice_ptr.append(slice_ptr[-1] + 32 * int(lens[rows].max()))
+    return np.array(slice_ptr, dtype=np.int64), np.concatenate(slice_rows).astype(np.int32)
+
+
+@pytest.mark.parametrize("name", ["small", "c1"])
+def test_layout_is_bit_exact(name):
+    S, w, rp, c, v, h = _create(name)
+    try:
+        L = S.sppc_get_layout(h)
+    finally:
+        S.sppc_destroy(h)
+    sp, sr = _sell_reference(rp, c, 2**31, list(w.level_offsets))
+    assert np.array_equal(L["slice_ptr"], sp) and np.array_equal(L["slice_rows"], sr)
+    sp11, sr11 = _sell_reference(rp, c, w.small_dim, [0, w.small_dim])
+    assert np.array_equal(L["h11_slice_ptr"], sp11) and np.array_equal(L["h11_slice_rows"], sr11)
+
+
+def _compare_orders(S, h, ref, k, rtol_theta=1e-10):
+    for o in ref.orders:
+        info = S.sppc_order_info(h, o.p, k)
+        assert np.allclose(info["theta"], o.theta, rtol=rtol_theta, atol=0), (o.p, info["theta"] - o.theta)
+        assert np.allclose(info["resid"], o.resid, rtol=1e-6, atol=1e-12), (o.p, info["resid"], o.resid)
+        if o.p >= 2:
+            assert np.allclose(info["E"], o.E, rtol=1e-8, atol=1e-10 * np.abs(o.E).max()), (o.p, info["E"], o.E)
+        if o.p == 1:
+            assert np.all(np.abs(info["E"]) <= 1e-12 * np.abs(ref.E0).max())
+
+
+@pytest.mark.parametrize("name,orders", [("small", 8), ("c1", 2)])
+def test_sppc_matches_oracle_order_by_order(name, orders):
+    S, w, rp, c, v, h = _create(name, p_max=max(orders, 2))
+    try:
+        conv, th, rs, st = S.sppc_solve(h, w.k, tol=1e-300, p_max=orders)
+        ref = oracle.sppc(rp, c, v, w.small_dim, w.k, fixed_orders=orders)
+        E0 = S.sppc_get_state(h, 5, (w.k,))
+        assert np.allclose(E0, ref.E0, rtol=1e-12, atol=0)
+        _compare_orders(S, h, ref, w.k)
+        assert st["orders"] == orders and st["spmv_h"] == w.k * (orders + 1)
+        assert np.allclose(th, ref.theta, rtol=1e-10, atol=0)
+    finally:
+        S.sppc_destroy(h)
+
+
+def test_stepwise_api_equals_solve():
+    S, w, rp, c, v, h = _create("small", p_max=4)
+    try:
+        th0, rs0 = S.sppc_start(h, w.k)
+        seq = [th0]
+        for _ in range(3):
+            S.sppc_correct(h)
+            th, rs = S.sppc_rayleigh_ritz(h, w.k)
+            seq.append(th)
+        conv, thS, rsS, st = S.sppc_solve(h, w.k, tol=1e-300, p_max=3)
+        assert np.array_equal(thS, seq[-1])
+        with pytest.raises(S.SppcError):
+            S.sppc_rayleigh_ritz(h, w.k)  # no correction pending
+    finally:
+        S.sppc_destroy(h)
+
+
+def test_ritz_vectors_and_basis():
+    """Returned Z: H Z - Z theta reproduces the reported residuals; Q^T Q = I;
+    the projected matrix equals Q^T H Q recomputed on the CPU."""
+    S, w, rp, c, v, h = _create("small", p_max=5)
+    try:
+        Z = torch.zeros((w.n, w.k), dtype=torch.float64, device="cuda")
+        conv, th, rs, st = S.sppc_solve(h, w.k, tol=1e-300, p_max=5, Z=Z)
+        Zh = Z.cpu().numpy()
+        HZ = csr_spmm(rp, c, v, Zh)
+        r = np.linalg.norm(HZ - Zh * th, axis=0) / np.abs(th)
+        assert np.allclose(r, rs, rtol=1e-5, atol=1e-12)
+        m = w.k * 6
+        Q = S.sppc_get_state(h, 1, (w.n, m))
+        assert np.abs(Q.T @ Q - np.eye(m)).max() <= 1e-12
+        Ht = S.sppc_get_state(h, 3, (m, m))
+        full = Q.T @ csr_spmm(rp, c, v, Q)
+        assert np.abs(Ht - 0.5 * (full + full.T)).max() <= 1e-11 * np.abs(full).max()
+    finally:
+        S.sppc_destroy(h)
+
+
+def test_small_space_eigenpairs():
+    S, w, rp, c, v, h = _create("c1")
+    try:
+        S.sppc_start(h, w.k)
+        psi = S.sppc_get_state(h, 0, (w.small_dim, w.k))
+        E0 = S.sppc_get_state(h, 5, (w.k,))
+    finally:
+        S.sppc_destroy(h)
+    n1 = w.small_dim
+    H11 = np.zeros((n1, n1))
+    for i in range(n1):
+        cc = c[rp[i]:rp[i + 1]]
+        m = cc < n1
+        H11[i, cc[m]] = v[rp[i]:rp[i + 1]][m]
+    lam = np.linalg.eigvalsh(H11)[: w.k]
+    assert np.allclose(E0, lam, rtol=1e-12)
+    assert np.abs(H11 @ psi - psi * E0).max() <= 1e-11
+    assert np.abs(psi.T @ psi - np.eye(w.k)).max() <= 1e-12
