@@ -75,6 +75,17 @@ typedef struct {
   int32_t check_symmetry; /* 1: verify H == H^T bit for bit at create (default 0) */
   uint64_t seed;          /* seed of the small eigensolve's start block (default 0) */
   int32_t timing;         /* 1: time kernels with CUDA events into sppc_stats (default 0) */
+  int64_t spmm_chunk_cols; /* SpMM column tile: -1 = untiled (default), 0 = 655360 columns (40 MB of
+                              an 8-column block), > 0 = that many columns (at most 255 tiles) */
+  int32_t hybrid;          /* 0: plain SPPC (Alg. 2, default); 1: after switch_order SPPC orders continue
+                              by block extension with preconditioned Ritz residuals (Sec. 5: SPPC
+                              combined with a second eigensolver started from its approximations) */
+  int32_t switch_order;    /* SPPC orders before the continuation (default 15, Sec. 6) */
+  int32_t hybrid_maxit;    /* continuation steps, k SpMVs each (default 1000) */
+  int32_t precond;         /* 1: residual_j / (diag(H) - theta_j) (default); 0: none (block Krylov) */
+  double precond_clamp;    /* denominators of the preconditioner clamped to |.| >= this (1e-2) */
+  int32_t hybrid_blocks;   /* continuation basis limit in blocks of k vectors before a thick restart
+                              to 2k Ritz vectors (default 0 = p_max + 1; at least 3) */
 } sppc_opts;
 
 typedef struct {
@@ -90,6 +101,9 @@ typedef struct {
   double small_eig_ms;       /* small eigensolve (timing=1) */
   double dense_ms;           /* Gram / orthogonalisation / Rayleigh-Ritz kernels (timing=1) */
   double total_ms;           /* whole call (timing=1) */
+  int32_t refine_steps;      /* continuation steps run (hybrid) */
+  int32_t restarts;          /* thick restarts of the continuation */
+  int32_t switched_at;       /* SPPC order at which the continuation started */
 } sppc_stats;
 
 /* Fill `o` with the defaults listed above. */
@@ -101,7 +115,7 @@ void sppc_default_opts(sppc_opts* o);
  *  n1 must equal level_offsets[j] for some j >= 1 (Sec. 6.1: H0_hat is the whole
  *    smaller configuration space), else SPPC_ERR_LEVELS;
  *  1 <= k <= 8 eigenpairs, k < n1.
- * Copies and reformats H into library-owned device memory (level-blocked SELL-32
+ * Copies and reformats H into library-owned device memory (level-blocked SELL-16
  * layout plus a separate copy of H0_hat).  Allocates the basis for opts.p_max
  * orders up front (SPPC_ERR_OOM if it does not fit).  opts may be NULL. */
 sppc_status sppc_create(const sppc_csr* H, const int64_t* level_offsets, int32_t n_levels, int64_t n1,
@@ -137,7 +151,9 @@ sppc_status sppc_correct(sppc_handle h, void* stream);
 sppc_status sppc_rayleigh_ritz(sppc_handle h, double* theta, double* resid, void* stream);
 
 /* Algorithm 2 end to end: start, then correct + rayleigh_ritz until every scaled
- * residual <= tol or p_max orders.  Outputs (any may be NULL):
+ * residual <= tol or p_max orders (switch_order orders when opts.hybrid, followed
+ * by sppc_refine_step until converged or hybrid_maxit steps).  Outputs (any may
+ * be NULL):
  *   theta[k], resid[k]: host arrays;
  *   Z: caller-owned DEVICE buffer n x k (ldz >= k), the Ritz vectors;
  *   stats: host struct.
@@ -146,10 +162,21 @@ sppc_status sppc_rayleigh_ritz(sppc_handle h, double* theta, double* resid, void
 sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, double* Z, int64_t ldz,
                        double* resid, sppc_stats* stats, void* stream);
 
-/* Per-order record of the last solve: E^(p) (k values), sine of the angle between
+/* One continuation step (after at least one Rayleigh-Ritz step): extend the basis
+ * by the k Ritz residuals of the current pairs, divided by diag(H) - theta_j when
+ * opts.precond (block Davidson; block Krylov otherwise), orthogonalised against
+ * the basis (Eq. blkGS twice, CholeskyQR2); k SpMVs; Rayleigh-Ritz.  When the
+ * basis holds opts.hybrid_blocks blocks it first restarts from the 2k lowest
+ * Ritz vectors.
+ * After the first step sppc_correct is no longer allowed.  theta, resid: optional
+ * host arrays of k. */
+sppc_status sppc_refine_step(sppc_handle h, double* theta, double* resid, void* stream);
+
+/* Per-step record of the last solve: E^(p) (k values), sine of the angle between
  * Psi_j^(p) and M^(p-1) after orthogonalisation (k values; Sec. 6.2), Ritz values
  * and scaled residuals after order p (k values each), MINRES iterations per column.
- * Any output may be NULL.  p in [0, orders]. */
+ * Steps 0..orders are SPPC orders; continuation steps follow (E and MINRES counts
+ * zero, angle of the appended residual block).  Any output may be NULL. */
 sppc_status sppc_order_info(sppc_handle h, int32_t p, double* E, double* angle, double* theta, double* resid,
                             int32_t* minres_iters);
 
@@ -164,13 +191,20 @@ sppc_status sppc_get_stats(sppc_handle h, sppc_stats* stats);
 sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t count);
 
 /* Integer layout of the device matrix copy, for bit-exact checks.  Host buffers:
- *   slice_ptr[n_slices+1] (int64), slice_rows[32*n_slices] (int32, -1 = padding lane),
- *   h11 same for the leading block.  Query sizes with NULL buffers. */
+ *   slice_ptr[n_slices+1] (int64), slice_rows[16*n_slices] (int32, -1 = padding row),
+ *   h11 same for the leading block (one column chunk), n_chunks and
+ *   chunk_slice[n_chunks+1] (first slice of each column chunk of H).
+ * Query sizes with NULL buffers. */
 sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr, int32_t* slice_rows,
-                            int64_t* n11_slices, int64_t* h11_slice_ptr, int32_t* h11_slice_rows);
+                            int64_t* n11_slices, int64_t* h11_slice_ptr, int32_t* h11_slice_rows, int32_t* n_chunks,
+                            int64_t* chunk_slice);
 
 /* Release everything the handle owns.  NULL is a no-op. */
 sppc_status sppc_destroy(sppc_handle h);
+
+/* Number of CUDA kernel launches this library has issued since it was loaded
+ * (all handles, all threads).  Lets a caller count the kernels of a timed region. */
+int64_t sppc_kernel_launches(void);
 
 /* Last error message of h (or of the calling thread's last failed create when
  * h == NULL).  The string is owned by the library and valid until the next call. */

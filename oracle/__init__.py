@@ -13,6 +13,8 @@ sppc.py      Algorithm 2 (SPPC for the k lowest eigenpairs) step by step, with
              Qp), the bordered projected matrix (Eq. proj) and the SpMV-saving
              identities of Sec. 4.3 (Eqs. avoid_SpMV2, HPsip).
 minres.py    MINRES (Paige and Saunders, 1975) for the small shifted solves.
+hybrid.py    SPPC followed by a block continuation (preconditioned residual
+             expansion) once SPPC stagnates (Sec. 5, 6).
 lanczos.py   Block Lanczos with full reorthogonalisation (eigenvalue truth for
              matrices too large for a dense eigendecomposition).
 spmm.py      CSR x dense block product (plain C loop with OpenMP, or SciPy).
@@ -25,3 +27,4 @@ from .sppc import sppc, small_eigenpairs, SPPCResult  # noqa: F401
 from .minres import minres  # noqa: F401
 from .lanczos import block_lanczos, dense_lowest  # noqa: F401
 from .spmm import csr_spmm  # noqa: F401
+from .hybrid import sppc_hybrid  # noqa: F401

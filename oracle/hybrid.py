@@ -1,0 +1,101 @@
+"""SPPC followed by a block continuation once SPPC stagnates (paper Sec. 5 and 6).
+
+The paper switches from SPPC to a second eigensolver that starts from SPPC's
+eigenvector approximations when adding corrections stops improving the
+subspace (around order 15); it lists Lanczos, block Lanczos, LOBPCG (with a
+shifted block-diagonal preconditioner) and RMM-DIIS (with a diagonal
+preconditioner) as partners.  Reading used here: the continuation keeps the
+whole SPPC subspace and extends it, one block per step, with the residuals of
+the k lowest Ritz pairs, preconditioned by the diagonal of H shifted by each
+Ritz value (block Davidson, Davidson 1975 / Liu 1978); with the identity as
+preconditioner the same loop extends the block Krylov space (block Lanczos
+with full reorthogonalisation and thick restart).  When the basis would exceed
+`max_blocks` blocks of k vectors it restarts from the 2k lowest Ritz vectors.
+
+Step by step, from Q (orthonormal, n x m), W = H Q, Ht = Q^T W:
+ 1. k lowest eigenpairs (theta, Y) of the symmetrised Ht; Z = Q Y, R = W Y - Z theta;
+    rho_j = ||R_j|| / |theta_j| (Eq. rrn); stop when every rho_j <= tol.
+ 2. T_j = R_j / (diag(H) - theta_j) elementwise, each denominator clamped to
+    magnitude >= clamp (Jacobi preconditioner), or T = R without preconditioner.
+ 3. Restart if m + k > max_blocks * k: Q <- Q Y_2k, W <- W Y_2k, Ht <- Q^T W.
+ 4. Phi = (I - Q Q^T) T applied twice, Phi = q R (Householder QR), Q <- [Q, q],
+    W <- [W, H q], Ht bordered.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from .spmm import csr_spmm
+from .sppc import sppc
+
+
+@dataclass
+class HybridRecord:
+    phase: str          # "sppc" or "davidson"
+    step: int           # SPPC order or Davidson iteration
+    theta: np.ndarray
+    resid: np.ndarray
+    spmv: int
+    m: int              # basis size after the step
+
+
+def _ritz(Q, W, k, nev):
+    Ht = Q.T @ W
+    Ht = 0.5 * (Ht + Ht.T)
+    th, Y = np.linalg.eigh(Ht)
+    return th[:nev], Y[:, :nev]
+
+
+def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, tol: float = 1e-6,
+                max_blocks: int = 16, maxit: int = 500, precond: str = "jacobi", clamp: float = 1e-2,
+                solver: str = "pinv", minres_tol: float = 1e-12):
+    """Run SPPC (Algorithm 2) for up to `switch_order` orders (stopping early if
+    every scaled residual is below tol), then the block continuation above.
+    Returns (theta, resid, converged, records)."""
+    n = row_ptr.shape[0] - 1
+    r = sppc(row_ptr, col, val, n1, k, p_max=switch_order, tol=tol, solver=solver, minres_tol=minres_tol,
+             keep=True)
+    records = [HybridRecord("sppc", o.p, o.theta, o.resid, o.spmv, k * (o.p + 1)) for o in r.orders]
+    spmv = r.spmv
+    if r.converged:
+        return r.theta, r.resid, True, records
+    Q, W = r.Q, r.W
+    diag = np.zeros(n)
+    rows = np.repeat(np.arange(n), np.diff(row_ptr))
+    on = rows == col
+    diag[rows[on]] = val[on]
+    for it in range(1, maxit + 1):
+        nev = min(2 * k, Q.shape[1])
+        th_all, Y_all = _ritz(Q, W, k, nev)
+        th, Y = th_all[:k], Y_all[:, :k]
+        Z = Q @ Y
+        R = W @ Y - Z * th
+        # step 2: preconditioned residuals
+        if precond == "jacobi":
+            den = diag[:, None] - th[None, :]
+            small = np.abs(den) < clamp
+            den[small] = np.where(den[small] >= 0, clamp, -clamp)
+            T = R / den
+        else:
+            T = R.copy()
+        # step 3: thick restart
+        if Q.shape[1] + k > max_blocks * k:
+            Q = Q @ Y_all[:, :2 * k]
+            W = W @ Y_all[:, :2 * k]
+        # step 4: block Gram-Schmidt twice + QR, extend the basis by k SpMVs
+        Phi = T - Q @ (Q.T @ T)
+        Phi = Phi - Q @ (Q.T @ Phi)
+        q, _ = np.linalg.qr(Phi)
+        Wq = csr_spmm(row_ptr, col, val, q)
+        spmv += k
+        Q = np.hstack([Q, q])
+        W = np.hstack([W, Wq])
+        th, Y = _ritz(Q, W, k, k)
+        Z = Q @ Y
+        res = np.linalg.norm(W @ Y - Z * th, axis=0) / np.abs(th)
+        records.append(HybridRecord("davidson", it, th, res, spmv, Q.shape[1]))
+        if np.all(res <= tol):
+            return th, res, True, records
+    return th, res, False, records

@@ -27,6 +27,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.sparse as sp
 
 from .minres import minres
 from .spmm import csr_spmm
@@ -106,6 +107,8 @@ def sppc(row_ptr, col, val, n1: int, k: int, *, p_max: int = 15, tol: float = 1e
     vpsi:   "recycled" (Eq. HPsip), "direct" (a fresh product H Psi^(p-1)) or
             "both" (both computed, recycled one used, both kept when keep=True).
     fixed_orders: run exactly this many correction orders (no early stop).
+    small_eig: optional (eigenvalues, eigenvectors) of H0_hat, ascending; "pinv"
+            needs all of them, "minres" only those the deflation rule can touch.
     """
     n = row_ptr.shape[0] - 1
     P = fixed_orders if fixed_orders is not None else p_max
@@ -113,14 +116,12 @@ def sppc(row_ptr, col, val, n1: int, k: int, *, p_max: int = 15, tol: float = 1e
     def spmm(X):
         return csr_spmm(row_ptr, col, val, X)
 
-    # leading block H0_hat = H11 (dense)
-    H11 = np.zeros((n1, n1))
-    for i in range(n1):
-        lo, hi = row_ptr[i], row_ptr[i + 1]
-        c = col[lo:hi]
-        m = c < n1
-        H11[i, c[m]] += val[lo:hi][m]
-    w_all, U_all = small_eig if small_eig is not None else small_eigenpairs(H11)
+    # leading block H0_hat = H11 (sparse for products; dense only for its eigendecomposition)
+    rows = np.repeat(np.arange(n1), np.diff(row_ptr[: n1 + 1]))
+    c1 = col[: row_ptr[n1]]
+    m1 = c1 < n1
+    H11 = sp.csr_matrix((val[: row_ptr[n1]][m1], (rows[m1], c1[m1])), shape=(n1, n1))
+    w_all, U_all = small_eig if small_eig is not None else small_eigenpairs(H11.toarray())
     normH11 = float(max(abs(w_all[0]), abs(w_all[-1])))
     E0 = w_all[:k].copy()
     psi_hat = U_all[:, :k].copy()

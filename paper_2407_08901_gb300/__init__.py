@@ -17,8 +17,8 @@ from .build import LIB
 
 __all__ = [
     "SppcError", "sppc_default_opts", "sppc_create", "sppc_spmm", "sppc_spmm_host", "sppc_start", "sppc_correct",
-    "sppc_rayleigh_ritz", "sppc_solve", "sppc_order_info", "sppc_get_stats", "sppc_get_state", "sppc_get_layout",
-    "sppc_destroy", "sppc_last_error", "EXPORTED_SYMBOLS", "STATUS",
+    "sppc_rayleigh_ritz", "sppc_refine_step", "sppc_solve", "sppc_order_info", "sppc_get_stats", "sppc_get_state", "sppc_get_layout",
+    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "EXPORTED_SYMBOLS", "STATUS",
 ]
 
 STATUS = {0: "SPPC_OK", 1: "SPPC_ERR_ARG", 2: "SPPC_ERR_NOT_SYMMETRIC", 3: "SPPC_ERR_LEVELS", 4: "SPPC_ERR_OOM",
@@ -26,6 +26,7 @@ STATUS = {0: "SPPC_OK", 1: "SPPC_ERR_ARG", 2: "SPPC_ERR_NOT_SYMMETRIC", 3: "SPPC
           9: "SPPC_NOT_CONVERGED", 10: "SPPC_ERR_STATE", 11: "SPPC_ERR_NAN"}
 SPPC_OK = 0
 SPPC_NOT_CONVERGED = 9
+SLICE_H = 16  # rows per SELL slice of the device layout
 
 
 class SppcError(RuntimeError):
@@ -43,14 +44,17 @@ class Opts(ctypes.Structure):
     _fields_ = [("p_max", ctypes.c_int32), ("tol", ctypes.c_double), ("minres_tol", ctypes.c_double),
                 ("minres_maxit", ctypes.c_int32), ("small_tol", ctypes.c_double), ("small_block", ctypes.c_int32),
                 ("degeneracy_tol", ctypes.c_double), ("check_symmetry", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("timing", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("timing", ctypes.c_int32), ("spmm_chunk_cols", ctypes.c_int64),
+                ("hybrid", ctypes.c_int32), ("switch_order", ctypes.c_int32), ("hybrid_maxit", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("precond_clamp", ctypes.c_double), ("hybrid_blocks", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("orders", ctypes.c_int32), ("converged", ctypes.c_int32), ("spmv_h", ctypes.c_int64),
                 ("spmv_h11", ctypes.c_int64), ("minres_iters", ctypes.c_int64), ("small_eig_iters", ctypes.c_int64),
                 ("spmm_launches", ctypes.c_int32), ("spmm_ms", ctypes.c_double), ("minres_ms", ctypes.c_double),
-                ("small_eig_ms", ctypes.c_double), ("dense_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+                ("small_eig_ms", ctypes.c_double), ("dense_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("refine_steps", ctypes.c_int32), ("restarts", ctypes.c_int32), ("switched_at", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -68,12 +72,14 @@ _SIGS = {
     "sppc_correct": (_I32, [_VP, _VP]),
     "sppc_rayleigh_ritz": (_I32, [_VP, _VP, _VP, _VP]),
     "sppc_solve": (_I32, [_VP, _D, _I32, _VP, _VP, _I64, _VP, ctypes.POINTER(Stats), _VP]),
+    "sppc_refine_step": (_I32, [_VP, _VP, _VP, _VP]),
     "sppc_order_info": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP, _VP]),
     "sppc_get_stats": (_I32, [_VP, ctypes.POINTER(Stats)]),
     "sppc_get_state": (_I32, [_VP, _I32, _VP, _I64]),
-    "sppc_get_layout": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sppc_get_layout": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sppc_destroy": (_I32, [_VP]),
     "sppc_last_error": (ctypes.c_char_p, [_VP]),
+    "sppc_kernel_launches": (_I64, []),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -178,6 +184,12 @@ def sppc_rayleigh_ritz(h, k: int, stream=None):
     return th, rs
 
 
+def sppc_refine_step(h, k: int, stream=None):
+    th, rs = np.zeros(k), np.zeros(k)
+    _check(h, _lib.sppc_refine_step(h, th.ctypes.data, rs.ctypes.data, _stream(stream)))
+    return th, rs
+
+
 def sppc_solve(h, k: int, tol: float = -1.0, p_max: int = -1, Z=None, stream=None):
     """Algorithm 2 end to end.  Z: optional torch CUDA float64 tensor (n, >=k).
 
@@ -212,15 +224,22 @@ def sppc_get_state(h, which: int, shape) -> np.ndarray:
 
 
 def sppc_get_layout(h) -> dict:
-    ns, n11 = ctypes.c_int64(), ctypes.c_int64()
-    _check(h, _lib.sppc_get_layout(h, ctypes.byref(ns), None, None, ctypes.byref(n11), None, None))
+    ns, n11, nch = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(h, _lib.sppc_get_layout(h, ctypes.byref(ns), None, None, ctypes.byref(n11), None, None,
+                                   ctypes.byref(nch), None))
     sp = np.zeros(ns.value + 1, dtype=np.int64)
-    sr = np.zeros(32 * ns.value, dtype=np.int32)
+    sr = np.zeros(SLICE_H * ns.value, dtype=np.int32)
     sp11 = np.zeros(n11.value + 1, dtype=np.int64)
-    sr11 = np.zeros(32 * n11.value, dtype=np.int32)
+    sr11 = np.zeros(SLICE_H * n11.value, dtype=np.int32)
+    cs = np.zeros(nch.value + 1, dtype=np.int64)
     _check(h, _lib.sppc_get_layout(h, None, sp.ctypes.data, sr.ctypes.data, None, sp11.ctypes.data,
-                                   sr11.ctypes.data))
-    return {"slice_ptr": sp, "slice_rows": sr, "h11_slice_ptr": sp11, "h11_slice_rows": sr11}
+                                   sr11.ctypes.data, None, cs.ctypes.data))
+    return {"slice_ptr": sp, "slice_rows": sr, "h11_slice_ptr": sp11, "h11_slice_rows": sr11,
+            "n_chunks": nch.value, "chunk_slice": cs}
+
+
+def sppc_kernel_launches() -> int:
+    return int(_lib.sppc_kernel_launches())
 
 
 def sppc_destroy(h) -> None:

@@ -50,11 +50,6 @@ enum CoefSlot : int {
   kCoefEnd = 848
 };
 
-struct MinresState {
-  double beta, c_prev, c_cur, s_prev, s_cur, eta, rnorm, beta1, alpha;
-  int done, it;
-};
-
 }  // namespace
 
 struct sppc_ctx {
@@ -69,6 +64,7 @@ struct sppc_ctx {
   SellDev H, H11;
   std::vector<void*> allocs;
   int64_t h_slices = 0, h11_slices = 0;
+  std::vector<int64_t> h_chunk_slice, h11_chunk_slice;  // host copies (SellDev points here)
   std::vector<int64_t> h_slice_ptr, h11_slice_ptr;  // host copies for sppc_get_layout
   std::vector<int32_t> h_slice_rows, h11_slice_rows;
   double h11_lo = 0, h11_hi = 0, h11_norm = 1;
@@ -85,14 +81,16 @@ struct sppc_ctx {
   double *dE = nullptr, *dHt = nullptr, *dGram = nullptr, *dC1 = nullptr, *dC2 = nullptr, *dR1 = nullptr,
          *dR2 = nullptr, *dTheta = nullptr, *dV = nullptr, *dDots = nullptr, *dS = nullptr;
   float2 *dCoef = nullptr, *dRinv = nullptr, *dRecycle = nullptr, *dY = nullptr, *dCoefBig = nullptr;
-  MinresState* dMin = nullptr;
   int* dStatus = nullptr;
+  unsigned* dBar = nullptr;
   float2* partials = nullptr;
   int64_t partial_cap = 0;
   double *stageX = nullptr, *stageY = nullptr;  // sppc_spmm_host staging (n x 8 each)
+  float2* dDiag = nullptr;                        // diag(H), double-float (Jacobi preconditioner)
+  int nev = 0;                                    // Ritz pairs kept by the last Rayleigh-Ritz
 
   // state
-  bool started = false, corrected = false;
+  bool started = false, corrected = false, in_refine = false, t_ready = false;
   int p = 0;
   std::vector<double> E0, theta, resid;
   std::vector<OrderRec> rec;
@@ -248,15 +246,28 @@ __global__ void k_assemble_ht(const double* B, int p, int k, int kp, double* Ht,
 
 // Ritz coefficients Y (compact m x k, ld k) -> padded double-float ((p+1)*kp x kp);
 // theta -> double-float per column.
-__global__ void k_expand_y(const double* V, int p, int k, int kp, const double* th, float2* Y, float2* thdf) {
+__global__ void k_expand_y(const double* V, int ldv, int p, int k, int kp, const double* th, float2* Y,
+                           float2* thdf) {
   const int t = threadIdx.x;
   const int rows = (p + 1) * kp;
   for (int e = t; e < rows * kp; e += blockDim.x) {
     const int r = e / kp, j = e % kp;
     const int a = r / kp, i = r % kp;
-    Y[e] = (i < k && j < k) ? df_from_double(V[(a * k + i) * k + j]) : make_float2(0.f, 0.f);
+    Y[e] = (i < k && j < k) ? df_from_double(V[(a * k + i) * ldv + j]) : make_float2(0.f, 0.f);
   }
   if (t < kp) thdf[t] = (t < k) ? df_from_double(th[t]) : make_float2(0.f, 0.f);
+}
+
+// Thick restart: coefficients of output block b (Ritz vectors b*k .. b*k+k-1) in
+// the padded layout of the block update: out[(a*kp+i)*kp + j] = V[(a*k+i)*ldv + b*k + j].
+__global__ void k_restart_coef(const double* V, int ldv, int p, int k, int kp, int b, float2* out) {
+  const int t = threadIdx.x;
+  const int rows = (p + 1) * kp;
+  for (int e = t; e < rows * kp; e += blockDim.x) {
+    const int r = e / kp, j = e % kp;
+    const int a = r / kp, i = r % kp;
+    out[e] = (i < k && j < k) ? df_from_double(V[(a * k + i) * ldv + b * k + j]) : make_float2(0.f, 0.f);
+  }
 }
 
 // Coefficient sub-block for block updates of multi-block sets: out[(a*8+i)*8+j] =
@@ -278,108 +289,15 @@ __global__ void k_vmat_df(const double* V, int m, int nev, int ldv, float2* out)
   }
 }
 
-__global__ void k_minres_init(const double* bb, int k, int kp, MinresState* st, float2* coef) {
-  const int j = threadIdx.x;
-  if (j >= kp) return;
-  MinresState s{};
-  const double b1 = (j < k) ? sqrt(bb[j]) : 0.0;
-  s.beta = b1;
-  s.beta1 = b1;
-  s.eta = b1;
-  s.rnorm = b1;
-  s.c_prev = s.c_cur = 1.0;
-  s.s_prev = s.s_cur = 0.0;
-  s.done = (b1 > 0.0) ? 0 : 1;
-  s.it = 0;
-  st[j] = s;
-  coef[kMinV + j] = s.done ? make_float2(0.f, 0.f) : df_from_double(1.0 / b1);
-}
-
-// Lanczos step on the projected operator P (H11 - E) P, P = I - psi psi^T, in the
-// order of the oracle: with y = (H11 - E) v and the dots (v,y), (psi,y), (v,psi),
-// (v,v_prev) from one pass, s = psi^T y, alpha = v^T (P y - beta v_prev) and
-// p = P y - beta v_prev - alpha v.
-__global__ void k_minres_a(const double* dots, int kp, MinresState* st, float2* coef) {
-  const int j = threadIdx.x;
-  if (j >= kp) return;
-  MinresState& s = st[j];
-  double a = 0.0, sp = 0.0, be = 0.0;
-  if (!s.done) {
-    sp = dots[kp + j];
-    be = s.beta;
-    a = dots[j] - sp * dots[2 * kp + j] - be * dots[3 * kp + j];
-  }
-  s.alpha = a;
-  coef[kMinA + j] = df_from_double(-sp);
-  coef[kMinA + 8 + j] = df_from_double(s.it == 0 ? 0.0 : -be);
-  coef[kMinA + 16 + j] = df_from_double(-a);
-}
-
-// Lanczos norm beta' = ||p||, Givens rotation and solution update coefficients
-// (MINRES, Paige and Saunders 1975).
-__global__ void k_minres_b(const double* pp, int kp, double tol, MinresState* st, float2* coef, int* flags) {
-  const int j = threadIdx.x;
-  if (j >= kp) return;
-  MinresState& s = st[j];
-  const float2 z = make_float2(0.f, 0.f);
-  if (s.done) {
-    coef[kMinWAlpha + j] = z;
-    coef[kMinW + j] = z;
-    coef[kMinW + 8 + j] = z;
-    coef[kMinX + j] = z;
-    coef[kMinV + j] = z;
-    flags[j] = 1;
-    return;
-  }
-  const double bn = sqrt(fmax(pp[j], 0.0));
-  const double delta = s.c_cur * s.alpha - s.c_prev * s.s_cur * s.beta;
-  const double rho1 = hypot(delta, bn);
-  const double rho2 = s.s_cur * s.alpha + s.c_prev * s.c_cur * s.beta;
-  const double rho3 = s.s_prev * s.beta;
-  s.it += 1;
-  if (rho1 == 0.0) {
-    s.done = 1;
-    coef[kMinWAlpha + j] = z;
-    coef[kMinW + j] = z;
-    coef[kMinW + 8 + j] = z;
-    coef[kMinX + j] = z;
-    coef[kMinV + j] = z;
-    flags[j] = 1;
-    return;
-  }
-  const double cn = delta / rho1, sn = bn / rho1;
-  coef[kMinWAlpha + j] = df_from_double(1.0 / rho1);
-  coef[kMinW + j] = df_from_double(-rho3 / rho1);
-  coef[kMinW + 8 + j] = df_from_double(-rho2 / rho1);
-  coef[kMinX + j] = df_from_double(cn * s.eta);
-  s.rnorm = fabs(sn) * s.rnorm;
-  s.eta = -sn * s.eta;
-  s.c_prev = s.c_cur;
-  s.c_cur = cn;
-  s.s_prev = s.s_cur;
-  s.s_cur = sn;
-  const bool conv = (s.rnorm <= tol * s.beta1) || (bn == 0.0);
-  if (conv) {
-    s.done = 1;
-    coef[kMinV + j] = z;
-  } else {
-    coef[kMinV + j] = df_from_double(1.0 / bn);
-  }
-  s.beta = bn;
-  flags[j] = s.done;
-}
-
-__global__ void k_minres_iters(const MinresState* st, int kp, int* out) {
-  const int j = threadIdx.x;
-  if (j < kp) out[j] = st[j].it;
-}
-
 // ------------------------------------------------------------ SELL builder
 struct SellHost {
   int64_t nslices = 0;
-  std::vector<int64_t> slice_ptr;
+  int nchunks = 1;
+  int64_t chunk_cols = 0;
+  std::vector<int64_t> chunk_slice, slice_ptr;
   std::vector<int32_t> rows, col;
   std::vector<float2> val;
+  std::vector<uint8_t> first, last;
 };
 
 void split_df(double x, float2& out) {
@@ -388,90 +306,126 @@ void split_df(double x, float2& out) {
   out.y = static_cast<float>(x - static_cast<double>(h));
 }
 
-// Rows [0, nrows) keeping only columns < col_limit.  `seg` are segment (level)
-// boundaries within [0, nrows]; rows are sorted by decreasing length inside windows
-// of `sigma` rows that never cross a segment, and cut into slices of 32 rows.
-void build_sell(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t col_limit,
-                const std::vector<int64_t>& seg, int64_t sigma, SellHost& S) {
-  std::vector<int64_t> len(nrows);
+// Rows [0, nrows), columns [0, ncols) cut into chunks of chunk_cols columns
+// (chunk_cols <= 0: one chunk).  For every chunk, inside every segment (level)
+// `seg`, the rows with entries in the chunk are sorted by decreasing entry count
+// within windows of `sigma` rows (stable) and cut into slices of kSliceH rows.  Rows
+// without any entry are listed in chunk 0 so that their output is written.
+void build_sell(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t ncols,
+                const std::vector<int64_t>& seg, int64_t sigma, int64_t chunk_cols, SellHost& S) {
+  const int64_t C = (chunk_cols > 0 && chunk_cols < ncols) ? chunk_cols : ncols;
+  const int nch = (int)((ncols + C - 1) / C);
+  S.nchunks = nch;
+  S.chunk_cols = C;
+  const int W = nch + 1;
+  std::vector<int64_t> off((size_t)nrows * W);
+  S.first.assign(nrows, 0);
+  S.last.assign(nrows, 0);
 #pragma omp parallel for schedule(static)
   for (int64_t r = 0; r < nrows; ++r) {
     const int32_t* b = ci + rp[r];
     const int32_t* e = ci + rp[r + 1];
-    len[r] = (col_limit >= (int64_t)1 << 31) ? (e - b) : (std::lower_bound(b, e, (int32_t)col_limit) - b);
-  }
-  std::vector<int32_t> order(nrows);
-  for (int64_t r = 0; r < nrows; ++r) order[r] = (int32_t)r;
-  std::vector<std::pair<int64_t, int64_t>> windows;
-  std::vector<int64_t> slice_first;  // first position in `order` of each slice
-  std::vector<int32_t> slice_count;
-  for (size_t sgi = 0; sgi + 1 < seg.size(); ++sgi) {
-    const int64_t a = seg[sgi], b = seg[sgi + 1];
-    for (int64_t w = a; w < b; w += sigma) windows.push_back({w, std::min(w + sigma, b)});
-    for (int64_t s = a; s < b; s += 32) {
-      slice_first.push_back(s);
-      slice_count.push_back((int32_t)std::min<int64_t>(32, b - s));
+    int fq = -1, lq = 0;
+    for (int q = 0; q <= nch; ++q) {
+      const int64_t lim = std::min<int64_t>((int64_t)q * C, ncols);
+      off[(size_t)r * W + q] = std::lower_bound(b, e, (int32_t)std::min<int64_t>(lim, INT32_MAX)) - b;
+      if (q > 0 && off[(size_t)r * W + q] > off[(size_t)r * W + q - 1]) {
+        if (fq < 0) fq = q - 1;
+        lq = q - 1;
+      }
     }
+    S.first[r] = (uint8_t)(fq < 0 ? 0 : fq);
+    S.last[r] = (uint8_t)lq;
   }
+  auto len_of = [&](int64_t r, int q) { return off[(size_t)r * W + q + 1] - off[(size_t)r * W + q]; };
+  std::vector<int32_t> slice_chunk;
+  S.chunk_slice.assign(nch + 1, 0);
+  S.slice_ptr.assign(1, 0);
+  S.rows.clear();
+  for (int q = 0; q < nch; ++q) {
+    S.chunk_slice[q] = (int64_t)slice_chunk.size();
+    for (size_t sgi = 0; sgi + 1 < seg.size(); ++sgi) {
+      std::vector<int32_t> part;
+      for (int64_t r = seg[sgi]; r < seg[sgi + 1]; ++r) {
+        const bool empty_row = off[(size_t)r * W + nch] == 0;
+        if (len_of(r, q) > 0 || (q == 0 && empty_row)) part.push_back((int32_t)r);
+      }
+      const int64_t np = (int64_t)part.size();
 #pragma omp parallel for schedule(dynamic, 4)
-  for (int64_t wi = 0; wi < (int64_t)windows.size(); ++wi) {
-    std::stable_sort(order.begin() + windows[wi].first, order.begin() + windows[wi].second,
-                     [&](int32_t x, int32_t y) { return len[x] > len[y]; });
-  }
-  const int64_t ns = (int64_t)slice_first.size();
-  S.nslices = ns;
-  S.slice_ptr.assign(ns + 1, 0);
-  S.rows.assign(ns * 32, -1);
-  for (int64_t s = 0; s < ns; ++s) {
-    int64_t w = 0;
-    for (int l = 0; l < slice_count[s]; ++l) {
-      const int32_t r = order[slice_first[s] + l];
-      S.rows[s * 32 + l] = r;
-      w = std::max(w, len[r]);
+      for (int64_t w0 = 0; w0 < np; w0 += sigma) {
+        std::stable_sort(part.begin() + w0, part.begin() + std::min(w0 + sigma, np),
+                         [&](int32_t x, int32_t y) { return len_of(x, q) > len_of(y, q); });
+      }
+      for (int64_t s0 = 0; s0 < np; s0 += kSliceH) {
+        int64_t w = 0;
+        for (int l = 0; l < kSliceH; ++l) {
+          const int32_t r = (s0 + l < np) ? part[s0 + l] : -1;
+          S.rows.push_back(r);
+          if (r >= 0) w = std::max<int64_t>(w, len_of(r, q));
+        }
+        S.slice_ptr.push_back(S.slice_ptr.back() + kSliceH * w);
+        slice_chunk.push_back(q);
+      }
     }
-    S.slice_ptr[s + 1] = S.slice_ptr[s] + 32 * w;
   }
+  S.chunk_slice[nch] = (int64_t)slice_chunk.size();
+  const int64_t ns = (int64_t)slice_chunk.size();
+  S.nslices = ns;
   S.col.assign(S.slice_ptr[ns], 0);
   S.val.assign(S.slice_ptr[ns], make_float2(0.f, 0.f));
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t s = 0; s < ns; ++s) {
+    const int q = slice_chunk[s];
     const int64_t base = S.slice_ptr[s];
-    const int64_t w = (S.slice_ptr[s + 1] - base) / 32;
-    for (int l = 0; l < 32; ++l) {
-      const int32_t r = S.rows[s * 32 + l];
-      const int64_t lr = (r >= 0) ? len[r] : 0;
+    const int64_t w = (S.slice_ptr[s + 1] - base) / kSliceH;
+    const int32_t pad_col = (int32_t)std::min<int64_t>((int64_t)q * C, ncols - 1);
+    for (int l = 0; l < kSliceH; ++l) {
+      const int32_t r = S.rows[s * kSliceH + l];
+      const int64_t lr = (r >= 0) ? len_of(r, q) : 0;
+      const int64_t o0 = (r >= 0) ? rp[r] + off[(size_t)r * W + q] : 0;
       for (int64_t t = 0; t < w; ++t) {
-        const int64_t o = base + 32 * t + l;
+        const int64_t o = base + kSliceH * t + l;
         if (t < lr) {
-          S.col[o] = ci[rp[r] + t];
-          split_df(va[rp[r] + t], S.val[o]);
+          S.col[o] = ci[o0 + t];
+          split_df(va[o0 + t], S.val[o]);
         } else {
-          S.col[o] = (r >= 0) ? r : 0;
+          S.col[o] = pad_col;
         }
       }
     }
   }
 }
 
-sppc_status upload_sell(sppc_ctx* h, const SellHost& S, SellDev& D, int64_t nrows) {
+sppc_status upload_sell(sppc_ctx* h, SellHost& S, SellDev& D, int64_t nrows, std::vector<int64_t>& chunk_store) {
   int64_t* sp;
   int32_t *rows, *col;
   float2* val;
+  uint8_t *fr, *la;
   CK(dalloc(h, &sp, S.slice_ptr.size()));
   CK(dalloc(h, &rows, S.rows.size()));
   CK(dalloc(h, &col, S.col.size()));
   CK(dalloc(h, &val, S.val.size()));
+  CK(dalloc(h, &fr, S.first.size()));
+  CK(dalloc(h, &la, S.last.size()));
   CK(cudaMemcpyAsync(sp, S.slice_ptr.data(), sizeof(int64_t) * S.slice_ptr.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(rows, S.rows.data(), sizeof(int32_t) * S.rows.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(col, S.col.data(), sizeof(int32_t) * S.col.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(val, S.val.data(), sizeof(float2) * S.val.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(fr, S.first.data(), S.first.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(la, S.last.data(), S.last.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  chunk_store = S.chunk_slice;
   D.nslices = S.nslices;
   D.nrows = nrows;
+  D.nchunks = S.nchunks;
+  D.chunk_cols = S.chunk_cols;
+  D.chunk_slice = chunk_store.data();
   D.slice_ptr = sp;
   D.slice_rows = rows;
   D.col = col;
   D.val = val;
+  D.row_first = fr;
+  D.row_last = la;
   return SPPC_OK;
 }
 
@@ -550,7 +504,7 @@ sppc_status rotate_set(sppc_ctx* h, float2** X, float2** Y, int nb, const float2
   L.n = nb;
   for (int a = 0; a < nb; ++a) L.p[a] = X[a];
   for (int ob = 0; ob < nb; ++ob) {
-    k_subblock<<<1, 128, 0, s>>>(M16, 16, nb, ob, h->dCoefBig);
+    k_subblock<<<1, 128, 0, s>>>(M16, 16, nb, ob, h->dCoefBig); count_launch();
     CK(cudaGetLastError());
     CK(update(Y[ob], nullptr, nullptr, L, h->dCoefBig, 8, 0, h->n1, s));
   }
@@ -613,7 +567,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
     h->stats.spmv_h11 += 8 * nb;
     CKS(gram_set(h, X, AX, nb, h->dS));
     CK(syev_lowest(h->dS, 16, b, b, h->dTheta, h->dV, b, s));
-    k_vmat_df<<<1, 256, 0, s>>>(h->dV, b, b, b, h->dRinv);
+    k_vmat_df<<<1, 256, 0, s>>>(h->dV, b, b, b, h->dRinv); count_launch();
     CK(cudaGetLastError());
     CKS(rotate_set(h, X, Tmp, nb, h->dRinv));
     for (int a = 0; a < nb; ++a) std::swap(X[a], Tmp[a]);
@@ -726,7 +680,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
   std::vector<double> e0p(h->kp, 0.0);
   for (int j = 0; j < k; ++j) e0p[j] = h->E0[j];
   CK(cudaMemcpyAsync(h->dE, e0p.data(), sizeof(double) * h->kp, cudaMemcpyHostToDevice, s));
-  k_set_e0<<<1, 32, 0, s>>>(h->dE, k, h->kp, h->dCoef);
+  k_set_e0<<<1, 32, 0, s>>>(h->dE, k, h->kp, h->dCoef); count_launch();
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   return SPPC_OK;
@@ -734,120 +688,67 @@ sppc_status small_eigensolve(sppc_ctx* h) {
 
 // ----------------------------------------------------------------- MINRES
 // Solves (H0_hat - E_k) x = b1 for the k columns at once on the complement of
-// psi_hat_k (Eq. sm_lin_proj): the right-hand side is already deflated and every
-// new Lanczos vector is projected against psi_hat_k, so the singular direction
-// never enters the Krylov space.  x0 = 0; stop at ||r|| <= minres_tol ||b1||.
+// psi_hat_k (Eq. sm_lin_proj) with the persistent kernel of k_minres.cu (one
+// cooperative launch); the right-hand side is already deflated.  x0 = 0; stop at
+// ||r|| <= minres_tol ||b1||.  Afterwards x is re-projected onto the complement.
 sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
   cudaStream_t s = h->stream;
   const int kp = h->kp;
   const int64_t n1 = h->n1;
   float2* c = h->dCoef;
-  {
-    const float2* A[1] = {h->b1};
-    const float2* B[1] = {h->b1};
-    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-  }
-  k_minres_init<<<1, 32, 0, s>>>(h->dDots, h->k, kp, h->dMin, c);
-  CK(cudaGetLastError());
-  float2 *v = h->mv, *vprev = h->mvprev, *p = h->mp, *y = h->my, *w1 = h->mw1, *w2 = h->mw2, *x = h->mx;
-  CK(combine_diag(v, h->b1, c + kMinV, BlockList{}, c, kp, 0, n1, s));
-  CK(fill_zero(vprev, n1 * kp, s));
-  CK(fill_zero(w1, n1 * kp, s));
-  CK(fill_zero(w2, n1 * kp, s));
-  CK(fill_zero(x, n1 * kp, s));
   int maxit = h->opt.minres_maxit;
   if (maxit <= 0) maxit = (int)std::min<int64_t>(200000, 20 * n1);
-  std::vector<int> flags(kp, 0);
-  int* dflags = h->dStatus + 4;
-  int it = 0;
-  bool all_done = false;
-  for (it = 1; it <= maxit; ++it) {
-    Epi e;
-    e.beta = c + kShiftNegE;
-    CK(spmm(h->H11, kp, v, y, e, s));
-    {
-      const float2* A[4] = {v, h->psi_hat, v, v};
-      const float2* B[4] = {y, y, h->psi_hat, vprev};
-      CK(coldots(A, B, 4, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    }
-    k_minres_a<<<1, 32, 0, s>>>(h->dDots, kp, h->dMin, c);
-    CK(cudaGetLastError());
-    {
-      BlockList L;
-      L.n = 3;
-      L.p[0] = h->psi_hat;
-      L.p[1] = vprev;
-      L.p[2] = v;
-      CK(combine_diag(p, y, c + kOnes, L, c + kMinA, kp, 0, n1, s));
-    }
-    {
-      const float2* A[1] = {p};
-      const float2* B[1] = {p};
-      CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    }
-    k_minres_b<<<1, 32, 0, s>>>(h->dDots, kp, h->opt.minres_tol, h->dMin, c, dflags);
-    CK(cudaGetLastError());
-    {
-      BlockList L;
-      L.n = 2;
-      L.p[0] = w2;
-      L.p[1] = w1;
-      CK(combine_diag(w2, v, c + kMinWAlpha, L, c + kMinW, kp, 0, n1, s));  // w_new into w2's buffer
-      std::swap(w1, w2);                                                    // w1 = w_new, w2 = old w1
-      CK(combine_diag(x, x, c + kOnes, one(w1), c + kMinX, kp, 0, n1, s));
-      CK(combine_diag(vprev, p, c + kMinV, BlockList{}, c, kp, 0, n1, s));  // v_next into vprev's buffer
-      std::swap(v, vprev);                                                   // v = v_next, vprev = old v
-    }
-    h->stats.spmv_h11 += h->k;
-    if ((it & 7) == 0 || it == maxit) {
-      CK(cudaMemcpyAsync(flags.data(), dflags, sizeof(int) * kp, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      all_done = true;
-      for (int j = 0; j < h->k; ++j) all_done &= (flags[j] != 0);
-      if (all_done) break;
-    }
-  }
+  int* dstat = h->dStatus + 32;
+  CK(minres_persistent(h->H11, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
+                       h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s));
   // x -= psi_hat (psi_hat^T x): keep the solution on the complement of psi_hat_k
+  float2* x = h->mx;
   {
     const float2* A[1] = {h->psi_hat};
     const float2* B[1] = {x};
     CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, h->k, kp, c + kDefl);
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, h->k, kp, c + kDefl); count_launch();
     CK(cudaGetLastError());
     CK(combine_diag(x, x, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
   }
-  std::vector<int> its(kp, 0);
-  k_minres_iters<<<1, 32, 0, s>>>(h->dMin, kp, h->dStatus + 16);
-  CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(its.data(), h->dStatus + 16, sizeof(int) * kp, cudaMemcpyDeviceToHost, s));
+  int st[10] = {0};
+  CK(cudaMemcpyAsync(st, dstat, sizeof(int) * 10, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (st[0]) return fail(h, SPPC_ERR_TIMEOUT, "MINRES: a grid barrier timed out");
   iters.assign(h->k, 0);
   int mx = 0;
   for (int j = 0; j < h->k; ++j) {
-    iters[j] = its[j];
-    mx = std::max(mx, its[j]);
+    iters[j] = st[2 + j];
+    mx = std::max(mx, st[2 + j]);
   }
   h->stats.minres_iters += mx;
-  if (!all_done) return fail(h, SPPC_ERR_MINRES, "MINRES reached %d iterations without meeting the tolerance", maxit);
-  // copy x into the leading n1 rows of Psi^(p)
+  h->stats.spmv_h11 += (int64_t)h->k * std::abs(st[1]);
+  if (st[1] < 0) return fail(h, SPPC_ERR_MINRES, "MINRES reached %d iterations without meeting the tolerance", maxit);
   return SPPC_OK;
 }
 
 // ------------------------------------------------------- Rayleigh-Ritz core
-sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz) {
+// Rayleigh-Ritz on blocks 0..p: border the projected matrix with Q^T W_p (Eq.
+// proj), its nev = min(2k, m) lowest eigenpairs (the first k are the Ritz pairs;
+// 2k are kept for a thick restart), Ritz residuals (Eq. rrn).  Optionally writes
+// the Ritz vectors (Z) and the preconditioned residual block (T, see ritz_resid).
+sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, float2* T = nullptr,
+                    const float2* diag = nullptr) {
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
-  // border B = Q_{0..p}^T W_p (Eq. proj)
   CK(gram(blocks(h->Q, n, kp, 0, p + 1), blk(h->W, n, kp, p), kp, 0, n, h->dGram, h->partials, h->partial_cap, s));
-  k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, p, k, kp, h->dHt, h->mmax);
+  k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, p, k, kp, h->dHt, h->mmax); count_launch();
   CK(cudaGetLastError());
   const int m = (p + 1) * k;
-  CK(syev_lowest(h->dHt, h->mmax, m, k, h->dTheta, h->dV, k, s));
-  k_expand_y<<<1, 256, 0, s>>>(h->dV, p, k, kp, h->dTheta, h->dY, h->dCoef + kTheta);
+  const int nev = std::min(std::min(2 * k, m), 16);
+  h->nev = nev;
+  CK(syev_lowest(h->dHt, h->mmax, m, nev, h->dTheta, h->dV, nev, s));
+  k_expand_y<<<1, 256, 0, s>>>(h->dV, nev, p, k, kp, h->dTheta, h->dY, h->dCoef + kTheta); count_launch();
   CK(cudaGetLastError());
   CK(ritz_resid(blocks(h->Q, n, kp, 0, p + 1), blocks(h->W, n, kp, 0, p + 1), h->dY, h->dCoef + kTheta, kp, n,
-                h->dDots, h->partials, h->partial_cap, want_z ? Z : nullptr, ldz, k, s));
+                h->dDots, h->partials, h->partial_cap, want_z ? Z : nullptr, ldz, k, T, diag,
+                (float)h->opt.precond_clamp, s));
   std::vector<double> th(k), r2(kp);
   CK(cudaMemcpyAsync(th.data(), h->dTheta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(r2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
@@ -855,6 +756,112 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz) {
   h->theta = th;
   h->resid.assign(k, 0.0);
   for (int j = 0; j < k; ++j) h->resid[j] = std::sqrt(std::max(r2[j], 0.0)) / std::fabs(th[j]);
+  return SPPC_OK;
+}
+
+// Block Gram-Schmidt with the projector applied twice (Eq. blkGS) of src against
+// Q blocks 0..p-1, then CholeskyQR2 (Eq. QR) into Q block p (Eq. Qp).  Leaves the
+// projection coefficients C = C1 + C2 in dC1 and R = R2 R1 in the recycle
+// coefficients [C; R] (Eq. HPsip).  dd (host, 2*kp) receives ||src_j||^2 and
+// ||Phi_j||^2 (valid after the next stream synchronisation).
+sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd) {
+  cudaStream_t s = h->stream;
+  const int k = h->k, kp = h->kp;
+  const int64_t n = h->n;
+  float2* c = h->dCoef;
+  BlockList Qs = blocks(h->Q, n, kp, 0, p);
+  const int nc = p * kp * kp;
+  CK(gram(Qs, src, kp, 0, n, h->dC1, h->partials, h->partial_cap, s));
+  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig); count_launch();
+  CK(cudaGetLastError());
+  CK(update(h->T1, src, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
+  CK(gram(Qs, h->T1, kp, 0, n, h->dC2, h->partials, h->partial_cap, s));
+  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig); count_launch();
+  CK(cudaGetLastError());
+  CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
+  k_addmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, h->dC2, nc, h->dC1); count_launch();  // C = C1 + C2
+  CK(cudaGetLastError());
+  {
+    const float2* A[2] = {src, h->T1};
+    const float2* B[2] = {src, h->T1};
+    CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+  }
+  CK(cudaMemcpyAsync(dd, h->dDots, sizeof(double) * 2 * kp, cudaMemcpyDeviceToHost, s));
+  float2* q = blk(h->Q, n, kp, p);
+  CK(gram(one(h->T1), h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
+  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR1, h->dRinv, h->dStatus, s));
+  CK(update(h->T2, nullptr, nullptr, one(h->T1), h->dRinv, kp, 0, n, s));
+  CK(gram(one(h->T2), h->T2, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
+  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR2, h->dRinv, h->dStatus + 1, s));
+  CK(update(q, nullptr, nullptr, one(h->T2), h->dRinv, kp, 0, n, s));
+  k_recycle_coefs<<<1, 256, 0, s>>>(h->dC1, p, kp, h->dR2, h->dR1, h->dRecycle); count_launch();
+  CK(cudaGetLastError());
+  int st[2] = {0, 0};
+  CK(cudaMemcpyAsync(st, h->dStatus, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st[0] || st[1])
+    return fail(h, SPPC_ERR_BREAKDOWN, "CholeskyQR breakdown appending block %d (rank-deficient block)", p);
+  return SPPC_OK;
+}
+
+// Thick restart of the continuation: Q <- Q Y_2k, W <- W Y_2k (two blocks of k
+// Ritz vectors, the 2k lowest), projected matrix recomputed from the new blocks.
+sppc_status restart(sppc_ctx* h) {
+  cudaStream_t s = h->stream;
+  const int k = h->k, kp = h->kp, p = h->p;
+  const int64_t n = h->n;
+  if (h->nev < 2 * k) return fail(h, SPPC_ERR_STATE, "restart needs 2k Ritz vectors");
+  for (int b = 0; b < 2; ++b) {
+    k_restart_coef<<<1, 256, 0, s>>>(h->dV, h->nev, p, k, kp, b, h->dCoefBig); count_launch();
+    CK(cudaGetLastError());
+    CK(update(blk(h->Psi, n, kp, b), nullptr, nullptr, blocks(h->Q, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n, s));
+    CK(update(blk(h->Psi, n, kp, 2 + b), nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n,
+              s));
+  }
+  CK(cudaMemcpyAsync(h->Q, h->Psi, sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->W, blk(h->Psi, n, kp, 2), sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
+  for (int b = 0; b < 2; ++b) {
+    CK(gram(blocks(h->Q, n, kp, 0, b + 1), blk(h->W, n, kp, b), kp, 0, n, h->dGram, h->partials, h->partial_cap,
+            s));
+    k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, b, k, kp, h->dHt, h->mmax); count_launch();
+    CK(cudaGetLastError());
+  }
+  h->p = 1;
+  h->stats.restarts += 1;
+  return SPPC_OK;
+}
+
+// One step of the continuation after SPPC (block Davidson, Jacobi-preconditioned
+// residuals; without preconditioner the block Krylov extension): from the last
+// Rayleigh-Ritz pairs, T = preconditioned residuals, thick restart if the basis
+// is full, orthogonalise T and append it, k SpMVs, Rayleigh-Ritz.
+sppc_status refine_step(sppc_ctx* h) {
+  const int kp = h->kp;
+  const int64_t n = h->n;
+  // T from the current Ritz pairs: written by the previous Rayleigh-Ritz pass when
+  // it already ran in continuation mode, else one extra pass over Q and W
+  if (!h->t_ready) {
+    CK(ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
+                  n, h->dDots, h->partials, h->partial_cap, nullptr, 0, 0, h->HPsi,
+                  h->opt.precond ? h->dDiag : nullptr, (float)h->opt.precond_clamp, h->stream));
+  }
+  h->t_ready = false;
+  if (h->p + 1 >= std::min(h->pmax + 1, h->opt.hybrid_blocks)) CKS(restart(h));
+  std::vector<double> dd(2 * kp);
+  CKS(orth_append(h, h->HPsi, h->p + 1, dd.data()));
+  h->p += 1;
+  CKS(big_spmm(h, blk(h->Q, n, kp, h->p), blk(h->W, n, kp, h->p), kp));
+  h->stats.spmv_h += h->k;
+  CKS(rr_core(h, h->p, false, nullptr, 0, h->HPsi, h->opt.precond ? h->dDiag : nullptr));
+  h->t_ready = true;
+  OrderRec r;
+  r.theta = h->theta;
+  r.resid = h->resid;
+  r.angle.resize(h->k);
+  for (int j = 0; j < h->k; ++j) r.angle[j] = std::sqrt(std::max(dd[kp + j], 0.0) / std::max(dd[j], 1e-300));
+  h->rec.push_back(r);
+  h->stats.refine_steps += 1;
+  if (h->opt.timing) CKS(collect_timing(h));
   return SPPC_OK;
 }
 
@@ -882,9 +889,18 @@ void sppc_default_opts(sppc_opts* o) {
   o->check_symmetry = 0;
   o->seed = 0;
   o->timing = 0;
+  o->spmm_chunk_cols = -1;
+  o->hybrid = 0;
+  o->switch_order = 15;
+  o->hybrid_maxit = 1000;
+  o->precond = 1;
+  o->precond_clamp = 1e-2;
+  o->hybrid_blocks = 0;
 }
 
 const char* sppc_last_error(sppc_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int64_t sppc_kernel_launches(void) { return (int64_t)launch_count(); }
 
 sppc_status sppc_destroy(sppc_handle h) {
   if (!h) return SPPC_OK;
@@ -922,6 +938,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "p_max out of range (k*(p_max+1) must be <= 144)");
 
   h = new sppc_ctx();
+  if (opt.hybrid_blocks <= 0 || opt.hybrid_blocks > opt.p_max + 1) opt.hybrid_blocks = opt.p_max + 1;
+  if (opt.hybrid_blocks < 3) opt.hybrid_blocks = 3;
   h->opt = opt;
   h->stream = static_cast<cudaStream_t>(stream);
   h->n = n;
@@ -1012,8 +1030,11 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   {
     SellHost S;
     std::vector<int64_t> seg(h->lev.begin(), h->lev.end());
-    build_sell(n, rp, ci, va, (int64_t)1 << 31, seg, 1024, S);
-    sppc_status st = upload_sell(h, S, h->H, n);
+    int64_t chunk = opt.spmm_chunk_cols;
+    if (chunk == 0) chunk = 655360;  // 40 MB of an 8-column double-float block
+    if (chunk > 0 && (n + chunk - 1) / chunk > 255) chunk = (n + 254) / 255;
+    build_sell(n, rp, ci, va, n, seg, 1024, chunk, S);
+    sppc_status st = upload_sell(h, S, h->H, n, h->h_chunk_slice);
     if (st != SPPC_OK) return bail(st);
     h->h_slices = S.nslices;
     h->h_slice_ptr = std::move(S.slice_ptr);
@@ -1022,12 +1043,26 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   {
     SellHost S;
     std::vector<int64_t> seg = {0, n1};
-    build_sell(n1, rp, ci, va, n1, seg, 1024, S);
-    sppc_status st = upload_sell(h, S, h->H11, n1);
+    build_sell(n1, rp, ci, va, n1, seg, 1024, 0, S);
+    sppc_status st = upload_sell(h, S, h->H11, n1, h->h11_chunk_slice);
     if (st != SPPC_OK) return bail(st);
     h->h11_slices = S.nslices;
     h->h11_slice_ptr = std::move(S.slice_ptr);
     h->h11_slice_rows = std::move(S.rows);
+  }
+  // diag(H) for the preconditioned continuation
+  {
+    std::vector<float2> dg(n, make_float2(0.f, 0.f));
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n; ++r) {
+      const int32_t* b = ci + rp[r];
+      const int32_t* e = ci + rp[r + 1];
+      const int32_t* f = std::lower_bound(b, e, (int32_t)r);
+      if (f != e && *f == r) split_df(va[rp[r] + (f - b)], dg[r]);
+    }
+    cudaError_t e = dalloc(h, &h->dDiag, (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(h->dDiag, dg.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_OOM, "diag upload failed: %s", cudaGetErrorString(e)));
   }
   // work buffers
   {
@@ -1057,7 +1092,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     D(&h->dR1, 256);
     D(&h->dR2, 256);
     D(&h->dTheta, 16);
-    D(&h->dV, 144 * 16);
+    D(&h->dV, 160 * 16);
     D(&h->dDots, 64);
     D(&h->dS, 256);
     A(&h->dCoef, kCoefEnd);
@@ -1065,14 +1100,14 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     A(&h->dRecycle, (size_t)kMaxBlocks * 64);
     A(&h->dY, (size_t)kMaxBlocks * 64);
     A(&h->dCoefBig, (size_t)kMaxBlocks * 64);
-    if (e == cudaSuccess) e = dalloc(h, &h->dMin, 16);
     if (e == cudaSuccess) e = dalloc(h, &h->dStatus, 64);
+    if (e == cudaSuccess) e = dalloc(h, &h->dBar, 4);
     h->partial_cap = ((n + 2047) / 2048 + 1) * (int64_t)kMaxBlocks * 64;
     A(&h->partials, (size_t)h->partial_cap);
     if (e != cudaSuccess)
       return bail(fail(h, e == cudaErrorMemoryAllocation ? SPPC_ERR_OOM : SPPC_ERR_CUDA, "allocation failed: %s",
                        cudaGetErrorString(e)));
-    k_set_consts<<<1, 32, 0, h->stream>>>(h->dCoef);
+    k_set_consts<<<1, 32, 0, h->stream>>>(h->dCoef); count_launch();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dHt, 0, sizeof(double) * h->mmax * h->mmax, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1091,7 +1126,7 @@ sppc_status sppc_spmm(sppc_handle h, const double* X, int64_t ldx, double* Y, in
   h->stream = s;
   const int kp = (ncols + 1) / 2 * 2;
   CK(f64_to_df(X, ldx, ncols, h->T1, kp, 0, h->n, s));
-  CKS(big_spmm(h, h->T1, h->T2, kp));
+  CK(spmm(h->H, kp, h->T1, h->T2, Epi{}, s));
   CK(df_to_f64(h->T2, kp, Y, ldy, ncols, 0, h->n, s));
   return SPPC_OK;
 }
@@ -1123,10 +1158,14 @@ sppc_status sppc_start(sppc_handle h, double* theta, double* resid, void* stream
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   h->stream = s;
   h->stats = sppc_stats{};
+  h->pending.clear();
+  h->evnext = 0;
   h->rec.clear();
   h->p = 0;
   h->started = false;
   h->corrected = false;
+  h->in_refine = false;
+  h->t_ready = false;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (h->opt.timing) {
     t0 = next_event(h);
@@ -1167,7 +1206,8 @@ sppc_status sppc_start(sppc_handle h, double* theta, double* resid, void* stream
 
 sppc_status sppc_correct(sppc_handle h, void* stream) {
   if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
-  if (!h->started || h->corrected) return fail(h, SPPC_ERR_STATE, "sppc_correct needs sppc_start / rayleigh_ritz first");
+  if (!h->started || h->corrected || h->in_refine)
+    return fail(h, SPPC_ERR_STATE, "sppc_correct needs sppc_start / rayleigh_ritz first (and no refinement yet)");
   if (h->p + 1 > h->pmax) return fail(h, SPPC_ERR_STATE, "p_max orders already done");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   h->stream = s;
@@ -1194,7 +1234,7 @@ sppc_status sppc_correct(sppc_handle h, void* stream) {
     const float2* B[1] = {h->vps};
     CK(coldots(A, B, 1, kp, 0, n1, h->dE + (size_t)p * kp, h->partials, h->partial_cap, s));
   }
-  k_rhs_coefs<<<1, 32, 0, s>>>(h->dE, p, k, kp, c);
+  k_rhs_coefs<<<1, 32, 0, s>>>(h->dE, p, k, kp, c); count_launch();
   CK(cudaGetLastError());
   // rows >= n1: Psi^(p)_2 = -b2 / E^(0) (Eq. sm_first)
   {
@@ -1216,7 +1256,7 @@ sppc_status sppc_correct(sppc_handle h, void* stream) {
     const float2* A[1] = {h->psi_hat};
     const float2* B[1] = {h->b1};
     CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl);
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl); count_launch();
     CK(cudaGetLastError());
     CK(combine_diag(h->b1, h->b1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
   }
@@ -1241,45 +1281,12 @@ sppc_status sppc_correct(sppc_handle h, void* stream) {
     CK(cudaEventElapsedTime(&ms, t0, t1));
     h->stats.minres_ms += ms;
   }
-  // block Gram-Schmidt, projector applied twice (Eq. blkGS)
-  BlockList Qs = blocks(h->Q, n, kp, 0, p);
-  const int nc = p * kp * kp;
-  CK(gram(Qs, Psip, kp, 0, n, h->dC1, h->partials, h->partial_cap, s));
-  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig);
-  CK(cudaGetLastError());
-  CK(update(h->T1, Psip, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
-  CK(gram(Qs, h->T1, kp, 0, n, h->dC2, h->partials, h->partial_cap, s));
-  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig);
-  CK(cudaGetLastError());
-  CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
-  k_addmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, h->dC2, nc, h->dC1);  // C = C1 + C2
-  CK(cudaGetLastError());
-  // angle diagnostics ||Phi_j|| / ||Psi_j^(p)||
-  {
-    const float2* A[2] = {Psip, h->T1};
-    const float2* B[2] = {Psip, h->T1};
-    CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
-  }
+  // block Gram-Schmidt twice (Eq. blkGS) + CholeskyQR2 (Eq. QR), q^(p) -> Q block p
   std::vector<double> dd(2 * kp);
-  CK(cudaMemcpyAsync(dd.data(), h->dDots, sizeof(double) * 2 * kp, cudaMemcpyDeviceToHost, s));
-  // CholeskyQR2: Phi = q R (Eq. QR)
-  float2* q = blk(h->Q, n, kp, p);
-  CK(gram(one(h->T1), h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
-  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR1, h->dRinv, h->dStatus, s));
-  CK(update(h->T2, nullptr, nullptr, one(h->T1), h->dRinv, kp, 0, n, s));
-  CK(gram(one(h->T2), h->T2, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
-  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR2, h->dRinv, h->dStatus + 1, s));
-  CK(update(q, nullptr, nullptr, one(h->T2), h->dRinv, kp, 0, n, s));
-  // recycle coefficients [C; R2 R1] for H Psi^(p) (Eq. HPsip)
-  k_recycle_coefs<<<1, 256, 0, s>>>(h->dC1, p, kp, h->dR2, h->dR1, h->dRecycle);
-  CK(cudaGetLastError());
-  int st[2] = {0, 0};
-  CK(cudaMemcpyAsync(st, h->dStatus, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  CKS(orth_append(h, Psip, p, dd.data()));
   std::vector<double> ep(kp);
   CK(cudaMemcpyAsync(ep.data(), h->dE + (size_t)p * kp, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (st[0] || st[1])
-    return fail(h, SPPC_ERR_BREAKDOWN, "CholeskyQR breakdown at order %d (rank-deficient correction block)", p);
   rec.E.assign(ep.begin(), ep.begin() + k);
   rec.angle.resize(k);
   for (int j = 0; j < k; ++j) rec.angle[j] = std::sqrt(std::max(dd[kp + j], 0.0) / std::max(dd[j], 1e-300));
@@ -1320,6 +1327,7 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
   if (p_max < 0) p_max = h->pmax;
   if (p_max > h->pmax) return fail(h, SPPC_ERR_ARG, "p_max exceeds the p_max given at create");
   if (Z && ldz < h->k) return fail(h, SPPC_ERR_ARG, "ldz < k");
+  if (h->opt.hybrid && h->pmax < 3) return fail(h, SPPC_ERR_ARG, "the continuation needs p_max >= 3");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (h->opt.timing) {
@@ -1329,14 +1337,23 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
   }
   CKS(sppc_start(h, nullptr, nullptr, stream));
   bool conv = all_converged(h, tol);
-  while (!conv && h->p < p_max) {
+  const int sppc_orders = h->opt.hybrid ? std::min(p_max, h->opt.switch_order) : p_max;
+  while (!conv && h->p < sppc_orders) {
     CKS(sppc_correct(h, stream));
     CKS(sppc_rayleigh_ritz(h, nullptr, nullptr, stream));
     conv = all_converged(h, tol);
   }
+  h->stats.orders = h->p;
+  if (h->opt.hybrid) {
+    h->stats.switched_at = h->p;
+    h->in_refine = true;
+    while (!conv && h->stats.refine_steps < h->opt.hybrid_maxit) {
+      CKS(refine_step(h));
+      conv = all_converged(h, tol);
+    }
+  }
   if (Z) CKS(rr_core(h, h->p, true, Z, ldz));
   h->stats.converged = conv ? 1 : 0;
-  h->stats.orders = h->p;
   if (h->opt.timing) {
     cudaEventRecord(t1, s);
     cudaEventSynchronize(t1);
@@ -1351,6 +1368,19 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
   if (resid) std::copy(h->resid.begin(), h->resid.end(), resid);
   if (stats) *stats = h->stats;
   return conv ? SPPC_OK : SPPC_NOT_CONVERGED;
+}
+
+sppc_status sppc_refine_step(sppc_handle h, double* theta, double* resid, void* stream) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (!h->started || h->corrected) return fail(h, SPPC_ERR_STATE, "sppc_refine_step needs a finished Rayleigh-Ritz step");
+  if (h->pmax < 3) return fail(h, SPPC_ERR_ARG, "the continuation needs p_max >= 3");
+  h->stream = static_cast<cudaStream_t>(stream);
+  if (!h->in_refine) h->stats.switched_at = h->p;
+  h->in_refine = true;
+  CKS(refine_step(h));
+  if (theta) std::copy(h->theta.begin(), h->theta.end(), theta);
+  if (resid) std::copy(h->resid.begin(), h->resid.end(), resid);
+  return SPPC_OK;
 }
 
 sppc_status sppc_order_info(sppc_handle h, int32_t p, double* E, double* angle, double* theta, double* resid,
@@ -1435,8 +1465,11 @@ sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t co
 }
 
 sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr, int32_t* slice_rows,
-                            int64_t* n11_slices, int64_t* h11_slice_ptr, int32_t* h11_slice_rows) {
+                            int64_t* n11_slices, int64_t* h11_slice_ptr, int32_t* h11_slice_rows, int32_t* n_chunks,
+                            int64_t* chunk_slice) {
   if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (n_chunks) *n_chunks = h->H.nchunks;
+  if (chunk_slice) std::copy(h->h_chunk_slice.begin(), h->h_chunk_slice.end(), chunk_slice);
   if (n_slices) *n_slices = h->h_slices;
   if (n11_slices) *n11_slices = h->h11_slices;
   if (slice_ptr) std::copy(h->h_slice_ptr.begin(), h->h_slice_ptr.end(), slice_ptr);

@@ -54,6 +54,14 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
   return fast_two_sum(p, e);
 }
 
+// a / b: fp32 quotient, remainder a - q1*b in double-float, corrected quotient.
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {
+  const float q1 = __fdiv_rn(a.x, b.x);
+  const float2 r = df_sub(a, df_mul(make_float2(q1, 0.f), b));
+  const float q2 = __fdiv_rn(r.x, b.x);
+  return fast_two_sum(q1, q2);
+}
+
 // Accumulator (sh, sl): sh is the plain fp32 running sum, sl collects every
 // rounding error exactly produced (TwoSum) plus the low-order product terms.
 // sl is left unnormalised between calls; acc_norm() folds it back.

@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(256) k_coldots(Pairs P, int nq, int64_t r0, in
 template <int KP>
 __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, const float2* __restrict__ Y,
                                                     const float2* __restrict__ theta, int64_t n, float2* partials,
-                                                    double* Zout, int64_t ldz, int ncols) {
+                                                    double* Zout, int64_t ldz, int ncols, float2* Tout,
+                                                    const float2* __restrict__ diag, float clamp) {
   extern __shared__ float2 sy[];
   const int ny = Q.n * KP * KP;
   for (int t = threadIdx.x; t < ny; t += blockDim.x) sy[t] = Y[t];
@@ -223,6 +224,16 @@ __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, c
       const float2 d = df_sub(acc_get(hh[j], hl[j]), df_mul(sth[j], z));
       acc_mac(rh[j], rl[j], d, d);
       if (Zout && j < ncols) Zout[r * ldz + j] = df_to_double(z);
+      if (Tout) {
+        // preconditioned residual d / (H_rr - theta_j), denominator clamped to |.| >= clamp
+        float2 t = d;
+        if (diag) {
+          float2 den = df_sub(diag[r], sth[j]);
+          if (fabsf(den.x) < clamp) den = make_float2(den.x < 0.f ? -clamp : clamp, 0.f);
+          t = df_div(d, den);
+        }
+        Tout[r * KP + j] = t;
+      }
     }
   }
 #pragma unroll
@@ -275,13 +286,13 @@ cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_
   if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(nchunks);
   switch (kp) {
-    case 2: k_gram<2><<<g, 64, 0, s>>>(A, B, r0, r1, partials); break;
-    case 4: k_gram<4><<<g, 128, 0, s>>>(A, B, r0, r1, partials); break;
-    case 6: k_gram<6><<<g, 192, 0, s>>>(A, B, r0, r1, partials); break;
-    case 8: k_gram<8><<<g, 256, 0, s>>>(A, B, r0, r1, partials); break;
+    case 2: k_gram<2><<<g, 64, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
+    case 4: k_gram<4><<<g, 128, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
+    case 6: k_gram<6><<<g, 192, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
+    case 8: k_gram<8><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
-  k_finish<<<nblk(nout, 256), 256, 0, s>>>(partials, nchunks, nout, out);
+  k_finish<<<nblk(nout, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
   return cudaGetLastError();
 }
 
@@ -291,10 +302,10 @@ cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockL
   const size_t smem = sizeof(float2) * (size_t)(A.n > 0 ? A.n : 1) * kp * kp;
   const unsigned g = nblk(r1 - r0, 256);
   switch (kp) {
-    case 2: k_update<2><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); break;
-    case 4: k_update<4><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); break;
-    case 6: k_update<6><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); break;
-    case 8: k_update<8><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    case 2: k_update<2><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+    case 4: k_update<4><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+    case 6: k_update<6><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+    case 8: k_update<8><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -305,10 +316,10 @@ cudaError_t combine_diag(float2* Y, const float2* X, const float2* alpha, const 
   if (r1 <= r0) return cudaSuccess;
   const unsigned g = nblk(r1 - r0, 256);
   switch (kp) {
-    case 2: k_combine_diag<2><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); break;
-    case 4: k_combine_diag<4><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); break;
-    case 6: k_combine_diag<6><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); break;
-    case 8: k_combine_diag<8><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); break;
+    case 2: k_combine_diag<2><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+    case 4: k_combine_diag<4><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+    case 6: k_combine_diag<6><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+    case 8: k_combine_diag<8><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -328,51 +339,51 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
   if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(nchunks);
   switch (kp) {
-    case 2: k_coldots<2><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); break;
-    case 4: k_coldots<4><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); break;
-    case 6: k_coldots<6><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); break;
-    case 8: k_coldots<8><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); break;
+    case 2: k_coldots<2><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
+    case 4: k_coldots<4><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
+    case 6: k_coldots<6><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
+    case 8: k_coldots<8><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
-  k_finish<<<nblk(nout, 256), 256, 0, s>>>(partials, nchunks, nout, out);
+  k_finish<<<nblk(nout, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t ritz_resid(const BlockList& Q, const BlockList& Wb, const float2* Y, const float2* theta, int kp,
                        int64_t n, double* out, float2* partials, int64_t partial_cap, double* Zout, int64_t ldz,
-                       int ncols, cudaStream_t s) {
+                       int ncols, float2* Tout, const float2* diag, float clamp, cudaStream_t s) {
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   if (nchunks * kp > partial_cap) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float2) * (size_t)Q.n * kp * kp;
   const unsigned g = static_cast<unsigned>(nchunks);
   switch (kp) {
-    case 2: k_ritz_resid<2><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols); break;
-    case 4: k_ritz_resid<4><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols); break;
-    case 6: k_ritz_resid<6><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols); break;
-    case 8: k_ritz_resid<8><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols); break;
+    case 2: k_ritz_resid<2><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
+    case 4: k_ritz_resid<4><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
+    case 6: k_ritz_resid<6><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
+    case 8: k_ritz_resid<8><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
-  k_finish<<<1, 32, 0, s>>>(partials, nchunks, kp, out);
+  k_finish<<<1, 32, 0, s>>>(partials, nchunks, kp, out); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t f64_to_df(const double* X, int64_t ldx, int ncols, float2* Y, int kp, int64_t r0, int64_t r1,
                       cudaStream_t s) {
   if (r1 <= r0) return cudaSuccess;
-  k_f64_to_df<<<nblk((r1 - r0) * kp, 256), 256, 0, s>>>(X, ldx, ncols, Y, kp, r0, r1);
+  k_f64_to_df<<<nblk((r1 - r0) * kp, 256), 256, 0, s>>>(X, ldx, ncols, Y, kp, r0, r1); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t df_to_f64(const float2* X, int kp, double* Y, int64_t ldy, int ncols, int64_t r0, int64_t r1,
                       cudaStream_t s) {
   if (r1 <= r0 || ncols <= 0) return cudaSuccess;
-  k_df_to_f64<<<nblk((r1 - r0) * ncols, 256), 256, 0, s>>>(X, kp, Y, ldy, ncols, r0, r1);
+  k_df_to_f64<<<nblk((r1 - r0) * ncols, 256), 256, 0, s>>>(X, kp, Y, ldy, ncols, r0, r1); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t fill_zero(float2* Y, int64_t count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_zero<<<nblk(count, 256), 256, 0, s>>>(Y, count);
+  k_zero<<<nblk(count, 256), 256, 0, s>>>(Y, count); count_launch();
   return cudaGetLastError();
 }
 

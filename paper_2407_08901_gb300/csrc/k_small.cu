@@ -437,7 +437,7 @@ __global__ void k_to_df(const double* __restrict__ x, float2* __restrict__ y, in
 cudaError_t chol_rinv(const double* G, int ldg, int kk, int kp, double shift_rel, double* R, float2* Rinv_df,
                       int* status, cudaStream_t s) {
   if (kk < 1 || kk > 16 || kp > 16) return cudaErrorInvalidValue;
-  k_chol_rinv<<<1, 32, 0, s>>>(G, ldg, kk, kp, shift_rel, R, Rinv_df, status);
+  k_chol_rinv<<<1, 32, 0, s>>>(G, ldg, kk, kp, shift_rel, R, Rinv_df, status); count_launch();
   return cudaGetLastError();
 }
 
@@ -457,13 +457,13 @@ cudaError_t syev_lowest(const double* S, int lds, int m, int nev, double* theta,
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_syev_lowest<<<1, 512, smem, s>>>(S, lds, m, nev, theta, V, ldv);
+  k_syev_lowest<<<1, 512, smem, s>>>(S, lds, m, nev, theta, V, ldv); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t to_df(const double* x, float2* y, int count, double scale, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_to_df<<<(count + 255) / 256, 256, 0, s>>>(x, y, count, scale);
+  k_to_df<<<(count + 255) / 256, 256, 0, s>>>(x, y, count, scale); count_launch();
   return cudaGetLastError();
 }
 

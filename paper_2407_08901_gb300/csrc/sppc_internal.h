@@ -5,19 +5,33 @@
 
 namespace sppc {
 
-constexpr int kMaxBlocks = 40;  // basis blocks a launch can address (p_max + 2)
+// Kernel launches issued by the library since load (every launch site counts).
+void count_launch();
+long long launch_count();
 
-// Level-blocked SELL-32 matrix on the device.  Slice s holds 32 rows (lanes);
-// its entries are stored column-major: entry t of lane l sits at
-// slice_ptr[s] + 32*t + l.  slice_rows[32*s + l] is the original row index of
-// lane l (-1 for a padding lane).  Padding entries have value 0.
+constexpr int kMaxBlocks = 40;  // basis blocks a launch can address (p_max + 2)
+constexpr int kSliceH = 16;     // rows per SELL slice (one warp, two lanes per row)
+
+// Level-blocked SELL-16 matrix on the device, tiled by column chunks.  The
+// columns are cut into `nchunks` ranges of `chunk_cols` columns; chunk q owns
+// slices [chunk_slice[q], chunk_slice[q+1]).  Slice s holds kSliceH rows and
+// the row's entries whose columns fall in the slice's chunk, stored
+// column-major: entry t of slice row l sits at slice_ptr[s] + kSliceH*t + l.
+// slice_rows[kSliceH*s + l] is the original row index (-1 = padding row).
+// Padding entries have value 0.  row_first/row_last give, per row, the first and
+// last chunk holding one of its entries (0 for an empty row, which chunk 0 lists).
 struct SellDev {
   int64_t nslices = 0;
   int64_t nrows = 0;
+  int nchunks = 1;
+  int64_t chunk_cols = 0;
+  const int64_t* chunk_slice = nullptr;  // host array, nchunks + 1
   const int64_t* slice_ptr = nullptr;
   const int32_t* slice_rows = nullptr;
   const int32_t* col = nullptr;
   const float2* val = nullptr;  // double-float values
+  const uint8_t* row_first = nullptr;
+  const uint8_t* row_last = nullptr;
 };
 
 // SpMM epilogue: Y[r][c] = alpha[c] * (A X)[r][c] + beta[c] * X[r][c] + gamma[c] * Z[r][c].
@@ -57,15 +71,25 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
                     double* out, float2* partials, int64_t partial_cap, cudaStream_t s);
 // Ritz residual: for every row, z = sum_a Q_a[r] Y_a, hz = sum_a W_a[r] Y_a (Y: (na*kp) x kp
 // double-float), accumulate (hz - theta*z)^2 per column -> out[j] (FP64); optionally
-// write z (FP64, leading dim ldz, first ncols columns) to Zout.
+// write z (FP64, leading dim ldz, first ncols columns) to Zout; optionally write
+// the residual hz - theta z (double-float, n x kp) to Tout, divided elementwise by
+// diag[r] - theta_j (magnitude clamped to >= clamp) when diag is given.
 cudaError_t ritz_resid(const BlockList& Q, const BlockList& Wb, const float2* Y, const float2* theta, int kp,
                        int64_t n, double* out, float2* partials, int64_t partial_cap, double* Zout, int64_t ldz,
-                       int ncols, cudaStream_t s);
+                       int ncols, float2* Tout, const float2* diag, float clamp, cudaStream_t s);
 cudaError_t f64_to_df(const double* X, int64_t ldx, int ncols, float2* Y, int kp, int64_t r0, int64_t r1,
                       cudaStream_t s);
 cudaError_t df_to_f64(const float2* X, int kp, double* Y, int64_t ldy, int ncols, int64_t r0, int64_t r1,
                       cudaStream_t s);
 cudaError_t fill_zero(float2* Y, int64_t count, cudaStream_t s);
+
+// ---- k_minres.cu
+// Persistent MINRES on (A - E_k) x = b for k columns on the complement of psi
+// (see k_minres.cu).  P holds b on entry; X receives the solution.
+cudaError_t minres_persistent(const SellDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
+                              float2* V, float2* VP, float2* Y, float2* W1, float2* W2, float2* X, double tol,
+                              int maxit, float2* partials, int64_t partial_cap, unsigned* bar, int* status,
+                              cudaStream_t s);
 
 // ---- k_small.cu (single-CTA FP64 kernels on small matrices)
 // Cholesky of the leading kk x kk part of G (ld = ldg) plus `shift` on the diagonal;

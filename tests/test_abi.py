@@ -11,7 +11,7 @@ from conftest import ROOT, make_matrix
 
 def _header_symbols():
     src = open(os.path.join(ROOT, "include", "sppc.h")).read()
-    return set(re.findall(r"^\s*(?:sppc_status|void|const char\*)\s+(sppc_\w+)\s*\(", src, re.M))
+    return set(re.findall(r"^\s*(?:sppc_status|void|const char\*|int64_t)\s+(sppc_\w+)\s*\(", src, re.M))
 
 
 def test_library_exports_every_declared_symbol():

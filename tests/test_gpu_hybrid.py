@@ -1,0 +1,61 @@
+"""CUDA SPPC + continuation (through the C ABI) against the oracle, step by step.
+GPU only.  Eigenvalues to 1e-10 relative at every step (FP64 path).  Scaled
+residuals are norms of differences of nearly equal vectors whose Ritz vectors
+agree only to ~1e-9 between the two sides, so they are compared to 1e-3
+relative plus 1e-11 (the double-float floor of ||Hz - theta z|| / |theta|)."""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import make_matrix
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("name,switch,pmax,precond", [("small", 3, 5, 1), ("small", 0, 4, 0), ("c1", 2, 6, 1)])
+def test_hybrid_matches_oracle(name, switch, pmax, precond):
+    import paper_2407_08901_gb300 as S
+    w, rp, c, v = make_matrix(name)
+    tol = 1e-9 if precond else 1e-7
+    opts = S.sppc_default_opts(p_max=pmax, hybrid=1, switch_order=switch, precond=precond, hybrid_maxit=300)
+    # the oracle restarts when a block would not fit in max_blocks = p_max + 1
+    h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, opts)
+    try:
+        conv, th, rs, st = S.sppc_solve(h, w.k, tol=tol)
+        ref_th, ref_rs, ref_conv, rec = oracle.sppc_hybrid(
+            rp, c, v, w.small_dim, w.k, switch_order=switch, tol=tol, max_blocks=pmax + 1,
+            precond="jacobi" if precond else "none", maxit=300)
+        assert conv and ref_conv
+        # near a tight tolerance the last steps may cross it one or two steps apart
+        steps_ref = len(rec) - (switch + 1)
+        assert st["switched_at"] == switch and abs(st["refine_steps"] - steps_ref) <= 2
+        common = min(len(rec), switch + 1 + st["refine_steps"])
+        if st["refine_steps"] == steps_ref:
+            assert st["spmv_h"] == rec[-1].spmv
+        for i, r in enumerate(rec[:common]):
+            info = S.sppc_order_info(h, i, w.k)
+            assert np.allclose(info["theta"], r.theta, rtol=1e-10, atol=0), (i, info["theta"] - r.theta)
+            assert np.allclose(info["resid"], r.resid, rtol=1e-3, atol=1e-11), (i, info["resid"], r.resid)
+        assert np.allclose(th, ref_th, rtol=1e-9, atol=0)
+        if pmax + 1 < len(rec):
+            assert st["restarts"] >= 1
+    finally:
+        S.sppc_destroy(h)
+
+
+def test_refine_step_entry_point():
+    import paper_2407_08901_gb300 as S
+    w, rp, c, v = make_matrix("small")
+    h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, S.sppc_default_opts(p_max=6))
+    try:
+        S.sppc_start(h, w.k)
+        S.sppc_correct(h)
+        S.sppc_rayleigh_ritz(h, w.k)
+        th1, rs1 = S.sppc_refine_step(h, w.k)
+        th2, rs2 = S.sppc_refine_step(h, w.k)
+        assert np.all(th2 <= th1 + 1e-12) and rs2.max() < rs1.max()
+        with pytest.raises(S.SppcError):
+            S.sppc_correct(h)  # SPPC orders cannot follow the continuation
+    finally:
+        S.sppc_destroy(h)

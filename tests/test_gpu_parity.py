@@ -62,7 +62,7 @@ def test_spmm_matches_oracle(name, ncols):
 
 def test_spmm_empty_and_ragged_rows():
     """A matrix with empty rows (no stored entry at all) and a level whose size is
-    not a multiple of the 32-row slice."""
+    not a multiple of the 16-row slice."""
     S = _lib()
     n = 203
     rng = np.random.Generator(np.random.PCG64(9))
@@ -96,38 +96,70 @@ def test_spmm_empty_and_ragged_rows():
         S.sppc_destroy(h)
 
 
-def _sell_reference(rp, c, n1_limit, seg, sigma=1024):
-    """The SELL-32 row order: inside each level, windows of 1024 rows sorted by
-    decreasing row length (stable), cut into slices of 32 rows."""
+def _sell_reference(rp, c, ncols, seg, chunk_cols=0, sigma=1024, sh=16):
+    """The SELL-16 layout: columns cut into chunks; per chunk and per level the
+    rows with entries in the chunk (plus, in chunk 0, rows with no entry at all)
+    are sorted by decreasing count inside windows of 1024 rows (stable) and cut
+    into slices of 16 rows."""
     nrows = seg[-1]
-    lens = np.array([np.count_nonzero(c[rp[r]:rp[r + 1]] < n1_limit) for r in range(nrows)])
-    order = np.arange(nrows)
-    slice_rows, slice_ptr = [], [0]
-    for a, b in zip(seg[:-1], seg[1:]):
-        for w0 in range(a, b, sigma):
-            w1 = min(w0 + sigma, b)
-            idx = np.arange(w0, w1)
-            order[w0:w1] = idx[np.argsort(-lens[idx], kind="stable")]
-        for s0 in range(a, b, 32):
-            rows = order[s0:min(s0 + 32, b)]
-            pad = np.full(32, -1)
-            pad[: len(rows)] = rows
-            slice_rows.append(pad)
-            slice_ptr.append(slice_ptr[-1] + 32 * int(lens[rows].max()))
-    return np.array(slice_ptr, dtype=np.int64), np.concatenate(slice_rows).astype(np.int32)
+    C = chunk_cols if 0 < chunk_cols < ncols else ncols
+    nch = -(-ncols // C)
+    lens = np.zeros((nrows, nch), dtype=np.int64)
+    for r in range(nrows):
+        cc = c[rp[r]:rp[r + 1]]
+        cc = cc[cc < ncols]
+        lens[r] = np.bincount(cc // C, minlength=nch)[:nch]
+    empty = lens.sum(axis=1) == 0
+    slice_rows, slice_ptr, chunk_slice = [], [0], []
+    for q in range(nch):
+        chunk_slice.append(len(slice_rows))
+        for a, b in zip(seg[:-1], seg[1:]):
+            part = np.array([r for r in range(a, b) if lens[r, q] > 0 or (q == 0 and empty[r])], dtype=np.int64)
+            for w0 in range(0, len(part), sigma):
+                idx = part[w0:w0 + sigma]
+                part[w0:w0 + sigma] = idx[np.argsort(-lens[idx, q], kind="stable")]
+            for s0 in range(0, len(part), sh):
+                rows = part[s0:s0 + sh]
+                pad = np.full(sh, -1)
+                pad[: len(rows)] = rows
+                slice_rows.append(pad)
+                slice_ptr.append(slice_ptr[-1] + sh * int(lens[rows, q].max()))
+    chunk_slice.append(len(slice_rows))
+    return (np.array(slice_ptr, dtype=np.int64), np.concatenate(slice_rows).astype(np.int32),
+            np.array(chunk_slice, dtype=np.int64))
 
 
-@pytest.mark.parametrize("name", ["small", "c1"])
-def test_layout_is_bit_exact(name):
-    S, w, rp, c, v, h = _create(name)
+@pytest.mark.parametrize("name,chunk", [("small", -1), ("small", 700), ("c1", -1), ("c1", 4096)])
+def test_layout_is_bit_exact(name, chunk):
+    S, w, rp, c, v, h = _create(name, spmm_chunk_cols=chunk)
     try:
         L = S.sppc_get_layout(h)
     finally:
         S.sppc_destroy(h)
-    sp, sr = _sell_reference(rp, c, 2**31, list(w.level_offsets))
+    sp, sr, cs = _sell_reference(rp, c, w.n, list(w.level_offsets), chunk)
+    assert L["n_chunks"] == len(cs) - 1
+    assert np.array_equal(L["chunk_slice"], cs)
     assert np.array_equal(L["slice_ptr"], sp) and np.array_equal(L["slice_rows"], sr)
-    sp11, sr11 = _sell_reference(rp, c, w.small_dim, [0, w.small_dim])
+    sp11, sr11, _ = _sell_reference(rp, c, w.small_dim, [0, w.small_dim])
     assert np.array_equal(L["h11_slice_ptr"], sp11) and np.array_equal(L["h11_slice_rows"], sr11)
+
+
+@pytest.mark.parametrize("chunk", [257, 1000, 5000])
+def test_chunked_spmm_matches_oracle(chunk):
+    """Column tiling: every chunk adds its partial row sums to Y; the row's first
+    chunk writes, its last one finishes."""
+    S, w, rp, c, v, h = _create("c1", spmm_chunk_cols=chunk)
+    try:
+        X = W.random_block(w.n, 8, 3)
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.full_like(Xd, float("nan"))
+        S.sppc_spmm(h, Xd, Yd)
+        Y = Yd.cpu().numpy()
+        ref = csr_spmm(rp, c, v, X)
+        mag = _abs_spmm(rp, c, v, X)
+        assert np.all(np.abs(Y - ref) <= 1e-12 * mag), np.max(np.abs(Y - ref) / mag)
+    finally:
+        S.sppc_destroy(h)
 
 
 def _compare_orders(S, h, ref, k, rtol_theta=1e-10):

@@ -1,0 +1,47 @@
+"""Pins for the SPPC + block continuation oracle (CPU only)."""
+import numpy as np
+
+import oracle
+import workloads as W
+from conftest import dense, make_matrix
+from test_oracle_sppc import TINY, _krylov_ritz
+
+
+def test_identity_preconditioner_continues_the_block_krylov_space():
+    """n1 = k makes SPPC's basis the block Krylov space of [I_k; 0]; extending it
+    by the Ritz residuals (no preconditioner) adds exactly the next Krylov block,
+    so the Ritz values stay those of block Lanczos."""
+    w, rp, c, v = make_matrix(TINY)
+    A = dense(rp, c, v)
+    k = 3
+    th, rs, conv, rec = oracle.sppc_hybrid(rp, c, v, k, k, switch_order=2, tol=1e-300, max_blocks=50, maxit=4,
+                                           precond="none")
+    S = np.zeros((w.n, k))
+    S[:k, :k] = np.eye(k)
+    kr = _krylov_ritz(A, S, 2 + 4, k)
+    dav = [r for r in rec if r.phase == "davidson"]
+    assert len(dav) == 4
+    for r in dav:
+        assert np.allclose(r.theta, kr[2 + r.step], rtol=1e-10, atol=0), r.step
+
+
+def test_hybrid_converges_to_dense_eigenvalues_within_kato_temple(small_matrix):
+    w, rp, c, v = small_matrix
+    lam = np.linalg.eigvalsh(dense(rp, c, v))[: w.k + 1]
+    th, rs, conv, rec = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, switch_order=4, tol=1e-8, max_blocks=8)
+    assert conv and np.all(rs <= 1e-8)
+    gap = np.abs(np.diff(lam)).min()
+    bound = (rs * np.abs(th)) ** 2 / gap
+    assert np.all(np.abs(th - lam[: w.k]) <= 10 * bound + 1e-12)
+    assert np.all(th >= lam[: w.k] - 1e-12)
+    # the records are monotone: SPPC orders, then Davidson steps, SpMV count grows by k
+    sp = [r.spmv for r in rec]
+    assert all(b - a == w.k for a, b in zip(sp, sp[1:]))
+
+
+def test_thick_restart_keeps_converging():
+    w, rp, c, v = make_matrix(TINY)
+    lam = np.linalg.eigvalsh(dense(rp, c, v))[: w.k]
+    th, rs, conv, rec = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, switch_order=2, tol=1e-9, max_blocks=4)
+    assert conv and max(r.m for r in rec) <= 4 * w.k
+    assert np.allclose(th, lam, rtol=1e-12)
