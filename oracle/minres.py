@@ -1,7 +1,7 @@
 """MINRES for symmetric (possibly indefinite) systems, oracle version.
 
 The paper solves the small shifted systems (H0_hat - E_k^(0)) x1 = b1 of
-Eq. (sm_lin_proj) "iteratively using, for example, the MINRES algorithm"
+Eq. (sm_lin_proj) with an iterative method and names MINRES as one choice
 (Sec. 4.3).  This is MINRES as published by Paige and Saunders (1975): the
 Lanczos three-term recurrence builds an orthonormal Krylov basis V_j with
 A V_j = V_{j+1} T_j; the least-squares problem min ||beta1 e1 - T_j y|| is
