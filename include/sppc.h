@@ -127,6 +127,23 @@ sppc_status sppc_create(const sppc_csr* H, const int64_t* level_offsets, int32_t
 sppc_status sppc_spmm(sppc_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t ncols,
                       void* stream);
 
+/* Y = H X like sppc_spmm, but the call allocates no device memory: for callers
+ * that cannot allocate while they multiply (a framework that owns all device
+ * memory through its own allocator and budget, a service that forbids growth
+ * after start-up, a loop that must not pay the synchronisation cudaMalloc or
+ * cudaFree may imply).  The paper has no counterpart; this is a property of the
+ * library.  Scratch (double-float copies of X and of the result) lives in a fixed
+ * 32 MiB device array that every GPU loading the library holds until exit; a call
+ * needs 2*n*kp*8 bytes of it (kp = ncols rounded up to even), so n*kp must be
+ * <= 2,097,152, else SPPC_ERR_ARG (nothing is launched).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU race on it.  X, Y: caller-owned DEVICE buffers as in
+ * sppc_spmm. */
+sppc_status sppc_spmm_noalloc(sppc_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t ncols,
+                              void* stream);
+
 /* Same product with HOST buffers: copies X to the device, multiplies, copies Y back
  * (synchronises the stream). */
 sppc_status sppc_spmm_host(sppc_handle h, const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t ncols,

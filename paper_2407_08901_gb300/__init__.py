@@ -16,7 +16,7 @@ import numpy as np
 from .build import LIB
 
 __all__ = [
-    "SppcError", "sppc_default_opts", "sppc_create", "sppc_spmm", "sppc_spmm_host", "sppc_start", "sppc_correct",
+    "SppcError", "sppc_default_opts", "sppc_create", "sppc_spmm", "sppc_spmm_noalloc", "sppc_spmm_host", "sppc_start", "sppc_correct",
     "sppc_rayleigh_ritz", "sppc_refine_step", "sppc_solve", "sppc_order_info", "sppc_get_stats", "sppc_get_state", "sppc_get_layout",
     "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "EXPORTED_SYMBOLS", "STATUS",
 ]
@@ -68,6 +68,7 @@ _SIGS = {
                            ctypes.POINTER(_VP)]),
     "sppc_spmm": (_I32, [_VP, _VP, _I64, _VP, _I64, _I32, _VP]),
     "sppc_spmm_host": (_I32, [_VP, _VP, _I64, _VP, _I64, _I32, _VP]),
+    "sppc_spmm_noalloc": (_I32, [_VP, _VP, _I64, _VP, _I64, _I32, _VP]),
     "sppc_start": (_I32, [_VP, _VP, _VP, _VP]),
     "sppc_correct": (_I32, [_VP, _VP]),
     "sppc_rayleigh_ritz": (_I32, [_VP, _VP, _VP, _VP]),
@@ -160,6 +161,13 @@ def sppc_spmm(h, X, Y, stream=None) -> None:
     """Y = H X for torch CUDA float64 tensors X, Y of shape (n, ncols), ncols <= 8."""
     assert X.dtype == Y.dtype and X.is_cuda and Y.is_cuda and X.stride(1) == 1 and Y.stride(1) == 1
     _check(h, _lib.sppc_spmm(h, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), X.shape[1], _stream(stream)))
+
+
+def sppc_spmm_noalloc(h, X, Y, stream=None) -> None:
+    """Y = H X like sppc_spmm, without allocating device memory in the call (the
+    scratch lives in a fixed 32 MiB device array; n * kp <= 2,097,152)."""
+    assert X.dtype == Y.dtype and X.is_cuda and Y.is_cuda and X.stride(1) == 1 and Y.stride(1) == 1
+    _check(h, _lib.sppc_spmm_noalloc(h, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), X.shape[1], _stream(stream)))
 
 
 def sppc_spmm_host(h, X: np.ndarray, Y: np.ndarray, stream=None) -> None:

@@ -873,6 +873,15 @@ bool all_converged(const sppc_ctx* h, double tol) {
 
 }  // namespace
 
+// Accessors used by the allocation-free SpMM entry point (noalloc.cu).
+namespace sppc {
+const SellDev* handle_matrix(sppc_handle h, int64_t* n) {
+  if (n) *n = h->n;
+  return &h->H;
+}
+sppc_status handle_fail(sppc_handle h, sppc_status st, const char* msg) { return fail(h, st, "%s", msg); }
+}  // namespace sppc
+
 // =================================================================== C ABI
 extern "C" {
 
