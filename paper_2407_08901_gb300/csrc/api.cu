@@ -898,7 +898,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->check_symmetry = 0;
   o->seed = 0;
   o->timing = 0;
-  o->spmm_chunk_cols = -1;
+  o->spmm_chunk_cols = 0;
   o->hybrid = 0;
   o->switch_order = 15;
   o->hybrid_maxit = 1000;

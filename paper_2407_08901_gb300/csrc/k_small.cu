@@ -1,13 +1,12 @@
-// Small dense FP64 kernels, one CTA each: the k x k Cholesky factor and its
-// inverse for CholeskyQR (Eq. QR), and the symmetric eigensolve of the projected
+// Small dense kernels, one CTA each: the k x k Cholesky factor and its inverse
+// for CholeskyQR (Eq. QR, FP64), and the symmetric eigensolve of the projected
 // matrix Q^T H Q (Eqs. tilde_H, proj; at most k(p_max+1) <= 144 rows).
 //
-// The eigensolve reduces the matrix to tridiagonal form with Householder
-// reflections (Golub and Van Loan, Alg. 8.3.1), finds the nev lowest eigenvalues
-// by Sturm-count multisection, their vectors by inverse iteration on the
-// tridiagonal matrix (Wilkinson), cleans the nev vectors with a Rayleigh-Ritz
-// step on their span (Jacobi on the nev x nev matrix), and back-transforms
-// through the stored reflectors.
+// FP64 runs at ~1/70 of FP32 on this GPU, so the eigensolve does its O(m^3)
+// parts (Householder tridiagonalisation, back-transformation) in double-float
+// and brackets the eigenvalues in FP32 first; FP64 is kept for the O(m) per
+// vector tridiagonal work (inverse iteration, Rayleigh quotients) and for
+// crowded eigenvalues.
 #include <math.h>
 
 #include "df.cuh"
@@ -78,10 +77,11 @@ __global__ void k_chol_rinv(const double* __restrict__ G, int ldg, int kk, int k
   if (t == 0) status[0] = bad;
 }
 
-// Sturm count: number of eigenvalues of the tridiagonal (d, e) below x.
-__device__ int sturm_count(const double* d, const double* e2, int m, double x, double pivmin) {
+// Sturm count: number of eigenvalues of the tridiagonal (d, e^2) below x.
+template <typename T>
+__device__ int sturm_count(const T* d, const T* e2, int m, T x, T pivmin) {
   int cnt = 0;
-  double q = d[0] - x;
+  T q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0) ++cnt;
   for (int i = 1; i < m; ++i) {
@@ -92,337 +92,345 @@ __device__ int sturm_count(const double* d, const double* e2, int m, double x, d
   return cnt;
 }
 
+// Multisection for eigenvalue index w with one warp: 32 Sturm counts per round
+// shrink [lo, hi] by a factor of 33.  Stops when hi - lo <= rel * max(|lo|,|hi|) + abs.
+template <typename T>
+__device__ void multisect(const T* d, const T* e2, int m, int w, T pivmin, T rel, T abs_tol, int max_rounds,
+                          double& lo_io, double& hi_io) {
+  const int lane = threadIdx.x & 31;
+  T lo = static_cast<T>(lo_io), hi = static_cast<T>(hi_io);
+  for (int it = 0; it < max_rounds; ++it) {
+    if (hi - lo <= rel * fmax(fabs(lo), fabs(hi)) + abs_tol) break;
+    const T x = lo + (hi - lo) * static_cast<T>(lane + 1) / static_cast<T>(33);
+    const int c = sturm_count<T>(d, e2, m, x, pivmin);
+    const unsigned ball = __ballot_sync(0xffffffffu, c > w);
+    T nlo = lo, nhi = hi;
+    if (ball) {
+      const int f = __ffs(ball) - 1;
+      nhi = lo + (hi - lo) * static_cast<T>(f + 1) / static_cast<T>(33);
+      if (f > 0) nlo = lo + (hi - lo) * static_cast<T>(f) / static_cast<T>(33);
+    } else {
+      nlo = lo + (hi - lo) * static_cast<T>(32) / static_cast<T>(33);
+    }
+    lo = __shfl_sync(0xffffffffu, nlo, 0);
+    hi = __shfl_sync(0xffffffffu, nhi, 0);
+  }
+  lo_io = static_cast<double>(lo);
+  hi_io = static_cast<double>(hi);
+}
+
+// sqrt of a double-float: fp32 root s, exact square s*s (TwoProd), one
+// correction step (a - s^2) / (2 s).
+__device__ __forceinline__ float2 df_sqrt(float2 a) {
+  if (!(a.x > 0.f)) return make_float2(0.f, 0.f);
+  const float s = __fsqrt_rn(a.x);
+  const float p = __fmul_rn(s, s);
+  const float2 sp = make_float2(p, __fmaf_rn(s, s, -p));
+  const float2 r = df_sub(a, sp);
+  return fast_two_sum(s, __fdiv_rn(r.x, __fmul_rn(2.f, s)));
+}
+
+// Block-wide double-float sum (all threads get the result).
+__device__ float2 block_sum_df(float2 v, float2* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum_df(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float2 t = red[0];
+    for (int w2 = 1; w2 < nw; ++w2) t = df_add(t, red[w2]);
+    red[32] = t;
+  }
+  __syncthreads();
+  const float2 r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// Solve (T - sigma I) y = y in place for the tridiagonal (d, e), FP64, with
+// partial pivoting; returns false on an exactly zero pivot set to eps.
+__device__ void tri_shift_solve(const double* d, const double* e, int m, double sigma, double eps_piv, double* y,
+                                double* du, double* u1, double* u2, double* lm, unsigned char* piv) {
+  double a0 = d[0] - sigma, b0 = (m > 1) ? e[0] : 0.0;
+  for (int i = 0; i + 1 < m; ++i) {
+    const double c = e[i];
+    const double a1 = d[i + 1] - sigma;
+    const double b1 = (i + 2 < m) ? e[i + 1] : 0.0;
+    if (fabs(c) > fabs(a0)) {
+      piv[i] = 1;
+      du[i] = c;
+      u1[i] = a1;
+      u2[i] = b1;
+      const double l = a0 / c;
+      lm[i] = l;
+      a0 = b0 - l * a1;
+      b0 = -l * b1;
+    } else {
+      piv[i] = 0;
+      if (a0 == 0.0) a0 = eps_piv;
+      du[i] = a0;
+      u1[i] = b0;
+      u2[i] = 0.0;
+      const double l = c / a0;
+      lm[i] = l;
+      a0 = a1 - l * b0;
+      b0 = b1;
+    }
+  }
+  du[m - 1] = (a0 == 0.0) ? eps_piv : a0;
+  for (int i = 0; i + 1 < m; ++i) {
+    if (piv[i]) {
+      const double tmp = y[i];
+      y[i] = y[i + 1];
+      y[i + 1] = tmp - lm[i] * y[i];
+    } else {
+      y[i + 1] -= lm[i] * y[i];
+    }
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double sv = y[i];
+    if (i + 1 < m) sv -= u1[i] * y[i + 1];
+    if (i + 2 < m) sv -= u2[i] * y[i + 2];
+    double di = du[i];
+    if (fabs(di) < eps_piv) di = (di < 0 ? -eps_piv : eps_piv);
+    y[i] = sv / di;
+  }
+}
+
+__device__ double rayleigh_tri(const double* d, const double* e, int m, const double* y) {
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double ty = d[i] * y[i];
+    if (i > 0) ty += e[i - 1] * y[i - 1];
+    if (i + 1 < m) ty += e[i] * y[i + 1];
+    num += y[i] * ty;
+    den += y[i] * y[i];
+  }
+  return num / den;
+}
+
+// Symmetric eigensolve of the projected matrix, nev lowest pairs.
+//  1. Householder tridiagonalisation (Golub and Van Loan, Alg. 8.3.1) in
+//     double-float, matrix in shared memory with leading dimension m+1.
+//  2. Eigenvalue brackets by Sturm-count multisection in FP32 to ~1e-5; indices
+//     whose brackets crowd a neighbour are narrowed further in FP64.
+//  3. Eigenvectors of the tridiagonal matrix by inverse iteration in FP64 (one
+//     thread per vector), shift updated by the Rayleigh quotient for isolated
+//     eigenvalues; crowded groups are orthogonalised (modified Gram-Schmidt).
+//     The eigenvalue is the final Rayleigh quotient.
+//  4. Back-transformation through the stored reflectors in double-float.
 __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ S, int lds, int m, int nev,
                                                      double* __restrict__ theta, double* __restrict__ V, int ldv) {
-  extern __shared__ double sm[];
-  double* A = sm;                    // m x m (row stride m), reflectors stored below the diagonal
-  double* tau = A + m * m;           // m
-  double* d = tau + m;               // m
-  double* e = d + m;                 // m
-  double* e2 = e + m;                // m
-  double* vec = e2 + m;              // m  (Householder vector work)
-  double* p = vec + m;               // m
-  double* Y = p + m;                 // m x nev (column c at Y[c*m])
-  double* ev = Y + m * kMaxNev;      // nev
-  double* red = ev + kMaxNev;        // 32 reduction slots
-  double* G = red + 32;              // nev x nev (Rayleigh-Ritz)
-  double* Gv = G + kMaxNev * kMaxNev;  // nev x nev eigenvectors
-  double* J = Gv + kMaxNev * kMaxNev;  // nev x nev Jacobi work
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ld = m + 1;
+  float2* A = reinterpret_cast<float2*>(smraw);  // m x ld, reflectors below the diagonal
+  float2* vec = A + m * ld;                        // m
+  float2* pw = vec + m;                            // m
+  float2* tau = pw + m;                            // m
+  float2* red = tau + m;                           // 33
+  float2* Yd = red + 40;                           // nev x m (double-float eigenvectors)
+  double* d = reinterpret_cast<double*>(Yd + kMaxNev * m);  // m
+  double* e = d + m;                                         // m
+  double* e2 = e + m;                                        // m
+  double* Y = e2 + m;                                        // nev x m (FP64 eigenvectors of T)
+  double* lo = Y + kMaxNev * m;                              // nev
+  double* hi = lo + kMaxNev;                                 // nev
+  double* ev = hi + kMaxNev;                                 // nev
+  float* d32 = reinterpret_cast<float*>(ev + kMaxNev);       // m
+  float* e232 = d32 + m;                                     // m
+  int* crowd = reinterpret_cast<int*>(e232 + m);             // nev
   const int t = threadIdx.x, nt = blockDim.x;
   const int lane = t & 31, warp = t >> 5, nwarp = nt >> 5;
   for (int x = t; x < m * m; x += nt) {
     const int i = x / m, j = x % m;
-    A[x] = 0.5 * (S[i * lds + j] + S[j * lds + i]);
+    A[i * ld + j] = df_from_double(0.5 * (S[i * lds + j] + S[j * lds + i]));
   }
   __syncthreads();
-  // ---- Householder tridiagonalisation
+  // ---- 1. Householder tridiagonalisation (double-float)
   for (int j = 0; j + 2 < m; ++j) {
     const int len = m - j - 1;
-    // norm of x = A[j+1:, j]
-    double part = 0.0;
+    float sh = 0.f, sl = 0.f;
     for (int i = t; i < len; i += nt) {
-      const double xv = A[(j + 1 + i) * m + j];
-      part += xv * xv;
+      const float2 xv = A[(j + 1 + i) * ld + j];
+      acc_mac(sh, sl, xv, xv);
     }
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane == 0) red[warp] = part;
-    __syncthreads();
+    const float2 s2 = block_sum_df(acc_get(sh, sl), red);
     if (t == 0) {
-      double s = 0.0;
-      for (int w = 0; w < nwarp; ++w) s += red[w];
-      const double x0 = A[(j + 1) * m + j];
-      const double nrm = sqrt(s);
-      if (nrm == 0.0) {
-        tau[j] = 0.0;
+      const float2 x0 = A[(j + 1) * ld + j];
+      const float2 nrm = df_sqrt(s2);
+      if (nrm.x == 0.f) {
+        tau[j] = make_float2(0.f, 0.f);
         e[j] = 0.0;
-        red[31] = 0.0;
+        red[34] = make_float2(0.f, 0.f);
       } else {
-        const double alpha = (x0 >= 0.0) ? -nrm : nrm;
-        const double v0 = x0 - alpha;
-        // v = x - alpha e1, tau = 2 / (v^T v) with v^T v = s - x0^2 + v0^2
-        const double vtv = s - x0 * x0 + v0 * v0;
-        tau[j] = 2.0 / vtv;
-        e[j] = alpha;
-        red[31] = v0;
+        const float2 alpha = (x0.x >= 0.f) ? df_neg(nrm) : nrm;
+        const float2 v0 = df_sub(x0, alpha);
+        const float2 vtv = df_add(df_sub(s2, df_mul(x0, x0)), df_mul(v0, v0));
+        tau[j] = df_div(make_float2(2.f, 0.f), vtv);
+        e[j] = df_to_double(alpha);
+        red[34] = v0;
       }
     }
     __syncthreads();
-    const double tj = tau[j];
-    for (int i = t; i < len; i += nt) vec[i] = (i == 0) ? red[31] : A[(j + 1 + i) * m + j];
+    const float2 tj = tau[j];
+    for (int i = t; i < len; i += nt) vec[i] = (i == 0) ? red[34] : A[(j + 1 + i) * ld + j];
     __syncthreads();
-    if (tj != 0.0) {
-      // p = tau * A22 v
+    if (tj.x != 0.f) {
       for (int i = t; i < len; i += nt) {
-        const double* row = A + (j + 1 + i) * m + (j + 1);
-        double s = 0.0;
-        for (int l = 0; l < len; ++l) s += row[l] * vec[l];
-        p[i] = tj * s;
+        const float2* row = A + (j + 1 + i) * ld + (j + 1);
+        float ph = 0.f, pl = 0.f;
+        for (int l = 0; l < len; ++l) {
+          acc_mac(ph, pl, row[l], vec[l]);
+          if ((l & 15) == 15) acc_norm(ph, pl);
+        }
+        pw[i] = df_mul(tj, acc_get(ph, pl));
       }
       __syncthreads();
-      double pv = 0.0;
-      for (int i = t; i < len; i += nt) pv += p[i] * vec[i];
-      for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
-      if (lane == 0) red[warp] = pv;
-      __syncthreads();
-      if (t == 0) {
-        double s = 0.0;
-        for (int w = 0; w < nwarp; ++w) s += red[w];
-        red[30] = 0.5 * tj * s;
-      }
-      __syncthreads();
-      const double K = red[30];
-      for (int i = t; i < len; i += nt) p[i] = p[i] - K * vec[i];  // w
+      float kh = 0.f, kl = 0.f;
+      for (int i = t; i < len; i += nt) acc_mac(kh, kl, pw[i], vec[i]);
+      const float2 pv = block_sum_df(acc_get(kh, kl), red);
+      const float2 K = df_mul(df_mul(make_float2(0.5f, 0.f), tj), pv);
+      for (int i = t; i < len; i += nt) pw[i] = df_sub(pw[i], df_mul(K, vec[i]));  // w
       __syncthreads();
       for (int x = t; x < len * len; x += nt) {
         const int i = x / len, l = x % len;
-        A[(j + 1 + i) * m + (j + 1 + l)] -= vec[i] * p[l] + p[i] * vec[l];
+        float2& a = A[(j + 1 + i) * ld + (j + 1 + l)];
+        a = df_sub(a, df_add(df_mul(vec[i], pw[l]), df_mul(pw[i], vec[l])));
       }
     }
     __syncthreads();
-    for (int i = t; i < len; i += nt) A[(j + 1 + i) * m + j] = vec[i];  // keep v for the back-transform
-    if (t == 0) d[j] = A[j * m + j];
+    for (int i = t; i < len; i += nt) A[(j + 1 + i) * ld + j] = vec[i];
+    if (t == 0) d[j] = df_to_double(A[j * ld + j]);
     __syncthreads();
   }
   if (t == 0) {
     if (m >= 2) {
-      d[m - 2] = A[(m - 2) * m + (m - 2)];
-      d[m - 1] = A[(m - 1) * m + (m - 1)];
-      e[m - 2] = A[(m - 1) * m + (m - 2)];
-      tau[m - 2] = 0.0;
+      d[m - 2] = df_to_double(A[(m - 2) * ld + (m - 2)]);
+      d[m - 1] = df_to_double(A[(m - 1) * ld + (m - 1)]);
+      e[m - 2] = df_to_double(A[(m - 1) * ld + (m - 2)]);
+      tau[m - 2] = make_float2(0.f, 0.f);
     } else {
-      d[0] = A[0];
+      d[0] = df_to_double(A[0]);
     }
-    for (int i = 0; i + 1 < m; ++i) e2[i] = e[i] * e[i];
+    if (m >= 1) tau[m - 1] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  // ---- Gershgorin bounds and multisection for eigenvalues 0..nev-1
-  __shared__ double gl, gu, pivmin;
+  for (int i = t; i < m; i += nt) {
+    e2[i] = (i + 1 < m) ? e[i] * e[i] : 0.0;
+    d32[i] = static_cast<float>(d[i]);
+    e232[i] = static_cast<float>(e2[i]);
+  }
+  __shared__ double gl, gu, tnorm;
   if (t == 0) {
-    double lo = 1e300, hi = -1e300, mx = 0.0;
+    double l0 = 1e300, h0 = -1e300, mx = 0.0;
     for (int i = 0; i < m; ++i) {
       const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
-      lo = fmin(lo, d[i] - r);
-      hi = fmax(hi, d[i] + r);
+      l0 = fmin(l0, d[i] - r);
+      h0 = fmax(h0, d[i] + r);
       mx = fmax(mx, fabs(d[i]) + r);
     }
-    const double pad = 2.2e-16 * mx * m + 1e-300;
-    gl = lo - pad;
-    gu = hi + pad;
-    pivmin = fmax(1e-290, 2.2e-16 * 2.2e-16 * fmax(mx * mx, 1e-300));
+    tnorm = fmax(mx, 1e-300);
+    const double pad = 1e-6 * tnorm + 1e-300;
+    gl = l0 - pad;
+    gu = h0 + pad;
+  }
+  __syncthreads();
+  // ---- 2. brackets: FP32 multisection, then FP64 for crowded indices
+  for (int w = warp; w < nev; w += nwarp) {
+    double l0 = gl, h0 = gu;
+    multisect<float>(d32, e232, m, w, 1e-30f, 2e-6f, static_cast<float>(1e-7 * tnorm), 12, l0, h0);
+    if (lane == 0) {
+      lo[w] = l0;
+      hi[w] = h0;
+    }
+  }
+  __syncthreads();
+  if (t < nev) {
+    // crowded: the bracket is not clearly separated from a neighbouring index's
+    const double sep = 1e-4 * tnorm;
+    int c = 0;
+    if (t > 0 && lo[t] - hi[t - 1] < sep) c = 1;
+    if (t + 1 < nev && lo[t + 1] - hi[t] < sep) c = 1;
+    if (hi[t] - lo[t] > 1e-4 * tnorm) c = 1;
+    crowd[t] = c;
   }
   __syncthreads();
   for (int w = warp; w < nev; w += nwarp) {
-    double lo = gl, hi = gu;
-    for (int it = 0; it < 40; ++it) {
-      if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi)) * 2.0 + pivmin) break;
-      const double x = lo + (hi - lo) * (lane + 1) / 33.0;
-      const int c = sturm_count(d, e2, m, x, pivmin);
-      // first point whose count exceeds w bounds the eigenvalue from above
-      const unsigned ball = __ballot_sync(0xffffffffu, c > w);
-      double nlo = lo, nhi = hi;
-      if (ball) {
-        const int f = __ffs(ball) - 1;
-        nhi = lo + (hi - lo) * (f + 1) / 33.0;
-        if (f > 0) nlo = lo + (hi - lo) * f / 33.0;
-      } else {
-        nlo = lo + (hi - lo) * 32 / 33.0;
-      }
-      lo = __shfl_sync(0xffffffffu, nlo, 0);
-      hi = __shfl_sync(0xffffffffu, nhi, 0);
+    if (!crowd[w]) continue;
+    double l0 = gl, h0 = gu;
+    multisect<double>(d, e2, m, w, 1e-280, 2.2e-16, 1e-300, 40, l0, h0);
+    if (lane == 0) {
+      lo[w] = l0;
+      hi[w] = h0;
     }
-    if (lane == 0) ev[w] = 0.5 * (lo + hi);
   }
   __syncthreads();
-  // ---- inverse iteration on T - ev I (thread c handles vector c), vectors in Y
+  // ---- 3. inverse iteration on T (FP64), thread c for vector c
   if (t < nev) {
     double* y = Y + t * m;
-    const double lam = ev[t];
     double du[kMaxM], u1[kMaxM], u2[kMaxM], lm[kMaxM];
     unsigned char piv[kMaxM];
-    double tnorm = 0.0;
-    for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0));
-    const double eps_piv = 2.2e-16 * fmax(tnorm, 1e-300);
-    // factor (T - lam I) = P L U, U with diagonals du, u1, u2
-    double a0 = d[0] - lam, b0 = (m > 1) ? e[0] : 0.0;
-    for (int i = 0; i + 1 < m; ++i) {
-      const double c = e[i];                          // subdiagonal element of row i+1
-      const double a1 = d[i + 1] - lam;
-      const double b1 = (i + 2 < m) ? e[i + 1] : 0.0;
-      if (fabs(c) > fabs(a0)) {
-        piv[i] = 1;
-        du[i] = c;
-        u1[i] = a1;
-        u2[i] = b1;
-        const double l = a0 / c;
-        lm[i] = l;
-        a0 = b0 - l * a1;
-        b0 = -l * b1;
-      } else {
-        piv[i] = 0;
-        if (a0 == 0.0) a0 = eps_piv;
-        du[i] = a0;
-        u1[i] = b0;
-        u2[i] = 0.0;
-        const double l = c / a0;
-        lm[i] = l;
-        a0 = a1 - l * b0;
-        b0 = b1;
-      }
-    }
-    du[m - 1] = (a0 == 0.0) ? eps_piv : a0;
-    // start vector: a fixed non-symmetric pattern, then 3 iterations
+    const double eps_piv = 2.2e-16 * tnorm;
+    double sigma = 0.5 * (lo[t] + hi[t]);
     for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.1 * (double)((i * 7 + t * 3) % 11);
-    for (int iter = 0; iter < 3; ++iter) {
-      // forward: apply P and L
-      for (int i = 0; i + 1 < m; ++i) {
-        if (piv[i]) {
-          const double tmp = y[i];
-          y[i] = y[i + 1];
-          y[i + 1] = tmp - lm[i] * y[i];
-        } else {
-          y[i + 1] -= lm[i] * y[i];
-        }
-      }
-      // backward: U
-      for (int i = m - 1; i >= 0; --i) {
-        double s = y[i];
-        if (i + 1 < m) s -= u1[i] * y[i + 1];
-        if (i + 2 < m) s -= u2[i] * y[i + 2];
-        double di = du[i];
-        if (fabs(di) < eps_piv) di = (di < 0 ? -eps_piv : eps_piv);
-        y[i] = s / di;
-      }
+    for (int it = 0; it < 4; ++it) {
+      tri_shift_solve(d, e, m, sigma, eps_piv, y, du, u1, u2, lm, piv);
       double nrm = 0.0;
       for (int i = 0; i < m; ++i) nrm = fmax(nrm, fabs(y[i]));
       for (int i = 0; i < m; ++i) y[i] /= nrm;
-    }
-  }
-  __syncthreads();
-  // ---- modified Gram-Schmidt over the nev vectors (parallel over rows)
-  for (int c = 0; c < nev; ++c) {
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int b = 0; b <= c; ++b) {
-        double part = 0.0;
-        for (int i = t; i < m; i += nt) part += Y[b * m + i] * Y[c * m + i];
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) red[warp] = part;
-        __syncthreads();
-        double s = 0.0;
-        for (int w = 0; w < nwarp; ++w) s += red[w];
-        __syncthreads();
-        if (b < c) {
-          for (int i = t; i < m; i += nt) Y[c * m + i] -= s * Y[b * m + i];
-        } else {
-          const double inv = 1.0 / sqrt(s);
-          for (int i = t; i < m; i += nt) Y[c * m + i] *= inv;
-        }
-        __syncthreads();
+      if (!crowd[t] && it >= 1) {
+        const double rq = rayleigh_tri(d, e, m, y);
+        if (rq >= lo[t] - 1e-6 * tnorm && rq <= hi[t] + 1e-6 * tnorm) sigma = rq;
       }
     }
   }
-  // ---- Rayleigh-Ritz on span(Y): G = Y^T T Y (T tridiagonal), Jacobi, rotate
-  for (int x = t; x < nev * nev; x += nt) {
-    const int a = x / nev, b = x % nev;
-    double s = 0.0;
-    for (int i = 0; i < m; ++i) {
-      double ty = d[i] * Y[b * m + i];
-      if (i > 0) ty += e[i - 1] * Y[b * m + i - 1];
-      if (i + 1 < m) ty += e[i] * Y[b * m + i + 1];
-      s += Y[a * m + i] * ty;
-    }
-    G[a * kMaxNev + b] = s;
-  }
   __syncthreads();
+  // crowded groups: modified Gram-Schmidt in index order (thread 0, rare)
   if (t == 0) {
-    for (int a = 0; a < nev; ++a)
-      for (int b = 0; b < nev; ++b) {
-        const double sym = 0.5 * (G[a * kMaxNev + b] + G[b * kMaxNev + a]);
-        J[a * kMaxNev + b] = sym;
-        Gv[a * kMaxNev + b] = (a == b) ? 1.0 : 0.0;
-      }
-    // cyclic Jacobi on the nev x nev matrix in p
-    for (int sweep = 0; sweep < 30; ++sweep) {
-      double off = 0.0, tot = 0.0;
-      for (int a = 0; a < nev; ++a)
-        for (int b = 0; b < nev; ++b) {
-          const double v = J[a * kMaxNev + b] * J[a * kMaxNev + b];
-          tot += v;
-          if (a != b) off += v;
-        }
-      if (off <= 1e-34 * tot || off == 0.0) break;
-      for (int a = 0; a < nev - 1; ++a)
-        for (int b = a + 1; b < nev; ++b) {
-          const double apq = J[a * kMaxNev + b];
-          if (apq == 0.0) continue;
-          const double app = J[a * kMaxNev + a], aqq = J[b * kMaxNev + b];
-          const double th = 0.5 * (aqq - app) / apq;
-          const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-          const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
-          for (int r = 0; r < nev; ++r) {
-            const double xa = J[r * kMaxNev + a], xb = J[r * kMaxNev + b];
-            J[r * kMaxNev + a] = c * xa - s * xb;
-            J[r * kMaxNev + b] = s * xa + c * xb;
-          }
-          for (int r = 0; r < nev; ++r) {
-            const double xa = J[a * kMaxNev + r], xb = J[b * kMaxNev + r];
-            J[a * kMaxNev + r] = c * xa - s * xb;
-            J[b * kMaxNev + r] = s * xa + c * xb;
-          }
-          for (int r = 0; r < nev; ++r) {
-            const double xa = Gv[r * kMaxNev + a], xb = Gv[r * kMaxNev + b];
-            Gv[r * kMaxNev + a] = c * xa - s * xb;
-            Gv[r * kMaxNev + b] = s * xa + c * xb;
-          }
-        }
-    }
-    // sort ascending (selection sort on the diagonal, permuting Gv columns)
-    for (int a = 0; a < nev; ++a) ev[a] = J[a * kMaxNev + a];
-    for (int a = 0; a < nev; ++a) {
-      int best = a;
-      for (int b = a + 1; b < nev; ++b)
-        if (ev[b] < ev[best]) best = b;
-      if (best != a) {
-        const double tv = ev[a];
-        ev[a] = ev[best];
-        ev[best] = tv;
-        for (int r = 0; r < nev; ++r) {
-          const double tg = Gv[r * kMaxNev + a];
-          Gv[r * kMaxNev + a] = Gv[r * kMaxNev + best];
-          Gv[r * kMaxNev + best] = tg;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  // rotate Y by Gv into the back-transform buffer (vec..p area reused: use G region)
-  // Yr[c][i] = sum_b Y[b][i] Gv[b][c]; computed row by row into Y in place via a temp per row
-  for (int i = t; i < m; i += nt) {
-    double tmp[kMaxNev];
     for (int c = 0; c < nev; ++c) {
-      double s = 0.0;
-      for (int b = 0; b < nev; ++b) s += Y[b * m + i] * Gv[b * kMaxNev + c];
-      tmp[c] = s;
+      double* yc = Y + c * m;
+      if (crowd[c]) {
+        for (int b = 0; b < c; ++b) {
+          if (!crowd[b]) continue;
+          const double* yb = Y + b * m;
+          double dot = 0.0, nb = 0.0;
+          for (int i = 0; i < m; ++i) {
+            dot += yb[i] * yc[i];
+            nb += yb[i] * yb[i];
+          }
+          for (int i = 0; i < m; ++i) yc[i] -= (dot / nb) * yb[i];
+        }
+      }
     }
-    for (int c = 0; c < nev; ++c) Y[c * m + i] = tmp[c];
   }
   __syncthreads();
-  // ---- back-transform: y <- H_0 H_1 ... H_{m-3} y, H_j = I - tau_j v_j v_j^T on rows j+1..
+  if (t < nev) {
+    double* y = Y + t * m;
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += y[i] * y[i];
+    nrm = 1.0 / sqrt(nrm);
+    for (int i = 0; i < m; ++i) y[i] *= nrm;
+    ev[t] = rayleigh_tri(d, e, m, y);
+    for (int i = 0; i < m; ++i) Yd[t * m + i] = df_from_double(y[i]);
+  }
+  __syncthreads();
+  // ---- 4. back-transform y <- H_0 H_1 ... H_{m-3} y (double-float), warp per vector
   for (int j = m - 3; j >= 0; --j) {
-    const double tj = tau[j];
-    if (tj == 0.0) continue;
+    const float2 tj = tau[j];
+    if (tj.x == 0.f) continue;
     const int len = m - j - 1;
     for (int c = warp; c < nev; c += nwarp) {
-      double part = 0.0;
-      for (int i = lane; i < len; i += 32) part += A[(j + 1 + i) * m + j] * Y[c * m + j + 1 + i];
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      const double s = tj * part;
-      for (int i = lane; i < len; i += 32) Y[c * m + j + 1 + i] -= s * A[(j + 1 + i) * m + j];
+      float ph = 0.f, pl = 0.f;
+      for (int i = lane; i < len; i += 32) acc_mac(ph, pl, A[(j + 1 + i) * ld + j], Yd[c * m + j + 1 + i]);
+      const float2 sdot = df_mul(tj, warp_sum_df(acc_get(ph, pl)));
+      for (int i = lane; i < len; i += 32)
+        Yd[c * m + j + 1 + i] = df_sub(Yd[c * m + j + 1 + i], df_mul(sdot, A[(j + 1 + i) * ld + j]));
     }
     __syncthreads();
   }
   for (int x = t; x < m * nev; x += nt) {
     const int i = x / nev, c = x % nev;
-    V[i * ldv + c] = Y[c * m + i];
+    V[i * ldv + c] = df_to_double(Yd[c * m + i]);
   }
   if (t < nev) theta[t] = ev[t];
 }
@@ -442,8 +450,10 @@ cudaError_t chol_rinv(const double* G, int ldg, int kk, int kp, double shift_rel
 }
 
 static size_t syev_smem(int m) {
-  return sizeof(double) * ((size_t)m * m + 6 * (size_t)m + (size_t)m * kMaxNev + kMaxNev + 32 +
-                           3 * kMaxNev * kMaxNev) + 1024;
+  const size_t f2 = (size_t)m * (m + 1) + 3 * (size_t)m + 40 + (size_t)kMaxNev * m;   // float2 entries
+  const size_t db = 3 * (size_t)m + (size_t)kMaxNev * m + 3 * kMaxNev;               // doubles
+  const size_t fl = 2 * (size_t)m;                                                   // floats
+  return f2 * sizeof(float2) + db * sizeof(double) + fl * sizeof(float) + kMaxNev * sizeof(int) + 256;
 }
 
 cudaError_t syev_lowest(const double* S, int lds, int m, int nev, double* theta, double* V, int ldv,
