@@ -87,6 +87,12 @@ typedef struct {
   double precond_clamp;    /* denominators of the preconditioner clamped to |.| >= this (1e-2) */
   int32_t hybrid_blocks;   /* continuation basis limit in blocks of k vectors before a thick restart
                               to 2k Ritz vectors (default 0 = p_max + 1; at least 3) */
+  int32_t spmm_kernel;     /* SpMM kernel for 8-column blocks: 1 = rows of X gathered into registers
+                              (default), 0 = gathered into shared memory by the tensor memory
+                              accelerator; both give identical results (other widths always use 1) */
+  int32_t reorth;          /* continuation's block Gram-Schmidt: 0 = second projection only when the
+                              first kept less than half of some column's norm (default), 1 = always
+                              twice (SPPC orders always project twice, Eq. blkGS) */
 } sppc_opts;
 
 typedef struct {
@@ -105,6 +111,7 @@ typedef struct {
   int32_t refine_steps;      /* continuation steps run (hybrid) */
   int32_t restarts;          /* thick restarts of the continuation */
   int32_t switched_at;       /* SPPC order at which the continuation started */
+  int32_t reorth_passes;     /* appended blocks that needed the second Gram-Schmidt pass */
 } sppc_stats;
 
 /* Fill `o` with the defaults listed above. */
@@ -158,8 +165,9 @@ sppc_status sppc_start(sppc_handle h, double* theta, double* resid, void* stream
 /* One correction order p -> p+1 (Alg. 2 loop body, first half): right-hand side
  * of Eq. exp_seq2 from the recycled H Psi^(p-1) (Eqs. avoid_SpMV2, HPsip), the
  * correction energies E^(p) (Eq. exp_seq), x2 = -b2/E^(0) (Eq. sm_first), the k
- * deflated small solves by MINRES (Eq. sm_lin_proj), block Gram-Schmidt twice
- * (Eq. blkGS) and CholeskyQR2 (Eq. QR), appending q^(p) to Q (Eq. Qp). */
+ * deflated small solves by MINRES (Eq. sm_lin_proj), block Gram-Schmidt (Eq.
+ * blkGS; a second pass when the first removed more than half of some column's
+ * norm) and CholeskyQR2 (Eq. QR), appending q^(p) to Q (Eq. Qp). */
 sppc_status sppc_correct(sppc_handle h, void* stream);
 
 /* Rayleigh-Ritz after sppc_correct (second half of the loop body): W_p = H q^(p)

@@ -18,8 +18,11 @@ Step by step, from Q (orthonormal, n x m), W = H Q, Ht = Q^T W:
  2. T_j = R_j / (diag(H) - theta_j) elementwise, each denominator clamped to
     magnitude >= clamp (Jacobi preconditioner), or T = R without preconditioner.
  3. Restart if m + k > max_blocks * k: Q <- Q Y_2k, W <- W Y_2k, Ht <- Q^T W.
- 4. Phi = (I - Q Q^T) T applied twice, Phi = q R (Householder QR), Q <- [Q, q],
-    W <- [W, H q], Ht bordered.
+ 4. Phi = (I - Q Q^T) T; a second application when the first left some
+    column with less than half of its norm (the reorthogonalisation criterion of
+    Daniel, Gragg, Kaufman and Stewart, 1976, with the factor 1/2 of Kahan's
+    "twice is enough" analysis; reorth="twice" always applies it);
+    Phi = q R (Householder QR), Q <- [Q, q], W <- [W, H q], Ht bordered.
 """
 from __future__ import annotations
 
@@ -50,10 +53,15 @@ def _ritz(Q, W, k, nev):
 
 def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, tol: float = 1e-6,
                 max_blocks: int = 16, maxit: int = 500, precond: str = "jacobi", clamp: float = 1e-2,
-                solver: str = "pinv", minres_tol: float = 1e-12):
+                solver: str = "pinv", minres_tol: float = 1e-12, reorth: str = "cond",
+                perturb: float = 0.0, perturb_seed: int = 0):
     """Run SPPC (Algorithm 2) for up to `switch_order` orders (stopping early if
     every scaled residual is below tol), then the block continuation above.
-    Returns (theta, resid, converged, records)."""
+    Returns (theta, resid, converged, records).
+
+    perturb > 0 multiplies every entry of T by (1 + perturb * N(0, 1)) each step
+    (seeded): a test hook that measures how far rounding-sized differences carry
+    along the trajectory."""
     n = row_ptr.shape[0] - 1
     r = sppc(row_ptr, col, val, n1, k, p_max=switch_order, tol=tol, solver=solver, minres_tol=minres_tol,
              keep=True)
@@ -62,6 +70,7 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
     if r.converged:
         return r.theta, r.resid, True, records
     Q, W = r.Q, r.W
+    rng = np.random.Generator(np.random.PCG64(perturb_seed))
     diag = np.zeros(n)
     rows = np.repeat(np.arange(n), np.diff(row_ptr))
     on = rows == col
@@ -80,13 +89,17 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
             T = R / den
         else:
             T = R.copy()
+        if perturb > 0.0:
+            T = T * (1.0 + perturb * rng.standard_normal(T.shape))
         # step 3: thick restart
         if Q.shape[1] + k > max_blocks * k:
             Q = Q @ Y_all[:, :2 * k]
             W = W @ Y_all[:, :2 * k]
-        # step 4: block Gram-Schmidt twice + QR, extend the basis by k SpMVs
+        # step 4: block Gram-Schmidt (second pass by the criterion) + QR, extend
+        # the basis by k SpMVs
         Phi = T - Q @ (Q.T @ T)
-        Phi = Phi - Q @ (Q.T @ Phi)
+        if reorth == "twice" or np.any(np.linalg.norm(Phi, axis=0) < 0.5 * np.linalg.norm(T, axis=0)):
+            Phi = Phi - Q @ (Q.T @ Phi)
         q, _ = np.linalg.qr(Phi)
         Wq = csr_spmm(row_ptr, col, val, q)
         spmv += k

@@ -46,7 +46,8 @@ class Opts(ctypes.Structure):
                 ("degeneracy_tol", ctypes.c_double), ("check_symmetry", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("timing", ctypes.c_int32), ("spmm_chunk_cols", ctypes.c_int64),
                 ("hybrid", ctypes.c_int32), ("switch_order", ctypes.c_int32), ("hybrid_maxit", ctypes.c_int32),
-                ("precond", ctypes.c_int32), ("precond_clamp", ctypes.c_double), ("hybrid_blocks", ctypes.c_int32)]
+                ("precond", ctypes.c_int32), ("precond_clamp", ctypes.c_double), ("hybrid_blocks", ctypes.c_int32),
+                ("spmm_kernel", ctypes.c_int32), ("reorth", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -54,7 +55,8 @@ class Stats(ctypes.Structure):
                 ("spmv_h11", ctypes.c_int64), ("minres_iters", ctypes.c_int64), ("small_eig_iters", ctypes.c_int64),
                 ("spmm_launches", ctypes.c_int32), ("spmm_ms", ctypes.c_double), ("minres_ms", ctypes.c_double),
                 ("small_eig_ms", ctypes.c_double), ("dense_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
-                ("refine_steps", ctypes.c_int32), ("restarts", ctypes.c_int32), ("switched_at", ctypes.c_int32)]
+                ("refine_steps", ctypes.c_int32), ("restarts", ctypes.c_int32), ("switched_at", ctypes.c_int32),
+                ("reorth_passes", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -62,6 +62,7 @@ struct sppc_ctx {
 
   // matrix (device)
   SellDev H, H11;
+  CsrDev H11c;  // H0_hat as CSR for the persistent MINRES
   std::vector<void*> allocs;
   int64_t h_slices = 0, h11_slices = 0;
   std::vector<int64_t> h_chunk_slice, h11_chunk_slice;  // host copies (SellDev points here)
@@ -429,6 +430,39 @@ sppc_status upload_sell(sppc_ctx* h, SellHost& S, SellDev& D, int64_t nrows, std
   return SPPC_OK;
 }
 
+// H0_hat (rows and columns < n1 of H) as CSR with double-float values.
+sppc_status upload_csr11(sppc_ctx* h, int64_t n1, const int64_t* rp, const int32_t* ci, const double* va) {
+  std::vector<int64_t> p(n1 + 1, 0);
+  for (int64_t r = 0; r < n1; ++r) {
+    int64_t c = 0;
+    for (int64_t t = rp[r]; t < rp[r + 1] && ci[t] < n1; ++t) ++c;
+    p[r + 1] = p[r] + c;
+  }
+  std::vector<int32_t> col(std::max<int64_t>(p[n1], 1));
+  std::vector<float2> val(std::max<int64_t>(p[n1], 1));
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < n1; ++r)
+    for (int64_t t = 0; t < p[r + 1] - p[r]; ++t) {
+      col[p[r] + t] = ci[rp[r] + t];
+      split_df(va[rp[r] + t], val[p[r] + t]);
+    }
+  int64_t* drp;
+  int32_t* dcol;
+  float2* dval;
+  CK(dalloc(h, &drp, p.size()));
+  CK(dalloc(h, &dcol, col.size()));
+  CK(dalloc(h, &dval, val.size()));
+  CK(cudaMemcpyAsync(drp, p.data(), sizeof(int64_t) * p.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(dcol, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(dval, val.data(), sizeof(float2) * val.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->H11c.nrows = n1;
+  h->H11c.rowptr = drp;
+  h->H11c.col = dcol;
+  h->H11c.val = dval;
+  return SPPC_OK;
+}
+
 // ---------------------------------------------------------- timing helpers
 cudaEvent_t next_event(sppc_ctx* h) {
   if (h->evnext >= (int)h->evpool.size()) {
@@ -699,7 +733,7 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
   int maxit = h->opt.minres_maxit;
   if (maxit <= 0) maxit = (int)std::min<int64_t>(200000, 20 * n1);
   int* dstat = h->dStatus + 32;
-  CK(minres_persistent(h->H11, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
+  CK(minres_persistent(h->H11c, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
                        h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s));
   // x -= psi_hat (psi_hat^T x): keep the solution on the complement of psi_hat_k
   float2* x = h->mx;
@@ -759,12 +793,16 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
   return SPPC_OK;
 }
 
-// Block Gram-Schmidt with the projector applied twice (Eq. blkGS) of src against
-// Q blocks 0..p-1, then CholeskyQR2 (Eq. QR) into Q block p (Eq. Qp).  Leaves the
-// projection coefficients C = C1 + C2 in dC1 and R = R2 R1 in the recycle
-// coefficients [C; R] (Eq. HPsip).  dd (host, 2*kp) receives ||src_j||^2 and
-// ||Phi_j||^2 (valid after the next stream synchronisation).
-sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd) {
+// Block Gram-Schmidt (Eq. blkGS) of src against Q blocks 0..p-1, then
+// CholeskyQR2 (Eq. QR) into Q block p (Eq. Qp).  SPPC orders apply the
+// projector twice, as Eq. blkGS does.  With `cond` (the block continuation) the
+// second application runs only when the first removed more than half of some
+// column's norm (criterion of Daniel, Gragg, Kaufman and Stewart with Kahan's
+// factor: after a pass that keeps at least half the norm the result is
+// orthogonal to Q to working accuracy).  Leaves the projection coefficients C
+// (sum of the passes) in dC1 and R = R2 R1 in the recycle coefficients [C; R]
+// (Eq. HPsip).  dd (host, 2*kp) receives ||src_j||^2 and ||Phi_j||^2.
+sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool cond) {
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
@@ -775,18 +813,28 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd) {
   k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig); count_launch();
   CK(cudaGetLastError());
   CK(update(h->T1, src, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
-  CK(gram(Qs, h->T1, kp, 0, n, h->dC2, h->partials, h->partial_cap, s));
-  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig); count_launch();
-  CK(cudaGetLastError());
-  CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
-  k_addmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, h->dC2, nc, h->dC1); count_launch();  // C = C1 + C2
-  CK(cudaGetLastError());
   {
     const float2* A[2] = {src, h->T1};
     const float2* B[2] = {src, h->T1};
     CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
   }
   CK(cudaMemcpyAsync(dd, h->dDots, sizeof(double) * 2 * kp, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  bool again = !cond;
+  for (int j = 0; j < k; ++j) again |= !(dd[kp + j] >= 0.25 * dd[j]);  // ||Phi_j|| < ||src_j|| / 2
+  h->stats.reorth_passes += again ? 1 : 0;
+  if (again) {
+    CK(gram(Qs, h->T1, kp, 0, n, h->dC2, h->partials, h->partial_cap, s));
+    k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig); count_launch();
+    CK(cudaGetLastError());
+    CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
+    k_addmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, h->dC2, nc, h->dC1); count_launch();  // C = C1 + C2
+    CK(cudaGetLastError());
+    const float2* A[1] = {h->T1};
+    const float2* B[1] = {h->T1};
+    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+    CK(cudaMemcpyAsync(dd + kp, h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+  }
   float2* q = blk(h->Q, n, kp, p);
   CK(gram(one(h->T1), h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
   CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR1, h->dRinv, h->dStatus, s));
@@ -796,9 +844,11 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd) {
   CK(update(q, nullptr, nullptr, one(h->T2), h->dRinv, kp, 0, n, s));
   k_recycle_coefs<<<1, 256, 0, s>>>(h->dC1, p, kp, h->dR2, h->dR1, h->dRecycle); count_launch();
   CK(cudaGetLastError());
-  int st[2] = {0, 0};
+  int st[2] = {0, 0}, tmo = 0;
   CK(cudaMemcpyAsync(st, h->dStatus, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  CK(spmm_tma_read_timeout(&tmo, s));
   CK(cudaStreamSynchronize(s));
+  if (tmo) return fail(h, SPPC_ERR_TIMEOUT, "SpMM: a shared-memory pipeline wait timed out");
   if (st[0] || st[1])
     return fail(h, SPPC_ERR_BREAKDOWN, "CholeskyQR breakdown appending block %d (rank-deficient block)", p);
   return SPPC_OK;
@@ -848,7 +898,7 @@ sppc_status refine_step(sppc_ctx* h) {
   h->t_ready = false;
   if (h->p + 1 >= std::min(h->pmax + 1, h->opt.hybrid_blocks)) CKS(restart(h));
   std::vector<double> dd(2 * kp);
-  CKS(orth_append(h, h->HPsi, h->p + 1, dd.data()));
+  CKS(orth_append(h, h->HPsi, h->p + 1, dd.data(), h->opt.reorth == 0));
   h->p += 1;
   CKS(big_spmm(h, blk(h->Q, n, kp, h->p), blk(h->W, n, kp, h->p), kp));
   h->stats.spmv_h += h->k;
@@ -905,6 +955,8 @@ void sppc_default_opts(sppc_opts* o) {
   o->precond = 1;
   o->precond_clamp = 1e-2;
   o->hybrid_blocks = 0;
+  o->spmm_kernel = 1;
+  o->reorth = 0;
 }
 
 const char* sppc_last_error(sppc_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -945,6 +997,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opts) opt = *opts;
   if (opt.p_max < 0 || opt.p_max > kMaxBlocks - 2 || (int64_t)k * (opt.p_max + 1) > 144)
     return fail(nullptr, SPPC_ERR_ARG, "p_max out of range (k*(p_max+1) must be <= 144)");
+  if (opt.spmm_kernel != 0 && opt.spmm_kernel != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.spmm_kernel must be 0 or 1");
+  if (opt.reorth != 0 && opt.reorth != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.reorth must be 0 or 1");
 
   h = new sppc_ctx();
   if (opt.hybrid_blocks <= 0 || opt.hybrid_blocks > opt.p_max + 1) opt.hybrid_blocks = opt.p_max + 1;
@@ -1045,6 +1099,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     build_sell(n, rp, ci, va, n, seg, 1024, chunk, S);
     sppc_status st = upload_sell(h, S, h->H, n, h->h_chunk_slice);
     if (st != SPPC_OK) return bail(st);
+    h->H.tma = (opt.spmm_kernel == 0 && spmm_tma_available()) ? 1 : 0;
     h->h_slices = S.nslices;
     h->h_slice_ptr = std::move(S.slice_ptr);
     h->h_slice_rows = std::move(S.rows);
@@ -1058,6 +1113,9 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     h->h11_slices = S.nslices;
     h->h11_slice_ptr = std::move(S.slice_ptr);
     h->h11_slice_rows = std::move(S.rows);
+    h->H11.tma = h->H.tma;
+    st = upload_csr11(h, n1, rp, ci, va);
+    if (st != SPPC_OK) return bail(st);
   }
   // diag(H) for the preconditioned continuation
   {
@@ -1158,7 +1216,10 @@ sppc_status sppc_spmm_host(sppc_handle h, const double* X, int64_t ldx, double* 
   CKS(sppc_spmm(h, dX, ncols, dY, ncols, ncols, stream));
   CK(cudaMemcpy2DAsync(Y, sizeof(double) * ldy, dY, sizeof(double) * ncols, sizeof(double) * ncols, h->n,
                        cudaMemcpyDeviceToHost, s));
+  int tmo = 0;
+  CK(spmm_tma_read_timeout(&tmo, s));
   CK(cudaStreamSynchronize(s));
+  if (tmo) return fail(h, SPPC_ERR_TIMEOUT, "SpMM: a shared-memory pipeline wait timed out");
   return SPPC_OK;
 }
 
@@ -1292,7 +1353,7 @@ sppc_status sppc_correct(sppc_handle h, void* stream) {
   }
   // block Gram-Schmidt twice (Eq. blkGS) + CholeskyQR2 (Eq. QR), q^(p) -> Q block p
   std::vector<double> dd(2 * kp);
-  CKS(orth_append(h, Psip, p, dd.data()));
+  CKS(orth_append(h, Psip, p, dd.data(), false));
   std::vector<double> ep(kp);
   CK(cudaMemcpyAsync(ep.data(), h->dE + (size_t)p * kp, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

@@ -15,24 +15,33 @@ namespace {
 
 constexpr int kChunk = 2048;  // rows per CTA in the reductions
 
+// One warp per output: lane l adds the partials of chunks l, l+32, ... in order,
+// then the 32 lane sums are combined by a fixed butterfly (deterministic).
 __global__ void k_finish(const float2* __restrict__ partials, int64_t nchunks, int nout, double* __restrict__ out) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (o >= nout) return;
   float sh = 0.f, sl = 0.f;
-  for (int64_t c = 0; c < nchunks; ++c) {
+  for (int64_t c = lane; c < nchunks; c += 32) {
     acc_add(sh, sl, partials[c * nout + o]);
     acc_norm(sh, sl);
   }
-  out[o] = (double)sh + (double)sl;
+  const float2 t = warp_sum_df(acc_get(sh, sl));
+  if (lane == 0) out[o] = (double)t.x + (double)t.y;
 }
 
-// One CTA = KP warps and kChunk rows; warp i owns column i of each A block,
-// lanes stride over rows.  B rows are shared through L1.
+// One CTA = 8 warps and kChunk rows.  A warp covers 32/KP rows at a time, lane
+// (row u, column i) with i = lane % KP: the A block rows are read contiguously
+// and the lanes of one row share (broadcast) its B row.  Each lane accumulates
+// the KP dots (i, j); lanes with equal i and the 8 warps are then combined.
 template <int KP>
 __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restrict__ B, int64_t r0, int64_t r1,
                                               float2* __restrict__ partials) {
-  const int lane = threadIdx.x & 31;
-  const int i = threadIdx.x >> 5;
+  constexpr int RPW = 32 / KP;   // rows per warp step (KP = 6 leaves 2 lanes idle)
+  __shared__ float2 red[8][KP * KP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = lane % KP, u = lane / KP;
+  const bool active = u < RPW;
   const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * kChunk;
   const int64_t c1 = min(c0 + kChunk, r1);
   const int nout = A.n * KP * KP;
@@ -42,25 +51,41 @@ __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restr
 #pragma unroll
     for (int j = 0; j < KP; ++j) sh[j] = sl[j] = 0.f;
     int cnt = 0;
-    for (int64_t r = c0 + lane; r < c1; r += 32) {
-      const float2 av = Aa[r * KP + i];
-      const float4* br = reinterpret_cast<const float4*>(B + r * KP);
+    if (active) {
+      for (int64_t r = c0 + warp * RPW + u; r < c1; r += 8 * RPW) {
+        const float2 av = Aa[r * KP + i];
+        const float4* br = reinterpret_cast<const float4*>(B + r * KP);
 #pragma unroll
-      for (int q = 0; q < KP / 2; ++q) {
-        const float4 b = br[q];
-        acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b.x, b.y));
-        acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b.z, b.w));
-      }
-      if (((++cnt) & 15) == 0) {
+        for (int q = 0; q < KP / 2; ++q) {
+          const float4 b = br[q];
+          acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b.x, b.y));
+          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b.z, b.w));
+        }
+        if (((++cnt) & 15) == 0) {
 #pragma unroll
-        for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
+          for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
+        }
       }
     }
+    // combine the RPW row-lanes of column i inside the warp (fixed order)
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
-      const float2 t = warp_sum_df(acc_get(sh[j], sl[j]));
-      if (lane == 0) partials[static_cast<int64_t>(blockIdx.x) * nout + (a * KP + i) * KP + j] = t;
+      float2 v = active ? acc_get(sh[j], sl[j]) : make_float2(0.f, 0.f);
+      for (int uu = 1; uu < RPW; ++uu) {
+        const float2 o = make_float2(__shfl_sync(0xffffffffu, v.x, lane + uu * KP < 32 ? lane + uu * KP : lane),
+                                     __shfl_sync(0xffffffffu, v.y, lane + uu * KP < 32 ? lane + uu * KP : lane));
+        if (u == 0) v = df_add(v, o);
+      }
+      if (u == 0 && lane < KP) red[warp][i * KP + j] = v;
     }
+    __syncthreads();
+    if (threadIdx.x < KP * KP) {
+      float2 t = red[0][threadIdx.x];
+      for (int w = 1; w < 8; ++w) t = df_add(t, red[w][threadIdx.x]);
+      const int ii = threadIdx.x / KP, jj = threadIdx.x % KP;
+      partials[static_cast<int64_t>(blockIdx.x) * nout + (a * KP + ii) * KP + jj] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -286,13 +311,13 @@ cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_
   if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(nchunks);
   switch (kp) {
-    case 2: k_gram<2><<<g, 64, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
-    case 4: k_gram<4><<<g, 128, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
-    case 6: k_gram<6><<<g, 192, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
+    case 2: k_gram<2><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
+    case 4: k_gram<4><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
+    case 6: k_gram<6><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
     case 8: k_gram<8><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
-  k_finish<<<nblk(nout, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
+  k_finish<<<nblk((int64_t)nout * 32, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
   return cudaGetLastError();
 }
 
@@ -345,7 +370,7 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
     case 8: k_coldots<8><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
-  k_finish<<<nblk(nout, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
+  k_finish<<<nblk((int64_t)nout * 32, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
   return cudaGetLastError();
 }
 
@@ -363,7 +388,7 @@ cudaError_t ritz_resid(const BlockList& Q, const BlockList& Wb, const float2* Y,
     case 8: k_ritz_resid<8><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
-  k_finish<<<1, 32, 0, s>>>(partials, nchunks, kp, out); count_launch();
+  k_finish<<<nblk((int64_t)kp * 32, 256), 256, 0, s>>>(partials, nchunks, kp, out); count_launch();
   return cudaGetLastError();
 }
 

@@ -11,20 +11,26 @@
 // s = psi^T y, alpha = v^T (P y - beta v_prev), p = P y - beta v_prev - alpha v.
 //
 // Schedule per iteration (two grid-wide barriers):
-//   A  per owned row: apply the previous step's Givens update to w and x,
+//   A  per owned element: apply the previous step's Givens update to w and x,
 //      v_new = p / beta, y = (H0_hat p - E p) / beta (the SpMM gathers p, which
 //      is final), partial dots -> barrier
 //   B  reduce the dots (every CTA, same order), p = y - s psi - beta v_prev -
 //      alpha v, partial ||p||^2 -> barrier
 //   C  reduce ||p||^2, Givens rotation, convergence, coefficients of the next A.
-// Rows are owned by the warp whose SpMM slice holds them (two lanes per row),
-// so all row updates are local.  Every CTA computes the same scalars from the
-// same partial sums, so no broadcast is needed.  The grid barrier spins with a
-// bound (about a second); on time-out it raises an error flag and every CTA
-// leaves at its next barrier.
+//
+// Work split: a row of H0_hat (CSR) is handled by 8 lanes, 4 rows per warp at a
+// time.  For the product the 8 lanes are 4 entry segments (entries seg, seg+4,
+// ...) x 2 column halves (a half row of p is one 256-bit gather for kp = 8);
+// after the segment sums are combined by shuffles, lane (half, seg) owns the
+// single element (row, half*kp/2 + seg) for every vector update.  A lane therefore
+// reads and writes only its own elements of v, w, x, y, and only p is exchanged
+// between CTAs; p is gathered with coherent loads, ordered by the barrier's
+// fences.  Every CTA computes the same scalars from the same partial sums, so no
+// broadcast is needed.  The grid barrier spins with a bound (about a second); on
+// time-out it raises an error flag and every CTA leaves at its next barrier.
 #include <cooperative_groups.h>
 
-#include "spmm_core.cuh"
+#include "spmm_core.cuh"  // policy_keep
 
 namespace sppc {
 
@@ -34,7 +40,7 @@ constexpr int kMinresThreads = 512;  // 16 warps: few CTAs keep barriers and red
 constexpr int kMinresWarps = kMinresThreads / 32;
 
 struct MinresKernelArgs {
-  SellDev A;
+  CsrDev A;
   int k;
   const float2* negE;  // -E_k^(0) per column, double-float
   const float2* psi;   // n1 x kp
@@ -102,14 +108,101 @@ __device__ void reduce_partials(const float2* partials, int nout, float2* sred /
   __syncthreads();
 }
 
+// Coherent gather of the CPL-column half row of p at row cidx (p is rewritten by
+// other CTAs between barriers, so the read-only path must not be used).
+template <int KP>
+__device__ __forceinline__ void gather_p(const float2* X, int cidx, int off, float2 (&x)[KP / 2], uint64_t pol) {
+  const float2* p = X + static_cast<int64_t>(cidx) * KP + off;
+  if constexpr (KP == 8) {
+    float4 a, b;
+    asm volatile("ld.global.L2::cache_hint.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p), "l"(pol)
+                 : "memory");
+    x[0] = make_float2(a.x, a.y);
+    x[1] = make_float2(a.z, a.w);
+    x[2] = make_float2(b.x, b.y);
+    x[3] = make_float2(b.z, b.w);
+  } else if constexpr (KP == 4) {
+    float4 a;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w)
+                 : "l"(p), "l"(pol)
+                 : "memory");
+    x[0] = make_float2(a.x, a.y);
+    x[1] = make_float2(a.z, a.w);
+  } else {
+#pragma unroll
+    for (int j = 0; j < KP / 2; ++j)
+      asm volatile("ld.global.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;"
+                   : "=f"(x[j].x), "=f"(x[j].y)
+                   : "l"(p + j), "l"(pol)
+                   : "memory");
+  }
+}
+
+// Row sums of H0_hat p for one row: this lane's segment (entries seg, seg+4, ...),
+// columns [off, off + CPL), in batches of 4 independent gathers, then the
+// segment sums combined across the 4 lanes of the half (all 32 lanes call it).
+template <int KP>
+__device__ __forceinline__ void row_product(const CsrDev& A, int64_t row, bool valid, int seg, int off,
+                                            const float2* P, uint64_t pol, float2 (&out)[KP / 2]) {
+  constexpr int CPL = KP / 2;
+  float ah[CPL], al[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) ah[c] = al[c] = 0.f;
+  if (valid) {
+    const int64_t rb = __ldg(A.rowptr + row), re = __ldg(A.rowptr + row + 1);
+    for (int64_t e = rb + seg; e < re; e += 16) {
+      int cc[4];
+      float2 vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t ee = e + 4 * u;
+        cc[u] = (ee < re) ? __ldg(A.col + ee) : -1;
+        vv[u] = (ee < re) ? __ldg(A.val + ee) : make_float2(0.f, 0.f);
+      }
+      float2 xx[4][CPL];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (cc[u] >= 0) {
+          gather_p<KP>(P, cc[u], off, xx[u], pol);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) xx[u][c] = make_float2(0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc_mac(ah[c], al[c], vv[u], xx[u][c]);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) acc_norm(ah[c], al[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    float2 v = acc_get(ah[c], al[c]);
+    v = df_add(v, shfl_xor_df(v, 1));
+    v = df_add(v, shfl_xor_df(v, 2));
+    out[c] = v;
+  }
+}
+
 template <int KP>
 __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
   constexpr int CPL = KP / 2;
+  constexpr int kRowsPerWarp = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rl = lane >> 1;
-  const int off = (lane & 1) * CPL;
-  const int64_t gw = static_cast<int64_t>(blockIdx.x) * kMinresWarps + warp;
-  const int64_t nw = static_cast<int64_t>(gridDim.x) * kMinresWarps;
+  const int rq = lane >> 3;             // row of the warp's group of 4
+  const int half = (lane >> 2) & 1;     // column half
+  const int seg = lane & 3;             // entry segment; element column in the half
+  const int off = half * CPL;
+  const int j = off + seg;              // owned element column (valid if seg < CPL)
+  const bool has_col = seg < CPL;
+  const int64_t n = a.A.nrows;
+  const int64_t row0 = (static_cast<int64_t>(blockIdx.x) * kMinresWarps + warp) * kRowsPerWarp;
+  const int64_t rstride = static_cast<int64_t>(gridDim.x) * kMinresWarps * kRowsPerWarp;
   const uint64_t pol = policy_keep();
   int* err = a.status;
 
@@ -119,32 +212,22 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
   // per-column MINRES state (identical in every CTA)
   __shared__ double st_beta[8], st_cp[8], st_cc[8], st_sp[8], st_sc[8], st_eta[8], st_rn[8], st_b1[8], st_alpha[8];
   __shared__ int st_done[8], st_it[8];
-  // coefficients (double-float) of the row updates
+  // coefficients (double-float) of the element updates
   __shared__ float2 c_invb[8], c_wa[8], c_w2[8], c_w1[8], c_x[8], c_s[8], c_beta[8], c_alpha[8];
   __shared__ int s_dow, s_all;
 
   float2 *P = a.P, *V = a.V, *VP = a.VP, *W1 = a.W1, *W2 = a.W2;
 
-  // block-level dot accumulation helpers: lane holds CPL columns of one row
-  auto zero_acc = [](float (&h)[4][CPL], float (&l)[4][CPL]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) h[q][c] = l[q][c] = 0.f;
-  };
   // write this CTA's partial of nq dots (columns 0..KP-1) to partials[blockIdx]
-  auto flush = [&](float (&h)[4][CPL], float (&l)[4][CPL], int nq) {
+  auto flush = [&](float (&h)[4], float (&l)[4], int nq) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (q >= nq) break;
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        float2 v = acc_get(h[q][c], l[q][c]);
-        // sum over the 16 rows of the warp (lanes of equal parity)
-#pragma unroll
-        for (int m = 2; m < 32; m <<= 1) v = df_add(v, shfl_xor_df(v, m));
-        if (lane < 2) wred[warp][q * 8 + off + c] = v;
-      }
+      float2 v = has_col ? acc_get(h[q], l[q]) : make_float2(0.f, 0.f);
+      // sum over the 4 rows of the warp (lanes with equal half and seg)
+      v = df_add(v, shfl_xor_df(v, 8));
+      v = df_add(v, shfl_xor_df(v, 16));
+      if (lane < 8 && has_col) wred[warp][q * 8 + j] = v;
     }
     __syncthreads();
     if (threadIdx.x < nq * 8) {
@@ -154,44 +237,46 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
     }
     __syncthreads();
   };
+  auto zero4 = [](float (&h)[4], float (&l)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = l[q] = 0.f;
+  };
 
   for (int t = threadIdx.x; t < kMinresWarps * 32; t += kMinresThreads)
     wred[t / 32][t % 32] = make_float2(0.f, 0.f);
   __syncthreads();
-  float dh[4][CPL], dl[4][CPL];
-  // ---- init: zero V, VP, W1, W2, X on owned rows; ||b1||^2 partial
-  zero_acc(dh, dl);
-  for (int64_t s = gw; s < a.A.nslices; s += nw) {
-    const int row = a.A.slice_rows[s * kSliceH + rl];
-    if (row < 0) continue;
-    const int64_t b = static_cast<int64_t>(row) * KP + off;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      const float2 z = make_float2(0.f, 0.f);
-      V[b + c] = z;
-      VP[b + c] = z;
-      W1[b + c] = z;
-      W2[b + c] = z;
-      a.X[b + c] = z;
-      const float2 pv = P[b + c];
-      acc_mac(dh[0][c], dl[0][c], pv, pv);
-    }
+  float dh[4], dl[4];
+  // ---- init: zero V, VP, W1, W2, X on owned elements; ||b1||^2 partial
+  zero4(dh, dl);
+  for (int64_t r0 = row0; r0 < n; r0 += rstride) {
+    const int64_t row = r0 + rq;
+    if (row >= n || !has_col) continue;
+    const int64_t b = row * KP + j;
+    const float2 z = make_float2(0.f, 0.f);
+    V[b] = z;
+    VP[b] = z;
+    W1[b] = z;
+    W2[b] = z;
+    a.X[b] = z;
+    const float2 pv = P[b];
+    acc_mac(dh[0], dl[0], pv, pv);
+    acc_norm(dh[0], dl[0]);
   }
   flush(dh, dl, 1);
   if (!grid_barrier(a.bar, err)) return;
   reduce_partials(a.partials, 8, sred, sdot);
   if (threadIdx.x < 8) {
-    const int j = threadIdx.x;
-    const double b1 = (j < a.k) ? sqrt(fmax(df_to_double(sdot[j]), 0.0)) : 0.0;
-    st_beta[j] = b1;
-    st_b1[j] = b1;
-    st_eta[j] = b1;
-    st_rn[j] = b1;
-    st_cp[j] = st_cc[j] = 1.0;
-    st_sp[j] = st_sc[j] = 0.0;
-    st_done[j] = (b1 > 0.0) ? 0 : 1;
-    st_it[j] = 0;
-    c_invb[j] = st_done[j] ? make_float2(0.f, 0.f) : df_from_double(1.0 / b1);
+    const int jj = threadIdx.x;
+    const double b1 = (jj < a.k) ? sqrt(fmax(df_to_double(sdot[jj]), 0.0)) : 0.0;
+    st_beta[jj] = b1;
+    st_b1[jj] = b1;
+    st_eta[jj] = b1;
+    st_rn[jj] = b1;
+    st_cp[jj] = st_cc[jj] = 1.0;
+    st_sp[jj] = st_sc[jj] = 0.0;
+    st_done[jj] = (b1 > 0.0) ? 0 : 1;
+    st_it[jj] = 0;
+    c_invb[jj] = st_done[jj] ? make_float2(0.f, 0.f) : df_from_double(1.0 / b1);
   }
   if (threadIdx.x == 0) {
     s_dow = 0;
@@ -203,39 +288,42 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
   bool finish = false;
   while (true) {
     // ---- phase A
-    zero_acc(dh, dl);
-    for (int64_t s = gw; s < a.A.nslices; s += nw) {
-      const int row = a.A.slice_rows[s * kSliceH + rl];
-      float ah[CPL], al[CPL];
-      if (!finish) slice_rowsum<KP>(a.A, s, rl, off, P, pol, ah, al);
-      if (row < 0) continue;
-      const int64_t b = static_cast<int64_t>(row) * KP + off;
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const int j = off + c;
-        const float2 vold = V[b + c];
-        if (s_dow) {
-          // w_new = (v - rho3 w2 - rho2 w1) / rho1 ; x += c eta w_new
-          float2 wn = df_mul(c_wa[j], vold);
-          wn = df_add(wn, df_mul(c_w2[j], W2[b + c]));
-          wn = df_add(wn, df_mul(c_w1[j], W1[b + c]));
-          W2[b + c] = wn;  // W2's buffer becomes w_new (roles swap below)
-          a.X[b + c] = df_add(a.X[b + c], df_mul(c_x[j], wn));
-        }
-        if (finish) continue;
-        const float2 pv = P[b + c];
-        const float2 vn = df_mul(c_invb[j], pv);
-        VP[b + c] = vn;  // VP's buffer becomes v_new (roles swap below)
-        // y = (H0_hat p - E p) / beta
-        float2 y = df_add(acc_get(ah[c], al[c]), df_mul(a.negE[j], pv));
-        y = df_mul(c_invb[j], y);
-        a.Y[b + c] = y;
-        const float2 ps = a.psi[b + c];
-        acc_mac(dh[0][c], dl[0][c], vn, y);
-        acc_mac(dh[1][c], dl[1][c], ps, y);
-        acc_mac(dh[2][c], dl[2][c], vn, ps);
-        acc_mac(dh[3][c], dl[3][c], vn, vold);
+    zero4(dh, dl);
+    for (int64_t r0 = row0; r0 < n; r0 += rstride) {
+      const int64_t row = r0 + rq;
+      const bool valid = row < n;
+      float2 hp[CPL];
+      if (!finish) row_product<KP>(a.A, row, valid, seg, off, P, pol, hp);
+      if (!valid || !has_col) continue;
+      const int64_t b = row * KP + j;
+      const float2 vold = V[b];
+      if (s_dow) {
+        // w_new = (v - rho3 w2 - rho2 w1) / rho1 ; x += c eta w_new
+        float2 wn = df_mul(c_wa[j], vold);
+        wn = df_add(wn, df_mul(c_w2[j], W2[b]));
+        wn = df_add(wn, df_mul(c_w1[j], W1[b]));
+        W2[b] = wn;  // W2's buffer becomes w_new (roles swap below)
+        a.X[b] = df_add(a.X[b], df_mul(c_x[j], wn));
       }
+      if (finish) continue;
+      float2 hj = hp[0];
+#pragma unroll
+      for (int c = 1; c < CPL; ++c)
+        if (c == seg) hj = hp[c];
+      const float2 pv = P[b];
+      const float2 vn = df_mul(c_invb[j], pv);
+      VP[b] = vn;  // VP's buffer becomes v_new (roles swap below)
+      // y = (H0_hat p - E p) / beta
+      float2 y = df_add(hj, df_mul(a.negE[j], pv));
+      y = df_mul(c_invb[j], y);
+      a.Y[b] = y;
+      const float2 ps = __ldg(a.psi + b);
+      acc_mac(dh[0], dl[0], vn, y);
+      acc_mac(dh[1], dl[1], ps, y);
+      acc_mac(dh[2], dl[2], vn, ps);
+      acc_mac(dh[3], dl[3], vn, vold);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc_norm(dh[q], dl[q]);
     }
     if (s_dow) {
       float2* t = W2;
@@ -253,33 +341,30 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
     // ---- phase B
     reduce_partials(a.partials, 32, sred, sdot);
     if (threadIdx.x < 8) {
-      const int j = threadIdx.x;
+      const int jj = threadIdx.x;
       double s = 0.0, al = 0.0;
-      if (!st_done[j]) {
-        s = df_to_double(sdot[8 + j]);
-        al = df_to_double(sdot[j]) - s * df_to_double(sdot[16 + j]) - st_beta[j] * df_to_double(sdot[24 + j]);
+      if (!st_done[jj]) {
+        s = df_to_double(sdot[8 + jj]);
+        al = df_to_double(sdot[jj]) - s * df_to_double(sdot[16 + jj]) - st_beta[jj] * df_to_double(sdot[24 + jj]);
       }
-      st_alpha[j] = al;
-      c_s[j] = df_from_double(-s);
-      c_beta[j] = df_from_double(st_done[j] ? 0.0 : -st_beta[j]);
-      c_alpha[j] = df_from_double(-al);
+      st_alpha[jj] = al;
+      c_s[jj] = df_from_double(-s);
+      c_beta[jj] = df_from_double(st_done[jj] ? 0.0 : -st_beta[jj]);
+      c_alpha[jj] = df_from_double(-al);
     }
     __syncthreads();
-    zero_acc(dh, dl);
-    for (int64_t s = gw; s < a.A.nslices; s += nw) {
-      const int row = a.A.slice_rows[s * kSliceH + rl];
-      if (row < 0) continue;
-      const int64_t b = static_cast<int64_t>(row) * KP + off;
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const int j = off + c;
-        float2 pn = a.Y[b + c];
-        pn = df_add(pn, df_mul(c_s[j], a.psi[b + c]));
-        pn = df_add(pn, df_mul(c_beta[j], VP[b + c]));
-        pn = df_add(pn, df_mul(c_alpha[j], V[b + c]));
-        P[b + c] = pn;
-        acc_mac(dh[0][c], dl[0][c], pn, pn);
-      }
+    zero4(dh, dl);
+    for (int64_t r0 = row0; r0 < n; r0 += rstride) {
+      const int64_t row = r0 + rq;
+      if (row >= n || !has_col) continue;
+      const int64_t b = row * KP + j;
+      float2 pn = a.Y[b];
+      pn = df_add(pn, df_mul(c_s[j], __ldg(a.psi + b)));
+      pn = df_add(pn, df_mul(c_beta[j], VP[b]));
+      pn = df_add(pn, df_mul(c_alpha[j], V[b]));
+      P[b] = pn;
+      acc_mac(dh[0], dl[0], pn, pn);
+      acc_norm(dh[0], dl[0]);
     }
     flush(dh, dl, 1);
     if (!grid_barrier(a.bar, err)) return;
@@ -287,44 +372,44 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
     reduce_partials(a.partials, 8, sred, sdot);
     ++it;
     if (threadIdx.x < 8) {
-      const int j = threadIdx.x;
+      const int jj = threadIdx.x;
       const float2 z = make_float2(0.f, 0.f);
-      if (st_done[j]) {
-        c_wa[j] = c_w2[j] = c_w1[j] = c_x[j] = c_invb[j] = z;
+      if (st_done[jj]) {
+        c_wa[jj] = c_w2[jj] = c_w1[jj] = c_x[jj] = c_invb[jj] = z;
       } else {
-        const double bn = sqrt(fmax(df_to_double(sdot[j]), 0.0));
-        const double al = st_alpha[j], be = st_beta[j];
-        const double delta = st_cc[j] * al - st_cp[j] * st_sc[j] * be;
+        const double bn = sqrt(fmax(df_to_double(sdot[jj]), 0.0));
+        const double al = st_alpha[jj], be = st_beta[jj];
+        const double delta = st_cc[jj] * al - st_cp[jj] * st_sc[jj] * be;
         const double rho1 = hypot(delta, bn);
-        const double rho2 = st_sc[j] * al + st_cp[j] * st_cc[j] * be;
-        const double rho3 = st_sp[j] * be;
-        st_it[j] += 1;
+        const double rho2 = st_sc[jj] * al + st_cp[jj] * st_cc[jj] * be;
+        const double rho3 = st_sp[jj] * be;
+        st_it[jj] += 1;
         if (rho1 == 0.0) {
-          st_done[j] = 1;
-          c_wa[j] = c_w2[j] = c_w1[j] = c_x[j] = c_invb[j] = z;
+          st_done[jj] = 1;
+          c_wa[jj] = c_w2[jj] = c_w1[jj] = c_x[jj] = c_invb[jj] = z;
         } else {
           const double cn = delta / rho1, sn = bn / rho1;
-          c_wa[j] = df_from_double(1.0 / rho1);
-          c_w2[j] = df_from_double(-rho3 / rho1);
-          c_w1[j] = df_from_double(-rho2 / rho1);
-          c_x[j] = df_from_double(cn * st_eta[j]);
-          st_rn[j] = fabs(sn) * st_rn[j];
-          st_eta[j] = -sn * st_eta[j];
-          st_cp[j] = st_cc[j];
-          st_cc[j] = cn;
-          st_sp[j] = st_sc[j];
-          st_sc[j] = sn;
-          const bool conv = (st_rn[j] <= a.tol * st_b1[j]) || (bn == 0.0);
-          if (conv) st_done[j] = 1;
-          c_invb[j] = conv ? z : df_from_double(1.0 / bn);
+          c_wa[jj] = df_from_double(1.0 / rho1);
+          c_w2[jj] = df_from_double(-rho3 / rho1);
+          c_w1[jj] = df_from_double(-rho2 / rho1);
+          c_x[jj] = df_from_double(cn * st_eta[jj]);
+          st_rn[jj] = fabs(sn) * st_rn[jj];
+          st_eta[jj] = -sn * st_eta[jj];
+          st_cp[jj] = st_cc[jj];
+          st_cc[jj] = cn;
+          st_sp[jj] = st_sc[jj];
+          st_sc[jj] = sn;
+          const bool conv = (st_rn[jj] <= a.tol * st_b1[jj]) || (bn == 0.0);
+          if (conv) st_done[jj] = 1;
+          c_invb[jj] = conv ? z : df_from_double(1.0 / bn);
         }
-        st_beta[j] = bn;
+        st_beta[jj] = bn;
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       int all = 1;
-      for (int j = 0; j < a.k; ++j) all &= st_done[j];
+      for (int jj = 0; jj < a.k; ++jj) all &= st_done[jj];
       s_all = all;
       s_dow = 1;
     }
@@ -343,7 +428,7 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
 // X receives the solution.  All n1 x kp double-float.  status (host-visible via
 // a copy): [0] time-out flag, [1] iterations (negative: limit reached),
 // [2+j] iterations of column j.  bar: two zeroed unsigned words.
-cudaError_t minres_persistent(const SellDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
+cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
                               float2* V, float2* VP, float2* Y, float2* W1, float2* W2, float2* X, double tol,
                               int maxit, float2* partials, int64_t partial_cap, unsigned* bar, int* status,
                               cudaStream_t s) {
@@ -363,7 +448,8 @@ cudaError_t minres_persistent(const SellDev& A, int k, int kp, const float2* neg
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMinresThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  int64_t grid = (A.nslices + kMinresWarps - 1) / kMinresWarps;
+  const int64_t rows_per_cta = static_cast<int64_t>(kMinresWarps) * 4;
+  int64_t grid = (A.nrows + rows_per_cta - 1) / rows_per_cta;
   const int64_t gmax = static_cast<int64_t>(sms) * per_sm;
   if (grid > gmax) grid = gmax;
   if (grid < 1) grid = 1;

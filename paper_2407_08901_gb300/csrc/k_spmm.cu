@@ -83,6 +83,7 @@ int spmm_default_grid() {
 
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s) {
   if (A.nslices == 0) return cudaSuccess;
+  if (kp == 8 && A.tma) return spmm_tma8(A, X, Y, epi, s);
   const int64_t gmax = spmm_default_grid();
   for (int q = 0; q < A.nchunks; ++q) {
     const int64_t s0 = A.nchunks == 1 ? 0 : A.chunk_slice[q];

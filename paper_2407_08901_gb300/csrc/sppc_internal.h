@@ -32,6 +32,16 @@ struct SellDev {
   const float2* val = nullptr;  // double-float values
   const uint8_t* row_first = nullptr;
   const uint8_t* row_last = nullptr;
+  int tma = 0;  // 1: 8-column products use the TMA-gather kernel (k_spmm_tma.cu)
+};
+
+// CSR matrix on the device with double-float values (rowptr has nrows + 1
+// entries; column indices strictly increasing within a row).
+struct CsrDev {
+  int64_t nrows = 0;
+  const int64_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const float2* val = nullptr;
 };
 
 // SpMM epilogue: Y[r][c] = alpha[c] * (A X)[r][c] + beta[c] * X[r][c] + gamma[c] * Z[r][c].
@@ -53,6 +63,13 @@ struct BlockList {
 // ---- k_spmm.cu
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
 int spmm_default_grid();
+
+// ---- k_spmm_tma.cu (kp = 8; X 16-byte aligned)
+bool spmm_tma_available();
+cudaError_t spmm_tma8(const SellDev& A, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
+// Copies the kernel's sticky time-out flag (nonzero after an mbarrier wait gave
+// up) to host memory; valid after the stream synchronises.
+cudaError_t spmm_tma_read_timeout(int* flag, cudaStream_t s);
 
 // ---- k_dense.cu
 // Gram: out[(a*kp+i)*kp + j] = sum_{r in [r0,r1)} A_a[r][i] * B[r][j]  (FP64 out)
@@ -86,7 +103,7 @@ cudaError_t fill_zero(float2* Y, int64_t count, cudaStream_t s);
 // ---- k_minres.cu
 // Persistent MINRES on (A - E_k) x = b for k columns on the complement of psi
 // (see k_minres.cu).  P holds b on entry; X receives the solution.
-cudaError_t minres_persistent(const SellDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
+cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
                               float2* V, float2* VP, float2* Y, float2* W1, float2* W2, float2* X, double tol,
                               int maxit, float2* partials, int64_t partial_cap, unsigned* bar, int* status,
                               cudaStream_t s);

@@ -60,9 +60,11 @@ def test_spmm_matches_oracle(name, ncols):
         S.sppc_destroy(h)
 
 
-def test_spmm_empty_and_ragged_rows():
+@pytest.mark.parametrize("ncols,kernel", [(3, 0), (8, 0), (8, 1)])
+def test_spmm_empty_and_ragged_rows(ncols, kernel):
     """A matrix with empty rows (no stored entry at all) and a level whose size is
-    not a multiple of the 16-row slice."""
+    not a multiple of the 16-row slice; 8 columns run the TMA-gather kernel
+    (kernel 0) or the register-gather one (kernel 1), including slices of width 0."""
     S = _lib()
     n = 203
     rng = np.random.Generator(np.random.PCG64(9))
@@ -82,9 +84,9 @@ def test_spmm_empty_and_ragged_rows():
     c = cols.astype(np.int32)
     v = A[rows, cols]
     lev = np.array([0, 37, 101, n], dtype=np.int64)
-    h = S.sppc_create(rp, c, v, lev, 37, 2)
+    h = S.sppc_create(rp, c, v, lev, 37, 2, S.sppc_default_opts(spmm_kernel=kernel))
     try:
-        X = W.random_block(n, 3, 1)
+        X = W.random_block(n, ncols, 1)
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.full_like(Xd, 7.0)
         S.sppc_spmm(h, Xd, Yd)
@@ -160,6 +162,30 @@ def test_chunked_spmm_matches_oracle(chunk):
         assert np.all(np.abs(Y - ref) <= 1e-12 * mag), np.max(np.abs(Y - ref) / mag)
     finally:
         S.sppc_destroy(h)
+
+
+@pytest.mark.parametrize("name,chunk", [("small", -1), ("small", 700), ("c1", 4096), ("c2mini", 0),
+                                        ("c2mini", 3000)])
+def test_tma_and_register_gather_kernels_agree_bit_for_bit(name, chunk):
+    """The TMA-gather SpMM (8 columns) accumulates every row in the same order and
+    with the same renormalisation as the register-gather kernel: identical bits,
+    and both within the accumulation bound of the oracle."""
+    S = _lib()
+    out = []
+    for kernel in (0, 1):
+        _, w, rp, c, v, h = _create(name, spmm_chunk_cols=chunk, spmm_kernel=kernel)
+        try:
+            X = W.random_block(w.n, 8, 5)
+            Xd = torch.from_numpy(X).cuda()
+            Yd = torch.full_like(Xd, float("nan"))
+            S.sppc_spmm(h, Xd, Yd)
+            out.append(Yd.cpu().numpy())
+        finally:
+            S.sppc_destroy(h)
+    assert np.array_equal(out[0], out[1])
+    ref = csr_spmm(rp, c, v, X)
+    mag = _abs_spmm(rp, c, v, X)
+    assert np.all(np.abs(out[0] - ref) <= 1e-12 * mag + 1e-300), np.max(np.abs(out[0] - ref) / mag)
 
 
 def _compare_orders(S, h, ref, k, rtol_theta=1e-10):

@@ -45,3 +45,31 @@ def test_thick_restart_keeps_converging():
     th, rs, conv, rec = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, switch_order=2, tol=1e-9, max_blocks=4)
     assert conv and max(r.m for r in rec) <= 4 * w.k
     assert np.allclose(th, lam, rtol=1e-12)
+
+
+def test_single_projection_is_enough_when_the_norm_survives():
+    """The second projection changes only rounding when the first one kept at
+    least half of each column's norm: with reorth="cond" and reorth="twice" the
+    eigenvalues of every step agree to rounding, and the basis stays orthonormal
+    to working accuracy either way."""
+    w, rp, c, v = make_matrix(TINY)
+    kw = dict(switch_order=2, tol=1e-300, max_blocks=50, maxit=6)
+    a = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, reorth="twice", **kw)[3]
+    b = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, reorth="cond", **kw)[3]
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        assert np.allclose(x.theta, y.theta, rtol=1e-12, atol=0), x.step
+
+
+def test_perturbation_hook_is_rounding_sized_early():
+    """perturb multiplies T by 1 + perturb*N(0,1): with 1e-15 the first steps of a
+    run differ from the unperturbed one at rounding level only, and perturb=0 is
+    the unperturbed run bit for bit."""
+    w, rp, c, v = make_matrix(TINY)
+    kw = dict(switch_order=1, tol=1e-300, max_blocks=6, maxit=8, precond="none")
+    a = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, **kw)[3]
+    b = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, perturb=1e-15, **kw)[3]
+    z = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, perturb=0.0, perturb_seed=5, **kw)[3]
+    assert all(np.array_equal(x.theta, y.theta) for x, y in zip(a, z))
+    diff = max(np.max(np.abs(x.theta - y.theta) / np.abs(x.theta)) for x, y in zip(a, b))
+    assert 0 < diff < 1e-12
