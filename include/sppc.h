@@ -75,7 +75,7 @@ typedef struct {
   int32_t check_symmetry; /* 1: verify H == H^T bit for bit at create (default 0) */
   uint64_t seed;          /* seed of the small eigensolve's start block (default 0) */
   int32_t timing;         /* 1: time kernels with CUDA events into sppc_stats (default 0) */
-  int64_t spmm_chunk_cols; /* SpMM column tile: 0 = 655360 columns, 40 MB of an 8-column block (default;
+  int64_t spmm_chunk_cols; /* SpMM column tile: 0 = 1310720 columns, 80 MB of an 8-column block (default;
                               keeps the gathered rows of X in L2), -1 = untiled, > 0 = that many
                               columns (at most 255 tiles) */
   int32_t hybrid;          /* 0: plain SPPC (Alg. 2, default); 1: after switch_order SPPC orders continue

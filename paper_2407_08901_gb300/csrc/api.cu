@@ -12,6 +12,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -23,6 +24,15 @@
 using namespace sppc;
 
 namespace {
+
+// Named NVTX ranges around the solver phases (no cost unless a tool such as
+// ncu or nsys is attached; profilers can filter kernels by phase).
+struct PhaseRange {
+  explicit PhaseRange(const char* name) { nvtxRangePushA(name); }
+  ~PhaseRange() { nvtxRangePop(); }
+  PhaseRange(const PhaseRange&) = delete;
+  PhaseRange& operator=(const PhaseRange&) = delete;
+};
 
 thread_local std::string g_create_error;
 
@@ -562,6 +572,7 @@ sppc_status ortho_set(sppc_ctx* h, float2** X, float2** Tmp, int nb, int b) {
 }
 
 sppc_status small_eigensolve(sppc_ctx* h) {
+  PhaseRange nvtx_range("small_eigensolve");
   cudaStream_t s = h->stream;
   const int64_t n1 = h->n1;
   const int k = h->k;
@@ -726,6 +737,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
 // cooperative launch); the right-hand side is already deflated.  x0 = 0; stop at
 // ||r|| <= minres_tol ||b1||.  Afterwards x is re-projected onto the complement.
 sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
+  PhaseRange nvtx_range("minres");
   cudaStream_t s = h->stream;
   const int kp = h->kp;
   const int64_t n1 = h->n1;
@@ -768,6 +780,7 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
 // the Ritz vectors (Z) and the preconditioned residual block (T, see ritz_resid).
 sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, float2* T = nullptr,
                     const float2* diag = nullptr) {
+  PhaseRange nvtx_range("rayleigh_ritz");
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
@@ -803,6 +816,7 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
 // (sum of the passes) in dC1 and R = R2 R1 in the recycle coefficients [C; R]
 // (Eq. HPsip).  dd (host, 2*kp) receives ||src_j||^2 and ||Phi_j||^2.
 sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool cond) {
+  PhaseRange nvtx_range("orth_append");
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
@@ -857,6 +871,7 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
 // Thick restart of the continuation: Q <- Q Y_2k, W <- W Y_2k (two blocks of k
 // Ritz vectors, the 2k lowest), projected matrix recomputed from the new blocks.
 sppc_status restart(sppc_ctx* h) {
+  PhaseRange nvtx_range("restart");
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp, p = h->p;
   const int64_t n = h->n;
@@ -886,6 +901,7 @@ sppc_status restart(sppc_ctx* h) {
 // Rayleigh-Ritz pairs, T = preconditioned residuals, thick restart if the basis
 // is full, orthogonalise T and append it, k SpMVs, Rayleigh-Ritz.
 sppc_status refine_step(sppc_ctx* h) {
+  PhaseRange nvtx_range("refine_step");
   const int kp = h->kp;
   const int64_t n = h->n;
   // T from the current Ritz pairs: written by the previous Rayleigh-Ritz pass when
@@ -925,6 +941,7 @@ bool all_converged(const sppc_ctx* h, double tol) {
 
 // Accessors used by the allocation-free SpMM entry point (noalloc.cu).
 namespace sppc {
+
 const SellDev* handle_matrix(sppc_handle h, int64_t* n) {
   if (n) *n = h->n;
   return &h->H;
@@ -1094,7 +1111,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     SellHost S;
     std::vector<int64_t> seg(h->lev.begin(), h->lev.end());
     int64_t chunk = opt.spmm_chunk_cols;
-    if (chunk == 0) chunk = 655360;  // 40 MB of an 8-column double-float block
+    if (chunk == 0) chunk = 1310720;  // 80 MB of an 8-column double-float block
     if (chunk > 0 && (n + chunk - 1) / chunk > 255) chunk = (n + 254) / 255;
     build_sell(n, rp, ci, va, n, seg, 1024, chunk, S);
     sppc_status st = upload_sell(h, S, h->H, n, h->h_chunk_slice);
@@ -1275,6 +1292,7 @@ sppc_status sppc_start(sppc_handle h, double* theta, double* resid, void* stream
 }
 
 sppc_status sppc_correct(sppc_handle h, void* stream) {
+  PhaseRange nvtx_range("sppc_correct");
   if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
   if (!h->started || h->corrected || h->in_refine)
     return fail(h, SPPC_ERR_STATE, "sppc_correct needs sppc_start / rayleigh_ritz first (and no refinement yet)");

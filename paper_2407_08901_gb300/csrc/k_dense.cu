@@ -13,7 +13,23 @@ namespace sppc {
 
 namespace {
 
-constexpr int kChunk = 2048;  // rows per CTA in the reductions
+constexpr int kChunk = 2048;  // rows per CTA in the reductions over long blocks
+
+// Rows per CTA of a reduction over `rows` rows: about eight CTAs per SM (so
+// that four resident CTAs of 8 warps run two full waves), in multiples of 32
+// rows, between 128 and kChunk.
+inline int64_t chunk_rows(int64_t rows) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int64_t c = (rows + 8 * sms - 1) / (8 * sms);
+  c = (c + 31) / 32 * 32;
+  return c < 128 ? 128 : (c > kChunk ? kChunk : c);
+}
 
 // One warp per output: lane l adds the partials of chunks l, l+32, ... in order,
 // then the 32 lane sums are combined by a fixed butterfly (deterministic).
@@ -30,20 +46,20 @@ __global__ void k_finish(const float2* __restrict__ partials, int64_t nchunks, i
   if (lane == 0) out[o] = (double)t.x + (double)t.y;
 }
 
-// One CTA = 8 warps and kChunk rows.  A warp covers 32/KP rows at a time, lane
+// One CTA = 8 warps and `chunk` rows.  A warp covers 32/KP rows at a time, lane
 // (row u, column i) with i = lane % KP: the A block rows are read contiguously
 // and the lanes of one row share (broadcast) its B row.  Each lane accumulates
 // the KP dots (i, j); lanes with equal i and the 8 warps are then combined.
 template <int KP>
 __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restrict__ B, int64_t r0, int64_t r1,
-                                              float2* __restrict__ partials) {
+                                              int64_t chunk, float2* __restrict__ partials) {
   constexpr int RPW = 32 / KP;   // rows per warp step (KP = 6 leaves 2 lanes idle)
   __shared__ float2 red[8][KP * KP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = lane % KP, u = lane / KP;
   const bool active = u < RPW;
-  const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * kChunk;
-  const int64_t c1 = min(c0 + kChunk, r1);
+  const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t c1 = min(c0 + chunk, r1);
   const int nout = A.n * KP * KP;
   for (int a = 0; a < A.n; ++a) {
     const float2* __restrict__ Aa = A.p[a];
@@ -52,7 +68,36 @@ __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restr
     for (int j = 0; j < KP; ++j) sh[j] = sl[j] = 0.f;
     int cnt = 0;
     if (active) {
-      for (int64_t r = c0 + warp * RPW + u; r < c1; r += 8 * RPW) {
+      // two rows per iteration, loads issued before the multiply-adds
+      int64_t r = c0 + warp * RPW + u;
+      for (; r + 8 * RPW < c1; r += 16 * RPW) {
+        const int64_t r2 = r + 8 * RPW;
+        const float2 av = Aa[r * KP + i];
+        const float2 av2 = Aa[r2 * KP + i];
+        float4 b[KP / 2], b2[KP / 2];
+        const float4* br = reinterpret_cast<const float4*>(B + r * KP);
+        const float4* br2 = reinterpret_cast<const float4*>(B + r2 * KP);
+#pragma unroll
+        for (int q = 0; q < KP / 2; ++q) {
+          b[q] = br[q];
+          b2[q] = br2[q];
+        }
+#pragma unroll
+        for (int q = 0; q < KP / 2; ++q) {
+          acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b[q].x, b[q].y));
+          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b[q].z, b[q].w));
+        }
+#pragma unroll
+        for (int q = 0; q < KP / 2; ++q) {
+          acc_mac(sh[2 * q], sl[2 * q], av2, make_float2(b2[q].x, b2[q].y));
+          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av2, make_float2(b2[q].z, b2[q].w));
+        }
+        if (((++cnt) & 7) == 0) {
+#pragma unroll
+          for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
+        }
+      }
+      if (r < c1) {
         const float2 av = Aa[r * KP + i];
         const float4* br = reinterpret_cast<const float4*>(B + r * KP);
 #pragma unroll
@@ -60,10 +105,6 @@ __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restr
           const float4 b = br[q];
           acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b.x, b.y));
           acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b.z, b.w));
-        }
-        if (((++cnt) & 15) == 0) {
-#pragma unroll
-          for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
         }
       }
     }
@@ -133,6 +174,37 @@ __global__ void __launch_bounds__(256) k_update(float2* Y, const float2* X, cons
   for (int j = 0; j < KP; ++j) Y[r * KP + j] = acc_get(sh[j], sl[j]);
 }
 
+// Short blocks: one thread per element (row r, column j) instead of per row,
+// the same sum in the same order as k_update.
+template <int KP>
+__global__ void __launch_bounds__(256) k_update_el(float2* Y, const float2* X, const float2* __restrict__ alpha,
+                                                   BlockList A, const float2* __restrict__ coef, int64_t r0,
+                                                   int64_t r1) {
+  extern __shared__ float2 scoef[];
+  const int ncoef = A.n * KP * KP;
+  for (int t = threadIdx.x; t < ncoef; t += blockDim.x) scoef[t] = coef[t];
+  __syncthreads();
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t r = r0 + t / KP;
+  const int j = static_cast<int>(t % KP);
+  if (r >= r1) return;
+  float sh = 0.f, sl = 0.f;
+  if (X && alpha) {
+    const float2 x = df_mul(alpha[j], X[r * KP + j]);
+    sh = x.x;
+    sl = x.y;
+  }
+  for (int a = 0; a < A.n; ++a) {
+    const float2* ar = A.p[a] + r * KP;
+    const float2* ca = scoef + a * KP * KP + j;
+#pragma unroll
+    for (int i = 0; i < KP; ++i) acc_mac(sh, sl, ar[i], ca[i * KP]);
+    acc_norm(sh, sl);
+  }
+  __syncwarp();
+  Y[r * KP + j] = acc_get(sh, sl);
+}
+
 template <int KP>
 __global__ void __launch_bounds__(256) k_combine_diag(float2* Y, const float2* X, const float2* __restrict__ alpha,
                                                       BlockList A, const float2* __restrict__ coef, int64_t r0,
@@ -169,11 +241,12 @@ struct Pairs {
 };
 
 template <int KP>
-__global__ void __launch_bounds__(256) k_coldots(Pairs P, int nq, int64_t r0, int64_t r1, float2* partials) {
+__global__ void __launch_bounds__(256) k_coldots(Pairs P, int nq, int64_t r0, int64_t r1, int64_t chunk,
+                                                 float2* partials) {
   __shared__ float2 red[8][4 * 8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * kChunk;
-  const int64_t c1 = min(c0 + kChunk, r1);
+  const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t c1 = min(c0 + chunk, r1);
   float sh[4 * KP], sl[4 * KP];
 #pragma unroll
   for (int t = 0; t < 4 * KP; ++t) sh[t] = sl[t] = 0.f;
@@ -202,11 +275,14 @@ __global__ void __launch_bounds__(256) k_coldots(Pairs P, int nq, int64_t r0, in
   }
 }
 
+// Two threads per row, each owning half of the KP columns (halves the
+// accumulator registers, so twice the warps fit per SM).
 template <int KP>
 __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, const float2* __restrict__ Y,
                                                     const float2* __restrict__ theta, int64_t n, float2* partials,
                                                     double* Zout, int64_t ldz, int ncols, float2* Tout,
                                                     const float2* __restrict__ diag, float clamp) {
+  constexpr int CH = KP / 2;
   extern __shared__ float2 sy[];
   const int ny = Q.n * KP * KP;
   for (int t = threadIdx.x; t < ny; t += blockDim.x) sy[t] = Y[t];
@@ -215,39 +291,45 @@ __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, c
   if (threadIdx.x < KP) sth[threadIdx.x] = theta[threadIdx.x];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float rh[KP], rl[KP];
+  const int half = threadIdx.x & 1;
+  const int j0 = half * CH;
+  float rh[CH], rl[CH];
 #pragma unroll
-  for (int j = 0; j < KP; ++j) rh[j] = rl[j] = 0.f;
+  for (int c = 0; c < CH; ++c) rh[c] = rl[c] = 0.f;
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kChunk;
   const int64_t c1 = min(c0 + kChunk, n);
-  for (int64_t r = c0 + threadIdx.x; r < c1; r += blockDim.x) {
-    float zh[KP], zl[KP], hh[KP], hl[KP];
+  for (int64_t r = c0 + (threadIdx.x >> 1); r < c1; r += blockDim.x >> 1) {
+    float zh[CH], zl[CH], hh[CH], hl[CH];
 #pragma unroll
-    for (int j = 0; j < KP; ++j) zh[j] = zl[j] = hh[j] = hl[j] = 0.f;
+    for (int c = 0; c < CH; ++c) zh[c] = zl[c] = hh[c] = hl[c] = 0.f;
     for (int a = 0; a < Q.n; ++a) {
-      const float2* qa = Q.p[a] + r * KP;
-      const float2* wa = Wb.p[a] + r * KP;
-      const float2* ya = sy + a * KP * KP;
+      const float4* qa = reinterpret_cast<const float4*>(Q.p[a] + r * KP);
+      const float4* wa = reinterpret_cast<const float4*>(Wb.p[a] + r * KP);
+      const float2* ya = sy + a * KP * KP + j0;
 #pragma unroll
-      for (int i = 0; i < KP; ++i) {
-        const float2 qv = qa[i], wv = wa[i];
+      for (int q = 0; q < KP / 2; ++q) {
+        const float4 qv = qa[q], wv = wa[q];
 #pragma unroll
-        for (int j = 0; j < KP; ++j) {
-          acc_mac(zh[j], zl[j], qv, ya[i * KP + j]);
-          acc_mac(hh[j], hl[j], wv, ya[i * KP + j]);
+        for (int c = 0; c < CH; ++c) {
+          const float2 y0 = ya[(2 * q) * KP + c], y1 = ya[(2 * q + 1) * KP + c];
+          acc_mac(zh[c], zl[c], make_float2(qv.x, qv.y), y0);
+          acc_mac(hh[c], hl[c], make_float2(wv.x, wv.y), y0);
+          acc_mac(zh[c], zl[c], make_float2(qv.z, qv.w), y1);
+          acc_mac(hh[c], hl[c], make_float2(wv.z, wv.w), y1);
         }
       }
 #pragma unroll
-      for (int j = 0; j < KP; ++j) {
-        acc_norm(zh[j], zl[j]);
-        acc_norm(hh[j], hl[j]);
+      for (int c = 0; c < CH; ++c) {
+        acc_norm(zh[c], zl[c]);
+        acc_norm(hh[c], hl[c]);
       }
     }
 #pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      const float2 z = acc_get(zh[j], zl[j]);
-      const float2 d = df_sub(acc_get(hh[j], hl[j]), df_mul(sth[j], z));
-      acc_mac(rh[j], rl[j], d, d);
+    for (int c = 0; c < CH; ++c) {
+      const int j = j0 + c;
+      const float2 z = acc_get(zh[c], zl[c]);
+      const float2 d = df_sub(acc_get(hh[c], hl[c]), df_mul(sth[j], z));
+      acc_mac(rh[c], rl[c], d, d);
       if (Zout && j < ncols) Zout[r * ldz + j] = df_to_double(z);
       if (Tout) {
         // preconditioned residual d / (H_rr - theta_j), denominator clamped to |.| >= clamp
@@ -262,9 +344,12 @@ __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, c
     }
   }
 #pragma unroll
-  for (int j = 0; j < KP; ++j) {
-    const float2 v = warp_sum_df(acc_get(rh[j], rl[j]));
-    if (lane == 0) red[warp][j] = v;
+  for (int c = 0; c < CH; ++c) {
+    float2 v = acc_get(rh[c], rl[c]);
+    // sum over the lanes of equal half (butterfly over the row bits)
+#pragma unroll
+    for (int m = 2; m < 32; m <<= 1) v = df_add(v, shfl_xor_df(v, m));
+    if (lane < 2) red[warp][j0 + c] = v;
   }
   __syncthreads();
   if (threadIdx.x < KP) {
@@ -307,14 +392,19 @@ cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_
   if (r1 <= r0 || A.n == 0) {
     return cudaMemsetAsync(out, 0, sizeof(double) * nout, s);
   }
-  const int64_t nchunks = (r1 - r0 + kChunk - 1) / kChunk;
+  int64_t chunk = chunk_rows(r1 - r0);
+  int64_t nchunks = (r1 - r0 + chunk - 1) / chunk;
+  if (nchunks * nout > partial_cap) {  // fall back to the coarse cut if the finer one does not fit
+    chunk = kChunk;
+    nchunks = (r1 - r0 + chunk - 1) / chunk;
+  }
   if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(nchunks);
   switch (kp) {
-    case 2: k_gram<2><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
-    case 4: k_gram<4><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
-    case 6: k_gram<6><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
-    case 8: k_gram<8><<<g, 256, 0, s>>>(A, B, r0, r1, partials); count_launch(); break;
+    case 2: k_gram<2><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); count_launch(); break;
+    case 4: k_gram<4><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); count_launch(); break;
+    case 6: k_gram<6><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); count_launch(); break;
+    case 8: k_gram<8><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
   k_finish<<<nblk((int64_t)nout * 32, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
@@ -325,6 +415,18 @@ cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockL
                    int64_t r0, int64_t r1, cudaStream_t s) {
   if (r1 <= r0) return cudaSuccess;
   const size_t smem = sizeof(float2) * (size_t)(A.n > 0 ? A.n : 1) * kp * kp;
+  if (r1 - r0 < static_cast<int64_t>(kChunk) * 64) {
+    // short blocks (the leading block): one thread per element for parallelism
+    const unsigned ge = nblk((r1 - r0) * kp, 256);
+    switch (kp) {
+      case 2: k_update_el<2><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+      case 4: k_update_el<4><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+      case 6: k_update_el<6><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+      case 8: k_update_el<8><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   const unsigned g = nblk(r1 - r0, 256);
   switch (kp) {
     case 2: k_update<2><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
@@ -360,14 +462,19 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
     P.a[q] = A[q];
     P.b[q] = B[q];
   }
-  const int64_t nchunks = (r1 - r0 + kChunk - 1) / kChunk;
+  int64_t chunk = chunk_rows(r1 - r0);
+  int64_t nchunks = (r1 - r0 + chunk - 1) / chunk;
+  if (nchunks * nout > partial_cap) {
+    chunk = kChunk;
+    nchunks = (r1 - r0 + chunk - 1) / chunk;
+  }
   if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(nchunks);
   switch (kp) {
-    case 2: k_coldots<2><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
-    case 4: k_coldots<4><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
-    case 6: k_coldots<6><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
-    case 8: k_coldots<8><<<g, 256, 0, s>>>(P, nq, r0, r1, partials); count_launch(); break;
+    case 2: k_coldots<2><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); count_launch(); break;
+    case 4: k_coldots<4><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); count_launch(); break;
+    case 6: k_coldots<6><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); count_launch(); break;
+    case 8: k_coldots<8><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
   k_finish<<<nblk((int64_t)nout * 32, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();

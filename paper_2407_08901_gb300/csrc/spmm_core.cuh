@@ -15,14 +15,16 @@ __device__ __forceinline__ uint64_t policy_keep() {
 
 // One lane's half of an X row: CPL double-float values starting at element
 // `off` of row cidx.  A kp = 8 half row is one 256-bit load, so the two lanes of
-// a row touch one 64-byte segment with a single L1 wavefront.
+// a row touch one 64-byte segment with a single L1 wavefront.  The rows are
+// random and rarely reused inside an SM, so they bypass L1 allocation (letting
+// them allocate cost 20-40% of the SpMM time on c2).
 template <int KP>
 __device__ __forceinline__ void gather_half(const float2* __restrict__ X, int cidx, int off, float2 (&x)[KP / 2],
                                             uint64_t pol) {
   const float2* p = X + static_cast<int64_t>(cidx) * KP + off;
   if constexpr (KP == 8) {
     float4 a, b;
-    asm volatile("ld.global.nc.L2::cache_hint.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
                  : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
                  : "l"(p), "l"(pol));
     x[0] = make_float2(a.x, a.y);
@@ -31,22 +33,38 @@ __device__ __forceinline__ void gather_half(const float2* __restrict__ X, int ci
     x[3] = make_float2(b.z, b.w);
   } else if constexpr (KP == 4) {
     float4 a;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
                  : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w)
                  : "l"(p), "l"(pol));
     x[0] = make_float2(a.x, a.y);
     x[1] = make_float2(a.z, a.w);
   } else {
 #pragma unroll
-    for (int j = 0; j < KP / 2; ++j) x[j] = __ldg(p + j);
+    for (int j = 0; j < KP / 2; ++j)
+      asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;"
+                   : "=f"(x[j].x), "=f"(x[j].y)
+                   : "l"(p + j), "l"(pol));
   }
+}
+
+// Streamed matrix entries (read once): no L1 allocation.
+__device__ __forceinline__ int ld_stream(const int32_t* p) {
+  int v;
+  asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
 }
 
 // Row sums of slice s: lane pair (2*r, 2*r+1) owns row r of the slice, lane h
 // of the pair accumulates columns [h*kp/2, (h+1)*kp/2) into (ah, al).  Software
-// pipeline per lane: the column index / value of entry t+2 and the half row of
-// X for entry t+1 are in flight while entry t is multiplied and accumulated.
-// All lanes of a slice run the same number of steps (the slice width).
+// pipeline of depth 2 per lane: the X half rows of entries t+1 and t+2 are in
+// flight while entry t is accumulated; the loop is unrolled by three so the
+// three buffers rotate without register copies.  Entries are accumulated in
+// order and renormalised after every 16th, whatever the unrolling.
 template <int KP>
 __device__ __forceinline__ void slice_rowsum(const SellDev& A, int64_t s, int rl, int off,
                                              const float2* __restrict__ X, uint64_t pol, float (&ah)[KP / 2],
@@ -57,42 +75,35 @@ __device__ __forceinline__ void slice_rowsum(const SellDev& A, int64_t s, int rl
   int64_t e = A.slice_ptr[s] + rl;
 #pragma unroll
   for (int c = 0; c < CPL; ++c) ah[c] = al[c] = 0.f;
-  float2 x0[CPL];
-  float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-  int c1 = 0;
-  if (e < end) {
-    const int c0 = __ldcs(A.col + e);
-    v0 = __ldcs(A.val + e);
-    gather_half<KP>(X, c0, off, x0, pol);
-    if (e + H < end) {
-      c1 = __ldcs(A.col + e + H);
-      v1 = __ldcs(A.val + e + H);
+  float2 x0[CPL], x1[CPL], x2[CPL];
+  float2 v0 = make_float2(0.f, 0.f), v1 = v0, v2 = v0;
+  auto fetch = [&](int64_t ee, float2 (&x)[CPL], float2& v) {
+    if (ee < end) {
+      const int c = ld_stream(A.col + ee);
+      v = ld_stream(A.val + ee);
+      gather_half<KP>(X, c, off, x, pol);
     }
-  }
+  };
   int cnt = 0;
-  for (; e < end; e += H) {
-    float2 x1[CPL];
-    const bool more1 = (e + H < end);
-    if (more1) gather_half<KP>(X, c1, off, x1, pol);
-    int c2 = 0;
-    float2 v2 = make_float2(0.f, 0.f);
-    if (e + 2 * H < end) {
-      c2 = __ldcs(A.col + e + 2 * H);
-      v2 = __ldcs(A.val + e + 2 * H);
-    }
+  auto mac = [&](const float2 (&x)[CPL], float2 v) {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) acc_mac(ah[c], al[c], v0, x0[c]);
+    for (int c = 0; c < CPL; ++c) acc_mac(ah[c], al[c], v, x[c]);
     if (((++cnt) & 15) == 0) {
 #pragma unroll
       for (int c = 0; c < CPL; ++c) acc_norm(ah[c], al[c]);
     }
-    if (more1) {
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) x0[c] = x1[c];
-    }
-    v0 = v1;
-    v1 = v2;
-    c1 = c2;
+  };
+  fetch(e, x0, v0);
+  fetch(e + H, x1, v1);
+  for (; e < end; e += 3 * H) {
+    fetch(e + 2 * H, x2, v2);
+    mac(x0, v0);
+    if (e + H >= end) break;
+    fetch(e + 3 * H, x0, v0);
+    mac(x1, v1);
+    if (e + 2 * H >= end) break;
+    fetch(e + 4 * H, x1, v1);
+    mac(x2, v2);
   }
 }
 

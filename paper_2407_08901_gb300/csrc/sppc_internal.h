@@ -76,7 +76,7 @@ cudaError_t spmm_tma_read_timeout(int* flag, cudaStream_t s);
 cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_t r1, double* out,
                  float2* partials, int64_t partial_cap, cudaStream_t s);
 // Update: Y[r][j] = alpha[j] X[r][j] + sum_a sum_i A_a[r][i] coef[(a*kp+i)*kp + j]
-// (coef double-float on device; X may be null; Y may alias X).
+// (coef double-float on device; X may be null; Y may alias X but no block of A).
 cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef,
                    int kp, int64_t r0, int64_t r1, cudaStream_t s);
 // Diagonal combine: Y[r][j] = alpha[j] X[r][j] + sum_b coef[b*8 + j] A_b[r][j]
