@@ -119,6 +119,28 @@ __device__ void multisect(const T* d, const T* e2, int m, int w, T pivmin, T rel
   hi_io = static_cast<double>(hi);
 }
 
+// Narrow [lo, hi] for index w by 4-section in FP64: three Sturm counts per round
+// (lanes 0-2 of the warp; FP64 throughput, not latency, is the scarce resource).
+// Stops when hi - lo <= rel * max(|lo|,|hi|) + abs_tol.
+__device__ void quadsect64(const double* d, const double* e2, int m, int w, double pivmin, double rel,
+                           double abs_tol, int max_rounds, double& lo_io, double& hi_io) {
+  const int lane = threadIdx.x & 31;
+  double lo = lo_io, hi = hi_io;
+  for (int it = 0; it < max_rounds; ++it) {
+    if (hi - lo <= rel * fmax(fabs(lo), fabs(hi)) + abs_tol) break;
+    const double h = hi - lo;
+    const int c = (lane < 3) ? sturm_count<double>(d, e2, m, lo + h * 0.25 * (double)(lane + 1), pivmin) : m + 1;
+    const unsigned ball = __ballot_sync(0xffffffffu, c > w) & 0x7u;
+    const int f = ball ? __ffs(ball) - 1 : 3;  // first quarter point above index w
+    const double nlo = (f > 0) ? lo + h * 0.25 * (double)f : lo;
+    const double nhi = (f < 3) ? lo + h * 0.25 * (double)(f + 1) : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  lo_io = lo;
+  hi_io = hi;
+}
+
 // sqrt of a double-float: fp32 root s, exact square s*s (TwoProd), one
 // correction step (a - s^2) / (2 s).
 __device__ __forceinline__ float2 df_sqrt(float2 a) {
@@ -149,38 +171,39 @@ __device__ float2 block_sum_df(float2 v, float2* red) {
 
 // Solve (T - sigma I) y = y in place for the tridiagonal (d, e), FP64, with
 // partial pivoting; returns false on an exactly zero pivot set to eps.
-__device__ void tri_shift_solve(const double* d, const double* e, int m, double sigma, double eps_piv, double* y,
-                                double* du, double* u1, double* u2, double* lm, unsigned char* piv) {
-  double a0 = d[0] - sigma, b0 = (m > 1) ? e[0] : 0.0;
+template <typename T>
+__device__ void tri_shift_solve(const T* d, const T* e, int m, T sigma, T eps_piv, T* y, T* du, T* u1, T* u2, T* lm,
+                                unsigned char* piv) {
+  T a0 = d[0] - sigma, b0 = (m > 1) ? e[0] : T(0);
   for (int i = 0; i + 1 < m; ++i) {
-    const double c = e[i];
-    const double a1 = d[i + 1] - sigma;
-    const double b1 = (i + 2 < m) ? e[i + 1] : 0.0;
+    const T c = e[i];
+    const T a1 = d[i + 1] - sigma;
+    const T b1 = (i + 2 < m) ? e[i + 1] : T(0);
     if (fabs(c) > fabs(a0)) {
       piv[i] = 1;
       du[i] = c;
       u1[i] = a1;
       u2[i] = b1;
-      const double l = a0 / c;
+      const T l = a0 / c;
       lm[i] = l;
       a0 = b0 - l * a1;
       b0 = -l * b1;
     } else {
       piv[i] = 0;
-      if (a0 == 0.0) a0 = eps_piv;
+      if (a0 == T(0)) a0 = eps_piv;
       du[i] = a0;
       u1[i] = b0;
-      u2[i] = 0.0;
-      const double l = c / a0;
+      u2[i] = T(0);
+      const T l = c / a0;
       lm[i] = l;
       a0 = a1 - l * b0;
       b0 = b1;
     }
   }
-  du[m - 1] = (a0 == 0.0) ? eps_piv : a0;
+  du[m - 1] = (a0 == T(0)) ? eps_piv : a0;
   for (int i = 0; i + 1 < m; ++i) {
     if (piv[i]) {
-      const double tmp = y[i];
+      const T tmp = y[i];
       y[i] = y[i + 1];
       y[i + 1] = tmp - lm[i] * y[i];
     } else {
@@ -188,19 +211,20 @@ __device__ void tri_shift_solve(const double* d, const double* e, int m, double 
     }
   }
   for (int i = m - 1; i >= 0; --i) {
-    double sv = y[i];
+    T sv = y[i];
     if (i + 1 < m) sv -= u1[i] * y[i + 1];
     if (i + 2 < m) sv -= u2[i] * y[i + 2];
-    double di = du[i];
+    T di = du[i];
     if (fabs(di) < eps_piv) di = (di < 0 ? -eps_piv : eps_piv);
     y[i] = sv / di;
   }
 }
 
-__device__ double rayleigh_tri(const double* d, const double* e, int m, const double* y) {
-  double num = 0.0, den = 0.0;
+template <typename T>
+__device__ T rayleigh_tri(const T* d, const T* e, int m, const T* y) {
+  T num = 0, den = 0;
   for (int i = 0; i < m; ++i) {
-    double ty = d[i] * y[i];
+    T ty = d[i] * y[i];
     if (i > 0) ty += e[i - 1] * y[i - 1];
     if (i + 1 < m) ty += e[i] * y[i + 1];
     num += y[i] * ty;
@@ -214,10 +238,12 @@ __device__ double rayleigh_tri(const double* d, const double* e, int m, const do
 //     double-float, matrix in shared memory with leading dimension m+1.
 //  2. Eigenvalue brackets by Sturm-count multisection in FP32 to ~1e-5; indices
 //     whose brackets crowd a neighbour are narrowed further in FP64.
-//  3. Eigenvectors of the tridiagonal matrix by inverse iteration in FP64 (one
-//     thread per vector), shift updated by the Rayleigh quotient for isolated
-//     eigenvalues; crowded groups are orthogonalised (modified Gram-Schmidt).
-//     The eigenvalue is the final Rayleigh quotient.
+//  3. Eigenvectors of the tridiagonal matrix by inverse iteration, one thread
+//     per vector.  Isolated eigenvalues: three FP32 steps with Rayleigh-quotient
+//     shifts, then one FP64 step shifted by the FP64 Rayleigh quotient of that
+//     vector (the FP64 pipe is ~1/64 of FP32 here, so FP64 is kept to the final
+//     step).  Crowded groups: four FP64 steps from the bracket midpoint, then
+//     modified Gram-Schmidt.  The eigenvalue is the final Rayleigh quotient.
 //  4. Back-transformation through the stored reflectors in double-float.
 __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ S, int lds, int m, int nev,
                                                      double* __restrict__ theta, double* __restrict__ V, int ldv) {
@@ -276,14 +302,22 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
     for (int i = t; i < len; i += nt) vec[i] = (i == 0) ? red[34] : A[(j + 1 + i) * ld + j];
     __syncthreads();
     if (tj.x != 0.f) {
-      for (int i = t; i < len; i += nt) {
-        const float2* row = A + (j + 1 + i) * ld + (j + 1);
+      // p = tau A v: four threads per row (entries sub, sub+4, ...), combined by shuffles
+      for (int i0 = 0; i0 < len; i0 += nt / 4) {
+        const int i = i0 + (t >> 2), sub = t & 3;
         float ph = 0.f, pl = 0.f;
-        for (int l = 0; l < len; ++l) {
-          acc_mac(ph, pl, row[l], vec[l]);
-          if ((l & 15) == 15) acc_norm(ph, pl);
+        if (i < len) {
+          const float2* row = A + (j + 1 + i) * ld + (j + 1);
+          int c = 0;
+          for (int l = sub; l < len; l += 4) {
+            acc_mac(ph, pl, row[l], vec[l]);
+            if (((++c) & 15) == 0) acc_norm(ph, pl);
+          }
         }
-        pw[i] = df_mul(tj, acc_get(ph, pl));
+        float2 pr = acc_get(ph, pl);
+        pr = df_add(pr, shfl_xor_df(pr, 1));
+        pr = df_add(pr, shfl_xor_df(pr, 2));
+        if (i < len && sub == 0) pw[i] = df_mul(tj, pr);
       }
       __syncthreads();
       float kh = 0.f, kl = 0.f;
@@ -292,10 +326,11 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
       const float2 K = df_mul(df_mul(make_float2(0.5f, 0.f), tj), pv);
       for (int i = t; i < len; i += nt) pw[i] = df_sub(pw[i], df_mul(K, vec[i]));  // w
       __syncthreads();
-      for (int x = t; x < len * len; x += nt) {
-        const int i = x / len, l = x % len;
-        float2& a = A[(j + 1 + i) * ld + (j + 1 + l)];
-        a = df_sub(a, df_add(df_mul(vec[i], pw[l]), df_mul(pw[i], vec[l])));
+      // A -= v w^T + w v^T: a warp per row, lanes along the row
+      for (int i = warp; i < len; i += nwarp) {
+        const float2 vi = vec[i], wi = pw[i];
+        float2* arow = A + (j + 1 + i) * ld + (j + 1);
+        for (int l = lane; l < len; l += 32) arow[l] = df_sub(arow[l], df_add(df_mul(vi, pw[l]), df_mul(wi, vec[l])));
       }
     }
     __syncthreads();
@@ -357,30 +392,63 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
   __syncthreads();
   for (int w = warp; w < nev; w += nwarp) {
     if (!crowd[w]) continue;
-    double l0 = gl, h0 = gu;
-    multisect<double>(d, e2, m, w, 1e-280, 2.2e-16, 1e-300, 40, l0, h0);
+    // start from the FP32 bracket widened well past the FP32 Sturm error
+    // (about m * 2^-24 * ||T||); if the FP64 counts disagree, from the whole interval
+    double l0 = lo[w] - 4e-5 * tnorm, h0 = hi[w] + 4e-5 * tnorm;
+    int c = 0;
+    if (lane == 0) c = sturm_count<double>(d, e2, m, l0, 1e-280);
+    if (lane == 1) c = sturm_count<double>(d, e2, m, h0, 1e-280);
+    const int cl = __shfl_sync(0xffffffffu, c, 0), ch = __shfl_sync(0xffffffffu, c, 1);
+    if (!(cl <= w && ch > w)) {
+      l0 = gl;
+      h0 = gu;
+    }
+    quadsect64(d, e2, m, w, 1e-280, 1e-13, 1e-15 * tnorm, 80, l0, h0);
     if (lane == 0) {
       lo[w] = l0;
       hi[w] = h0;
     }
   }
   __syncthreads();
-  // ---- 3. inverse iteration on T (FP64), thread c for vector c
+  // ---- 3. inverse iteration on T, thread c for vector c
   if (t < nev) {
     double* y = Y + t * m;
     double du[kMaxM], u1[kMaxM], u2[kMaxM], lm[kMaxM];
     unsigned char piv[kMaxM];
     const double eps_piv = 2.2e-16 * tnorm;
-    double sigma = 0.5 * (lo[t] + hi[t]);
-    for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.1 * (double)((i * 7 + t * 3) % 11);
-    for (int it = 0; it < 4; ++it) {
-      tri_shift_solve(d, e, m, sigma, eps_piv, y, du, u1, u2, lm, piv);
+    if (!crowd[t]) {
+      float yf[kMaxM], duf[kMaxM], u1f[kMaxM], u2f[kMaxM], lmf[kMaxM], ef[kMaxM];
+      for (int i = 0; i < m; ++i) {
+        yf[i] = 1.f + 0.1f * (float)((i * 7 + t * 3) % 11);
+        ef[i] = (i + 1 < m) ? static_cast<float>(e[i]) : 0.f;
+      }
+      const float epsf = static_cast<float>(1.2e-7 * tnorm);
+      float sf = static_cast<float>(0.5 * (lo[t] + hi[t]));
+      for (int it = 0; it < 3; ++it) {
+        tri_shift_solve<float>(d32, ef, m, sf, epsf, yf, duf, u1f, u2f, lmf, piv);
+        float nrm = 0.f;
+        for (int i = 0; i < m; ++i) nrm = fmaxf(nrm, fabsf(yf[i]));
+        for (int i = 0; i < m; ++i) yf[i] /= nrm;
+        if (it >= 1) {
+          const float rq = rayleigh_tri<float>(d32, ef, m, yf);
+          if (rq >= lo[t] - 1e-6 * tnorm && rq <= hi[t] + 1e-6 * tnorm) sf = rq;
+        }
+      }
+      for (int i = 0; i < m; ++i) y[i] = static_cast<double>(yf[i]);
+      double sigma = rayleigh_tri<double>(d, e, m, y);
+      if (!(sigma >= lo[t] - 1e-6 * tnorm && sigma <= hi[t] + 1e-6 * tnorm)) sigma = 0.5 * (lo[t] + hi[t]);
+      tri_shift_solve<double>(d, e, m, sigma, eps_piv, y, du, u1, u2, lm, piv);
       double nrm = 0.0;
       for (int i = 0; i < m; ++i) nrm = fmax(nrm, fabs(y[i]));
       for (int i = 0; i < m; ++i) y[i] /= nrm;
-      if (!crowd[t] && it >= 1) {
-        const double rq = rayleigh_tri(d, e, m, y);
-        if (rq >= lo[t] - 1e-6 * tnorm && rq <= hi[t] + 1e-6 * tnorm) sigma = rq;
+    } else {
+      double sigma = 0.5 * (lo[t] + hi[t]);
+      for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.1 * (double)((i * 7 + t * 3) % 11);
+      for (int it = 0; it < 4; ++it) {
+        tri_shift_solve<double>(d, e, m, sigma, eps_piv, y, du, u1, u2, lm, piv);
+        double nrm = 0.0;
+        for (int i = 0; i < m; ++i) nrm = fmax(nrm, fabs(y[i]));
+        for (int i = 0; i < m; ++i) y[i] /= nrm;
       }
     }
   }
@@ -410,7 +478,7 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
     for (int i = 0; i < m; ++i) nrm += y[i] * y[i];
     nrm = 1.0 / sqrt(nrm);
     for (int i = 0; i < m; ++i) y[i] *= nrm;
-    ev[t] = rayleigh_tri(d, e, m, y);
+    ev[t] = rayleigh_tri<double>(d, e, m, y);
     for (int i = 0; i < m; ++i) Yd[t * m + i] = df_from_double(y[i]);
   }
   __syncthreads();

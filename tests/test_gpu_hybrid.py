@@ -43,18 +43,22 @@ def test_hybrid_matches_oracle(name, switch, pmax, precond):
         assert abs(st["refine_steps"] - steps_ref) <= 3 + steps_ref // 10, (st["refine_steps"], steps_ref)
         # Every common step: eigenvalues to 1e-10 and residuals (while above 1e-6)
         # to 1e-2, or to 100x the oracle's own spread under 1e-15 noise where that
-        # is larger (double-float rounding is ~2^-48 per operation).
+        # is larger (double-float rounding is ~2^-48 per operation).  The spread
+        # is the running maximum over the steps so far (sensitivity only grows
+        # along the trajectory; one noisy run samples it unevenly).
         common = min(len(rec), len(rec_p), switch + 1 + st["refine_steps"])
+        run_t = run_r = 0.0
         for i, r in enumerate(rec[:common]):
             info = S.sppc_order_info(h, i, w.k)
-            spread_t = np.abs(rec_p[i].theta - r.theta) / np.abs(r.theta)
-            assert np.all(np.abs(info["theta"] - r.theta) <= np.maximum(1e-10, 100 * spread_t) * np.abs(r.theta)), \
-                (i, info["theta"] - r.theta)
+            run_t = max(run_t, float(np.max(np.abs(rec_p[i].theta - r.theta) / np.abs(r.theta))))
             big = r.resid > 1e-6
-            spread_r = np.abs(rec_p[i].resid - r.resid) / r.resid
-            lim = np.maximum(1e-2, 100 * spread_r)
-            assert np.all(np.abs(info["resid"][big] - r.resid[big]) <= lim[big] * r.resid[big]), \
-                (i, info["resid"], r.resid)
+            if big.any():
+                run_r = max(run_r, float(np.max(np.abs(rec_p[i].resid[big] - r.resid[big]) / r.resid[big])))
+            assert np.all(np.abs(info["theta"] - r.theta) <= max(1e-10, 100 * run_t) * np.abs(r.theta)), \
+                (i, info["theta"] - r.theta)
+            lim = max(1e-2, 100 * run_r)
+            assert np.all(np.abs(info["resid"][big] - r.resid[big]) <= lim * r.resid[big]), \
+                (i, info["resid"], r.resid, lim)
         # converged values: equal to the oracle's up to the Kato-Temple error of a
         # 1e-6..1e-9 residual (the two may stop a step apart)
         assert np.allclose(th, ref_th, rtol=1e-8, atol=0)
