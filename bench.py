@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default="none", choices=["none", "spmm", "solve"],
+                    help="run the workload's SpMM twice (spmm) or one solve with the bench options (solve) and "
+                         "exit, for profilers; prints no JSON line")
     return ap.parse_args()
 
 
@@ -285,7 +288,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"kernel": "k_spmm_sell<8>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes": alg, "avg_launch_ms": avg_ms, "launches": spmm_n},
+                     "algorithmic_bytes": alg, "avg_launch_ms": avg_ms, "launches": spmm_n,
+                     "launch_unit": "one 8-column product H X (all column tiles)"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "breakdown_ms_per_step": {kk: float(np.mean([s[kk] for s in stats]))
@@ -305,10 +309,43 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    """Fixed, short invocations of the library for profilers (ncu launch lists and
+    counter captures): two 8-column SpMM products with H, or one whole solve with
+    the options the timed steps use."""
+    import torch
+
+    import paper_2407_08901_gb300 as S
+    import workloads as W
+
+    w = W.config(args.workload)
+    rp, c, v = W.generate(w)
+    k = w.k
+    if args.profile == "spmm":
+        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=1))
+        X = torch.from_numpy(W.random_block(w.n, 8, 1)).cuda()
+        Y = torch.empty_like(X)
+        for _ in range(2):
+            S.sppc_spmm(h, X, Y)
+        torch.cuda.synchronize()
+        print(f"profile spmm: {w.name}, 2 products, column tiles {S.sppc_get_layout(h)['n_chunks']}", flush=True)
+    else:
+        opts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL)
+        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts)
+        conv, th, rs, st = S.sppc_solve(h, k, tol=TOL)
+        torch.cuda.synchronize()
+        print(f"profile solve: {w.name}, converged {conv}, orders {st['orders']}, steps {st['refine_steps']}, "
+              f"launches {S.sppc_kernel_launches()}", flush=True)
+    S.sppc_destroy(h)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile != "none":
+        return run_profile(args)
     return run_ours(args)
 
 

@@ -124,6 +124,8 @@ def config(name: str) -> Workload:
     c3: n = 20,000,000 in 9 levels x2.2, ~250 nnz/row, k = 8 (mixed precision).
     c5train: n = 50,000 in 7 levels x2.2 (training matrices for the learned proposal).
     small: n = 3,000 in 4 levels, for quick tests.
+    c2lite: c2's levels at ~60 nnz/row (1.2e8 entries, 1.45 GB): larger than L2
+        but small enough for multi-pass profiler captures.
     """
     if name == "c1":
         return Workload("c1", [2000, 3000, 4000, 5000, 6000], 50, 5, seed=0, orders=2)
@@ -135,6 +137,8 @@ def config(name: str) -> Workload:
         return Workload("c5train", level_sizes_geometric(50_000, 7, 2.2), 200, 8, seed=1)
     if name == "small":
         return Workload("small", [300, 500, 900, 1300], 40, 4, seed=7)
+    if name == "c2lite":
+        return Workload("c2lite", level_sizes_geometric(2_000_000, 7, 2.2), 60, 8, seed=0)
     if name == "c2mini":
         # c2's law at 1/40 of the size (oracle-friendly, spans many tiles)
         return Workload("c2mini", level_sizes_geometric(50_000, 7, 2.2), 200, 8, seed=3)
