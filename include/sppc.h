@@ -83,7 +83,10 @@ typedef struct {
                               combined with a second eigensolver started from its approximations) */
   int32_t switch_order;    /* SPPC orders before the continuation (default 15, Sec. 6) */
   int32_t hybrid_maxit;    /* continuation steps, k SpMVs each (default 1000) */
-  int32_t precond;         /* 1: residual_j / (diag(H) - theta_j) (default); 0: none (block Krylov) */
+  int32_t precond;         /* 1: residual_j / (diag(H) - theta_j) (default); 0: none (block Krylov);
+                              2: as 1, then the leading n1 rows replaced by precond_iters MINRES steps on
+                              P (H0_hat - theta_j) P t = P r_j[:n1], P deflating the Ritz vector's leading
+                              part (shifted block-diagonal preconditioner, Sec. 5) */
   double precond_clamp;    /* denominators of the preconditioner clamped to |.| >= this (1e-2) */
   int32_t hybrid_blocks;   /* continuation basis limit in blocks of k vectors before a thick restart
                               to 2k Ritz vectors (default 0 = p_max + 1; at least 3) */
@@ -93,6 +96,7 @@ typedef struct {
   int32_t reorth;          /* continuation's block Gram-Schmidt: 0 = second projection only when the
                               first kept less than half of some column's norm (default), 1 = always
                               twice (SPPC orders always project twice, Eq. blkGS) */
+  int32_t precond_iters;   /* MINRES steps of the leading-block preconditioner (precond 2; default 20) */
 } sppc_opts;
 
 typedef struct {
@@ -190,7 +194,8 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
 
 /* One continuation step (after at least one Rayleigh-Ritz step): extend the basis
  * by the k Ritz residuals of the current pairs, divided by diag(H) - theta_j when
- * opts.precond (block Davidson; block Krylov otherwise), orthogonalised against
+ * opts.precond (block Davidson; block Krylov otherwise; with precond 2 the leading
+ * rows come from the deflated leading-block solve), orthogonalised against
  * the basis (Eq. blkGS twice, CholeskyQR2); k SpMVs; Rayleigh-Ritz.  When the
  * basis holds opts.hybrid_blocks blocks it first restarts from the 2k lowest
  * Ritz vectors.

@@ -17,6 +17,14 @@ Step by step, from Q (orthonormal, n x m), W = H Q, Ht = Q^T W:
     rho_j = ||R_j|| / |theta_j| (Eq. rrn); stop when every rho_j <= tol.
  2. T_j = R_j / (diag(H) - theta_j) elementwise, each denominator clamped to
     magnitude >= clamp (Jacobi preconditioner), or T = R without preconditioner.
+    With precond="lead" the leading n1 rows of T_j are then replaced by an
+    approximate solve with the leading block: z_hat = Z_j[:n1] / ||Z_j[:n1]||,
+    P = I - z_hat z_hat^T, and `lead_iters` MINRES steps (x0 = 0, no stopping
+    test) on P (H0_hat - theta_j) P t = P R_j[:n1], then t <- P t.  This is this
+    repository's reading of the paper's shifted block-diagonal preconditioner:
+    the exact leading block, shifted by the Ritz value and deflated by the Ritz
+    vector (the projection of Jacobi-Davidson, Sleijpen and van der Vorst 1996),
+    and the shifted diagonal on the other levels.
  3. Restart if m + k > max_blocks * k: Q <- Q Y_2k, W <- W Y_2k, Ht <- Q^T W.
  4. Phi = (I - Q Q^T) T; a second application when the first left some
     column with less than half of its norm (the reorthogonalisation criterion of
@@ -30,6 +38,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from .minres import minres
 from .spmm import csr_spmm
 from .sppc import sppc
 
@@ -44,6 +53,28 @@ class HybridRecord:
     m: int              # basis size after the step
 
 
+def _leading_block(row_ptr, col, val, n1: int):
+    """H0_hat = H[:n1, :n1] as a scipy CSR matrix (the oracle's own copy)."""
+    import scipy.sparse as sp
+    H = sp.csr_matrix((val, col, row_ptr), shape=(row_ptr.shape[0] - 1,) * 2)
+    return H[:n1, :n1].tocsr()
+
+
+def lead_block_correction(H11, z_lead: np.ndarray, r_lead: np.ndarray, theta: float, iters: int) -> np.ndarray:
+    """`iters` MINRES steps (x0 = 0, no stopping test) on P (H11 - theta) P t =
+    P r with P = I - z z^T, z = z_lead / ||z_lead||; returns P t."""
+    nz = float(np.linalg.norm(z_lead))
+    z = z_lead / nz if nz > 0.0 else np.zeros_like(z_lead)
+    b = r_lead - z * (z @ r_lead)
+
+    def op(x):
+        y = H11 @ x - theta * x
+        return y - z * (z @ y)
+
+    t, _, _ = minres(op, b, tol=0.0, maxit=iters)
+    return t - z * (z @ t)
+
+
 def _ritz(Q, W, k, nev):
     Ht = Q.T @ W
     Ht = 0.5 * (Ht + Ht.T)
@@ -54,7 +85,7 @@ def _ritz(Q, W, k, nev):
 def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, tol: float = 1e-6,
                 max_blocks: int = 16, maxit: int = 500, precond: str = "jacobi", clamp: float = 1e-2,
                 solver: str = "pinv", minres_tol: float = 1e-12, reorth: str = "cond",
-                perturb: float = 0.0, perturb_seed: int = 0):
+                perturb: float = 0.0, perturb_seed: int = 0, lead_iters: int = 20):
     """Run SPPC (Algorithm 2) for up to `switch_order` orders (stopping early if
     every scaled residual is below tol), then the block continuation above.
     Returns (theta, resid, converged, records).
@@ -71,6 +102,7 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
         return r.theta, r.resid, True, records
     Q, W = r.Q, r.W
     rng = np.random.Generator(np.random.PCG64(perturb_seed))
+    H11 = _leading_block(row_ptr, col, val, n1) if precond == "lead" else None
     diag = np.zeros(n)
     rows = np.repeat(np.arange(n), np.diff(row_ptr))
     on = rows == col
@@ -87,6 +119,13 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
             small = np.abs(den) < clamp
             den[small] = np.where(den[small] >= 0, clamp, -clamp)
             T = R / den
+        elif precond == "lead":
+            den = diag[:, None] - th[None, :]
+            small = np.abs(den) < clamp
+            den[small] = np.where(den[small] >= 0, clamp, -clamp)
+            T = R / den
+            for j in range(k):
+                T[:n1, j] = lead_block_correction(H11, Z[:n1, j], R[:n1, j], th[j], lead_iters)
         else:
             T = R.copy()
         if perturb > 0.0:

@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("timing", ctypes.c_int32), ("spmm_chunk_cols", ctypes.c_int64),
                 ("hybrid", ctypes.c_int32), ("switch_order", ctypes.c_int32), ("hybrid_maxit", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precond_clamp", ctypes.c_double), ("hybrid_blocks", ctypes.c_int32),
-                ("spmm_kernel", ctypes.c_int32), ("reorth", ctypes.c_int32)]
+                ("spmm_kernel", ctypes.c_int32), ("reorth", ctypes.c_int32), ("precond_iters", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

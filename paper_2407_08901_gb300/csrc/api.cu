@@ -57,7 +57,9 @@ enum CoefSlot : int {
   kMinV = 776,       // 8: 1/beta'
   kCheb = 784,       // 3 x 16: alpha, beta, gamma of the Chebyshev filter
   kTheta = 832,      // 16
-  kCoefEnd = 848
+  kLeadScale = 848,  // 8: 1 / ||z_j[:n1]||
+  kLeadNegE = 856,   // 8: -theta_j (shift of the leading-block solve)
+  kCoefEnd = 864
 };
 
 }  // namespace
@@ -84,6 +86,7 @@ struct sppc_ctx {
   float2 *Q = nullptr, *W = nullptr, *Psi = nullptr, *HPsi = nullptr, *T1 = nullptr, *T2 = nullptr;
   // small-space vectors (n1 x kp)
   float2 *psi_hat = nullptr, *vps = nullptr, *b1 = nullptr;
+  float2 *zlead = nullptr, *rlead = nullptr;  // leading rows of the Ritz vectors / residuals (precond 2)
   float2 *mv = nullptr, *mvprev = nullptr, *mp = nullptr, *my = nullptr, *mw1 = nullptr, *mw2 = nullptr,
          *mx = nullptr;
   // small eigensolve (n1 x 8 blocks, up to 2 per set; 3 filter sets + X + AX + tmp)
@@ -203,6 +206,16 @@ __global__ void k_rhs_coefs(const double* dE, int p, int k, int kp, float2* c) {
     c[kRhsSmall + l * 8 + j] = (j < k) ? df_from_double(el) : make_float2(0.f, 0.f);
   }
   c[kRhsSmall + j] = (j < k) ? df_from_double(dE[p * kp + j]) : make_float2(0.f, 0.f);
+}
+
+__global__ void k_inv_norm_coef(const double* d, int k, int kp, float2* out) {
+  const int j = threadIdx.x;
+  if (j < kp) out[j] = (j < k && d[j] > 0.0) ? df_from_double(1.0 / sqrt(d[j])) : make_float2(0.f, 0.f);
+}
+
+__global__ void k_neg_coef(const float2* in, int k, int kp, float2* out) {
+  const int j = threadIdx.x;
+  if (j < kp) out[j] = (j < k) ? df_neg(in[j]) : make_float2(0.f, 0.f);
 }
 
 __global__ void k_neg_dots_to_coef(const double* d, int k, int kp, float2* out) {
@@ -793,9 +806,11 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
   CK(syev_lowest(h->dHt, h->mmax, m, nev, h->dTheta, h->dV, nev, s));
   k_expand_y<<<1, 256, 0, s>>>(h->dV, nev, p, k, kp, h->dTheta, h->dY, h->dCoef + kTheta); count_launch();
   CK(cudaGetLastError());
+  const bool lead = T != nullptr && h->opt.precond == 2;
   CK(ritz_resid(blocks(h->Q, n, kp, 0, p + 1), blocks(h->W, n, kp, 0, p + 1), h->dY, h->dCoef + kTheta, kp, n,
                 h->dDots, h->partials, h->partial_cap, want_z ? Z : nullptr, ldz, k, T, diag,
-                (float)h->opt.precond_clamp, s));
+                (float)h->opt.precond_clamp, s, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
+                lead ? h->n1 : 0));
   std::vector<double> th(k), r2(kp);
   CK(cudaMemcpyAsync(th.data(), h->dTheta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(r2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
@@ -896,6 +911,75 @@ sppc_status restart(sppc_ctx* h) {
   return SPPC_OK;
 }
 
+// Leading-block preconditioner of the continuation (opts.precond = 2): replace the
+// leading n1 rows of T by precond_iters MINRES steps (x0 = 0, no stopping test) on
+// P (H0_hat - theta_j) P t = P r_j[:n1] with P = I - z z^T, z = z_j[:n1] / ||z_j[:n1]||,
+// then t <- P t.  The Ritz vectors' and residuals' leading rows come from the pass
+// that produced T (zlead, rlead).  The shifted exact leading block, deflated by the
+// Ritz vector, with the shifted diagonal elsewhere: this repository's reading of
+// the shifted block-diagonal preconditioner the paper pairs with LOBPCG (Sec. 5).
+sppc_status lead_correction(sppc_ctx* h, float2* T) {
+  cudaStream_t s = h->stream;
+  const int k = h->k, kp = h->kp;
+  const int64_t n1 = h->n1;
+  float2* c = h->dCoef;
+  const int iters = h->opt.precond_iters;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (h->opt.timing) {
+    t0 = next_event(h);
+    t1 = next_event(h);
+    CK(cudaEventRecord(t0, s));
+  }
+  {  // z <- z / ||z|| (columnwise)
+    const float2* A[1] = {h->zlead};
+    const float2* B[1] = {h->zlead};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    k_inv_norm_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kLeadScale); count_launch();
+    CK(cudaGetLastError());
+    CK(combine_diag(h->zlead, nullptr, nullptr, one(h->zlead), c + kLeadScale, kp, 0, n1, s));
+  }
+  {  // b = r - z (z^T r)
+    const float2* A[1] = {h->zlead};
+    const float2* B[1] = {h->rlead};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl); count_launch();
+    CK(cudaGetLastError());
+    CK(combine_diag(h->b1, h->rlead, c + kOnes, one(h->zlead), c + kDefl, kp, 0, n1, s));
+  }
+  k_neg_coef<<<1, 32, 0, s>>>(c + kTheta, k, kp, c + kLeadNegE); count_launch();
+  CK(cudaGetLastError());
+  int* dstat = h->dStatus + 32;
+  if (iters > 0) {
+    CK(minres_persistent(h->H11c, k, kp, c + kLeadNegE, h->zlead, h->b1, h->mv, h->mvprev, h->my, h->mw1, h->mw2,
+                         h->mx, 0.0, iters, h->partials, h->partial_cap, h->dBar, dstat, s));
+    // x <- x - z (z^T x)
+    const float2* A[1] = {h->zlead};
+    const float2* B[1] = {h->mx};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl); count_launch();
+    CK(cudaGetLastError());
+    CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->zlead), c + kDefl, kp, 0, n1, s));
+    CK(cudaMemcpyAsync(T, h->mx, sizeof(float2) * n1 * kp, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(fill_zero(T, n1 * kp, s));
+  }
+  int st[10] = {0};
+  if (iters > 0) CK(cudaMemcpyAsync(st, dstat, sizeof(int) * 10, cudaMemcpyDeviceToHost, s));
+  if (h->opt.timing) CK(cudaEventRecord(t1, s));
+  CK(cudaStreamSynchronize(s));
+  if (st[0]) return fail(h, SPPC_ERR_TIMEOUT, "leading-block MINRES: a grid barrier timed out");
+  int mx = 0;
+  for (int j = 0; j < k; ++j) mx = std::max(mx, st[2 + j]);
+  h->stats.minres_iters += mx;
+  h->stats.spmv_h11 += (int64_t)k * std::abs(st[1]);
+  if (h->opt.timing) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, t0, t1));
+    h->stats.minres_ms += ms;
+  }
+  return SPPC_OK;
+}
+
 // One step of the continuation after SPPC (block Davidson, Jacobi-preconditioned
 // residuals; without preconditioner the block Krylov extension): from the last
 // Rayleigh-Ritz pairs, T = preconditioned residuals, thick restart if the basis
@@ -907,11 +991,14 @@ sppc_status refine_step(sppc_ctx* h) {
   // T from the current Ritz pairs: written by the previous Rayleigh-Ritz pass when
   // it already ran in continuation mode, else one extra pass over Q and W
   if (!h->t_ready) {
+    const bool lead = h->opt.precond == 2;
     CK(ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
                   n, h->dDots, h->partials, h->partial_cap, nullptr, 0, 0, h->HPsi,
-                  h->opt.precond ? h->dDiag : nullptr, (float)h->opt.precond_clamp, h->stream));
+                  h->opt.precond ? h->dDiag : nullptr, (float)h->opt.precond_clamp, h->stream,
+                  lead ? h->zlead : nullptr, lead ? h->rlead : nullptr, lead ? h->n1 : 0));
   }
   h->t_ready = false;
+  if (h->opt.precond == 2) CKS(lead_correction(h, h->HPsi));
   if (h->p + 1 >= std::min(h->pmax + 1, h->opt.hybrid_blocks)) CKS(restart(h));
   std::vector<double> dd(2 * kp);
   CKS(orth_append(h, h->HPsi, h->p + 1, dd.data(), h->opt.reorth == 0));
@@ -971,6 +1058,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->hybrid_maxit = 1000;
   o->precond = 1;
   o->precond_clamp = 1e-2;
+  o->precond_iters = 20;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1016,6 +1104,9 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "p_max out of range (k*(p_max+1) must be <= 144)");
   if (opt.spmm_kernel != 0 && opt.spmm_kernel != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.spmm_kernel must be 0 or 1");
   if (opt.reorth != 0 && opt.reorth != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.reorth must be 0 or 1");
+  if (opt.precond < 0 || opt.precond > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precond must be 0, 1 or 2");
+  if (opt.precond_iters < 0 || opt.precond_iters > 10000)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.precond_iters must be in [0, 10000]");
 
   h = new sppc_ctx();
   if (opt.hybrid_blocks <= 0 || opt.hybrid_blocks > opt.p_max + 1) opt.hybrid_blocks = opt.p_max + 1;
@@ -1183,6 +1274,10 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     A(&h->dRinv, 256);
     A(&h->dRecycle, (size_t)kMaxBlocks * 64);
     A(&h->dY, (size_t)kMaxBlocks * 64);
+    if (h->opt.precond == 2) {
+      A(&h->zlead, (size_t)h->n1 * kp);
+      A(&h->rlead, (size_t)h->n1 * kp);
+    }
     A(&h->dCoefBig, (size_t)kMaxBlocks * 64);
     if (e == cudaSuccess) e = dalloc(h, &h->dStatus, 64);
     if (e == cudaSuccess) e = dalloc(h, &h->dBar, 4);

@@ -281,7 +281,8 @@ template <int KP>
 __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, const float2* __restrict__ Y,
                                                     const float2* __restrict__ theta, int64_t n, float2* partials,
                                                     double* Zout, int64_t ldz, int ncols, float2* Tout,
-                                                    const float2* __restrict__ diag, float clamp) {
+                                                    const float2* __restrict__ diag, float clamp, float2* Zlead,
+                                                    float2* Rlead, int64_t nlead) {
   constexpr int CH = KP / 2;
   extern __shared__ float2 sy[];
   const int ny = Q.n * KP * KP;
@@ -331,6 +332,10 @@ __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, c
       const float2 d = df_sub(acc_get(hh[c], hl[c]), df_mul(sth[j], z));
       acc_mac(rh[c], rl[c], d, d);
       if (Zout && j < ncols) Zout[r * ldz + j] = df_to_double(z);
+      if (Zlead && r < nlead) {
+        Zlead[r * KP + j] = z;
+        Rlead[r * KP + j] = d;
+      }
       if (Tout) {
         // preconditioned residual d / (H_rr - theta_j), denominator clamped to |.| >= clamp
         float2 t = d;
@@ -483,16 +488,17 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
 
 cudaError_t ritz_resid(const BlockList& Q, const BlockList& Wb, const float2* Y, const float2* theta, int kp,
                        int64_t n, double* out, float2* partials, int64_t partial_cap, double* Zout, int64_t ldz,
-                       int ncols, float2* Tout, const float2* diag, float clamp, cudaStream_t s) {
+                       int ncols, float2* Tout, const float2* diag, float clamp, cudaStream_t s, float2* Zlead,
+                       float2* Rlead, int64_t nlead) {
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   if (nchunks * kp > partial_cap) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float2) * (size_t)Q.n * kp * kp;
   const unsigned g = static_cast<unsigned>(nchunks);
   switch (kp) {
-    case 2: k_ritz_resid<2><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
-    case 4: k_ritz_resid<4><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
-    case 6: k_ritz_resid<6><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
-    case 8: k_ritz_resid<8><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp); count_launch(); break;
+    case 2: k_ritz_resid<2><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead, Rlead, nlead); count_launch(); break;
+    case 4: k_ritz_resid<4><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead, Rlead, nlead); count_launch(); break;
+    case 6: k_ritz_resid<6><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead, Rlead, nlead); count_launch(); break;
+    case 8: k_ritz_resid<8><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead, Rlead, nlead); count_launch(); break;
     default: return cudaErrorInvalidValue;
   }
   k_finish<<<nblk((int64_t)kp * 32, 256), 256, 0, s>>>(partials, nchunks, kp, out); count_launch();

@@ -90,10 +90,13 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
 // double-float), accumulate (hz - theta*z)^2 per column -> out[j] (FP64); optionally
 // write z (FP64, leading dim ldz, first ncols columns) to Zout; optionally write
 // the residual hz - theta z (double-float, n x kp) to Tout, divided elementwise by
-// diag[r] - theta_j (magnitude clamped to >= clamp) when diag is given.
+// diag[r] - theta_j (magnitude clamped to >= clamp) when diag is given;
+// optionally write z and the undivided residual of rows < nlead (double-float,
+// nlead x kp) to Zlead and Rlead.
 cudaError_t ritz_resid(const BlockList& Q, const BlockList& Wb, const float2* Y, const float2* theta, int kp,
                        int64_t n, double* out, float2* partials, int64_t partial_cap, double* Zout, int64_t ldz,
-                       int ncols, float2* Tout, const float2* diag, float clamp, cudaStream_t s);
+                       int ncols, float2* Tout, const float2* diag, float clamp, cudaStream_t s,
+                       float2* Zlead = nullptr, float2* Rlead = nullptr, int64_t nlead = 0);
 cudaError_t f64_to_df(const double* X, int64_t ldx, int ncols, float2* Y, int kp, int64_t r0, int64_t r1,
                       cudaStream_t s);
 cudaError_t df_to_f64(const float2* X, int kp, double* Y, int64_t ldy, int ncols, int64_t r0, int64_t r1,

@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("name,switch,pmax,precond", [("small", 3, 5, 1), ("small", 0, 4, 0), ("c1", 2, 6, 1)])
+@pytest.mark.parametrize("name,switch,pmax,precond", [("small", 3, 5, 1), ("small", 0, 4, 0), ("c1", 2, 6, 1),
+                                                     ("small", 3, 5, 2), ("c1", 2, 6, 2)])
 def test_hybrid_matches_oracle(name, switch, pmax, precond):
     import paper_2407_08901_gb300 as S
     w, rp, c, v = make_matrix(name)
@@ -28,8 +29,8 @@ def test_hybrid_matches_oracle(name, switch, pmax, precond):
     h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, opts)
     try:
         conv, th, rs, st = S.sppc_solve(h, w.k, tol=tol)
-        kw = dict(switch_order=switch, tol=tol, max_blocks=pmax + 1, precond="jacobi" if precond else "none",
-                  maxit=400, reorth="cond" if reorth == 0 else "twice")
+        kw = dict(switch_order=switch, tol=tol, max_blocks=pmax + 1, precond=["none", "jacobi", "lead"][precond],
+                  maxit=400, reorth="cond" if reorth == 0 else "twice", lead_iters=20)
         ref_th, ref_rs, ref_conv, rec = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, **kw)
         # the same run with 1e-15 relative noise on every expansion block: how far
         # rounding-sized differences carry at each step (the block Krylov case with

@@ -73,3 +73,37 @@ def test_perturbation_hook_is_rounding_sized_early():
     assert all(np.array_equal(x.theta, y.theta) for x, y in zip(a, z))
     diff = max(np.max(np.abs(x.theta - y.theta) / np.abs(x.theta)) for x, y in zip(a, b))
     assert 0 < diff < 1e-12
+
+
+def test_lead_block_correction_solves_the_deflated_system():
+    """With as many MINRES steps as unknowns the leading-block correction is the
+    minimum-norm solution of P (H11 - theta) P t = P r (P = I - z z^T), which a
+    dense least-squares solve gives independently; it is always orthogonal to z,
+    and zero steps give zero."""
+    from oracle.hybrid import lead_block_correction, _leading_block
+    w, rp, c, v = make_matrix(TINY)
+    n1 = w.small_dim
+    H11 = _leading_block(rp, c, v, n1)
+    A = H11.toarray()
+    rng = np.random.Generator(np.random.PCG64(3))
+    z = rng.standard_normal(n1)
+    r = rng.standard_normal(n1)
+    theta = float(np.linalg.eigvalsh(A)[1]) + 0.37
+    t = lead_block_correction(H11, z, r, theta, 3 * n1)
+    zh = z / np.linalg.norm(z)
+    P = np.eye(n1) - np.outer(zh, zh)
+    M = P @ (A - theta * np.eye(n1)) @ P
+    ref = np.linalg.lstsq(M, P @ r, rcond=None)[0]
+    assert abs(zh @ t) <= 1e-12 * np.linalg.norm(t)
+    assert np.allclose(t, ref, rtol=0, atol=1e-9 * np.linalg.norm(ref))
+    assert np.array_equal(lead_block_correction(H11, z, r, theta, 0), np.zeros(n1))
+
+
+def test_lead_preconditioner_converges_to_dense_eigenvalues(small_matrix):
+    w, rp, c, v = small_matrix
+    lam = np.linalg.eigvalsh(dense(rp, c, v))[: w.k + 1]
+    th, rs, conv, rec = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, switch_order=3, tol=1e-8, max_blocks=8,
+                                           precond="lead", lead_iters=20)
+    assert conv and np.all(rs <= 1e-8)
+    gap = np.abs(np.diff(lam)).min()
+    assert np.all(np.abs(th - lam[: w.k]) <= 10 * (rs * np.abs(th)) ** 2 / gap + 1e-12)
