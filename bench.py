@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true", help="skip the block Lanczos comparator solve")
     ap.add_argument("--profile", default="none", choices=["none", "spmm", "solve"],
                     help="run the workload's SpMM twice (spmm) or one solve with the bench options (solve) and "
                          "exit, for profilers; prints no JSON line")
@@ -240,6 +241,7 @@ def run_ours(args):
         times.append(ms)
         stats.append(st)
     launches = S.sppc_kernel_launches() - launches0
+    th_last = th
     barrier()
     clk = clocks.stop()
     ms_step = float(np.mean(times))
@@ -302,6 +304,26 @@ def run_ours(args):
         "breakdown_ms_per_step": {kk: float(np.mean([s[kk] for s in stats]))
                                   for kk in ("spmm_ms", "minres_ms", "small_eig_ms", "dense_ms", "total_ms")},
     }
+    if rank == 0 and world == 1 and not args.no_comparator:
+        # C2's comparator: block Lanczos from Psi^(0) (the same loop, no SPPC orders,
+        # no preconditioner), one untimed-loop solve timed with CUDA events
+        copts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=0, tol=TOL, precond=0,
+                                    hybrid_maxit=5000)
+        hc = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, copts, stream=stream)
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            cconv, cth, crs, cst = S.sppc_solve(hc, k, tol=TOL, stream=stream)
+            c1.record(stream)
+        torch.cuda.synchronize()
+        line["comparator"] = {"method": "block Lanczos from Psi^(0), full reorthogonalisation, thick restart",
+                              "value": c0.elapsed_time(c1) / 1e3, "unit": "s", "spmv_h": cst["spmv_h"],
+                              "steps": cst["refine_steps"], "converged": bool(cconv),
+                              "max_rel_theta_diff": float(np.max(np.abs(np.asarray(cth) - np.asarray(th_last))
+                                                                 / np.abs(np.asarray(th_last))))}
+        S.sppc_destroy(hc)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, spmv, threads = cpu_oracle_sample(w, rp, c, v)
         value = t * st["spmv_h"] / spmv
