@@ -18,7 +18,7 @@ from .build import LIB
 __all__ = [
     "SppcError", "sppc_default_opts", "sppc_create", "sppc_spmm", "sppc_spmm_noalloc", "sppc_spmm_host", "sppc_start", "sppc_correct",
     "sppc_rayleigh_ritz", "sppc_refine_step", "sppc_solve", "sppc_order_info", "sppc_get_stats", "sppc_get_state", "sppc_get_layout",
-    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "EXPORTED_SYMBOLS", "STATUS",
+    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "sppc_small_syev", "EXPORTED_SYMBOLS", "STATUS",
 ]
 
 STATUS = {0: "SPPC_OK", 1: "SPPC_ERR_ARG", 2: "SPPC_ERR_NOT_SYMMETRIC", 3: "SPPC_ERR_LEVELS", 4: "SPPC_ERR_OOM",
@@ -83,6 +83,7 @@ _SIGS = {
     "sppc_destroy": (_I32, [_VP]),
     "sppc_last_error": (ctypes.c_char_p, [_VP]),
     "sppc_kernel_launches": (_I64, []),
+    "sppc_small_syev": (_I32, [_VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -250,6 +251,19 @@ def sppc_get_layout(h) -> dict:
 
 def sppc_kernel_launches() -> int:
     return int(_lib.sppc_kernel_launches())
+
+
+def sppc_small_syev(S, nev: int, stream=None):
+    """nev lowest eigenpairs of the symmetric m x m torch CUDA float64 tensor S
+    (m <= 144, nev <= 16); returns (theta, V) as CUDA tensors (V: m x nev)."""
+    import torch
+    S = S.contiguous()
+    m = int(S.shape[0])
+    theta = torch.empty(nev, dtype=torch.float64, device=S.device)
+    V = torch.empty(m, nev, dtype=torch.float64, device=S.device)
+    _check(None, _lib.sppc_small_syev(S.data_ptr(), m, m, int(nev), theta.data_ptr(), V.data_ptr(), int(nev),
+                                      _stream(stream)))
+    return theta, V
 
 
 def sppc_destroy(h) -> None:

@@ -87,14 +87,23 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
 
 // Deterministic grid reduction of nout (<= 32) double-float values: every CTA
 // reads all CTAs' partials in the same order (warp w sums CTAs w, w+16, ...;
-// the 16 warp sums are then added in order).  Result in red_out (shared).
+// the 16 warp sums are then added in order).  Result in red_out (shared).  The
+// loads of a warp are all issued before the additions (one L2 round trip).
+constexpr int kMaxPartialsPerWarp = 16;  // gridDim.x <= 16 * kMinresWarps
 __device__ void reduce_partials(const float2* partials, int nout, float2* sred /*[16][32]*/, float2* red_out) {
   const int t = threadIdx.x;
   const int o = t & 31, part = t >> 5;
   if (o < nout) {
+    float2 v[kMaxPartialsPerWarp];
+#pragma unroll
+    for (int i = 0; i < kMaxPartialsPerWarp; ++i) {
+      const int g = part + i * kMinresWarps;
+      v[i] = (g < (int)gridDim.x) ? __ldcg(partials + static_cast<int64_t>(g) * 32 + o) : make_float2(0.f, 0.f);
+    }
     float sh = 0.f, sl = 0.f;
-    for (int g = part; g < (int)gridDim.x; g += kMinresWarps) {
-      acc_add(sh, sl, partials[static_cast<int64_t>(g) * 32 + o]);
+#pragma unroll
+    for (int i = 0; i < kMaxPartialsPerWarp; ++i) {
+      acc_add(sh, sl, v[i]);
       acc_norm(sh, sl);
     }
     sred[part * 32 + o] = acc_get(sh, sl);
@@ -380,7 +389,8 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
         const double bn = sqrt(fmax(df_to_double(sdot[jj]), 0.0));
         const double al = st_alpha[jj], be = st_beta[jj];
         const double delta = st_cc[jj] * al - st_cp[jj] * st_sc[jj] * be;
-        const double rho1 = hypot(delta, bn);
+        // delta and beta are of the order of ||H0_hat||: no overflow guard needed
+        const double rho1 = sqrt(delta * delta + bn * bn);
         const double rho2 = st_sc[jj] * al + st_cp[jj] * st_cc[jj] * be;
         const double rho3 = st_sp[jj] * be;
         st_it[jj] += 1;
@@ -388,10 +398,11 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
           st_done[jj] = 1;
           c_wa[jj] = c_w2[jj] = c_w1[jj] = c_x[jj] = c_invb[jj] = z;
         } else {
-          const double cn = delta / rho1, sn = bn / rho1;
-          c_wa[jj] = df_from_double(1.0 / rho1);
-          c_w2[jj] = df_from_double(-rho3 / rho1);
-          c_w1[jj] = df_from_double(-rho2 / rho1);
+          const double inv = 1.0 / rho1;  // one division, the rest are products
+          const double cn = delta * inv, sn = bn * inv;
+          c_wa[jj] = df_from_double(inv);
+          c_w2[jj] = df_from_double(-rho3 * inv);
+          c_w1[jj] = df_from_double(-rho2 * inv);
           c_x[jj] = df_from_double(cn * st_eta[jj]);
           st_rn[jj] = fabs(sn) * st_rn[jj];
           st_eta[jj] = -sn * st_eta[jj];
@@ -453,6 +464,7 @@ cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE
   const int64_t gmax = static_cast<int64_t>(sms) * per_sm;
   if (grid > gmax) grid = gmax;
   if (grid < 1) grid = 1;
+  if (grid > static_cast<int64_t>(kMaxPartialsPerWarp) * kMinresWarps) grid = kMaxPartialsPerWarp * kMinresWarps;
   if (grid * 32 > partial_cap) return cudaErrorInvalidValue;
   e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;

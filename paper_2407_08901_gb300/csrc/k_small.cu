@@ -239,11 +239,12 @@ __device__ T rayleigh_tri(const T* d, const T* e, int m, const T* y) {
 //  2. Eigenvalue brackets by Sturm-count multisection in FP32 to ~1e-5; indices
 //     whose brackets crowd a neighbour are narrowed further in FP64.
 //  3. Eigenvectors of the tridiagonal matrix by inverse iteration, one thread
-//     per vector.  Isolated eigenvalues: three FP32 steps with Rayleigh-quotient
-//     shifts, then one FP64 step shifted by the FP64 Rayleigh quotient of that
-//     vector (the FP64 pipe is ~1/64 of FP32 here, so FP64 is kept to the final
-//     step).  Crowded groups: four FP64 steps from the bracket midpoint, then
-//     modified Gram-Schmidt.  The eigenvalue is the final Rayleigh quotient.
+//     per vector: three FP32 steps, then FP64 steps (the FP64 pipe is ~1/64 of
+//     FP32 here, so FP64 is kept to the last steps).  Isolated eigenvalues: FP32
+//     Rayleigh-quotient shifts, one FP64 step at the FP64 Rayleigh quotient.
+//     Crowded groups: shifts at the bracket midpoints (FP64 brackets ~1e-13
+//     wide), two FP64 steps, then modified Gram-Schmidt in the group.  The
+//     eigenvalue is the final Rayleigh quotient.
 //  4. Back-transformation through the stored reflectors in double-float.
 __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ S, int lds, int m, int nev,
                                                      double* __restrict__ theta, double* __restrict__ V, int ldv) {
@@ -416,40 +417,41 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
     double du[kMaxM], u1[kMaxM], u2[kMaxM], lm[kMaxM];
     unsigned char piv[kMaxM];
     const double eps_piv = 2.2e-16 * tnorm;
+    // three FP32 steps (isolated: Rayleigh-quotient shifts; crowded: the bracket
+    // midpoint), then FP64 steps: one at the FP64 Rayleigh quotient (isolated) or
+    // two at the FP64 bracket midpoint, ~1e-13 wide (crowded; orthogonalised in
+    // the group below).  The FP64 pipe is ~1/64 of FP32 here.
+    float yf[kMaxM], duf[kMaxM], u1f[kMaxM], u2f[kMaxM], lmf[kMaxM], ef[kMaxM];
+    for (int i = 0; i < m; ++i) {
+      yf[i] = 1.f + 0.1f * (float)((i * 7 + t * 3) % 11);
+      ef[i] = (i + 1 < m) ? static_cast<float>(e[i]) : 0.f;
+    }
+    const float epsf = static_cast<float>(1.2e-7 * tnorm);
+    float sf = static_cast<float>(0.5 * (lo[t] + hi[t]));
+    for (int it = 0; it < 3; ++it) {
+      tri_shift_solve<float>(d32, ef, m, sf, epsf, yf, duf, u1f, u2f, lmf, piv);
+      float nrm = 0.f;
+      for (int i = 0; i < m; ++i) nrm = fmaxf(nrm, fabsf(yf[i]));
+      const float inv = 1.f / nrm;
+      for (int i = 0; i < m; ++i) yf[i] *= inv;
+      if (!crowd[t] && it >= 1) {
+        const float rq = rayleigh_tri<float>(d32, ef, m, yf);
+        if (rq >= lo[t] - 1e-6 * tnorm && rq <= hi[t] + 1e-6 * tnorm) sf = rq;
+      }
+    }
+    for (int i = 0; i < m; ++i) y[i] = static_cast<double>(yf[i]);
+    double sigma = 0.5 * (lo[t] + hi[t]);
     if (!crowd[t]) {
-      float yf[kMaxM], duf[kMaxM], u1f[kMaxM], u2f[kMaxM], lmf[kMaxM], ef[kMaxM];
-      for (int i = 0; i < m; ++i) {
-        yf[i] = 1.f + 0.1f * (float)((i * 7 + t * 3) % 11);
-        ef[i] = (i + 1 < m) ? static_cast<float>(e[i]) : 0.f;
-      }
-      const float epsf = static_cast<float>(1.2e-7 * tnorm);
-      float sf = static_cast<float>(0.5 * (lo[t] + hi[t]));
-      for (int it = 0; it < 3; ++it) {
-        tri_shift_solve<float>(d32, ef, m, sf, epsf, yf, duf, u1f, u2f, lmf, piv);
-        float nrm = 0.f;
-        for (int i = 0; i < m; ++i) nrm = fmaxf(nrm, fabsf(yf[i]));
-        for (int i = 0; i < m; ++i) yf[i] /= nrm;
-        if (it >= 1) {
-          const float rq = rayleigh_tri<float>(d32, ef, m, yf);
-          if (rq >= lo[t] - 1e-6 * tnorm && rq <= hi[t] + 1e-6 * tnorm) sf = rq;
-        }
-      }
-      for (int i = 0; i < m; ++i) y[i] = static_cast<double>(yf[i]);
-      double sigma = rayleigh_tri<double>(d, e, m, y);
-      if (!(sigma >= lo[t] - 1e-6 * tnorm && sigma <= hi[t] + 1e-6 * tnorm)) sigma = 0.5 * (lo[t] + hi[t]);
+      const double rq = rayleigh_tri<double>(d, e, m, y);
+      if (rq >= lo[t] - 1e-6 * tnorm && rq <= hi[t] + 1e-6 * tnorm) sigma = rq;
+    }
+    const int steps64 = crowd[t] ? 2 : 1;
+    for (int it = 0; it < steps64; ++it) {
       tri_shift_solve<double>(d, e, m, sigma, eps_piv, y, du, u1, u2, lm, piv);
       double nrm = 0.0;
       for (int i = 0; i < m; ++i) nrm = fmax(nrm, fabs(y[i]));
-      for (int i = 0; i < m; ++i) y[i] /= nrm;
-    } else {
-      double sigma = 0.5 * (lo[t] + hi[t]);
-      for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.1 * (double)((i * 7 + t * 3) % 11);
-      for (int it = 0; it < 4; ++it) {
-        tri_shift_solve<double>(d, e, m, sigma, eps_piv, y, du, u1, u2, lm, piv);
-        double nrm = 0.0;
-        for (int i = 0; i < m; ++i) nrm = fmax(nrm, fabs(y[i]));
-        for (int i = 0; i < m; ++i) y[i] /= nrm;
-      }
+      const double inv = 1.0 / nrm;
+      for (int i = 0; i < m; ++i) y[i] *= inv;
     }
   }
   __syncthreads();

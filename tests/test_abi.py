@@ -71,3 +71,16 @@ def test_create_rejects_bad_input(case, status):
         S.sppc_create(rp, c, v, lev, n1, k, opts)
     assert ei.value.status == status, str(ei.value)
     assert S.sppc_last_error(None)
+
+
+def test_small_syev_rejects_bad_sizes_before_any_device_call():
+    import ctypes
+    import paper_2407_08901_gb300 as S
+    lib = ctypes.CDLL(S.LIB)
+    lib.sppc_small_syev.restype = ctypes.c_int32
+    lib.sppc_small_syev.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    buf = ctypes.c_void_p(1)  # never dereferenced: the size check fails first
+    assert lib.sppc_small_syev(buf, 200, 200, 8, buf, buf, 8, None) == 1
+    assert lib.sppc_small_syev(buf, 10, 10, 0, buf, buf, 8, None) == 1
+    assert lib.sppc_small_syev(None, 10, 10, 4, buf, buf, 4, None) == 1
