@@ -157,6 +157,17 @@ def cpu_oracle_sample(w, rp, c, v, orders: int = 3):
     return time.perf_counter() - t0, r.spmv, threads
 
 
+def slowest_rank(value: float, dist=None, device: str = "cuda") -> float:
+    """Replicas under torchrun: every rank solves its own copy of the workload; the
+    job's time per step is the slowest rank's (max over ranks)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -244,11 +255,7 @@ def run_ours(args):
     th_last = th
     barrier()
     clk = clocks.stop()
-    ms_step = float(np.mean(times))
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = slowest_rank(float(np.mean(times)), dist, "cuda")
     S.sppc_destroy(h)
 
     # end to end through the C ABI from host buffers
