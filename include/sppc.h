@@ -97,6 +97,13 @@ typedef struct {
                               first kept less than half of some column's norm (default), 1 = always
                               twice (SPPC orders always project twice, Eq. blkGS) */
   int32_t precond_iters;   /* MINRES steps of the leading-block preconditioner (precond 2; default 20) */
+  int32_t precision;       /* 0: FP64 path (double-float, default).  1: mixed precision: H's values
+                              rounded to FP32 everywhere; the products with H during the solve in FP32
+                              (X rounded to FP32, FP32 accumulation); Gram, CholeskyQR2, the projected
+                              eigensolve and MINRES in double-float; at the end the Ritz values and
+                              residuals are recomputed with double-float products (Rayleigh
+                              quotients) and the continuation goes on with double-float products
+                              if they miss tol.  Needs k = 7 or 8. */
 } sppc_opts;
 
 typedef struct {
@@ -116,6 +123,8 @@ typedef struct {
   int32_t restarts;          /* thick restarts of the continuation */
   int32_t switched_at;       /* SPPC order at which the continuation started */
   int32_t reorth_passes;     /* appended blocks that needed the second Gram-Schmidt pass */
+  int32_t refine_df;         /* mixed precision: continuation steps run with double-float products
+                                after the FP32 phase */
 } sppc_stats;
 
 /* Fill `o` with the defaults listed above. */

@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("timing", ctypes.c_int32), ("spmm_chunk_cols", ctypes.c_int64),
                 ("hybrid", ctypes.c_int32), ("switch_order", ctypes.c_int32), ("hybrid_maxit", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precond_clamp", ctypes.c_double), ("hybrid_blocks", ctypes.c_int32),
-                ("spmm_kernel", ctypes.c_int32), ("reorth", ctypes.c_int32), ("precond_iters", ctypes.c_int32)]
+                ("spmm_kernel", ctypes.c_int32), ("reorth", ctypes.c_int32), ("precond_iters", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -56,7 +57,7 @@ class Stats(ctypes.Structure):
                 ("spmm_launches", ctypes.c_int32), ("spmm_ms", ctypes.c_double), ("minres_ms", ctypes.c_double),
                 ("small_eig_ms", ctypes.c_double), ("dense_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("restarts", ctypes.c_int32), ("switched_at", ctypes.c_int32),
-                ("reorth_passes", ctypes.c_int32)]
+                ("reorth_passes", ctypes.c_int32), ("refine_df", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -101,6 +101,9 @@ struct sppc_ctx {
   int64_t partial_cap = 0;
   double *stageX = nullptr, *stageY = nullptr;  // sppc_spmm_host staging (n x 8 each)
   float2* dDiag = nullptr;                        // diag(H), double-float (Jacobi preconditioner)
+  float* val32 = nullptr;                         // FP32 copy of H's SELL values (mixed precision)
+  float* X32 = nullptr;                           // FP32 copy of the SpMM input block (mixed precision)
+  bool f32_products = false;                      // big SpMMs in FP32 (mixed precision, until verified)
   int nev = 0;                                    // Ritz pairs kept by the last Rayleigh-Ritz
 
   // state
@@ -516,7 +519,10 @@ sppc_status big_spmm(sppc_ctx* h, const float2* X, float2* Y, int kp) {
     b = next_event(h);
     CK(cudaEventRecord(a, h->stream));
   }
-  CK(spmm(h->H, kp, X, Y, Epi{}, h->stream));
+  if (h->f32_products && kp == 8)
+    CK(spmm_f32(h->H, h->val32, X, h->X32, Y, h->stream));
+  else
+    CK(spmm(h->H, kp, X, Y, Epi{}, h->stream));
   if (h->opt.timing) {
     CK(cudaEventRecord(b, h->stream));
     h->pending.push_back({a, b});
@@ -885,7 +891,7 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
 
 // Thick restart of the continuation: Q <- Q Y_2k, W <- W Y_2k (two blocks of k
 // Ritz vectors, the 2k lowest), projected matrix recomputed from the new blocks.
-sppc_status restart(sppc_ctx* h) {
+sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
   PhaseRange nvtx_range("restart");
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp, p = h->p;
@@ -899,7 +905,13 @@ sppc_status restart(sppc_ctx* h) {
               s));
   }
   CK(cudaMemcpyAsync(h->Q, h->Psi, sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(h->W, blk(h->Psi, n, kp, 2), sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
+  if (fresh_products) {
+    // W = H Q recomputed (mixed precision: replaces products made in FP32)
+    for (int b = 0; b < 2; ++b) CKS(big_spmm(h, blk(h->Q, n, kp, b), blk(h->W, n, kp, b), kp));
+    h->stats.spmv_h += 2 * h->k;
+  } else {
+    CK(cudaMemcpyAsync(h->W, blk(h->Psi, n, kp, 2), sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
+  }
   for (int b = 0; b < 2; ++b) {
     CK(gram(blocks(h->Q, n, kp, 0, b + 1), blk(h->W, n, kp, b), kp, 0, n, h->dGram, h->partials, h->partial_cap,
             s));
@@ -1059,6 +1071,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->precond = 1;
   o->precond_clamp = 1e-2;
   o->precond_iters = 20;
+  o->precision = 0;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1114,6 +1127,9 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.spmm_kernel != 0 && opt.spmm_kernel != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.spmm_kernel must be 0 or 1");
   if (opt.reorth != 0 && opt.reorth != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.reorth must be 0 or 1");
   if (opt.precond < 0 || opt.precond > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precond must be 0, 1 or 2");
+  if (opt.precision != 0 && opt.precision != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.precision must be 0 or 1");
+  if (opt.precision == 1 && (k + 1) / 2 * 2 != 8)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.precision = 1 needs k = 7 or 8 (8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precond_iters must be in [0, 10000]");
 
@@ -1152,6 +1168,14 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       return bail(fail(h, SPPC_ERR_CUDA, "copying the device CSR to the host failed"));
     rp = rp_h.data();
     ci = ci_h.data();
+    va = va_h.data();
+  }
+  if (opt.precision == 1) {
+    // mixed precision: the matrix is H rounded to FP32, everywhere (SpMM, leading
+    // block, diagonal); the solver's error is measured against that matrix
+    if (va_h.empty()) va_h.assign(va, va + Hc->nnz);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < Hc->nnz; ++t) va_h[t] = static_cast<double>(static_cast<float>(va_h[t]));
     va = va_h.data();
   }
   // validation
@@ -1217,6 +1241,16 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     sppc_status st = upload_sell(h, S, h->H, n, h->h_chunk_slice);
     if (st != SPPC_OK) return bail(st);
     h->H.tma = (opt.spmm_kernel == 0 && spmm_tma_available()) ? 1 : 0;
+    if (opt.precision == 1) {
+      std::vector<float> v32(S.val.size());
+#pragma omp parallel for schedule(static)
+      for (int64_t t = 0; t < (int64_t)S.val.size(); ++t) v32[t] = S.val[t].x;  // exact: values are FP32
+      cudaError_t e = dalloc(h, &h->val32, v32.size());
+      if (e == cudaSuccess) e = dalloc(h, &h->X32, (size_t)n * 8);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(h->val32, v32.data(), sizeof(float) * v32.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_OOM, "FP32 values: %s", cudaGetErrorString(e)));
+    }
     h->h_slices = S.nslices;
     h->h_slice_ptr = std::move(S.slice_ptr);
     h->h_slice_rows = std::move(S.rows);
@@ -1314,7 +1348,10 @@ sppc_status sppc_spmm(sppc_handle h, const double* X, int64_t ldx, double* Y, in
   h->stream = s;
   const int kp = (ncols + 1) / 2 * 2;
   CK(f64_to_df(X, ldx, ncols, h->T1, kp, 0, h->n, s));
-  CK(spmm(h->H, kp, h->T1, h->T2, Epi{}, s));
+  if (h->opt.precision == 1 && kp == 8)
+    CK(spmm_f32(h->H, h->val32, h->T1, h->X32, h->T2, s));
+  else
+    CK(spmm(h->H, kp, h->T1, h->T2, Epi{}, s));
   CK(df_to_f64(h->T2, kp, Y, ldy, ncols, 0, h->n, s));
   return SPPC_OK;
 }
@@ -1512,6 +1549,49 @@ sppc_status sppc_rayleigh_ritz(sppc_handle h, double* theta, double* resid, void
   return SPPC_OK;
 }
 
+// Mixed precision: the k Ritz vectors z_j = Q Y_j, their product with H in
+// double-float (the FP32-rounded matrix, exact to double-float), Rayleigh
+// quotients theta_j = z^T H z / z^T z and residuals ||H z - theta z|| / |theta|.
+// Replaces the Ritz values and residuals of the last Rayleigh-Ritz step, whose
+// H-products were FP32.
+sppc_status verify_df(sppc_ctx* h) {
+  cudaStream_t s = h->stream;
+  const int k = h->k, kp = h->kp;
+  const int64_t n = h->n;
+  float2* c = h->dCoef;
+  CK(update(h->T1, nullptr, nullptr, blocks(h->Q, n, kp, 0, h->p + 1), h->dY, kp, 0, n, s));
+  CK(spmm(h->H, kp, h->T1, h->T2, Epi{}, s));
+  {
+    const float2* A[2] = {h->T1, h->T1};
+    const float2* B[2] = {h->T2, h->T1};
+    CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+  }
+  std::vector<double> dd(2 * kp);
+  CK(cudaMemcpyAsync(dd.data(), h->dDots, sizeof(double) * 2 * kp, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> th(k), negth(kp, 0.0);
+  for (int j = 0; j < k; ++j) {
+    th[j] = dd[j] / dd[kp + j];
+    negth[j] = -th[j];
+  }
+  CK(cudaMemcpyAsync(h->dDots + 2 * kp, negth.data(), sizeof(double) * kp, cudaMemcpyHostToDevice, s));
+  CK(to_df(h->dDots + 2 * kp, c + kDefl, kp, 1.0, s));
+  CK(combine_diag(h->T2, h->T2, c + kOnes, one(h->T1), c + kDefl, kp, 0, n, s));  // H z - theta z
+  {
+    const float2* A[1] = {h->T2};
+    const float2* B[1] = {h->T2};
+    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+  }
+  std::vector<double> r2(kp);
+  CK(cudaMemcpyAsync(r2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->theta = th;
+  h->resid.assign(k, 0.0);
+  for (int j = 0; j < k; ++j) h->resid[j] = std::sqrt(std::max(r2[j], 0.0) / std::max(dd[kp + j], 1e-300)) /
+                                           std::fabs(th[j]);
+  return SPPC_OK;
+}
+
 sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, double* Z, int64_t ldz,
                        double* resid, sppc_stats* stats, void* stream) {
   if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
@@ -1527,6 +1607,7 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     cudaEventCreate(&t1);
     cudaEventRecord(t0, s);
   }
+  h->f32_products = (h->opt.precision == 1);
   CKS(sppc_start(h, nullptr, nullptr, stream));
   bool conv = all_converged(h, tol);
   const int sppc_orders = h->opt.hybrid ? std::min(p_max, h->opt.switch_order) : p_max;
@@ -1539,12 +1620,52 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
   if (h->opt.hybrid) {
     h->stats.switched_at = h->p;
     h->in_refine = true;
+    // mixed precision: the FP32 phase stops at max(tol, 1e-6) or when its largest
+    // residual estimate has not dropped by 10% in 8 steps (the FP32 products'
+    // floor is about 2^-24 ||H|| / |theta|); the double-float phase below finishes
+    const double tol_phase = h->f32_products ? std::max(tol, 1e-6) : tol;
+    double best = 1e300;
+    int since_best = 0;
+    conv = all_converged(h, tol_phase);
     while (!conv && h->stats.refine_steps < h->opt.hybrid_maxit) {
       CKS(refine_step(h));
+      conv = all_converged(h, tol_phase);
+      if (h->f32_products) {
+        const double worst = *std::max_element(h->resid.begin(), h->resid.end());
+        if (worst < 0.9 * best) {
+          best = worst;
+          since_best = 0;
+        } else if (++since_best >= 8) {
+          break;
+        }
+      }
+    }
+    conv = all_converged(h, tol);
+  }
+  const bool fresh = h->opt.precision == 1 && h->opt.hybrid && h->p >= 1 && h->nev >= 2 * h->k;
+  h->f32_products = false;
+  if (fresh) {
+    // Mixed precision: the residuals of the FP32 phase are estimates and its W
+    // blocks carry FP32 errors.  Restart from the 2k lowest Ritz vectors with
+    // their products recomputed in double-float, and continue with double-float
+    // products until the (now exact) residuals meet tol.
+    CKS(restart(h, true));
+    CKS(rr_core(h, h->p, false, nullptr, 0, h->HPsi, h->opt.precond ? h->dDiag : nullptr));
+    h->t_ready = true;
+    conv = all_converged(h, tol);
+    while (!conv && h->stats.refine_df < h->opt.hybrid_maxit) {
+      CKS(refine_step(h));
       conv = all_converged(h, tol);
+      h->stats.refine_df += 1;
     }
   }
   if (Z) CKS(rr_core(h, h->p, true, Z, ldz));
+  if (h->opt.precision == 1 && !fresh) {
+    // plain SPPC in mixed precision: Rayleigh quotients and residuals of the Ritz
+    // vectors from double-float products
+    CKS(verify_df(h));
+    conv = all_converged(h, tol);
+  }
   h->stats.converged = conv ? 1 : 0;
   if (h->opt.timing) {
     cudaEventRecord(t1, s);

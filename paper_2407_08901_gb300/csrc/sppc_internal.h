@@ -64,6 +64,11 @@ struct BlockList {
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
 int spmm_default_grid();
 
+// ---- k_spmm_f32.cu (mixed precision, 8 columns): X (double-float) rounded to
+// FP32 into X32 (n x 8 floats), Y = H X with FP32 values val32 (same SELL layout as
+// A) and FP32 accumulation, written as double-float with zero low words.
+cudaError_t spmm_f32(const SellDev& A, const float* val32, const float2* X, float* X32, float2* Y, cudaStream_t s);
+
 // ---- k_spmm_tma.cu (kp = 8; X 16-byte aligned)
 bool spmm_tma_available();
 cudaError_t spmm_tma8(const SellDev& A, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
