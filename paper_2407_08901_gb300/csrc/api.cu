@@ -1230,30 +1230,64 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     h->h11_hi = hi;
     h->h11_norm = std::max(std::fabs(lo), std::fabs(hi));
   }
-  // layouts
+  // layouts: H's SELL-16 built on the GPU from a device copy of the CSR
   {
-    SellHost S;
     std::vector<int64_t> seg(h->lev.begin(), h->lev.end());
     int64_t chunk = opt.spmm_chunk_cols;
     if (chunk == 0) chunk = 1310720;  // 80 MB of an 8-column double-float block
     if (chunk > 0 && (n + chunk - 1) / chunk > 255) chunk = (n + 254) / 255;
-    build_sell(n, rp, ci, va, n, seg, 1024, chunk, S);
-    sppc_status st = upload_sell(h, S, h->H, n, h->h_chunk_slice);
-    if (st != SPPC_OK) return bail(st);
+    cudaStream_t s = h->stream;
+    int64_t* d_rp = nullptr;
+    int32_t* d_ci = nullptr;
+    double* d_va = nullptr;
+    const int64_t nnz1 = Hc->nnz > 0 ? Hc->nnz : 1;
+    cudaError_t e = cudaMallocAsync(&d_rp, sizeof(int64_t) * (n + 1), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_ci, sizeof(int32_t) * nnz1, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_va, sizeof(double) * nnz1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && Hc->nnz > 0)
+      e = cudaMemcpyAsync(d_ci, ci, sizeof(int32_t) * Hc->nnz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && Hc->nnz > 0)
+      e = cudaMemcpyAsync(d_va, va, sizeof(double) * Hc->nnz, cudaMemcpyHostToDevice, s);
+    SellDeviceLayout L;
+    const DeviceAlloc alloc = [h](void** p, size_t bytes) {
+      unsigned char* q = nullptr;
+      const cudaError_t x = dalloc(h, &q, bytes);
+      *p = q;
+      return x;
+    };
+    if (e == cudaSuccess) e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, chunk, s, alloc, L);
+    if (d_rp) cudaFreeAsync(d_rp, s);
+    if (d_ci) cudaFreeAsync(d_ci, s);
+    if (d_va) cudaFreeAsync(d_va, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+      return bail(fail(h, e == cudaErrorMemoryAllocation ? SPPC_ERR_OOM : SPPC_ERR_CUDA, "SELL build on the GPU: %s",
+                       cudaGetErrorString(e)));
+    h->h_chunk_slice = L.chunk_slice;
+    h->H.nslices = L.nslices;
+    h->H.nrows = n;
+    h->H.nchunks = L.nchunks;
+    h->H.chunk_cols = L.chunk_cols;
+    h->H.chunk_slice = h->h_chunk_slice.data();
+    h->H.slice_ptr = L.slice_ptr_d;
+    h->H.slice_rows = L.rows_d;
+    h->H.col = L.col_d;
+    h->H.val = L.val_d;
+    h->H.row_first = L.first_d;
+    h->H.row_last = L.last_d;
     h->H.tma = (opt.spmm_kernel == 0 && spmm_tma_available()) ? 1 : 0;
     if (opt.precision == 1) {
-      std::vector<float> v32(S.val.size());
-#pragma omp parallel for schedule(static)
-      for (int64_t t = 0; t < (int64_t)S.val.size(); ++t) v32[t] = S.val[t].x;  // exact: values are FP32
-      cudaError_t e = dalloc(h, &h->val32, v32.size());
+      // FP32 copy of the values (exact: they are FP32 already)
+      e = dalloc(h, &h->val32, (size_t)(L.total > 0 ? L.total : 1));
       if (e == cudaSuccess) e = dalloc(h, &h->X32, (size_t)n * 8);
-      if (e == cudaSuccess)
-        e = cudaMemcpy(h->val32, v32.data(), sizeof(float) * v32.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = df_hi_parts(L.val_d, h->val32, L.total, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_OOM, "FP32 values: %s", cudaGetErrorString(e)));
     }
-    h->h_slices = S.nslices;
-    h->h_slice_ptr = std::move(S.slice_ptr);
-    h->h_slice_rows = std::move(S.rows);
+    h->h_slices = L.nslices;
+    h->h_slice_ptr = std::move(L.slice_ptr);
+    h->h_slice_rows = std::move(L.rows);
   }
   {
     SellHost S;

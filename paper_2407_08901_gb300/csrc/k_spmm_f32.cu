@@ -87,6 +87,13 @@ int g_grid32 = 0;
 
 }  // namespace
 
+cudaError_t df_hi_parts(const float2* in, float* out, int64_t count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_df_hi<<<static_cast<unsigned>((count + 255) / 256), 256, 0, s>>>(in, out, count);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t spmm_f32(const SellDev& A, const float* val32, const float2* X, float* X32, float2* Y, cudaStream_t s) {
   if (A.nslices == 0) return cudaSuccess;
   if (g_grid32 == 0) {

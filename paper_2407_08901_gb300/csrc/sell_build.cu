@@ -1,0 +1,411 @@
+// SELL-16 layout of H built on the GPU from a device copy of its CSR.
+//
+// Same layout as the host builder (build_sell in api.cu, bit for bit): columns
+// cut into chunks of C columns; per chunk, inside every level segment, the rows
+// with entries in the chunk (plus, in chunk 0, rows without any entry) are
+// stably sorted by decreasing entry count within windows of sigma rows and cut
+// into slices of 16 rows; entry t of slice row l sits at slice_ptr[s] + 16 t + l;
+// padding entries take the chunk's first column and value 0.  Steps:
+//   1. per row, the offsets of the chunk boundaries (binary search in the row);
+//   2. per chunk, the listed rows by an exclusive scan of their flags;
+//   3. per window (<= 1024 rows), a bitonic sort on (decreasing count, position);
+//   4. per slice, its rows and width; slice_ptr by an exclusive scan of 16 x width;
+//   5. the entries, one half-warp per slice, values split into double-float.
+// On c2 (4e8 entries) this replaces ~0.42 s of host work.
+#include <algorithm>
+#include <vector>
+
+#include "df.cuh"
+#include "sppc_internal.h"
+
+namespace sppc {
+
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kWindow = 1024;
+
+// ---- exclusive scan of int64 values (three-phase, recursive on block totals)
+__global__ void k_scan_block(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                             int64_t* __restrict__ block_sums) {
+  __shared__ int64_t warp_tot[32];
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kScanBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t v = (i < n) ? in[i] : 0;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t t = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;  // inclusive over warps
+  }
+  __syncthreads();
+  const int64_t before = (warp > 0) ? warp_tot[warp - 1] : 0;
+  if (i < n) out[i] = before + x - v;  // exclusive
+  if (threadIdx.x == kScanBlock - 1) block_sums[blockIdx.x] = warp_tot[31];
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ block_offsets) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kScanBlock + threadIdx.x;
+  if (i < n) out[i] += block_offsets[blockIdx.x];
+}
+
+cudaError_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+  int64_t* sums = nullptr;
+  int64_t* offs = nullptr;
+  cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * nb * 2, s);
+  if (e != cudaSuccess) return e;
+  offs = sums + nb;
+  k_scan_block<<<static_cast<unsigned>(nb), kScanBlock, 0, s>>>(in, out, n, sums);
+  count_launch();
+  if (nb > 1) {
+    e = exclusive_scan(sums, offs, nb, s);
+    if (e == cudaSuccess) {
+      k_scan_add<<<static_cast<unsigned>(nb), kScanBlock, 0, s>>>(out, n, offs);
+      count_launch();
+    }
+  }
+  cudaFreeAsync(sums, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// ---- 1. chunk boundary offsets per row, first/last chunk with entries
+__global__ void k_row_chunks(int64_t nrows, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             int64_t C, int64_t ncols, int nch, int32_t* __restrict__ off, uint8_t* __restrict__ first,
+                             uint8_t* __restrict__ last) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int32_t* b = ci + rp[r];
+  const int32_t len = static_cast<int32_t>(rp[r + 1] - rp[r]);
+  int fq = -1, lq = 0;
+  int32_t prev = 0;
+  for (int q = 0; q <= nch; ++q) {
+    const int64_t lim64 = min(static_cast<int64_t>(q) * C, ncols);
+    const int32_t lim = static_cast<int32_t>(min(lim64, static_cast<int64_t>(INT32_MAX)));
+    int32_t lo = 0, hi = len;  // first position with b[pos] >= lim
+    while (lo < hi) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (b[mid] < lim) lo = mid + 1;
+      else hi = mid;
+    }
+    off[r * (nch + 1) + q] = lo;
+    if (q > 0 && lo > prev) {
+      if (fq < 0) fq = q - 1;
+      lq = q - 1;
+    }
+    prev = lo;
+  }
+  first[r] = static_cast<uint8_t>(fq < 0 ? 0 : fq);
+  last[r] = static_cast<uint8_t>(lq);
+}
+
+// ---- 2. rows listed in chunk q: entries in the chunk, or (chunk 0) no entry at all
+__global__ void k_flags(int64_t nrows, const int32_t* __restrict__ off, int nch, int q, int64_t* __restrict__ flag) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int32_t* o = off + r * (nch + 1);
+  const bool listed = (o[q + 1] > o[q]) || (q == 0 && o[nch] == 0);
+  flag[r] = listed ? 1 : 0;
+}
+
+__global__ void k_compact(int64_t nrows, const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                          int32_t* __restrict__ list) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r < nrows && flag[r]) list[pos[r]] = static_cast<int32_t>(r);
+}
+
+// ---- 3. stable sort of each window by decreasing count (bitonic on a 64-bit key
+// (~count << 32 | position), one CTA per window of <= 1024 rows)
+struct Window {
+  int64_t start;
+  int32_t size;
+  int32_t q;
+};
+
+__global__ void __launch_bounds__(512) k_sort_windows(const Window* __restrict__ win, int32_t* __restrict__ list,
+                                                      const int32_t* __restrict__ off, int nch) {
+  __shared__ unsigned long long key[kWindow];
+  __shared__ int32_t row[kWindow];
+  const Window w = win[blockIdx.x];
+  for (int i = threadIdx.x; i < kWindow; i += blockDim.x) {
+    if (i < w.size) {
+      const int32_t r = list[w.start + i];
+      const int32_t* o = off + static_cast<int64_t>(r) * (nch + 1);
+      const uint32_t cnt = static_cast<uint32_t>(o[w.q + 1] - o[w.q]);
+      key[i] = (static_cast<unsigned long long>(~cnt) << 32) | static_cast<unsigned>(i);
+      row[i] = r;
+    } else {
+      key[i] = ~0ull;  // padding sorts last
+      row[i] = -1;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= kWindow; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < kWindow / 2; t += blockDim.x) {
+        const int i = 2 * t - (t & (stride - 1));
+        const int j = i + stride;
+        const bool up = ((i & size) == 0);
+        const unsigned long long a = key[i], b = key[j];
+        if ((a > b) == up) {
+          key[i] = b;
+          key[j] = a;
+          const int32_t tr = row[i];
+          row[i] = row[j];
+          row[j] = tr;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < w.size; i += blockDim.x) list[w.start + i] = row[i];
+}
+
+// ---- 4. slices: rows and widths
+struct Part {
+  int64_t list_off;   // first row of the part in the list
+  int64_t count;      // rows in the part
+  int64_t slice_base; // first slice of the part
+  int32_t q;
+};
+
+__global__ void k_slices(int64_t nslices, const Part* __restrict__ parts, int nparts, const int32_t* __restrict__ list,
+                         const int32_t* __restrict__ off, int nch, int32_t* __restrict__ slice_rows,
+                         int64_t* __restrict__ slice_len, int32_t* __restrict__ slice_q) {
+  const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= nslices) return;
+  int lo = 0, hi = nparts - 1;  // last part with slice_base <= s
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (parts[mid].slice_base <= s) lo = mid;
+    else hi = mid - 1;
+  }
+  const Part p = parts[lo];
+  const int64_t first = p.list_off + (s - p.slice_base) * kSliceH;
+  int32_t w = 0;
+  for (int l = 0; l < kSliceH; ++l) {
+    const int64_t idx = (s - p.slice_base) * kSliceH + l;
+    int32_t r = -1;
+    if (idx < p.count) {
+      r = list[first + l];
+      const int32_t* o = off + static_cast<int64_t>(r) * (nch + 1);
+      w = max(w, o[p.q + 1] - o[p.q]);
+    }
+    slice_rows[s * kSliceH + l] = r;
+  }
+  slice_len[s] = static_cast<int64_t>(w) * kSliceH;
+  slice_q[s] = p.q;
+}
+
+// ---- 5. entries: a half-warp per slice, lane l = slice row l
+__global__ void k_fill(int64_t nslices, const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ slice_rows,
+                       const int32_t* __restrict__ slice_q, const int64_t* __restrict__ rp,
+                       const int32_t* __restrict__ ci, const double* __restrict__ va, const int32_t* __restrict__ off,
+                       int nch, int64_t C, int64_t ncols, int32_t* __restrict__ col, float2* __restrict__ val) {
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t s = g / kSliceH;
+  const int l = static_cast<int>(g % kSliceH);
+  if (s >= nslices) return;
+  const int64_t base = slice_ptr[s];
+  const int64_t w = (slice_ptr[s + 1] - base) / kSliceH;
+  const int q = slice_q[s];
+  const int32_t r = slice_rows[s * kSliceH + l];
+  int64_t len = 0, src = 0;
+  if (r >= 0) {
+    const int32_t* o = off + static_cast<int64_t>(r) * (nch + 1);
+    len = o[q + 1] - o[q];
+    src = rp[r] + o[q];
+  }
+  const int32_t pad = static_cast<int32_t>(min(static_cast<int64_t>(q) * C, ncols - 1));
+  for (int64_t t = 0; t < w; ++t) {
+    const int64_t idx = base + kSliceH * t + l;
+    if (t < len) {
+      col[idx] = ci[src + t];
+      val[idx] = df_from_double(va[src + t]);
+    } else {
+      col[idx] = pad;
+      val[idx] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t ncols,
+                              const std::vector<int64_t>& seg, int64_t chunk_cols, cudaStream_t s,
+                              const DeviceAlloc& alloc, SellDeviceLayout& out) {
+  const int64_t C = (chunk_cols > 0 && chunk_cols < ncols) ? chunk_cols : ncols;
+  const int nch = static_cast<int>((ncols + C - 1) / C);
+  out.nchunks = nch;
+  out.chunk_cols = C;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+    return e == cudaSuccess;
+  };
+  // persistent outputs
+  uint8_t *first = nullptr, *last = nullptr;
+  if (!chk(alloc(reinterpret_cast<void**>(&first), nrows > 0 ? nrows : 1))) return e;
+  if (!chk(alloc(reinterpret_cast<void**>(&last), nrows > 0 ? nrows : 1))) return e;
+  // temporaries
+  int32_t* off = nullptr;
+  int64_t *flag = nullptr, *pos = nullptr;
+  int32_t* list = nullptr;
+  const int64_t rows1 = nrows > 0 ? nrows : 1;
+  chk(cudaMallocAsync(&off, sizeof(int32_t) * rows1 * (nch + 1), s));
+  chk(cudaMallocAsync(&flag, sizeof(int64_t) * rows1, s));
+  chk(cudaMallocAsync(&pos, sizeof(int64_t) * rows1, s));
+  chk(cudaMallocAsync(&list, sizeof(int32_t) * rows1 * nch, s));
+  const unsigned gr = static_cast<unsigned>((rows1 + 255) / 256);
+  if (e == cudaSuccess) {
+    k_row_chunks<<<gr, 256, 0, s>>>(nrows, rp, ci, C, ncols, nch, off, first, last);
+    count_launch();
+    chk(cudaGetLastError());
+  }
+  // 2. per chunk: listed rows in row order, counts per level segment
+  std::vector<Part> parts;
+  std::vector<Window> wins;
+  std::vector<int64_t> chunk_slice(nch + 1, 0);
+  int64_t list_base = 0, slice_base = 0;
+  for (int q = 0; q < nch && e == cudaSuccess; ++q) {
+    k_flags<<<gr, 256, 0, s>>>(nrows, off, nch, q, flag);
+    count_launch();
+    chk(cudaGetLastError());
+    chk(exclusive_scan(flag, pos, nrows, s));
+    if (e != cudaSuccess) break;
+    k_compact<<<gr, 256, 0, s>>>(nrows, flag, pos, list + list_base);
+    count_launch();
+    chk(cudaGetLastError());
+    // positions at the segment boundaries (exclusive scan; the total from the last row)
+    std::vector<int64_t> bpos(seg.size(), 0);
+    for (size_t i = 0; i < seg.size() && e == cudaSuccess; ++i) {
+      if (seg[i] < nrows) {
+        chk(cudaMemcpyAsync(&bpos[i], pos + seg[i], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      } else {
+        int64_t lp = 0, lf = 0;
+        chk(cudaMemcpyAsync(&lp, pos + nrows - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        chk(cudaMemcpyAsync(&lf, flag + nrows - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        chk(cudaStreamSynchronize(s));
+        bpos[i] = lp + lf;
+      }
+    }
+    chk(cudaStreamSynchronize(s));
+    chunk_slice[q] = slice_base;
+    for (size_t g = 0; g + 1 < seg.size(); ++g) {
+      const int64_t cnt = bpos[g + 1] - bpos[g];
+      Part p;
+      p.list_off = list_base + bpos[g];
+      p.count = cnt;
+      p.slice_base = slice_base;
+      p.q = q;
+      parts.push_back(p);
+      for (int64_t w0 = 0; w0 < cnt; w0 += kWindow) {
+        Window w;
+        w.start = p.list_off + w0;
+        w.size = static_cast<int32_t>(std::min<int64_t>(kWindow, cnt - w0));
+        w.q = q;
+        wins.push_back(w);
+      }
+      slice_base += (cnt + kSliceH - 1) / kSliceH;
+    }
+    list_base += bpos.back();
+  }
+  chunk_slice[nch] = slice_base;
+  const int64_t ns = slice_base;
+  out.nslices = ns;
+  out.chunk_slice = chunk_slice;
+  // 3. sort windows
+  Window* dwin = nullptr;
+  Part* dparts = nullptr;
+  if (e == cudaSuccess && !wins.empty()) {
+    chk(cudaMallocAsync(&dwin, sizeof(Window) * wins.size(), s));
+    chk(cudaMemcpyAsync(dwin, wins.data(), sizeof(Window) * wins.size(), cudaMemcpyHostToDevice, s));
+    if (e == cudaSuccess) {
+      k_sort_windows<<<static_cast<unsigned>(wins.size()), 512, 0, s>>>(dwin, list, off, nch);
+      count_launch();
+      chk(cudaGetLastError());
+    }
+  }
+  // 4. slices
+  int64_t* slice_ptr = nullptr;
+  int32_t* slice_rows = nullptr;
+  int64_t* slice_len = nullptr;
+  int32_t* slice_q = nullptr;
+  const int64_t ns1 = ns > 0 ? ns : 1;
+  chk(alloc(reinterpret_cast<void**>(&slice_ptr), sizeof(int64_t) * (ns + 1)));
+  chk(alloc(reinterpret_cast<void**>(&slice_rows), sizeof(int32_t) * ns1 * kSliceH));
+  chk(cudaMallocAsync(&slice_len, sizeof(int64_t) * (ns + 1), s));
+  chk(cudaMallocAsync(&slice_q, sizeof(int32_t) * ns1, s));
+  if (e == cudaSuccess && ns > 0) {
+    chk(cudaMallocAsync(&dparts, sizeof(Part) * parts.size(), s));
+    chk(cudaMemcpyAsync(dparts, parts.data(), sizeof(Part) * parts.size(), cudaMemcpyHostToDevice, s));
+    if (e == cudaSuccess) {
+      k_slices<<<static_cast<unsigned>((ns + 255) / 256), 256, 0, s>>>(ns, dparts, static_cast<int>(parts.size()),
+                                                                       list, off, nch, slice_rows, slice_len, slice_q);
+      count_launch();
+      chk(cudaGetLastError());
+    }
+  }
+  if (e == cudaSuccess) {
+    chk(cudaMemsetAsync(slice_len + ns, 0, sizeof(int64_t), s));
+    chk(exclusive_scan(slice_len, slice_ptr, ns + 1, s));
+  }
+  int64_t total = 0;
+  if (e == cudaSuccess) {
+    chk(cudaMemcpyAsync(&total, slice_ptr + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    chk(cudaStreamSynchronize(s));
+  }
+  // 5. entries
+  int32_t* col = nullptr;
+  float2* val = nullptr;
+  chk(alloc(reinterpret_cast<void**>(&col), sizeof(int32_t) * (total > 0 ? total : 1)));
+  chk(alloc(reinterpret_cast<void**>(&val), sizeof(float2) * (total > 0 ? total : 1)));
+  if (e == cudaSuccess && ns > 0) {
+    const int64_t threads = ns * kSliceH;
+    k_fill<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(ns, slice_ptr, slice_rows, slice_q, rp, ci, va,
+                                                                         off, nch, C, ncols, col, val);
+    count_launch();
+    chk(cudaGetLastError());
+  }
+  // host copies for the layout query
+  if (e == cudaSuccess) {
+    out.slice_ptr.resize(ns + 1);
+    out.rows.resize(ns * kSliceH);
+    chk(cudaMemcpyAsync(out.slice_ptr.data(), slice_ptr, sizeof(int64_t) * (ns + 1), cudaMemcpyDeviceToHost, s));
+    if (ns > 0)
+      chk(cudaMemcpyAsync(out.rows.data(), slice_rows, sizeof(int32_t) * ns * kSliceH, cudaMemcpyDeviceToHost, s));
+    chk(cudaStreamSynchronize(s));
+  }
+  cudaFreeAsync(off, s);
+  cudaFreeAsync(flag, s);
+  cudaFreeAsync(pos, s);
+  cudaFreeAsync(list, s);
+  if (dwin) cudaFreeAsync(dwin, s);
+  if (dparts) cudaFreeAsync(dparts, s);
+  cudaFreeAsync(slice_len, s);
+  cudaFreeAsync(slice_q, s);
+  if (e != cudaSuccess) return e;
+  out.total = total;
+  out.slice_ptr_d = slice_ptr;
+  out.rows_d = slice_rows;
+  out.col_d = col;
+  out.val_d = val;
+  out.first_d = first;
+  out.last_d = last;
+  return cudaStreamSynchronize(s);
+}
+
+}  // namespace sppc

@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+#include <vector>
+
 namespace sppc {
 
 // Kernel launches issued by the library since load (every launch site counts).
@@ -60,6 +63,27 @@ struct BlockList {
   int n = 0;
 };
 
+// ---- sell_build.cu: the SELL-16 layout of H built on the GPU from its CSR on the
+// device (rp, ci, va), bit-identical to the host builder.  Persistent arrays come
+// from `alloc` (bytes); temporaries are stream-ordered allocations freed before
+// return.  Synchronises the stream.
+using DeviceAlloc = std::function<cudaError_t(void**, size_t)>;
+struct SellDeviceLayout {
+  int64_t nslices = 0, chunk_cols = 0, total = 0;
+  int nchunks = 1;
+  std::vector<int64_t> chunk_slice, slice_ptr;  // host copies
+  std::vector<int32_t> rows;                    // host copy
+  int64_t* slice_ptr_d = nullptr;
+  int32_t* rows_d = nullptr;
+  int32_t* col_d = nullptr;
+  float2* val_d = nullptr;
+  uint8_t* first_d = nullptr;
+  uint8_t* last_d = nullptr;
+};
+cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t ncols,
+                              const std::vector<int64_t>& seg, int64_t chunk_cols, cudaStream_t s,
+                              const DeviceAlloc& alloc, SellDeviceLayout& out);
+
 // ---- k_spmm.cu
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
 int spmm_default_grid();
@@ -68,6 +92,8 @@ int spmm_default_grid();
 // FP32 into X32 (n x 8 floats), Y = H X with FP32 values val32 (same SELL layout as
 // A) and FP32 accumulation, written as double-float with zero low words.
 cudaError_t spmm_f32(const SellDev& A, const float* val32, const float2* X, float* X32, float2* Y, cudaStream_t s);
+// out[i] = in[i].x (the FP32 high words of double-float values)
+cudaError_t df_hi_parts(const float2* in, float* out, int64_t count, cudaStream_t s);
 
 // ---- k_spmm_tma.cu (kp = 8; X 16-byte aligned)
 bool spmm_tma_available();
