@@ -21,7 +21,7 @@ namespace {
 
 // SELL-16: a warp owns a 16-row slice, two lanes per row (slice_rowsum); the
 // epilogue writes, accumulates (column tiles) or finishes Y.
-template <int KP>
+template <int KP, bool EPI>
 __global__ void __launch_bounds__(128) k_spmm_sell(SellDev A, int64_t s0, int64_t s1, int q,
                                                    const float2* __restrict__ X, float2* __restrict__ Y, Epi epi) {
   static_assert(KP % 2 == 0 && KP <= 8, "kp must be 2, 4, 6 or 8");
@@ -40,18 +40,16 @@ __global__ void __launch_bounds__(128) k_spmm_sell(SellDev A, int64_t s0, int64_
     const int64_t base = static_cast<int64_t>(row) * KP + off;
     // the first chunk of a row writes, later chunks accumulate, the last applies the epilogue
     const bool first = (A.nchunks == 1) || (A.row_first[row] == q);
-    const bool last = (A.nchunks == 1) || (A.row_last[row] == q);
+    const bool last = !EPI || (A.nchunks == 1) || (A.row_last[row] == q);
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
       float2 r = acc_get(ah[c], al[c]);
       if (!first) r = df_add(r, Y[base + c]);
-      if (!last) {
-        Y[base + c] = r;
-        continue;
+      if (EPI && last) {
+        if (epi.alpha) r = df_mul(epi.alpha[off + c], r);
+        if (epi.beta) r = df_add(r, df_mul(epi.beta[off + c], X[base + c]));
+        if (epi.gamma) r = df_add(r, df_mul(epi.gamma[off + c], epi.Z[base + c]));
       }
-      if (epi.alpha) r = df_mul(epi.alpha[off + c], r);
-      if (epi.beta) r = df_add(r, df_mul(epi.beta[off + c], X[base + c]));
-      if (epi.gamma) r = df_add(r, df_mul(epi.gamma[off + c], epi.Z[base + c]));
       Y[base + c] = r;
     }
   }
@@ -70,11 +68,7 @@ int spmm_default_grid() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_spmm_sell<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_spmm_sell<4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_spmm_sell<6>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_spmm_sell<8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell<8>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell<8, false>, 128, 0);
     if (per_sm < 1) per_sm = 1;
     g_grid = sms * per_sm;
   }
@@ -91,13 +85,20 @@ cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi
     if (s1 <= s0) continue;
     int64_t grid = (s1 - s0 + 3) / 4;
     if (grid > gmax) grid = gmax;
-    switch (kp) {
-      case 2: k_spmm_sell<2><<<(unsigned)grid, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); count_launch(); break;
-      case 4: k_spmm_sell<4><<<(unsigned)grid, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); count_launch(); break;
-      case 6: k_spmm_sell<6><<<(unsigned)grid, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); count_launch(); break;
-      case 8: k_spmm_sell<8><<<(unsigned)grid, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); count_launch(); break;
+    const bool has_epi = epi.alpha || epi.beta || epi.gamma;
+    const unsigned g = (unsigned)grid;
+    switch (kp * 2 + (has_epi ? 1 : 0)) {
+      case 4: k_spmm_sell<2, false><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
+      case 5: k_spmm_sell<2, true><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
+      case 8: k_spmm_sell<4, false><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
+      case 9: k_spmm_sell<4, true><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
+      case 12: k_spmm_sell<6, false><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
+      case 13: k_spmm_sell<6, true><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
+      case 16: k_spmm_sell<8, false><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
+      case 17: k_spmm_sell<8, true><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
       default: return cudaErrorInvalidValue;
     }
+    count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -59,22 +59,46 @@ __device__ __forceinline__ float2 ld_stream(const float2* p) {
   return v;
 }
 
+// Double-float multiply-add of one value v into two columns at once with packed
+// f32x2 arithmetic: the same operations, in the same order and rounding, as two
+// acc_mac calls (b - a is formed as fma(a, -1, b), rounded once like a
+// subtraction), so the sums are bit-identical, in half the instructions.
+__device__ __forceinline__ void acc_mac2(float2& sh, float2& sl, float2 v, float2 xc, float2 xd) {
+  const float2 vh = make_float2(v.x, v.x), vl = make_float2(v.y, v.y);
+  const float2 xh = make_float2(xc.x, xd.x), xl = make_float2(xc.y, xd.y);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 p = __fmul2_rn(vh, xh);
+  float2 e = __ffma2_rn(vh, xh, __fmul2_rn(p, m1));
+  e = __ffma2_rn(vh, xl, e);
+  e = __ffma2_rn(vl, xh, e);
+  const float2 sn = __fadd2_rn(sh, p);
+  const float2 bb = __ffma2_rn(sh, m1, sn);                        // sn - sh
+  const float2 d1 = __ffma2_rn(__ffma2_rn(bb, m1, sn), m1, sh);    // sh - (sn - bb)
+  const float2 d2 = __ffma2_rn(bb, m1, p);                         // p - bb
+  sh = sn;
+  sl = __fadd2_rn(sl, __fadd2_rn(__fadd2_rn(d1, d2), e));
+}
+
 // Row sums of slice s: lane pair (2*r, 2*r+1) owns row r of the slice, lane h
 // of the pair accumulates columns [h*kp/2, (h+1)*kp/2) into (ah, al).  Software
 // pipeline of depth 2 per lane: the X half rows of entries t+1 and t+2 are in
 // flight while entry t is accumulated; the loop is unrolled by three so the
 // three buffers rotate without register copies.  Entries are accumulated in
-// order and renormalised after every 16th, whatever the unrolling.
+// order and renormalised after every 16th, whatever the unrolling; column pairs
+// use the packed form (acc_mac2), an odd last column the scalar one.
 template <int KP>
 __device__ __forceinline__ void slice_rowsum(const SellDev& A, int64_t s, int rl, int off,
                                              const float2* __restrict__ X, uint64_t pol, float (&ah)[KP / 2],
                                              float (&al)[KP / 2]) {
   constexpr int CPL = KP / 2;
+  constexpr int NP = CPL / 2;  // column pairs
   constexpr int H = kSliceH;
   const int64_t end = A.slice_ptr[s + 1];
   int64_t e = A.slice_ptr[s] + rl;
+  float2 ph[NP > 0 ? NP : 1], pl[NP > 0 ? NP : 1];
 #pragma unroll
-  for (int c = 0; c < CPL; ++c) ah[c] = al[c] = 0.f;
+  for (int c = 0; c < NP; ++c) ph[c] = pl[c] = make_float2(0.f, 0.f);
+  float oh = 0.f, ol = 0.f;  // odd last column
   float2 x0[CPL], x1[CPL], x2[CPL];
   float2 v0 = make_float2(0.f, 0.f), v1 = v0, v2 = v0;
   auto fetch = [&](int64_t ee, float2 (&x)[CPL], float2& v) {
@@ -87,10 +111,15 @@ __device__ __forceinline__ void slice_rowsum(const SellDev& A, int64_t s, int rl
   int cnt = 0;
   auto mac = [&](const float2 (&x)[CPL], float2 v) {
 #pragma unroll
-    for (int c = 0; c < CPL; ++c) acc_mac(ah[c], al[c], v, x[c]);
+    for (int c = 0; c < NP; ++c) acc_mac2(ph[c], pl[c], v, x[2 * c], x[2 * c + 1]);
+    if constexpr (CPL % 2 == 1) acc_mac(oh, ol, v, x[CPL - 1]);
     if (((++cnt) & 15) == 0) {
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) acc_norm(ah[c], al[c]);
+      for (int c = 0; c < NP; ++c) {
+        acc_norm(ph[c].x, pl[c].x);
+        acc_norm(ph[c].y, pl[c].y);
+      }
+      if constexpr (CPL % 2 == 1) acc_norm(oh, ol);
     }
   };
   fetch(e, x0, v0);
@@ -104,6 +133,17 @@ __device__ __forceinline__ void slice_rowsum(const SellDev& A, int64_t s, int rl
     if (e + 2 * H >= end) break;
     fetch(e + 4 * H, x1, v1);
     mac(x2, v2);
+  }
+#pragma unroll
+  for (int c = 0; c < NP; ++c) {
+    ah[2 * c] = ph[c].x;
+    al[2 * c] = pl[c].x;
+    ah[2 * c + 1] = ph[c].y;
+    al[2 * c + 1] = pl[c].y;
+  }
+  if constexpr (CPL % 2 == 1) {
+    ah[CPL - 1] = oh;
+    al[CPL - 1] = ol;
   }
 }
 
