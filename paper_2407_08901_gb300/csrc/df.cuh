@@ -86,6 +86,26 @@ __device__ __forceinline__ void acc_add(float& sh, float& sl, float2 a) {
   sl = __fadd_rn(sl, __fadd_rn(err, a.y));
 }
 
+// Double-float multiply-add of one value v into two columns at once with packed
+// f32x2 arithmetic: the same operations, in the same order and rounding, as two
+// acc_mac calls (b - a is formed as fma(a, -1, b), rounded once like a
+// subtraction), so the sums are bit-identical, in half the instructions.
+__device__ __forceinline__ void acc_mac2(float2& sh, float2& sl, float2 v, float2 xc, float2 xd) {
+  const float2 vh = make_float2(v.x, v.x), vl = make_float2(v.y, v.y);
+  const float2 xh = make_float2(xc.x, xd.x), xl = make_float2(xc.y, xd.y);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 p = __fmul2_rn(vh, xh);
+  float2 e = __ffma2_rn(vh, xh, __fmul2_rn(p, m1));
+  e = __ffma2_rn(vh, xl, e);
+  e = __ffma2_rn(vl, xh, e);
+  const float2 sn = __fadd2_rn(sh, p);
+  const float2 bb = __ffma2_rn(sh, m1, sn);                        // sn - sh
+  const float2 d1 = __ffma2_rn(__ffma2_rn(bb, m1, sn), m1, sh);    // sh - (sn - bb)
+  const float2 d2 = __ffma2_rn(bb, m1, p);                         // p - bb
+  sh = sn;
+  sl = __fadd2_rn(sl, __fadd2_rn(__fadd2_rn(d1, d2), e));
+}
+
 __device__ __forceinline__ void acc_norm(float& sh, float& sl) {
   const float2 t = fast_two_sum(sh, sl);
   sh = t.x;

@@ -21,8 +21,10 @@ namespace {
 
 // SELL-16: a warp owns a 16-row slice, two lanes per row (slice_rowsum); the
 // epilogue writes, accumulates (column tiles) or finishes Y.
+// Seven resident CTAs per SM (<= 73 registers): measured fastest for the
+// 8-column instance (a 64-register cap spills and is 6% slower).
 template <int KP, bool EPI>
-__global__ void __launch_bounds__(128) k_spmm_sell(SellDev A, int64_t s0, int64_t s1, int q,
+__global__ void __launch_bounds__(128, 7) k_spmm_sell(SellDev A, int64_t s0, int64_t s1, int q,
                                                    const float2* __restrict__ X, float2* __restrict__ Y, Epi epi) {
   static_assert(KP % 2 == 0 && KP <= 8, "kp must be 2, 4, 6 or 8");
   constexpr int CPL = KP / 2;

@@ -59,26 +59,6 @@ __device__ __forceinline__ float2 ld_stream(const float2* p) {
   return v;
 }
 
-// Double-float multiply-add of one value v into two columns at once with packed
-// f32x2 arithmetic: the same operations, in the same order and rounding, as two
-// acc_mac calls (b - a is formed as fma(a, -1, b), rounded once like a
-// subtraction), so the sums are bit-identical, in half the instructions.
-__device__ __forceinline__ void acc_mac2(float2& sh, float2& sl, float2 v, float2 xc, float2 xd) {
-  const float2 vh = make_float2(v.x, v.x), vl = make_float2(v.y, v.y);
-  const float2 xh = make_float2(xc.x, xd.x), xl = make_float2(xc.y, xd.y);
-  const float2 m1 = make_float2(-1.f, -1.f);
-  const float2 p = __fmul2_rn(vh, xh);
-  float2 e = __ffma2_rn(vh, xh, __fmul2_rn(p, m1));
-  e = __ffma2_rn(vh, xl, e);
-  e = __ffma2_rn(vl, xh, e);
-  const float2 sn = __fadd2_rn(sh, p);
-  const float2 bb = __ffma2_rn(sh, m1, sn);                        // sn - sh
-  const float2 d1 = __ffma2_rn(__ffma2_rn(bb, m1, sn), m1, sh);    // sh - (sn - bb)
-  const float2 d2 = __ffma2_rn(bb, m1, p);                         // p - bb
-  sh = sn;
-  sl = __fadd2_rn(sl, __fadd2_rn(__fadd2_rn(d1, d2), e));
-}
-
 // Row sums of slice s: lane pair (2*r, 2*r+1) owns row r of the slice, lane h
 // of the pair accumulates columns [h*kp/2, (h+1)*kp/2) into (ah, al).  Software
 // pipeline of depth 2 per lane: the X half rows of entries t+1 and t+2 are in
