@@ -313,33 +313,49 @@ def run_ours(args):
                                   for kk in ("spmm_ms", "minres_ms", "small_eig_ms", "dense_ms", "total_ms")},
     }
     if rank == 0 and world == 1 and not args.no_mixed:
-        # mixed precision (H rounded to FP32, FP32 products with H during the solve,
-        # double-float elsewhere, double-float products at the end): one solve timed
-        # with CUDA events, eigenvalues against this run's FP64 solve of the
-        # unrounded H (the difference is the FP32 quantisation of H's values)
-        mopts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL, timing=1,
-                                    precond=PRECOND, precond_iters=PRECOND_ITERS, precision=1)
-        hm = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, mopts, stream=stream)
-        mt = []
-        for _ in range(2):
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-                m0 = torch.cuda.Event(enable_timing=True)
-                m1 = torch.cuda.Event(enable_timing=True)
-                m0.record(stream)
-                mconv, mth, mrs, mst = S.sppc_solve(hm, k, tol=TOL, stream=stream)
-                m1.record(stream)
-            torch.cuda.synchronize()
-            mt.append(m0.elapsed_time(m1) / 1e3)
-        line["mixed_precision"] = {
-            "method": "H values rounded to FP32; FP32 products with H (FP32 X, FP32 accumulation) until the "
-                      "residual estimates reach 1e-6, then a restart with double-float products; Gram, "
-                      "CholeskyQR2, projected eigensolve and MINRES in double-float",
-            "value": mt[-1], "unit": "s", "spmv_h": mst["spmv_h"], "converged": bool(mconv),
-            "max_scaled_resid": float(np.max(mrs)), "spmm_ms": mst["spmm_ms"],
-            "max_rel_theta_diff_vs_fp64_unrounded": float(np.max(np.abs(np.asarray(mth) - np.asarray(th_last))
-                                                                 / np.abs(np.asarray(th_last))))}
-        S.sppc_destroy(hm)
+        # mixed precision (H rounded to FP32, or off-diagonals to BF16; FP32 products
+        # with H during the solve, double-float elsewhere, double-float products at
+        # the end): one solve timed with CUDA events.  Eigenvalues against an FP64
+        # solve of the same rounded matrix (the solver error) and against this run's
+        # FP64 solve of the unrounded H (the quantisation of H's values).
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        f32 = v.astype(np.float32)
+        u = f32.view(np.uint32).astype(np.uint64)
+        bf = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32).view(np.float32)
+        rounded = {1: f32.astype(np.float64), 2: np.where(rows == c, f32, bf).astype(np.float64)}
+        del rows, u, bf
+        for prec, key, desc in ((1, "mixed_precision", "H values rounded to FP32"),
+                                (2, "mixed_precision_bf16", "off-diagonal values rounded to BF16 (diagonal FP32)")):
+            mopts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL, timing=1,
+                                        precond=PRECOND, precond_iters=PRECOND_ITERS, precision=prec)
+            hm = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, mopts, stream=stream)
+            mt = []
+            for _ in range(2):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1.0)
+                    m0 = torch.cuda.Event(enable_timing=True)
+                    m1 = torch.cuda.Event(enable_timing=True)
+                    m0.record(stream)
+                    mconv, mth, mrs, mst = S.sppc_solve(hm, k, tol=TOL, stream=stream)
+                    m1.record(stream)
+                torch.cuda.synchronize()
+                mt.append(m0.elapsed_time(m1) / 1e3)
+            S.sppc_destroy(hm)
+            ropts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL,
+                                        precond=PRECOND, precond_iters=PRECOND_ITERS)
+            hr = S.sppc_create(rp, c, rounded[prec], w.level_offsets, w.small_dim, k, ropts, stream=stream)
+            _, rth, _, _ = S.sppc_solve(hr, k, tol=TOL, stream=stream)
+            S.sppc_destroy(hr)
+            mth, rth, th0 = np.asarray(mth), np.asarray(rth), np.asarray(th_last)
+            line[key] = {
+                "method": desc + "; FP32 products with H (FP32 X, FP32 accumulation) until the residual "
+                          "estimates reach 1e-6, then a restart with double-float products; Gram, CholeskyQR2, "
+                          "projected eigensolve and MINRES in double-float",
+                "value": mt[-1], "unit": "s", "spmv_h": mst["spmv_h"], "converged": bool(mconv),
+                "max_scaled_resid": float(np.max(mrs)), "spmm_ms": mst["spmm_ms"],
+                "max_rel_theta_err_vs_fp64_same_rounded_matrix": float(np.max(np.abs(mth - rth) / np.abs(rth))),
+                "max_rel_theta_diff_vs_fp64_unrounded": float(np.max(np.abs(mth - th0) / np.abs(th0)))}
+        del rounded
     if rank == 0 and world == 1 and not args.no_comparator:
         # C2's comparator: block Lanczos from Psi^(0) (the same loop, no SPPC orders,
         # no preconditioner), one untimed-loop solve timed with CUDA events

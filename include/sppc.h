@@ -103,7 +103,10 @@ typedef struct {
                               eigensolve and MINRES in double-float; at the end the Ritz values and
                               residuals are recomputed with double-float products (Rayleigh
                               quotients) and the continuation goes on with double-float products
-                              if they miss tol.  Needs k = 7 or 8. */
+                              if they miss tol.  2: as 1 with BF16 values: off-diagonal values
+                              rounded to FP32 and then to BF16 (nearest, ties to even), the
+                              diagonal to FP32, everywhere; the FP32 products read the BF16 values
+                              (2 bytes per entry) and the FP32 diagonal.  1 and 2 need k = 7 or 8. */
 } sppc_opts;
 
 typedef struct {

@@ -103,6 +103,8 @@ struct sppc_ctx {
   float2* dDiag = nullptr;                        // diag(H), double-float (Jacobi preconditioner)
   float* val32 = nullptr;                         // FP32 copy of H's SELL values (mixed precision)
   float* X32 = nullptr;                           // FP32 copy of the SpMM input block (mixed precision)
+  uint16_t* val16 = nullptr;                      // BF16 off-diagonal values (precision 2)
+  float* diag32 = nullptr;                        // FP32 diagonal (precision 2)
   bool f32_products = false;                      // big SpMMs in FP32 (mixed precision, until verified)
   int nev = 0;                                    // Ritz pairs kept by the last Rayleigh-Ritz
 
@@ -333,6 +335,18 @@ void split_df(double x, float2& out) {
   out.y = static_cast<float>(x - static_cast<double>(h));
 }
 
+// FP32 -> nearest BF16 (ties to even), returned as FP32; finite inputs only
+// (an input whose rounding overflows becomes Inf and is rejected by validation)
+float round_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
 // Rows [0, nrows), columns [0, ncols) cut into chunks of chunk_cols columns
 // (chunk_cols <= 0: one chunk).  For every chunk, inside every segment (level)
 // `seg`, the rows with entries in the chunk are sorted by decreasing entry count
@@ -520,7 +534,7 @@ sppc_status big_spmm(sppc_ctx* h, const float2* X, float2* Y, int kp) {
     CK(cudaEventRecord(a, h->stream));
   }
   if (h->f32_products && kp == 8)
-    CK(spmm_f32(h->H, h->val32, X, h->X32, Y, h->stream));
+    CK(spmm_f32(h->H, h->val32, h->val16, h->diag32, X, h->X32, Y, h->stream));
   else
     CK(spmm(h->H, kp, X, Y, Epi{}, h->stream));
   if (h->opt.timing) {
@@ -1127,9 +1141,9 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.spmm_kernel != 0 && opt.spmm_kernel != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.spmm_kernel must be 0 or 1");
   if (opt.reorth != 0 && opt.reorth != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.reorth must be 0 or 1");
   if (opt.precond < 0 || opt.precond > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precond must be 0, 1 or 2");
-  if (opt.precision != 0 && opt.precision != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.precision must be 0 or 1");
-  if (opt.precision == 1 && (k + 1) / 2 * 2 != 8)
-    return fail(nullptr, SPPC_ERR_ARG, "opts.precision = 1 needs k = 7 or 8 (8-column FP32 products)");
+  if (opt.precision < 0 || opt.precision > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precision must be 0, 1 or 2");
+  if (opt.precision != 0 && (k + 1) / 2 * 2 != 8)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k = 7 or 8 (8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precond_iters must be in [0, 10000]");
 
@@ -1176,6 +1190,21 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     if (va_h.empty()) va_h.assign(va, va + Hc->nnz);
 #pragma omp parallel for schedule(static)
     for (int64_t t = 0; t < Hc->nnz; ++t) va_h[t] = static_cast<double>(static_cast<float>(va_h[t]));
+    va = va_h.data();
+  } else if (opt.precision == 2) {
+    // BF16 path: off-diagonal values rounded to FP32 and then to BF16 (round to
+    // nearest even), the diagonal to FP32, everywhere; the solver's error is
+    // measured against that matrix
+    if (va_h.empty()) va_h.assign(va, va + Hc->nnz);
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n; ++r) {
+      const int64_t lo = rp[r], hi = rp[r + 1];
+      if (lo < 0 || hi < lo || hi > Hc->nnz) continue;  // rejected by the validation below
+      for (int64_t t = lo; t < hi; ++t) {
+        const float f = static_cast<float>(va_h[t]);
+        va_h[t] = ci[t] == r ? static_cast<double>(f) : static_cast<double>(round_bf16(f));
+      }
+    }
     va = va_h.data();
   }
   // validation
@@ -1284,6 +1313,13 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       if (e == cudaSuccess) e = df_hi_parts(L.val_d, h->val32, L.total, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_OOM, "FP32 values: %s", cudaGetErrorString(e)));
+    } else if (opt.precision == 2) {
+      // BF16 copy of the off-diagonal values (exact: they are BF16 already)
+      e = dalloc(h, &h->val16, (size_t)(L.total > 0 ? L.total : 1));
+      if (e == cudaSuccess) e = dalloc(h, &h->X32, (size_t)n * 8);
+      if (e == cudaSuccess) e = make_val16(h->H, h->val16, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_OOM, "BF16 values: %s", cudaGetErrorString(e)));
     }
     h->h_slices = L.nslices;
     h->h_slice_ptr = std::move(L.slice_ptr);
@@ -1314,6 +1350,11 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     }
     cudaError_t e = dalloc(h, &h->dDiag, (size_t)n);
     if (e == cudaSuccess) e = cudaMemcpy(h->dDiag, dg.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && opt.precision == 2) {
+      e = dalloc(h, &h->diag32, (size_t)n);
+      if (e == cudaSuccess) e = df_hi_parts(h->dDiag, h->diag32, n, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
     if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_OOM, "diag upload failed: %s", cudaGetErrorString(e)));
   }
   // work buffers
@@ -1382,8 +1423,8 @@ sppc_status sppc_spmm(sppc_handle h, const double* X, int64_t ldx, double* Y, in
   h->stream = s;
   const int kp = (ncols + 1) / 2 * 2;
   CK(f64_to_df(X, ldx, ncols, h->T1, kp, 0, h->n, s));
-  if (h->opt.precision == 1 && kp == 8)
-    CK(spmm_f32(h->H, h->val32, h->T1, h->X32, h->T2, s));
+  if (h->opt.precision != 0 && kp == 8)
+    CK(spmm_f32(h->H, h->val32, h->val16, h->diag32, h->T1, h->X32, h->T2, s));
   else
     CK(spmm(h->H, kp, h->T1, h->T2, Epi{}, s));
   CK(df_to_f64(h->T2, kp, Y, ldy, ncols, 0, h->n, s));
@@ -1641,7 +1682,7 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     cudaEventCreate(&t1);
     cudaEventRecord(t0, s);
   }
-  h->f32_products = (h->opt.precision == 1);
+  h->f32_products = (h->opt.precision != 0);
   CKS(sppc_start(h, nullptr, nullptr, stream));
   bool conv = all_converged(h, tol);
   const int sppc_orders = h->opt.hybrid ? std::min(p_max, h->opt.switch_order) : p_max;
@@ -1676,7 +1717,7 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     }
     conv = all_converged(h, tol);
   }
-  const bool fresh = h->opt.precision == 1 && h->opt.hybrid && h->p >= 1 && h->nev >= 2 * h->k;
+  const bool fresh = h->opt.precision != 0 && h->opt.hybrid && h->p >= 1 && h->nev >= 2 * h->k;
   h->f32_products = false;
   if (fresh) {
     // Mixed precision: the residuals of the FP32 phase are estimates and its W
@@ -1694,7 +1735,7 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     }
   }
   if (Z) CKS(rr_core(h, h->p, true, Z, ldz));
-  if (h->opt.precision == 1 && !fresh) {
+  if (h->opt.precision != 0 && !fresh) {
     // plain SPPC in mixed precision: Rayleigh quotients and residuals of the Ritz
     // vectors from double-float products
     CKS(verify_df(h));

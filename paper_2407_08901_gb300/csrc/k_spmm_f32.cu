@@ -6,6 +6,9 @@
 // request count, not the bytes, sets the pace.)
 // The result is written into a double-float block (low word zero) so that the
 // double-float kernels downstream read it unchanged.
+// BF16 variant: off-diagonal values stored as BF16 (2 bytes per entry, the
+// diagonal entries stored as 0), the diagonal kept in FP32 and applied once per
+// row in the epilogue of the row's first column tile.
 #include "spmm_core.cuh"
 
 namespace sppc {
@@ -18,12 +21,22 @@ __device__ __forceinline__ float ld_stream_f(const float* p) {
   return v;
 }
 
+// BF16 bits -> FP32 (exact: BF16 is the upper half of an FP32 word)
+__device__ __forceinline__ float ld_stream_bf16(const uint16_t* p) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return __uint_as_float(static_cast<uint32_t>(v) << 16);
+}
+
 // One lane per row: the 8 FP32 columns of an X row are one 32-byte gather, and a
 // warp covers two 16-row slices (one per half-warp).  Depth-2 pipeline per lane
 // (entries t+1, t+2 in flight while t is accumulated), unrolled by three so the
 // buffers rotate without copies.
-__global__ void __launch_bounds__(128) k_spmm_sell_f32r(SellDev A, const float* __restrict__ val32, int64_t s0,
-                                                        int64_t s1, int q, const float* __restrict__ X,
+template <bool BF>
+__global__ void __launch_bounds__(128) k_spmm_sell_f32r(SellDev A, const float* __restrict__ val32,
+                                                        const uint16_t* __restrict__ val16,
+                                                        const float* __restrict__ diag32, int64_t s0, int64_t s1,
+                                                        int q, const float* __restrict__ X,
                                                         float2* __restrict__ Y) {
   constexpr int H = kSliceH;
   const int lane = threadIdx.x & 31;
@@ -43,7 +56,7 @@ __global__ void __launch_bounds__(128) k_spmm_sell_f32r(SellDev A, const float* 
     auto fetch = [&](int64_t ee, float4& a, float4& b, float& v) {
       if (ee < end) {
         const int c = ld_stream(A.col + ee);
-        v = ld_stream_f(val32 + ee);
+        v = BF ? ld_stream_bf16(val16 + ee) : ld_stream_f(val32 + ee);
         const float* p = X + static_cast<int64_t>(c) * 8;
         asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
                      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
@@ -72,6 +85,12 @@ __global__ void __launch_bounds__(128) k_spmm_sell_f32r(SellDev A, const float* 
     if (row < 0) continue;
     float2* y = Y + static_cast<int64_t>(row) * 8;
     const bool first = (A.nchunks == 1) || (A.row_first[row] == q);
+    if (BF && first) {
+      const float d = diag32[row];
+      const float4 xa = *reinterpret_cast<const float4*>(X + static_cast<int64_t>(row) * 8);
+      const float4 xb = *reinterpret_cast<const float4*>(X + static_cast<int64_t>(row) * 8 + 4);
+      mac(xa, xb, d);
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) y[c] = make_float2(first ? acc[c] : __fadd_rn(acc[c], y[c].x), 0.f);
   }
@@ -83,9 +102,32 @@ __global__ void k_df_hi(const float2* __restrict__ X, float* __restrict__ X32, i
   if (i < count) X32[i] = X[i].x;
 }
 
-int g_grid32 = 0;
+// BF16 copy of the SELL values: entry e of slice s belongs to slice row
+// (e - slice_ptr[s]) mod 16; diagonal entries become 0 (applied from diag32).
+// The values must already be BF16-exact (their double-float high words).
+__global__ void k_make_val16(SellDev A, uint16_t* __restrict__ val16) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t s = t >> 4;
+  const int l = static_cast<int>(t & 15);
+  if (s >= A.nslices) return;
+  const int row = A.slice_rows[s * kSliceH + l];
+  for (int64_t e = A.slice_ptr[s] + l; e < A.slice_ptr[s + 1]; e += kSliceH) {
+    const bool dg = row >= 0 && A.col[e] == row;
+    val16[e] = dg ? 0 : static_cast<uint16_t>(__float_as_uint(A.val[e].x) >> 16);
+  }
+}
+
+int g_grid32[2] = {0, 0};
 
 }  // namespace
+
+cudaError_t make_val16(const SellDev& A, uint16_t* val16, cudaStream_t s) {
+  if (A.nslices == 0) return cudaSuccess;
+  const int64_t threads = A.nslices * kSliceH;
+  k_make_val16<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(A, val16);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t df_hi_parts(const float2* in, float* out, int64_t count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
@@ -94,15 +136,25 @@ cudaError_t df_hi_parts(const float2* in, float* out, int64_t count, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t spmm_f32(const SellDev& A, const float* val32, const float2* X, float* X32, float2* Y, cudaStream_t s) {
+cudaError_t spmm_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
+                     const float2* X, float* X32, float2* Y, cudaStream_t s) {
   if (A.nslices == 0) return cudaSuccess;
-  if (g_grid32 == 0) {
+  const bool bf = val16 != nullptr;
+  if (bf && !diag32) return cudaErrorInvalidValue;
+  if (!bf && !val32) return cudaErrorInvalidValue;
+  int& gmax = g_grid32[bf ? 1 : 0];
+  if (gmax == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_spmm_sell_f32r, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell_f32r, 128, 0);
-    g_grid32 = sms * (per_sm < 1 ? 1 : per_sm);
+    if (bf) {
+      cudaFuncSetAttribute(k_spmm_sell_f32r<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell_f32r<true>, 128, 0);
+    } else {
+      cudaFuncSetAttribute(k_spmm_sell_f32r<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell_f32r<false>, 128, 0);
+    }
+    gmax = sms * (per_sm < 1 ? 1 : per_sm);
   }
   const int64_t count = A.nrows * 8;
   k_df_hi<<<static_cast<unsigned>((count + 255) / 256), 256, 0, s>>>(X, X32, count);
@@ -114,8 +166,11 @@ cudaError_t spmm_f32(const SellDev& A, const float* val32, const float2* X, floa
     const int64_t c1 = A.nchunks == 1 ? A.nslices : A.chunk_slice[q + 1];
     if (c1 <= c0) continue;
     int64_t grid = (c1 - c0 + 7) / 8;  // 4 warps x 2 slices per CTA
-    if (grid > g_grid32) grid = g_grid32;
-    k_spmm_sell_f32r<<<static_cast<unsigned>(grid), 128, 0, s>>>(A, val32, c0, c1, q, X32, Y);
+    if (grid > gmax) grid = gmax;
+    if (bf)
+      k_spmm_sell_f32r<true><<<static_cast<unsigned>(grid), 128, 0, s>>>(A, val32, val16, diag32, c0, c1, q, X32, Y);
+    else
+      k_spmm_sell_f32r<false><<<static_cast<unsigned>(grid), 128, 0, s>>>(A, val32, val16, diag32, c0, c1, q, X32, Y);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -90,8 +90,13 @@ int spmm_default_grid();
 
 // ---- k_spmm_f32.cu (mixed precision, 8 columns): X (double-float) rounded to
 // FP32 into X32 (n x 8 floats), Y = H X with FP32 values val32 (same SELL layout as
-// A) and FP32 accumulation, written as double-float with zero low words.
-cudaError_t spmm_f32(const SellDev& A, const float* val32, const float2* X, float* X32, float2* Y, cudaStream_t s);
+// A) and FP32 accumulation, written as double-float with zero low words.  With
+// val16 != nullptr the values are BF16 (diagonal entries 0) and diag32 holds the
+// FP32 diagonal; val32 is then unused.
+cudaError_t spmm_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
+                     const float2* X, float* X32, float2* Y, cudaStream_t s);
+// val16[e] = BF16 bits of A.val[e].x (BF16-exact values), 0 for diagonal entries
+cudaError_t make_val16(const SellDev& A, uint16_t* val16, cudaStream_t s);
 // out[i] = in[i].x (the FP32 high words of double-float values)
 cudaError_t df_hi_parts(const float2* in, float* out, int64_t count, cudaStream_t s);
 
