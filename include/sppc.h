@@ -107,6 +107,13 @@ typedef struct {
                               rounded to FP32 and then to BF16 (nearest, ties to even), the
                               diagonal to FP32, everywhere; the FP32 products read the BF16 values
                               (2 bytes per entry) and the FP32 diagonal.  1 and 2 need k = 7 or 8. */
+  int32_t proposal;        /* 0: none (default).  1: learned correction proposal (not in the paper):
+                              each continuation step extends the basis by the network's block
+                              g_j = (r_j / (diag(H) - theta_j)) (1 + m_j) instead of the plain
+                              preconditioned residuals (leading n1 rows still from the precond 2
+                              solve); kept iff the largest scaled residual drops, else the step is
+                              redone with the plain block.  Needs hybrid = 1, precond 1 or 2 and
+                              sppc_set_proposal before the solve. */
 } sppc_opts;
 
 typedef struct {
@@ -128,6 +135,8 @@ typedef struct {
   int32_t reorth_passes;     /* appended blocks that needed the second Gram-Schmidt pass */
   int32_t refine_df;         /* mixed precision: continuation steps run with double-float products
                                 after the FP32 phase */
+  int32_t proposals_tried;   /* learned proposal: continuation steps that tried the network's block */
+  int32_t proposals_kept;    /* ... and kept it (the largest scaled residual dropped) */
 } sppc_stats;
 
 /* Fill `o` with the defaults listed above. */
@@ -229,7 +238,9 @@ sppc_status sppc_get_stats(sppc_handle h, sppc_stats* stats);
 /* Copies of internal state for tests (host buffers, FP64):
  *   which = 0: psi_hat, n1 x k;   1: Q, n x m (m = k * (orders+1));   2: W = H Q, n x m;
  *           3: projected matrix, m x m;   4: Psi^(p) of the last order, n x k;
- *           5: E^(0), k.
+ *           5: E^(0), k;   6: the learned proposal's block of the last continuation step,
+ *           n x k;   7: the plain preconditioned block of that step, n x k (its leading n1
+ *           rows from the precond 2 solve; after sppc_proposal_samples: the raw residuals).
  * `count` is the number of doubles the buffer holds; returns SPPC_ERR_ARG if too small. */
 sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t count);
 
@@ -252,6 +263,69 @@ sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr
  * on `stream`; SPPC_ERR_ARG on bad sizes.  All buffers are caller-owned. */
 sppc_status sppc_small_syev(const double* S, int32_t m, int32_t lds, int32_t nev, double* theta, double* V,
                             int32_t ldv, void* stream);
+
+/* ---- Learned correction proposal (not in the paper; the continuation of
+ * Sec. 5-6 extended by a network's block).  Network: per (row i, Ritz pair j),
+ * features f = (H_ii, level(i), ||H_i,:||_2, rhat_ij = r_ij sqrt(n)/||r_j||, theta_j,
+ * (|H| |rhat_j|)_i), x = (f - mu) / sd, h1 = gelu(W1 x + b1), h2 = gelu(W2 h1 + b2),
+ * m = w3 . h2 + b3 (64 hidden units, tanh-form GELU).  Parameters: one FP32
+ * vector of SPPC_NET_PARAMS values, W1 (64 x 6 row-major), b1 (64), W2 (64 x 64,
+ * W2[o][i] at o*64 + i), b2 (64), w3 (64), b3.  Training minimises
+ * mean (rhat (1 + m) - y)^2 with y the exact correction in rhat's scale (see
+ * sppc_proposal_samples). */
+#define SPPC_NET_PARAMS 4673
+#define SPPC_NET_FEATURES 6
+
+/* Install a trained network in h (host arrays: params[SPPC_NET_PARAMS], mu[6],
+ * sd[6] > 0), copied into library memory; the solve then uses BF16 inference
+ * (weights, inputs and hidden activations rounded to BF16, FP32 sums).
+ * SPPC_ERR_ARG on non-finite values or sd <= 0. */
+sppc_status sppc_set_proposal(sppc_handle h, const float* params, const float* mu, const float* sd);
+
+/* Training samples from h's current Rayleigh-Ritz state (after sppc_start or
+ * sppc_rayleigh_ritz) and exact eigenvectors psi (device, n x k row-major, leading
+ * dimension ldpsi >= k, column j the converged eigenvector of pair j): for rows
+ * i >= n1 and pairs j < k, sample s = (i - n1) k + j gets raw features F[s*6 + f]
+ * (device float), rhat[s] and target y[s] = -(H_ii - theta_j) t_ij sqrt(n)/||r_j||,
+ * t_j = psi_j / (z_j^T psi_j) - z_j the exact correction of the Ritz vector z_j
+ * (denominator clamped as by precond_clamp).  *count = (n - n1) k.  Does not change
+ * the SPPC state.  Synchronises `stream`. */
+sppc_status sppc_proposal_samples(sppc_handle h, const double* psi, int64_t ldpsi, float* F, float* rhat, float* y,
+                                  int64_t* count, void* stream);
+
+/* Network output m for `count` standardised samples X (device, count x 6) into
+ * out (device); bf16 != 0 selects the solve's BF16 inference, else FP32.
+ * Asynchronous on `stream`. */
+sppc_status sppc_mlp_forward(const float* params, const float* X, int64_t count, int32_t bf16, float* out,
+                             void* stream);
+
+/* FP32 loss L = mean_s (rhat_s (1 + m_s) - y_s)^2 over `count` samples (device
+ * X count x 6 standardised, rhat, y) and its gradient grad[SPPC_NET_PARAMS]
+ * (device); *loss (device, may be NULL).  Deterministic (fixed summation order).
+ * Synchronises `stream`. */
+sppc_status sppc_mlp_loss_grad(const float* params, const float* X, const float* rhat, const float* y, int64_t count,
+                               float* grad, float* loss, void* stream);
+
+/* One Adam step (Kingma and Ba 2015) with bias correction, step number t >= 1:
+ * mom, vel (device, SPPC_NET_PARAMS each) updated in place with params. */
+sppc_status sppc_mlp_adam(float* params, float* mom, float* vel, const float* grad, int32_t t, float lr, float beta1,
+                          float beta2, float eps, void* stream);
+
+/* One epoch: minibatches of `batch` samples in the order perm[0..nsamples)
+ * (device int64, NULL = 0, 1, 2, ...), each a gradient (mean over the batch) and
+ * an Adam step; *step counts Adam steps (in/out); *mean_loss (host) = mean of the
+ * batch losses.  Synchronises `stream`. */
+sppc_status sppc_mlp_train_epoch(float* params, float* mom, float* vel, const float* X, const float* rhat,
+                                 const float* y, const int64_t* perm, int64_t nsamples, int32_t batch, int32_t* step,
+                                 float lr, float beta1, float beta2, float eps, double* mean_loss, void* stream);
+
+/* Per-feature mean and (population) spread of `count` raw samples F (device,
+ * count x 6) into host mean[6], sd[6] (FP64 sums).  Synchronises `stream`. */
+sppc_status sppc_feature_moments(const float* F, int64_t count, double* mean, double* sd, void* stream);
+
+/* X = (F - mu) / sd per feature (F, X device count x 6; mu, sd host, sd > 0). */
+sppc_status sppc_standardize(const float* F, int64_t count, const float* mu, const float* sd, float* X,
+                             void* stream);
 
 /* Release everything the handle owns.  NULL is a no-op. */
 sppc_status sppc_destroy(sppc_handle h);

@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
                 ("hybrid", ctypes.c_int32), ("switch_order", ctypes.c_int32), ("hybrid_maxit", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precond_clamp", ctypes.c_double), ("hybrid_blocks", ctypes.c_int32),
                 ("spmm_kernel", ctypes.c_int32), ("reorth", ctypes.c_int32), ("precond_iters", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("proposal", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("spmm_launches", ctypes.c_int32), ("spmm_ms", ctypes.c_double), ("minres_ms", ctypes.c_double),
                 ("small_eig_ms", ctypes.c_double), ("dense_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("restarts", ctypes.c_int32), ("switched_at", ctypes.c_int32),
-                ("reorth_passes", ctypes.c_int32), ("refine_df", ctypes.c_int32)]
+                ("reorth_passes", ctypes.c_int32), ("refine_df", ctypes.c_int32),
+                ("proposals_tried", ctypes.c_int32), ("proposals_kept", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -85,7 +86,18 @@ _SIGS = {
     "sppc_last_error": (ctypes.c_char_p, [_VP]),
     "sppc_kernel_launches": (_I64, []),
     "sppc_small_syev": (_I32, [_VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP]),
+    "sppc_set_proposal": (_I32, [_VP, _VP, _VP, _VP]),
+    "sppc_proposal_samples": (_I32, [_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
+    "sppc_mlp_forward": (_I32, [_VP, _VP, _I64, _I32, _VP, _VP]),
+    "sppc_mlp_loss_grad": (_I32, [_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    "sppc_mlp_adam": (_I32, [_VP, _VP, _VP, _VP, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, _VP]),
+    "sppc_mlp_train_epoch": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I64, _I32, _VP, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP, _VP]),
+    "sppc_feature_moments": (_I32, [_VP, _I64, _VP, _VP, _VP]),
+    "sppc_standardize": (_I32, [_VP, _I64, _VP, _VP, _VP, _VP]),
 }
+NET_PARAMS, NET_FEATURES = 4673, 6
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
 
@@ -265,6 +277,86 @@ def sppc_small_syev(S, nev: int, stream=None):
     _check(None, _lib.sppc_small_syev(S.data_ptr(), m, m, int(nev), theta.data_ptr(), V.data_ptr(), int(nev),
                                       _stream(stream)))
     return theta, V
+
+
+def _f32_dev(t, n=None):
+    assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous(), "contiguous CUDA tensor expected"
+    if n is not None:
+        assert t.numel() >= n
+    return t.data_ptr()
+
+
+def sppc_set_proposal(h, params: np.ndarray, mu: np.ndarray, sd: np.ndarray) -> None:
+    """Install a trained proposal network (host float32 arrays)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    m = np.ascontiguousarray(mu, dtype=np.float32)
+    d = np.ascontiguousarray(sd, dtype=np.float32)
+    assert p.size == NET_PARAMS and m.size == NET_FEATURES and d.size == NET_FEATURES
+    _check(h, _lib.sppc_set_proposal(h, p.ctypes.data, m.ctypes.data, d.ctypes.data))
+
+
+def sppc_proposal_samples(h, psi, F, rhat, y, stream=None) -> int:
+    """Training samples of the current Rayleigh-Ritz state against exact
+    eigenvectors psi (CUDA float64 (n, >=k)); F (count x 6), rhat, y CUDA float32."""
+    assert psi.is_cuda and psi.dtype.__str__() == "torch.float64" and psi.stride(1) == 1
+    cnt = ctypes.c_int64()
+    _check(h, _lib.sppc_proposal_samples(h, psi.data_ptr(), psi.stride(0), _f32_dev(F), _f32_dev(rhat), _f32_dev(y),
+                                         ctypes.byref(cnt), _stream(stream)))
+    return int(cnt.value)
+
+
+def sppc_mlp_forward(params, X, out, bf16: bool = False, stream=None) -> None:
+    n = int(X.shape[0])
+    _check(None, _lib.sppc_mlp_forward(_f32_dev(params, NET_PARAMS), _f32_dev(X, 6 * n), n, 1 if bf16 else 0,
+                                       _f32_dev(out, n), _stream(stream)))
+
+
+def sppc_mlp_loss_grad(params, X, rhat, y, grad, loss, stream=None) -> None:
+    n = int(X.shape[0])
+    _check(None, _lib.sppc_mlp_loss_grad(_f32_dev(params, NET_PARAMS), _f32_dev(X, 6 * n), _f32_dev(rhat, n),
+                                         _f32_dev(y, n), n, _f32_dev(grad, NET_PARAMS), _f32_dev(loss, 1),
+                                         _stream(stream)))
+
+
+def sppc_mlp_adam(params, mom, vel, grad, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                  eps: float = 1e-8, stream=None) -> None:
+    _check(None, _lib.sppc_mlp_adam(_f32_dev(params, NET_PARAMS), _f32_dev(mom, NET_PARAMS),
+                                    _f32_dev(vel, NET_PARAMS), _f32_dev(grad, NET_PARAMS), int(t), float(lr),
+                                    float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def sppc_mlp_train_epoch(params, mom, vel, X, rhat, y, perm, batch: int, step: int, lr: float,
+                         beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
+    """One epoch of minibatch Adam; perm: CUDA int64 order of the samples or None.
+    Returns (new step count, mean batch loss)."""
+    n = int(X.shape[0])
+    st = ctypes.c_int32(int(step))
+    loss = ctypes.c_double()
+    pp = 0
+    if perm is not None:
+        assert perm.is_cuda and str(perm.dtype) == "torch.int64" and perm.numel() >= n
+        pp = perm.data_ptr()
+    _check(None, _lib.sppc_mlp_train_epoch(_f32_dev(params, NET_PARAMS), _f32_dev(mom, NET_PARAMS),
+                                           _f32_dev(vel, NET_PARAMS), _f32_dev(X, 6 * n), _f32_dev(rhat, n),
+                                           _f32_dev(y, n), pp, n, int(batch), ctypes.byref(st), float(lr),
+                                           float(beta1), float(beta2), float(eps), ctypes.byref(loss),
+                                           _stream(stream)))
+    return int(st.value), float(loss.value)
+
+
+def sppc_feature_moments(F, stream=None):
+    n = int(F.shape[0])
+    mean, sd = np.zeros(6), np.zeros(6)
+    _check(None, _lib.sppc_feature_moments(_f32_dev(F, 6 * n), n, mean.ctypes.data, sd.ctypes.data, _stream(stream)))
+    return mean, sd
+
+
+def sppc_standardize(F, mu, sd, X, stream=None) -> None:
+    n = int(F.shape[0])
+    m = np.ascontiguousarray(mu, dtype=np.float32)
+    d = np.ascontiguousarray(sd, dtype=np.float32)
+    _check(None, _lib.sppc_standardize(_f32_dev(F, 6 * n), n, m.ctypes.data, d.ctypes.data, _f32_dev(X, 6 * n),
+                                       _stream(stream)))
 
 
 def sppc_destroy(h) -> None:

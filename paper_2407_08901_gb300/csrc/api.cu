@@ -106,6 +106,12 @@ struct sppc_ctx {
   uint16_t* val16 = nullptr;                      // BF16 off-diagonal values (precision 2)
   float* diag32 = nullptr;                        // FP32 diagonal (precision 2)
   bool f32_products = false;                      // big SpMMs in FP32 (mixed precision, until verified)
+  // learned correction proposal
+  float2* rowc = nullptr;                         // (level(i), ||H_i,:||_2) per row
+  float* net = nullptr;                           // network parameters + mu + sd (device)
+  bool net_ready = false;
+  float* rhat32 = nullptr;                        // scaled residual entries, n x 8
+  float2 *Tprop = nullptr, *Tplain = nullptr;     // proposal and plain preconditioned blocks, n x kp
   int nev = 0;                                    // Ritz pairs kept by the last Rayleigh-Ritz
 
   // state
@@ -1006,32 +1012,108 @@ sppc_status lead_correction(sppc_ctx* h, float2* T) {
   return SPPC_OK;
 }
 
+// Diagonal of the Ritz-residual pass's T output: the Jacobi denominators, or none
+// (T = the raw residual) when the learned proposal builds the block itself.
+const float2* t_diag(const sppc_ctx* h) {
+  if (h->opt.proposal == 1) return nullptr;
+  return h->opt.precond ? h->dDiag : nullptr;
+}
+
+// Buffers of the learned proposal (allocated on first use).
+sppc_status ensure_proposal_buffers(sppc_ctx* h) {
+  const int64_t n = h->n;
+  cudaError_t e = cudaSuccess;
+  if (!h->net) e = dalloc(h, &h->net, (size_t)(kNetParams + 2 * kNetFeatures));
+  if (e == cudaSuccess && !h->rhat32) e = dalloc(h, &h->rhat32, (size_t)n * 8);
+  if (e == cudaSuccess && !h->Tprop) e = dalloc(h, &h->Tprop, (size_t)n * h->kp);
+  if (e == cudaSuccess && !h->Tplain) e = dalloc(h, &h->Tplain, (size_t)n * h->kp);
+  if (e == cudaSuccess && !h->X32) e = dalloc(h, &h->X32, (size_t)n * 8);
+  if (e == cudaSuccess && !h->val32 && !h->val16) {
+    // FP32 copy of the values for the |H| product (their double-float high words)
+    const int64_t total = h->h_slice_ptr.empty() ? 0 : h->h_slice_ptr.back();
+    e = dalloc(h, &h->val32, (size_t)(total > 0 ? total : 1));
+    if (e == cudaSuccess) e = df_hi_parts(h->H.val, h->val32, total, h->stream);
+  }
+  if (e != cudaSuccess)
+    return fail(h, e == cudaErrorMemoryAllocation ? SPPC_ERR_OOM : SPPC_ERR_CUDA, "proposal buffers: %s",
+                cudaGetErrorString(e));
+  return SPPC_OK;
+}
+
+// Learned proposal from the raw Ritz residuals R (n x kp) of the last
+// Rayleigh-Ritz pass and their squared norms in dDots: rhat, |H| |rhat|, the
+// network, Tprop = (R / den)(1 + m) and Tplain = R / den for rows [n0, n)
+// (n0 = n1 when the leading block has its own correction).
+sppc_status proposal_block(sppc_ctx* h, const float2* R) {
+  PhaseRange nvtx_range("proposal");
+  cudaStream_t s = h->stream;
+  const int k = h->k, kp = h->kp;
+  const int64_t n = h->n;
+  const int64_t n0 = h->opt.precond == 2 ? h->n1 : 0;
+  CK(prop_prep(R, kp, k, h->dDots, n, h->rhat32, h->X32, s));
+  CK(spmm_abs_f32(h->H, h->val32, h->val16, h->diag32, h->X32, h->T2, s));
+  CK(prop_mlp(h->net, R, h->dDiag, h->rowc, h->rhat32, h->T2, h->dCoef + kTheta, (float)h->opt.precond_clamp, k,
+              kp, n0, n, h->Tprop, h->Tplain, s));
+  return SPPC_OK;
+}
+
 // One step of the continuation after SPPC (block Davidson, Jacobi-preconditioned
 // residuals; without preconditioner the block Krylov extension): from the last
 // Rayleigh-Ritz pairs, T = preconditioned residuals, thick restart if the basis
 // is full, orthogonalise T and append it, k SpMVs, Rayleigh-Ritz.
+// With the learned proposal (opts.proposal = 1) T is the network's block; it is
+// kept iff the largest scaled residual drops, else the step is redone with the
+// plain preconditioned block.
 sppc_status refine_step(sppc_ctx* h) {
   PhaseRange nvtx_range("refine_step");
   const int kp = h->kp;
   const int64_t n = h->n;
+  const bool learn = h->opt.proposal == 1;
+  const bool lead = h->opt.precond == 2;
+  if (learn && !h->net_ready) return fail(h, SPPC_ERR_STATE, "opts.proposal = 1 needs sppc_set_proposal first");
   // T from the current Ritz pairs: written by the previous Rayleigh-Ritz pass when
   // it already ran in continuation mode, else one extra pass over Q and W
   if (!h->t_ready) {
-    const bool lead = h->opt.precond == 2;
     CK(ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
-                  n, h->dDots, h->partials, h->partial_cap, nullptr, 0, 0, h->HPsi,
-                  h->opt.precond ? h->dDiag : nullptr, (float)h->opt.precond_clamp, h->stream,
-                  lead ? h->zlead : nullptr, lead ? h->rlead : nullptr, lead ? h->n1 : 0));
+                  n, h->dDots, h->partials, h->partial_cap, nullptr, 0, 0, h->HPsi, t_diag(h),
+                  (float)h->opt.precond_clamp, h->stream, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
+                  lead ? h->n1 : 0));
   }
   h->t_ready = false;
-  if (h->opt.precond == 2) CKS(lead_correction(h, h->HPsi));
+  float2* T = h->HPsi;
+  if (learn) {
+    CKS(proposal_block(h, h->HPsi));
+    if (lead) {
+      CKS(lead_correction(h, h->Tplain));
+      CK(cudaMemcpyAsync(h->Tprop, h->Tplain, sizeof(float2) * h->n1 * kp, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    T = h->Tprop;
+  } else if (lead) {
+    CKS(lead_correction(h, h->HPsi));
+  }
   if (h->p + 1 >= std::min(h->pmax + 1, h->opt.hybrid_blocks)) CKS(restart(h));
+  const double before = h->resid.empty() ? 0.0 : *std::max_element(h->resid.begin(), h->resid.end());
   std::vector<double> dd(2 * kp);
-  CKS(orth_append(h, h->HPsi, h->p + 1, dd.data(), h->opt.reorth == 0));
+  CKS(orth_append(h, T, h->p + 1, dd.data(), h->opt.reorth == 0));
   h->p += 1;
   CKS(big_spmm(h, blk(h->Q, n, kp, h->p), blk(h->W, n, kp, h->p), kp));
   h->stats.spmv_h += h->k;
-  CKS(rr_core(h, h->p, false, nullptr, 0, h->HPsi, h->opt.precond ? h->dDiag : nullptr));
+  CKS(rr_core(h, h->p, false, nullptr, 0, h->HPsi, t_diag(h)));
+  if (learn) {
+    h->stats.proposals_tried += 1;
+    const double after = *std::max_element(h->resid.begin(), h->resid.end());
+    if (after < before) {
+      h->stats.proposals_kept += 1;
+    } else {
+      // drop the proposal's block, extend by the plain preconditioned block
+      h->p -= 1;
+      CKS(orth_append(h, h->Tplain, h->p + 1, dd.data(), h->opt.reorth == 0));
+      h->p += 1;
+      CKS(big_spmm(h, blk(h->Q, n, kp, h->p), blk(h->W, n, kp, h->p), kp));
+      h->stats.spmv_h += h->k;
+      CKS(rr_core(h, h->p, false, nullptr, 0, h->HPsi, t_diag(h)));
+    }
+  }
   h->t_ready = true;
   OrderRec r;
   r.theta = h->theta;
@@ -1086,6 +1168,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->precond_clamp = 1e-2;
   o->precond_iters = 20;
   o->precision = 0;
+  o->proposal = 0;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1142,6 +1225,9 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.reorth != 0 && opt.reorth != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.reorth must be 0 or 1");
   if (opt.precond < 0 || opt.precond > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precond must be 0, 1 or 2");
   if (opt.precision < 0 || opt.precision > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precision must be 0, 1 or 2");
+  if (opt.proposal != 0 && opt.proposal != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.proposal must be 0 or 1");
+  if (opt.proposal == 1 && (opt.hybrid != 1 || opt.precond < 1))
+    return fail(nullptr, SPPC_ERR_ARG, "opts.proposal = 1 needs hybrid = 1 and precond 1 or 2");
   if (opt.precision != 0 && (k + 1) / 2 * 2 != 8)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k = 7 or 8 (8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
@@ -1286,6 +1372,16 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       return x;
     };
     if (e == cudaSuccess) e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, chunk, s, alloc, L);
+    if (e == cudaSuccess) {
+      // per-row constants of the learned proposal's features
+      int64_t* d_lev = nullptr;
+      e = cudaMallocAsync(&d_lev, sizeof(int64_t) * h->lev.size(), s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_lev, h->lev.data(), sizeof(int64_t) * h->lev.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = dalloc(h, &h->rowc, (size_t)n);
+      if (e == cudaSuccess) e = row_consts(n, d_rp, d_va, d_lev, (int)h->lev.size() - 1, h->rowc, s);
+      if (d_lev) cudaFreeAsync(d_lev, s);
+    }
     if (d_rp) cudaFreeAsync(d_rp, s);
     if (d_ci) cudaFreeAsync(d_ci, s);
     if (d_va) cudaFreeAsync(d_va, s);
@@ -1725,7 +1821,7 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     // their products recomputed in double-float, and continue with double-float
     // products until the (now exact) residuals meet tol.
     CKS(restart(h, true));
-    CKS(rr_core(h, h->p, false, nullptr, 0, h->HPsi, h->opt.precond ? h->dDiag : nullptr));
+    CKS(rr_core(h, h->p, false, nullptr, 0, h->HPsi, t_diag(h)));
     h->t_ready = true;
     conv = all_converged(h, tol);
     while (!conv && h->stats.refine_df < h->opt.hybrid_maxit) {
@@ -1847,6 +1943,11 @@ sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t co
       if (count < k) return fail(h, SPPC_ERR_ARG, "buffer too small");
       for (int j = 0; j < k; ++j) out[j] = j < (int)h->E0.size() ? h->E0[j] : 0.0;
       return SPPC_OK;
+    case 6:
+    case 7:
+      if (!h->Tprop) return fail(h, SPPC_ERR_STATE, "no proposal block yet");
+      if (count < n * k) return fail(h, SPPC_ERR_ARG, "buffer too small");
+      return dl(which == 6 ? h->Tprop : h->Tplain, n, k, out, k);
     default:
       return fail(h, SPPC_ERR_ARG, "unknown state id %d", which);
   }
@@ -1864,6 +1965,156 @@ sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr
   if (slice_rows) std::copy(h->h_slice_rows.begin(), h->h_slice_rows.end(), slice_rows);
   if (h11_slice_ptr) std::copy(h->h11_slice_ptr.begin(), h->h11_slice_ptr.end(), h11_slice_ptr);
   if (h11_slice_rows) std::copy(h->h11_slice_rows.begin(), h->h11_slice_rows.end(), h11_slice_rows);
+  return SPPC_OK;
+}
+
+// ---------------------------------------------------- learned proposal (C-ABI)
+static_assert(kNetParams == SPPC_NET_PARAMS && kNetFeatures == SPPC_NET_FEATURES, "network layout");
+sppc_status sppc_set_proposal(sppc_handle h, const float* params, const float* mu, const float* sd) {
+  if (!h || !params || !mu || !sd) return fail(h, SPPC_ERR_ARG, "NULL argument");
+  for (int q = 0; q < kNetParams; ++q)
+    if (!std::isfinite(params[q])) return fail(h, SPPC_ERR_ARG, "network parameter %d is not finite", q);
+  for (int f = 0; f < kNetFeatures; ++f)
+    if (!std::isfinite(mu[f]) || !(sd[f] > 0.f) || !std::isfinite(sd[f]))
+      return fail(h, SPPC_ERR_ARG, "feature %d: mean must be finite and spread positive", f);
+  CKS(ensure_proposal_buffers(h));
+  std::vector<float> buf(params, params + kNetParams);
+  buf.insert(buf.end(), mu, mu + kNetFeatures);
+  buf.insert(buf.end(), sd, sd + kNetFeatures);
+  CK(cudaMemcpyAsync(h->net, buf.data(), sizeof(float) * buf.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->net_ready = true;
+  return SPPC_OK;
+}
+
+sppc_status sppc_proposal_samples(sppc_handle h, const double* psi, int64_t ldpsi, float* F, float* rhat, float* y,
+                                  int64_t* count, void* stream) {
+  if (!h || !psi || !F || !rhat || !y) return fail(h, SPPC_ERR_ARG, "NULL argument");
+  if (!h->started || h->corrected) return fail(h, SPPC_ERR_STATE, "sppc_proposal_samples needs a finished Rayleigh-Ritz step");
+  if (ldpsi < h->k) return fail(h, SPPC_ERR_ARG, "ldpsi < k");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->stream = s;
+  CKS(ensure_proposal_buffers(h));
+  const int k = h->k, kp = h->kp;
+  const int64_t n = h->n;
+  double* Zd = nullptr;
+  double* scr = nullptr;
+  CK(cudaMallocAsync(&Zd, sizeof(double) * n * k, s));
+  cudaError_t e = cudaMallocAsync(&scr, sizeof(double) * prop_samples_scratch_doubles(), s);
+  // Ritz vectors and raw residuals (into Tplain) of the current subspace
+  if (e == cudaSuccess)
+    e = ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
+                   n, h->dDots, h->partials, h->partial_cap, Zd, k, k, h->Tplain, nullptr, (float)h->opt.precond_clamp,
+                   s, nullptr, nullptr, 0);
+  if (e == cudaSuccess) e = prop_prep(h->Tplain, kp, k, h->dDots, n, h->rhat32, h->X32, s);
+  if (e == cudaSuccess) e = spmm_abs_f32(h->H, h->val32, h->val16, h->diag32, h->X32, h->T2, s);
+  if (e == cudaSuccess)
+    e = prop_samples(h->Tplain, Zd, k, psi, ldpsi, h->dDots, h->dDiag, h->rowc, h->rhat32, h->T2, h->dCoef + kTheta,
+                     (float)h->opt.precond_clamp, k, kp, h->n1, n, scr, F, rhat, y, s);
+  if (Zd) cudaFreeAsync(Zd, s);
+  if (scr) cudaFreeAsync(scr, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h, SPPC_ERR_CUDA, "proposal samples: %s", cudaGetErrorString(e));
+  if (count) *count = (n - h->n1) * k;
+  return SPPC_OK;
+}
+
+sppc_status sppc_mlp_forward(const float* params, const float* X, int64_t count, int32_t bf16, float* out,
+                             void* stream) {
+  if (!params || !X || !out || count < 0) return fail(nullptr, SPPC_ERR_ARG, "sppc_mlp_forward: bad arguments");
+  const cudaError_t e = mlp_forward(params, X, count, bf16 != 0, out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_mlp_forward: %s", cudaGetErrorString(e));
+  return SPPC_OK;
+}
+
+sppc_status sppc_mlp_loss_grad(const float* params, const float* X, const float* rhat, const float* y, int64_t count,
+                               float* grad, float* loss, void* stream) {
+  if (!params || !X || !rhat || !y || !grad || count < 1)
+    return fail(nullptr, SPPC_ERR_ARG, "sppc_mlp_loss_grad: bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* part = nullptr;
+  cudaError_t e = cudaMallocAsync(&part, sizeof(float) * mlp_grad_part_floats(count), s);
+  if (e == cudaSuccess)
+    e = mlp_grad(params, X, rhat, y, nullptr, 0, count, static_cast<float>(1.0 / count), part, grad, loss, s);
+  if (part) cudaFreeAsync(part, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_mlp_loss_grad: %s", cudaGetErrorString(e));
+  return SPPC_OK;
+}
+
+sppc_status sppc_mlp_adam(float* params, float* mom, float* vel, const float* grad, int32_t t, float lr, float beta1,
+                          float beta2, float eps, void* stream) {
+  if (!params || !mom || !vel || !grad || t < 1) return fail(nullptr, SPPC_ERR_ARG, "sppc_mlp_adam: bad arguments");
+  const float c1 = static_cast<float>(1.0 / (1.0 - std::pow((double)beta1, t)));
+  const float c2 = static_cast<float>(1.0 / (1.0 - std::pow((double)beta2, t)));
+  const cudaError_t e = mlp_adam(params, mom, vel, grad, lr, beta1, beta2, eps, c1, c2, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_mlp_adam: %s", cudaGetErrorString(e));
+  return SPPC_OK;
+}
+
+sppc_status sppc_mlp_train_epoch(float* params, float* mom, float* vel, const float* X, const float* rhat,
+                                 const float* y, const int64_t* perm, int64_t nsamples, int32_t batch, int32_t* step,
+                                 float lr, float beta1, float beta2, float eps, double* mean_loss, void* stream) {
+  if (!params || !mom || !vel || !X || !rhat || !y || !step || nsamples < 1 || batch < 1 || *step < 0)
+    return fail(nullptr, SPPC_ERR_ARG, "sppc_mlp_train_epoch: bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t nb = (nsamples + batch - 1) / batch;
+  float *part = nullptr, *grad = nullptr, *losses = nullptr;
+  cudaError_t e = cudaMallocAsync(&part, sizeof(float) * mlp_grad_part_floats(batch), s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&grad, sizeof(float) * kNetParams, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&losses, sizeof(float) * nb, s);
+  for (int64_t b = 0; b < nb && e == cudaSuccess; ++b) {
+    const int64_t base = b * batch;
+    const int64_t cnt = std::min<int64_t>(batch, nsamples - base);
+    e = mlp_grad(params, X, rhat, y, perm, base, cnt, static_cast<float>(1.0 / cnt), part, grad, losses + b, s);
+    if (e != cudaSuccess) break;
+    const int32_t t = ++(*step);
+    const float c1 = static_cast<float>(1.0 / (1.0 - std::pow((double)beta1, t)));
+    const float c2 = static_cast<float>(1.0 / (1.0 - std::pow((double)beta2, t)));
+    e = mlp_adam(params, mom, vel, grad, lr, beta1, beta2, eps, c1, c2, s);
+  }
+  std::vector<float> hl(nb > 0 ? nb : 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hl.data(), losses, sizeof(float) * nb, cudaMemcpyDeviceToHost, s);
+  if (part) cudaFreeAsync(part, s);
+  if (grad) cudaFreeAsync(grad, s);
+  if (losses) cudaFreeAsync(losses, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_mlp_train_epoch: %s", cudaGetErrorString(e));
+  if (mean_loss) {
+    double a = 0.0;
+    for (int64_t b = 0; b < nb; ++b) a += hl[b];
+    *mean_loss = a / static_cast<double>(nb);
+  }
+  return SPPC_OK;
+}
+
+sppc_status sppc_feature_moments(const float* F, int64_t count, double* mean, double* sd, void* stream) {
+  if (!F || !mean || !sd || count < 1) return fail(nullptr, SPPC_ERR_ARG, "sppc_feature_moments: bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* scr = nullptr;
+  const int64_t ns = feature_moments_scratch_doubles();
+  cudaError_t e = cudaMallocAsync(&scr, sizeof(double) * ns, s);
+  if (e == cudaSuccess) e = feature_moments(F, count, scr, s);
+  double out[2 * kNetFeatures] = {0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, scr + ns - 2 * kNetFeatures, sizeof(out), cudaMemcpyDeviceToHost, s);
+  if (scr) cudaFreeAsync(scr, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_feature_moments: %s", cudaGetErrorString(e));
+  for (int f = 0; f < kNetFeatures; ++f) {
+    mean[f] = out[f];
+    sd[f] = out[kNetFeatures + f];
+  }
+  return SPPC_OK;
+}
+
+sppc_status sppc_standardize(const float* F, int64_t count, const float* mu, const float* sd, float* X,
+                             void* stream) {
+  if (!F || !mu || !sd || !X || count < 0) return fail(nullptr, SPPC_ERR_ARG, "sppc_standardize: bad arguments");
+  for (int f = 0; f < kNetFeatures; ++f)
+    if (!(sd[f] > 0.f)) return fail(nullptr, SPPC_ERR_ARG, "sppc_standardize: spread %d must be positive", f);
+  const cudaError_t e = standardize(F, count, mu, sd, X, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_standardize: %s", cudaGetErrorString(e));
   return SPPC_OK;
 }
 

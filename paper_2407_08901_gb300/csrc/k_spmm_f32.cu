@@ -32,7 +32,10 @@ __device__ __forceinline__ float ld_stream_bf16(const uint16_t* p) {
 // warp covers two 16-row slices (one per half-warp).  Depth-2 pipeline per lane
 // (entries t+1, t+2 in flight while t is accumulated), unrolled by three so the
 // buffers rotate without copies.
-template <bool BF>
+// MODE 0: FP32 values; 1: BF16 values + FP32 diagonal; 2 and 3: the same with
+// the absolute values of the matrix (|H| X, the neighbourhood aggregate of the
+// learned proposal).
+template <int MODE>
 __global__ void __launch_bounds__(128) k_spmm_sell_f32r(SellDev A, const float* __restrict__ val32,
                                                         const uint16_t* __restrict__ val16,
                                                         const float* __restrict__ diag32, int64_t s0, int64_t s1,
@@ -56,7 +59,8 @@ __global__ void __launch_bounds__(128) k_spmm_sell_f32r(SellDev A, const float* 
     auto fetch = [&](int64_t ee, float4& a, float4& b, float& v) {
       if (ee < end) {
         const int c = ld_stream(A.col + ee);
-        v = BF ? ld_stream_bf16(val16 + ee) : ld_stream_f(val32 + ee);
+        v = (MODE & 1) ? ld_stream_bf16(val16 + ee) : ld_stream_f(val32 + ee);
+        if (MODE >= 2) v = fabsf(v);
         const float* p = X + static_cast<int64_t>(c) * 8;
         asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
                      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
@@ -85,8 +89,8 @@ __global__ void __launch_bounds__(128) k_spmm_sell_f32r(SellDev A, const float* 
     if (row < 0) continue;
     float2* y = Y + static_cast<int64_t>(row) * 8;
     const bool first = (A.nchunks == 1) || (A.row_first[row] == q);
-    if (BF && first) {
-      const float d = diag32[row];
+    if ((MODE & 1) && first) {
+      const float d = MODE >= 2 ? fabsf(diag32[row]) : diag32[row];
       const float4 xa = *reinterpret_cast<const float4*>(X + static_cast<int64_t>(row) * 8);
       const float4 xb = *reinterpret_cast<const float4*>(X + static_cast<int64_t>(row) * 8 + 4);
       mac(xa, xb, d);
@@ -117,8 +121,6 @@ __global__ void k_make_val16(SellDev A, uint16_t* __restrict__ val16) {
   }
 }
 
-int g_grid32[2] = {0, 0};
-
 }  // namespace
 
 cudaError_t make_val16(const SellDev& A, uint16_t* val16, cudaStream_t s) {
@@ -136,46 +138,57 @@ cudaError_t df_hi_parts(const float2* in, float* out, int64_t count, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t spmm_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
-                     const float2* X, float* X32, float2* Y, cudaStream_t s) {
-  if (A.nslices == 0) return cudaSuccess;
-  const bool bf = val16 != nullptr;
-  if (bf && !diag32) return cudaErrorInvalidValue;
-  if (!bf && !val32) return cudaErrorInvalidValue;
-  int& gmax = g_grid32[bf ? 1 : 0];
+namespace {
+
+template <int MODE>
+cudaError_t launch_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
+                       const float* X32, float2* Y, cudaStream_t s) {
+  static int gmax = 0;
   if (gmax == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (bf) {
-      cudaFuncSetAttribute(k_spmm_sell_f32r<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell_f32r<true>, 128, 0);
-    } else {
-      cudaFuncSetAttribute(k_spmm_sell_f32r<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell_f32r<false>, 128, 0);
-    }
+    cudaFuncSetAttribute(k_spmm_sell_f32r<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell_f32r<MODE>, 128, 0);
     gmax = sms * (per_sm < 1 ? 1 : per_sm);
   }
-  const int64_t count = A.nrows * 8;
-  k_df_hi<<<static_cast<unsigned>((count + 255) / 256), 256, 0, s>>>(X, X32, count);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   for (int q = 0; q < A.nchunks; ++q) {
     const int64_t c0 = A.nchunks == 1 ? 0 : A.chunk_slice[q];
     const int64_t c1 = A.nchunks == 1 ? A.nslices : A.chunk_slice[q + 1];
     if (c1 <= c0) continue;
     int64_t grid = (c1 - c0 + 7) / 8;  // 4 warps x 2 slices per CTA
     if (grid > gmax) grid = gmax;
-    if (bf)
-      k_spmm_sell_f32r<true><<<static_cast<unsigned>(grid), 128, 0, s>>>(A, val32, val16, diag32, c0, c1, q, X32, Y);
-    else
-      k_spmm_sell_f32r<false><<<static_cast<unsigned>(grid), 128, 0, s>>>(A, val32, val16, diag32, c0, c1, q, X32, Y);
+    k_spmm_sell_f32r<MODE><<<static_cast<unsigned>(grid), 128, 0, s>>>(A, val32, val16, diag32, c0, c1, q, X32, Y);
     count_launch();
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t spmm_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
+                     const float2* X, float* X32, float2* Y, cudaStream_t s) {
+  if (A.nslices == 0) return cudaSuccess;
+  const bool bf = val16 != nullptr;
+  if (bf && !diag32) return cudaErrorInvalidValue;
+  if (!bf && !val32) return cudaErrorInvalidValue;
+  const int64_t count = A.nrows * 8;
+  k_df_hi<<<static_cast<unsigned>((count + 255) / 256), 256, 0, s>>>(X, X32, count);
+  count_launch();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return bf ? launch_f32<1>(A, val32, val16, diag32, X32, Y, s) : launch_f32<0>(A, val32, val16, diag32, X32, Y, s);
+}
+
+cudaError_t spmm_abs_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
+                         const float* X32, float2* Y, cudaStream_t s) {
+  if (A.nslices == 0) return cudaSuccess;
+  const bool bf = val16 != nullptr;
+  if (bf && !diag32) return cudaErrorInvalidValue;
+  if (!bf && !val32) return cudaErrorInvalidValue;
+  return bf ? launch_f32<3>(A, val32, val16, diag32, X32, Y, s) : launch_f32<2>(A, val32, val16, diag32, X32, Y, s);
 }
 
 }  // namespace sppc

@@ -95,10 +95,52 @@ int spmm_default_grid();
 // FP32 diagonal; val32 is then unused.
 cudaError_t spmm_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
                      const float2* X, float* X32, float2* Y, cudaStream_t s);
+// Y = |H| X32 (entrywise absolute values; X32 FP32 n x 8, prepared by the caller)
+cudaError_t spmm_abs_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
+                         const float* X32, float2* Y, cudaStream_t s);
 // val16[e] = BF16 bits of A.val[e].x (BF16-exact values), 0 for diagonal entries
 cudaError_t make_val16(const SellDev& A, uint16_t* val16, cudaStream_t s);
 // out[i] = in[i].x (the FP32 high words of double-float values)
 cudaError_t df_hi_parts(const float2* in, float* out, int64_t count, cudaStream_t s);
+
+// ---- k_learned.cu: learned correction proposal (network 6 -> 64 -> 64 -> 1)
+constexpr int kNetFeatures = 6, kNetHidden = 64;
+constexpr int kNetParams = kNetHidden * kNetFeatures + kNetHidden + kNetHidden * kNetHidden + kNetHidden +
+                           kNetHidden + 1;  // 4,673
+// out[s] = network output for standardised sample X[s] (count x 6); bf16: BF16 inference
+cudaError_t mlp_forward(const float* params, const float* X, int64_t count, bool bf16, float* out, cudaStream_t s);
+// Minibatch gradient of L = inv_b * sum_s (rhat_s (1 + m_s) - y_s)^2 over samples
+// perm[base + s] (or base + s), s < count; part holds mlp_grad_part_floats(count)
+// floats; grad[kNetParams]; *loss_slot (device, nullable) = L.
+cudaError_t mlp_grad(const float* params, const float* X, const float* rhat, const float* y, const int64_t* perm,
+                     int64_t base, int64_t count, float inv_b, float* part, float* grad, float* loss_slot,
+                     cudaStream_t s);
+int64_t mlp_grad_part_floats(int64_t batch);
+// Adam update; c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
+cudaError_t mlp_adam(float* params, float* mom, float* vel, const float* grad, float lr, float b1, float b2,
+                     float eps, float c1, float c2, cudaStream_t s);
+// out[i] = (level(i), ||H_i,:||_2) from a device CSR and device level offsets
+cudaError_t row_consts(int64_t n, const int64_t* rp, const double* va, const int64_t* lev, int nlev, float2* out,
+                       cudaStream_t s);
+// rhat (n x 8) and |rhat| (n x 8) from the residual block R (n x kp) and ||r_j||^2
+cudaError_t prop_prep(const float2* R, int kp, int k, const double* rn2, int64_t n, float* rhat, float* absr,
+                      cudaStream_t s);
+// proposal rows [n0, n): Tprop = (R / den)(1 + m), Tplain = R / den (n x kp)
+cudaError_t prop_mlp(const float* net, const float2* R, const float2* diag, const float2* rowc, const float* rhat,
+                     const float2* agg, const float2* theta, float clamp, int k, int kp, int64_t n0, int64_t n,
+                     float2* Tprop, float2* Tplain, cudaStream_t s);
+// training samples (rows [n0, n), pairs j < k): raw features F, rhat, target y
+cudaError_t prop_samples(const float2* R, const double* Z, int64_t ldz, const double* psi, int64_t ldpsi,
+                         const double* rn2, const float2* diag, const float2* rowc, const float* rhat,
+                         const float2* agg, const float2* theta, float clamp, int k, int kp, int64_t n0, int64_t n,
+                         double* scratch, float* F, float* rh_out, float* y, cudaStream_t s);
+int64_t prop_samples_scratch_doubles();
+// mean and spread (population) of each feature over `count` samples: written to
+// scratch[feature_moments_scratch_doubles() - 12 ...] as mean[6], sd[6]
+cudaError_t feature_moments(const float* F, int64_t count, double* scratch, cudaStream_t s);
+int64_t feature_moments_scratch_doubles();
+// X = (F - mu) / sd per feature (mu, sd host arrays of 6)
+cudaError_t standardize(const float* F, int64_t count, const float* mu, const float* sd, float* X, cudaStream_t s);
 
 // ---- k_spmm_tma.cu (kp = 8; X 16-byte aligned)
 bool spmm_tma_available();
