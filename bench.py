@@ -61,6 +61,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the block Lanczos comparator solve")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision solve")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal solve")
     ap.add_argument("--profile", default="none", choices=["none", "spmm", "solve"],
                     help="run the workload's SpMM twice (spmm) or one solve with the bench options (solve) and "
                          "exit, for profilers; prints no JSON line")
@@ -257,6 +258,8 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms_step = slowest_rank(float(np.mean(times)), dist, "cuda")
+    # plain SPPC's own result: the largest scaled residual after its last order
+    plain_resid = float(np.max(S.sppc_order_info(h, int(st["switched_at"]), k)["resid"]))
     S.sppc_destroy(h)
 
     # end to end through the C ABI from host buffers
@@ -356,6 +359,43 @@ def run_ours(args):
                 "max_rel_theta_err_vs_fp64_same_rounded_matrix": float(np.max(np.abs(mth - rth) / np.abs(rth))),
                 "max_rel_theta_diff_vs_fp64_unrounded": float(np.max(np.abs(mth - th0) / np.abs(th0)))}
         del rounded
+    if rank == 0 and world == 1 and not args.no_learned:
+        # learned correction proposal: the same solve with the trained network's
+        # block in each continuation step (kept iff the largest scaled residual
+        # drops), network from the committed training run
+        from paper_2407_08901_gb300 import proposal as PR
+        if os.path.exists(PR.DEFAULT_NET):
+            params, mu, sd, meta = PR.load(PR.DEFAULT_NET)
+            lopts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL, timing=1,
+                                        precond=PRECOND, precond_iters=PRECOND_ITERS, proposal=1)
+            hl = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, lopts, stream=stream)
+            S.sppc_set_proposal(hl, params, mu, sd)
+            lt = []
+            for _ in range(2):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1.0)
+                    l0 = torch.cuda.Event(enable_timing=True)
+                    l1 = torch.cuda.Event(enable_timing=True)
+                    l0.record(stream)
+                    lconv, lth, lrs, lst = S.sppc_solve(hl, k, tol=TOL, stream=stream)
+                    l1.record(stream)
+                torch.cuda.synchronize()
+                lt.append(l0.elapsed_time(l1) / 1e3)
+            S.sppc_destroy(hl)
+            line["learned_proposal"] = {
+                "method": "per-row network (6 features, 2x64 GELU, BF16 inference) proposing each continuation "
+                          "step's block as (r / (diag(H) - theta)) (1 + m); kept iff the largest scaled residual "
+                          "drops, else the plain preconditioned block",
+                "training": {kk: meta.get(kk) for kk in ("matrices", "n", "samples", "epochs", "losses", "loss_m0")},
+                "value": lt[-1], "unit": "s", "spmv_h": lst["spmv_h"], "steps": lst["refine_steps"],
+                "proposals_kept": lst["proposals_kept"], "proposals_tried": lst["proposals_tried"],
+                "converged": bool(lconv), "max_scaled_resid": float(np.max(lrs)),
+                "vs_without": {"value": ms_step / 1e3, "spmv_h": st["spmv_h"], "steps": st["refine_steps"]},
+                "plain_sppc_after_15_orders_max_scaled_resid": plain_resid,
+                "max_rel_theta_diff_vs_fp64": float(np.max(np.abs(np.asarray(lth) - np.asarray(th_last))
+                                                           / np.abs(np.asarray(th_last))))}
+        else:
+            line["learned_proposal"] = {"unavailable": "no trained network at " + os.path.relpath(PR.DEFAULT_NET, ROOT)}
     if rank == 0 and world == 1 and not args.no_comparator:
         # C2's comparator: block Lanczos from Psi^(0) (the same loop, no SPPC orders,
         # no preconditioner), one untimed-loop solve timed with CUDA events

@@ -141,6 +141,50 @@ def load(path: str = DEFAULT_NET):
     return z["params"], z["mu"], z["sd"], json.loads(str(z["meta"]))
 
 
+def evaluate(seeds, net_path: str = DEFAULT_NET, n: int = 2_000_000, tol: float = 1e-6, log=print):
+    """Solve matrices of the 2,000,000-row law (seeds `seeds`) with SPPC (15
+    orders) + preconditioned continuation, with and without the network's
+    proposal; per matrix the CUDA-event time, H-vector products, continuation
+    steps, proposals kept, and plain SPPC's largest scaled residual after its
+    15 orders."""
+    import torch
+    import workloads as W
+    from . import sppc_order_info, sppc_set_proposal
+    params, mu, sd, _ = load(net_path)
+    rows = []
+    for seed in seeds:
+        w = W.Workload(f"c2law_{seed}", W.level_sizes_geometric(n, 7, 2.2), 200, 8, seed=int(seed))
+        rp, c, v = W.generate(w)
+        rec = {"seed": int(seed)}
+        for name, prop in (("without", 0), ("learned", 1)):
+            o = sppc_default_opts(p_max=15, hybrid=1, switch_order=15, precond=2, precond_iters=10, tol=tol,
+                                  proposal=prop)
+            h = sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, o)
+            try:
+                if prop:
+                    sppc_set_proposal(h, params, mu, sd)
+                for rep in range(2):   # the second solve is timed
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    conv, th, rs, st = sppc_solve(h, w.k, tol=tol)
+                    e1.record()
+                    torch.cuda.synchronize()
+                if not prop:
+                    rec["plain_sppc_resid_after_15"] = float(np.max(sppc_order_info(h, 15, w.k)["resid"]))
+                    th0 = np.asarray(th)
+            finally:
+                sppc_destroy(h)
+            rec[name] = {"s": e0.elapsed_time(e1) / 1e3, "converged": bool(conv), "spmv_h": int(st["spmv_h"]),
+                         "steps": int(st["refine_steps"]), "kept": int(st["proposals_kept"]),
+                         "tried": int(st["proposals_tried"])}
+            if prop:
+                rec[name]["max_rel_theta_diff"] = float(np.max(np.abs(np.asarray(th) - th0) / np.abs(th0)))
+        log(json.dumps(rec))
+        rows.append(rec)
+    return rows
+
+
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--matrices", type=int, default=200, help="training matrices (seeds 1..N)")
@@ -150,7 +194,12 @@ def main(argv=None) -> None:
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=DEFAULT_NET)
+    ap.add_argument("--evaluate", type=int, nargs="*", default=None,
+                    help="instead of training: evaluate the saved network on these seeds of the 2,000,000-row law")
     a = ap.parse_args(argv)
+    if a.evaluate is not None:
+        evaluate(a.evaluate or [1000, 1001, 1002, 1003], net_path=a.out)
+        return
     t0 = time.time()
     F, rh, y = collect(range(1, a.matrices + 1), n=a.n, keep_fraction=a.keep)
     t1 = time.time()

@@ -76,10 +76,13 @@ def test_adam_and_epoch_match_the_oracle():
     S.sppc_mlp_adam(P, M, V, G, 7, 1e-3)
     torch.cuda.synchronize()
     p32, m32, v32, g32 = (a.astype(np.float32).astype(np.float64) for a in (p, mo, ve, g))
-    pr, mr, vr = L.adam_step(p32, m32, v32, g32, 7, 1e-3)
+    # the kernel's constants are FP32 (1 - beta is then exact in FP32 and FP64)
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    pr, mr, vr = L.adam_step(p32, m32, v32, g32, 7, f32(1e-3), beta1=f32(0.9), beta2=f32(0.999), eps=f32(1e-8))
     assert np.allclose(P.cpu().numpy(), pr, rtol=1e-6, atol=1e-7)
-    assert np.allclose(M.cpu().numpy(), mr, rtol=1e-6, atol=1e-9)
-    assert np.allclose(V.cpu().numpy(), vr, rtol=1e-6, atol=1e-12)
+    # FP32 rounding of b1 m + (1 - b1) g (terms of size ~0.1 that can cancel)
+    assert np.allclose(M.cpu().numpy(), mr, rtol=1e-6, atol=1e-7)
+    assert np.allclose(V.cpu().numpy(), vr, rtol=1e-6, atol=1e-8)
     # an epoch with one minibatch = one gradient + one Adam step (same kernels)
     B = 300
     X = rng.standard_normal((B, 6)).astype(np.float32)
