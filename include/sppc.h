@@ -288,7 +288,9 @@ sppc_status sppc_set_proposal(sppc_handle h, const float* params, const float* m
  * i >= n1 and pairs j < k, sample s = (i - n1) k + j gets raw features F[s*6 + f]
  * (device float), rhat[s] and target y[s] = -(H_ii - theta_j) t_ij sqrt(n)/||r_j||,
  * t_j = psi_j / (z_j^T psi_j) - z_j the exact correction of the Ritz vector z_j
- * (denominator clamped as by precond_clamp).  *count = (n - n1) k.  Does not change
+ * (denominator clamped as by precond_clamp); rhat and y are 0 for the pairs with
+ * |z_j^T psi_j| < 1/2 (a Ritz vector far from its eigenvector: zero loss and
+ * gradient).  *count = (n - n1) k.  Does not change
  * the SPPC state.  Synchronises `stream`. */
 sppc_status sppc_proposal_samples(sppc_handle h, const double* psi, int64_t ldpsi, float* F, float* rhat, float* y,
                                   int64_t* count, void* stream);

@@ -27,6 +27,10 @@ target     the exact correction of pair j is t_j = psi_j / (z_j^T psi_j) - z_j
            -(diag(H) - theta_j)^-1 r_j, the regression target in the scale of
            rhat is y_ij = -den_ij t_ij sqrt(n) / ||r_j||, and the loss is
            L = mean over samples of (rhat (1 + m) - y)^2.
+samples    a training sample is (x, rhat, y) for row i >= n1 and pair j; a pair whose
+           Ritz vector is far from its eigenvector (|z_j^T psi_j| < 1/2: the
+           Ritz value approximates another eigenvalue, so t_j is meaningless and
+           huge) gets rhat = y = 0, which makes its loss and gradient zero.
 keep rule  after the Rayleigh-Ritz step on the extended basis the proposal is
            kept iff the largest scaled residual ||r_j|| / |theta_j| dropped;
            otherwise the step is redone with the plain preconditioned block.
@@ -198,6 +202,17 @@ def target(psi, Z, R, diag, theta, clamp: float):
     c = np.sum(Z * psi, axis=0)
     t = psi / c - Z
     return -shifted_diag(diag, theta, clamp) * t * (np.sqrt(n) / np.linalg.norm(R, axis=0))
+
+
+MIN_OVERLAP = 0.5
+
+
+def training_pairs(psi, Z, R, diag, theta, clamp: float, rhat):
+    """(rhat, y) of the training samples: the target of `target`, both zeroed
+    for the pairs with |z_j^T psi_j| < MIN_OVERLAP."""
+    ok = np.abs(np.sum(Z * psi, axis=0)) >= MIN_OVERLAP
+    y = target(psi, Z, R, diag, theta, clamp)
+    return np.where(ok, rhat, 0.0), np.where(ok, y, 0.0)
 
 
 def keep(resid_before, resid_after) -> bool:

@@ -34,6 +34,7 @@ constexpr float kC = 0.7978845608028654f;           // sqrt(2 / pi)
 constexpr float kA = 0.044715f;
 constexpr int TB = 128;   // training samples per CTA
 constexpr int LD = 65;    // padded row stride of the per-sample activations
+constexpr double kMinOverlap = 0.5;  // training pairs need |z_j^T psi_j| >= this
 
 __device__ __forceinline__ float tanh_fast(float x) {
   float y;
@@ -355,7 +356,8 @@ __global__ void __launch_bounds__(128) k_prop_mlp(const float* __restrict__ net,
 
 // Training samples from the current Ritz state and exact eigenvectors psi:
 // rows [n0, n), pairs j < k, sample (i - n0) * k + j: raw features, rhat and the
-// target y = -den (psi_j / c_j - z_j)_i sqrt(n) / ||r_j||, c_j = z_j^T psi_j.
+// target y = -den (psi_j / c_j - z_j)_i sqrt(n) / ||r_j||, c_j = z_j^T psi_j
+// (rhat = y = 0 for pairs with |c_j| < 1/2).
 __global__ void k_prop_samples(const float2* __restrict__ R, const double* __restrict__ Z, int64_t ldz,
                                const double* __restrict__ psi, int64_t ldpsi, const double* __restrict__ c,
                                const double* __restrict__ rn2, const float2* __restrict__ diag,
@@ -372,6 +374,13 @@ __global__ void k_prop_samples(const float2* __restrict__ R, const double* __res
   sample_features(f, dg, rowc[i], rhat[i * 8 + j], th, agg[i * 8 + j].x);
 #pragma unroll
   for (int q = 0; q < NF; ++q) F[s * NF + q] = f[q];
+  // a Ritz vector far from its eigenvector (|c_j| < 1/2) gives no usable target:
+  // rhat = y = 0 (zero loss and gradient)
+  if (fabs(c[j]) < kMinOverlap) {
+    rh_out[s] = 0.f;
+    y[s] = 0.f;
+    return;
+  }
   rh_out[s] = f[3];
   const float2 den = shifted_den(dg, th, clamp);
   const double t = psi[i * ldpsi + j] / c[j] - Z[i * ldz + j];

@@ -163,7 +163,7 @@ def test_training_samples_match_the_oracle():
     R = r.W[:, :m] @ Y - Z * th
     F0, rh0 = L.features(rp, c, v, w.level_offsets, R, th)
     diag = F0[:, 0, 0]
-    y0 = L.target(psi, Z, R, diag, th, 1e-2)
+    rh0, y0 = L.training_pairs(psi, Z, R, diag, th, 1e-2, rh0)
     h = S.sppc_create(rp, c, v, w.level_offsets, n1, k, S.sppc_default_opts(p_max=6))
     try:
         S.sppc_start(h, k)

@@ -152,3 +152,18 @@ def test_bf16_inference_tracks_fp64_forward():
 def test_keep_rule():
     assert L.keep([1e-3, 2e-3], [1e-3, 1.5e-3])
     assert not L.keep([1e-3, 2e-3], [1e-4, 2e-3])
+
+
+def test_training_pairs_zero_unmatched_ritz_vectors():
+    w, rp, c, v = make_matrix("small")
+    A = dense(rp, c, v)
+    n = A.shape[0]
+    lam, V = np.linalg.eigh(A)
+    Z = V[:, :3].copy()
+    Z[:, 2] = V[:, 3]                  # pair 2's Ritz vector is another eigenvector
+    theta = np.sum(Z * (A @ Z), axis=0)
+    R = A @ Z - Z * theta + 1e-3       # any residual block (sets the scale)
+    rhat = R * np.sqrt(n) / np.linalg.norm(R, axis=0)
+    rh, y = L.training_pairs(V[:, :3], Z, R, np.diag(A).copy(), theta, 1e-2, rhat)
+    assert np.array_equal(rh[:, :2], rhat[:, :2]) and np.all(rh[:, 2] == 0) and np.all(y[:, 2] == 0)
+    assert np.array_equal(y[:, :2], L.target(V[:, :3], Z, R, np.diag(A).copy(), theta, 1e-2)[:, :2])
