@@ -386,7 +386,8 @@ def run_ours(args):
                 "method": "per-row network (6 features, 2x64 GELU, BF16 inference) proposing each continuation "
                           "step's block as (r / (diag(H) - theta)) (1 + m); kept iff the largest scaled residual "
                           "drops, else the plain preconditioned block",
-                "training": {kk: meta.get(kk) for kk in ("matrices", "n", "samples", "epochs", "losses", "loss_m0")},
+                "training": {kk: meta.get(kk) for kk in ("matrices", "n", "samples", "epochs", "losses", "loss_m0",
+                                                          "loss_trained")},
                 "value": lt[-1], "unit": "s", "spmv_h": lst["spmv_h"], "steps": lst["refine_steps"],
                 "proposals_kept": lst["proposals_kept"], "proposals_tried": lst["proposals_tried"],
                 "converged": bool(lconv), "max_scaled_resid": float(np.max(lrs)),

@@ -102,7 +102,8 @@ def collect(seeds, n: int = 50_000, keep_fraction: float = 0.125, order_lo: int 
 
 def train(F, rhat, y, epochs: int = 4, batch: int = 4096, lr: float = 1e-3, seed: int = 0, log=print):
     """Standardise, then minibatch Adam on the GPU.  Returns (params, mu, sd,
-    per-epoch mean batch losses, loss of the m = 0 network on a prefix)."""
+    per-epoch mean batch losses, loss of the m = 0 network and of the trained
+    network on one random subset of the samples)."""
     import torch
     from . import sppc_mlp_loss_grad
     mu, sd = sppc_feature_moments(F)
@@ -114,20 +115,24 @@ def train(F, rhat, y, epochs: int = 4, batch: int = 4096, lr: float = 1e-3, seed
     vel = torch.zeros_like(params)
     gen = torch.Generator(device=F.device)
     gen.manual_seed(seed)
-    # loss of the plain Jacobi block (m = 0) on a prefix of the samples
-    nz = min(int(F.shape[0]), 262_144)
-    zero = torch.zeros_like(params)
-    g0 = torch.empty_like(params)
-    l0 = torch.empty(1, dtype=torch.float32, device=F.device)
-    sppc_mlp_loss_grad(zero, X[:nz], rhat[:nz], y[:nz], g0, l0)
-    loss_m0 = float(l0.item())
     step, losses = 0, []
     for ep in range(epochs):
         perm = torch.randperm(F.shape[0], generator=gen, device=F.device)
         step, loss = sppc_mlp_train_epoch(params, mom, vel, X, rhat, y, perm, batch, step, lr)
         losses.append(loss)
         log(f"  epoch {ep + 1}: mean batch loss {loss:.6g}")
-    return params.cpu().numpy(), mu.astype(np.float32), sd.astype(np.float32), losses, loss_m0
+    # loss of the plain Jacobi block (m = 0) and of the trained network on the
+    # same random subset of the samples
+    sub = torch.randperm(F.shape[0], generator=gen, device=F.device)[:262_144]
+    Xs, rs, ys = X[sub].contiguous(), rhat[sub].contiguous(), y[sub].contiguous()
+    g0 = torch.empty_like(params)
+    l0 = torch.empty(1, dtype=torch.float32, device=F.device)
+    sppc_mlp_loss_grad(torch.zeros_like(params), Xs, rs, ys, g0, l0)
+    loss_m0 = float(l0.item())
+    sppc_mlp_loss_grad(params, Xs, rs, ys, g0, l0)
+    loss_net = float(l0.item())
+    log(f"  loss on a {Xs.shape[0]}-sample subset: m = 0 {loss_m0:.6g}, trained {loss_net:.6g}")
+    return params.cpu().numpy(), mu.astype(np.float32), sd.astype(np.float32), losses, loss_m0, loss_net
 
 
 def save(path: str, params, mu, sd, meta: dict) -> None:
@@ -204,10 +209,11 @@ def main(argv=None) -> None:
     F, rh, y = collect(range(1, a.matrices + 1), n=a.n, keep_fraction=a.keep)
     t1 = time.time()
     print(f"{F.shape[0]} samples from {a.matrices} matrices in {t1 - t0:.1f} s")
-    params, mu, sd, losses, base = train(F, rh, y, epochs=a.epochs, batch=a.batch, lr=a.lr)
+    params, mu, sd, losses, base, trained = train(F, rh, y, epochs=a.epochs, batch=a.batch, lr=a.lr)
     t2 = time.time()
     meta = {"matrices": a.matrices, "n": a.n, "samples": int(F.shape[0]), "epochs": a.epochs, "batch": a.batch,
-            "lr": a.lr, "losses": losses, "loss_m0": base, "collect_s": t1 - t0, "train_s": t2 - t1}
+            "lr": a.lr, "losses": losses, "loss_m0": base, "loss_trained": trained, "collect_s": t1 - t0,
+            "train_s": t2 - t1}
     save(a.out, params, mu, sd, meta)
     print(json.dumps(meta))
 
