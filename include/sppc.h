@@ -106,7 +106,7 @@ typedef struct {
                               if they miss tol.  2: as 1 with BF16 values: off-diagonal values
                               rounded to FP32 and then to BF16 (nearest, ties to even), the
                               diagonal to FP32, everywhere; the FP32 products read the BF16 values
-                              (2 bytes per entry) and the FP32 diagonal.  1 and 2 need k = 7 or 8. */
+                              (2 bytes per entry) and the FP32 diagonal.  1 and 2 need k in {3, 4, 7, 8}. */
   int32_t proposal;        /* 0: none (default).  1: learned correction proposal (not in the paper):
                               each continuation step extends the basis by the network's block
                               g_j = (r_j / (diag(H) - theta_j)) (1 + m_j) instead of the plain
@@ -328,6 +328,18 @@ sppc_status sppc_feature_moments(const float* F, int64_t count, double* mean, do
 /* X = (F - mu) / sd per feature (F, X device count x 6; mu, sd host, sd > 0). */
 sppc_status sppc_standardize(const float* F, int64_t count, const float* mu, const float* sd, float* X,
                              void* stream);
+
+/* Solve `count` independent problems (handles created beforehand, each with its
+ * own matrix and options) concurrently: `workers` host threads, each with its own
+ * non-blocking CUDA stream, take problems in decreasing order of stored entries
+ * and run sppc_solve(tol, p_max of the handle) on them; results equal solving
+ * them one by one.  Host outputs: theta, resid (count x kmax row-major, row i
+ * holds problem i's k values, the rest 0), converged[count], stats[count] (may
+ * be NULL).  kmax >= every handle's k.  Returns the first hard error by problem
+ * index, else SPPC_NOT_CONVERGED if some problem missed tol, else SPPC_OK.
+ * Handles must not be used by other threads during the call. */
+sppc_status sppc_solve_batch(sppc_handle* handles, int32_t count, double tol, int32_t workers, int32_t kmax,
+                             double* theta, double* resid, int32_t* converged, sppc_stats* stats);
 
 /* Release everything the handle owns.  NULL is a no-op. */
 sppc_status sppc_destroy(sppc_handle h);

@@ -96,6 +96,7 @@ _SIGS = {
                                     ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP, _VP]),
     "sppc_feature_moments": (_I32, [_VP, _I64, _VP, _VP, _VP]),
     "sppc_standardize": (_I32, [_VP, _I64, _VP, _VP, _VP, _VP]),
+    "sppc_solve_batch": (_I32, [_VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
 }
 NET_PARAMS, NET_FEATURES = 4673, 6
 EXPORTED_SYMBOLS = tuple(_SIGS)
@@ -357,6 +358,21 @@ def sppc_standardize(F, mu, sd, X, stream=None) -> None:
     d = np.ascontiguousarray(sd, dtype=np.float32)
     _check(None, _lib.sppc_standardize(_f32_dev(F, 6 * n), n, m.ctypes.data, d.ctypes.data, _f32_dev(X, 6 * n),
                                        _stream(stream)))
+
+
+def sppc_solve_batch(handles, kmax: int, tol: float = -1.0, workers: int = 8):
+    """Solve independent problems concurrently (see include/sppc.h).  Returns
+    (status, theta (count x kmax), resid (count x kmax), converged (count), stats list)."""
+    count = len(handles)
+    arr = (ctypes.c_void_p * count)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    th = np.zeros((count, kmax))
+    rs = np.zeros((count, kmax))
+    cv = np.zeros(count, dtype=np.int32)
+    st = (Stats * count)()
+    status = _lib.sppc_solve_batch(ctypes.cast(arr, ctypes.c_void_p), count, float(tol), int(workers), int(kmax),
+                                   th.ctypes.data, rs.ctypes.data, cv.ctypes.data, ctypes.cast(st, ctypes.c_void_p))
+    _check(None, status, allow=(SPPC_OK, SPPC_NOT_CONVERGED))
+    return status, th, rs, cv.astype(bool), [s.as_dict() for s in st]
 
 
 def sppc_destroy(h) -> None:

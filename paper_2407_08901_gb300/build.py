@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsppc.so")
-SOURCES = ["k_spmm.cu", "k_spmm_tma.cu", "k_spmm_f32.cu", "sell_build.cu", "k_dense.cu", "k_small.cu", "k_minres.cu", "k_learned.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["k_spmm.cu", "k_spmm_tma.cu", "k_spmm_f32.cu", "sell_build.cu", "k_dense.cu", "k_small.cu", "k_minres.cu", "k_learned.cu", "api.cu", "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -23,7 +23,7 @@ def nvcc() -> str:
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-pthread",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [cc] + ARCH + ["-shared", "-Xcompiler", "-fopenmp", "-o", tmp] + objs
+    cmd = [cc] + ARCH + ["-shared", "-Xcompiler", "-fopenmp,-pthread", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -539,8 +539,8 @@ sppc_status big_spmm(sppc_ctx* h, const float2* X, float2* Y, int kp) {
     b = next_event(h);
     CK(cudaEventRecord(a, h->stream));
   }
-  if (h->f32_products && kp == 8)
-    CK(spmm_f32(h->H, h->val32, h->val16, h->diag32, X, h->X32, Y, h->stream));
+  if (h->f32_products && (kp == 4 || kp == 8))
+    CK(spmm_f32(h->H, h->val32, h->val16, h->diag32, X, h->X32, Y, kp, h->stream));
   else
     CK(spmm(h->H, kp, X, Y, Epi{}, h->stream));
   if (h->opt.timing) {
@@ -1142,6 +1142,11 @@ const SellDev* handle_matrix(sppc_handle h, int64_t* n) {
   return &h->H;
 }
 sppc_status handle_fail(sppc_handle h, sppc_status st, const char* msg) { return fail(h, st, "%s", msg); }
+void handle_size(sppc_handle h, int64_t* n, int64_t* nnz, int* k) {
+  if (n) *n = h->n;
+  if (nnz) *nnz = h->nnz;
+  if (k) *k = h->k;
+}
 }  // namespace sppc
 
 // =================================================================== C ABI
@@ -1228,8 +1233,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.proposal != 0 && opt.proposal != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.proposal must be 0 or 1");
   if (opt.proposal == 1 && (opt.hybrid != 1 || opt.precond < 1))
     return fail(nullptr, SPPC_ERR_ARG, "opts.proposal = 1 needs hybrid = 1 and precond 1 or 2");
-  if (opt.precision != 0 && (k + 1) / 2 * 2 != 8)
-    return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k = 7 or 8 (8-column FP32 products)");
+  if (opt.precision != 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precond_iters must be in [0, 10000]");
 
@@ -1519,8 +1524,8 @@ sppc_status sppc_spmm(sppc_handle h, const double* X, int64_t ldx, double* Y, in
   h->stream = s;
   const int kp = (ncols + 1) / 2 * 2;
   CK(f64_to_df(X, ldx, ncols, h->T1, kp, 0, h->n, s));
-  if (h->opt.precision != 0 && kp == 8)
-    CK(spmm_f32(h->H, h->val32, h->val16, h->diag32, h->T1, h->X32, h->T2, s));
+  if (h->opt.precision != 0 && (kp == 4 || kp == 8))
+    CK(spmm_f32(h->H, h->val32, h->val16, h->diag32, h->T1, h->X32, h->T2, kp, s));
   else
     CK(spmm(h->H, kp, h->T1, h->T2, Epi{}, s));
   CK(df_to_f64(h->T2, kp, Y, ldy, ncols, 0, h->n, s));

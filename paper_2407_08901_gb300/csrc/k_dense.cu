@@ -19,13 +19,12 @@ constexpr int kChunk = 2048;  // rows per CTA in the reductions over long blocks
 // that four resident CTAs of 8 warps run two full waves), in multiples of 32
 // rows, between 128 and kChunk.
 inline int64_t chunk_rows(int64_t rows) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   int64_t c = (rows + 8 * sms - 1) / (8 * sms);
   c = (c + 31) / 32 * 32;
   return c < 128 ? 128 : (c > kChunk ? kChunk : c);

@@ -499,14 +499,10 @@ cudaError_t mlp_grad(const float* params, const float* X, const float* rhat, con
                      int64_t base, int64_t count, float inv_b, float* part, float* grad, float* loss_slot,
                      cudaStream_t s) {
   if (count <= 0) return cudaErrorInvalidValue;
-  static bool attr = false;
   const size_t sm = grad_smem();
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(sm));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(grad_smem()));
+  if (attr != cudaSuccess) return attr;
   const int nb = static_cast<int>((count + TB - 1) / TB);
   k_mlp_grad<<<nb, TB, sm, s>>>(params, X, rhat, y, perm, base, count, inv_b, part);
   count_launch();
@@ -544,8 +540,7 @@ cudaError_t prop_mlp(const float* net, const float2* R, const float2* diag, cons
                      const float2* agg, const float2* theta, float clamp, int k, int kp, int64_t n0, int64_t n,
                      float2* Tprop, float2* Tplain, cudaStream_t s) {
   if (n <= n0) return cudaSuccess;
-  static int gmax = 0;
-  if (gmax == 0) gmax = persistent_grid(reinterpret_cast<const void*>(k_prop_mlp), 128);
+  static const int gmax = persistent_grid(reinterpret_cast<const void*>(k_prop_mlp), 128);
   int64_t grid = ((n - n0) * kp + 127) / 128;
   if (grid > gmax) grid = gmax;
   k_prop_mlp<<<static_cast<unsigned>(grid), 128, 0, s>>>(net, R, diag, rowc, rhat, agg, theta, clamp, k, kp, n0, n,

@@ -530,13 +530,9 @@ cudaError_t syev_lowest(const double* S, int lds, int m, int nev, double* theta,
                         cudaStream_t s) {
   if (m < 1 || m > kMaxM || nev < 1 || nev > kMaxNev || nev > m) return cudaErrorInvalidValue;
   const size_t smem = syev_smem(m);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_syev_lowest, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)syev_smem(kMaxM));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_syev_lowest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syev_smem(kMaxM));
+  if (attr != cudaSuccess) return attr;
   k_syev_lowest<<<1, 512, smem, s>>>(S, lds, m, nev, theta, V, ldv); count_launch();
   return cudaGetLastError();
 }

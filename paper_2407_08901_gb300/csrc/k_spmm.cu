@@ -57,7 +57,6 @@ __global__ void __launch_bounds__(128, 7) k_spmm_sell(SellDev A, int64_t s0, int
   }
 }
 
-int g_grid = 0;
 std::atomic<long long> g_launches{0};
 
 }  // namespace
@@ -66,15 +65,16 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int spmm_default_grid() {
-  if (g_grid == 0) {
+  // computed once (thread-safe static initialisation: handles may solve on several host threads)
+  static const int grid = [] {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell<8, false>, 128, 0);
     if (per_sm < 1) per_sm = 1;
-    g_grid = sms * per_sm;
-  }
-  return g_grid;
+    return sms * per_sm;
+  }();
+  return grid;
 }
 
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s) {

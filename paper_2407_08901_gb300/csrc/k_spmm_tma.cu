@@ -238,8 +238,6 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma8(SellDev A, const _
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
-int g_tma_grid = 0;
-
 }  // namespace
 
 bool spmm_tma_available() {
@@ -263,17 +261,18 @@ cudaError_t spmm_tma8(const SellDev& A, const float2* X, float2* Y, const Epi& e
   if (!spmm_tma_available()) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorMisalignedAddress;
   const size_t smem = static_cast<size_t>(kTmaWarps) * kTmaDepth * kStageBytes;
-  if (g_tma_grid == 0) {
+  // grid limit computed once (thread-safe static initialisation); 0 = setup failed
+  static const int g_tma_grid = [smem] {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaFuncSetAttribute(k_spmm_tma8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_tma8, kTmaWarps * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    g_tma_grid = sms * per_sm;
-  }
+    if (cudaFuncSetAttribute(k_spmm_tma8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_tma8, kTmaWarps * 32, smem) != cudaSuccess)
+      return 0;
+    return per_sm < 1 ? 0 : sms * per_sm;
+  }();
+  if (g_tma_grid == 0) return cudaErrorInvalidConfiguration;
   // X (nrows x 8 double-float) as a 2-D fp32 tensor of 16 columns; one box is
   // one 64-byte row, four boxes per gather4.
   CUtensorMap tm;

@@ -88,14 +88,14 @@ cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* c
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
 int spmm_default_grid();
 
-// ---- k_spmm_f32.cu (mixed precision, 8 columns): X (double-float) rounded to
-// FP32 into X32 (n x 8 floats), Y = H X with FP32 values val32 (same SELL layout as
-// A) and FP32 accumulation, written as double-float with zero low words.  With
-// val16 != nullptr the values are BF16 (diagonal entries 0) and diag32 holds the
-// FP32 diagonal; val32 is then unused.
+// ---- k_spmm_f32.cu (mixed precision, kp = 4 or 8 columns): X (double-float)
+// rounded to FP32 into X32 (n x kp floats), Y = H X with FP32 values val32 (same
+// SELL layout as A) and FP32 accumulation, written as double-float with zero low
+// words.  With val16 != nullptr the values are BF16 (diagonal entries 0) and
+// diag32 holds the FP32 diagonal; val32 is then unused.
 cudaError_t spmm_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
-                     const float2* X, float* X32, float2* Y, cudaStream_t s);
-// Y = |H| X32 (entrywise absolute values; X32 FP32 n x 8, prepared by the caller)
+                     const float2* X, float* X32, float2* Y, int kp, cudaStream_t s);
+// Y = |H| X32 (entrywise absolute values; X32 FP32 n x 8, Y n x 8, prepared by the caller)
 cudaError_t spmm_abs_f32(const SellDev& A, const float* val32, const uint16_t* val16, const float* diag32,
                          const float* X32, float2* Y, cudaStream_t s);
 // val16[e] = BF16 bits of A.val[e].x (BF16-exact values), 0 for diagonal entries

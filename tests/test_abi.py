@@ -56,6 +56,8 @@ def test_create_rejects_bad_input(case, status):
         k = 0
     elif case == "k_nine":
         k = 9
+    elif case == "precision_k":
+        k = 5      # 6-column blocks: no FP32 product kernel
     elif case == "levels_bad":
         lev[2] = lev[1]
     elif case == "unsorted":

@@ -45,16 +45,18 @@ def test_bf16_rounding_pins():
     assert np.array_equal(got, want), got
 
 
-@pytest.mark.parametrize("name,chunk", [("c1", 0), ("c2mini", 0), ("c2mini", 9000)])
-def test_fp32_spmm_within_its_error_bound(name, chunk):
+@pytest.mark.parametrize("name,chunk,ncols", [("c1", 0, 8), ("c2mini", 0, 8), ("c2mini", 9000, 8),
+                                               ("c1", 0, 4), ("c2mini", 9000, 4)])
+def test_fp32_spmm_within_its_error_bound(name, chunk, ncols):
     """FP32 accumulation of a row of m products: error <= (m + 4) 2^-24 sum |a||x|
-    (m roundings of the running sum, X rounded to FP32, tile partial sums)."""
+    (m roundings of the running sum, X rounded to FP32, tile partial sums);
+    8-column (32-byte gathers) and 4-column (16-byte gathers) kernels."""
     import paper_2407_08901_gb300 as S
     w, rp, c, v = make_matrix(name)
-    h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, 8 if w.k < 7 else w.k,
+    h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, ncols,
                       S.sppc_default_opts(precision=1, spmm_chunk_cols=chunk))
     try:
-        X = W.random_block(w.n, 8, 21)
+        X = W.random_block(w.n, ncols, 21)
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.full_like(Xd, float("nan"))
         S.sppc_spmm(h, Xd, Yd)
@@ -109,9 +111,10 @@ def test_bf16_solve_matches_dense_eigenvalues_of_the_rounded_matrix():
     assert np.max(np.abs(lam - lam0) / np.abs(lam0)) < 1e-2
 
 
-def test_mixed_solve_matches_dense_eigenvalues_of_the_rounded_matrix():
+@pytest.mark.parametrize("k", [8, 4])
+def test_mixed_solve_matches_dense_eigenvalues_of_the_rounded_matrix(k):
     import paper_2407_08901_gb300 as S
-    w, rp, c, v = make_matrix(SMALL8)
+    w, rp, c, v = make_matrix(W.Workload(f"small{k}", [300, 500, 900, 1300], 40, k, seed=7))
     vr = _rounded(v)
     lam = np.linalg.eigvalsh(dense(rp, c, vr))[: w.k]
     opts = S.sppc_default_opts(p_max=6, hybrid=1, switch_order=3, precond=2, precision=1, tol=1e-8)
