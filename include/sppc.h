@@ -84,9 +84,10 @@ typedef struct {
   int32_t switch_order;    /* SPPC orders before the continuation (default 15, Sec. 6) */
   int32_t hybrid_maxit;    /* continuation steps, k SpMVs each (default 1000) */
   int32_t precond;         /* 1: residual_j / (diag(H) - theta_j) (default); 0: none (block Krylov);
-                              2: as 1, then the leading n1 rows replaced by precond_iters MINRES steps on
-                              P (H0_hat - theta_j) P t = P r_j[:n1], P deflating the Ritz vector's leading
-                              part (shifted block-diagonal preconditioner, Sec. 5) */
+                              2: as 1, then the leading rows replaced by precond_iters MINRES steps on
+                              P (H_L - theta_j) P t = P r_j[:nL], H_L the leading block (H0_hat, or more
+                              levels by precond_levels), P deflating the Ritz vector's leading part
+                              (shifted block-diagonal preconditioner, Sec. 5) */
   double precond_clamp;    /* denominators of the preconditioner clamped to |.| >= this (1e-2) */
   int32_t hybrid_blocks;   /* continuation basis limit in blocks of k vectors before a thick restart
                               to 2k Ritz vectors (default 0 = p_max + 1; at least 3) */
@@ -114,6 +115,10 @@ typedef struct {
                               solve); kept iff the largest scaled residual drops, else the step is
                               redone with the plain block.  Needs hybrid = 1, precond 1 or 2 and
                               sppc_set_proposal before the solve. */
+  int32_t precond_levels;  /* precond 2: the MINRES-solved leading block spans levels [0, precond_levels)
+                              (rows [0, max(n1, level_offsets[precond_levels])); default 1 = the
+                              small space H0_hat).  More levels: a stronger preconditioner (fewer
+                              continuation steps) for more work per MINRES step. */
 } sppc_opts;
 
 typedef struct {

@@ -17,10 +17,11 @@ Step by step, from Q (orthonormal, n x m), W = H Q, Ht = Q^T W:
     rho_j = ||R_j|| / |theta_j| (Eq. rrn); stop when every rho_j <= tol.
  2. T_j = R_j / (diag(H) - theta_j) elementwise, each denominator clamped to
     magnitude >= clamp (Jacobi preconditioner), or T = R without preconditioner.
-    With precond="lead" the leading n1 rows of T_j are then replaced by an
-    approximate solve with the leading block: z_hat = Z_j[:n1] / ||Z_j[:n1]||,
+    With precond="lead" the leading nl rows of T_j (nl = n1 unless lead_rows
+    says otherwise; H_L = H[:nl, :nl]) are then replaced by an approximate
+    solve with the leading block: z_hat = Z_j[:nl] / ||Z_j[:nl]||,
     P = I - z_hat z_hat^T, and `lead_iters` MINRES steps (x0 = 0, no stopping
-    test) on P (H0_hat - theta_j) P t = P R_j[:n1], then t <- P t.  This is this
+    test) on P (H_L - theta_j) P t = P R_j[:nl], then t <- P t.  This is this
     repository's reading of the paper's shifted block-diagonal preconditioner:
     the exact leading block, shifted by the Ritz value and deflated by the Ritz
     vector (the projection of Jacobi-Davidson, Sleijpen and van der Vorst 1996),
@@ -85,14 +86,16 @@ def _ritz(Q, W, k, nev):
 def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, tol: float = 1e-6,
                 max_blocks: int = 16, maxit: int = 500, precond: str = "jacobi", clamp: float = 1e-2,
                 solver: str = "pinv", minres_tol: float = 1e-12, reorth: str = "cond",
-                perturb: float = 0.0, perturb_seed: int = 0, lead_iters: int = 20):
+                perturb: float = 0.0, perturb_seed: int = 0, lead_iters: int = 20, lead_rows: int | None = None):
     """Run SPPC (Algorithm 2) for up to `switch_order` orders (stopping early if
     every scaled residual is below tol), then the block continuation above.
     Returns (theta, resid, converged, records).
 
     perturb > 0 multiplies every entry of T by (1 + perturb * N(0, 1)) each step
     (seeded): a test hook that measures how far rounding-sized differences carry
-    along the trajectory."""
+    along the trajectory.  lead_rows (default n1): rows of the leading block that
+    precond="lead" solves with MINRES (a level boundary; more levels than the
+    small space make a stronger preconditioner)."""
     n = row_ptr.shape[0] - 1
     r = sppc(row_ptr, col, val, n1, k, p_max=switch_order, tol=tol, solver=solver, minres_tol=minres_tol,
              keep=True)
@@ -102,7 +105,8 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
         return r.theta, r.resid, True, records
     Q, W = r.Q, r.W
     rng = np.random.Generator(np.random.PCG64(perturb_seed))
-    H11 = _leading_block(row_ptr, col, val, n1) if precond == "lead" else None
+    nl = n1 if lead_rows is None else int(lead_rows)
+    H11 = _leading_block(row_ptr, col, val, nl) if precond == "lead" else None
     diag = np.zeros(n)
     rows = np.repeat(np.arange(n), np.diff(row_ptr))
     on = rows == col
@@ -125,7 +129,7 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
             den[small] = np.where(den[small] >= 0, clamp, -clamp)
             T = R / den
             for j in range(k):
-                T[:n1, j] = lead_block_correction(H11, Z[:n1, j], R[:n1, j], th[j], lead_iters)
+                T[:nl, j] = lead_block_correction(H11, Z[:nl, j], R[:nl, j], th[j], lead_iters)
         else:
             T = R.copy()
         if perturb > 0.0:

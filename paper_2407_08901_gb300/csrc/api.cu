@@ -75,6 +75,8 @@ struct sppc_ctx {
   // matrix (device)
   SellDev H, H11;
   CsrDev H11c;  // H0_hat as CSR for the persistent MINRES
+  CsrDev Hlead; // leading block of the precond 2 solve (H11c unless precond_levels > 1)
+  int64_t n_lead = 0;
   std::vector<void*> allocs;
   int64_t h_slices = 0, h11_slices = 0;
   std::vector<int64_t> h_chunk_slice, h11_chunk_slice;  // host copies (SellDev points here)
@@ -477,7 +479,10 @@ sppc_status upload_sell(sppc_ctx* h, SellHost& S, SellDev& D, int64_t nrows, std
 }
 
 // H0_hat (rows and columns < n1 of H) as CSR with double-float values.
-sppc_status upload_csr11(sppc_ctx* h, int64_t n1, const int64_t* rp, const int32_t* ci, const double* va) {
+// Leading block H[:n1, :n1] as a double-float CSR on the device (columns sorted
+// within each row, so a row's block entries are its first ones).
+sppc_status upload_csr11(sppc_ctx* h, int64_t n1, const int64_t* rp, const int32_t* ci, const double* va,
+                         CsrDev& out) {
   std::vector<int64_t> p(n1 + 1, 0);
   for (int64_t r = 0; r < n1; ++r) {
     int64_t c = 0;
@@ -502,10 +507,10 @@ sppc_status upload_csr11(sppc_ctx* h, int64_t n1, const int64_t* rp, const int32
   CK(cudaMemcpyAsync(dcol, col.data(), sizeof(int32_t) * col.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(dval, val.data(), sizeof(float2) * val.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  h->H11c.nrows = n1;
-  h->H11c.rowptr = drp;
-  h->H11c.col = dcol;
-  h->H11c.val = dval;
+  out.nrows = n1;
+  out.rowptr = drp;
+  out.col = dcol;
+  out.val = dval;
   return SPPC_OK;
 }
 
@@ -836,7 +841,7 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
   CK(ritz_resid(blocks(h->Q, n, kp, 0, p + 1), blocks(h->W, n, kp, 0, p + 1), h->dY, h->dCoef + kTheta, kp, n,
                 h->dDots, h->partials, h->partial_cap, want_z ? Z : nullptr, ldz, k, T, diag,
                 (float)h->opt.precond_clamp, s, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
-                lead ? h->n1 : 0));
+                lead ? h->n_lead : 0));
   std::vector<double> th(k), r2(kp);
   CK(cudaMemcpyAsync(th.data(), h->dTheta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(r2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
@@ -953,7 +958,7 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
 sppc_status lead_correction(sppc_ctx* h, float2* T) {
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
-  const int64_t n1 = h->n1;
+  const int64_t n1 = h->n_lead;  // rows of the leading block
   float2* c = h->dCoef;
   const int iters = h->opt.precond_iters;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -982,7 +987,7 @@ sppc_status lead_correction(sppc_ctx* h, float2* T) {
   CK(cudaGetLastError());
   int* dstat = h->dStatus + 32;
   if (iters > 0) {
-    CK(minres_persistent(h->H11c, k, kp, c + kLeadNegE, h->zlead, h->b1, h->mv, h->mvprev, h->my, h->mw1, h->mw2,
+    CK(minres_persistent(h->Hlead, k, kp, c + kLeadNegE, h->zlead, h->b1, h->mv, h->mvprev, h->my, h->mw1, h->mw2,
                          h->mx, 0.0, iters, h->partials, h->partial_cap, h->dBar, dstat, s));
     // x <- x - z (z^T x)
     const float2* A[1] = {h->zlead};
@@ -1049,7 +1054,7 @@ sppc_status proposal_block(sppc_ctx* h, const float2* R) {
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
-  const int64_t n0 = h->opt.precond == 2 ? h->n1 : 0;
+  const int64_t n0 = h->opt.precond == 2 ? h->n_lead : 0;
   CK(prop_prep(R, kp, k, h->dDots, n, h->rhat32, h->X32, s));
   CK(spmm_abs_f32(h->H, h->val32, h->val16, h->diag32, h->X32, h->T2, s));
   CK(prop_mlp(h->net, R, h->dDiag, h->rowc, h->rhat32, h->T2, h->dCoef + kTheta, (float)h->opt.precond_clamp, k,
@@ -1077,7 +1082,7 @@ sppc_status refine_step(sppc_ctx* h) {
     CK(ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
                   n, h->dDots, h->partials, h->partial_cap, nullptr, 0, 0, h->HPsi, t_diag(h),
                   (float)h->opt.precond_clamp, h->stream, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
-                  lead ? h->n1 : 0));
+                  lead ? h->n_lead : 0));
   }
   h->t_ready = false;
   float2* T = h->HPsi;
@@ -1085,7 +1090,8 @@ sppc_status refine_step(sppc_ctx* h) {
     CKS(proposal_block(h, h->HPsi));
     if (lead) {
       CKS(lead_correction(h, h->Tplain));
-      CK(cudaMemcpyAsync(h->Tprop, h->Tplain, sizeof(float2) * h->n1 * kp, cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->Tprop, h->Tplain, sizeof(float2) * h->n_lead * kp, cudaMemcpyDeviceToDevice,
+                         h->stream));
     }
     T = h->Tprop;
   } else if (lead) {
@@ -1174,6 +1180,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->precond_iters = 20;
   o->precision = 0;
   o->proposal = 0;
+  o->precond_levels = 1;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1233,6 +1240,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.proposal != 0 && opt.proposal != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.proposal must be 0 or 1");
   if (opt.proposal == 1 && (opt.hybrid != 1 || opt.precond < 1))
     return fail(nullptr, SPPC_ERR_ARG, "opts.proposal = 1 needs hybrid = 1 and precond 1 or 2");
+  if (opt.precond_levels < 1 || opt.precond_levels > n_levels)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.precond_levels must be in [1, n_levels]");
   if (opt.precision != 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
@@ -1251,6 +1260,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   h->pmax = opt.p_max;
   h->mmax = k * (opt.p_max + 1);
   h->lev.assign(level_offsets, level_offsets + n_levels + 1);
+  h->n_lead = (opt.precond == 2) ? std::max<int64_t>(n1, level_offsets[opt.precond_levels]) : n1;
   auto bail = [&](sppc_status st) {
     g_create_error = h->err;
     sppc_destroy(h);
@@ -1436,8 +1446,13 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     h->h11_slice_ptr = std::move(S.slice_ptr);
     h->h11_slice_rows = std::move(S.rows);
     h->H11.tma = h->H.tma;
-    st = upload_csr11(h, n1, rp, ci, va);
+    st = upload_csr11(h, n1, rp, ci, va, h->H11c);
     if (st != SPPC_OK) return bail(st);
+    h->Hlead = h->H11c;
+    if (h->n_lead > n1) {
+      st = upload_csr11(h, h->n_lead, rp, ci, va, h->Hlead);
+      if (st != SPPC_OK) return bail(st);
+    }
   }
   // diag(H) for the preconditioned continuation
   {
@@ -1475,8 +1490,11 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     A(&h->HPsi, (size_t)n * kp);
     A(&h->T1, (size_t)n * 8);
     A(&h->T2, (size_t)n * 8);
-    for (float2** q : {&h->psi_hat, &h->vps, &h->b1, &h->mv, &h->mvprev, &h->mp, &h->my, &h->mw1, &h->mw2, &h->mx})
-      A(q, (size_t)n1 * kp);
+    A(&h->psi_hat, (size_t)n1 * kp);
+    A(&h->vps, (size_t)n1 * kp);
+    // MINRES vectors: the small-space solves (n1 rows) and the precond 2 solve (n_lead rows)
+    for (float2** q : {&h->b1, &h->mv, &h->mvprev, &h->mp, &h->my, &h->mw1, &h->mw2, &h->mx})
+      A(q, (size_t)std::max(n1, h->n_lead) * kp);
     for (int i = 0; i < 12; ++i) A(&h->se[i], (size_t)n1 * 8);
     D(&h->dE, (size_t)(kMaxBlocks + 2) * 8);
     D(&h->dHt, (size_t)h->mmax * h->mmax);
@@ -1494,8 +1512,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     A(&h->dRecycle, (size_t)kMaxBlocks * 64);
     A(&h->dY, (size_t)kMaxBlocks * 64);
     if (h->opt.precond == 2) {
-      A(&h->zlead, (size_t)h->n1 * kp);
-      A(&h->rlead, (size_t)h->n1 * kp);
+      A(&h->zlead, (size_t)h->n_lead * kp);
+      A(&h->rlead, (size_t)h->n_lead * kp);
     }
     A(&h->dCoefBig, (size_t)kMaxBlocks * 64);
     if (e == cudaSuccess) e = dalloc(h, &h->dStatus, 64);

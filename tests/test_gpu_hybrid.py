@@ -15,22 +15,25 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("name,switch,pmax,precond", [("small", 3, 5, 1), ("small", 0, 4, 0), ("c1", 2, 6, 1),
-                                                     ("small", 3, 5, 2), ("c1", 2, 6, 2)])
-def test_hybrid_matches_oracle(name, switch, pmax, precond):
+@pytest.mark.parametrize("name,switch,pmax,precond,levels", [("small", 3, 5, 1, 1), ("small", 0, 4, 0, 1),
+                                                            ("c1", 2, 6, 1, 1), ("small", 3, 5, 2, 1),
+                                                            ("c1", 2, 6, 2, 1), ("c1", 2, 6, 2, 3),
+                                                            ("small", 3, 5, 2, 2)])
+def test_hybrid_matches_oracle(name, switch, pmax, precond, levels):
     import paper_2407_08901_gb300 as S
     w, rp, c, v = make_matrix(name)
     tol = 1e-9 if precond else 1e-7
     # both settings of the continuation's second projection are covered
     reorth = 0 if precond else 1
     opts = S.sppc_default_opts(p_max=pmax, hybrid=1, switch_order=switch, precond=precond, hybrid_maxit=400,
-                               reorth=reorth)
+                               reorth=reorth, precond_levels=levels)
     # the oracle restarts when a block would not fit in max_blocks = p_max + 1
     h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, opts)
     try:
         conv, th, rs, st = S.sppc_solve(h, w.k, tol=tol)
         kw = dict(switch_order=switch, tol=tol, max_blocks=pmax + 1, precond=["none", "jacobi", "lead"][precond],
-                  maxit=400, reorth="cond" if reorth == 0 else "twice", lead_iters=20)
+                  maxit=400, reorth="cond" if reorth == 0 else "twice", lead_iters=20,
+                  lead_rows=int(w.level_offsets[levels]) if precond == 2 else None)
         ref_th, ref_rs, ref_conv, rec = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, **kw)
         # the same run with 1e-15 relative noise on every expansion block: how far
         # rounding-sized differences carry at each step (the block Krylov case with

@@ -107,3 +107,15 @@ def test_lead_preconditioner_converges_to_dense_eigenvalues(small_matrix):
     assert conv and np.all(rs <= 1e-8)
     gap = np.abs(np.diff(lam)).min()
     assert np.all(np.abs(th - lam[: w.k]) <= 10 * (rs * np.abs(th)) ** 2 / gap + 1e-12)
+
+
+def test_lead_block_over_more_levels_converges_to_the_same_eigenvalues():
+    """precond="lead" with a leading block of two levels (lead_rows) reaches the
+    same eigenpairs as with the small space alone, in no more steps here."""
+    w, rp, c, v = make_matrix("c1")
+    kw = dict(switch_order=2, tol=1e-9, max_blocks=7, precond="lead", maxit=300, lead_iters=20)
+    th1, rs1, cv1, rec1 = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, **kw)
+    th2, rs2, cv2, rec2 = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, lead_rows=int(w.level_offsets[2]), **kw)
+    assert cv1 and cv2
+    assert np.allclose(th1, th2, rtol=1e-12, atol=0)
+    assert len(rec2) <= len(rec1)
