@@ -47,7 +47,19 @@ METRIC = "s to k eigenpairs at scaled resid 1e-6 vs FP64 SPPC; SpMM HBM GB/s vs 
 SWITCH_ORDER = 15
 TOL = 1e-6
 PRECOND = 2          # continuation: shifted diagonal + deflated leading-block solve
-PRECOND_ITERS = 10   # MINRES steps of the leading-block solve
+PRECOND_ITERS = 20   # MINRES steps of the leading-block solve
+PRECOND_LEVELS = 3   # the leading block spans levels 0-2 (77,670 rows of c2)
+
+
+def solve_opts(S, n_levels: int = 7, **kw):
+    """The timed method's options: SPPC for SWITCH_ORDER orders, then the block
+    continuation with the leading-block preconditioner; keyword overrides."""
+    base = dict(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL, precond=PRECOND,
+                precond_iters=PRECOND_ITERS, precond_levels=min(PRECOND_LEVELS, max(1, n_levels - 1)))
+    base.update(kw)
+    if base["switch_order"] > base["p_max"]:
+        base["p_max"] = base["switch_order"]
+    return S.sppc_default_opts(**base)
 
 
 def parse_args():
@@ -226,8 +238,7 @@ def run_ours(args):
     rp, c, v = W.generate(w)
     n, nnz, k = w.n, int(c.shape[0]), w.k
     kp = (k + 1) // 2 * 2
-    opts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL, timing=1,
-                               precond=PRECOND, precond_iters=PRECOND_ITERS)
+    opts = solve_opts(S, timing=1)
     stream = torch.cuda.Stream()
     h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts, stream=stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -301,7 +312,8 @@ def run_ours(args):
         "config": {"workload": f"{w.name}: n={n}, 7 levels x2.2, n1={w.small_dim}, nnz={nnz}, k={k}, FP64 values, "
                                f"seed {w.seed}",
                    "method": f"SPPC {SWITCH_ORDER} orders + block continuation preconditioned by the shifted "
-                             f"diagonal and {PRECOND_ITERS} MINRES steps on the deflated leading block",
+                             f"diagonal and {PRECOND_ITERS} MINRES steps on the deflated leading block "
+                             f"(levels 0-{PRECOND_LEVELS - 1})",
                    "l2": "flushed by a 512 MB write before every step",
                    "orders": st["orders"], "refine_steps": st["refine_steps"], "spmv_h": st["spmv_h"],
                    "converged": bool(st["converged"]), "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -330,8 +342,7 @@ def run_ours(args):
         del rows, u, bf
         for prec, key, desc in ((1, "mixed_precision", "H values rounded to FP32"),
                                 (2, "mixed_precision_bf16", "off-diagonal values rounded to BF16 (diagonal FP32)")):
-            mopts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL, timing=1,
-                                        precond=PRECOND, precond_iters=PRECOND_ITERS, precision=prec)
+            mopts = solve_opts(S, timing=1, precision=prec)
             hm = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, mopts, stream=stream)
             mt = []
             for _ in range(2):
@@ -345,8 +356,7 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 mt.append(m0.elapsed_time(m1) / 1e3)
             S.sppc_destroy(hm)
-            ropts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL,
-                                        precond=PRECOND, precond_iters=PRECOND_ITERS)
+            ropts = solve_opts(S)
             hr = S.sppc_create(rp, c, rounded[prec], w.level_offsets, w.small_dim, k, ropts, stream=stream)
             _, rth, _, _ = S.sppc_solve(hr, k, tol=TOL, stream=stream)
             S.sppc_destroy(hr)
@@ -367,8 +377,7 @@ def run_ours(args):
         from paper_2407_08901_gb300 import proposal as PR
         if os.path.exists(PR.DEFAULT_NET):
             params, mu, sd, meta = PR.load(PR.DEFAULT_NET)
-            lopts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL, timing=1,
-                                        precond=PRECOND, precond_iters=PRECOND_ITERS, proposal=1)
+            lopts = solve_opts(S, timing=1, proposal=1)
             hl = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, lopts, stream=stream)
             S.sppc_set_proposal(hl, params, mu, sd)
             lt = []
@@ -405,11 +414,10 @@ def run_ours(args):
         # wall clock around the whole batch (one worker = one by one)
         ws = W.c4_batch(64, seed=0)
         mats = [W.generate(wb) for wb in ws]
-        bopts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL,
-                                    precond=PRECOND, precond_iters=PRECOND_ITERS, precision=1, hybrid_maxit=2000)
         res = {}
         for nwork in (1, 8):
-            hs = [S.sppc_create(rpb, cb, vb, wb.level_offsets, wb.small_dim, wb.k, bopts)
+            hs = [S.sppc_create(rpb, cb, vb, wb.level_offsets, wb.small_dim, wb.k,
+                                solve_opts(S, len(wb.level_sizes), precision=1, hybrid_maxit=2000))
                   for wb, (rpb, cb, vb) in zip(ws, mats)]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -430,6 +438,28 @@ def run_ours(args):
             "converged": int(cv8.sum()), "max_scaled_resid": float(np.max(rs8)),
             "spmv_h": int(sum(x["spmv_h"] for x in st8))}
         del mats
+    if rank == 0 and world == 1 and not args.no_comparator:
+        # sensitivity to the switch point: the same method switching to the
+        # continuation after fewer SPPC orders (the paper switches at stagnation,
+        # about order 15; the timed method keeps that)
+        sw = {}
+        for so in (6, 3):
+            hs_ = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, solve_opts(S, switch_order=so),
+                                stream=stream)
+            for _ in range(2):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1.0)
+                    s0 = torch.cuda.Event(enable_timing=True)
+                    s1 = torch.cuda.Event(enable_timing=True)
+                    s0.record(stream)
+                    sconv, sth, srs, sst = S.sppc_solve(hs_, k, tol=TOL, stream=stream)
+                    s1.record(stream)
+                torch.cuda.synchronize()
+            S.sppc_destroy(hs_)
+            sw[f"switch_after_{so}_orders"] = {"value": s0.elapsed_time(s1) / 1e3, "unit": "s",
+                                               "spmv_h": sst["spmv_h"], "steps": sst["refine_steps"],
+                                               "converged": bool(sconv)}
+        line["switch_sensitivity"] = sw
     if rank == 0 and world == 1 and not args.no_comparator:
         # C2's comparator: block Lanczos from Psi^(0) (the same loop, no SPPC orders,
         # no preconditioner), one untimed-loop solve timed with CUDA events
@@ -485,8 +515,7 @@ def run_profile(args):
         torch.cuda.synchronize()
         print(f"profile spmm: {w.name}, 2 products, column tiles {S.sppc_get_layout(h)['n_chunks']}", flush=True)
     else:
-        opts = S.sppc_default_opts(p_max=SWITCH_ORDER, hybrid=1, switch_order=SWITCH_ORDER, tol=TOL,
-                                   precond=PRECOND, precond_iters=PRECOND_ITERS)
+        opts = solve_opts(S, len(w.level_sizes))
         h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts)
         conv, th, rs, st = S.sppc_solve(h, k, tol=TOL)
         torch.cuda.synchronize()

@@ -146,7 +146,8 @@ def load(path: str = DEFAULT_NET):
     return z["params"], z["mu"], z["sd"], json.loads(str(z["meta"]))
 
 
-def evaluate(seeds, net_path: str = DEFAULT_NET, n: int = 2_000_000, tol: float = 1e-6, log=print):
+def evaluate(seeds, net_path: str = DEFAULT_NET, n: int = 2_000_000, tol: float = 1e-6, precond_levels: int = 3,
+             precond_iters: int = 20, log=print):
     """Solve matrices of the 2,000,000-row law (seeds `seeds`) with SPPC (15
     orders) + preconditioned continuation, with and without the network's
     proposal; per matrix the CUDA-event time, H-vector products, continuation
@@ -162,8 +163,8 @@ def evaluate(seeds, net_path: str = DEFAULT_NET, n: int = 2_000_000, tol: float 
         rp, c, v = W.generate(w)
         rec = {"seed": int(seed)}
         for name, prop in (("without", 0), ("learned", 1)):
-            o = sppc_default_opts(p_max=15, hybrid=1, switch_order=15, precond=2, precond_iters=10, tol=tol,
-                                  proposal=prop)
+            o = sppc_default_opts(p_max=15, hybrid=1, switch_order=15, precond=2, precond_iters=precond_iters,
+                                  precond_levels=precond_levels, tol=tol, proposal=prop)
             h = sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, o)
             try:
                 if prop:
