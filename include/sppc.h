@@ -119,6 +119,10 @@ typedef struct {
                               (rows [0, max(n1, level_offsets[precond_levels])); default 1 = the
                               small space H0_hat).  More levels: a stronger preconditioner (fewer
                               continuation steps) for more work per MINRES step. */
+  int32_t minres_deflate;  /* 1 (default): the small solves of Eq. sm_lin_proj take the solution's
+                              components along the small eigensolve's other eigenvectors in closed
+                              form and run MINRES on the remainder (same solution, fewer
+                              iterations; 8-column blocks, k = 7 or 8); 0: plain MINRES */
 } sppc_opts;
 
 typedef struct {

@@ -59,7 +59,8 @@ enum CoefSlot : int {
   kTheta = 832,      // 16
   kLeadScale = 848,  // 8: 1 / ||z_j[:n1]||
   kLeadNegE = 856,   // 8: -theta_j (shift of the leading-block solve)
-  kCoefEnd = 864
+  kPosE0 = 864,      // 8: +E0 per column (right-hand side after deflation)
+  kCoefEnd = 872
 };
 
 }  // namespace
@@ -93,6 +94,11 @@ struct sppc_ctx {
          *mx = nullptr;
   // small eigensolve (n1 x 8 blocks, up to 2 per set; 3 filter sets + X + AX + tmp)
   float2* se[12] = {nullptr};
+  // the small eigensolve's b lowest eigenpairs (two blocks of n1 x 8; values
+  // ascending), kept to deflate the small solves' right-hand sides
+  float2* psib[2] = {nullptr, nullptr};
+  double* dEb = nullptr;
+  int nb_small = 0, b_small = 0;
   // FP64 scalars / small matrices
   double *dE = nullptr, *dHt = nullptr, *dGram = nullptr, *dC1 = nullptr, *dC2 = nullptr, *dR1 = nullptr,
          *dR2 = nullptr, *dTheta = nullptr, *dV = nullptr, *dDots = nullptr, *dS = nullptr;
@@ -202,6 +208,7 @@ __global__ void k_set_e0(const double* E0, int k, int kp, float2* c) {
   const int j = threadIdx.x;
   if (j >= kp) return;
   c[kShiftNegE + j] = (j < k) ? df_from_double(-E0[j]) : make_float2(0.f, 0.f);
+  c[kPosE0 + j] = (j < k) ? df_from_double(E0[j]) : make_float2(0.f, 0.f);
   c[kInvE0 + j] = (j < k) ? df_from_double(1.0 / E0[j]) : make_float2(0.f, 0.f);
 }
 
@@ -229,6 +236,19 @@ __global__ void k_inv_norm_coef(const double* d, int k, int kp, float2* out) {
 __global__ void k_neg_coef(const float2* in, int k, int kp, float2* out) {
   const int j = threadIdx.x;
   if (j < kp) out[j] = (j < k) ? df_neg(in[j]) : make_float2(0.f, 0.f);
+}
+
+// Deflation coefficients of the small solves: D[v][c] = G[v][c] / (E_v - E_c) for
+// the small eigensolve's vectors v < b other than column c's own psi_hat_c
+// (G = Psi_b^T b1, FP64, b x 8), zero elsewhere; x_defl = Psi_b D solves the
+// system exactly on span(Psi_b) minus psi_hat_c.
+__global__ void k_defl_coefs(const double* G, const double* Eb, int b, int k, float2* D) {
+  const int t = threadIdx.x;  // 16 x 8 entries, one thread each
+  if (t >= 128) return;
+  const int v = t >> 3, c = t & 7;
+  double d = 0.0;
+  if (v < b && c < k && v != c) d = G[v * 8 + c] / (Eb[v] - Eb[c]);
+  D[t] = df_from_double(d);
 }
 
 __global__ void k_neg_dots_to_coef(const double* d, int k, int kp, float2* out) {
@@ -758,6 +778,16 @@ sppc_status small_eigensolve(sppc_ctx* h) {
   for (int j = 0; j < k; ++j)
     if (std::fabs(h->E0[j]) <= 1e-8 * h->h11_norm)
       return fail(h, SPPC_ERR_ARG, "E^(0)_%d is zero: x2 = -b2/E^(0) is undefined", j);
+  // keep all b eigenpairs of the block (deflation of the small solves)
+  for (int a = 0; a < nb; ++a)
+    CK(cudaMemcpyAsync(h->psib[a], X[a], sizeof(float2) * n1 * 8, cudaMemcpyDeviceToDevice, s));
+  {
+    std::vector<double> eb(16, 0.0);
+    for (int j = 0; j < b; ++j) eb[j] = th[j];
+    CK(cudaMemcpyAsync(h->dEb, eb.data(), sizeof(double) * 16, cudaMemcpyHostToDevice, s));
+  }
+  h->nb_small = nb;
+  h->b_small = b;
   // copy columns 0..k-1 of X[0] (n1 x 8) into psi_hat (n1 x kp)
   CK(cudaMemcpy2DAsync(h->psi_hat, sizeof(float2) * h->kp, X[0], sizeof(float2) * 8, sizeof(float2) * h->kp, n1,
                        cudaMemcpyDeviceToDevice, s));
@@ -789,8 +819,39 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
   int maxit = h->opt.minres_maxit;
   if (maxit <= 0) maxit = (int)std::min<int64_t>(200000, 20 * n1);
   int* dstat = h->dStatus + 32;
+  // Deflation by the small eigensolve's other eigenvectors (kp = 8): with
+  // Psi_b (b > k vectors, E_b) the solution on span(Psi_b) is exact,
+  // x_defl = Psi_b D, D[v][c] = (psi_v^T b1_c) / (E_v - E_c) (v != c); MINRES then
+  // solves for the rest, right-hand side b1 - (H0_hat - E) x_defl (exact whatever
+  // the accuracy of Psi_b), projected off psi_hat_c.  Same solution, far fewer
+  // iterations: the eigenvalues nearest the shift are gone from the operator.
+  const bool defl = h->opt.minres_deflate && kp == 8 && h->b_small > h->k;
+  if (defl) {
+    BlockList Lb;
+    Lb.n = h->nb_small;
+    Lb.p[0] = h->psib[0];
+    Lb.p[1] = h->psib[1];
+    CK(gram(Lb, h->b1, 8, 0, n1, h->dGram, h->partials, h->partial_cap, s));
+    k_defl_coefs<<<1, 128, 0, s>>>(h->dGram, h->dEb, h->b_small, h->k, h->dCoefBig); count_launch();
+    CK(cudaGetLastError());
+    CK(update(h->T2, nullptr, nullptr, Lb, h->dCoefBig, 8, 0, n1, s));       // x_defl
+    Epi e;
+    e.alpha = c + kNegOnes;
+    e.beta = c + kPosE0;
+    e.gamma = c + kOnes;
+    e.Z = h->b1;
+    CK(spmm(h->H11, 8, h->T2, h->T1, e, s));                                // b1 - (H - E) x_defl
+    h->stats.spmv_h11 += h->k;
+    const float2* A[1] = {h->psi_hat};
+    const float2* B[1] = {h->T1};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, h->k, kp, c + kDefl); count_launch();
+    CK(cudaGetLastError());
+    CK(combine_diag(h->b1, h->T1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
+  }
   CK(minres_persistent(h->H11c, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
                        h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s));
+  if (defl) CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->T2), c + kOnes, kp, 0, n1, s));  // + x_defl
   // x -= psi_hat (psi_hat^T x): keep the solution on the complement of psi_hat_k
   float2* x = h->mx;
   {
@@ -1181,6 +1242,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->precision = 0;
   o->proposal = 0;
   o->precond_levels = 1;
+  o->minres_deflate = 1;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1242,6 +1304,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "opts.proposal = 1 needs hybrid = 1 and precond 1 or 2");
   if (opt.precond_levels < 1 || opt.precond_levels > n_levels)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precond_levels must be in [1, n_levels]");
+  if (opt.minres_deflate != 0 && opt.minres_deflate != 1)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.minres_deflate must be 0 or 1");
   if (opt.precision != 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
@@ -1496,6 +1560,9 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     for (float2** q : {&h->b1, &h->mv, &h->mvprev, &h->mp, &h->my, &h->mw1, &h->mw2, &h->mx})
       A(q, (size_t)std::max(n1, h->n_lead) * kp);
     for (int i = 0; i < 12; ++i) A(&h->se[i], (size_t)n1 * 8);
+    A(&h->psib[0], (size_t)n1 * 8);
+    A(&h->psib[1], (size_t)n1 * 8);
+    D(&h->dEb, 16);
     D(&h->dE, (size_t)(kMaxBlocks + 2) * 8);
     D(&h->dHt, (size_t)h->mmax * h->mmax);
     D(&h->dGram, (size_t)kMaxBlocks * 64);

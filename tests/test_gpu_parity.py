@@ -199,8 +199,12 @@ def _compare_orders(S, h, ref, k, rtol_theta=1e-10):
             assert np.all(np.abs(info["E"]) <= 1e-12 * np.abs(ref.E0).max())
 
 
-@pytest.mark.parametrize("name,orders", [("small", 8), ("c1", 2)])
+SMALL8 = W.Workload("small8", [300, 500, 900, 1300], 40, 8, seed=7)
+
+
+@pytest.mark.parametrize("name,orders", [("small", 8), ("c1", 2), (SMALL8, 8), ("c2mini", 3)])
 def test_sppc_matches_oracle_order_by_order(name, orders):
+    """k = 8 workloads exercise the deflated small solves (opts.minres_deflate)."""
     S, w, rp, c, v, h = _create(name, p_max=max(orders, 2))
     try:
         conv, th, rs, st = S.sppc_solve(h, w.k, tol=1e-300, p_max=orders)
