@@ -123,6 +123,7 @@ typedef struct {
                               components along the small eigensolve's other eigenvectors in closed
                               form and run MINRES on the remainder (same solution, fewer
                               iterations; 8-column blocks, k = 7 or 8); 0: plain MINRES */
+  int32_t small_degree;    /* degree of the Chebyshev filter in the small eigensolve (default 12) */
 } sppc_opts;
 
 typedef struct {

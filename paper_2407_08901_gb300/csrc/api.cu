@@ -668,7 +668,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
   CKS(ortho_set(h, X, Tmp, nb, b));
   const double upper = h->h11_hi;
   std::vector<double> th(16), res(16);
-  const int degree = 12;
+  const int degree = h->opt.small_degree;
   int outer = 0;
   for (; outer < 400; ++outer) {
     // Rayleigh-Ritz on the block
@@ -1243,6 +1243,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->proposal = 0;
   o->precond_levels = 1;
   o->minres_deflate = 1;
+  o->small_degree = 12;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1306,6 +1307,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "opts.precond_levels must be in [1, n_levels]");
   if (opt.minres_deflate != 0 && opt.minres_deflate != 1)
     return fail(nullptr, SPPC_ERR_ARG, "opts.minres_deflate must be 0 or 1");
+  if (opt.small_degree < 1 || opt.small_degree > 200)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.small_degree must be in [1, 200]");
   if (opt.precision != 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
