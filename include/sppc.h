@@ -96,7 +96,7 @@ typedef struct {
                               accelerator; both give identical results (other widths always use 1) */
   int32_t reorth;          /* continuation's block Gram-Schmidt: 0 = second projection only when the
                               first kept less than half of some column's norm (default), 1 = always
-                              twice (SPPC orders always project twice, Eq. blkGS) */
+                              twice (SPPC orders always project twice: Eq. blkGS applied twice) */
   int32_t precond_iters;   /* MINRES steps of the leading-block preconditioner (precond 2; default 20) */
   int32_t precision;       /* 0: FP64 path (double-float, default).  1: mixed precision: H's values
                               rounded to FP32 everywhere; the products with H during the solve in FP32
@@ -123,7 +123,9 @@ typedef struct {
                               components along the small eigensolve's other eigenvectors in closed
                               form and run MINRES on the remainder (same solution, fewer
                               iterations; 8-column blocks, k = 7 or 8); 0: plain MINRES */
-  int32_t small_degree;    /* degree of the Chebyshev filter in the small eigensolve (default 12) */
+  int32_t small_degree;    /* degree of the Chebyshev filter in the small eigensolve (default 30; halved
+                              and redone when the filtered block is too ill-conditioned for
+                              CholeskyQR) */
 } sppc_opts;
 
 typedef struct {
@@ -147,6 +149,8 @@ typedef struct {
                                 after the FP32 phase */
   int32_t proposals_tried;   /* learned proposal: continuation steps that tried the network's block */
   int32_t proposals_kept;    /* ... and kept it (the largest scaled residual dropped) */
+  int32_t small_filter_retries; /* small eigensolve: filters redone with half the degree after a
+                                   CholeskyQR breakdown of the filtered block */
 } sppc_stats;
 
 /* Fill `o` with the defaults listed above. */

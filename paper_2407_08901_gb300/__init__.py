@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("small_eig_ms", ctypes.c_double), ("dense_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("restarts", ctypes.c_int32), ("switched_at", ctypes.c_int32),
                 ("reorth_passes", ctypes.c_int32), ("refine_df", ctypes.c_int32),
-                ("proposals_tried", ctypes.c_int32), ("proposals_kept", ctypes.c_int32)]
+                ("proposals_tried", ctypes.c_int32), ("proposals_kept", ctypes.c_int32),
+                ("small_filter_retries", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

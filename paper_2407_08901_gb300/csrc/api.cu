@@ -715,56 +715,69 @@ sppc_status small_eigensolve(sppc_ctx* h) {
       CK(cudaMemcpyAsync(h->dCoef + kCheb, v.data(), sizeof(float2) * 48, cudaMemcpyHostToDevice, s));
       return SPPC_OK;
     };
-    // Y1 = (A X - c X)/e
-    CKS(put3(1.0 / e, -c / e, 0.0));
-    Epi e1;
-    e1.alpha = h->dCoef + kCheb;
-    e1.beta = h->dCoef + kCheb + 16;
-    for (int a = 0; a < nb; ++a) CK(spmm(h->H11, 8, X[a], Y1[a], e1, s));
-    CKS(put3(2.0 / e, -2.0 * c / e, -1.0));
-    float2* setA[2] = {X[0], X[1]};
-    float2* setB[2] = {Y1[0], Y1[1]};
-    float2* setC[2] = {Y0[0], Y0[1]};
-    for (int dgi = 2; dgi <= degree; ++dgi) {
-      Epi e2;
-      e2.alpha = h->dCoef + kCheb;
-      e2.beta = h->dCoef + kCheb + 16;
-      e2.gamma = h->dCoef + kCheb + 32;
+    // A filter of high degree can leave the block too ill-conditioned for
+    // CholeskyQR (its columns collapse onto the lowest eigenvectors): then the
+    // block is restored and filtered again with half the degree.
+    for (int a = 0; a < nb; ++a)
+      CK(cudaMemcpyAsync(h->se[10 + a], X[a], sizeof(float2) * n1 * 8, cudaMemcpyDeviceToDevice, s));
+    sppc_status st_f = SPPC_OK;
+    for (int deg = degree;; deg /= 2) {
+      // Y1 = (A X - c X)/e
+      CKS(put3(1.0 / e, -c / e, 0.0));
+      Epi e1;
+      e1.alpha = h->dCoef + kCheb;
+      e1.beta = h->dCoef + kCheb + 16;
+      for (int a = 0; a < nb; ++a) CK(spmm(h->H11, 8, X[a], Y1[a], e1, s));
+      CKS(put3(2.0 / e, -2.0 * c / e, -1.0));
+      float2* setA[2] = {X[0], X[1]};
+      float2* setB[2] = {Y1[0], Y1[1]};
+      float2* setC[2] = {Y0[0], Y0[1]};
+      for (int dgi = 2; dgi <= deg; ++dgi) {
+        Epi e2;
+        e2.alpha = h->dCoef + kCheb;
+        e2.beta = h->dCoef + kCheb + 16;
+        e2.gamma = h->dCoef + kCheb + 32;
+        for (int a = 0; a < nb; ++a) {
+          e2.Z = setA[a];
+          CK(spmm(h->H11, 8, setB[a], setC[a], e2, s));
+        }
+        for (int a = 0; a < nb; ++a) {
+          float2* t0 = setA[a];
+          setA[a] = setB[a];
+          setB[a] = setC[a];
+          setC[a] = t0;
+        }
+      }
+      h->stats.spmv_h11 += (int64_t)8 * nb * deg;
+      h->stats.small_eig_iters += deg;
+      // new X = setB (the last filtered block); keep the buffers distinct
       for (int a = 0; a < nb; ++a) {
-        e2.Z = setA[a];
-        CK(spmm(h->H11, 8, setB[a], setC[a], e2, s));
+        X[a] = setB[a];
+        // the remaining two buffers become AX / Tmp / filter scratch
       }
-      for (int a = 0; a < nb; ++a) {
-        float2* t0 = setA[a];
-        setA[a] = setB[a];
-        setB[a] = setC[a];
-        setC[a] = t0;
+      {
+        // re-assign scratch buffers so that none aliases X
+        std::vector<float2*> pool;
+        for (int i = 0; i < 10; ++i) pool.push_back(h->se[i]);
+        std::vector<float2*> freeb;
+        for (float2* q : pool) {
+          bool used = false;
+          for (int a = 0; a < nb; ++a) used |= (q == X[a]);
+          if (!used) freeb.push_back(q);
+        }
+        int fi = 0;
+        for (int a = 0; a < nb; ++a) AX[a] = freeb[fi++];
+        for (int a = 0; a < nb; ++a) Y0[a] = freeb[fi++];
+        for (int a = 0; a < nb; ++a) Y1[a] = freeb[fi++];
+        for (int a = 0; a < nb; ++a) Tmp[a] = freeb[fi++];
       }
+      st_f = ortho_set(h, X, Tmp, nb, b);
+      if (st_f == SPPC_OK) break;
+      if (st_f != SPPC_ERR_BREAKDOWN || deg <= 2) return st_f;
+      for (int a = 0; a < nb; ++a)
+        CK(cudaMemcpyAsync(X[a], h->se[10 + a], sizeof(float2) * n1 * 8, cudaMemcpyDeviceToDevice, s));
+      h->stats.small_filter_retries += 1;
     }
-    h->stats.spmv_h11 += (int64_t)8 * nb * degree;
-    h->stats.small_eig_iters += degree;
-    // new X = setB (the last filtered block); keep the buffers distinct
-    for (int a = 0; a < nb; ++a) {
-      X[a] = setB[a];
-      // the remaining two buffers become AX / Tmp / filter scratch
-    }
-    {
-      // re-assign scratch buffers so that none aliases X
-      std::vector<float2*> pool;
-      for (int i = 0; i < 10; ++i) pool.push_back(h->se[i]);
-      std::vector<float2*> freeb;
-      for (float2* q : pool) {
-        bool used = false;
-        for (int a = 0; a < nb; ++a) used |= (q == X[a]);
-        if (!used) freeb.push_back(q);
-      }
-      int fi = 0;
-      for (int a = 0; a < nb; ++a) AX[a] = freeb[fi++];
-      for (int a = 0; a < nb; ++a) Y0[a] = freeb[fi++];
-      for (int a = 0; a < nb; ++a) Y1[a] = freeb[fi++];
-      for (int a = 0; a < nb; ++a) Tmp[a] = freeb[fi++];
-    }
-    CKS(ortho_set(h, X, Tmp, nb, b));
   }
   if (outer >= 400) return fail(h, SPPC_ERR_BREAKDOWN, "small eigensolve did not converge");
   // psi_hat = first k columns (block 0), padded to kp
@@ -915,7 +928,7 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
 
 // Block Gram-Schmidt (Eq. blkGS) of src against Q blocks 0..p-1, then
 // CholeskyQR2 (Eq. QR) into Q block p (Eq. Qp).  SPPC orders apply the
-// projector twice, as Eq. blkGS does.  With `cond` (the block continuation) the
+// projector of Eq. blkGS twice (CGS2, against round-off).  With `cond` (the block continuation) the
 // second application runs only when the first removed more than half of some
 // column's norm (criterion of Daniel, Gragg, Kaufman and Stewart with Kahan's
 // factor: after a pass that keeps at least half the norm the result is
@@ -1243,7 +1256,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->proposal = 0;
   o->precond_levels = 1;
   o->minres_deflate = 1;
-  o->small_degree = 12;
+  o->small_degree = 30;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
