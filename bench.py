@@ -75,9 +75,10 @@ def parse_args():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision solve")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-matrix workload")
-    ap.add_argument("--profile", default="none", choices=["none", "spmm", "solve"],
-                    help="run the workload's SpMM twice (spmm) or one solve with the bench options (solve) and "
-                         "exit, for profilers; prints no JSON line")
+    ap.add_argument("--profile", default="none", choices=["none", "spmm", "solve", "minres"],
+                    help="run the workload's SpMM twice (spmm), one solve with the bench options (solve), or "
+                         "three plain SPPC orders (minres: two small-space MINRES solves, few GB held) and exit, "
+                         "for profilers; prints no JSON line")
     return ap.parse_args()
 
 
@@ -514,6 +515,11 @@ def run_profile(args):
             S.sppc_spmm(h, X, Y)
         torch.cuda.synchronize()
         print(f"profile spmm: {w.name}, 2 products, column tiles {S.sppc_get_layout(h)['n_chunks']}", flush=True)
+    elif args.profile == "minres":
+        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=3))
+        conv, th, rs, st = S.sppc_solve(h, k, tol=1e-300, p_max=3)
+        torch.cuda.synchronize()
+        print(f"profile minres: {w.name}, orders {st['orders']}, MINRES iterations {st['minres_iters']}", flush=True)
     else:
         opts = solve_opts(S, len(w.level_sizes))
         h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts)
