@@ -121,6 +121,13 @@ struct sppc_ctx {
   float* rhat32 = nullptr;                        // scaled residual entries, n x 8
   float2 *Tprop = nullptr, *Tplain = nullptr;     // proposal and plain preconditioned blocks, n x kp
   int nev = 0;                                    // Ritz pairs kept by the last Rayleigh-Ritz
+  // overlap of an SPPC order's Rayleigh-Ritz step with the next order's
+  // correction: a second stream and its own reduction scratch
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  float2* partials2 = nullptr;
+  double* dDots2 = nullptr;
+  double* pinned = nullptr;                       // host (pinned): theta[16], r2[16] of a deferred step
 
   // state
   bool started = false, corrected = false, in_refine = false, t_ready = false;
@@ -844,8 +851,9 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
     Lb.n = h->nb_small;
     Lb.p[0] = h->psib[0];
     Lb.p[1] = h->psib[1];
-    CK(gram(Lb, h->b1, 8, 0, n1, h->dGram, h->partials, h->partial_cap, s));
-    k_defl_coefs<<<1, 128, 0, s>>>(h->dGram, h->dEb, h->b_small, h->k, h->dCoefBig); count_launch();
+    // (dC2, not dGram: this may run beside a Rayleigh-Ritz step, which uses dGram)
+    CK(gram(Lb, h->b1, 8, 0, n1, h->dC2, h->partials, h->partial_cap, s));
+    k_defl_coefs<<<1, 128, 0, s>>>(h->dC2, h->dEb, h->b_small, h->k, h->dCoefBig); count_launch();
     CK(cudaGetLastError());
     CK(update(h->T2, nullptr, nullptr, Lb, h->dCoefBig, 8, 0, n1, s));       // x_defl
     Epi e;
@@ -897,7 +905,7 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
 // 2k are kept for a thick restart), Ritz residuals (Eq. rrn).  Optionally writes
 // the Ritz vectors (Z) and the preconditioned residual block (T, see ritz_resid).
 sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, float2* T = nullptr,
-                    const float2* diag = nullptr) {
+                    const float2* diag = nullptr, bool defer = false) {
   PhaseRange nvtx_range("rayleigh_ritz");
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
@@ -916,6 +924,12 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
                 h->dDots, h->partials, h->partial_cap, want_z ? Z : nullptr, ldz, k, T, diag,
                 (float)h->opt.precond_clamp, s, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
                 lead ? h->n_lead : 0));
+  if (defer) {
+    // results land in pinned host memory; rr_finish() reads them after a sync
+    CK(cudaMemcpyAsync(h->pinned, h->dTheta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->pinned + 16, h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+    return SPPC_OK;
+  }
   std::vector<double> th(k), r2(kp);
   CK(cudaMemcpyAsync(th.data(), h->dTheta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(r2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
@@ -923,6 +937,18 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
   h->theta = th;
   h->resid.assign(k, 0.0);
   for (int j = 0; j < k; ++j) h->resid[j] = std::sqrt(std::max(r2[j], 0.0)) / std::fabs(th[j]);
+  return SPPC_OK;
+}
+
+// Completes a deferred rr_core: waits for its stream, then Ritz values and
+// scaled residuals from the pinned copies.
+sppc_status rr_finish(sppc_ctx* h, cudaStream_t s) {
+  CK(cudaStreamSynchronize(s));
+  const int k = h->k;
+  h->theta.assign(h->pinned, h->pinned + k);
+  h->resid.assign(k, 0.0);
+  for (int j = 0; j < k; ++j)
+    h->resid[j] = std::sqrt(std::max(h->pinned[16 + j], 0.0)) / std::fabs(h->pinned[j]);
   return SPPC_OK;
 }
 
@@ -1277,7 +1303,12 @@ sppc_status sppc_small_syev(const double* S, int32_t m, int32_t lds, int32_t nev
 
 sppc_status sppc_destroy(sppc_handle h) {
   if (!h) return SPPC_OK;
+  if (h->stream2) cudaStreamSynchronize(h->stream2);
   for (void* p : h->allocs) cudaFree(p);
+  if (h->stream2) cudaStreamDestroy(h->stream2);
+  if (h->ev_a) cudaEventDestroy(h->ev_a);
+  if (h->ev_b) cudaEventDestroy(h->ev_b);
+  if (h->pinned) cudaFreeHost(h->pinned);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   delete h;
   return SPPC_OK;
@@ -1869,6 +1900,62 @@ sppc_status verify_df(sppc_ctx* h) {
   return SPPC_OK;
 }
 
+// One SPPC order's Rayleigh-Ritz step (the order is h->p, corrected), with the
+// next order's correction overlapped on a second stream when `next`: the
+// correction needs only H Psi^(p) (the recycled product), not the Ritz pairs,
+// and its small-space MINRES leaves most of the GPU idle while the Gram,
+// projected eigensolve and Ritz residuals of this order run beside it.  The
+// correction uses its own reduction scratch (partials2, dDots2); everything else
+// it writes (Psi and Q block p+1, the MINRES vectors, its coefficient slots) the
+// Rayleigh-Ritz step does not touch.  Returns in *pre whether the next order's
+// correction is done (then h->p = order + 1 and h->corrected is set).
+static sppc_status overlap_order(sppc_ctx* h, bool next, bool* pre) {
+  cudaStream_t s = h->stream;
+  const int p = h->p, kp = h->kp;
+  const int64_t n = h->n;
+  *pre = false;
+  if (next && !h->stream2) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = dalloc(h, &h->partials2, (size_t)h->partial_cap);
+    if (e == cudaSuccess) e = dalloc(h, &h->dDots2, 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, sizeof(double) * 32);
+    if (e != cudaSuccess) return fail(h, SPPC_ERR_CUDA, "overlap setup: %s", cudaGetErrorString(e));
+  }
+  // W_p = H q^(p), then H Psi^(p) = W_{0..p-1} C + W_p R (Eq. HPsip): all the
+  // next correction needs
+  CKS(big_spmm(h, blk(h->Q, n, kp, p), blk(h->W, n, kp, p), kp));
+  h->stats.spmv_h += h->k;
+  CK(update(h->HPsi, nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dRecycle, kp, 0, n, s));
+  if (next) CK(cudaEventRecord(h->ev_a, s));  // the correction waits for H Psi^(p) only
+  CKS(rr_core(h, p, false, nullptr, 0, nullptr, nullptr, next));
+  const size_t rec_p = h->rec.size() - 1;
+  h->corrected = false;
+  h->stats.orders = p;
+  if (next) {
+    CK(cudaStreamWaitEvent(h->stream2, h->ev_a, 0));
+    float2* part0 = h->partials;
+    double* dots0 = h->dDots;
+    h->partials = h->partials2;
+    h->dDots = h->dDots2;
+    const sppc_status st = sppc_correct(h, h->stream2);
+    h->partials = part0;
+    h->dDots = dots0;
+    h->stream = s;
+    CK(cudaEventRecord(h->ev_b, h->stream2));
+    CK(cudaStreamWaitEvent(s, h->ev_b, 0));
+    if (st != SPPC_OK) return st;
+    *pre = true;
+    CKS(rr_finish(h, s));
+  }
+  OrderRec& r = h->rec[rec_p];
+  r.theta = h->theta;
+  r.resid = h->resid;
+  if (h->opt.timing) CKS(collect_timing(h));
+  return SPPC_OK;
+}
+
 sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, double* Z, int64_t ldz,
                        double* resid, sppc_stats* stats, void* stream) {
   if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
@@ -1888,11 +1975,23 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
   CKS(sppc_start(h, nullptr, nullptr, stream));
   bool conv = all_converged(h, tol);
   const int sppc_orders = h->opt.hybrid ? std::min(p_max, h->opt.switch_order) : p_max;
-  while (!conv && h->p < sppc_orders) {
-    CKS(sppc_correct(h, stream));
-    CKS(sppc_rayleigh_ritz(h, nullptr, nullptr, stream));
+  // SPPC orders; each order's Rayleigh-Ritz step overlaps the next correction
+  bool pending = false;  // the next order's correction is already done
+  while (!conv && h->p + (pending ? 0 : 1) <= sppc_orders) {
+    if (!pending) CKS(sppc_correct(h, stream));
+    const int p = h->p;
+    CKS(overlap_order(h, p + 1 <= sppc_orders, &pending));
     conv = all_converged(h, tol);
+    if (conv && pending) {
+      // converged at order p: drop the overlapped correction of order p + 1
+      h->rec.pop_back();
+      h->p = p;
+      h->corrected = false;
+      pending = false;
+    }
+    if (!pending && h->p >= sppc_orders) break;
   }
+  h->stats.orders = h->p;
   h->stats.orders = h->p;
   if (h->opt.hybrid) {
     h->stats.switched_at = h->p;
