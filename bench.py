@@ -416,7 +416,7 @@ def run_ours(args):
         ws = W.c4_batch(64, seed=0)
         mats = [W.generate(wb) for wb in ws]
         res = {}
-        for nwork in (1, 8):
+        for nwork in (1, 8, 16):
             hs = [S.sppc_create(rpb, cb, vb, wb.level_offsets, wb.small_dim, wb.k,
                                 solve_opts(S, len(wb.level_sizes), precision=1, hybrid_maxit=2000))
                   for wb, (rpb, cb, vb) in zip(ws, mats)]
@@ -428,14 +428,16 @@ def run_ours(args):
             for hb in hs:
                 S.sppc_destroy(hb)
         t1, cv1, st1, rs1 = res[1]
-        t8, cv8, st8, rs8 = res[8]
+        best = min((8, 16), key=lambda q: res[q][0])
+        t8, cv8, st8, rs8 = res[best]
         line["batched"] = {
             "workload": "64 matrices, n log-uniform in [5e3, 2e5] (total " + str(sum(wb.n for wb in ws)) +
                         " rows, " + str(int(sum(m[1].shape[0] for m in mats))) + " entries), 3-6 levels x2.2, "
                         "~80 entries/row, k=4, seeds 0..63",
-            "method": "concurrent batch runner, 8 host threads x 1 CUDA stream each, largest first; each problem "
-                      "SPPC + preconditioned continuation, FP32 products with H",
+            "method": f"concurrent batch runner, {best} host threads x 1 CUDA stream each, largest first; each "
+                      "problem SPPC + preconditioned continuation, FP32 products with H",
             "value": t8, "unit": "s", "matrices_per_s": 64 / t8, "one_by_one_s": t1,
+            "workers_s": {str(q): res[q][0] for q in res},
             "converged": int(cv8.sum()), "max_scaled_resid": float(np.max(rs8)),
             "spmv_h": int(sum(x["spmv_h"] for x in st8))}
         del mats
