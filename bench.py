@@ -446,9 +446,9 @@ def run_ours(args):
         # continuation after fewer SPPC orders (the paper switches at stagnation,
         # about order 15; the timed method keeps that)
         sw = {}
-        for so in (6, 3):
-            hs_ = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, solve_opts(S, switch_order=so),
-                                stream=stream)
+        for so in (6, 3, "stall"):
+            so_opts = (solve_opts(S, switch_stall=0.9) if so == "stall" else solve_opts(S, switch_order=so))
+            hs_ = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, so_opts, stream=stream)
             for _ in range(2):
                 with torch.cuda.stream(stream):
                     flush.fill_(1.0)
@@ -459,9 +459,10 @@ def run_ours(args):
                     s1.record(stream)
                 torch.cuda.synchronize()
             S.sppc_destroy(hs_)
-            sw[f"switch_after_{so}_orders"] = {"value": s0.elapsed_time(s1) / 1e3, "unit": "s",
-                                               "spmv_h": sst["spmv_h"], "steps": sst["refine_steps"],
-                                               "converged": bool(sconv)}
+            key = ("switch_when_a_residual_drops_less_than_10pct" if so == "stall"
+                   else f"switch_after_{so}_orders")
+            sw[key] = {"value": s0.elapsed_time(s1) / 1e3, "unit": "s", "spmv_h": sst["spmv_h"],
+                       "steps": sst["refine_steps"], "switched_at": sst["switched_at"], "converged": bool(sconv)}
         line["switch_sensitivity"] = sw
     if rank == 0 and world == 1 and not args.no_comparator:
         # C2's comparator: block Lanczos from Psi^(0) (the same loop, no SPPC orders,

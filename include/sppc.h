@@ -126,6 +126,10 @@ typedef struct {
   int32_t small_degree;    /* degree of the Chebyshev filter in the small eigensolve (default 30; halved
                               and redone when the filtered block is too ill-conditioned for
                               CholeskyQR) */
+  double switch_stall;     /* hybrid: also leave SPPC (before switch_order) at the first order p >= 2
+                              where some eigenpair's scaled residual exceeds switch_stall times its
+                              value at order p - 1 (Sec. 6: switch when a residual starts to
+                              stagnate); 0 (default) = off */
 } sppc_opts;
 
 typedef struct {

@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
                 ("precond", ctypes.c_int32), ("precond_clamp", ctypes.c_double), ("hybrid_blocks", ctypes.c_int32),
                 ("spmm_kernel", ctypes.c_int32), ("reorth", ctypes.c_int32), ("precond_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("proposal", ctypes.c_int32), ("precond_levels", ctypes.c_int32),
-                ("minres_deflate", ctypes.c_int32), ("small_degree", ctypes.c_int32)]
+                ("minres_deflate", ctypes.c_int32), ("small_degree", ctypes.c_int32),
+                ("switch_stall", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

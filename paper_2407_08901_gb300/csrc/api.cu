@@ -1283,6 +1283,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->precond_levels = 1;
   o->minres_deflate = 1;
   o->small_degree = 30;
+  o->switch_stall = 0.0;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1353,6 +1354,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "opts.minres_deflate must be 0 or 1");
   if (opt.small_degree < 1 || opt.small_degree > 200)
     return fail(nullptr, SPPC_ERR_ARG, "opts.small_degree must be in [1, 200]");
+  if (!(opt.switch_stall >= 0.0) || opt.switch_stall > 1.0)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.switch_stall must be in [0, 1]");
   if (opt.precision != 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
@@ -1982,14 +1985,22 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     const int p = h->p;
     CKS(overlap_order(h, p + 1 <= sppc_orders, &pending));
     conv = all_converged(h, tol);
-    if (conv && pending) {
-      // converged at order p: drop the overlapped correction of order p + 1
+    // the paper's switch rule (Sec. 6): leave SPPC once the scaled residual of
+    // some eigenpair stops dropping (ratio to the previous order above switch_stall)
+    bool stalled = false;
+    if (h->opt.hybrid && h->opt.switch_stall > 0.0 && p >= 2 && (size_t)p < h->rec.size()) {
+      const std::vector<double>& r0 = h->rec[p - 1].resid;
+      for (int j = 0; j < h->k && j < (int)r0.size(); ++j)
+        stalled |= h->resid[j] > h->opt.switch_stall * r0[j];
+    }
+    if ((conv || stalled) && pending) {
+      // converged (or switching) at order p: drop the overlapped correction of order p + 1
       h->rec.pop_back();
       h->p = p;
       h->corrected = false;
       pending = false;
     }
-    if (!pending && h->p >= sppc_orders) break;
+    if (stalled || (!pending && h->p >= sppc_orders)) break;
   }
   h->stats.orders = h->p;
   h->stats.orders = h->p;

@@ -87,3 +87,27 @@ def test_refine_step_entry_point():
             S.sppc_correct(h)  # SPPC orders cannot follow the continuation
     finally:
         S.sppc_destroy(h)
+
+
+def test_switch_on_stagnation():
+    """opts.switch_stall: SPPC is left at the first order where some scaled
+    residual stops dropping (Sec. 6); the continuation still converges to the
+    dense eigenvalues."""
+    import paper_2407_08901_gb300 as S
+    from conftest import dense
+    w, rp, c, v = make_matrix("c1")
+    lam = np.linalg.eigvalsh(dense(rp, c, v))[: w.k]
+    opts = S.sppc_default_opts(p_max=12, hybrid=1, switch_order=12, precond=2, switch_stall=0.9, tol=1e-9,
+                               hybrid_maxit=400)
+    h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, opts)
+    try:
+        conv, th, rs, st = S.sppc_solve(h, w.k, tol=1e-9)
+        sw = st["switched_at"]
+        assert conv and np.allclose(th, lam, rtol=1e-10, atol=0)
+        if sw < 12:
+            # the rule fired: some residual at order sw exceeds 0.9x its value at sw - 1
+            a = S.sppc_order_info(h, sw - 1, w.k)["resid"]
+            b = S.sppc_order_info(h, sw, w.k)["resid"]
+            assert np.any(b > 0.9 * a)
+    finally:
+        S.sppc_destroy(h)
