@@ -47,78 +47,83 @@ __global__ void k_finish(const float2* __restrict__ partials, int64_t nchunks, i
 
 // One CTA = 8 warps and `chunk` rows.  A warp covers 32/KP rows at a time, lane
 // (row u, column i) with i = lane % KP: the A block rows are read contiguously
-// and the lanes of one row share (broadcast) its B row.  Blocks of A go in
-// pairs: one B row feeds the dots of two blocks (half the B loads per
-// multiply-add).  Each lane accumulates the KP dots (i, j) of both blocks;
-// lanes with equal i and the 8 warps are then combined.
+// and the lanes of one row share (broadcast) its B row.  Each lane accumulates
+// the KP dots (i, j); lanes with equal i and the 8 warps are then combined.
 template <int KP>
 __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restrict__ B, int64_t r0, int64_t r1,
                                               int64_t chunk, float2* __restrict__ partials) {
   constexpr int RPW = 32 / KP;   // rows per warp step (KP = 6 leaves 2 lanes idle)
-  __shared__ float2 red[8][2 * KP * KP];
+  __shared__ float2 red[8][KP * KP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = lane % KP, u = lane / KP;
   const bool active = u < RPW;
   const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * chunk;
   const int64_t c1 = min(c0 + chunk, r1);
   const int nout = A.n * KP * KP;
-  for (int a = 0; a < A.n; a += 2) {
-    const bool two = a + 1 < A.n;
+  for (int a = 0; a < A.n; ++a) {
     const float2* __restrict__ Aa = A.p[a];
-    const float2* __restrict__ Ab = two ? A.p[a + 1] : A.p[a];
-    float sh[2][KP], sl[2][KP];
+    float sh[KP], sl[KP];
 #pragma unroll
-    for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-      for (int j = 0; j < KP; ++j) sh[bb][j] = sl[bb][j] = 0.f;
+    for (int j = 0; j < KP; ++j) sh[j] = sl[j] = 0.f;
+    int cnt = 0;
     if (active) {
-      int cnt = 0;
-      for (int64_t r = c0 + warp * RPW + u; r < c1; r += 8 * RPW) {
+      // two rows per iteration, loads issued before the multiply-adds
+      int64_t r = c0 + warp * RPW + u;
+      for (; r + 8 * RPW < c1; r += 16 * RPW) {
+        const int64_t r2 = r + 8 * RPW;
         const float2 av = Aa[r * KP + i];
-        const float2 bv = Ab[r * KP + i];
-        float4 b[KP / 2];
+        const float2 av2 = Aa[r2 * KP + i];
+        float4 b[KP / 2], b2[KP / 2];
         const float4* br = reinterpret_cast<const float4*>(B + r * KP);
-#pragma unroll
-        for (int q = 0; q < KP / 2; ++q) b[q] = br[q];
+        const float4* br2 = reinterpret_cast<const float4*>(B + r2 * KP);
 #pragma unroll
         for (int q = 0; q < KP / 2; ++q) {
-          acc_mac(sh[0][2 * q], sl[0][2 * q], av, make_float2(b[q].x, b[q].y));
-          acc_mac(sh[0][2 * q + 1], sl[0][2 * q + 1], av, make_float2(b[q].z, b[q].w));
+          b[q] = br[q];
+          b2[q] = br2[q];
         }
-        if (two) {
 #pragma unroll
-          for (int q = 0; q < KP / 2; ++q) {
-            acc_mac(sh[1][2 * q], sl[1][2 * q], bv, make_float2(b[q].x, b[q].y));
-            acc_mac(sh[1][2 * q + 1], sl[1][2 * q + 1], bv, make_float2(b[q].z, b[q].w));
-          }
+        for (int q = 0; q < KP / 2; ++q) {
+          acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b[q].x, b[q].y));
+          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b[q].z, b[q].w));
         }
-        if (((++cnt) & 15) == 0) {
 #pragma unroll
-          for (int bb = 0; bb < 2; ++bb)
+        for (int q = 0; q < KP / 2; ++q) {
+          acc_mac(sh[2 * q], sl[2 * q], av2, make_float2(b2[q].x, b2[q].y));
+          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av2, make_float2(b2[q].z, b2[q].w));
+        }
+        if (((++cnt) & 7) == 0) {
 #pragma unroll
-            for (int j = 0; j < KP; ++j) acc_norm(sh[bb][j], sl[bb][j]);
+          for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
+        }
+      }
+      if (r < c1) {
+        const float2 av = Aa[r * KP + i];
+        const float4* br = reinterpret_cast<const float4*>(B + r * KP);
+#pragma unroll
+        for (int q = 0; q < KP / 2; ++q) {
+          const float4 b = br[q];
+          acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b.x, b.y));
+          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b.z, b.w));
         }
       }
     }
     // combine the RPW row-lanes of column i inside the warp (fixed order)
-    const int nb = two ? 2 : 1;
-    for (int bb = 0; bb < nb; ++bb) {
 #pragma unroll
-      for (int j = 0; j < KP; ++j) {
-        float2 v = active ? acc_get(sh[bb][j], sl[bb][j]) : make_float2(0.f, 0.f);
-        for (int uu = 1; uu < RPW; ++uu) {
-          const float2 o = make_float2(__shfl_sync(0xffffffffu, v.x, lane + uu * KP < 32 ? lane + uu * KP : lane),
-                                       __shfl_sync(0xffffffffu, v.y, lane + uu * KP < 32 ? lane + uu * KP : lane));
-          if (u == 0) v = df_add(v, o);
-        }
-        if (u == 0 && lane < KP) red[warp][bb * KP * KP + i * KP + j] = v;
+    for (int j = 0; j < KP; ++j) {
+      float2 v = active ? acc_get(sh[j], sl[j]) : make_float2(0.f, 0.f);
+      for (int uu = 1; uu < RPW; ++uu) {
+        const float2 o = make_float2(__shfl_sync(0xffffffffu, v.x, lane + uu * KP < 32 ? lane + uu * KP : lane),
+                                     __shfl_sync(0xffffffffu, v.y, lane + uu * KP < 32 ? lane + uu * KP : lane));
+        if (u == 0) v = df_add(v, o);
       }
+      if (u == 0 && lane < KP) red[warp][i * KP + j] = v;
     }
     __syncthreads();
-    if (threadIdx.x < nb * KP * KP) {
+    if (threadIdx.x < KP * KP) {
       float2 t = red[0][threadIdx.x];
       for (int w = 1; w < 8; ++w) t = df_add(t, red[w][threadIdx.x]);
-      partials[static_cast<int64_t>(blockIdx.x) * nout + a * KP * KP + threadIdx.x] = t;
+      const int ii = threadIdx.x / KP, jj = threadIdx.x % KP;
+      partials[static_cast<int64_t>(blockIdx.x) * nout + (a * KP + ii) * KP + jj] = t;
     }
     __syncthreads();
   }
