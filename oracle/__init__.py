@@ -18,6 +18,7 @@ hybrid.py    SPPC followed by a block continuation (preconditioned residual
 lanczos.py   Block Lanczos with full reorthogonalisation (eigenvalue truth for
              matrices too large for a dense eigendecomposition).
 spmm.py      CSR x dense block product (plain C loop with OpenMP, or SciPy).
+rmmdiis.py   SPPC followed by per-pair RMM-DIIS (the paper's hybrid, Sec. 6).
 learned.py   Learned correction proposal (not in the paper): features, the
              per-row network, its gradient, Adam, the regression target built
              from exact eigenvectors, and the keep rule.
