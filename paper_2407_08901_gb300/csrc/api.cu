@@ -60,7 +60,9 @@ enum CoefSlot : int {
   kLeadScale = 848,  // 8: 1 / ||z_j[:n1]||
   kLeadNegE = 856,   // 8: -theta_j (shift of the leading-block solve)
   kPosE0 = 864,      // 8: +E0 per column (right-hand side after deflation)
-  kCoefEnd = 872
+  kRmmNegTh = 872,   // 8: -theta_j of the RMM-DIIS iterate
+  kRmmScale = 880,   // 8: 1 / ||x_j|| (RMM-DIIS normalisation)
+  kCoefEnd = 888
 };
 
 }  // namespace
@@ -128,6 +130,12 @@ struct sppc_ctx {
   float2* partials2 = nullptr;
   double* dDots2 = nullptr;
   double* pinned = nullptr;                       // host (pinned): theta[16], r2[16] of a deferred step
+  // RMM-DIIS (opts.hybrid = 2): per-column DIIS Gram matrices, theta, step
+  // lengths, flags and coefficients; rmm_x = the current iterate block
+  double *rmm_G = nullptr, *rmm_th = nullptr, *rmm_lam = nullptr, *rmm_g = nullptr;
+  int *rmm_frozen = nullptr, *rmm_status = nullptr;
+  float2* rmm_coef = nullptr;
+  float2* rmm_x = nullptr;
 
   // state
   bool started = false, corrected = false, in_refine = false, t_ready = false;
@@ -256,6 +264,107 @@ __global__ void k_defl_coefs(const double* G, const double* Eb, int b, int k, fl
   double d = 0.0;
   if (v < b && c < k && v != c) d = G[v * 8 + c] / (Eb[v] - Eb[c]);
   D[t] = df_from_double(d);
+}
+
+// RMM-DIIS: theta_j = (x^T w) / (x^T x) per column (dots at d[0..kp) = x^T x,
+// d[kp..2kp) = x^T w); -theta as a double-float coefficient and theta in FP64.
+__global__ void k_rmm_theta(const double* d, int k, int kp, float2* negth, double* th) {
+  const int j = threadIdx.x;
+  if (j >= kp) return;
+  const double t = (j < k && d[j] > 0.0) ? d[kp + j] / d[j] : 0.0;
+  th[j] = t;
+  negth[j] = df_from_double(-t);
+}
+
+// RMM-DIIS history step, one thread per column: the nh active ring slots end at
+// `cur` (slot[t] = cur - nh + 1 + t mod nslot); g (nh x kp, FP64) holds
+// r_slot[t]^T r_cur; G (kp x 8 x 8) is each column's Gram of the stored
+// residuals, updated in row/column `cur`.  Solves [G 1; 1^T 0][c; mu] = [0; 1] (G's diagonal raised by 1e-14 of
+// its largest entry) by Gaussian elimination with partial pivoting and writes
+// the coefficients per slot (coef[slot * 8 + j], double-float; zero for
+// inactive slots).  Frozen columns get c = e_cur.  status[j] = 1 on a singular
+// system (then also c = e_cur).
+__global__ void k_diis(const double* g, int nslot, int cur, int nh, double* G, const int* frozen, int k, int kp,
+                       float2* coef, int* status) {
+  const int j = threadIdx.x;
+  if (j >= kp) return;
+  double* Gj = G + (size_t)j * 64;
+  int slot[8];
+  for (int t = 0; t < nh; ++t) slot[t] = (cur - (nh - 1) + t + nslot) % nslot;
+  for (int t = 0; t < nh; ++t) {
+    Gj[cur * 8 + slot[t]] = g[t * kp + j];
+    Gj[slot[t] * 8 + cur] = g[t * kp + j];
+  }
+  double c[8];
+  for (int a = 0; a < 8; ++a) c[a] = 0.0;
+  bool ok = j < k && !frozen[j];
+  if (ok) {
+    double M[9][10];
+    const int m = nh;
+    double mx = 0.0;
+    for (int t = 0; t < m; ++t) mx = fmax(mx, Gj[slot[t] * 8 + slot[t]]);
+    for (int a = 0; a < m; ++a) {
+      for (int b = 0; b < m; ++b) M[a][b] = Gj[slot[a] * 8 + slot[b]];
+      M[a][a] += 1e-14 * fmax(mx, 1e-300);
+      M[a][m] = 1.0;
+      M[a][m + 1] = 0.0;
+    }
+    for (int b = 0; b < m; ++b) M[m][b] = 1.0;
+    M[m][m] = 0.0;
+    M[m][m + 1] = 1.0;
+    const int N = m + 1;
+    for (int col = 0; col < N && ok; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < N; ++r)
+        if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+      if (!(fabs(M[piv][col]) > 0.0)) {
+        ok = false;
+        break;
+      }
+      if (piv != col)
+        for (int q = 0; q <= N; ++q) {
+          const double t = M[col][q];
+          M[col][q] = M[piv][q];
+          M[piv][q] = t;
+        }
+      for (int r = col + 1; r < N; ++r) {
+        const double f = M[r][col] / M[col][col];
+        for (int q = col; q <= N; ++q) M[r][q] -= f * M[col][q];
+      }
+    }
+    if (ok) {
+      double x[9];
+      for (int r = N - 1; r >= 0; --r) {
+        double t = M[r][N];
+        for (int q = r + 1; q < N; ++q) t -= M[r][q] * x[q];
+        x[r] = t / M[r][r];
+      }
+      for (int t = 0; t < m; ++t) c[slot[t]] = x[t];
+    } else if (j < k && !frozen[j]) {
+      status[j] = 1;
+    }
+  }
+  if (!ok) c[cur] = 1.0;
+  for (int a = 0; a < 8; ++a) coef[a * 8 + j] = (j < k) ? df_from_double(c[a]) : make_float2(0.f, 0.f);
+}
+
+// RMM-DIIS trial vector: Y = Xb - lam_j Rb / (D - theta_j), every |D_i - theta_j|
+// clamped to >= clamp (Jacobi preconditioner); lam_j = 0 keeps Xb.
+__global__ void k_rmm_step(const float2* __restrict__ Xb, const float2* __restrict__ Rb,
+                           const float2* __restrict__ diag, const double* __restrict__ th,
+                           const double* __restrict__ lam, float clamp, int k, int kp, int64_t n, float2* Y) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * kp) return;
+  const int64_t i = t / kp;
+  const int j = static_cast<int>(t % kp);
+  if (j >= k || lam[j] == 0.0) {
+    Y[t] = j < k ? Xb[t] : make_float2(0.f, 0.f);
+    return;
+  }
+  float2 den = df_sub(diag[i], df_from_double(th[j]));
+  if (fabsf(den.x) < clamp) den = make_float2(den.x < 0.f ? -clamp : clamp, 0.f);
+  const float2 step = df_mul(df_from_double(lam[j]), df_div(Rb[t], den));
+  Y[t] = df_sub(Xb[t], step);
 }
 
 __global__ void k_neg_dots_to_coef(const double* d, int k, int kp, float2* out) {
@@ -1232,6 +1341,130 @@ sppc_status refine_step(sppc_ctx* h) {
   return SPPC_OK;
 }
 
+// SPPC + per-pair RMM-DIIS (opts.hybrid = 2; Sec. 6): from the Ritz vectors of
+// the last Rayleigh-Ritz step, each column runs its own RMM-DIIS (DIIS over the
+// last `depth` = min(8, p_max + 1) residuals, Jacobi-preconditioned step of
+// length 1), all columns in one 8-column product per iteration; a column stops
+// (is frozen) once its scaled residual meets tol.  The SPPC basis Q / W is no
+// longer needed and holds the history ring (x in Q blocks, r in W blocks).
+sppc_status rmm_run(sppc_ctx* h, double tol) {
+  PhaseRange nvtx_range("rmm_diis");
+  cudaStream_t s = h->stream;
+  const int k = h->k, kp = h->kp;
+  const int64_t n = h->n;
+  const int d = std::min(8, h->pmax + 1);
+  float2* c = h->dCoef;
+  if (!h->rmm_G) {
+    cudaError_t e = dalloc(h, &h->rmm_G, (size_t)8 * 64);
+    if (e == cudaSuccess) e = dalloc(h, &h->rmm_th, 16);
+    if (e == cudaSuccess) e = dalloc(h, &h->rmm_lam, 16);
+    if (e == cudaSuccess) e = dalloc(h, &h->rmm_g, 64);
+    if (e == cudaSuccess) e = dalloc(h, &h->rmm_frozen, 16);
+    if (e == cudaSuccess) e = dalloc(h, &h->rmm_status, 16);
+    if (e == cudaSuccess) e = dalloc(h, &h->rmm_coef, 64);
+    if (e != cudaSuccess) return fail(h, SPPC_ERR_OOM, "RMM-DIIS buffers: %s", cudaGetErrorString(e));
+  }
+  float2* Wt = blk(h->Psi, n, kp, 0);
+  float2* Xb = blk(h->Psi, n, kp, 1);
+  float2* Rb = blk(h->Psi, n, kp, 2);
+  BlockList Lx, Lr;
+  Lx.n = Lr.n = d;
+  float2* hx[8];
+  float2* hr[8];
+  for (int a = 0; a < d; ++a) {
+    hx[a] = blk(h->Q, n, kp, a);
+    hr[a] = blk(h->W, n, kp, a);
+    Lx.p[a] = hx[a];
+    Lr.p[a] = hr[a];
+  }
+  auto normalise = [&](float2* X) -> sppc_status {
+    const float2* A[1] = {X};
+    const float2* B[1] = {X};
+    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+    k_inv_norm_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kRmmScale); count_launch();
+    CK(cudaGetLastError());
+    CK(combine_diag(X, nullptr, nullptr, one(X), c + kRmmScale, kp, 0, n, s));
+    return SPPC_OK;
+  };
+  // x_0: the Ritz vectors Z = Q Y of the last Rayleigh-Ritz step, normalised
+  CK(update(Xb, nullptr, nullptr, blocks(h->Q, n, kp, 0, h->p + 1), h->dY, kp, 0, n, s));
+  CK(cudaMemcpyAsync(hx[0], Xb, sizeof(float2) * n * kp, cudaMemcpyDeviceToDevice, s));
+  CKS(normalise(hx[0]));
+  CK(cudaMemsetAsync(h->rmm_G, 0, sizeof(double) * 8 * 64, s));
+  CK(cudaMemsetAsync(h->rmm_status, 0, sizeof(int) * 16, s));
+  std::vector<int> frozen(16, 1);
+  for (int j = 0; j < k; ++j) frozen[j] = 0;
+  std::vector<double> lam(16, 0.0);
+  std::vector<double> th(kp), rr(kp);
+  int cur = 0, nh = 0;
+  for (;;) {
+    float2* X = hx[cur];
+    CKS(big_spmm(h, X, Wt, kp));
+    h->stats.spmv_h += k;
+    {
+      const float2* A[2] = {X, X};
+      const float2* B[2] = {X, Wt};
+      CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+    }
+    k_rmm_theta<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kRmmNegTh, h->rmm_th); count_launch();
+    CK(cudaGetLastError());
+    CK(combine_diag(hr[cur], Wt, c + kOnes, one(X), c + kRmmNegTh, kp, 0, n, s));   // r = w - theta x
+    {
+      const float2* A[1] = {hr[cur]};
+      const float2* B[1] = {hr[cur]};
+      CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+    }
+    CK(cudaMemcpyAsync(th.data(), h->rmm_th, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(rr.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->theta.assign(th.begin(), th.begin() + k);
+    h->resid.assign(k, 0.0);
+    bool all = true;
+    for (int j = 0; j < k; ++j) {
+      h->resid[j] = std::sqrt(std::max(rr[j], 0.0)) / std::fabs(th[j]);
+      if (h->resid[j] <= tol) frozen[j] = 1;
+      all = all && frozen[j];
+    }
+    OrderRec r;
+    r.theta = h->theta;
+    r.resid = h->resid;
+    r.angle.assign(k, 0.0);
+    h->rec.push_back(r);
+    h->rmm_x = X;
+    if (all || h->stats.refine_steps >= h->opt.hybrid_maxit) break;
+    h->stats.refine_steps += 1;
+    nh = std::min(nh + 1, d);
+    // r_a^T r_cur for the active slots, four pairs per call
+    for (int t0 = 0; t0 < nh; t0 += 4) {
+      const float2* A[4];
+      const float2* B[4];
+      const int nq = std::min(4, nh - t0);
+      for (int q = 0; q < nq; ++q) {
+        A[q] = hr[(cur - (nh - 1) + t0 + q + d) % d];
+        B[q] = hr[cur];
+      }
+      CK(coldots(A, B, nq, kp, 0, n, h->rmm_g + (size_t)t0 * kp, h->partials, h->partial_cap, s));
+    }
+    for (int j = 0; j < 16; ++j) lam[j] = frozen[j] ? 0.0 : 1.0;
+    CK(cudaMemcpyAsync(h->rmm_frozen, frozen.data(), sizeof(int) * 16, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->rmm_lam, lam.data(), sizeof(double) * 16, cudaMemcpyHostToDevice, s));
+    k_diis<<<1, 32, 0, s>>>(h->rmm_g, d, cur, nh, h->rmm_G, h->rmm_frozen, k, kp, h->rmm_coef, h->rmm_status);
+    count_launch();
+    CK(cudaGetLastError());
+    CK(combine_diag(Xb, nullptr, nullptr, Lx, h->rmm_coef, kp, 0, n, s));   // x_bar
+    CK(combine_diag(Rb, nullptr, nullptr, Lr, h->rmm_coef, kp, 0, n, s));   // r_bar
+    const int next = (cur + 1) % d;
+    k_rmm_step<<<static_cast<unsigned>((n * kp + 255) / 256), 256, 0, s>>>(
+        Xb, Rb, h->dDiag, h->rmm_th, h->rmm_lam, (float)h->opt.precond_clamp, k, kp, n, hx[next]);
+    count_launch();
+    CK(cudaGetLastError());
+    CKS(normalise(hx[next]));
+    cur = next;
+    if (h->opt.timing) CKS(collect_timing(h));
+  }
+  return SPPC_OK;
+}
+
 bool all_converged(const sppc_ctx* h, double tol) {
   for (double r : h->resid)
     if (!(r <= tol)) return false;
@@ -1345,6 +1578,9 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.reorth != 0 && opt.reorth != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.reorth must be 0 or 1");
   if (opt.precond < 0 || opt.precond > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precond must be 0, 1 or 2");
   if (opt.precision < 0 || opt.precision > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precision must be 0, 1 or 2");
+  if (opt.hybrid < 0 || opt.hybrid > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.hybrid must be 0, 1 or 2");
+  if (opt.hybrid == 2 && (opt.precision != 0 || opt.proposal != 0))
+    return fail(nullptr, SPPC_ERR_ARG, "opts.hybrid = 2 (RMM-DIIS) runs with precision 0 and no proposal");
   if (opt.proposal != 0 && opt.proposal != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.proposal must be 0 or 1");
   if (opt.proposal == 1 && (opt.hybrid != 1 || opt.precond < 1))
     return fail(nullptr, SPPC_ERR_ARG, "opts.proposal = 1 needs hybrid = 1 and precond 1 or 2");
@@ -2003,8 +2239,12 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     if (stalled || (!pending && h->p >= sppc_orders)) break;
   }
   h->stats.orders = h->p;
-  h->stats.orders = h->p;
-  if (h->opt.hybrid) {
+  if (h->opt.hybrid == 2) {
+    h->stats.switched_at = h->p;
+    h->in_refine = true;
+    if (!conv) CKS(rmm_run(h, tol));
+    conv = all_converged(h, tol);
+  } else if (h->opt.hybrid) {
     h->stats.switched_at = h->p;
     h->in_refine = true;
     // mixed precision: the FP32 phase stops at max(tol, 1e-6) or when its largest
@@ -2046,7 +2286,12 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
       h->stats.refine_df += 1;
     }
   }
-  if (Z) CKS(rr_core(h, h->p, true, Z, ldz));
+  if (Z) {
+    if (h->opt.hybrid == 2 && h->rmm_x && h->in_refine)
+      CK(df_to_f64(h->rmm_x, h->kp, Z, ldz, h->k, 0, h->n, s));   // each pair's own vector
+    else
+      CKS(rr_core(h, h->p, true, Z, ldz));
+  }
   if (h->opt.precision != 0 && !fresh) {
     // plain SPPC in mixed precision: Rayleigh quotients and residuals of the Ritz
     // vectors from double-float products

@@ -40,7 +40,7 @@ def _small():
 @pytest.mark.parametrize("case,status", [
     ("n1_not_level", 3), ("k_zero", 1), ("k_nine", 1), ("levels_bad", 3), ("unsorted", 1), ("col_range", 1),
     ("nan", 11), ("asym", 2), ("rowptr", 1), ("spmm_kernel", 1), ("reorth", 1), ("precond", 1), ("precision", 1),
-    ("precision_k", 1), ("precond_levels", 1), ("switch_stall", 1),
+    ("precision_k", 1), ("precond_levels", 1), ("switch_stall", 1), ("hybrid", 1), ("rmm_mixed", 1),
 ])
 def test_create_rejects_bad_input(case, status):
     import paper_2407_08901_gb300 as S
@@ -51,7 +51,11 @@ def test_create_rejects_bad_input(case, status):
                                reorth=-1 if case == "reorth" else 0, precond=3 if case == "precond" else 1,
                                precision={"precision": 3, "precision_k": 2}.get(case, 0),
                                precond_levels=99 if case == "precond_levels" else 1,
-                               switch_stall=-0.5 if case == "switch_stall" else 0.0)
+                               switch_stall=-0.5 if case == "switch_stall" else 0.0,
+                               hybrid={"hybrid": 3, "rmm_mixed": 2}.get(case, 0))
+    if case == "rmm_mixed":
+        opts.precision = 1
+        k = 8
     if case == "n1_not_level":
         n1 = n1 + 1
     elif case == "k_zero":
