@@ -80,7 +80,10 @@ typedef struct {
                               columns (at most 255 tiles) */
   int32_t hybrid;          /* 0: plain SPPC (Alg. 2, default); 1: after switch_order SPPC orders continue
                               by block extension with preconditioned Ritz residuals (Sec. 5: SPPC
-                              combined with a second eigensolver started from its approximations) */
+                              combined with a second eigensolver started from its approximations);
+                              2: after switch_order orders, per-pair RMM-DIIS from the Ritz vectors
+                              (Sec. 6: DIIS over the last min(8, p_max + 1) iterates, Jacobi-
+                              preconditioned step; needs precision 0; Z returns each pair's vector) */
   int32_t switch_order;    /* SPPC orders before the continuation (default 15, Sec. 6) */
   int32_t hybrid_maxit;    /* continuation steps, k SpMVs each (default 1000) */
   int32_t precond;         /* 1: residual_j / (diag(H) - theta_j) (default); 0: none (block Krylov);
