@@ -442,6 +442,16 @@ def run_ours(args):
             "spmv_h": int(sum(x["spmv_h"] for x in st8))}
         del mats
     if rank == 0 and world == 1 and not args.no_comparator:
+        # the SpMM column tile chosen by the library's autotuner (spmm_chunk_cols = -2)
+        ht = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=1, spmm_chunk_cols=-2),
+                           stream=stream)
+        tc, tms = S.sppc_spmm_tiling(ht)
+        S.sppc_destroy(ht)
+        line["spmm_tile_autotune"] = {
+            "chosen_columns_per_tile": tc,
+            "ms_per_product": {name: float(x) for name, x in zip(("untiled", "2621440", "1310720", "655360",
+                                                                  "327680"), tms) if x > 0}}
+    if rank == 0 and world == 1 and not args.no_comparator:
         # the paper's own hybrid: SPPC for 15 orders, then per-pair RMM-DIIS
         # (Jacobi preconditioner, DIIS depth 8), capped at 600 iterations
         hr_ = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k,

@@ -77,7 +77,9 @@ typedef struct {
   int32_t timing;         /* 1: time kernels with CUDA events into sppc_stats (default 0) */
   int64_t spmm_chunk_cols; /* SpMM column tile: 0 = 1310720 columns, 80 MB of an 8-column block (default;
                               keeps the gathered rows of X in L2), -1 = untiled, > 0 = that many
-                              columns (at most 255 tiles) */
+                              columns (at most 255 tiles), -2 = autotuned at create (untiled and
+                              2.6M/1.31M/655k/328k-column tiles timed on two 8-column products each;
+                              the fastest kept, see sppc_spmm_tiling) */
   int32_t hybrid;          /* 0: plain SPPC (Alg. 2, default); 1: after switch_order SPPC orders continue
                               by block extension with preconditioned Ritz residuals (Sec. 5: SPPC
                               combined with a second eigensolver started from its approximations);
@@ -361,6 +363,12 @@ sppc_status sppc_standardize(const float* F, int64_t count, const float* mu, con
  * Handles must not be used by other threads during the call. */
 sppc_status sppc_solve_batch(sppc_handle* handles, int32_t count, double tol, int32_t workers, int32_t kmax,
                              double* theta, double* resid, int32_t* converged, sppc_stats* stats);
+
+/* The SpMM column tile of h's layout (*chunk_cols: -1 untiled, else columns per
+ * tile) and, when it was autotuned (spmm_chunk_cols = -2), the measured ms per
+ * 8-column product of each candidate tried, in the order untiled, 2.6M, 1.31M,
+ * 655k, 328k columns (skipped candidates absent; candidate_ms[5], may be NULL). */
+sppc_status sppc_spmm_tiling(sppc_handle h, int64_t* chunk_cols, double* candidate_ms);
 
 /* Release everything the handle owns.  NULL is a no-op. */
 sppc_status sppc_destroy(sppc_handle h);

@@ -100,6 +100,7 @@ _SIGS = {
     "sppc_feature_moments": (_I32, [_VP, _I64, _VP, _VP, _VP]),
     "sppc_standardize": (_I32, [_VP, _I64, _VP, _VP, _VP, _VP]),
     "sppc_solve_batch": (_I32, [_VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
+    "sppc_spmm_tiling": (_I32, [_VP, _VP, _VP]),
 }
 NET_PARAMS, NET_FEATURES = 4673, 6
 EXPORTED_SYMBOLS = tuple(_SIGS)
@@ -376,6 +377,14 @@ def sppc_solve_batch(handles, kmax: int, tol: float = -1.0, workers: int = 8):
                                    th.ctypes.data, rs.ctypes.data, cv.ctypes.data, ctypes.cast(st, ctypes.c_void_p))
     _check(None, status, allow=(SPPC_OK, SPPC_NOT_CONVERGED))
     return status, th, rs, cv.astype(bool), [s.as_dict() for s in st]
+
+
+def sppc_spmm_tiling(h):
+    """(column tile of H's layout, -1 untiled; autotuner's ms per product of the candidates tried)."""
+    cc = ctypes.c_int64()
+    ms = np.zeros(5)
+    _check(h, _lib.sppc_spmm_tiling(h, ctypes.byref(cc), ms.ctypes.data))
+    return int(cc.value), ms
 
 
 def sppc_destroy(h) -> None:

@@ -136,6 +136,8 @@ struct sppc_ctx {
   int *rmm_frozen = nullptr, *rmm_status = nullptr;
   float2* rmm_coef = nullptr;
   float2* rmm_x = nullptr;
+  int64_t chunk_cols_used = 0;                    // SpMM column tile of H's layout (-1: untiled)
+  double tuned_ms[8] = {0};                       // autotuner: ms per product of each candidate
 
   // state
   bool started = false, corrected = false, in_refine = false, t_ready = false;
@@ -1473,6 +1475,75 @@ bool all_converged(const sppc_ctx* h, double tol) {
 
 }  // namespace
 
+namespace {
+
+// Candidates of the SpMM column tile: untiled, then 2.6M, 1.31M, 655k and
+// 328k columns (at most 255 tiles).  Each layout is built with a temporary
+// allocator, timed on two 8-column products (register-gather kernel, X = 0;
+// the gather pattern, not the values, sets the time) and freed.
+cudaError_t tune_chunk_cols(int64_t n, const int64_t* d_rp, const int32_t* d_ci, const double* d_va,
+                            const std::vector<int64_t>& seg, cudaStream_t s, int64_t* best, double* ms_out) {
+  const int64_t cand[5] = {-1, 2621440, 1310720, 655360, 327680};
+  float2 *X = nullptr, *Y = nullptr;
+  cudaError_t e = cudaMallocAsync(&X, sizeof(float2) * n * 8, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&Y, sizeof(float2) * n * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(float2) * n * 8, s);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  double best_ms = 1e300;
+  int slot = 0;
+  for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
+    const int64_t c = cand[ci];
+    if (c > 0 && (c >= n || (n + c - 1) / c > 255)) continue;
+    std::vector<void*> mine;
+    const DeviceAlloc tmp = [&mine](void** p, size_t bytes) {
+      const cudaError_t x = cudaMalloc(p, bytes ? bytes : 1);
+      if (x == cudaSuccess) mine.push_back(*p);
+      return x;
+    };
+    SellDeviceLayout T;
+    e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, c, s, tmp, T);
+    if (e == cudaSuccess) {
+      SellDev A;
+      A.nslices = T.nslices;
+      A.nrows = n;
+      A.nchunks = T.nchunks;
+      A.chunk_cols = T.chunk_cols;
+      A.chunk_slice = T.chunk_slice.data();
+      A.slice_ptr = T.slice_ptr_d;
+      A.slice_rows = T.rows_d;
+      A.col = T.col_d;
+      A.val = T.val_d;
+      A.row_first = T.first_d;
+      A.row_last = T.last_d;
+      e = spmm(A, 8, X, Y, Epi{}, s);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(a, s);
+      for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = spmm(A, 8, X, Y, Epi{}, s);
+      if (e == cudaSuccess) e = cudaEventRecord(b, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess) {
+        if (slot < 8) ms_out[slot++] = ms / 2.0;
+        if (ms / 2.0 < 0.98 * best_ms) {  // a finer tile must win by 2%
+          best_ms = ms / 2.0;
+          *best = c;
+        }
+      }
+    }
+    cudaStreamSynchronize(s);
+    for (void* p : mine) cudaFree(p);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (X) cudaFreeAsync(X, s);
+  if (Y) cudaFreeAsync(Y, s);
+  return e;
+}
+
+}  // namespace
+
 // Accessors used by the allocation-free SpMM entry point (noalloc.cu).
 namespace sppc {
 
@@ -1578,6 +1649,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.reorth != 0 && opt.reorth != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.reorth must be 0 or 1");
   if (opt.precond < 0 || opt.precond > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precond must be 0, 1 or 2");
   if (opt.precision < 0 || opt.precision > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precision must be 0, 1 or 2");
+  if (opt.spmm_chunk_cols < -2) return fail(nullptr, SPPC_ERR_ARG, "opts.spmm_chunk_cols must be >= -2");
   if (opt.hybrid < 0 || opt.hybrid > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.hybrid must be 0, 1 or 2");
   if (opt.hybrid == 2 && (opt.precision != 0 || opt.proposal != 0))
     return fail(nullptr, SPPC_ERR_ARG, "opts.hybrid = 2 (RMM-DIIS) runs with precision 0 and no proposal");
@@ -1714,6 +1786,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   {
     std::vector<int64_t> seg(h->lev.begin(), h->lev.end());
     int64_t chunk = opt.spmm_chunk_cols;
+    const bool tune = chunk == -2;
     if (chunk == 0) chunk = 1310720;  // 80 MB of an 8-column double-float block
     if (chunk > 0 && (n + chunk - 1) / chunk > 255) chunk = (n + 254) / 255;
     cudaStream_t s = h->stream;
@@ -1736,6 +1809,12 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       *p = q;
       return x;
     };
+    if (e == cudaSuccess && tune) {
+      // autotuner of the column tile: build the layout for each candidate, time
+      // two 8-column products, keep the fastest (ties to the coarser tile)
+      e = tune_chunk_cols(n, d_rp, d_ci, d_va, seg, s, &chunk, h->tuned_ms);
+    }
+    h->chunk_cols_used = chunk;
     if (e == cudaSuccess) e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, chunk, s, alloc, L);
     if (e == cudaSuccess) {
       // per-row constants of the learned proposal's features
@@ -2576,6 +2655,13 @@ sppc_status sppc_standardize(const float* F, int64_t count, const float* mu, con
     if (!(sd[f] > 0.f)) return fail(nullptr, SPPC_ERR_ARG, "sppc_standardize: spread %d must be positive", f);
   const cudaError_t e = standardize(F, count, mu, sd, X, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_standardize: %s", cudaGetErrorString(e));
+  return SPPC_OK;
+}
+
+sppc_status sppc_spmm_tiling(sppc_handle h, int64_t* chunk_cols, double* candidate_ms) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
+  if (chunk_cols) *chunk_cols = h->chunk_cols_used;
+  if (candidate_ms) std::copy(h->tuned_ms, h->tuned_ms + 5, candidate_ms);
   return SPPC_OK;
 }
 

@@ -274,3 +274,26 @@ def test_small_space_eigenpairs():
     assert np.allclose(E0, lam, rtol=1e-12)
     assert np.abs(H11 @ psi - psi * E0).max() <= 1e-11
     assert np.abs(psi.T @ psi - np.eye(w.k)).max() <= 1e-12
+
+
+def test_autotuned_tiling():
+    """spmm_chunk_cols = -2: the candidates that fit are timed and one is kept;
+    the product equals the one of a handle built with that tile directly."""
+    S = _lib()
+    w, rp, c, v = make_matrix("c2mini")
+    h1 = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, S.sppc_default_opts(spmm_chunk_cols=-2))
+    try:
+        cc, ms = S.sppc_spmm_tiling(h1)
+        assert cc == -1 and ms[0] > 0     # 50,000 columns: only the untiled layout is a candidate
+        h2 = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, S.sppc_default_opts(spmm_chunk_cols=cc))
+        try:
+            X = torch.from_numpy(W.random_block(w.n, 8, 5)).cuda()
+            Y1, Y2 = torch.empty_like(X), torch.empty_like(X)
+            S.sppc_spmm(h1, X, Y1)
+            S.sppc_spmm(h2, X, Y2)
+            torch.cuda.synchronize()
+            assert torch.equal(Y1, Y2)
+        finally:
+            S.sppc_destroy(h2)
+    finally:
+        S.sppc_destroy(h1)
