@@ -366,8 +366,8 @@ sppc_status sppc_solve_batch(sppc_handle* handles, int32_t count, double tol, in
 
 /* The SpMM column tile of h's layout (*chunk_cols: -1 untiled, else columns per
  * tile) and, when it was autotuned (spmm_chunk_cols = -2), the measured ms per
- * 8-column product of each candidate tried, in the order untiled, 2.6M, 1.31M,
- * 655k, 328k columns (skipped candidates absent; candidate_ms[5], may be NULL). */
+ * 8-column product of each candidate, in the order untiled, 2.6M, 1.31M, 655k,
+ * 328k columns (0 for a candidate not tried; candidate_ms[5], may be NULL). */
 sppc_status sppc_spmm_tiling(sppc_handle h, int64_t* chunk_cols, double* candidate_ms);
 
 /* Release everything the handle owns.  NULL is a no-op. */

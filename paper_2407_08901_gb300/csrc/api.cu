@@ -1492,7 +1492,6 @@ cudaError_t tune_chunk_cols(int64_t n, const int64_t* d_rp, const int32_t* d_ci,
   if (e == cudaSuccess) e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   double best_ms = 1e300;
-  int slot = 0;
   for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
     const int64_t c = cand[ci];
     if (c > 0 && (c >= n || (n + c - 1) / c > 255)) continue;
@@ -1525,7 +1524,7 @@ cudaError_t tune_chunk_cols(int64_t n, const int64_t* d_rp, const int32_t* d_ci,
       float ms = 0.f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
       if (e == cudaSuccess) {
-        if (slot < 8) ms_out[slot++] = ms / 2.0;
+        ms_out[ci] = ms / 2.0;
         if (ms / 2.0 < 0.98 * best_ms) {  // a finer tile must win by 2%
           best_ms = ms / 2.0;
           *best = c;
