@@ -370,6 +370,21 @@ sppc_status sppc_solve_batch(sppc_handle* handles, int32_t count, double tol, in
  * 328k columns (0 for a candidate not tried; candidate_ms[5], may be NULL). */
 sppc_status sppc_spmm_tiling(sppc_handle h, int64_t* chunk_cols, double* candidate_ms);
 
+/* ---- Batched SpMM: Y_i = H_i X_i for `count` handles (1..1024, untiled layouts,
+ * i.e. at most 1,310,720 columns each by default) in one persistent launch: the
+ * slices of all matrices form one index space that warps drain through a
+ * device work queue; results equal per-handle sppc_spmm bit for bit.  The
+ * plan captures the launch and the FP64 <-> double-float conversions in a CUDA
+ * graph once; each run replays it.  X[i], Y[i]: device FP64, n_i x ncols
+ * row-major (ncols in [1, 8], leading dimension ncols), fixed per plan; the
+ * handles' SpMM scratch is used, so a handle must not run other calls while a
+ * plan that holds it runs. */
+typedef struct sppc_batch_plan_s* sppc_batch_plan;
+sppc_status sppc_spmm_batch_plan(sppc_handle* handles, int32_t count, const double* const* X, double* const* Y,
+                                 int32_t ncols, sppc_batch_plan* out);
+sppc_status sppc_spmm_batch_run(sppc_batch_plan plan, void* stream);
+sppc_status sppc_spmm_batch_destroy(sppc_batch_plan plan);
+
 /* Release everything the handle owns.  NULL is a no-op. */
 sppc_status sppc_destroy(sppc_handle h);
 

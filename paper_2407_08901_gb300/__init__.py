@@ -101,6 +101,9 @@ _SIGS = {
     "sppc_standardize": (_I32, [_VP, _I64, _VP, _VP, _VP, _VP]),
     "sppc_solve_batch": (_I32, [_VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
     "sppc_spmm_tiling": (_I32, [_VP, _VP, _VP]),
+    "sppc_spmm_batch_plan": (_I32, [_VP, _I32, _VP, _VP, _I32, ctypes.POINTER(_VP)]),
+    "sppc_spmm_batch_run": (_I32, [_VP, _VP]),
+    "sppc_spmm_batch_destroy": (_I32, [_VP]),
 }
 NET_PARAMS, NET_FEATURES = 4673, 6
 EXPORTED_SYMBOLS = tuple(_SIGS)
@@ -385,6 +388,32 @@ def sppc_spmm_tiling(h):
     ms = np.zeros(5)
     _check(h, _lib.sppc_spmm_tiling(h, ctypes.byref(cc), ms.ctypes.data))
     return int(cc.value), ms
+
+
+def sppc_spmm_batch_plan(handles, Xs, Ys):
+    """Plan Y_i = H_i X_i for all handles (CUDA float64 tensors (n_i, ncols), one
+    ncols) as one persistent launch captured in a CUDA graph."""
+    count = len(handles)
+    ncols = int(Xs[0].shape[1])
+    for X, Y in zip(Xs, Ys):
+        assert X.is_cuda and Y.is_cuda and X.is_contiguous() and Y.is_contiguous()
+        assert X.shape[1] == ncols and Y.shape[1] == ncols
+    hs = (ctypes.c_void_p * count)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    xs = (ctypes.c_void_p * count)(*[X.data_ptr() for X in Xs])
+    ys = (ctypes.c_void_p * count)(*[Y.data_ptr() for Y in Ys])
+    plan = ctypes.c_void_p()
+    _check(None, _lib.sppc_spmm_batch_plan(ctypes.cast(hs, ctypes.c_void_p), count, ctypes.cast(xs, ctypes.c_void_p),
+                                           ctypes.cast(ys, ctypes.c_void_p), ncols, ctypes.byref(plan)))
+    return plan
+
+
+def sppc_spmm_batch_run(plan, stream=None) -> None:
+    _check(None, _lib.sppc_spmm_batch_run(plan, _stream(stream)))
+
+
+def sppc_spmm_batch_destroy(plan) -> None:
+    if plan:
+        _lib.sppc_spmm_batch_destroy(plan)
 
 
 def sppc_destroy(h) -> None:

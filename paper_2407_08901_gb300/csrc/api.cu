@@ -1551,6 +1551,10 @@ const SellDev* handle_matrix(sppc_handle h, int64_t* n) {
   return &h->H;
 }
 sppc_status handle_fail(sppc_handle h, sppc_status st, const char* msg) { return fail(h, st, "%s", msg); }
+void handle_scratch(sppc_handle h, float2** t1, float2** t2) {
+  *t1 = h->T1;
+  *t2 = h->T2;
+}
 void handle_size(sppc_handle h, int64_t* n, int64_t* nnz, int* k) {
   if (n) *n = h->n;
   if (nnz) *nnz = h->nnz;

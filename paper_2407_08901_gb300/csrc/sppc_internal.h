@@ -103,6 +103,17 @@ cudaError_t make_val16(const SellDev& A, uint16_t* val16, cudaStream_t s);
 // out[i] = in[i].x (the FP32 high words of double-float values)
 cudaError_t df_hi_parts(const float2* in, float* out, int64_t count, cudaStream_t s);
 
+// ---- k_spmm_batch.cu: Y_m = H_m X_m for many matrices in one persistent launch
+// (device work queue over the matrices' slices; untiled layouts)
+struct BatchItem {
+  SellDev A;
+  const float2* X;  // n_m x kp double-float
+  float2* Y;        // n_m x kp double-float
+};
+// items, prefix (nitems + 1 global slice offsets) and queue (one counter) on the device
+cudaError_t spmm_batch(const BatchItem* items, int nitems, const int64_t* prefix, int64_t total, int kp,
+                       unsigned long long* queue, cudaStream_t s);
+
 // ---- k_learned.cu: learned correction proposal (network 6 -> 64 -> 64 -> 1)
 constexpr int kNetFeatures = 6, kNetHidden = 64;
 constexpr int kNetParams = kNetHidden * kNetFeatures + kNetHidden + kNetHidden * kNetHidden + kNetHidden +

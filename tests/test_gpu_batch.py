@@ -63,3 +63,31 @@ def test_batch_rejects_small_kmax():
             S.sppc_solve_batch([h], 2, tol=1e-8, workers=1)
     finally:
         S.sppc_destroy(h)
+
+
+@pytest.mark.parametrize("ncols", [8, 4, 3])
+def test_batched_spmm_equals_per_handle_products(ncols):
+    """One persistent launch over six matrices (work queue over their slices),
+    replayed from a CUDA graph: bit-identical to per-handle products."""
+    import paper_2407_08901_gb300 as S
+    probs = _problems()
+    hs = [S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, S.sppc_default_opts()) for w, rp, c, v in probs]
+    plan = None
+    try:
+        Xs = [torch.from_numpy(W.random_block(w.n, ncols, 40 + i)).cuda() for i, (w, *_r) in enumerate(probs)]
+        Ys = [torch.full_like(X, float("nan")) for X in Xs]
+        plan = S.sppc_spmm_batch_plan(hs, Xs, Ys)
+        for _ in range(2):                       # graph replays give the same products
+            S.sppc_spmm_batch_run(plan)
+            torch.cuda.synchronize()
+            for h, X, Y in zip(hs, Xs, Ys):
+                Yr = torch.empty_like(X)
+                S.sppc_spmm(h, X, Yr)
+                torch.cuda.synchronize()
+                assert torch.equal(Y, Yr)
+            for Y in Ys:
+                Y.fill_(float("nan"))
+    finally:
+        S.sppc_spmm_batch_destroy(plan)
+        for h in hs:
+            S.sppc_destroy(h)
