@@ -135,6 +135,8 @@ typedef struct {
                               where some eigenpair's scaled residual exceeds switch_stall times its
                               value at order p - 1 (Sec. 6: switch when a residual starts to
                               stagnate); 0 (default) = off */
+  int32_t minres_ctas;     /* cap on the CTAs of the small-space MINRES kernel (0 = one per 64 rows,
+                              at most the resident limit; default) */
 } sppc_opts;
 
 typedef struct {

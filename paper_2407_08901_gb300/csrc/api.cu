@@ -982,7 +982,8 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
     CK(combine_diag(h->b1, h->T1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
   }
   CK(minres_persistent(h->H11c, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
-                       h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s));
+                       h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s,
+                       h->opt.minres_ctas));
   if (defl) CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->T2), c + kOnes, kp, 0, n1, s));  // + x_defl
   // x -= psi_hat (psi_hat^T x): keep the solution on the complement of psi_hat_k
   float2* x = h->mx;
@@ -1591,6 +1592,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->minres_deflate = 1;
   o->small_degree = 30;
   o->switch_stall = 0.0;
+  o->minres_ctas = 0;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1667,6 +1669,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "opts.small_degree must be in [1, 200]");
   if (!(opt.switch_stall >= 0.0) || opt.switch_stall > 1.0)
     return fail(nullptr, SPPC_ERR_ARG, "opts.switch_stall must be in [0, 1]");
+  if (opt.minres_ctas < 0) return fail(nullptr, SPPC_ERR_ARG, "opts.minres_ctas must be >= 0");
   if (opt.precision != 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)

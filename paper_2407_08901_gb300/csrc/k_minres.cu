@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
 cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
                               float2* V, float2* VP, float2* Y, float2* W1, float2* W2, float2* X, double tol,
                               int maxit, float2* partials, int64_t partial_cap, unsigned* bar, int* status,
-                              cudaStream_t s) {
+                              cudaStream_t s, int max_ctas) {
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -465,6 +465,7 @@ cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE
   if (grid > gmax) grid = gmax;
   if (grid < 1) grid = 1;
   if (grid > static_cast<int64_t>(kMaxPartialsPerWarp) * kMinresWarps) grid = kMaxPartialsPerWarp * kMinresWarps;
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   if (grid * 32 > partial_cap) return cudaErrorInvalidValue;
   e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
