@@ -199,8 +199,8 @@ def run_reference(args):
         if it >= args.warmup:
             times.append(t)
     # scale the sample to one whole solve by products with H (the GPU solve of this
-    # workload needs about 512 H-vector products: 15 orders + 48 continuation steps)
-    gpu_products = int(os.environ.get("SPPC_BENCH_PRODUCTS", "512"))
+    # workload needs 216 H-vector products: 15 orders + 11 continuation steps)
+    gpu_products = int(os.environ.get("SPPC_BENCH_PRODUCTS", "216"))
     per_step = float(np.mean(times))
     value = per_step * gpu_products / spmv
     sample = (f"{args.workload}: ARPACK small-space start + {orders} SPPC orders of the FP64 oracle (MINRES mode), "
