@@ -75,10 +75,10 @@ def parse_args():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision solve")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-matrix workload")
-    ap.add_argument("--profile", default="none", choices=["none", "spmm", "solve", "minres"],
-                    help="run the workload's SpMM twice (spmm), one solve with the bench options (solve), or "
-                         "three plain SPPC orders (minres: two small-space MINRES solves, few GB held) and exit, "
-                         "for profilers; prints no JSON line")
+    ap.add_argument("--profile", default="none", choices=["none", "spmm", "spmm32", "spmm16", "solve", "minres"],
+                    help="run the workload's SpMM twice (spmm; spmm32 / spmm16: the FP32- / BF16-value kernels), "
+                         "one solve with the bench options (solve), or three plain SPPC orders (minres: two "
+                         "small-space MINRES solves, few GB held) and exit, for profilers; prints no JSON line")
     return ap.parse_args()
 
 
@@ -566,7 +566,16 @@ def run_profile(args):
     w = W.config(args.workload)
     rp, c, v = W.generate(w)
     k = w.k
-    if args.profile == "spmm":
+    if args.profile in ("spmm32", "spmm16"):
+        prec = 1 if args.profile == "spmm32" else 2
+        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=1, precision=prec))
+        X = torch.from_numpy(W.random_block(w.n, 8, 1)).cuda()
+        Y = torch.empty_like(X)
+        for _ in range(2):
+            S.sppc_spmm(h, X, Y)
+        torch.cuda.synchronize()
+        print(f"profile {args.profile}: {w.name}, 2 products", flush=True)
+    elif args.profile == "spmm":
         h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=1))
         X = torch.from_numpy(W.random_block(w.n, 8, 1)).cuda()
         Y = torch.empty_like(X)
