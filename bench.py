@@ -75,10 +75,11 @@ def parse_args():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision solve")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-matrix workload")
-    ap.add_argument("--profile", default="none", choices=["none", "spmm", "spmm32", "spmm16", "solve", "minres"],
+    ap.add_argument("--profile", default="none", choices=["none", "spmm", "spmm32", "spmm16", "solve", "minres", "learned"],
                     help="run the workload's SpMM twice (spmm; spmm32 / spmm16: the FP32- / BF16-value kernels), "
                          "one solve with the bench options (solve), or three plain SPPC orders (minres: two "
-                         "small-space MINRES solves, few GB held) and exit, for profilers; prints no JSON line")
+                         "small-space MINRES solves, few GB held) or one solve with the learned proposal (learned) "
+                         "and exit, for profilers; prints no JSON line")
     return ap.parse_args()
 
 
@@ -583,6 +584,14 @@ def run_profile(args):
             S.sppc_spmm(h, X, Y)
         torch.cuda.synchronize()
         print(f"profile spmm: {w.name}, 2 products, column tiles {S.sppc_get_layout(h)['n_chunks']}", flush=True)
+    elif args.profile == "learned":
+        from paper_2407_08901_gb300 import proposal as PR
+        params, mu, sd, _ = PR.load(PR.DEFAULT_NET)
+        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, solve_opts(S, len(w.level_sizes), proposal=1))
+        S.sppc_set_proposal(h, params, mu, sd)
+        conv, th, rs, st = S.sppc_solve(h, k, tol=TOL)
+        torch.cuda.synchronize()
+        print(f"profile learned: {w.name}, converged {conv}, steps {st['refine_steps']}", flush=True)
     elif args.profile == "minres":
         h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=3))
         conv, th, rs, st = S.sppc_solve(h, k, tol=1e-300, p_max=3)
