@@ -228,10 +228,14 @@ sppc_status sppc_rayleigh_ritz(sppc_handle h, double* theta, double* resid, void
 
 /* Algorithm 2 end to end: start, then correct + rayleigh_ritz until every scaled
  * residual <= tol or p_max orders (switch_order orders when opts.hybrid, followed
- * by sppc_refine_step until converged or hybrid_maxit steps).  Outputs (any may
- * be NULL):
+ * by sppc_refine_step until converged or hybrid_maxit steps, or by per-pair
+ * RMM-DIIS when opts.hybrid = 2).  Each order's Rayleigh-Ritz step runs beside
+ * the next order's correction on a second stream the handle owns; that stream
+ * is joined to `stream` before the call returns.  Results equal the step-by-step
+ * calls.  Outputs (any may be NULL):
  *   theta[k], resid[k]: host arrays;
- *   Z: caller-owned DEVICE buffer n x k (ldz >= k), the Ritz vectors;
+ *   Z: caller-owned DEVICE buffer n x k (ldz >= k), the Ritz vectors (each
+ *      pair's own iterate after RMM-DIIS);
  *   stats: host struct.
  * tol <= 0 or p_max < 0 take the handle's options.  Returns SPPC_NOT_CONVERGED
  * (with the last order's pairs filled in) when p_max is reached first. */
