@@ -25,8 +25,8 @@
 // single element (row, half*kp/2 + seg) for every vector update.  A lane therefore
 // reads and writes only its own elements of v, w, x, y, and only p is exchanged
 // between CTAs; p is gathered with coherent loads, ordered by the barrier's
-// fences.  Every CTA computes the same scalars from the same partial sums, so no
-// broadcast is needed.  The grid barrier spins with a bound (about a second); on
+// release and acquire operations.  Every CTA computes the same scalars from the same partial sums, so no
+// broadcast is needed.  The grid barrier polls with a bound (a few seconds); on
 // time-out it raises an error flag and every CTA leaves at its next barrier.
 #include <cooperative_groups.h>
 
@@ -58,31 +58,54 @@ struct MinresKernelArgs {
   int* status;         // [0] error flag, [1] iterations run, [2 + j] iterations of column j
 };
 
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier: bar[0] counts arrivals and is never reset (barrier b takes the
+// values b G .. b G + G - 1, G CTAs), bar[1] holds the number of completed
+// barriers.  One thread per CTA arrives with an acquire-release add; the last
+// arriver of barrier b publishes b + 1 with a release store, the others poll
+// bar[1] with acquire loads.  The CTA barriers on both sides extend the
+// ordering to the CTA's other threads.  The poll is bounded (a few seconds); on
+// time-out, or when another CTA has raised the error flag, it raises the flag
+// and the CTA leaves (the others leave at their next barrier).
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int s_bar_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      bar[0] = 0;
-      __threadfence();
-      atomicExch(bar + 1, g + 1);
+    const unsigned G = gridDim.x;
+    const unsigned old = atom_add_acq_rel(bar, 1u);
+    const unsigned gen = old / G + 1;
+    int ok = 1;
+    if (old % G == G - 1) {
+      st_release_u32(bar + 1, gen);
     } else {
       unsigned spins = 0;
-      while (*gen == g) {
-        if (++spins > (1u << 24) || *reinterpret_cast<volatile int*>(err)) {
+      while (static_cast<int>(ld_acquire_u32(bar + 1) - gen) < 0) {
+        if ((++spins & 255u) == 0 && (spins > (1u << 22) || *reinterpret_cast<volatile int*>(err))) {
           atomicExch(err, 1);
+          ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
-    __threadfence();
+    s_bar_ok = ok;
   }
   __syncthreads();
-  return *reinterpret_cast<volatile int*>(err) == 0;
+  return s_bar_ok != 0;
 }
 
 // Deterministic grid reduction of nout (<= 32) double-float values: every CTA
@@ -199,7 +222,7 @@ __device__ __forceinline__ void row_product(const CsrDev& A, int64_t row, bool v
 }
 
 template <int KP>
-__global__ void __launch_bounds__(kMinresThreads) k_minres(MinresKernelArgs a) {
+__global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a) {
   constexpr int CPL = KP / 2;
   constexpr int kRowsPerWarp = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
