@@ -616,6 +616,15 @@ sppc_status upload_sell(sppc_ctx* h, SellHost& S, SellDev& D, int64_t nrows, std
   return SPPC_OK;
 }
 
+// Products with H0_hat: a few thousand rows leave each SELL lane pair a long
+// chain of dependent gathers, so up to kCsrRowsMax rows the CSR kernel (8 lanes
+// per row) runs them; the SELL layout above that.
+constexpr int64_t kCsrRowsMax = 65536;
+static cudaError_t spmm11(const sppc_ctx* h, int kp, const float2* X, float2* Y, const Epi& e, cudaStream_t s) {
+  if (h->H11c.rowptr && h->H11c.nrows <= kCsrRowsMax) return spmm_csr(h->H11c, kp, X, Y, e, s);
+  return spmm(h->H11, kp, X, Y, e, s);
+}
+
 // H0_hat (rows and columns < n1 of H) as CSR with double-float values.
 // Leading block H[:n1, :n1] as a double-float CSR on the device (columns sorted
 // within each row, so a row's block entries are its first ones).
@@ -790,7 +799,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
   int outer = 0;
   for (; outer < 400; ++outer) {
     // Rayleigh-Ritz on the block
-    for (int a = 0; a < nb; ++a) CK(spmm(h->H11, 8, X[a], AX[a], Epi{}, s));
+    for (int a = 0; a < nb; ++a) CK(spmm11(h, 8, X[a], AX[a], Epi{}, s));
     h->stats.spmv_h11 += 8 * nb;
     CKS(gram_set(h, X, AX, nb, h->dS));
     CK(syev_lowest(h->dS, 16, b, b, h->dTheta, h->dV, b, s));
@@ -845,7 +854,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
       Epi e1;
       e1.alpha = h->dCoef + kCheb;
       e1.beta = h->dCoef + kCheb + 16;
-      for (int a = 0; a < nb; ++a) CK(spmm(h->H11, 8, X[a], Y1[a], e1, s));
+      for (int a = 0; a < nb; ++a) CK(spmm11(h, 8, X[a], Y1[a], e1, s));
       CKS(put3(2.0 / e, -2.0 * c / e, -1.0));
       float2* setA[2] = {X[0], X[1]};
       float2* setB[2] = {Y1[0], Y1[1]};
@@ -857,7 +866,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
         e2.gamma = h->dCoef + kCheb + 32;
         for (int a = 0; a < nb; ++a) {
           e2.Z = setA[a];
-          CK(spmm(h->H11, 8, setB[a], setC[a], e2, s));
+          CK(spmm11(h, 8, setB[a], setC[a], e2, s));
         }
         for (int a = 0; a < nb; ++a) {
           float2* t0 = setA[a];
@@ -972,7 +981,7 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
     e.beta = c + kPosE0;
     e.gamma = c + kOnes;
     e.Z = h->b1;
-    CK(spmm(h->H11, 8, h->T2, h->T1, e, s));                                // b1 - (H - E) x_defl
+    CK(spmm11(h, 8, h->T2, h->T1, e, s));                                // b1 - (H - E) x_defl
     h->stats.spmv_h11 += h->k;
     const float2* A[1] = {h->psi_hat};
     const float2* B[1] = {h->T1};
@@ -2086,7 +2095,7 @@ sppc_status sppc_correct(sppc_handle h, void* stream) {
     e.alpha = c + kNegOnes;
     e.gamma = c + kOnes;
     e.Z = h->HPsi;
-    CK(spmm(h->H11, kp, Psim1, h->vps, e, s));
+    CK(spmm11(h, kp, Psim1, h->vps, e, s));
     h->stats.spmv_h11 += k;
   }
   // E^(p) = psi_hat^T (V Psi^(p-1))_1 = (Psi^(p-1))^T V Psi^(0) (Eq. exp_seq, V symmetric)

@@ -57,6 +57,90 @@ __global__ void __launch_bounds__(128, 7) k_spmm_sell(SellDev A, int64_t s0, int
   }
 }
 
+// Product with a short CSR matrix (the n1-row H0_hat): 8 lanes per row (4
+// entry segments x 2 column halves), 4 rows per warp.  A segment takes entries
+// seg, seg + 4, ... and issues its gathers 4 at a time, so a row of m entries
+// costs about m / 16 dependent L2 round trips; in the SELL kernel a lane pair
+// walks a whole slice row (about m / 2 of them), which sets the time of a
+// product over a few thousand rows.  The segment sums combine by shuffles in a
+// fixed order; lane (half, seg) then owns element (row, half * KP/2 + seg).
+template <int KP, bool EPI>
+__global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __restrict__ X, float2* __restrict__ Y,
+                                                  Epi epi) {
+  constexpr int CPL = KP / 2;
+  constexpr int NP = CPL / 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rq = lane >> 3, half = (lane >> 2) & 1, seg = lane & 3;
+  const int off = half * CPL;
+  const int64_t row = (static_cast<int64_t>(blockIdx.x) * 4 + warp) * 4 + rq;
+  const bool valid = row < A.nrows;
+  const uint64_t pol = policy_keep();
+  float2 ph[NP > 0 ? NP : 1], pl[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int c = 0; c < NP; ++c) ph[c] = pl[c] = make_float2(0.f, 0.f);
+  float oh = 0.f, ol = 0.f;  // odd last column
+  if (valid) {
+    const int64_t rb = __ldg(A.rowptr + row), re = __ldg(A.rowptr + row + 1);
+    for (int64_t e = rb + seg; e < re; e += 16) {
+      int cc[4];
+      float2 vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t ee = e + 4 * u;
+        cc[u] = (ee < re) ? __ldg(A.col + ee) : -1;
+        vv[u] = (ee < re) ? __ldg(A.val + ee) : make_float2(0.f, 0.f);
+      }
+      float2 xx[4][CPL];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (cc[u] >= 0) {
+          gather_half<KP>(X, cc[u], off, xx[u], pol);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) xx[u][c] = make_float2(0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int c = 0; c < NP; ++c) acc_mac2(ph[c], pl[c], vv[u], xx[u][2 * c], xx[u][2 * c + 1]);
+        if constexpr (CPL % 2 == 1) acc_mac(oh, ol, vv[u], xx[u][CPL - 1]);
+      }
+#pragma unroll
+      for (int c = 0; c < NP; ++c) {
+        acc_norm(ph[c].x, pl[c].x);
+        acc_norm(ph[c].y, pl[c].y);
+      }
+      if constexpr (CPL % 2 == 1) acc_norm(oh, ol);
+    }
+  }
+  float2 out[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    float2 v;
+    if (c < 2 * NP)
+      v = (c & 1) ? acc_get(ph[c / 2].y, pl[c / 2].y) : acc_get(ph[c / 2].x, pl[c / 2].x);
+    else
+      v = acc_get(oh, ol);
+    v = df_add(v, shfl_xor_df(v, 1));
+    v = df_add(v, shfl_xor_df(v, 2));
+    out[c] = v;
+  }
+  if (!valid || seg >= CPL) return;
+  float2 r = out[0];
+#pragma unroll
+  for (int c = 1; c < CPL; ++c)
+    if (c == seg) r = out[c];
+  const int64_t b = row * KP + off + seg;
+  if (EPI) {
+    const int j = off + seg;
+    if (epi.alpha) r = df_mul(epi.alpha[j], r);
+    if (epi.beta) r = df_add(r, df_mul(epi.beta[j], X[b]));
+    if (epi.gamma) r = df_add(r, df_mul(epi.gamma[j], epi.Z[b]));
+  }
+  Y[b] = r;
+}
+
 std::atomic<long long> g_launches{0};
 
 }  // namespace
@@ -105,6 +189,25 @@ cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t spmm_csr(const CsrDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s) {
+  if (A.nrows == 0) return cudaSuccess;
+  const unsigned g = static_cast<unsigned>((A.nrows + 15) / 16);
+  const bool has_epi = epi.alpha || epi.beta || epi.gamma;
+  switch (kp * 2 + (has_epi ? 1 : 0)) {
+    case 4: k_spmm_csr<2, false><<<g, 128, 0, s>>>(A, X, Y, epi); break;
+    case 5: k_spmm_csr<2, true><<<g, 128, 0, s>>>(A, X, Y, epi); break;
+    case 8: k_spmm_csr<4, false><<<g, 128, 0, s>>>(A, X, Y, epi); break;
+    case 9: k_spmm_csr<4, true><<<g, 128, 0, s>>>(A, X, Y, epi); break;
+    case 12: k_spmm_csr<6, false><<<g, 128, 0, s>>>(A, X, Y, epi); break;
+    case 13: k_spmm_csr<6, true><<<g, 128, 0, s>>>(A, X, Y, epi); break;
+    case 16: k_spmm_csr<8, false><<<g, 128, 0, s>>>(A, X, Y, epi); break;
+    case 17: k_spmm_csr<8, true><<<g, 128, 0, s>>>(A, X, Y, epi); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace sppc

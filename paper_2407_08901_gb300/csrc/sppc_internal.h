@@ -87,6 +87,9 @@ cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* c
 // ---- k_spmm.cu
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
 int spmm_default_grid();
+// The same product (and epilogue) for a CSR matrix of few rows: 8 lanes per row
+// (latency of the gather chains, not bandwidth, sets the time there).
+cudaError_t spmm_csr(const CsrDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
 
 // ---- k_spmm_f32.cu (mixed precision, kp = 4 or 8 columns): X (double-float)
 // rounded to FP32 into X32 (n x kp floats), Y = H X with FP32 values val32 (same
