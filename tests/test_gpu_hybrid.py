@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 @pytest.mark.parametrize("name,switch,pmax,precond,levels", [("small", 3, 5, 1, 1), ("small", 0, 4, 0, 1),
                                                             ("c1", 2, 6, 1, 1), ("small", 3, 5, 2, 1),
                                                             ("c1", 2, 6, 2, 1), ("c1", 2, 6, 2, 3),
-                                                            ("small", 3, 5, 2, 2)])
+                                                            ("small", 3, 5, 2, 2), ("c1", 2, 6, 2, 4)])
 def test_hybrid_matches_oracle(name, switch, pmax, precond, levels):
     import paper_2407_08901_gb300 as S
     w, rp, c, v = make_matrix(name)
