@@ -53,7 +53,7 @@ struct MinresKernelArgs {
   float2* X;           // out: solution
   double tol;
   int maxit;
-  float2* partials;    // [G][32] double-float
+  float2* partials;    // 2 x [32][G] double-float (alternate phases)
   unsigned* bar;       // [0] arrival count, [1] generation
   int* status;         // [0] error flag, [1] iterations run, [2 + j] iterations of column j
 };
@@ -108,35 +108,35 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
   return s_bar_ok != 0;
 }
 
-// Deterministic grid reduction of nout (<= 32) double-float values: every CTA
-// reads all CTAs' partials in the same order (warp w sums CTAs w, w+16, ...;
-// the 16 warp sums are then added in order).  Result in red_out (shared).  The
-// loads of a warp are all issued before the additions (one L2 round trip).
+// Deterministic grid reduction of nout (<= 32) double-float values.  The
+// partials are stored output-major (partials[o * G + g], G CTAs), so the 16
+// lanes of a half-warp that share output o = t / 16 read 16 consecutive CTAs'
+// values at once.  Lane (o, part) adds CTAs part, part + 16, ... in order, and
+// the 16 lane sums are combined by a fixed shuffle tree.  Every CTA computes the
+// same result; it lands in red_out (shared).
 constexpr int kMaxPartialsPerWarp = 16;  // gridDim.x <= 16 * kMinresWarps
-__device__ void reduce_partials(const float2* partials, int nout, float2* sred /*[16][32]*/, float2* red_out) {
+__device__ void reduce_partials(const float2* partials, int nout, float2* red_out) {
   const int t = threadIdx.x;
-  const int o = t & 31, part = t >> 5;
+  const int o = t >> 4, part = t & 15;
+  const int G = static_cast<int>(gridDim.x);
+  float sh = 0.f, sl = 0.f;
   if (o < nout) {
     float2 v[kMaxPartialsPerWarp];
 #pragma unroll
     for (int i = 0; i < kMaxPartialsPerWarp; ++i) {
-      const int g = part + i * kMinresWarps;
-      v[i] = (g < (int)gridDim.x) ? __ldcg(partials + static_cast<int64_t>(g) * 32 + o) : make_float2(0.f, 0.f);
+      const int g = part + i * 16;
+      v[i] = (g < G) ? __ldcg(partials + static_cast<int64_t>(o) * G + g) : make_float2(0.f, 0.f);
     }
-    float sh = 0.f, sl = 0.f;
 #pragma unroll
     for (int i = 0; i < kMaxPartialsPerWarp; ++i) {
       acc_add(sh, sl, v[i]);
       acc_norm(sh, sl);
     }
-    sred[part * 32 + o] = acc_get(sh, sl);
   }
-  __syncthreads();
-  if (t < nout) {
-    float2 r = sred[t];
-    for (int w = 1; w < kMinresWarps; ++w) r = df_add(r, sred[w * 32 + t]);
-    red_out[t] = r;
-  }
+  float2 r = acc_get(sh, sl);
+#pragma unroll
+  for (int m = 8; m > 0; m >>= 1) r = df_add(r, shfl_xor_df(r, m));
+  if (part == 0 && o < nout) red_out[o] = r;
   __syncthreads();
 }
 
@@ -238,7 +238,6 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
   const uint64_t pol = policy_keep();
   int* err = a.status;
 
-  __shared__ float2 sred[kMinresWarps * 32];
   __shared__ float2 sdot[32];
   __shared__ float2 wred[kMinresWarps][32];
   // per-column MINRES state (identical in every CTA)
@@ -250,8 +249,12 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
 
   float2 *P = a.P, *V = a.V, *VP = a.VP, *W1 = a.W1, *W2 = a.W2;
 
-  // write this CTA's partial of nq dots (columns 0..KP-1) to partials[blockIdx]
-  auto flush = [&](float (&h)[4], float (&l)[4], int nq) {
+  // Two partial buffers, used by alternate phases (init and B: 1, A: 0): a CTA
+  // rewrites a buffer only after the next grid barrier, which every CTA reaches
+  // after its reads of that buffer.
+  float2* const pbuf[2] = {a.partials, a.partials + static_cast<int64_t>(32) * gridDim.x};
+  // write this CTA's partial of nq dots (columns 0..KP-1) to buf[o * G + blockIdx]
+  auto flush = [&](float (&h)[4], float (&l)[4], int nq, float2* buf) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (q >= nq) break;
@@ -262,10 +265,14 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       if (lane < 8 && has_col) wred[warp][q * 8 + j] = v;
     }
     __syncthreads();
-    if (threadIdx.x < nq * 8) {
-      float2 sacc = wred[0][threadIdx.x];
-      for (int w = 1; w < kMinresWarps; ++w) sacc = df_add(sacc, wred[w][threadIdx.x]);
-      a.partials[static_cast<int64_t>(blockIdx.x) * 32 + threadIdx.x] = sacc;
+    {
+      // the 16 warps' values of output o, combined by a fixed shuffle tree
+      static_assert(kMinresWarps == 16, "one half-warp per output");
+      const int o = threadIdx.x >> 4, w = threadIdx.x & 15;
+      float2 v = (o < nq * 8) ? wred[w][o] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int m = 8; m > 0; m >>= 1) v = df_add(v, shfl_xor_df(v, m));
+      if (w == 0 && o < nq * 8) buf[static_cast<int64_t>(o) * gridDim.x + blockIdx.x] = v;
     }
     __syncthreads();
   };
@@ -294,9 +301,9 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
     acc_mac(dh[0], dl[0], pv, pv);
     acc_norm(dh[0], dl[0]);
   }
-  flush(dh, dl, 1);
+  flush(dh, dl, 1, pbuf[1]);
   if (!grid_barrier(a.bar, err)) return;
-  reduce_partials(a.partials, 8, sred, sdot);
+  reduce_partials(pbuf[1], 8, sdot);
   if (threadIdx.x < 8) {
     const int jj = threadIdx.x;
     const double b1 = (jj < a.k) ? sqrt(fmax(df_to_double(sdot[jj]), 0.0)) : 0.0;
@@ -368,10 +375,10 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       VP = V;
       V = t;
     }
-    flush(dh, dl, 4);
+    flush(dh, dl, 4, pbuf[0]);
     if (!grid_barrier(a.bar, err)) return;
     // ---- phase B
-    reduce_partials(a.partials, 32, sred, sdot);
+    reduce_partials(pbuf[0], 32, sdot);
     if (threadIdx.x < 8) {
       const int jj = threadIdx.x;
       double s = 0.0, al = 0.0;
@@ -398,10 +405,10 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       acc_mac(dh[0], dl[0], pn, pn);
       acc_norm(dh[0], dl[0]);
     }
-    flush(dh, dl, 1);
+    flush(dh, dl, 1, pbuf[1]);
     if (!grid_barrier(a.bar, err)) return;
     // ---- phase C
-    reduce_partials(a.partials, 8, sred, sdot);
+    reduce_partials(pbuf[1], 8, sdot);
     ++it;
     if (threadIdx.x < 8) {
       const int jj = threadIdx.x;
@@ -489,7 +496,7 @@ cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE
   if (grid < 1) grid = 1;
   if (grid > static_cast<int64_t>(kMaxPartialsPerWarp) * kMinresWarps) grid = kMaxPartialsPerWarp * kMinresWarps;
   if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
-  if (grid * 32 > partial_cap) return cudaErrorInvalidValue;
+  if (grid * 64 > partial_cap) return cudaErrorInvalidValue;
   e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(status, 0, 10 * sizeof(int), s);
