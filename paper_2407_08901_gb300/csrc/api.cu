@@ -933,7 +933,6 @@ sppc_status small_eigensolve(sppc_ctx* h) {
                        cudaMemcpyDeviceToDevice, s));
   if (k < h->kp) {
     // zero the padding columns
-    std::vector<float2> z((size_t)(h->kp - k), make_float2(0.f, 0.f));
     CK(cudaMemset2DAsync(h->psi_hat + k, sizeof(float2) * h->kp, 0, sizeof(float2) * (h->kp - k), n1, s));
   }
   std::vector<double> e0p(h->kp, 0.0);
