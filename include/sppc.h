@@ -137,6 +137,10 @@ typedef struct {
                               stagnate); 0 (default) = off */
   int32_t minres_ctas;     /* cap on the CTAs of the small-space MINRES kernel (0 = one per 64 rows,
                               at most the resident limit; default) */
+  int32_t spin_cap;        /* polls after which a grid barrier of the persistent MINRES kernel gives
+                              up: the kernel raises its error flag, every CTA leaves, and the call
+                              returns SPPC_ERR_TIMEOUT (0 = default, 4,194,304 polls, a few seconds;
+                              a tiny value forces that path, for tests) */
 } sppc_opts;
 
 typedef struct {

@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
                 ("spmm_kernel", ctypes.c_int32), ("reorth", ctypes.c_int32), ("precond_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("proposal", ctypes.c_int32), ("precond_levels", ctypes.c_int32),
                 ("minres_deflate", ctypes.c_int32), ("small_degree", ctypes.c_int32),
-                ("switch_stall", ctypes.c_double), ("minres_ctas", ctypes.c_int32)]
+                ("switch_stall", ctypes.c_double), ("minres_ctas", ctypes.c_int32),
+                ("spin_cap", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -991,7 +991,7 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
   }
   CK(minres_persistent(h->H11c, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
                        h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s,
-                       h->opt.minres_ctas));
+                       h->opt.minres_ctas, h->opt.spin_cap));
   if (defl) CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->T2), c + kOnes, kp, 0, n1, s));  // + x_defl
   // x -= psi_hat (psi_hat^T x): keep the solution on the complement of psi_hat_k
   float2* x = h->mx;
@@ -1208,7 +1208,7 @@ sppc_status lead_correction(sppc_ctx* h, float2* T) {
   int* dstat = h->dStatus + 32;
   if (iters > 0) {
     CK(minres_persistent(h->Hlead, k, kp, c + kLeadNegE, h->zlead, h->b1, h->mv, h->mvprev, h->my, h->mw1, h->mw2,
-                         h->mx, 0.0, iters, h->partials, h->partial_cap, h->dBar, dstat, s));
+                         h->mx, 0.0, iters, h->partials, h->partial_cap, h->dBar, dstat, s, 0, h->opt.spin_cap));
     // x <- x - z (z^T x)
     const float2* A[1] = {h->zlead};
     const float2* B[1] = {h->mx};
@@ -1601,6 +1601,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->small_degree = 30;
   o->switch_stall = 0.0;
   o->minres_ctas = 0;
+  o->spin_cap = 0;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1678,6 +1679,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (!(opt.switch_stall >= 0.0) || opt.switch_stall > 1.0)
     return fail(nullptr, SPPC_ERR_ARG, "opts.switch_stall must be in [0, 1]");
   if (opt.minres_ctas < 0) return fail(nullptr, SPPC_ERR_ARG, "opts.minres_ctas must be >= 0");
+  if (opt.spin_cap < 0) return fail(nullptr, SPPC_ERR_ARG, "opts.spin_cap must be >= 0");
   if (opt.precision != 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)

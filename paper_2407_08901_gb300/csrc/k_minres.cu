@@ -56,6 +56,7 @@ struct MinresKernelArgs {
   float2* partials;    // 2 x [32][G] double-float (alternate phases)
   unsigned* bar;       // [0] arrival count, [1] generation
   int* status;         // [0] error flag, [1] iterations run, [2 + j] iterations of column j
+  unsigned spin_limit; // polls after which a grid barrier gives up
 };
 
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
@@ -82,7 +83,9 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 // ordering to the CTA's other threads.  The poll is bounded (a few seconds); on
 // time-out, or when another CTA has raised the error flag, it raises the flag
 // and the CTA leaves (the others leave at their next barrier).
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+constexpr unsigned kSpinLimit = 1u << 22;  // default poll bound (a few seconds)
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned limit) {
   __shared__ int s_bar_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -95,7 +98,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
     } else {
       unsigned spins = 0;
       while (static_cast<int>(ld_acquire_u32(bar + 1) - gen) < 0) {
-        if ((++spins & 255u) == 0 && (spins > (1u << 22) || *reinterpret_cast<volatile int*>(err))) {
+        ++spins;
+        if (spins > limit || ((spins & 255u) == 0 && *reinterpret_cast<volatile int*>(err))) {
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
     acc_norm(dh[0], dl[0]);
   }
   flush(dh, dl, 1, pbuf[1]);
-  if (!grid_barrier(a.bar, err)) return;
+  if (!grid_barrier(a.bar, err, a.spin_limit)) return;
   reduce_partials(pbuf[1], 8, sdot);
   if (threadIdx.x < 8) {
     const int jj = threadIdx.x;
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       V = t;
     }
     flush(dh, dl, 4, pbuf[0]);
-    if (!grid_barrier(a.bar, err)) return;
+    if (!grid_barrier(a.bar, err, a.spin_limit)) return;
     // ---- phase B
     reduce_partials(pbuf[0], 32, sdot);
     if (threadIdx.x < 8) {
@@ -406,7 +410,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       acc_norm(dh[0], dl[0]);
     }
     flush(dh, dl, 1, pbuf[1]);
-    if (!grid_barrier(a.bar, err)) return;
+    if (!grid_barrier(a.bar, err, a.spin_limit)) return;
     // ---- phase C
     reduce_partials(pbuf[1], 8, sdot);
     ++it;
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
 cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
                               float2* V, float2* VP, float2* Y, float2* W1, float2* W2, float2* X, double tol,
                               int maxit, float2* partials, int64_t partial_cap, unsigned* bar, int* status,
-                              cudaStream_t s, int max_ctas) {
+                              cudaStream_t s, int max_ctas, int spin_cap) {
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -501,7 +505,8 @@ cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(status, 0, 10 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  MinresKernelArgs args{A, k, negE, psi, P, V, VP, Y, W1, W2, X, tol, maxit, partials, bar, status};
+  const unsigned spin_limit = spin_cap > 0 ? static_cast<unsigned>(spin_cap) : kSpinLimit;
+  MinresKernelArgs args{A, k, negE, psi, P, V, VP, Y, W1, W2, X, tol, maxit, partials, bar, status, spin_limit};
   void* params[] = {&args};
   count_launch();
   return cudaLaunchCooperativeKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(kMinresThreads), params, 0, s);

@@ -41,6 +41,7 @@ def _small():
     ("n1_not_level", 3), ("k_zero", 1), ("k_nine", 1), ("levels_bad", 3), ("unsorted", 1), ("col_range", 1),
     ("nan", 11), ("asym", 2), ("rowptr", 1), ("spmm_kernel", 1), ("reorth", 1), ("precond", 1), ("precision", 1),
     ("precision_k", 1), ("precond_levels", 1), ("switch_stall", 1), ("hybrid", 1), ("rmm_mixed", 1),
+    ("spin_cap", 1),
 ])
 def test_create_rejects_bad_input(case, status):
     import paper_2407_08901_gb300 as S
@@ -56,6 +57,8 @@ def test_create_rejects_bad_input(case, status):
     if case == "rmm_mixed":
         opts.precision = 1
         k = 8
+    if case == "spin_cap":
+        opts.spin_cap = -1
     if case == "n1_not_level":
         n1 = n1 + 1
     elif case == "k_zero":
