@@ -25,9 +25,12 @@
 // single element (row, half*kp/2 + seg) for every vector update.  A lane therefore
 // reads and writes only its own elements of v, w, x, y, and only p is exchanged
 // between CTAs; p is gathered with coherent loads, ordered by the barrier's
-// release and acquire operations.  Every CTA computes the same scalars from the same partial sums, so no
-// broadcast is needed.  The grid barrier polls with a bound (a few seconds); on
-// time-out it raises an error flag and every CTA leaves at its next barrier.
+// release and acquire operations.  Every CTA computes the same scalars from the
+// same partial sums, so no broadcast is needed; the partials of consecutive
+// phases go to two alternating buffers, so none is rewritten before every CTA
+// has read it.  The grid barrier polls with a bound (default a few seconds,
+// opts.spin_cap); on time-out it raises an error flag and every CTA leaves at
+// its next barrier.
 #include <cooperative_groups.h>
 
 #include "spmm_core.cuh"  // policy_keep
