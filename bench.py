@@ -144,6 +144,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# Nominal FP64 (DFMA) rate of one GB300: 152 SMs x 2.07 GHz x 2 FMA per clock per
+# SM x 2 FLOP = 1.26 TFLOP/s (the rate the GPU's tables give, 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def bench_config(w, nnz: int) -> dict:
+    """The workload and method, identical in both arms (no run-dependent keys)."""
+    return {"workload": f"{w.name}: n={w.n}, {len(w.level_sizes)} levels x2.2, n1={w.small_dim}, nnz={nnz}, "
+                        f"k={w.k}, FP64 values, seed {w.seed}",
+            "method": f"SPPC {SWITCH_ORDER} orders + block continuation preconditioned by the shifted diagonal and "
+                      f"{PRECOND_ITERS} MINRES steps on the deflated leading block (levels 0-{PRECOND_LEVELS - 1}), "
+                      f"to scaled residual {TOL:g}",
+            "l2": "flushed by a 512 MB write before every step"}
+
+
+def read_traffic(name: str):
+    """DRAM bytes per launch from a committed one-pass ncu summary
+    (profiles/<name>_traffic.json), or None."""
+    path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f).get("dram_bytes_per_launch")
+
+
 def spmm_algorithmic_bytes(n: int, nnz: int, kp: int) -> int:
     """Compulsory bytes of one SpMM Y = H X (kp double-float columns): matrix
     values (8 B) and column indices (4 B) once, one row-pointer word per row,
@@ -240,35 +265,37 @@ def run_ours(args):
     rp, c, v = W.generate(w)
     n, nnz, k = w.n, int(c.shape[0]), w.k
     kp = (k + 1) // 2 * 2
-    opts = solve_opts(S, timing=1)
     stream = torch.cuda.Stream()
-    h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts, stream=stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one_solve():
+    def timed_solve(hh, **kw):
+        """One solve on `stream` after a 512 MB L2 flush, timed with CUDA events."""
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            conv, th, rs, st = S.sppc_solve(h, k, tol=TOL, stream=stream)
+            out = S.sppc_solve(hh, k, tol=TOL, stream=stream, **kw)
             e1.record(stream)
         e1.synchronize()
-        return e0.elapsed_time(e1), conv, th, rs, st
+        return (e0.elapsed_time(e1),) + tuple(out)
 
+    # the headline: the method in native FP64 (every value an IEEE double, DFMA)
+    opts = solve_opts(S, len(w.level_sizes), timing=1, precision=-1)
+    h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts, stream=stream)
     for _ in range(args.warmup):
-        one_solve()
+        timed_solve(h)
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = S.sppc_kernel_launches()
     times, stats = [], []
     for _ in range(args.steps):
-        ms, conv, th, rs, st = one_solve()
+        ms, conv, th, rs, st = timed_solve(h)
         times.append(ms)
         stats.append(st)
     launches = S.sppc_kernel_launches() - launches0
-    th_last = th
+    th_last = np.asarray(th)
     barrier()
     clk = clocks.stop()
     ms_step = slowest_rank(float(np.mean(times)), dist, "cuda")
@@ -294,42 +321,66 @@ def run_ours(args):
     h2d = rp.nbytes + c.nbytes + v.nbytes + w.level_offsets.nbytes
     d2h = n * k * 8 + 2 * k * 8
 
-    # SpMM roofline from the event-timed launches inside the timed solves
-    spmm_ms = sum(s["spmm_ms"] for s in stats)
-    spmm_n = sum(s["spmm_launches"] for s in stats)
+    peak, peak_kind = peaks()
+    st = stats[-1]
+    spmm_ms = sum(s_["spmm_ms"] for s_ in stats)
+    spmm_n = sum(s_["spmm_launches"] for s_ in stats)
     avg_ms = spmm_ms / max(spmm_n, 1)
     alg = spmm_algorithmic_bytes(n, nnz, kp)
-    peak, peak_kind = peaks()
-    achieved = alg / (avg_ms * 1e-3) / 1e9
-    traffic_path = os.path.join(ROOT, "profiles", "spmm_c2_traffic.json")
-    traffic = None
-    if os.path.exists(traffic_path):
-        with open(traffic_path) as f:
-            traffic = json.load(f).get("dram_bytes_per_launch")
-    st = stats[-1]
+    flops = 2 * nnz * kp
     line = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "df64 (fp32 pair, ~48-bit)", "data": "synthetic",
-        "config": {"workload": f"{w.name}: n={n}, 7 levels x2.2, n1={w.small_dim}, nnz={nnz}, k={k}, FP64 values, "
-                               f"seed {w.seed}",
-                   "method": f"SPPC {SWITCH_ORDER} orders + block continuation preconditioned by the shifted "
-                             f"diagonal and {PRECOND_ITERS} MINRES steps on the deflated leading block "
-                             f"(levels 0-{PRECOND_LEVELS - 1})",
-                   "l2": "flushed by a 512 MB write before every step",
-                   "orders": st["orders"], "refine_steps": st["refine_steps"], "spmv_h": st["spmv_h"],
-                   "converged": bool(st["converged"]), "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": bench_config(w, nnz),
+        "solve": {"orders": st["orders"], "refine_steps": st["refine_steps"], "spmv_h": st["spmv_h"],
+                  "converged": bool(st["converged"]), "max_scaled_resid": float(np.max(rs)),
+                  "parallelism": "replicas" if world > 1 else "1 GPU"},
         "e2e": {"value": float(np.mean(e2e_times)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "roofline": {"kernel": "k_spmm_sell<8>", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes": alg, "avg_launch_ms": avg_ms, "launches": spmm_n,
+        "roofline": {"kernel": "k_spmm_sell<8, FP64>", "bound": "alu",
+                     "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                     "peak_kind": "nominal FP64 (DFMA) rate, 152 SMs x 2.07 GHz x 2 FMA/clk x 2 FLOP",
+                     "unit": "TFLOP/s", "frac": flops / (avg_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                     "traffic": read_traffic("spmm_f64_c2"), "flops_per_launch": flops,
+                     "avg_launch_ms": avg_ms, "launches": spmm_n,
+                     "hbm": {"algorithmic_bytes": alg, "achieved": alg / (avg_ms * 1e-3) / 1e9, "peak": peak,
+                             "peak_kind": peak_kind, "unit": "GB/s",
+                             "frac": alg / (avg_ms * 1e-3) / 1e9 / peak},
                      "launch_unit": "one 8-column product H X (all column tiles)"},
         "gpu_launches": int(launches),
         "clocks": clk,
-        "breakdown_ms_per_step": {kk: float(np.mean([s[kk] for s in stats]))
+        "breakdown_ms_per_step": {kk: float(np.mean([s_[kk] for s_ in stats]))
                                   for kk in ("spmm_ms", "minres_ms", "small_eig_ms", "dense_ms", "total_ms")},
     }
+    if rank == 0 and world == 1:
+        # the same method in double-float (two fp32 words, ~48 bits, on the FP32
+        # pipes): time, agreement with the FP64 run, and its SpMM against HBM
+        hd = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, solve_opts(S, len(w.level_sizes), timing=1),
+                           stream=stream)
+        timed_solve(hd)
+        dts, dstats = [], []
+        for _ in range(3):
+            ms_d, dconv, dth, drs, dst = timed_solve(hd)
+            dts.append(ms_d)
+            dstats.append(dst)
+        S.sppc_destroy(hd)
+        d_ms = sum(x["spmm_ms"] for x in dstats) / max(sum(x["spmm_launches"] for x in dstats), 1)
+        line["df64"] = {
+            "method": "the same method with double-float values and arithmetic (fp32 pairs, ~48 significant "
+                      "bits, error-free transformations on the FP32 pipes)",
+            "value": float(np.mean(dts)) / 1e3, "unit": "s", "speedup_vs_f64": ms_step / float(np.mean(dts)),
+            "spmv_h": dstats[-1]["spmv_h"], "converged": bool(dconv), "max_scaled_resid": float(np.max(drs)),
+            "max_rel_theta_diff_vs_f64": float(np.max(np.abs(np.asarray(dth) - th_last) / np.abs(th_last))),
+            "breakdown_ms_per_step": {kk: float(np.mean([x[kk] for x in dstats]))
+                                      for kk in ("spmm_ms", "minres_ms", "small_eig_ms", "dense_ms")},
+            "roofline": {"kernel": "k_spmm_sell<8>", "bound": "hbm", "achieved": alg / (d_ms * 1e-3) / 1e9,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": alg / (d_ms * 1e-3) / 1e9 / peak, "traffic": read_traffic("spmm_df64_c2"),
+                         "algorithmic_bytes": alg, "avg_launch_ms": d_ms,
+                         "gather_bytes": nnz * kp * 8,
+                         "gather_GBps": nnz * kp * 8 / (d_ms * 1e-3) / 1e9}}
+        df_th = np.asarray(dth)
     if rank == 0 and world == 1 and not args.no_mixed:
         # mixed precision (H rounded to FP32, or off-diagonals to BF16; FP32 products
         # with H during the solve, double-float elsewhere, double-float products at
@@ -358,7 +409,7 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 mt.append(m0.elapsed_time(m1) / 1e3)
             S.sppc_destroy(hm)
-            ropts = solve_opts(S)
+            ropts = solve_opts(S, len(w.level_sizes), precision=-1)
             hr = S.sppc_create(rp, c, rounded[prec], w.level_offsets, w.small_dim, k, ropts, stream=stream)
             _, rth, _, _ = S.sppc_solve(hr, k, tol=TOL, stream=stream)
             S.sppc_destroy(hr)
@@ -367,8 +418,8 @@ def run_ours(args):
                 "method": desc + "; FP32 products with H (FP32 X, FP32 accumulation) until the residual "
                           "estimates reach 1e-6, then a restart with double-float products; Gram, CholeskyQR2, "
                           "projected eigensolve and MINRES in double-float",
-                "value": mt[-1], "unit": "s", "spmv_h": mst["spmv_h"], "converged": bool(mconv),
-                "max_scaled_resid": float(np.max(mrs)), "spmm_ms": mst["spmm_ms"],
+                "value": mt[-1], "unit": "s", "speedup_vs_f64": ms_step / 1e3 / mt[-1], "spmv_h": mst["spmv_h"],
+                "converged": bool(mconv), "max_scaled_resid": float(np.max(mrs)), "spmm_ms": mst["spmm_ms"],
                 "max_rel_theta_err_vs_fp64_same_rounded_matrix": float(np.max(np.abs(mth - rth) / np.abs(rth))),
                 "max_rel_theta_diff_vs_fp64_unrounded": float(np.max(np.abs(mth - th0) / np.abs(th0)))}
         del rounded
@@ -403,7 +454,10 @@ def run_ours(args):
                 "value": lt[-1], "unit": "s", "spmv_h": lst["spmv_h"], "steps": lst["refine_steps"],
                 "proposals_kept": lst["proposals_kept"], "proposals_tried": lst["proposals_tried"],
                 "converged": bool(lconv), "max_scaled_resid": float(np.max(lrs)),
-                "vs_without": {"value": ms_step / 1e3, "spmv_h": st["spmv_h"], "steps": st["refine_steps"]},
+                "vs_without": {"what": "the same method in double-float without the network",
+                               "value": line["df64"]["value"], "spmv_h": dstats[-1]["spmv_h"],
+                               "steps": dstats[-1]["refine_steps"]},
+                "vs_f64": {"value": ms_step / 1e3, "spmv_h": st["spmv_h"]},
                 "plain_sppc_after_15_orders_max_scaled_resid": plain_resid,
                 "max_rel_theta_diff_vs_fp64": float(np.max(np.abs(np.asarray(lth) - np.asarray(th_last))
                                                            / np.abs(np.asarray(th_last))))}

@@ -22,9 +22,11 @@
  *    sppc_destroy.
  *  - Dense blocks are row-major n x ncols with a leading dimension (elements).
  *  - All values crossing the ABI are IEEE FP64.  Internally the library stores
- *    matrix values and vectors as double-float pairs (two fp32 whose sum carries
- *    ~48 significant bits) and computes with error-free fp32 transformations,
- *    because native FP64 throughput on this GPU is ~1/70 of FP32.
+ *    matrix values and vectors by default as double-float pairs (two fp32 whose
+ *    sum carries ~48 significant bits) and computes with error-free fp32
+ *    transformations, because native FP64 throughput on this GPU is ~1/70 of
+ *    FP32; opts.precision = -1 selects native FP64 storage and arithmetic
+ *    (DFMA) for the whole path instead.
  *  - A handle is not thread-safe: one host thread at a time.
  */
 #ifndef SPPC_H_
@@ -103,7 +105,11 @@ typedef struct {
                               first kept less than half of some column's norm (default), 1 = always
                               twice (SPPC orders always project twice: Eq. blkGS applied twice) */
   int32_t precond_iters;   /* MINRES steps of the leading-block preconditioner (precond 2; default 20) */
-  int32_t precision;       /* 0: FP64 path (double-float, default).  1: mixed precision: H's values
+  int32_t precision;       /* 0: FP64-quality path in double-float (default).  -1: native FP64: H's
+                              values, every vector and coefficient stored as IEEE doubles, every
+                              product, Gram, update, MINRES step and the projected eigensolve's
+                              Householder part in FP64 arithmetic (DFMA); not with hybrid = 2 or
+                              the proposal; spmm_kernel 0 falls back to 1.  1: mixed precision: H's values
                               rounded to FP32 everywhere; the products with H during the solve in FP32
                               (X rounded to FP32, FP32 accumulation); Gram, CholeskyQR2, the projected
                               eigensolve and MINRES in double-float; at the end the Ritz values and
@@ -140,7 +146,13 @@ typedef struct {
   int32_t spin_cap;        /* polls after which a grid barrier of the persistent MINRES kernel gives
                               up: the kernel raises its error flag, every CTA leaves, and the call
                               returns SPPC_ERR_TIMEOUT (0 = default, 4,194,304 polls, a few seconds;
-                              a tiny value forces that path, for tests) */
+                              a tiny value forces that path, for tests).  With spmm_kernel = 0 it
+                              also bounds each mbarrier wait of the TMA-gather SpMM to spin_cap - 1
+                              non-blocking tests (1 = give up at the first wait; 0 = about a second
+                              of clock): the warp gives up,
+                              waits for its copies in flight, raises the handle's flag, and
+                              sppc_spmm_host (or the next correction order) returns
+                              SPPC_ERR_TIMEOUT */
 } sppc_opts;
 
 typedef struct {
@@ -273,7 +285,9 @@ sppc_status sppc_get_stats(sppc_handle h, sppc_stats* stats);
  *           3: projected matrix, m x m;   4: Psi^(p) of the last order, n x k;
  *           5: E^(0), k;   6: the learned proposal's block of the last continuation step,
  *           n x k;   7: the plain preconditioned block of that step, n x k (its leading n1
- *           rows from the precond 2 solve; after sppc_proposal_samples: the raw residuals).
+ *           rows from the precond 2 solve; after sppc_proposal_samples: the raw residuals);
+ *           8: the block the last continuation step appended to the basis, before its
+ *           orthogonalisation, n x k (hybrid = 1; SPPC_ERR_STATE before the first step).
  * `count` is the number of doubles the buffer holds; returns SPPC_ERR_ARG if too small. */
 sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t count);
 
@@ -287,7 +301,8 @@ sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr
                             int64_t* chunk_slice);
 
 /* The nev lowest eigenpairs of a small dense symmetric matrix: the projected
- * eigensolve of the Rayleigh-Ritz step (Alg. 2; Eqs. tilde_H, rrn) on its own.
+ * eigensolve of the Rayleigh-Ritz step (Alg. 2; Eqs. tilde_H, rrn) on its own
+ * (the default path's double-float form).
  * S: device, m x m row-major with leading dimension lds (symmetrised as
  * (S + S^T)/2), 1 <= m <= 144; theta: device, nev values ascending; V: device,
  * m x nev row-major with leading dimension ldv >= nev, orthonormal columns.

@@ -86,7 +86,8 @@ def _ritz(Q, W, k, nev):
 def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, tol: float = 1e-6,
                 max_blocks: int = 16, maxit: int = 500, precond: str = "jacobi", clamp: float = 1e-2,
                 solver: str = "pinv", minres_tol: float = 1e-12, reorth: str = "cond",
-                perturb: float = 0.0, perturb_seed: int = 0, lead_iters: int = 20, lead_rows: int | None = None):
+                perturb: float = 0.0, perturb_seed: int = 0, lead_iters: int = 20, lead_rows: int | None = None,
+                small_eig=None):
     """Run SPPC (Algorithm 2) for up to `switch_order` orders (stopping early if
     every scaled residual is below tol), then the block continuation above.
     Returns (theta, resid, converged, records).
@@ -95,10 +96,11 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
     (seeded): a test hook that measures how far rounding-sized differences carry
     along the trajectory.  lead_rows (default n1): rows of the leading block that
     precond="lead" solves with MINRES (a level boundary; more levels than the
-    small space make a stronger preconditioner)."""
+    small space make a stronger preconditioner).  small_eig: optional eigenpairs of
+    H0_hat passed to the SPPC phase (see sppc)."""
     n = row_ptr.shape[0] - 1
     r = sppc(row_ptr, col, val, n1, k, p_max=switch_order, tol=tol, solver=solver, minres_tol=minres_tol,
-             keep=True)
+             keep=True, small_eig=small_eig)
     records = [HybridRecord("sppc", o.p, o.theta, o.resid, o.spmv, k * (o.p + 1)) for o in r.orders]
     spmv = r.spmv
     if r.converged:

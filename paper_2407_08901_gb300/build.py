@@ -23,7 +23,7 @@ def nvcc() -> str:
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-pthread",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC,-fopenmp,-pthread",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 

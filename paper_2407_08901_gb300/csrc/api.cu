@@ -18,6 +18,7 @@
 #endif
 
 #include "df.cuh"
+#include "val.cuh"
 #include "sppc.h"
 #include "sppc_internal.h"
 
@@ -69,6 +70,7 @@ enum CoefSlot : int {
 
 struct sppc_ctx {
   int64_t n = 0, nnz = 0, n1 = 0;
+  bool f64 = false;  // value slots hold IEEE doubles (opts.precision = -1), else double-float pairs
   int k = 0, kp = 0, pmax = 0, mmax = 0;
   std::vector<int64_t> lev;
   sppc_opts opt{};
@@ -122,6 +124,8 @@ struct sppc_ctx {
   bool net_ready = false;
   float* rhat32 = nullptr;                        // scaled residual entries, n x 8
   float2 *Tprop = nullptr, *Tplain = nullptr;     // proposal and plain preconditioned blocks, n x kp
+  float2* Tspare = nullptr;                       // continuation: second n x kp buffer for the appended block
+  const float2* t_last = nullptr;                 // the block the last continuation step appended
   int nev = 0;                                    // Ritz pairs kept by the last Rayleigh-Ritz
   // overlap of an SPPC order's Rayleigh-Ritz step with the next order's
   // correction: a second stream and its own reduction scratch
@@ -213,59 +217,59 @@ uint64_t mix64(uint64_t z) {
 }
 
 // ------------------------------------------------------------ tiny kernels
-__global__ void k_set_consts(float2* c) {
+__global__ void k_set_consts(float2* c, bool f64) {
   const int t = threadIdx.x;
   if (t < 16) {
-    c[kOnes + t] = make_float2(1.f, 0.f);
-    c[kNegOnes + t] = make_float2(-1.f, 0.f);
+    c[kOnes + t] = slot_put(1.0, f64);
+    c[kNegOnes + t] = slot_put(-1.0, f64);
   }
 }
 
-__global__ void k_set_e0(const double* E0, int k, int kp, float2* c) {
+__global__ void k_set_e0(const double* E0, int k, int kp, float2* c, bool f64) {
   const int j = threadIdx.x;
   if (j >= kp) return;
-  c[kShiftNegE + j] = (j < k) ? df_from_double(-E0[j]) : make_float2(0.f, 0.f);
-  c[kPosE0 + j] = (j < k) ? df_from_double(E0[j]) : make_float2(0.f, 0.f);
-  c[kInvE0 + j] = (j < k) ? df_from_double(1.0 / E0[j]) : make_float2(0.f, 0.f);
+  c[kShiftNegE + j] = (j < k) ? slot_put(-E0[j], f64) : make_float2(0.f, 0.f);
+  c[kPosE0 + j] = (j < k) ? slot_put(E0[j], f64) : make_float2(0.f, 0.f);
+  c[kInvE0 + j] = (j < k) ? slot_put(1.0 / E0[j], f64) : make_float2(0.f, 0.f);
 }
 
 // Coefficients of the right-hand side of Eq. exp_seq2 at order p:
 //  big rows:   Psi^(p)_2 = (1/E0) H Psi^(p-1)_2 - sum_{l=1}^{p-2} (E^(p-l)/E0) Psi^(l)_2
 //  small rows: b1 = -V Psi^(p-1)_1 + E^(p) psi_hat + sum_{l=1}^{p-2} E^(p-l) Psi^(l)_1
 // E is stored as dE[q*kp + j] = E^(q)_j.
-__global__ void k_rhs_coefs(const double* dE, int p, int k, int kp, float2* c) {
+__global__ void k_rhs_coefs(const double* dE, int p, int k, int kp, float2* c, bool f64) {
   const int j = threadIdx.x;
   if (j >= kp) return;
   const double e0 = dE[j];
   for (int l = 1; l <= p - 2; ++l) {
     const double el = (j < k) ? dE[(p - l) * kp + j] : 0.0;
-    c[kRhsBig + (l - 1) * 8 + j] = (j < k) ? df_from_double(-el / e0) : make_float2(0.f, 0.f);
-    c[kRhsSmall + l * 8 + j] = (j < k) ? df_from_double(el) : make_float2(0.f, 0.f);
+    c[kRhsBig + (l - 1) * 8 + j] = (j < k) ? slot_put(-el / e0, f64) : make_float2(0.f, 0.f);
+    c[kRhsSmall + l * 8 + j] = (j < k) ? slot_put(el, f64) : make_float2(0.f, 0.f);
   }
-  c[kRhsSmall + j] = (j < k) ? df_from_double(dE[p * kp + j]) : make_float2(0.f, 0.f);
+  c[kRhsSmall + j] = (j < k) ? slot_put(dE[p * kp + j], f64) : make_float2(0.f, 0.f);
 }
 
-__global__ void k_inv_norm_coef(const double* d, int k, int kp, float2* out) {
+__global__ void k_inv_norm_coef(const double* d, int k, int kp, float2* out, bool f64) {
   const int j = threadIdx.x;
-  if (j < kp) out[j] = (j < k && d[j] > 0.0) ? df_from_double(1.0 / sqrt(d[j])) : make_float2(0.f, 0.f);
+  if (j < kp) out[j] = (j < k && d[j] > 0.0) ? slot_put(1.0 / sqrt(d[j]), f64) : make_float2(0.f, 0.f);
 }
 
-__global__ void k_neg_coef(const float2* in, int k, int kp, float2* out) {
+__global__ void k_neg_coef(const float2* in, int k, int kp, float2* out, bool f64) {
   const int j = threadIdx.x;
-  if (j < kp) out[j] = (j < k) ? df_neg(in[j]) : make_float2(0.f, 0.f);
+  if (j < kp) out[j] = (j < k) ? slot_put(-slot_get(in[j], f64), f64) : make_float2(0.f, 0.f);
 }
 
 // Deflation coefficients of the small solves: D[v][c] = G[v][c] / (E_v - E_c) for
 // the small eigensolve's vectors v < b other than column c's own psi_hat_c
 // (G = Psi_b^T b1, FP64, b x 8), zero elsewhere; x_defl = Psi_b D solves the
 // system exactly on span(Psi_b) minus psi_hat_c.
-__global__ void k_defl_coefs(const double* G, const double* Eb, int b, int k, float2* D) {
+__global__ void k_defl_coefs(const double* G, const double* Eb, int b, int k, float2* D, bool f64) {
   const int t = threadIdx.x;  // 16 x 8 entries, one thread each
   if (t >= 128) return;
   const int v = t >> 3, c = t & 7;
   double d = 0.0;
   if (v < b && c < k && v != c) d = G[v * 8 + c] / (Eb[v] - Eb[c]);
-  D[t] = df_from_double(d);
+  D[t] = slot_put(d, f64);
 }
 
 // RMM-DIIS: theta_j = (x^T w) / (x^T x) per column (dots at d[0..kp) = x^T x,
@@ -369,15 +373,15 @@ __global__ void k_rmm_step(const float2* __restrict__ Xb, const float2* __restri
   Y[t] = df_sub(Xb[t], step);
 }
 
-__global__ void k_neg_dots_to_coef(const double* d, int k, int kp, float2* out) {
+__global__ void k_neg_dots_to_coef(const double* d, int k, int kp, float2* out, bool f64) {
   const int j = threadIdx.x;
-  if (j < kp) out[j] = (j < k) ? df_from_double(-d[j]) : make_float2(0.f, 0.f);
+  if (j < kp) out[j] = (j < k) ? slot_put(-d[j], f64) : make_float2(0.f, 0.f);
 }
 
 // Coefficient matrix for X - A C given C (FP64, (na*kp) x kp): writes -C as double-float.
-__global__ void k_negmat(const double* C, int count, float2* out) {
+__global__ void k_negmat(const double* C, int count, float2* out, bool f64) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) out[i] = df_from_double(-C[i]);
+  if (i < count) out[i] = slot_put(-C[i], f64);
 }
 
 __global__ void k_addmat(const double* A, const double* B, int count, double* out) {
@@ -387,14 +391,14 @@ __global__ void k_addmat(const double* A, const double* B, int count, double* ou
 
 // R = R2 * R1 (kp x kp upper triangular FP64), stored as double-float rows
 // [dst + p*kp*kp ...] of the recycle coefficient matrix; Cacc (p*kp x kp) goes first.
-__global__ void k_recycle_coefs(const double* Cacc, int p, int kp, const double* R2, const double* R1, float2* dst) {
+__global__ void k_recycle_coefs(const double* Cacc, int p, int kp, const double* R2, const double* R1, float2* dst, bool f64) {
   const int t = threadIdx.x;
-  for (int i = t; i < p * kp * kp; i += blockDim.x) dst[i] = df_from_double(Cacc[i]);
+  for (int i = t; i < p * kp * kp; i += blockDim.x) dst[i] = slot_put(Cacc[i], f64);
   for (int e = t; e < kp * kp; e += blockDim.x) {
     const int i = e / kp, j = e % kp;
     double s = 0.0;
     for (int l = 0; l < kp; ++l) s += R2[i * kp + l] * R1[l * kp + j];
-    dst[p * kp * kp + e] = df_from_double(s);
+    dst[p * kp * kp + e] = slot_put(s, f64);
   }
 }
 
@@ -422,26 +426,26 @@ __global__ void k_assemble_ht(const double* B, int p, int k, int kp, double* Ht,
 // Ritz coefficients Y (compact m x k, ld k) -> padded double-float ((p+1)*kp x kp);
 // theta -> double-float per column.
 __global__ void k_expand_y(const double* V, int ldv, int p, int k, int kp, const double* th, float2* Y,
-                           float2* thdf) {
+                           float2* thdf, bool f64) {
   const int t = threadIdx.x;
   const int rows = (p + 1) * kp;
   for (int e = t; e < rows * kp; e += blockDim.x) {
     const int r = e / kp, j = e % kp;
     const int a = r / kp, i = r % kp;
-    Y[e] = (i < k && j < k) ? df_from_double(V[(a * k + i) * ldv + j]) : make_float2(0.f, 0.f);
+    Y[e] = (i < k && j < k) ? slot_put(V[(a * k + i) * ldv + j], f64) : make_float2(0.f, 0.f);
   }
-  if (t < kp) thdf[t] = (t < k) ? df_from_double(th[t]) : make_float2(0.f, 0.f);
+  if (t < kp) thdf[t] = (t < k) ? slot_put(th[t], f64) : make_float2(0.f, 0.f);
 }
 
 // Thick restart: coefficients of output block b (Ritz vectors b*k .. b*k+k-1) in
 // the padded layout of the block update: out[(a*kp+i)*kp + j] = V[(a*k+i)*ldv + b*k + j].
-__global__ void k_restart_coef(const double* V, int ldv, int p, int k, int kp, int b, float2* out) {
+__global__ void k_restart_coef(const double* V, int ldv, int p, int k, int kp, int b, float2* out, bool f64) {
   const int t = threadIdx.x;
   const int rows = (p + 1) * kp;
   for (int e = t; e < rows * kp; e += blockDim.x) {
     const int r = e / kp, j = e % kp;
     const int a = r / kp, i = r % kp;
-    out[e] = (i < k && j < k) ? df_from_double(V[(a * k + i) * ldv + b * k + j]) : make_float2(0.f, 0.f);
+    out[e] = (i < k && j < k) ? slot_put(V[(a * k + i) * ldv + b * k + j], f64) : make_float2(0.f, 0.f);
   }
 }
 
@@ -456,11 +460,11 @@ __global__ void k_subblock(const float2* src, int lds, int na, int ob, float2* o
 }
 
 // V (m x nev FP64, ld nev) -> double-float rotation coefficients (m x m padded to 16x16 ld 16)
-__global__ void k_vmat_df(const double* V, int m, int nev, int ldv, float2* out) {
+__global__ void k_vmat_df(const double* V, int m, int nev, int ldv, float2* out, bool f64) {
   const int t = threadIdx.x;
   for (int e = t; e < 256; e += blockDim.x) {
     const int i = e / 16, j = e % 16;
-    out[e] = (i < m && j < nev) ? df_from_double(V[i * ldv + j]) : make_float2(0.f, 0.f);
+    out[e] = (i < m && j < nev) ? slot_put(V[i * ldv + j], f64) : make_float2(0.f, 0.f);
   }
 }
 
@@ -481,6 +485,14 @@ void split_df(double x, float2& out) {
   out.y = static_cast<float>(x - static_cast<double>(h));
 }
 
+// x into a value slot of the given format (double-float pair, or the bits of x)
+void put_slot(double x, float2& out, bool f64) {
+  if (f64)
+    std::memcpy(&out, &x, sizeof(double));
+  else
+    split_df(x, out);
+}
+
 // FP32 -> nearest BF16 (ties to even), returned as FP32; finite inputs only
 // (an input whose rounding overflows becomes Inf and is rejected by validation)
 float round_bf16(float f) {
@@ -499,7 +511,7 @@ float round_bf16(float f) {
 // within windows of `sigma` rows (stable) and cut into slices of kSliceH rows.  Rows
 // without any entry are listed in chunk 0 so that their output is written.
 void build_sell(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t ncols,
-                const std::vector<int64_t>& seg, int64_t sigma, int64_t chunk_cols, SellHost& S) {
+                const std::vector<int64_t>& seg, int64_t sigma, int64_t chunk_cols, bool f64, SellHost& S) {
   const int64_t C = (chunk_cols > 0 && chunk_cols < ncols) ? chunk_cols : ncols;
   const int nch = (int)((ncols + C - 1) / C);
   S.nchunks = nch;
@@ -574,7 +586,7 @@ void build_sell(int64_t nrows, const int64_t* rp, const int32_t* ci, const doubl
         const int64_t o = base + kSliceH * t + l;
         if (t < lr) {
           S.col[o] = ci[o0 + t];
-          split_df(va[o0 + t], S.val[o]);
+          put_slot(va[o0 + t], S.val[o], f64);
         } else {
           S.col[o] = pad_col;
         }
@@ -642,7 +654,7 @@ sppc_status upload_csr11(sppc_ctx* h, int64_t n1, const int64_t* rp, const int32
   for (int64_t r = 0; r < n1; ++r)
     for (int64_t t = 0; t < p[r + 1] - p[r]; ++t) {
       col[p[r] + t] = ci[rp[r] + t];
-      split_df(va[rp[r] + t], val[p[r] + t]);
+      put_slot(va[rp[r] + t], val[p[r] + t], h->f64);
     }
   int64_t* drp;
   int32_t* dcol;
@@ -658,6 +670,7 @@ sppc_status upload_csr11(sppc_ctx* h, int64_t n1, const int64_t* rp, const int32
   out.rowptr = drp;
   out.col = dcol;
   out.val = dval;
+  out.f64 = h->f64;
   return SPPC_OK;
 }
 
@@ -723,7 +736,7 @@ sppc_status gram_set(sppc_ctx* h, float2** X, float2** Z, int nb, double* G16) {
   for (int a = 0; a < nb; ++a) L.p[a] = X[a];
   for (int ob = 0; ob < nb; ++ob) {
     // out[(a*8+i)*8 + j] for column block ob
-    CK(gram(L, Z[ob], 8, 0, h->n1, h->dGram, h->partials, h->partial_cap, s));
+    CK(gram(L, Z[ob], 8, 0, h->n1, h->dGram, h->partials, h->partial_cap, h->f64, s));
     // scatter into G16[(a*8+i)*16 + ob*8 + j]
     for (int a = 0; a < nb; ++a)
       CK(cudaMemcpy2DAsync(G16 + (a * 8) * 16 + ob * 8, 16 * sizeof(double), h->dGram + a * 64, 8 * sizeof(double),
@@ -741,7 +754,7 @@ sppc_status rotate_set(sppc_ctx* h, float2** X, float2** Y, int nb, const float2
   for (int ob = 0; ob < nb; ++ob) {
     k_subblock<<<1, 128, 0, s>>>(M16, 16, nb, ob, h->dCoefBig); count_launch();
     CK(cudaGetLastError());
-    CK(update(Y[ob], nullptr, nullptr, L, h->dCoefBig, 8, 0, h->n1, s));
+    CK(update(Y[ob], nullptr, nullptr, L, h->dCoefBig, 8, 0, h->n1, h->f64, s));
   }
   return SPPC_OK;
 }
@@ -751,7 +764,7 @@ sppc_status ortho_set(sppc_ctx* h, float2** X, float2** Tmp, int nb, int b) {
   for (int pass = 0; pass < 3; ++pass) {
     CKS(gram_set(h, X, X, nb, h->dS));
     const double shift = (pass == 0) ? 1e-12 : 0.0;
-    CK(chol_rinv(h->dS, 16, b, 16, shift, h->dR1, h->dRinv, h->dStatus, h->stream));
+    CK(chol_rinv(h->dS, 16, b, 16, shift, h->dR1, h->dRinv, h->dStatus, h->f64, h->stream));
     int st = 0;
     CK(cudaMemcpyAsync(&st, h->dStatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -787,7 +800,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
         const double u1 = ((mix64(seed + (2 * idx + 1) * 0x9E3779B97F4A7C15ULL) >> 11) + 1) * 0x1.0p-53;
         const double u2 = (mix64(seed + (2 * idx + 2) * 0x9E3779B97F4A7C15ULL) >> 11) * 0x1.0p-53;
         const double g = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
-        split_df(g, host[(size_t)(c / 8) * n1 * 8 + (size_t)r * 8 + (c % 8)]);
+        put_slot(g, host[(size_t)(c / 8) * n1 * 8 + (size_t)r * 8 + (c % 8)], h->f64);
       }
     for (int a = 0; a < nb; ++a)
       CK(cudaMemcpyAsync(X[a], host.data() + (size_t)a * n1 * 8, sizeof(float2) * n1 * 8, cudaMemcpyHostToDevice, s));
@@ -802,8 +815,8 @@ sppc_status small_eigensolve(sppc_ctx* h) {
     for (int a = 0; a < nb; ++a) CK(spmm11(h, 8, X[a], AX[a], Epi{}, s));
     h->stats.spmv_h11 += 8 * nb;
     CKS(gram_set(h, X, AX, nb, h->dS));
-    CK(syev_lowest(h->dS, 16, b, b, h->dTheta, h->dV, b, s));
-    k_vmat_df<<<1, 256, 0, s>>>(h->dV, b, b, b, h->dRinv); count_launch();
+    CK(syev_lowest(h->dS, 16, b, b, h->dTheta, h->dV, b, h->f64, s));
+    k_vmat_df<<<1, 256, 0, s>>>(h->dV, b, b, b, h->dRinv, h->f64); count_launch();
     CK(cudaGetLastError());
     CKS(rotate_set(h, X, Tmp, nb, h->dRinv));
     for (int a = 0; a < nb; ++a) std::swap(X[a], Tmp[a]);
@@ -813,16 +826,12 @@ sppc_status small_eigensolve(sppc_ctx* h) {
     CK(cudaStreamSynchronize(s));
     // residuals of the k lowest: D = AX - X theta (block 0 holds columns 0..7)
     std::vector<float2> thdf(8);
-    for (int c = 0; c < 8; ++c) {
-      const double v = (c < b) ? -th[c] : 0.0;
-      thdf[c].x = (float)v;
-      thdf[c].y = (float)(v - (double)thdf[c].x);
-    }
+    for (int c = 0; c < 8; ++c) put_slot((c < b) ? -th[c] : 0.0, thdf[c], h->f64);
     CK(cudaMemcpyAsync(h->dCoef + kTheta, thdf.data(), sizeof(float2) * 8, cudaMemcpyHostToDevice, s));
-    CK(combine_diag(Tmp[0], AX[0], h->dCoef + kOnes, one(X[0]), h->dCoef + kTheta, 8, 0, n1, s));
+    CK(combine_diag(Tmp[0], AX[0], h->dCoef + kOnes, one(X[0]), h->dCoef + kTheta, 8, 0, n1, h->f64, s));
     const float2* A1[1] = {Tmp[0]};
     const float2* B1[1] = {Tmp[0]};
-    CK(coldots(A1, B1, 1, 8, 0, n1, h->dDots, h->partials, h->partial_cap, s));
+    CK(coldots(A1, B1, 1, 8, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
     CK(cudaMemcpyAsync(res.data(), h->dDots, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     double worst = 0.0;
@@ -835,9 +844,9 @@ sppc_status small_eigensolve(sppc_ctx* h) {
     auto put3 = [&](double al, double be, double ga) -> sppc_status {
       std::vector<float2> v(48);
       for (int j = 0; j < 16; ++j) {
-        split_df(al, v[j]);
-        split_df(be, v[16 + j]);
-        split_df(ga, v[32 + j]);
+        put_slot(al, v[j], h->f64);
+        put_slot(be, v[16 + j], h->f64);
+        put_slot(ga, v[32 + j], h->f64);
       }
       CK(cudaMemcpyAsync(h->dCoef + kCheb, v.data(), sizeof(float2) * 48, cudaMemcpyHostToDevice, s));
       return SPPC_OK;
@@ -938,7 +947,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
   std::vector<double> e0p(h->kp, 0.0);
   for (int j = 0; j < k; ++j) e0p[j] = h->E0[j];
   CK(cudaMemcpyAsync(h->dE, e0p.data(), sizeof(double) * h->kp, cudaMemcpyHostToDevice, s));
-  k_set_e0<<<1, 32, 0, s>>>(h->dE, k, h->kp, h->dCoef); count_launch();
+  k_set_e0<<<1, 32, 0, s>>>(h->dE, k, h->kp, h->dCoef, h->f64); count_launch();
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   return SPPC_OK;
@@ -971,10 +980,10 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
     Lb.p[0] = h->psib[0];
     Lb.p[1] = h->psib[1];
     // (dC2, not dGram: this may run beside a Rayleigh-Ritz step, which uses dGram)
-    CK(gram(Lb, h->b1, 8, 0, n1, h->dC2, h->partials, h->partial_cap, s));
-    k_defl_coefs<<<1, 128, 0, s>>>(h->dC2, h->dEb, h->b_small, h->k, h->dCoefBig); count_launch();
+    CK(gram(Lb, h->b1, 8, 0, n1, h->dC2, h->partials, h->partial_cap, h->f64, s));
+    k_defl_coefs<<<1, 128, 0, s>>>(h->dC2, h->dEb, h->b_small, h->k, h->dCoefBig, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(update(h->T2, nullptr, nullptr, Lb, h->dCoefBig, 8, 0, n1, s));       // x_defl
+    CK(update(h->T2, nullptr, nullptr, Lb, h->dCoefBig, 8, 0, n1, h->f64, s));       // x_defl
     Epi e;
     e.alpha = c + kNegOnes;
     e.beta = c + kPosE0;
@@ -984,24 +993,24 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
     h->stats.spmv_h11 += h->k;
     const float2* A[1] = {h->psi_hat};
     const float2* B[1] = {h->T1};
-    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, h->k, kp, c + kDefl); count_launch();
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, h->k, kp, c + kDefl, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(h->b1, h->T1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
+    CK(combine_diag(h->b1, h->T1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, h->f64, s));
   }
   CK(minres_persistent(h->H11c, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
                        h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s,
                        h->opt.minres_ctas, h->opt.spin_cap));
-  if (defl) CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->T2), c + kOnes, kp, 0, n1, s));  // + x_defl
+  if (defl) CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->T2), c + kOnes, kp, 0, n1, h->f64, s));  // + x_defl
   // x -= psi_hat (psi_hat^T x): keep the solution on the complement of psi_hat_k
   float2* x = h->mx;
   {
     const float2* A[1] = {h->psi_hat};
     const float2* B[1] = {x};
-    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, h->k, kp, c + kDefl); count_launch();
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, h->k, kp, c + kDefl, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(x, x, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
+    CK(combine_diag(x, x, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, h->f64, s));
   }
   int st[10] = {0};
   CK(cudaMemcpyAsync(st, dstat, sizeof(int) * 10, cudaMemcpyDeviceToHost, s));
@@ -1030,19 +1039,19 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
-  CK(gram(blocks(h->Q, n, kp, 0, p + 1), blk(h->W, n, kp, p), kp, 0, n, h->dGram, h->partials, h->partial_cap, s));
+  CK(gram(blocks(h->Q, n, kp, 0, p + 1), blk(h->W, n, kp, p), kp, 0, n, h->dGram, h->partials, h->partial_cap, h->f64, s));
   k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, p, k, kp, h->dHt, h->mmax); count_launch();
   CK(cudaGetLastError());
   const int m = (p + 1) * k;
   const int nev = std::min(std::min(2 * k, m), 16);
   h->nev = nev;
-  CK(syev_lowest(h->dHt, h->mmax, m, nev, h->dTheta, h->dV, nev, s));
-  k_expand_y<<<1, 256, 0, s>>>(h->dV, nev, p, k, kp, h->dTheta, h->dY, h->dCoef + kTheta); count_launch();
+  CK(syev_lowest(h->dHt, h->mmax, m, nev, h->dTheta, h->dV, nev, h->f64, s));
+  k_expand_y<<<1, 256, 0, s>>>(h->dV, nev, p, k, kp, h->dTheta, h->dY, h->dCoef + kTheta, h->f64); count_launch();
   CK(cudaGetLastError());
   const bool lead = T != nullptr && h->opt.precond == 2;
   CK(ritz_resid(blocks(h->Q, n, kp, 0, p + 1), blocks(h->W, n, kp, 0, p + 1), h->dY, h->dCoef + kTheta, kp, n,
                 h->dDots, h->partials, h->partial_cap, want_z ? Z : nullptr, ldz, k, T, diag,
-                (float)h->opt.precond_clamp, s, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
+                (float)h->opt.precond_clamp, h->f64, s, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
                 lead ? h->n_lead : 0));
   if (defer) {
     // results land in pinned host memory; rr_finish() reads them after a sync
@@ -1089,14 +1098,14 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   float2* c = h->dCoef;
   BlockList Qs = blocks(h->Q, n, kp, 0, p);
   const int nc = p * kp * kp;
-  CK(gram(Qs, src, kp, 0, n, h->dC1, h->partials, h->partial_cap, s));
-  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig); count_launch();
+  CK(gram(Qs, src, kp, 0, n, h->dC1, h->partials, h->partial_cap, h->f64, s));
+  k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig, h->f64); count_launch();
   CK(cudaGetLastError());
-  CK(update(h->T1, src, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
+  CK(update(h->T1, src, c + kOnes, Qs, h->dCoefBig, kp, 0, n, h->f64, s));
   {
     const float2* A[2] = {src, h->T1};
     const float2* B[2] = {src, h->T1};
-    CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+    CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, h->f64, s));
   }
   CK(cudaMemcpyAsync(dd, h->dDots, sizeof(double) * 2 * kp, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1104,29 +1113,29 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   for (int j = 0; j < k; ++j) again |= !(dd[kp + j] >= 0.25 * dd[j]);  // ||Phi_j|| < ||src_j|| / 2
   h->stats.reorth_passes += again ? 1 : 0;
   if (again) {
-    CK(gram(Qs, h->T1, kp, 0, n, h->dC2, h->partials, h->partial_cap, s));
-    k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig); count_launch();
+    CK(gram(Qs, h->T1, kp, 0, n, h->dC2, h->partials, h->partial_cap, h->f64, s));
+    k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, s));
+    CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, h->f64, s));
     k_addmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, h->dC2, nc, h->dC1); count_launch();  // C = C1 + C2
     CK(cudaGetLastError());
     const float2* A[1] = {h->T1};
     const float2* B[1] = {h->T1};
-    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, h->f64, s));
     CK(cudaMemcpyAsync(dd + kp, h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
   }
   float2* q = blk(h->Q, n, kp, p);
-  CK(gram(one(h->T1), h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
-  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR1, h->dRinv, h->dStatus, s));
-  CK(update(h->T2, nullptr, nullptr, one(h->T1), h->dRinv, kp, 0, n, s));
-  CK(gram(one(h->T2), h->T2, kp, 0, n, h->dS, h->partials, h->partial_cap, s));
-  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR2, h->dRinv, h->dStatus + 1, s));
-  CK(update(q, nullptr, nullptr, one(h->T2), h->dRinv, kp, 0, n, s));
-  k_recycle_coefs<<<1, 256, 0, s>>>(h->dC1, p, kp, h->dR2, h->dR1, h->dRecycle); count_launch();
+  CK(gram(one(h->T1), h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, h->f64, s));
+  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR1, h->dRinv, h->dStatus, h->f64, s));
+  CK(update(h->T2, nullptr, nullptr, one(h->T1), h->dRinv, kp, 0, n, h->f64, s));
+  CK(gram(one(h->T2), h->T2, kp, 0, n, h->dS, h->partials, h->partial_cap, h->f64, s));
+  CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR2, h->dRinv, h->dStatus + 1, h->f64, s));
+  CK(update(q, nullptr, nullptr, one(h->T2), h->dRinv, kp, 0, n, h->f64, s));
+  k_recycle_coefs<<<1, 256, 0, s>>>(h->dC1, p, kp, h->dR2, h->dR1, h->dRecycle, h->f64); count_launch();
   CK(cudaGetLastError());
   int st[2] = {0, 0}, tmo = 0;
   CK(cudaMemcpyAsync(st, h->dStatus, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-  CK(spmm_tma_read_timeout(&tmo, s));
+  CK(spmm_tma_read_timeout(h->H, &tmo, s));
   CK(cudaStreamSynchronize(s));
   if (tmo) return fail(h, SPPC_ERR_TIMEOUT, "SpMM: a shared-memory pipeline wait timed out");
   if (st[0] || st[1])
@@ -1143,10 +1152,10 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
   const int64_t n = h->n;
   if (h->nev < 2 * k) return fail(h, SPPC_ERR_STATE, "restart needs 2k Ritz vectors");
   for (int b = 0; b < 2; ++b) {
-    k_restart_coef<<<1, 256, 0, s>>>(h->dV, h->nev, p, k, kp, b, h->dCoefBig); count_launch();
+    k_restart_coef<<<1, 256, 0, s>>>(h->dV, h->nev, p, k, kp, b, h->dCoefBig, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(update(blk(h->Psi, n, kp, b), nullptr, nullptr, blocks(h->Q, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n, s));
-    CK(update(blk(h->Psi, n, kp, 2 + b), nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n,
+    CK(update(blk(h->Psi, n, kp, b), nullptr, nullptr, blocks(h->Q, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n, h->f64, s));
+    CK(update(blk(h->Psi, n, kp, 2 + b), nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n, h->f64,
               s));
   }
   CK(cudaMemcpyAsync(h->Q, h->Psi, sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
@@ -1158,7 +1167,7 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
     CK(cudaMemcpyAsync(h->W, blk(h->Psi, n, kp, 2), sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
   }
   for (int b = 0; b < 2; ++b) {
-    CK(gram(blocks(h->Q, n, kp, 0, b + 1), blk(h->W, n, kp, b), kp, 0, n, h->dGram, h->partials, h->partial_cap,
+    CK(gram(blocks(h->Q, n, kp, 0, b + 1), blk(h->W, n, kp, b), kp, 0, n, h->dGram, h->partials, h->partial_cap, h->f64,
             s));
     k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, b, k, kp, h->dHt, h->mmax); count_launch();
     CK(cudaGetLastError());
@@ -1190,20 +1199,20 @@ sppc_status lead_correction(sppc_ctx* h, float2* T) {
   {  // z <- z / ||z|| (columnwise)
     const float2* A[1] = {h->zlead};
     const float2* B[1] = {h->zlead};
-    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    k_inv_norm_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kLeadScale); count_launch();
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    k_inv_norm_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kLeadScale, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(h->zlead, nullptr, nullptr, one(h->zlead), c + kLeadScale, kp, 0, n1, s));
+    CK(combine_diag(h->zlead, nullptr, nullptr, one(h->zlead), c + kLeadScale, kp, 0, n1, h->f64, s));
   }
   {  // b = r - z (z^T r)
     const float2* A[1] = {h->zlead};
     const float2* B[1] = {h->rlead};
-    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl); count_launch();
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(h->b1, h->rlead, c + kOnes, one(h->zlead), c + kDefl, kp, 0, n1, s));
+    CK(combine_diag(h->b1, h->rlead, c + kOnes, one(h->zlead), c + kDefl, kp, 0, n1, h->f64, s));
   }
-  k_neg_coef<<<1, 32, 0, s>>>(c + kTheta, k, kp, c + kLeadNegE); count_launch();
+  k_neg_coef<<<1, 32, 0, s>>>(c + kTheta, k, kp, c + kLeadNegE, h->f64); count_launch();
   CK(cudaGetLastError());
   int* dstat = h->dStatus + 32;
   if (iters > 0) {
@@ -1212,10 +1221,10 @@ sppc_status lead_correction(sppc_ctx* h, float2* T) {
     // x <- x - z (z^T x)
     const float2* A[1] = {h->zlead};
     const float2* B[1] = {h->mx};
-    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl); count_launch();
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->zlead), c + kDefl, kp, 0, n1, s));
+    CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->zlead), c + kDefl, kp, 0, n1, h->f64, s));
     CK(cudaMemcpyAsync(T, h->mx, sizeof(float2) * n1 * kp, cudaMemcpyDeviceToDevice, s));
   } else {
     CK(fill_zero(T, n1 * kp, s));
@@ -1301,7 +1310,7 @@ sppc_status refine_step(sppc_ctx* h) {
   if (!h->t_ready) {
     CK(ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
                   n, h->dDots, h->partials, h->partial_cap, nullptr, 0, 0, h->HPsi, t_diag(h),
-                  (float)h->opt.precond_clamp, h->stream, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
+                  (float)h->opt.precond_clamp, h->f64, h->stream, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
                   lead ? h->n_lead : 0));
   }
   h->t_ready = false;
@@ -1321,6 +1330,13 @@ sppc_status refine_step(sppc_ctx* h) {
   const double before = h->resid.empty() ? 0.0 : *std::max_element(h->resid.begin(), h->resid.end());
   std::vector<double> dd(2 * kp);
   CKS(orth_append(h, T, h->p + 1, dd.data(), h->opt.reorth == 0));
+  if (T == h->HPsi && h->Tspare) {
+    // keep the appended block readable (sppc_get_state 8): the next
+    // Rayleigh-Ritz pass writes its block into the other buffer
+    std::swap(h->HPsi, h->Tspare);
+    T = h->Tspare;
+  }
+  h->t_last = T;
   h->p += 1;
   CKS(big_spmm(h, blk(h->Q, n, kp, h->p), blk(h->W, n, kp, h->p), kp));
   h->stats.spmv_h += h->k;
@@ -1334,6 +1350,7 @@ sppc_status refine_step(sppc_ctx* h) {
       // drop the proposal's block, extend by the plain preconditioned block
       h->p -= 1;
       CKS(orth_append(h, h->Tplain, h->p + 1, dd.data(), h->opt.reorth == 0));
+      h->t_last = h->Tplain;
       h->p += 1;
       CKS(big_spmm(h, blk(h->Q, n, kp, h->p), blk(h->W, n, kp, h->p), kp));
       h->stats.spmv_h += h->k;
@@ -1391,14 +1408,14 @@ sppc_status rmm_run(sppc_ctx* h, double tol) {
   auto normalise = [&](float2* X) -> sppc_status {
     const float2* A[1] = {X};
     const float2* B[1] = {X};
-    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
-    k_inv_norm_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kRmmScale); count_launch();
+    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    k_inv_norm_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kRmmScale, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(X, nullptr, nullptr, one(X), c + kRmmScale, kp, 0, n, s));
+    CK(combine_diag(X, nullptr, nullptr, one(X), c + kRmmScale, kp, 0, n, h->f64, s));
     return SPPC_OK;
   };
   // x_0: the Ritz vectors Z = Q Y of the last Rayleigh-Ritz step, normalised
-  CK(update(Xb, nullptr, nullptr, blocks(h->Q, n, kp, 0, h->p + 1), h->dY, kp, 0, n, s));
+  CK(update(Xb, nullptr, nullptr, blocks(h->Q, n, kp, 0, h->p + 1), h->dY, kp, 0, n, h->f64, s));
   CK(cudaMemcpyAsync(hx[0], Xb, sizeof(float2) * n * kp, cudaMemcpyDeviceToDevice, s));
   CKS(normalise(hx[0]));
   CK(cudaMemsetAsync(h->rmm_G, 0, sizeof(double) * 8 * 64, s));
@@ -1415,15 +1432,15 @@ sppc_status rmm_run(sppc_ctx* h, double tol) {
     {
       const float2* A[2] = {X, X};
       const float2* B[2] = {X, Wt};
-      CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+      CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, h->f64, s));
     }
     k_rmm_theta<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kRmmNegTh, h->rmm_th); count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(hr[cur], Wt, c + kOnes, one(X), c + kRmmNegTh, kp, 0, n, s));   // r = w - theta x
+    CK(combine_diag(hr[cur], Wt, c + kOnes, one(X), c + kRmmNegTh, kp, 0, n, h->f64, s));   // r = w - theta x
     {
       const float2* A[1] = {hr[cur]};
       const float2* B[1] = {hr[cur]};
-      CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+      CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, h->f64, s));
     }
     CK(cudaMemcpyAsync(th.data(), h->rmm_th, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(rr.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
@@ -1454,7 +1471,7 @@ sppc_status rmm_run(sppc_ctx* h, double tol) {
         A[q] = hr[(cur - (nh - 1) + t0 + q + d) % d];
         B[q] = hr[cur];
       }
-      CK(coldots(A, B, nq, kp, 0, n, h->rmm_g + (size_t)t0 * kp, h->partials, h->partial_cap, s));
+      CK(coldots(A, B, nq, kp, 0, n, h->rmm_g + (size_t)t0 * kp, h->partials, h->partial_cap, h->f64, s));
     }
     for (int j = 0; j < 16; ++j) lam[j] = frozen[j] ? 0.0 : 1.0;
     CK(cudaMemcpyAsync(h->rmm_frozen, frozen.data(), sizeof(int) * 16, cudaMemcpyHostToDevice, s));
@@ -1462,8 +1479,8 @@ sppc_status rmm_run(sppc_ctx* h, double tol) {
     k_diis<<<1, 32, 0, s>>>(h->rmm_g, d, cur, nh, h->rmm_G, h->rmm_frozen, k, kp, h->rmm_coef, h->rmm_status);
     count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(Xb, nullptr, nullptr, Lx, h->rmm_coef, kp, 0, n, s));   // x_bar
-    CK(combine_diag(Rb, nullptr, nullptr, Lr, h->rmm_coef, kp, 0, n, s));   // r_bar
+    CK(combine_diag(Xb, nullptr, nullptr, Lx, h->rmm_coef, kp, 0, n, h->f64, s));   // x_bar
+    CK(combine_diag(Rb, nullptr, nullptr, Lr, h->rmm_coef, kp, 0, n, h->f64, s));   // r_bar
     const int next = (cur + 1) % d;
     k_rmm_step<<<static_cast<unsigned>((n * kp + 255) / 256), 256, 0, s>>>(
         Xb, Rb, h->dDiag, h->rmm_th, h->rmm_lam, (float)h->opt.precond_clamp, k, kp, n, hx[next]);
@@ -1491,7 +1508,7 @@ namespace {
 // allocator, timed on two 8-column products (register-gather kernel, X = 0;
 // the gather pattern, not the values, sets the time) and freed.
 cudaError_t tune_chunk_cols(int64_t n, const int64_t* d_rp, const int32_t* d_ci, const double* d_va,
-                            const std::vector<int64_t>& seg, cudaStream_t s, int64_t* best, double* ms_out) {
+                            const std::vector<int64_t>& seg, bool f64, cudaStream_t s, int64_t* best, double* ms_out) {
   const int64_t cand[5] = {-1, 2621440, 1310720, 655360, 327680};
   float2 *X = nullptr, *Y = nullptr;
   cudaError_t e = cudaMallocAsync(&X, sizeof(float2) * n * 8, s);
@@ -1511,7 +1528,7 @@ cudaError_t tune_chunk_cols(int64_t n, const int64_t* d_rp, const int32_t* d_ci,
       return x;
     };
     SellDeviceLayout T;
-    e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, c, s, tmp, T);
+    e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, c, f64, 0, s, tmp, T);
     if (e == cudaSuccess) {
       SellDev A;
       A.nslices = T.nslices;
@@ -1525,6 +1542,7 @@ cudaError_t tune_chunk_cols(int64_t n, const int64_t* d_rp, const int32_t* d_ci,
       A.val = T.val_d;
       A.row_first = T.first_d;
       A.row_last = T.last_d;
+      A.f64 = f64;
       e = spmm(A, 8, X, Y, Epi{}, s);  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(a, s);
       for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = spmm(A, 8, X, Y, Epi{}, s);
@@ -1563,6 +1581,14 @@ sppc_status handle_fail(sppc_handle h, sppc_status st, const char* msg) { return
 void handle_scratch(sppc_handle h, float2** t1, float2** t2) {
   *t1 = h->T1;
   *t2 = h->T2;
+}
+// Value arrays of the mixed-precision products (precision 1: val32; 2: val16 and
+// diag32; both null otherwise) and the handle's precision option.
+void handle_values(sppc_handle h, int* precision, const float** val32, const uint16_t** val16, const float** diag32) {
+  *precision = h->opt.precision;
+  *val32 = h->val32;
+  *val16 = h->val16;
+  *diag32 = h->diag32;
 }
 void handle_size(sppc_handle h, int64_t* n, int64_t* nnz, int* k) {
   if (n) *n = h->n;
@@ -1615,7 +1641,7 @@ sppc_status sppc_small_syev(const double* S, int32_t m, int32_t lds, int32_t nev
                             int32_t ldv, void* stream) {
   if (!S || !theta || !V || m < 1 || m > 144 || nev < 1 || nev > 16 || nev > m || lds < m || ldv < nev)
     return fail(nullptr, SPPC_ERR_ARG, "sppc_small_syev: bad arguments (1 <= m <= 144, 1 <= nev <= min(16, m))");
-  const cudaError_t e = syev_lowest(S, lds, m, nev, theta, V, ldv, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = syev_lowest(S, lds, m, nev, theta, V, ldv, false, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_small_syev: %s", cudaGetErrorString(e));
   return SPPC_OK;
 }
@@ -1662,7 +1688,10 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.spmm_kernel != 0 && opt.spmm_kernel != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.spmm_kernel must be 0 or 1");
   if (opt.reorth != 0 && opt.reorth != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.reorth must be 0 or 1");
   if (opt.precond < 0 || opt.precond > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precond must be 0, 1 or 2");
-  if (opt.precision < 0 || opt.precision > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.precision must be 0, 1 or 2");
+  if (opt.precision < -1 || opt.precision > 2)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.precision must be -1, 0, 1 or 2");
+  if (opt.precision == -1 && (opt.hybrid == 2 || opt.proposal != 0))
+    return fail(nullptr, SPPC_ERR_ARG, "opts.precision = -1 (native FP64) runs without RMM-DIIS and the proposal");
   if (opt.spmm_chunk_cols < -2) return fail(nullptr, SPPC_ERR_ARG, "opts.spmm_chunk_cols must be >= -2");
   if (opt.hybrid < 0 || opt.hybrid > 2) return fail(nullptr, SPPC_ERR_ARG, "opts.hybrid must be 0, 1 or 2");
   if (opt.hybrid == 2 && (opt.precision != 0 || opt.proposal != 0))
@@ -1680,7 +1709,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "opts.switch_stall must be in [0, 1]");
   if (opt.minres_ctas < 0) return fail(nullptr, SPPC_ERR_ARG, "opts.minres_ctas must be >= 0");
   if (opt.spin_cap < 0) return fail(nullptr, SPPC_ERR_ARG, "opts.spin_cap must be >= 0");
-  if (opt.precision != 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
+  if (opt.precision > 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precond_iters must be in [0, 10000]");
@@ -1689,6 +1718,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.hybrid_blocks <= 0 || opt.hybrid_blocks > opt.p_max + 1) opt.hybrid_blocks = opt.p_max + 1;
   if (opt.hybrid_blocks < 3) opt.hybrid_blocks = 3;
   h->opt = opt;
+  h->f64 = opt.precision == -1;
   h->stream = static_cast<cudaStream_t>(stream);
   h->n = n;
   h->nnz = Hc->nnz;
@@ -1704,21 +1734,35 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     sppc_destroy(h);
     return st;
   };
-  // host copy of the CSR if needed
+  // The CSR.  A host CSR is read on the host.  A device CSR stays on the device:
+  // the host reads its row pointers and the leading rows (the small space and
+  // the preconditioner's leading block) only, and the checks, the rounding of
+  // precision 1 / 2 and the diagonal run on the GPU, so a matrix whose host copy
+  // would not fit is never copied.
+  const bool dev_in = Hc->on_device != 0;
   std::vector<int64_t> rp_h;
   std::vector<int32_t> ci_h;
   std::vector<double> va_h;
   const int64_t* rp = Hc->row_ptr;
   const int32_t* ci = Hc->col;
   const double* va = Hc->val;
-  if (Hc->on_device) {
+  const int64_t rows_h = dev_in ? std::max<int64_t>(n1, h->n_lead) : n;  // rows readable on the host
+  const int round_mode = opt.precision > 0 ? opt.precision : 0;
+  if (dev_in) {
     rp_h.resize(n + 1);
-    ci_h.resize(Hc->nnz);
-    va_h.resize(Hc->nnz);
-    if (cudaMemcpy(rp_h.data(), rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(ci_h.data(), ci, sizeof(int32_t) * Hc->nnz, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(va_h.data(), va, sizeof(double) * Hc->nnz, cudaMemcpyDeviceToHost) != cudaSuccess)
-      return bail(fail(h, SPPC_ERR_CUDA, "copying the device CSR to the host failed"));
+    if (cudaMemcpy(rp_h.data(), rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bail(fail(h, SPPC_ERR_CUDA, "copying the device row pointers to the host failed"));
+    if (rp_h[0] != 0 || rp_h[n] != Hc->nnz)
+      return bail(fail(h, SPPC_ERR_ARG, "row_ptr[0] must be 0 and row_ptr[n] = nnz"));
+    for (int64_t r = 0; r < n; ++r)
+      if (rp_h[r + 1] < rp_h[r]) return bail(fail(h, SPPC_ERR_ARG, "row_ptr is not monotone"));
+    const int64_t lead_nnz = rp_h[rows_h];
+    ci_h.resize(std::max<int64_t>(lead_nnz, 1));
+    va_h.resize(std::max<int64_t>(lead_nnz, 1));
+    if (lead_nnz > 0 &&
+        (cudaMemcpy(ci_h.data(), ci, sizeof(int32_t) * lead_nnz, cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(va_h.data(), va, sizeof(double) * lead_nnz, cudaMemcpyDeviceToHost) != cudaSuccess))
+      return bail(fail(h, SPPC_ERR_CUDA, "copying the leading rows of the device CSR to the host failed"));
     rp = rp_h.data();
     ci = ci_h.data();
     va = va_h.data();
@@ -1726,9 +1770,10 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.precision == 1) {
     // mixed precision: the matrix is H rounded to FP32, everywhere (SpMM, leading
     // block, diagonal); the solver's error is measured against that matrix
-    if (va_h.empty()) va_h.assign(va, va + Hc->nnz);
+    const int64_t cnt = rp[rows_h];
+    if (va_h.empty()) va_h.assign(va, va + cnt);
 #pragma omp parallel for schedule(static)
-    for (int64_t t = 0; t < Hc->nnz; ++t) va_h[t] = static_cast<double>(static_cast<float>(va_h[t]));
+    for (int64_t t = 0; t < cnt; ++t) va_h[t] = static_cast<double>(static_cast<float>(va_h[t]));
     va = va_h.data();
   } else if (opt.precision == 2) {
     // BF16 path: off-diagonal values rounded to FP32 and then to BF16 (round to
@@ -1736,7 +1781,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     // measured against that matrix
     if (va_h.empty()) va_h.assign(va, va + Hc->nnz);
 #pragma omp parallel for schedule(static)
-    for (int64_t r = 0; r < n; ++r) {
+    for (int64_t r = 0; r < rows_h; ++r) {
       const int64_t lo = rp[r], hi = rp[r + 1];
       if (lo < 0 || hi < lo || hi > Hc->nnz) continue;  // rejected by the validation below
       for (int64_t t = lo; t < hi; ++t) {
@@ -1748,9 +1793,19 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   }
   // validation
   if (rp[0] != 0 || rp[n] != Hc->nnz) return bail(fail(h, SPPC_ERR_ARG, "row_ptr[0] must be 0 and row_ptr[n] = nnz"));
+  if (dev_in) {
+    int flags = 0;
+    const cudaError_t e = csr_check_device(n, Hc->row_ptr, Hc->col, Hc->val, opt.check_symmetry != 0, &flags,
+                                           h->stream);
+    if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_CUDA, "device CSR check: %s", cudaGetErrorString(e)));
+    if (flags & 2) return bail(fail(h, SPPC_ERR_ARG, "column index out of range"));
+    if (flags & 4) return bail(fail(h, SPPC_ERR_ARG, "column indices must increase strictly within a row"));
+    if (flags & 8) return bail(fail(h, SPPC_ERR_NAN, "H holds a NaN or Inf"));
+    if (flags & 1) return bail(fail(h, SPPC_ERR_NOT_SYMMETRIC, "H is not symmetric"));
+  }
   int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
-  for (int64_t r = 0; r < n; ++r) {
+  for (int64_t r = 0; r < (dev_in ? 0 : n); ++r) {
     if (rp[r + 1] < rp[r]) {
       bad |= 1;
       continue;
@@ -1765,7 +1820,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (bad & 2) return bail(fail(h, SPPC_ERR_ARG, "column index out of range"));
   if (bad & 4) return bail(fail(h, SPPC_ERR_ARG, "column indices must increase strictly within a row"));
   if (bad & 8) return bail(fail(h, SPPC_ERR_NAN, "H holds a NaN or Inf"));
-  if (opt.check_symmetry) {
+  if (opt.check_symmetry && !dev_in) {
     int asym = 0;
 #pragma omp parallel for schedule(dynamic, 1024) reduction(| : asym)
     for (int64_t r = 0; r < n; ++r) {
@@ -1809,15 +1864,23 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     int64_t* d_rp = nullptr;
     int32_t* d_ci = nullptr;
     double* d_va = nullptr;
-    const int64_t nnz1 = Hc->nnz > 0 ? Hc->nnz : 1;
-    cudaError_t e = cudaMallocAsync(&d_rp, sizeof(int64_t) * (n + 1), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_ci, sizeof(int32_t) * nnz1, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_va, sizeof(double) * nnz1, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && Hc->nnz > 0)
-      e = cudaMemcpyAsync(d_ci, ci, sizeof(int32_t) * Hc->nnz, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && Hc->nnz > 0)
-      e = cudaMemcpyAsync(d_va, va, sizeof(double) * Hc->nnz, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    if (dev_in) {
+      // the caller's device CSR, read in place (values rounded in the layout fill)
+      d_rp = const_cast<int64_t*>(Hc->row_ptr);
+      d_ci = const_cast<int32_t*>(Hc->col);
+      d_va = const_cast<double*>(Hc->val);
+    } else {
+      const int64_t nnz1 = Hc->nnz > 0 ? Hc->nnz : 1;
+      e = cudaMallocAsync(&d_rp, sizeof(int64_t) * (n + 1), s);
+      if (e == cudaSuccess) e = cudaMallocAsync(&d_ci, sizeof(int32_t) * nnz1, s);
+      if (e == cudaSuccess) e = cudaMallocAsync(&d_va, sizeof(double) * nnz1, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_rp, rp, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && Hc->nnz > 0)
+        e = cudaMemcpyAsync(d_ci, ci, sizeof(int32_t) * Hc->nnz, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && Hc->nnz > 0)
+        e = cudaMemcpyAsync(d_va, va, sizeof(double) * Hc->nnz, cudaMemcpyHostToDevice, s);
+    }
     SellDeviceLayout L;
     const DeviceAlloc alloc = [h](void** p, size_t bytes) {
       unsigned char* q = nullptr;
@@ -1828,10 +1891,11 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     if (e == cudaSuccess && tune) {
       // autotuner of the column tile: build the layout for each candidate, time
       // two 8-column products, keep the fastest (ties to the coarser tile)
-      e = tune_chunk_cols(n, d_rp, d_ci, d_va, seg, s, &chunk, h->tuned_ms);
+      e = tune_chunk_cols(n, d_rp, d_ci, d_va, seg, h->f64, s, &chunk, h->tuned_ms);
     }
     h->chunk_cols_used = chunk;
-    if (e == cudaSuccess) e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, chunk, s, alloc, L);
+    if (e == cudaSuccess)
+      e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, chunk, h->f64, dev_in ? round_mode : 0, s, alloc, L);
     if (e == cudaSuccess) {
       // per-row constants of the learned proposal's features
       int64_t* d_lev = nullptr;
@@ -1842,9 +1906,11 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       if (e == cudaSuccess) e = row_consts(n, d_rp, d_va, d_lev, (int)h->lev.size() - 1, h->rowc, s);
       if (d_lev) cudaFreeAsync(d_lev, s);
     }
-    if (d_rp) cudaFreeAsync(d_rp, s);
-    if (d_ci) cudaFreeAsync(d_ci, s);
-    if (d_va) cudaFreeAsync(d_va, s);
+    if (!dev_in) {
+      if (d_rp) cudaFreeAsync(d_rp, s);
+      if (d_ci) cudaFreeAsync(d_ci, s);
+      if (d_va) cudaFreeAsync(d_va, s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess)
       return bail(fail(h, e == cudaErrorMemoryAllocation ? SPPC_ERR_OOM : SPPC_ERR_CUDA, "SELL build on the GPU: %s",
@@ -1861,7 +1927,15 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     h->H.val = L.val_d;
     h->H.row_first = L.first_d;
     h->H.row_last = L.last_d;
-    h->H.tma = (opt.spmm_kernel == 0 && spmm_tma_available()) ? 1 : 0;
+    h->H.f64 = h->f64;
+    h->H.tma = (opt.spmm_kernel == 0 && !h->f64 && spmm_tma_available()) ? 1 : 0;
+    if (h->H.tma) {
+      // the TMA kernel's time-out flag (per handle; cleared by sppc_start and sppc_spmm_host)
+      e = dalloc(h, &h->H.tma_flag, 1);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->H.tma_flag, 0, sizeof(int), s);
+      if (e != cudaSuccess) return bail(fail(h, SPPC_ERR_OOM, "TMA flag: %s", cudaGetErrorString(e)));
+      h->H.spin_limit = static_cast<unsigned>(opt.spin_cap);
+    }
     if (opt.precision == 1) {
       // FP32 copy of the values (exact: they are FP32 already)
       e = dalloc(h, &h->val32, (size_t)(L.total > 0 ? L.total : 1));
@@ -1884,13 +1958,16 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   {
     SellHost S;
     std::vector<int64_t> seg = {0, n1};
-    build_sell(n1, rp, ci, va, n1, seg, 1024, 0, S);
+    build_sell(n1, rp, ci, va, n1, seg, 1024, 0, h->f64, S);
     sppc_status st = upload_sell(h, S, h->H11, n1, h->h11_chunk_slice);
     if (st != SPPC_OK) return bail(st);
+    h->H11.f64 = h->f64;
     h->h11_slices = S.nslices;
     h->h11_slice_ptr = std::move(S.slice_ptr);
     h->h11_slice_rows = std::move(S.rows);
     h->H11.tma = h->H.tma;
+    h->H11.tma_flag = h->H.tma_flag;
+    h->H11.spin_limit = h->H.spin_limit;
     st = upload_csr11(h, n1, rp, ci, va, h->H11c);
     if (st != SPPC_OK) return bail(st);
     h->Hlead = h->H11c;
@@ -1901,16 +1978,22 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   }
   // diag(H) for the preconditioned continuation
   {
-    std::vector<float2> dg(n, make_float2(0.f, 0.f));
-#pragma omp parallel for schedule(static)
-    for (int64_t r = 0; r < n; ++r) {
-      const int32_t* b = ci + rp[r];
-      const int32_t* e = ci + rp[r + 1];
-      const int32_t* f = std::lower_bound(b, e, (int32_t)r);
-      if (f != e && *f == r) split_df(va[rp[r] + (f - b)], dg[r]);
-    }
     cudaError_t e = dalloc(h, &h->dDiag, (size_t)n);
-    if (e == cudaSuccess) e = cudaMemcpy(h->dDiag, dg.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+    if (dev_in) {
+      if (e == cudaSuccess)
+        e = csr_diag_device(n, Hc->row_ptr, Hc->col, Hc->val, round_mode, h->f64, h->dDiag, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    } else {
+      std::vector<float2> dg(n, make_float2(0.f, 0.f));
+#pragma omp parallel for schedule(static)
+      for (int64_t r = 0; r < n; ++r) {
+        const int32_t* b = ci + rp[r];
+        const int32_t* e2 = ci + rp[r + 1];
+        const int32_t* f = std::lower_bound(b, e2, (int32_t)r);
+        if (f != e2 && *f == r) put_slot(va[rp[r] + (f - b)], dg[r], h->f64);
+      }
+      if (e == cudaSuccess) e = cudaMemcpy(h->dDiag, dg.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && opt.precision == 2) {
       e = dalloc(h, &h->diag32, (size_t)n);
       if (e == cudaSuccess) e = df_hi_parts(h->dDiag, h->diag32, n, h->stream);
@@ -1963,6 +2046,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       A(&h->zlead, (size_t)h->n_lead * kp);
       A(&h->rlead, (size_t)h->n_lead * kp);
     }
+    if (h->opt.hybrid == 1) A(&h->Tspare, (size_t)n * kp);
     A(&h->dCoefBig, (size_t)kMaxBlocks * 64);
     if (e == cudaSuccess) e = dalloc(h, &h->dStatus, 64);
     if (e == cudaSuccess) e = dalloc(h, &h->dBar, 4);
@@ -1971,7 +2055,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     if (e != cudaSuccess)
       return bail(fail(h, e == cudaErrorMemoryAllocation ? SPPC_ERR_OOM : SPPC_ERR_CUDA, "allocation failed: %s",
                        cudaGetErrorString(e)));
-    k_set_consts<<<1, 32, 0, h->stream>>>(h->dCoef); count_launch();
+    k_set_consts<<<1, 32, 0, h->stream>>>(h->dCoef, h->f64); count_launch();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dHt, 0, sizeof(double) * h->mmax * h->mmax, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1989,12 +2073,12 @@ sppc_status sppc_spmm(sppc_handle h, const double* X, int64_t ldx, double* Y, in
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   h->stream = s;
   const int kp = (ncols + 1) / 2 * 2;
-  CK(f64_to_df(X, ldx, ncols, h->T1, kp, 0, h->n, s));
-  if (h->opt.precision != 0 && (kp == 4 || kp == 8))
+  CK(f64_to_df(X, ldx, ncols, h->T1, kp, 0, h->n, h->f64, s));
+  if (h->opt.precision > 0 && (kp == 4 || kp == 8))
     CK(spmm_f32(h->H, h->val32, h->val16, h->diag32, h->T1, h->X32, h->T2, kp, s));
   else
     CK(spmm(h->H, kp, h->T1, h->T2, Epi{}, s));
-  CK(df_to_f64(h->T2, kp, Y, ldy, ncols, 0, h->n, s));
+  CK(df_to_f64(h->T2, kp, Y, ldy, ncols, 0, h->n, h->f64, s));
   return SPPC_OK;
 }
 
@@ -2011,13 +2095,14 @@ sppc_status sppc_spmm_host(sppc_handle h, const double* X, int64_t ldx, double* 
   }
   double* dX = h->stageX;
   double* dY = h->stageY;
+  if (h->H.tma_flag) CK(cudaMemsetAsync(h->H.tma_flag, 0, sizeof(int), s));
   CK(cudaMemcpy2DAsync(dX, sizeof(double) * ncols, X, sizeof(double) * ldx, sizeof(double) * ncols, h->n,
                        cudaMemcpyHostToDevice, s));
   CKS(sppc_spmm(h, dX, ncols, dY, ncols, ncols, stream));
   CK(cudaMemcpy2DAsync(Y, sizeof(double) * ldy, dY, sizeof(double) * ncols, sizeof(double) * ncols, h->n,
                        cudaMemcpyDeviceToHost, s));
   int tmo = 0;
-  CK(spmm_tma_read_timeout(&tmo, s));
+  CK(spmm_tma_read_timeout(h->H, &tmo, s));
   CK(cudaStreamSynchronize(s));
   if (tmo) return fail(h, SPPC_ERR_TIMEOUT, "SpMM: a shared-memory pipeline wait timed out");
   return SPPC_OK;
@@ -2036,6 +2121,8 @@ sppc_status sppc_start(sppc_handle h, double* theta, double* resid, void* stream
   h->corrected = false;
   h->in_refine = false;
   h->t_ready = false;
+  h->t_last = nullptr;
+  if (h->H.tma_flag) CK(cudaMemsetAsync(h->H.tma_flag, 0, sizeof(int), s));
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (h->opt.timing) {
     t0 = next_event(h);
@@ -2103,16 +2190,16 @@ sppc_status sppc_correct(sppc_handle h, void* stream) {
   {
     const float2* A[1] = {h->psi_hat};
     const float2* B[1] = {h->vps};
-    CK(coldots(A, B, 1, kp, 0, n1, h->dE + (size_t)p * kp, h->partials, h->partial_cap, s));
+    CK(coldots(A, B, 1, kp, 0, n1, h->dE + (size_t)p * kp, h->partials, h->partial_cap, h->f64, s));
   }
-  k_rhs_coefs<<<1, 32, 0, s>>>(h->dE, p, k, kp, c); count_launch();
+  k_rhs_coefs<<<1, 32, 0, s>>>(h->dE, p, k, kp, c, h->f64); count_launch();
   CK(cudaGetLastError());
   // rows >= n1: Psi^(p)_2 = -b2 / E^(0) (Eq. sm_first)
   {
     BlockList L;
     L.n = 0;
     for (int l = 1; l <= p - 2; ++l) L.p[L.n++] = blk(h->Psi, n, kp, l);
-    CK(combine_diag(Psip, h->HPsi, c + kInvE0, L, c + kRhsBig, kp, n1, n, s));
+    CK(combine_diag(Psip, h->HPsi, c + kInvE0, L, c + kRhsBig, kp, n1, n, h->f64, s));
   }
   // rows < n1: b1 = -V Psi^(p-1)_1 + E^(p) psi_hat + sum_{l=1}^{p-2} E^(p-l) Psi^(l)_1
   {
@@ -2120,16 +2207,16 @@ sppc_status sppc_correct(sppc_handle h, void* stream) {
     L.n = 0;
     L.p[L.n++] = h->psi_hat;
     for (int l = 1; l <= p - 2; ++l) L.p[L.n++] = blk(h->Psi, n, kp, l);
-    CK(combine_diag(h->b1, h->vps, c + kNegOnes, L, c + kRhsSmall, kp, 0, n1, s));
+    CK(combine_diag(h->b1, h->vps, c + kNegOnes, L, c + kRhsSmall, kp, 0, n1, h->f64, s));
   }
   // deflate psi_hat_k (Eq. sm_lin_proj)
   {
     const float2* A[1] = {h->psi_hat};
     const float2* B[1] = {h->b1};
-    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, s));
-    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl); count_launch();
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(combine_diag(h->b1, h->b1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, s));
+    CK(combine_diag(h->b1, h->b1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, h->f64, s));
   }
   // small solves (H0_hat - E_k^(0)) x1 = b1; at p = 1 b1 = 0 since V11 = 0 (Eq. first_PC)
   cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -2179,7 +2266,7 @@ sppc_status sppc_rayleigh_ritz(sppc_handle h, double* theta, double* resid, void
   h->stats.spmv_h += h->k;
   CKS(rr_core(h, p, false, nullptr, 0));
   // H Psi^(p) = W_{0..p-1} C + W_p R (Eq. HPsip)
-  CK(update(h->HPsi, nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dRecycle, kp, 0, n, s));
+  CK(update(h->HPsi, nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dRecycle, kp, 0, n, h->f64, s));
   OrderRec& r = h->rec.back();
   r.theta = h->theta;
   r.resid = h->resid;
@@ -2201,12 +2288,12 @@ sppc_status verify_df(sppc_ctx* h) {
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
   float2* c = h->dCoef;
-  CK(update(h->T1, nullptr, nullptr, blocks(h->Q, n, kp, 0, h->p + 1), h->dY, kp, 0, n, s));
+  CK(update(h->T1, nullptr, nullptr, blocks(h->Q, n, kp, 0, h->p + 1), h->dY, kp, 0, n, h->f64, s));
   CK(spmm(h->H, kp, h->T1, h->T2, Epi{}, s));
   {
     const float2* A[2] = {h->T1, h->T1};
     const float2* B[2] = {h->T2, h->T1};
-    CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+    CK(coldots(A, B, 2, kp, 0, n, h->dDots, h->partials, h->partial_cap, h->f64, s));
   }
   std::vector<double> dd(2 * kp);
   CK(cudaMemcpyAsync(dd.data(), h->dDots, sizeof(double) * 2 * kp, cudaMemcpyDeviceToHost, s));
@@ -2217,12 +2304,12 @@ sppc_status verify_df(sppc_ctx* h) {
     negth[j] = -th[j];
   }
   CK(cudaMemcpyAsync(h->dDots + 2 * kp, negth.data(), sizeof(double) * kp, cudaMemcpyHostToDevice, s));
-  CK(to_df(h->dDots + 2 * kp, c + kDefl, kp, 1.0, s));
-  CK(combine_diag(h->T2, h->T2, c + kOnes, one(h->T1), c + kDefl, kp, 0, n, s));  // H z - theta z
+  CK(to_df(h->dDots + 2 * kp, c + kDefl, kp, 1.0, h->f64, s));
+  CK(combine_diag(h->T2, h->T2, c + kOnes, one(h->T1), c + kDefl, kp, 0, n, h->f64, s));  // H z - theta z
   {
     const float2* A[1] = {h->T2};
     const float2* B[1] = {h->T2};
-    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, s));
+    CK(coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, h->f64, s));
   }
   std::vector<double> r2(kp);
   CK(cudaMemcpyAsync(r2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
@@ -2261,7 +2348,7 @@ static sppc_status overlap_order(sppc_ctx* h, bool next, bool* pre) {
   // next correction needs
   CKS(big_spmm(h, blk(h->Q, n, kp, p), blk(h->W, n, kp, p), kp));
   h->stats.spmv_h += h->k;
-  CK(update(h->HPsi, nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dRecycle, kp, 0, n, s));
+  CK(update(h->HPsi, nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dRecycle, kp, 0, n, h->f64, s));
   if (next) CK(cudaEventRecord(h->ev_a, s));  // the correction waits for H Psi^(p) only
   CKS(rr_core(h, p, false, nullptr, 0, nullptr, nullptr, next));
   const size_t rec_p = h->rec.size() - 1;
@@ -2305,7 +2392,7 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     cudaEventCreate(&t1);
     cudaEventRecord(t0, s);
   }
-  h->f32_products = (h->opt.precision != 0);
+  h->f32_products = (h->opt.precision > 0);
   CKS(sppc_start(h, nullptr, nullptr, stream));
   bool conv = all_converged(h, tol);
   const int sppc_orders = h->opt.hybrid ? std::min(p_max, h->opt.switch_order) : p_max;
@@ -2364,7 +2451,7 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
     }
     conv = all_converged(h, tol);
   }
-  const bool fresh = h->opt.precision != 0 && h->opt.hybrid && h->p >= 1 && h->nev >= 2 * h->k;
+  const bool fresh = h->opt.precision > 0 && h->opt.hybrid && h->p >= 1 && h->nev >= 2 * h->k;
   h->f32_products = false;
   if (fresh) {
     // Mixed precision: the residuals of the FP32 phase are estimates and its W
@@ -2383,11 +2470,11 @@ sppc_status sppc_solve(sppc_handle h, double tol, int32_t p_max, double* theta, 
   }
   if (Z) {
     if (h->opt.hybrid == 2 && h->rmm_x && h->in_refine)
-      CK(df_to_f64(h->rmm_x, h->kp, Z, ldz, h->k, 0, h->n, s));   // each pair's own vector
+      CK(df_to_f64(h->rmm_x, h->kp, Z, ldz, h->k, 0, h->n, h->f64, s));   // each pair's own vector
     else
       CKS(rr_core(h, h->p, true, Z, ldz));
   }
-  if (h->opt.precision != 0 && !fresh) {
+  if (h->opt.precision > 0 && !fresh) {
     // plain SPPC in mixed precision: Rayleigh quotients and residuals of the Ritz
     // vectors from double-float products
     CKS(verify_df(h));
@@ -2457,7 +2544,7 @@ sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t co
   auto dl = [&](const float2* src, int64_t rows, int ncols, double* dst, int64_t ld) -> sppc_status {
     double* tmp = nullptr;
     CK(cudaMalloc(&tmp, sizeof(double) * rows * ncols));
-    CK(df_to_f64(src, kp, tmp, ncols, ncols, 0, rows, s));
+    CK(df_to_f64(src, kp, tmp, ncols, ncols, 0, rows, h->f64, s));
     std::vector<double> hbuf((size_t)rows * ncols);
     CK(cudaMemcpyAsync(hbuf.data(), tmp, sizeof(double) * rows * ncols, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -2504,6 +2591,10 @@ sppc_status sppc_get_state(sppc_handle h, int32_t which, double* out, int64_t co
       if (!h->Tprop) return fail(h, SPPC_ERR_STATE, "no proposal block yet");
       if (count < n * k) return fail(h, SPPC_ERR_ARG, "buffer too small");
       return dl(which == 6 ? h->Tprop : h->Tplain, n, k, out, k);
+    case 8:
+      if (!h->t_last) return fail(h, SPPC_ERR_STATE, "no continuation step yet");
+      if (count < n * k) return fail(h, SPPC_ERR_ARG, "buffer too small");
+      return dl(h->t_last, n, k, out, k);
     default:
       return fail(h, SPPC_ERR_ARG, "unknown state id %d", which);
   }
@@ -2560,7 +2651,7 @@ sppc_status sppc_proposal_samples(sppc_handle h, const double* psi, int64_t ldps
   // Ritz vectors and raw residuals (into Tplain) of the current subspace
   if (e == cudaSuccess)
     e = ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
-                   n, h->dDots, h->partials, h->partial_cap, Zd, k, k, h->Tplain, nullptr, (float)h->opt.precond_clamp,
+                   n, h->dDots, h->partials, h->partial_cap, Zd, k, k, h->Tplain, nullptr, (float)h->opt.precond_clamp, h->f64,
                    s, nullptr, nullptr, 0);
   if (e == cudaSuccess) e = prop_prep(h->Tplain, kp, k, h->dDots, n, h->rhat32, h->X32, s);
   if (e == cudaSuccess) e = spmm_abs_f32(h->H, h->val32, h->val16, h->diag32, h->X32, h->T2, s);

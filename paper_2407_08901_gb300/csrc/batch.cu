@@ -122,6 +122,8 @@ extern "C" sppc_status sppc_spmm_batch_plan(sppc_handle* handles, int32_t count,
     const SellDev* A = handle_matrix(handles[i], &n);
     if (A->nchunks != 1)
       return handle_fail(nullptr, SPPC_ERR_ARG, "sppc_spmm_batch_plan: matrices must use an untiled layout");
+    if (A->f64)
+      return handle_fail(nullptr, SPPC_ERR_ARG, "sppc_spmm_batch_plan: handles must use the double-float format");
     handle_scratch(handles[i], &t1[i], &t2[i]);
     items[i].A = *A;
     items[i].A.chunk_slice = nullptr;
@@ -142,9 +144,9 @@ extern "C" sppc_status sppc_spmm_batch_plan(sppc_handle* handles, int32_t count,
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t ce = cudaSuccess;
-    for (int32_t i = 0; i < count && ce == cudaSuccess; ++i) ce = f64_to_df(X[i], ncols, ncols, t1[i], kp, 0, rows[i], cs);
+    for (int32_t i = 0; i < count && ce == cudaSuccess; ++i) ce = f64_to_df(X[i], ncols, ncols, t1[i], kp, 0, rows[i], false, cs);
     if (ce == cudaSuccess) ce = spmm_batch(p->items, count, p->prefix, prefix[count], kp, p->queue, cs);
-    for (int32_t i = 0; i < count && ce == cudaSuccess; ++i) ce = df_to_f64(t2[i], kp, Y[i], ncols, ncols, 0, rows[i], cs);
+    for (int32_t i = 0; i < count && ce == cudaSuccess; ++i) ce = df_to_f64(t2[i], kp, Y[i], ncols, ncols, 0, rows[i], false, cs);
     e = cudaStreamEndCapture(cs, &p->graph);
     if (e == cudaSuccess) e = ce;
   }

@@ -5,9 +5,11 @@
 // side of Eq. exp_seq2) and the Ritz residual norms of Eq. rrn.
 //
 // Reductions over rows are two-stage and deterministic: each CTA writes its
-// partial sums, a finishing kernel adds the partials in a fixed order.
-#include "df.cuh"
+// partial sums, a finishing kernel adds the partials in a fixed order.  Every
+// kernel is instantiated for both slot formats (val.cuh): double-float (F64 =
+// false) and native FP64 (F64 = true); the host wrappers take the format.
 #include "sppc_internal.h"
+#include "val.cuh"
 
 namespace sppc {
 
@@ -32,26 +34,30 @@ inline int64_t chunk_rows(int64_t rows) {
 
 // One warp per output: lane l adds the partials of chunks l, l+32, ... in order,
 // then the 32 lane sums are combined by a fixed butterfly (deterministic).
+template <bool F64>
 __global__ void k_finish(const float2* __restrict__ partials, int64_t nchunks, int nout, double* __restrict__ out) {
+  using A = Ar<F64>;
   const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (o >= nout) return;
-  float sh = 0.f, sl = 0.f;
+  typename A::Acc s;
+  A::zero(s);
   for (int64_t c = lane; c < nchunks; c += 32) {
-    acc_add(sh, sl, partials[c * nout + o]);
-    acc_norm(sh, sl);
+    A::acc(s, partials[c * nout + o]);
+    A::norm(s);
   }
-  const float2 t = warp_sum_df(acc_get(sh, sl));
-  if (lane == 0) out[o] = (double)t.x + (double)t.y;
+  const float2 t = warp_sum<F64>(A::get(s));
+  if (lane == 0) out[o] = A::to_d(t);
 }
 
 // One CTA = 8 warps and `chunk` rows.  A warp covers 32/KP rows at a time, lane
 // (row u, column i) with i = lane % KP: the A block rows are read contiguously
 // and the lanes of one row share (broadcast) its B row.  Each lane accumulates
 // the KP dots (i, j); lanes with equal i and the 8 warps are then combined.
-template <int KP>
+template <int KP, bool F64>
 __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restrict__ B, int64_t r0, int64_t r1,
                                               int64_t chunk, float2* __restrict__ partials) {
+  using V = Ar<F64>;
   constexpr int RPW = 32 / KP;   // rows per warp step (KP = 6 leaves 2 lanes idle)
   __shared__ float2 red[8][KP * KP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -62,9 +68,9 @@ __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restr
   const int nout = A.n * KP * KP;
   for (int a = 0; a < A.n; ++a) {
     const float2* __restrict__ Aa = A.p[a];
-    float sh[KP], sl[KP];
+    typename V::Acc acc[KP];
 #pragma unroll
-    for (int j = 0; j < KP; ++j) sh[j] = sl[j] = 0.f;
+    for (int j = 0; j < KP; ++j) V::zero(acc[j]);
     int cnt = 0;
     if (active) {
       // two rows per iteration, loads issued before the multiply-adds
@@ -83,17 +89,17 @@ __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restr
         }
 #pragma unroll
         for (int q = 0; q < KP / 2; ++q) {
-          acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b[q].x, b[q].y));
-          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b[q].z, b[q].w));
+          V::mac(acc[2 * q], av, make_float2(b[q].x, b[q].y));
+          V::mac(acc[2 * q + 1], av, make_float2(b[q].z, b[q].w));
         }
 #pragma unroll
         for (int q = 0; q < KP / 2; ++q) {
-          acc_mac(sh[2 * q], sl[2 * q], av2, make_float2(b2[q].x, b2[q].y));
-          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av2, make_float2(b2[q].z, b2[q].w));
+          V::mac(acc[2 * q], av2, make_float2(b2[q].x, b2[q].y));
+          V::mac(acc[2 * q + 1], av2, make_float2(b2[q].z, b2[q].w));
         }
         if (((++cnt) & 7) == 0) {
 #pragma unroll
-          for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
+          for (int j = 0; j < KP; ++j) V::norm(acc[j]);
         }
       }
       if (r < c1) {
@@ -102,26 +108,26 @@ __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restr
 #pragma unroll
         for (int q = 0; q < KP / 2; ++q) {
           const float4 b = br[q];
-          acc_mac(sh[2 * q], sl[2 * q], av, make_float2(b.x, b.y));
-          acc_mac(sh[2 * q + 1], sl[2 * q + 1], av, make_float2(b.z, b.w));
+          V::mac(acc[2 * q], av, make_float2(b.x, b.y));
+          V::mac(acc[2 * q + 1], av, make_float2(b.z, b.w));
         }
       }
     }
     // combine the RPW row-lanes of column i inside the warp (fixed order)
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
-      float2 v = active ? acc_get(sh[j], sl[j]) : make_float2(0.f, 0.f);
+      float2 v = active ? V::get(acc[j]) : make_float2(0.f, 0.f);
       for (int uu = 1; uu < RPW; ++uu) {
         const float2 o = make_float2(__shfl_sync(0xffffffffu, v.x, lane + uu * KP < 32 ? lane + uu * KP : lane),
                                      __shfl_sync(0xffffffffu, v.y, lane + uu * KP < 32 ? lane + uu * KP : lane));
-        if (u == 0) v = df_add(v, o);
+        if (u == 0) v = V::add(v, o);
       }
       if (u == 0 && lane < KP) red[warp][i * KP + j] = v;
     }
     __syncthreads();
     if (threadIdx.x < KP * KP) {
       float2 t = red[0][threadIdx.x];
-      for (int w = 1; w < 8; ++w) t = df_add(t, red[w][threadIdx.x]);
+      for (int w = 1; w < 8; ++w) t = V::add(t, red[w][threadIdx.x]);
       const int ii = threadIdx.x / KP, jj = threadIdx.x % KP;
       partials[static_cast<int64_t>(blockIdx.x) * nout + (a * KP + ii) * KP + jj] = t;
     }
@@ -129,9 +135,10 @@ __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restr
   }
 }
 
-template <int KP>
+template <int KP, bool F64>
 __global__ void __launch_bounds__(256) k_update(float2* Y, const float2* X, const float2* __restrict__ alpha,
                                                 BlockList A, const float2* __restrict__ coef, int64_t r0, int64_t r1) {
+  using V = Ar<F64>;
   extern __shared__ float2 scoef[];
   const int ncoef = A.n * KP * KP;
   for (int t = threadIdx.x; t < ncoef; t += blockDim.x) scoef[t] = coef[t];
@@ -140,16 +147,12 @@ __global__ void __launch_bounds__(256) k_update(float2* Y, const float2* X, cons
   __syncthreads();
   const int64_t r = r0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= r1) return;
-  float sh[KP], sl[KP];
+  typename V::Acc acc[KP];
 #pragma unroll
-  for (int j = 0; j < KP; ++j) sh[j] = sl[j] = 0.f;
+  for (int j = 0; j < KP; ++j) V::zero(acc[j]);
   if (X && alpha) {
 #pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      const float2 t = df_mul(salpha[j], X[r * KP + j]);
-      sh[j] = t.x;
-      sl[j] = t.y;
-    }
+    for (int j = 0; j < KP; ++j) V::set(acc[j], V::mul(salpha[j], X[r * KP + j]));
   }
   for (int a = 0; a < A.n; ++a) {
     const float4* ar = reinterpret_cast<const float4*>(A.p[a] + r * KP);
@@ -164,21 +167,22 @@ __global__ void __launch_bounds__(256) k_update(float2* Y, const float2* X, cons
 #pragma unroll
     for (int i = 0; i < KP; ++i) {
 #pragma unroll
-      for (int j = 0; j < KP; ++j) acc_mac(sh[j], sl[j], av[i], ca[i * KP + j]);
+      for (int j = 0; j < KP; ++j) V::mac(acc[j], av[i], ca[i * KP + j]);
     }
 #pragma unroll
-    for (int j = 0; j < KP; ++j) acc_norm(sh[j], sl[j]);
+    for (int j = 0; j < KP; ++j) V::norm(acc[j]);
   }
 #pragma unroll
-  for (int j = 0; j < KP; ++j) Y[r * KP + j] = acc_get(sh[j], sl[j]);
+  for (int j = 0; j < KP; ++j) Y[r * KP + j] = V::get(acc[j]);
 }
 
 // Short blocks: one thread per element (row r, column j) instead of per row,
 // the same sum in the same order as k_update.
-template <int KP>
+template <int KP, bool F64>
 __global__ void __launch_bounds__(256) k_update_el(float2* Y, const float2* X, const float2* __restrict__ alpha,
                                                    BlockList A, const float2* __restrict__ coef, int64_t r0,
                                                    int64_t r1) {
+  using V = Ar<F64>;
   extern __shared__ float2 scoef[];
   const int ncoef = A.n * KP * KP;
   for (int t = threadIdx.x; t < ncoef; t += blockDim.x) scoef[t] = coef[t];
@@ -187,27 +191,25 @@ __global__ void __launch_bounds__(256) k_update_el(float2* Y, const float2* X, c
   const int64_t r = r0 + t / KP;
   const int j = static_cast<int>(t % KP);
   if (r >= r1) return;
-  float sh = 0.f, sl = 0.f;
-  if (X && alpha) {
-    const float2 x = df_mul(alpha[j], X[r * KP + j]);
-    sh = x.x;
-    sl = x.y;
-  }
+  typename V::Acc acc;
+  V::zero(acc);
+  if (X && alpha) V::set(acc, V::mul(alpha[j], X[r * KP + j]));
   for (int a = 0; a < A.n; ++a) {
     const float2* ar = A.p[a] + r * KP;
     const float2* ca = scoef + a * KP * KP + j;
 #pragma unroll
-    for (int i = 0; i < KP; ++i) acc_mac(sh, sl, ar[i], ca[i * KP]);
-    acc_norm(sh, sl);
+    for (int i = 0; i < KP; ++i) V::mac(acc, ar[i], ca[i * KP]);
+    V::norm(acc);
   }
   __syncwarp();
-  Y[r * KP + j] = acc_get(sh, sl);
+  Y[r * KP + j] = V::get(acc);
 }
 
-template <int KP>
+template <int KP, bool F64>
 __global__ void __launch_bounds__(256) k_combine_diag(float2* Y, const float2* X, const float2* __restrict__ alpha,
                                                       BlockList A, const float2* __restrict__ coef, int64_t r0,
                                                       int64_t r1) {
+  using V = Ar<F64>;
   __shared__ float2 sc[kMaxBlocks * 8];
   __shared__ float2 salpha[8];
   for (int t = threadIdx.x; t < A.n * 8; t += blockDim.x) sc[t] = coef[t];
@@ -215,23 +217,19 @@ __global__ void __launch_bounds__(256) k_combine_diag(float2* Y, const float2* X
   __syncthreads();
   const int64_t r = r0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= r1) return;
-  float sh[KP], sl[KP];
+  typename V::Acc acc[KP];
 #pragma unroll
   for (int j = 0; j < KP; ++j) {
-    sh[j] = sl[j] = 0.f;
-    if (X && alpha) {
-      const float2 t = df_mul(salpha[j], X[r * KP + j]);
-      sh[j] = t.x;
-      sl[j] = t.y;
-    }
+    V::zero(acc[j]);
+    if (X && alpha) V::set(acc[j], V::mul(salpha[j], X[r * KP + j]));
   }
   for (int b = 0; b < A.n; ++b) {
     const float2* ab = A.p[b] + r * KP;
 #pragma unroll
-    for (int j = 0; j < KP; ++j) acc_mac(sh[j], sl[j], sc[b * 8 + j], ab[j]);
+    for (int j = 0; j < KP; ++j) V::mac(acc[j], sc[b * 8 + j], ab[j]);
   }
 #pragma unroll
-  for (int j = 0; j < KP; ++j) Y[r * KP + j] = acc_get(sh[j], sl[j]);
+  for (int j = 0; j < KP; ++j) Y[r * KP + j] = V::get(acc[j]);
 }
 
 struct Pairs {
@@ -239,22 +237,23 @@ struct Pairs {
   const float2* b[4];
 };
 
-template <int KP>
+template <int KP, bool F64>
 __global__ void __launch_bounds__(256) k_coldots(Pairs P, int nq, int64_t r0, int64_t r1, int64_t chunk,
                                                  float2* partials) {
+  using V = Ar<F64>;
   __shared__ float2 red[8][4 * 8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * chunk;
   const int64_t c1 = min(c0 + chunk, r1);
-  float sh[4 * KP], sl[4 * KP];
+  typename V::Acc acc[4 * KP];
 #pragma unroll
-  for (int t = 0; t < 4 * KP; ++t) sh[t] = sl[t] = 0.f;
+  for (int t = 0; t < 4 * KP; ++t) V::zero(acc[t]);
   for (int64_t r = c0 + threadIdx.x; r < c1; r += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (q < nq) {
 #pragma unroll
-        for (int j = 0; j < KP; ++j) acc_mac(sh[q * KP + j], sl[q * KP + j], P.a[q][r * KP + j], P.b[q][r * KP + j]);
+        for (int j = 0; j < KP; ++j) V::mac(acc[q * KP + j], P.a[q][r * KP + j], P.b[q][r * KP + j]);
       }
     }
   }
@@ -262,26 +261,27 @@ __global__ void __launch_bounds__(256) k_coldots(Pairs P, int nq, int64_t r0, in
 #pragma unroll
   for (int t = 0; t < 4 * KP; ++t) {
     if (t < nout) {
-      const float2 v = warp_sum_df(acc_get(sh[t], sl[t]));
+      const float2 v = warp_sum<F64>(V::get(acc[t]));
       if (lane == 0) red[warp][t] = v;
     }
   }
   __syncthreads();
   if (threadIdx.x < nout) {
     float2 s = red[0][threadIdx.x];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = df_add(s, red[w][threadIdx.x]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = V::add(s, red[w][threadIdx.x]);
     partials[static_cast<int64_t>(blockIdx.x) * nout + threadIdx.x] = s;
   }
 }
 
 // Two threads per row, each owning half of the KP columns (halves the
 // accumulator registers, so twice the warps fit per SM).
-template <int KP>
+template <int KP, bool F64>
 __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, const float2* __restrict__ Y,
                                                     const float2* __restrict__ theta, int64_t n, float2* partials,
                                                     double* Zout, int64_t ldz, int ncols, float2* Tout,
                                                     const float2* __restrict__ diag, float clamp, float2* Zlead,
                                                     float2* Rlead, int64_t nlead) {
+  using V = Ar<F64>;
   constexpr int CH = KP / 2;
   extern __shared__ float2 sy[];
   const int ny = Q.n * KP * KP;
@@ -293,15 +293,18 @@ __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, c
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int half = threadIdx.x & 1;
   const int j0 = half * CH;
-  float rh[CH], rl[CH];
+  typename V::Acc racc[CH];
 #pragma unroll
-  for (int c = 0; c < CH; ++c) rh[c] = rl[c] = 0.f;
+  for (int c = 0; c < CH; ++c) V::zero(racc[c]);
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kChunk;
   const int64_t c1 = min(c0 + kChunk, n);
   for (int64_t r = c0 + (threadIdx.x >> 1); r < c1; r += blockDim.x >> 1) {
-    float zh[CH], zl[CH], hh[CH], hl[CH];
+    typename V::Acc za[CH], ha[CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) zh[c] = zl[c] = hh[c] = hl[c] = 0.f;
+    for (int c = 0; c < CH; ++c) {
+      V::zero(za[c]);
+      V::zero(ha[c]);
+    }
     for (int a = 0; a < Q.n; ++a) {
       const float4* qa = reinterpret_cast<const float4*>(Q.p[a] + r * KP);
       const float4* wa = reinterpret_cast<const float4*>(Wb.p[a] + r * KP);
@@ -312,25 +315,25 @@ __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, c
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
           const float2 y0 = ya[(2 * q) * KP + c], y1 = ya[(2 * q + 1) * KP + c];
-          acc_mac(zh[c], zl[c], make_float2(qv.x, qv.y), y0);
-          acc_mac(hh[c], hl[c], make_float2(wv.x, wv.y), y0);
-          acc_mac(zh[c], zl[c], make_float2(qv.z, qv.w), y1);
-          acc_mac(hh[c], hl[c], make_float2(wv.z, wv.w), y1);
+          V::mac(za[c], make_float2(qv.x, qv.y), y0);
+          V::mac(ha[c], make_float2(wv.x, wv.y), y0);
+          V::mac(za[c], make_float2(qv.z, qv.w), y1);
+          V::mac(ha[c], make_float2(wv.z, wv.w), y1);
         }
       }
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
-        acc_norm(zh[c], zl[c]);
-        acc_norm(hh[c], hl[c]);
+        V::norm(za[c]);
+        V::norm(ha[c]);
       }
     }
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       const int j = j0 + c;
-      const float2 z = acc_get(zh[c], zl[c]);
-      const float2 d = df_sub(acc_get(hh[c], hl[c]), df_mul(sth[j], z));
-      acc_mac(rh[c], rl[c], d, d);
-      if (Zout && j < ncols) Zout[r * ldz + j] = df_to_double(z);
+      const float2 z = V::get(za[c]);
+      const float2 d = V::sub(V::get(ha[c]), V::mul(sth[j], z));
+      V::mac(racc[c], d, d);
+      if (Zout && j < ncols) Zout[r * ldz + j] = V::to_d(z);
       if (Zlead && r < nlead) {
         Zlead[r * KP + j] = z;
         Rlead[r * KP + j] = d;
@@ -338,47 +341,45 @@ __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, c
       if (Tout) {
         // preconditioned residual d / (H_rr - theta_j), denominator clamped to |.| >= clamp
         float2 t = d;
-        if (diag) {
-          float2 den = df_sub(diag[r], sth[j]);
-          if (fabsf(den.x) < clamp) den = make_float2(den.x < 0.f ? -clamp : clamp, 0.f);
-          t = df_div(d, den);
-        }
+        if (diag) t = V::div(d, V::clamp_den(V::sub(diag[r], sth[j]), clamp));
         Tout[r * KP + j] = t;
       }
     }
   }
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
-    float2 v = acc_get(rh[c], rl[c]);
+    float2 v = V::get(racc[c]);
     // sum over the lanes of equal half (butterfly over the row bits)
 #pragma unroll
-    for (int m = 2; m < 32; m <<= 1) v = df_add(v, shfl_xor_df(v, m));
+    for (int m = 2; m < 32; m <<= 1) v = V::add(v, shfl_xor_df(v, m));
     if (lane < 2) red[warp][j0 + c] = v;
   }
   __syncthreads();
   if (threadIdx.x < KP) {
     float2 s = red[0][threadIdx.x];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = df_add(s, red[w][threadIdx.x]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = V::add(s, red[w][threadIdx.x]);
     partials[static_cast<int64_t>(blockIdx.x) * KP + threadIdx.x] = s;
   }
 }
 
+template <bool F64>
 __global__ void k_f64_to_df(const double* __restrict__ X, int64_t ldx, int ncols, float2* __restrict__ Y, int kp,
                             int64_t r0, int64_t r1) {
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t r = r0 + t / kp;
   const int c = static_cast<int>(t % kp);
   if (r >= r1) return;
-  Y[r * kp + c] = (c < ncols) ? df_from_double(X[r * ldx + c]) : make_float2(0.f, 0.f);
+  Y[r * kp + c] = (c < ncols) ? Ar<F64>::from_d(X[r * ldx + c]) : make_float2(0.f, 0.f);
 }
 
+template <bool F64>
 __global__ void k_df_to_f64(const float2* __restrict__ X, int kp, double* __restrict__ Y, int64_t ldy, int ncols,
                             int64_t r0, int64_t r1) {
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t r = r0 + t / ncols;
   const int c = static_cast<int>(t % ncols);
   if (r >= r1) return;
-  Y[r * ldy + c] = df_to_double(X[r * kp + c]);
+  Y[r * ldy + c] = Ar<F64>::to_d(X[r * kp + c]);
 }
 
 __global__ void k_zero(float2* Y, int64_t count) {
@@ -388,10 +389,37 @@ __global__ void k_zero(float2* Y, int64_t count) {
 
 inline unsigned nblk(int64_t work, int threads) { return static_cast<unsigned>((work + threads - 1) / threads); }
 
+// Calls f.template operator()<KP, F64>() for the run-time column count and format.
+template <class F>
+cudaError_t dispatch(int kp, bool f64, F&& f) {
+  switch (kp * 2 + (f64 ? 1 : 0)) {
+    case 4: f.template operator()<2, false>(); break;
+    case 5: f.template operator()<2, true>(); break;
+    case 8: f.template operator()<4, false>(); break;
+    case 9: f.template operator()<4, true>(); break;
+    case 12: f.template operator()<6, false>(); break;
+    case 13: f.template operator()<6, true>(); break;
+    case 16: f.template operator()<8, false>(); break;
+    case 17: f.template operator()<8, true>(); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t finish(const float2* partials, int64_t nchunks, int nout, double* out, bool f64, cudaStream_t s) {
+  if (f64)
+    k_finish<true><<<nblk((int64_t)nout * 32, 256), 256, 0, s>>>(partials, nchunks, nout, out);
+  else
+    k_finish<false><<<nblk((int64_t)nout * 32, 256), 256, 0, s>>>(partials, nchunks, nout, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_t r1, double* out,
-                 float2* partials, int64_t partial_cap, cudaStream_t s) {
+                 float2* partials, int64_t partial_cap, bool f64, cudaStream_t s) {
   const int nout = A.n * kp * kp;
   if (r1 <= r0 || A.n == 0) {
     return cudaMemsetAsync(out, 0, sizeof(double) * nout, s);
@@ -404,60 +432,35 @@ cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_
   }
   if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(nchunks);
-  switch (kp) {
-    case 2: k_gram<2><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); count_launch(); break;
-    case 4: k_gram<4><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); count_launch(); break;
-    case 6: k_gram<6><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); count_launch(); break;
-    case 8: k_gram<8><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); count_launch(); break;
-    default: return cudaErrorInvalidValue;
-  }
-  k_finish<<<nblk((int64_t)nout * 32, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
-  return cudaGetLastError();
+  cudaError_t e = dispatch(kp, f64, [&]<int KP, bool F>() { k_gram<KP, F><<<g, 256, 0, s>>>(A, B, r0, r1, chunk, partials); });
+  if (e != cudaSuccess) return e;
+  return finish(partials, nchunks, nout, out, f64, s);
 }
 
 cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef, int kp,
-                   int64_t r0, int64_t r1, cudaStream_t s) {
+                   int64_t r0, int64_t r1, bool f64, cudaStream_t s) {
   if (r1 <= r0) return cudaSuccess;
   const size_t smem = sizeof(float2) * (size_t)(A.n > 0 ? A.n : 1) * kp * kp;
   if (r1 - r0 < static_cast<int64_t>(kChunk) * 64) {
     // short blocks (the leading block): one thread per element for parallelism
     const unsigned ge = nblk((r1 - r0) * kp, 256);
-    switch (kp) {
-      case 2: k_update_el<2><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-      case 4: k_update_el<4><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-      case 6: k_update_el<6><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-      case 8: k_update_el<8><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-      default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return dispatch(kp, f64,
+                    [&]<int KP, bool F>() { k_update_el<KP, F><<<ge, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); });
   }
   const unsigned g = nblk(r1 - r0, 256);
-  switch (kp) {
-    case 2: k_update<2><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-    case 4: k_update<4><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-    case 6: k_update<6><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-    case 8: k_update<8><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return dispatch(kp, f64, [&]<int KP, bool F>() { k_update<KP, F><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); });
 }
 
 cudaError_t combine_diag(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef,
-                         int kp, int64_t r0, int64_t r1, cudaStream_t s) {
+                         int kp, int64_t r0, int64_t r1, bool f64, cudaStream_t s) {
   if (r1 <= r0) return cudaSuccess;
   const unsigned g = nblk(r1 - r0, 256);
-  switch (kp) {
-    case 2: k_combine_diag<2><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-    case 4: k_combine_diag<4><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-    case 6: k_combine_diag<6><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-    case 8: k_combine_diag<8><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); count_launch(); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return dispatch(kp, f64,
+                  [&]<int KP, bool F>() { k_combine_diag<KP, F><<<g, 256, 0, s>>>(Y, X, alpha, A, coef, r0, r1); });
 }
 
 cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int kp, int64_t r0, int64_t r1,
-                    double* out, float2* partials, int64_t partial_cap, cudaStream_t s) {
+                    double* out, float2* partials, int64_t partial_cap, bool f64, cudaStream_t s) {
   if (nq < 1 || nq > 4) return cudaErrorInvalidValue;
   const int nout = nq * kp;
   if (r1 <= r0) return cudaMemsetAsync(out, 0, sizeof(double) * nout, s);
@@ -474,47 +477,47 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
   }
   if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(nchunks);
-  switch (kp) {
-    case 2: k_coldots<2><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); count_launch(); break;
-    case 4: k_coldots<4><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); count_launch(); break;
-    case 6: k_coldots<6><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); count_launch(); break;
-    case 8: k_coldots<8><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); count_launch(); break;
-    default: return cudaErrorInvalidValue;
-  }
-  k_finish<<<nblk((int64_t)nout * 32, 256), 256, 0, s>>>(partials, nchunks, nout, out); count_launch();
-  return cudaGetLastError();
+  cudaError_t e =
+      dispatch(kp, f64, [&]<int KP, bool F>() { k_coldots<KP, F><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); });
+  if (e != cudaSuccess) return e;
+  return finish(partials, nchunks, nout, out, f64, s);
 }
 
 cudaError_t ritz_resid(const BlockList& Q, const BlockList& Wb, const float2* Y, const float2* theta, int kp,
                        int64_t n, double* out, float2* partials, int64_t partial_cap, double* Zout, int64_t ldz,
-                       int ncols, float2* Tout, const float2* diag, float clamp, cudaStream_t s, float2* Zlead,
-                       float2* Rlead, int64_t nlead) {
+                       int ncols, float2* Tout, const float2* diag, float clamp, bool f64, cudaStream_t s,
+                       float2* Zlead, float2* Rlead, int64_t nlead) {
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   if (nchunks * kp > partial_cap) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float2) * (size_t)Q.n * kp * kp;
   const unsigned g = static_cast<unsigned>(nchunks);
-  switch (kp) {
-    case 2: k_ritz_resid<2><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead, Rlead, nlead); count_launch(); break;
-    case 4: k_ritz_resid<4><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead, Rlead, nlead); count_launch(); break;
-    case 6: k_ritz_resid<6><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead, Rlead, nlead); count_launch(); break;
-    case 8: k_ritz_resid<8><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead, Rlead, nlead); count_launch(); break;
-    default: return cudaErrorInvalidValue;
-  }
-  k_finish<<<nblk((int64_t)kp * 32, 256), 256, 0, s>>>(partials, nchunks, kp, out); count_launch();
-  return cudaGetLastError();
+  cudaError_t e = dispatch(kp, f64, [&]<int KP, bool F>() {
+    k_ritz_resid<KP, F><<<g, 256, smem, s>>>(Q, Wb, Y, theta, n, partials, Zout, ldz, ncols, Tout, diag, clamp, Zlead,
+                                             Rlead, nlead);
+  });
+  if (e != cudaSuccess) return e;
+  return finish(partials, nchunks, kp, out, f64, s);
 }
 
-cudaError_t f64_to_df(const double* X, int64_t ldx, int ncols, float2* Y, int kp, int64_t r0, int64_t r1,
+cudaError_t f64_to_df(const double* X, int64_t ldx, int ncols, float2* Y, int kp, int64_t r0, int64_t r1, bool f64,
                       cudaStream_t s) {
   if (r1 <= r0) return cudaSuccess;
-  k_f64_to_df<<<nblk((r1 - r0) * kp, 256), 256, 0, s>>>(X, ldx, ncols, Y, kp, r0, r1); count_launch();
+  if (f64)
+    k_f64_to_df<true><<<nblk((r1 - r0) * kp, 256), 256, 0, s>>>(X, ldx, ncols, Y, kp, r0, r1);
+  else
+    k_f64_to_df<false><<<nblk((r1 - r0) * kp, 256), 256, 0, s>>>(X, ldx, ncols, Y, kp, r0, r1);
+  count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t df_to_f64(const float2* X, int kp, double* Y, int64_t ldy, int ncols, int64_t r0, int64_t r1,
+cudaError_t df_to_f64(const float2* X, int kp, double* Y, int64_t ldy, int ncols, int64_t r0, int64_t r1, bool f64,
                       cudaStream_t s) {
   if (r1 <= r0 || ncols <= 0) return cudaSuccess;
-  k_df_to_f64<<<nblk((r1 - r0) * ncols, 256), 256, 0, s>>>(X, kp, Y, ldy, ncols, r0, r1); count_launch();
+  if (f64)
+    k_df_to_f64<true><<<nblk((r1 - r0) * ncols, 256), 256, 0, s>>>(X, kp, Y, ldy, ncols, r0, r1);
+  else
+    k_df_to_f64<false><<<nblk((r1 - r0) * ncols, 256), 256, 0, s>>>(X, kp, Y, ldy, ncols, r0, r1);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@
 // its next barrier.
 #include <cooperative_groups.h>
 
-#include "spmm_core.cuh"  // policy_keep
+#include "spmm_core.cuh"  // policy_keep, val.cuh
 
 namespace sppc {
 
@@ -122,11 +122,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned l
 // the 16 lane sums are combined by a fixed shuffle tree.  Every CTA computes the
 // same result; it lands in red_out (shared).
 constexpr int kMaxPartialsPerWarp = 16;  // gridDim.x <= 16 * kMinresWarps
+template <bool F64>
 __device__ void reduce_partials(const float2* partials, int nout, float2* red_out) {
+  using V = Ar<F64>;
   const int t = threadIdx.x;
   const int o = t >> 4, part = t & 15;
   const int G = static_cast<int>(gridDim.x);
-  float sh = 0.f, sl = 0.f;
+  typename V::Acc sa;
+  V::zero(sa);
   if (o < nout) {
     float2 v[kMaxPartialsPerWarp];
 #pragma unroll
@@ -136,13 +139,13 @@ __device__ void reduce_partials(const float2* partials, int nout, float2* red_ou
     }
 #pragma unroll
     for (int i = 0; i < kMaxPartialsPerWarp; ++i) {
-      acc_add(sh, sl, v[i]);
-      acc_norm(sh, sl);
+      V::acc(sa, v[i]);
+      V::norm(sa);
     }
   }
-  float2 r = acc_get(sh, sl);
+  float2 r = V::get(sa);
 #pragma unroll
-  for (int m = 8; m > 0; m >>= 1) r = df_add(r, shfl_xor_df(r, m));
+  for (int m = 8; m > 0; m >>= 1) r = V::add(r, shfl_xor_df(r, m));
   if (part == 0 && o < nout) red_out[o] = r;
   __syncthreads();
 }
@@ -183,13 +186,14 @@ __device__ __forceinline__ void gather_p(const float2* X, int cidx, int off, flo
 // Row sums of H0_hat p for one row: this lane's segment (entries seg, seg+4, ...),
 // columns [off, off + CPL), in batches of 4 independent gathers, then the
 // segment sums combined across the 4 lanes of the half (all 32 lanes call it).
-template <int KP>
+template <int KP, bool F64>
 __device__ __forceinline__ void row_product(const CsrDev& A, int64_t row, bool valid, int seg, int off,
                                             const float2* P, uint64_t pol, float2 (&out)[KP / 2]) {
+  using V = Ar<F64>;
   constexpr int CPL = KP / 2;
-  float ah[CPL], al[CPL];
+  typename V::Acc acc[CPL];
 #pragma unroll
-  for (int c = 0; c < CPL; ++c) ah[c] = al[c] = 0.f;
+  for (int c = 0; c < CPL; ++c) V::zero(acc[c]);
   if (valid) {
     const int64_t rb = __ldg(A.rowptr + row), re = __ldg(A.rowptr + row + 1);
     for (int64_t e = rb + seg; e < re; e += 16) {
@@ -214,22 +218,24 @@ __device__ __forceinline__ void row_product(const CsrDev& A, int64_t row, bool v
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) acc_mac(ah[c], al[c], vv[u], xx[u][c]);
+        for (int c = 0; c < CPL; ++c) V::mac(acc[c], vv[u], xx[u][c]);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) acc_norm(ah[c], al[c]);
+      for (int c = 0; c < CPL; ++c) V::norm(acc[c]);
     }
   }
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
-    float2 v = acc_get(ah[c], al[c]);
-    v = df_add(v, shfl_xor_df(v, 1));
-    v = df_add(v, shfl_xor_df(v, 2));
+    float2 v = V::get(acc[c]);
+    v = V::add(v, shfl_xor_df(v, 1));
+    v = V::add(v, shfl_xor_df(v, 2));
     out[c] = v;
   }
 }
 
-template <int KP>
+template <int KP, bool F64>
 __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a) {
+  using V = Ar<F64>;
+  using Acc = typename V::Acc;
   constexpr int CPL = KP / 2;
   constexpr int kRowsPerWarp = 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -254,21 +260,21 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
   __shared__ float2 c_invb[8], c_wa[8], c_w2[8], c_w1[8], c_x[8], c_s[8], c_beta[8], c_alpha[8];
   __shared__ int s_dow, s_all;
 
-  float2 *P = a.P, *V = a.V, *VP = a.VP, *W1 = a.W1, *W2 = a.W2;
+  float2 *P = a.P, *Vv = a.V, *VP = a.VP, *W1 = a.W1, *W2 = a.W2;
 
   // Two partial buffers, used by alternate phases (init and B: 1, A: 0): a CTA
   // rewrites a buffer only after the next grid barrier, which every CTA reaches
   // after its reads of that buffer.
   float2* const pbuf[2] = {a.partials, a.partials + static_cast<int64_t>(32) * gridDim.x};
   // write this CTA's partial of nq dots (columns 0..KP-1) to buf[o * G + blockIdx]
-  auto flush = [&](float (&h)[4], float (&l)[4], int nq, float2* buf) {
+  auto flush = [&](Acc (&d)[4], int nq, float2* buf) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (q >= nq) break;
-      float2 v = has_col ? acc_get(h[q], l[q]) : make_float2(0.f, 0.f);
+      float2 v = has_col ? V::get(d[q]) : make_float2(0.f, 0.f);
       // sum over the 4 rows of the warp (lanes with equal half and seg)
-      v = df_add(v, shfl_xor_df(v, 8));
-      v = df_add(v, shfl_xor_df(v, 16));
+      v = V::add(v, shfl_xor_df(v, 8));
+      v = V::add(v, shfl_xor_df(v, 16));
       if (lane < 8 && has_col) wred[warp][q * 8 + j] = v;
     }
     __syncthreads();
@@ -278,42 +284,42 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       const int o = threadIdx.x >> 4, w = threadIdx.x & 15;
       float2 v = (o < nq * 8) ? wred[w][o] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int m = 8; m > 0; m >>= 1) v = df_add(v, shfl_xor_df(v, m));
+      for (int m = 8; m > 0; m >>= 1) v = V::add(v, shfl_xor_df(v, m));
       if (w == 0 && o < nq * 8) buf[static_cast<int64_t>(o) * gridDim.x + blockIdx.x] = v;
     }
     __syncthreads();
   };
-  auto zero4 = [](float (&h)[4], float (&l)[4]) {
+  auto zero4 = [](Acc (&d)[4]) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) h[q] = l[q] = 0.f;
+    for (int q = 0; q < 4; ++q) V::zero(d[q]);
   };
 
   for (int t = threadIdx.x; t < kMinresWarps * 32; t += kMinresThreads)
     wred[t / 32][t % 32] = make_float2(0.f, 0.f);
   __syncthreads();
-  float dh[4], dl[4];
+  Acc dd[4];
   // ---- init: zero V, VP, W1, W2, X on owned elements; ||b1||^2 partial
-  zero4(dh, dl);
+  zero4(dd);
   for (int64_t r0 = row0; r0 < n; r0 += rstride) {
     const int64_t row = r0 + rq;
     if (row >= n || !has_col) continue;
     const int64_t b = row * KP + j;
     const float2 z = make_float2(0.f, 0.f);
-    V[b] = z;
+    Vv[b] = z;
     VP[b] = z;
     W1[b] = z;
     W2[b] = z;
     a.X[b] = z;
     const float2 pv = P[b];
-    acc_mac(dh[0], dl[0], pv, pv);
-    acc_norm(dh[0], dl[0]);
+    V::mac(dd[0], pv, pv);
+    V::norm(dd[0]);
   }
-  flush(dh, dl, 1, pbuf[1]);
+  flush(dd, 1, pbuf[1]);
   if (!grid_barrier(a.bar, err, a.spin_limit)) return;
-  reduce_partials(pbuf[1], 8, sdot);
+  reduce_partials<F64>(pbuf[1], 8, sdot);
   if (threadIdx.x < 8) {
     const int jj = threadIdx.x;
-    const double b1 = (jj < a.k) ? sqrt(fmax(df_to_double(sdot[jj]), 0.0)) : 0.0;
+    const double b1 = (jj < a.k) ? sqrt(fmax(V::to_d(sdot[jj]), 0.0)) : 0.0;
     st_beta[jj] = b1;
     st_b1[jj] = b1;
     st_eta[jj] = b1;
@@ -322,7 +328,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
     st_sp[jj] = st_sc[jj] = 0.0;
     st_done[jj] = (b1 > 0.0) ? 0 : 1;
     st_it[jj] = 0;
-    c_invb[jj] = st_done[jj] ? make_float2(0.f, 0.f) : df_from_double(1.0 / b1);
+    c_invb[jj] = st_done[jj] ? make_float2(0.f, 0.f) : V::from_d(1.0 / b1);
   }
   if (threadIdx.x == 0) {
     s_dow = 0;
@@ -334,22 +340,22 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
   bool finish = false;
   while (true) {
     // ---- phase A
-    zero4(dh, dl);
+    zero4(dd);
     for (int64_t r0 = row0; r0 < n; r0 += rstride) {
       const int64_t row = r0 + rq;
       const bool valid = row < n;
       float2 hp[CPL];
-      if (!finish) row_product<KP>(a.A, row, valid, seg, off, P, pol, hp);
+      if (!finish) row_product<KP, F64>(a.A, row, valid, seg, off, P, pol, hp);
       if (!valid || !has_col) continue;
       const int64_t b = row * KP + j;
-      const float2 vold = V[b];
+      const float2 vold = Vv[b];
       if (s_dow) {
         // w_new = (v - rho3 w2 - rho2 w1) / rho1 ; x += c eta w_new
-        float2 wn = df_mul(c_wa[j], vold);
-        wn = df_add(wn, df_mul(c_w2[j], W2[b]));
-        wn = df_add(wn, df_mul(c_w1[j], W1[b]));
+        float2 wn = V::mul(c_wa[j], vold);
+        wn = V::add(wn, V::mul(c_w2[j], W2[b]));
+        wn = V::add(wn, V::mul(c_w1[j], W1[b]));
         W2[b] = wn;  // W2's buffer becomes w_new (roles swap below)
-        a.X[b] = df_add(a.X[b], df_mul(c_x[j], wn));
+        a.X[b] = V::add(a.X[b], V::mul(c_x[j], wn));
       }
       if (finish) continue;
       float2 hj = hp[0];
@@ -357,19 +363,19 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       for (int c = 1; c < CPL; ++c)
         if (c == seg) hj = hp[c];
       const float2 pv = P[b];
-      const float2 vn = df_mul(c_invb[j], pv);
+      const float2 vn = V::mul(c_invb[j], pv);
       VP[b] = vn;  // VP's buffer becomes v_new (roles swap below)
       // y = (H0_hat p - E p) / beta
-      float2 y = df_add(hj, df_mul(a.negE[j], pv));
-      y = df_mul(c_invb[j], y);
+      float2 y = V::add(hj, V::mul(a.negE[j], pv));
+      y = V::mul(c_invb[j], y);
       a.Y[b] = y;
       const float2 ps = __ldg(a.psi + b);
-      acc_mac(dh[0], dl[0], vn, y);
-      acc_mac(dh[1], dl[1], ps, y);
-      acc_mac(dh[2], dl[2], vn, ps);
-      acc_mac(dh[3], dl[3], vn, vold);
+      V::mac(dd[0], vn, y);
+      V::mac(dd[1], ps, y);
+      V::mac(dd[2], vn, ps);
+      V::mac(dd[3], vn, vold);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc_norm(dh[q], dl[q]);
+      for (int q = 0; q < 4; ++q) V::norm(dd[q]);
     }
     if (s_dow) {
       float2* t = W2;
@@ -379,43 +385,43 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
     if (finish) break;
     {
       float2* t = VP;
-      VP = V;
-      V = t;
+      VP = Vv;
+      Vv = t;
     }
-    flush(dh, dl, 4, pbuf[0]);
+    flush(dd, 4, pbuf[0]);
     if (!grid_barrier(a.bar, err, a.spin_limit)) return;
     // ---- phase B
-    reduce_partials(pbuf[0], 32, sdot);
+    reduce_partials<F64>(pbuf[0], 32, sdot);
     if (threadIdx.x < 8) {
       const int jj = threadIdx.x;
       double s = 0.0, al = 0.0;
       if (!st_done[jj]) {
-        s = df_to_double(sdot[8 + jj]);
-        al = df_to_double(sdot[jj]) - s * df_to_double(sdot[16 + jj]) - st_beta[jj] * df_to_double(sdot[24 + jj]);
+        s = V::to_d(sdot[8 + jj]);
+        al = V::to_d(sdot[jj]) - s * V::to_d(sdot[16 + jj]) - st_beta[jj] * V::to_d(sdot[24 + jj]);
       }
       st_alpha[jj] = al;
-      c_s[jj] = df_from_double(-s);
-      c_beta[jj] = df_from_double(st_done[jj] ? 0.0 : -st_beta[jj]);
-      c_alpha[jj] = df_from_double(-al);
+      c_s[jj] = V::from_d(-s);
+      c_beta[jj] = V::from_d(st_done[jj] ? 0.0 : -st_beta[jj]);
+      c_alpha[jj] = V::from_d(-al);
     }
     __syncthreads();
-    zero4(dh, dl);
+    zero4(dd);
     for (int64_t r0 = row0; r0 < n; r0 += rstride) {
       const int64_t row = r0 + rq;
       if (row >= n || !has_col) continue;
       const int64_t b = row * KP + j;
       float2 pn = a.Y[b];
-      pn = df_add(pn, df_mul(c_s[j], __ldg(a.psi + b)));
-      pn = df_add(pn, df_mul(c_beta[j], VP[b]));
-      pn = df_add(pn, df_mul(c_alpha[j], V[b]));
+      pn = V::add(pn, V::mul(c_s[j], __ldg(a.psi + b)));
+      pn = V::add(pn, V::mul(c_beta[j], VP[b]));
+      pn = V::add(pn, V::mul(c_alpha[j], Vv[b]));
       P[b] = pn;
-      acc_mac(dh[0], dl[0], pn, pn);
-      acc_norm(dh[0], dl[0]);
+      V::mac(dd[0], pn, pn);
+      V::norm(dd[0]);
     }
-    flush(dh, dl, 1, pbuf[1]);
+    flush(dd, 1, pbuf[1]);
     if (!grid_barrier(a.bar, err, a.spin_limit)) return;
     // ---- phase C
-    reduce_partials(pbuf[1], 8, sdot);
+    reduce_partials<F64>(pbuf[1], 8, sdot);
     ++it;
     if (threadIdx.x < 8) {
       const int jj = threadIdx.x;
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       if (st_done[jj]) {
         c_wa[jj] = c_w2[jj] = c_w1[jj] = c_x[jj] = c_invb[jj] = z;
       } else {
-        const double bn = sqrt(fmax(df_to_double(sdot[jj]), 0.0));
+        const double bn = sqrt(fmax(V::to_d(sdot[jj]), 0.0));
         const double al = st_alpha[jj], be = st_beta[jj];
         const double delta = st_cc[jj] * al - st_cp[jj] * st_sc[jj] * be;
         // delta and beta are of the order of ||H0_hat||: no overflow guard needed
@@ -437,10 +443,10 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
         } else {
           const double inv = 1.0 / rho1;  // one division, the rest are products
           const double cn = delta * inv, sn = bn * inv;
-          c_wa[jj] = df_from_double(inv);
-          c_w2[jj] = df_from_double(-rho3 * inv);
-          c_w1[jj] = df_from_double(-rho2 * inv);
-          c_x[jj] = df_from_double(cn * st_eta[jj]);
+          c_wa[jj] = V::from_d(inv);
+          c_w2[jj] = V::from_d(-rho3 * inv);
+          c_w1[jj] = V::from_d(-rho2 * inv);
+          c_x[jj] = V::from_d(cn * st_eta[jj]);
           st_rn[jj] = fabs(sn) * st_rn[jj];
           st_eta[jj] = -sn * st_eta[jj];
           st_cp[jj] = st_cc[jj];
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
           st_sc[jj] = sn;
           const bool conv = (st_rn[jj] <= a.tol * st_b1[jj]) || (bn == 0.0);
           if (conv) st_done[jj] = 1;
-          c_invb[jj] = conv ? z : df_from_double(1.0 / bn);
+          c_invb[jj] = conv ? z : V::from_d(1.0 / bn);
         }
         st_beta[jj] = bn;
       }
@@ -473,7 +479,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
 }  // namespace
 
 // Buffers: P holds b1 on entry (overwritten); V, VP, Y, W1, W2 are scratch;
-// X receives the solution.  All n1 x kp double-float.  status (host-visible via
+// X receives the solution.  All n1 x kp value slots in A's format.  status (host-visible via
 // a copy): [0] time-out flag, [1] iterations (negative: limit reached),
 // [2+j] iterations of column j.  bar: two zeroed unsigned words.
 cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
@@ -486,11 +492,15 @@ cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (!coop) return cudaErrorNotSupported;
   const void* fn = nullptr;
-  switch (kp) {
-    case 2: fn = reinterpret_cast<const void*>(k_minres<2>); break;
-    case 4: fn = reinterpret_cast<const void*>(k_minres<4>); break;
-    case 6: fn = reinterpret_cast<const void*>(k_minres<6>); break;
-    case 8: fn = reinterpret_cast<const void*>(k_minres<8>); break;
+  switch (kp * 2 + (A.f64 ? 1 : 0)) {
+    case 4: fn = reinterpret_cast<const void*>(k_minres<2, false>); break;
+    case 5: fn = reinterpret_cast<const void*>(k_minres<2, true>); break;
+    case 8: fn = reinterpret_cast<const void*>(k_minres<4, false>); break;
+    case 9: fn = reinterpret_cast<const void*>(k_minres<4, true>); break;
+    case 12: fn = reinterpret_cast<const void*>(k_minres<6, false>); break;
+    case 13: fn = reinterpret_cast<const void*>(k_minres<6, true>); break;
+    case 16: fn = reinterpret_cast<const void*>(k_minres<8, false>); break;
+    case 17: fn = reinterpret_cast<const void*>(k_minres<8, true>); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMinresThreads, 0);

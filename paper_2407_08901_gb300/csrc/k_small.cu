@@ -3,14 +3,15 @@
 // matrix Q^T H Q (Eqs. tilde_H, proj; at most k(p_max+1) <= 144 rows).
 //
 // FP64 runs at ~1/70 of FP32 on this GPU, so the eigensolve does its O(m^3)
-// parts (Householder tridiagonalisation, back-transformation) in double-float
-// and brackets the eigenvalues in FP32 first; FP64 is kept for the O(m) per
-// vector tridiagonal work (inverse iteration, Rayleigh quotients) and for
-// crowded eigenvalues.
+// parts (Householder tridiagonalisation, back-transformation) in the slot
+// format (double-float on the default path, FP64 on the native FP64 path) and
+// brackets the eigenvalues in FP32 first; FP64 is kept for the O(m) per vector
+// tridiagonal work (inverse iteration, Rayleigh quotients) and for crowded
+// eigenvalues.
 #include <math.h>
 
-#include "df.cuh"
 #include "sppc_internal.h"
+#include "val.cuh"
 
 namespace sppc {
 
@@ -20,7 +21,7 @@ constexpr int kMaxM = 144;
 constexpr int kMaxNev = 16;
 
 __global__ void k_chol_rinv(const double* __restrict__ G, int ldg, int kk, int kp, double shift_rel,
-                            double* __restrict__ R, float2* __restrict__ Rinv_df, int* status) {
+                            double* __restrict__ R, float2* __restrict__ Rinv_df, int* status, bool f64) {
   __shared__ double A[16][17];
   __shared__ double Ri[16][17];
   __shared__ int bad;
@@ -72,7 +73,7 @@ __global__ void k_chol_rinv(const double* __restrict__ G, int ldg, int kk, int k
     const int i = e / kp, j = e % kp;
     const bool in = (i < kk && j < kk);
     R[i * kp + j] = (in && j >= i) ? A[i][j] : 0.0;
-    Rinv_df[e] = in ? df_from_double(Ri[i][j]) : make_float2(0.f, 0.f);
+    Rinv_df[e] = in ? slot_put(Ri[i][j], f64) : make_float2(0.f, 0.f);
   }
   if (t == 0) status[0] = bad;
 }
@@ -152,15 +153,26 @@ __device__ __forceinline__ float2 df_sqrt(float2 a) {
   return fast_two_sum(s, __fdiv_rn(r.x, __fmul_rn(2.f, s)));
 }
 
-// Block-wide double-float sum (all threads get the result).
-__device__ float2 block_sum_df(float2 v, float2* red) {
+template <bool F64>
+__device__ __forceinline__ float2 slot_sqrt(float2 a) {
+  if constexpr (F64) {
+    const double x = slot_d(a);
+    return d_slot(x > 0.0 ? __dsqrt_rn(x) : 0.0);
+  } else {
+    return df_sqrt(a);
+  }
+}
+
+// Block-wide sum in the slot format (all threads get the result).
+template <bool F64>
+__device__ float2 block_sum(float2 v, float2* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum_df(v);
+  v = warp_sum<F64>(v);
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     float2 t = red[0];
-    for (int w2 = 1; w2 < nw; ++w2) t = df_add(t, red[w2]);
+    for (int w2 = 1; w2 < nw; ++w2) t = Ar<F64>::add(t, red[w2]);
     red[32] = t;
   }
   __syncthreads();
@@ -234,8 +246,9 @@ __device__ T rayleigh_tri(const T* d, const T* e, int m, const T* y) {
 }
 
 // Symmetric eigensolve of the projected matrix, nev lowest pairs.
-//  1. Householder tridiagonalisation (Golub and Van Loan, Alg. 8.3.1) in
-//     double-float, matrix in shared memory with leading dimension m+1.
+//  1. Householder tridiagonalisation (Golub and Van Loan, Alg. 8.3.1) in the
+//     slot format (double-float, or FP64 for the native FP64 path), matrix in
+//     shared memory with leading dimension m+1.
 //  2. Eigenvalue brackets by Sturm-count multisection in FP32 to ~1e-5; indices
 //     whose brackets crowd a neighbour are narrowed further in FP64.
 //  3. Eigenvectors of the tridiagonal matrix by inverse iteration, one thread
@@ -245,9 +258,11 @@ __device__ T rayleigh_tri(const T* d, const T* e, int m, const T* y) {
 //     Crowded groups: shifts at the bracket midpoints (FP64 brackets ~1e-13
 //     wide), two FP64 steps, then modified Gram-Schmidt in the group.  The
 //     eigenvalue is the final Rayleigh quotient.
-//  4. Back-transformation through the stored reflectors in double-float.
+//  4. Back-transformation through the stored reflectors in the slot format.
+template <bool F64>
 __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ S, int lds, int m, int nev,
                                                      double* __restrict__ theta, double* __restrict__ V, int ldv) {
+  using AR = Ar<F64>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = m + 1;
   float2* A = reinterpret_cast<float2*>(smraw);  // m x ld, reflectors below the diagonal
@@ -270,31 +285,32 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
   const int lane = t & 31, warp = t >> 5, nwarp = nt >> 5;
   for (int x = t; x < m * m; x += nt) {
     const int i = x / m, j = x % m;
-    A[i * ld + j] = df_from_double(0.5 * (S[i * lds + j] + S[j * lds + i]));
+    A[i * ld + j] = AR::from_d(0.5 * (S[i * lds + j] + S[j * lds + i]));
   }
   __syncthreads();
-  // ---- 1. Householder tridiagonalisation (double-float)
+  // ---- 1. Householder tridiagonalisation (slot format)
   for (int j = 0; j + 2 < m; ++j) {
     const int len = m - j - 1;
-    float sh = 0.f, sl = 0.f;
+    typename AR::Acc sa;
+    AR::zero(sa);
     for (int i = t; i < len; i += nt) {
       const float2 xv = A[(j + 1 + i) * ld + j];
-      acc_mac(sh, sl, xv, xv);
+      AR::mac(sa, xv, xv);
     }
-    const float2 s2 = block_sum_df(acc_get(sh, sl), red);
+    const float2 s2 = block_sum<F64>(AR::get(sa), red);
     if (t == 0) {
       const float2 x0 = A[(j + 1) * ld + j];
-      const float2 nrm = df_sqrt(s2);
-      if (nrm.x == 0.f) {
+      const float2 nrm = slot_sqrt<F64>(s2);
+      if (AR::lead(nrm) == 0.0) {
         tau[j] = make_float2(0.f, 0.f);
         e[j] = 0.0;
         red[34] = make_float2(0.f, 0.f);
       } else {
-        const float2 alpha = (x0.x >= 0.f) ? df_neg(nrm) : nrm;
-        const float2 v0 = df_sub(x0, alpha);
-        const float2 vtv = df_add(df_sub(s2, df_mul(x0, x0)), df_mul(v0, v0));
-        tau[j] = df_div(make_float2(2.f, 0.f), vtv);
-        e[j] = df_to_double(alpha);
+        const float2 alpha = (AR::lead(x0) >= 0.0) ? AR::neg(nrm) : nrm;
+        const float2 v0 = AR::sub(x0, alpha);
+        const float2 vtv = AR::add(AR::sub(s2, AR::mul(x0, x0)), AR::mul(v0, v0));
+        tau[j] = AR::div(AR::from_d(2.0), vtv);
+        e[j] = AR::to_d(alpha);
         red[34] = v0;
       }
     }
@@ -302,51 +318,54 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
     const float2 tj = tau[j];
     for (int i = t; i < len; i += nt) vec[i] = (i == 0) ? red[34] : A[(j + 1 + i) * ld + j];
     __syncthreads();
-    if (tj.x != 0.f) {
+    if (AR::lead(tj) != 0.0) {
       // p = tau A v: four threads per row (entries sub, sub+4, ...), combined by shuffles
       for (int i0 = 0; i0 < len; i0 += nt / 4) {
         const int i = i0 + (t >> 2), sub = t & 3;
-        float ph = 0.f, pl = 0.f;
+        typename AR::Acc pa;
+        AR::zero(pa);
         if (i < len) {
           const float2* row = A + (j + 1 + i) * ld + (j + 1);
           int c = 0;
           for (int l = sub; l < len; l += 4) {
-            acc_mac(ph, pl, row[l], vec[l]);
-            if (((++c) & 15) == 0) acc_norm(ph, pl);
+            AR::mac(pa, row[l], vec[l]);
+            if (((++c) & 15) == 0) AR::norm(pa);
           }
         }
-        float2 pr = acc_get(ph, pl);
-        pr = df_add(pr, shfl_xor_df(pr, 1));
-        pr = df_add(pr, shfl_xor_df(pr, 2));
-        if (i < len && sub == 0) pw[i] = df_mul(tj, pr);
+        float2 pr = AR::get(pa);
+        pr = AR::add(pr, shfl_xor_df(pr, 1));
+        pr = AR::add(pr, shfl_xor_df(pr, 2));
+        if (i < len && sub == 0) pw[i] = AR::mul(tj, pr);
       }
       __syncthreads();
-      float kh = 0.f, kl = 0.f;
-      for (int i = t; i < len; i += nt) acc_mac(kh, kl, pw[i], vec[i]);
-      const float2 pv = block_sum_df(acc_get(kh, kl), red);
-      const float2 K = df_mul(df_mul(make_float2(0.5f, 0.f), tj), pv);
-      for (int i = t; i < len; i += nt) pw[i] = df_sub(pw[i], df_mul(K, vec[i]));  // w
+      typename AR::Acc ka;
+      AR::zero(ka);
+      for (int i = t; i < len; i += nt) AR::mac(ka, pw[i], vec[i]);
+      const float2 pv = block_sum<F64>(AR::get(ka), red);
+      const float2 K = AR::mul(AR::mul(AR::from_d(0.5), tj), pv);
+      for (int i = t; i < len; i += nt) pw[i] = AR::sub(pw[i], AR::mul(K, vec[i]));  // w
       __syncthreads();
       // A -= v w^T + w v^T: a warp per row, lanes along the row
       for (int i = warp; i < len; i += nwarp) {
         const float2 vi = vec[i], wi = pw[i];
         float2* arow = A + (j + 1 + i) * ld + (j + 1);
-        for (int l = lane; l < len; l += 32) arow[l] = df_sub(arow[l], df_add(df_mul(vi, pw[l]), df_mul(wi, vec[l])));
+        for (int l = lane; l < len; l += 32)
+          arow[l] = AR::sub(arow[l], AR::add(AR::mul(vi, pw[l]), AR::mul(wi, vec[l])));
       }
     }
     __syncthreads();
     for (int i = t; i < len; i += nt) A[(j + 1 + i) * ld + j] = vec[i];
-    if (t == 0) d[j] = df_to_double(A[j * ld + j]);
+    if (t == 0) d[j] = AR::to_d(A[j * ld + j]);
     __syncthreads();
   }
   if (t == 0) {
     if (m >= 2) {
-      d[m - 2] = df_to_double(A[(m - 2) * ld + (m - 2)]);
-      d[m - 1] = df_to_double(A[(m - 1) * ld + (m - 1)]);
-      e[m - 2] = df_to_double(A[(m - 1) * ld + (m - 2)]);
+      d[m - 2] = AR::to_d(A[(m - 2) * ld + (m - 2)]);
+      d[m - 1] = AR::to_d(A[(m - 1) * ld + (m - 1)]);
+      e[m - 2] = AR::to_d(A[(m - 1) * ld + (m - 2)]);
       tau[m - 2] = make_float2(0.f, 0.f);
     } else {
-      d[0] = df_to_double(A[0]);
+      d[0] = AR::to_d(A[0]);
     }
     if (m >= 1) tau[m - 1] = make_float2(0.f, 0.f);
   }
@@ -481,41 +500,42 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
     nrm = 1.0 / sqrt(nrm);
     for (int i = 0; i < m; ++i) y[i] *= nrm;
     ev[t] = rayleigh_tri<double>(d, e, m, y);
-    for (int i = 0; i < m; ++i) Yd[t * m + i] = df_from_double(y[i]);
+    for (int i = 0; i < m; ++i) Yd[t * m + i] = AR::from_d(y[i]);
   }
   __syncthreads();
-  // ---- 4. back-transform y <- H_0 H_1 ... H_{m-3} y (double-float), warp per vector
+  // ---- 4. back-transform y <- H_0 H_1 ... H_{m-3} y (slot format), warp per vector
   for (int j = m - 3; j >= 0; --j) {
     const float2 tj = tau[j];
-    if (tj.x == 0.f) continue;
+    if (AR::lead(tj) == 0.0) continue;
     const int len = m - j - 1;
     for (int c = warp; c < nev; c += nwarp) {
-      float ph = 0.f, pl = 0.f;
-      for (int i = lane; i < len; i += 32) acc_mac(ph, pl, A[(j + 1 + i) * ld + j], Yd[c * m + j + 1 + i]);
-      const float2 sdot = df_mul(tj, warp_sum_df(acc_get(ph, pl)));
+      typename AR::Acc pa;
+      AR::zero(pa);
+      for (int i = lane; i < len; i += 32) AR::mac(pa, A[(j + 1 + i) * ld + j], Yd[c * m + j + 1 + i]);
+      const float2 sdot = AR::mul(tj, warp_sum<F64>(AR::get(pa)));
       for (int i = lane; i < len; i += 32)
-        Yd[c * m + j + 1 + i] = df_sub(Yd[c * m + j + 1 + i], df_mul(sdot, A[(j + 1 + i) * ld + j]));
+        Yd[c * m + j + 1 + i] = AR::sub(Yd[c * m + j + 1 + i], AR::mul(sdot, A[(j + 1 + i) * ld + j]));
     }
     __syncthreads();
   }
   for (int x = t; x < m * nev; x += nt) {
     const int i = x / nev, c = x % nev;
-    V[i * ldv + c] = df_to_double(Yd[c * m + i]);
+    V[i * ldv + c] = AR::to_d(Yd[c * m + i]);
   }
   if (t < nev) theta[t] = ev[t];
 }
 
-__global__ void k_to_df(const double* __restrict__ x, float2* __restrict__ y, int count, double scale) {
+__global__ void k_to_df(const double* __restrict__ x, float2* __restrict__ y, int count, double scale, bool f64) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) y[i] = df_from_double(scale * x[i]);
+  if (i < count) y[i] = slot_put(scale * x[i], f64);
 }
 
 }  // namespace
 
 cudaError_t chol_rinv(const double* G, int ldg, int kk, int kp, double shift_rel, double* R, float2* Rinv_df,
-                      int* status, cudaStream_t s) {
+                      int* status, bool f64, cudaStream_t s) {
   if (kk < 1 || kk > 16 || kp > 16) return cudaErrorInvalidValue;
-  k_chol_rinv<<<1, 32, 0, s>>>(G, ldg, kk, kp, shift_rel, R, Rinv_df, status); count_launch();
+  k_chol_rinv<<<1, 32, 0, s>>>(G, ldg, kk, kp, shift_rel, R, Rinv_df, status, f64); count_launch();
   return cudaGetLastError();
 }
 
@@ -526,23 +546,31 @@ static size_t syev_smem(int m) {
   return f2 * sizeof(float2) + db * sizeof(double) + fl * sizeof(float) + kMaxNev * sizeof(int) + 256;
 }
 
-cudaError_t syev_lowest(const double* S, int lds, int m, int nev, double* theta, double* V, int ldv,
+cudaError_t syev_lowest(const double* S, int lds, int m, int nev, double* theta, double* V, int ldv, bool f64,
                         cudaStream_t s) {
   if (m < 1 || m > kMaxM || nev < 1 || nev > kMaxNev || nev > m) return cudaErrorInvalidValue;
   const size_t smem = syev_smem(m);
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(k_syev_lowest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syev_smem(kMaxM));
+  static const cudaError_t attr = [] {
+    cudaError_t e = cudaFuncSetAttribute(k_syev_lowest<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)syev_smem(kMaxM));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_syev_lowest<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)syev_smem(kMaxM));
+    return e;
+  }();
   if (attr != cudaSuccess) return attr;
-  k_syev_lowest<<<1, 512, smem, s>>>(S, lds, m, nev, theta, V, ldv); count_launch();
+  if (f64)
+    k_syev_lowest<true><<<1, 512, smem, s>>>(S, lds, m, nev, theta, V, ldv);
+  else
+    k_syev_lowest<false><<<1, 512, smem, s>>>(S, lds, m, nev, theta, V, ldv);
+  count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t to_df(const double* x, float2* y, int count, double scale, cudaStream_t s) {
+cudaError_t to_df(const double* x, float2* y, int count, double scale, bool f64, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_to_df<<<(count + 255) / 256, 256, 0, s>>>(x, y, count, scale); count_launch();
+  k_to_df<<<(count + 255) / 256, 256, 0, s>>>(x, y, count, scale, f64); count_launch();
   return cudaGetLastError();
 }
-
-cudaError_t negate_to_df(const double* x, float2* y, int count, cudaStream_t s) { return to_df(x, y, count, -1.0, s); }
 
 }  // namespace sppc

@@ -1,4 +1,5 @@
-// SpMM Y = H X over the level-blocked SELL-16 layout, double-float arithmetic.
+// SpMM Y = H X over the level-blocked SELL-16 layout, in double-float or native
+// FP64 arithmetic (the matrix's slot format, val.cuh).
 //
 // The product with H is the dominant cost of SPPC: k SpMVs per order (paper
 // Sec. 4.2-4.3), plus the products with the leading block H0_hat inside the
@@ -23,10 +24,11 @@ namespace {
 // epilogue writes, accumulates (column tiles) or finishes Y.
 // Seven resident CTAs per SM (<= 73 registers): measured fastest for the
 // 8-column instance (a 64-register cap spills and is 6% slower).
-template <int KP, bool EPI>
+template <int KP, bool EPI, bool F64>
 __global__ void __launch_bounds__(128, 7) k_spmm_sell(SellDev A, int64_t s0, int64_t s1, int q,
                                                    const float2* __restrict__ X, float2* __restrict__ Y, Epi epi) {
   static_assert(KP % 2 == 0 && KP <= 8, "kp must be 2, 4, 6 or 8");
+  using V = Ar<F64>;
   constexpr int CPL = KP / 2;
   const int lane = threadIdx.x & 31;
   const int rl = lane >> 1;
@@ -36,8 +38,8 @@ __global__ void __launch_bounds__(128, 7) k_spmm_sell(SellDev A, int64_t s0, int
   const uint64_t pol = policy_keep();
   for (int64_t s = s0 + gw; s < s1; s += nw) {
     const int row = A.slice_rows[s * kSliceH + rl];
-    float ah[CPL], al[CPL];
-    slice_rowsum<KP>(A, s, rl, off, X, pol, ah, al);
+    float2 sum[CPL];
+    slice_rowsum<KP, F64>(A, s, rl, off, X, pol, sum);
     if (row < 0) continue;
     const int64_t base = static_cast<int64_t>(row) * KP + off;
     // the first chunk of a row writes, later chunks accumulate, the last applies the epilogue
@@ -45,12 +47,12 @@ __global__ void __launch_bounds__(128, 7) k_spmm_sell(SellDev A, int64_t s0, int
     const bool last = !EPI || (A.nchunks == 1) || (A.row_last[row] == q);
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
-      float2 r = acc_get(ah[c], al[c]);
-      if (!first) r = df_add(r, Y[base + c]);
+      float2 r = sum[c];
+      if (!first) r = V::add(r, Y[base + c]);
       if (EPI && last) {
-        if (epi.alpha) r = df_mul(epi.alpha[off + c], r);
-        if (epi.beta) r = df_add(r, df_mul(epi.beta[off + c], X[base + c]));
-        if (epi.gamma) r = df_add(r, df_mul(epi.gamma[off + c], epi.Z[base + c]));
+        if (epi.alpha) r = V::mul(epi.alpha[off + c], r);
+        if (epi.beta) r = V::add(r, V::mul(epi.beta[off + c], X[base + c]));
+        if (epi.gamma) r = V::add(r, V::mul(epi.gamma[off + c], epi.Z[base + c]));
       }
       Y[base + c] = r;
     }
@@ -64,9 +66,10 @@ __global__ void __launch_bounds__(128, 7) k_spmm_sell(SellDev A, int64_t s0, int
 // walks a whole slice row (about m / 2 of them), which sets the time of a
 // product over a few thousand rows.  The segment sums combine by shuffles in a
 // fixed order; lane (half, seg) then owns element (row, half * KP/2 + seg).
-template <int KP, bool EPI>
+template <int KP, bool EPI, bool F64>
 __global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __restrict__ X, float2* __restrict__ Y,
                                                   Epi epi) {
+  using V = Ar<F64>;
   constexpr int CPL = KP / 2;
   constexpr int NP = CPL / 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -75,10 +78,11 @@ __global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __rest
   const int64_t row = (static_cast<int64_t>(blockIdx.x) * 4 + warp) * 4 + rq;
   const bool valid = row < A.nrows;
   const uint64_t pol = policy_keep();
-  float2 ph[NP > 0 ? NP : 1], pl[NP > 0 ? NP : 1];
+  typename V::Acc2 pa[NP > 0 ? NP : 1];
 #pragma unroll
-  for (int c = 0; c < NP; ++c) ph[c] = pl[c] = make_float2(0.f, 0.f);
-  float oh = 0.f, ol = 0.f;  // odd last column
+  for (int c = 0; c < NP; ++c) V::zero(pa[c]);
+  typename V::Acc oa;  // odd last column
+  V::zero(oa);
   if (valid) {
     const int64_t rb = __ldg(A.rowptr + row), re = __ldg(A.rowptr + row + 1);
     for (int64_t e = rb + seg; e < re; e += 16) {
@@ -103,15 +107,12 @@ __global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __rest
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) acc_mac2(ph[c], pl[c], vv[u], xx[u][2 * c], xx[u][2 * c + 1]);
-        if constexpr (CPL % 2 == 1) acc_mac(oh, ol, vv[u], xx[u][CPL - 1]);
+        for (int c = 0; c < NP; ++c) V::mac2(pa[c], vv[u], xx[u][2 * c], xx[u][2 * c + 1]);
+        if constexpr (CPL % 2 == 1) V::mac(oa, vv[u], xx[u][CPL - 1]);
       }
 #pragma unroll
-      for (int c = 0; c < NP; ++c) {
-        acc_norm(ph[c].x, pl[c].x);
-        acc_norm(ph[c].y, pl[c].y);
-      }
-      if constexpr (CPL % 2 == 1) acc_norm(oh, ol);
+      for (int c = 0; c < NP; ++c) V::norm(pa[c]);
+      if constexpr (CPL % 2 == 1) V::norm(oa);
     }
   }
   float2 out[CPL];
@@ -119,11 +120,11 @@ __global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __rest
   for (int c = 0; c < CPL; ++c) {
     float2 v;
     if (c < 2 * NP)
-      v = (c & 1) ? acc_get(ph[c / 2].y, pl[c / 2].y) : acc_get(ph[c / 2].x, pl[c / 2].x);
+      v = (c & 1) ? V::get1(pa[c / 2]) : V::get0(pa[c / 2]);
     else
-      v = acc_get(oh, ol);
-    v = df_add(v, shfl_xor_df(v, 1));
-    v = df_add(v, shfl_xor_df(v, 2));
+      v = V::get(oa);
+    v = V::add(v, shfl_xor_df(v, 1));
+    v = V::add(v, shfl_xor_df(v, 2));
     out[c] = v;
   }
   if (!valid || seg >= CPL) return;
@@ -134,14 +135,38 @@ __global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __rest
   const int64_t b = row * KP + off + seg;
   if (EPI) {
     const int j = off + seg;
-    if (epi.alpha) r = df_mul(epi.alpha[j], r);
-    if (epi.beta) r = df_add(r, df_mul(epi.beta[j], X[b]));
-    if (epi.gamma) r = df_add(r, df_mul(epi.gamma[j], epi.Z[b]));
+    if (epi.alpha) r = V::mul(epi.alpha[j], r);
+    if (epi.beta) r = V::add(r, V::mul(epi.beta[j], X[b]));
+    if (epi.gamma) r = V::add(r, V::mul(epi.gamma[j], epi.Z[b]));
   }
   Y[b] = r;
 }
 
 std::atomic<long long> g_launches{0};
+
+// Calls f.template operator()<KP, EPI, F64>() for the run-time column count,
+// epilogue and value format.
+template <class F>
+cudaError_t dispatch_spmm(int kp, bool epi, bool f64, F&& f) {
+  auto fmt = [&]<int KP, bool EPI>() {
+    if (f64)
+      f.template operator()<KP, EPI, true>();
+    else
+      f.template operator()<KP, EPI, false>();
+  };
+  switch (kp * 2 + (epi ? 1 : 0)) {
+    case 4: fmt.template operator()<2, false>(); break;
+    case 5: fmt.template operator()<2, true>(); break;
+    case 8: fmt.template operator()<4, false>(); break;
+    case 9: fmt.template operator()<4, true>(); break;
+    case 12: fmt.template operator()<6, false>(); break;
+    case 13: fmt.template operator()<6, true>(); break;
+    case 16: fmt.template operator()<8, false>(); break;
+    case 17: fmt.template operator()<8, true>(); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -154,7 +179,7 @@ int spmm_default_grid() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell<8, false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_sell<8, false, false>, 128, 0);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
   }();
@@ -163,7 +188,7 @@ int spmm_default_grid() {
 
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s) {
   if (A.nslices == 0) return cudaSuccess;
-  if (kp == 8 && A.tma) return spmm_tma8(A, X, Y, epi, s);
+  if (kp == 8 && A.tma && !A.f64) return spmm_tma8(A, X, Y, epi, s);
   const int64_t gmax = spmm_default_grid();
   for (int q = 0; q < A.nchunks; ++q) {
     const int64_t s0 = A.nchunks == 1 ? 0 : A.chunk_slice[q];
@@ -173,17 +198,10 @@ cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi
     if (grid > gmax) grid = gmax;
     const bool has_epi = epi.alpha || epi.beta || epi.gamma;
     const unsigned g = (unsigned)grid;
-    switch (kp * 2 + (has_epi ? 1 : 0)) {
-      case 4: k_spmm_sell<2, false><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
-      case 5: k_spmm_sell<2, true><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
-      case 8: k_spmm_sell<4, false><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
-      case 9: k_spmm_sell<4, true><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
-      case 12: k_spmm_sell<6, false><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
-      case 13: k_spmm_sell<6, true><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
-      case 16: k_spmm_sell<8, false><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
-      case 17: k_spmm_sell<8, true><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi); break;
-      default: return cudaErrorInvalidValue;
-    }
+    const cudaError_t e0 = dispatch_spmm(kp, has_epi, A.f64, [&]<int KP, bool EPI, bool F>() {
+      k_spmm_sell<KP, EPI, F><<<g, 128, 0, s>>>(A, s0, s1, q, X, Y, epi);
+    });
+    if (e0 != cudaSuccess) return e0;
     count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -195,17 +213,10 @@ cudaError_t spmm_csr(const CsrDev& A, int kp, const float2* X, float2* Y, const 
   if (A.nrows == 0) return cudaSuccess;
   const unsigned g = static_cast<unsigned>((A.nrows + 15) / 16);
   const bool has_epi = epi.alpha || epi.beta || epi.gamma;
-  switch (kp * 2 + (has_epi ? 1 : 0)) {
-    case 4: k_spmm_csr<2, false><<<g, 128, 0, s>>>(A, X, Y, epi); break;
-    case 5: k_spmm_csr<2, true><<<g, 128, 0, s>>>(A, X, Y, epi); break;
-    case 8: k_spmm_csr<4, false><<<g, 128, 0, s>>>(A, X, Y, epi); break;
-    case 9: k_spmm_csr<4, true><<<g, 128, 0, s>>>(A, X, Y, epi); break;
-    case 12: k_spmm_csr<6, false><<<g, 128, 0, s>>>(A, X, Y, epi); break;
-    case 13: k_spmm_csr<6, true><<<g, 128, 0, s>>>(A, X, Y, epi); break;
-    case 16: k_spmm_csr<8, false><<<g, 128, 0, s>>>(A, X, Y, epi); break;
-    case 17: k_spmm_csr<8, true><<<g, 128, 0, s>>>(A, X, Y, epi); break;
-    default: return cudaErrorInvalidValue;
-  }
+  const cudaError_t e0 = dispatch_spmm(kp, has_epi, A.f64, [&]<int KP, bool EPI, bool F>() {
+    k_spmm_csr<KP, EPI, F><<<g, 128, 0, s>>>(A, X, Y, epi);
+  });
+  if (e0 != cudaSuccess) return e0;
   count_launch();
   return cudaGetLastError();
 }

@@ -45,12 +45,12 @@ __global__ void __launch_bounds__(128, 7) k_spmm_batch(const BatchItem* __restri
       const BatchItem& it = items[lo];
       const int64_t s = g - sp[lo];
       const int row = it.A.slice_rows[s * kSliceH + rl];
-      float ah[CPL], al[CPL];
-      slice_rowsum<KP>(it.A, s, rl, off, it.X, pol, ah, al);
+      float2 sum[CPL];
+      slice_rowsum<KP, false>(it.A, s, rl, off, it.X, pol, sum);
       if (row < 0) continue;
       const int64_t b = static_cast<int64_t>(row) * KP + off;
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) it.Y[b + c] = acc_get(ah[c], al[c]);
+      for (int c = 0; c < CPL; ++c) it.Y[b + c] = sum[c];
     }
   }
 }

@@ -16,9 +16,10 @@
 //
 // Every lane pair accumulates its row exactly as the register-gather kernel does
 // (same entry order, same renormalisation cadence), so the two give identical
-// bits.  mbarrier waits are bounded (about a second of clock); on time-out the
-// kernel raises a device flag, waits (bounded) for its own copies in flight and
-// returns.
+// bits.  mbarrier waits are bounded (about a second of clock, or A.spin_limit - 1
+// non-blocking polls when that is set); on time-out the kernel raises the
+// handle's flag, waits (bounded by the clock) for its own copies in flight and
+// returns.  The decision to give up is taken by the whole warp at once.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -36,8 +37,6 @@ constexpr int kStageBytes = 1280;  // 1024 B of X rows + 128 B values + 64 B col
 constexpr int kValOff = 1024;
 constexpr int kColOff = 1152;
 constexpr int kStageTx = 1024 + 128;
-
-__device__ int g_tma_timeout = 0;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -65,6 +64,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete; false after ~2^31 clocks.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   if (mbar_try(bar, parity)) return true;
@@ -73,6 +87,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (clock64() - t0 > (1ll << 31)) return false;
   }
   return true;
+}
+
+// The pipeline's wait: with cap > 0 at most cap - 1 non-blocking tests (cap = 1
+// gives up at the first wait, which makes the time-out path testable), else
+// mbar_wait; the warp gives up together if any lane did.
+__device__ __forceinline__ bool mbar_wait_capped(uint32_t bar, uint32_t parity, unsigned cap) {
+  bool done;
+  if (cap > 0) {
+    done = false;
+    for (unsigned i = 1; i < cap && !done; ++i) done = mbar_test(bar, parity);
+  } else {
+    done = mbar_wait(bar, parity);
+  }
+  return __all_sync(0xffffffffu, done) != 0;
 }
 
 // Four rows (rows.x .. rows.w) of the 2-D tensor map, columns from x, into dst.
@@ -180,7 +208,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma8(SellDev A, const _
     int cnt = 0;
     for (int64_t e = sp[s]; e < end; e += H) {
       const int j = static_cast<int>(used % D);
-      if (!mbar_wait(bar_s + 8 * j, (used / D) & 1u)) {
+      if (!mbar_wait_capped(bar_s + 8 * j, (used / D) & 1u, A.spin_limit)) {
         ok = false;
         break;
       }
@@ -230,7 +258,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma8(SellDev A, const _
     }
   }
   if (!ok) {
-    if (lane == 0) atomicExch(&g_tma_timeout, 1);
+    if (lane == 0 && A.tma_flag) atomicExch(A.tma_flag, 1);
     // copies still in flight target this warp's ring: wait for them (bounded)
     for (uint32_t u = used; u < issued; ++u) mbar_wait(bar_s + 8 * (u % D), (u / D) & 1u);
   }
@@ -252,8 +280,10 @@ bool spmm_tma_available() {
   return g_encode != nullptr;
 }
 
-cudaError_t spmm_tma_read_timeout(int* flag, cudaStream_t s) {
-  return cudaMemcpyFromSymbolAsync(flag, g_tma_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+cudaError_t spmm_tma_read_timeout(const SellDev& A, int* flag, cudaStream_t s) {
+  *flag = 0;
+  if (!A.tma_flag) return cudaSuccess;
+  return cudaMemcpyAsync(flag, A.tma_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
 cudaError_t spmm_tma8(const SellDev& A, const float2* X, float2* Y, const Epi& epi, cudaStream_t s) {

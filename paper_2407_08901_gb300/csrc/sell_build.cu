@@ -15,7 +15,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "df.cuh"
+#include "val.cuh"
 #include "sppc_internal.h"
 
 namespace sppc {
@@ -211,10 +211,26 @@ __global__ void k_slices(int64_t nslices, const Part* __restrict__ parts, int np
 }
 
 // ---- 5. entries: a half-warp per slice, lane l = slice row l
+// The value the matrix holds under opts.precision: 0 as given, 1 rounded to
+// FP32, 2 rounded to FP32 and then, off the diagonal, to BF16 (nearest, ties to
+// even) - the same rounding sppc_create applies to a host CSR.
+__device__ __forceinline__ double round_value(double v, bool diag, int mode) {
+  if (mode == 0) return v;
+  float f = __double2float_rn(v);
+  if (mode == 2 && !diag) {
+    uint32_t u = __float_as_uint(f);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    f = __uint_as_float(u);
+  }
+  return static_cast<double>(f);
+}
+
 __global__ void k_fill(int64_t nslices, const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ slice_rows,
                        const int32_t* __restrict__ slice_q, const int64_t* __restrict__ rp,
                        const int32_t* __restrict__ ci, const double* __restrict__ va, const int32_t* __restrict__ off,
-                       int nch, int64_t C, int64_t ncols, int32_t* __restrict__ col, float2* __restrict__ val) {
+                       int nch, int64_t C, int64_t ncols, int32_t* __restrict__ col, float2* __restrict__ val,
+                       bool f64, int round_mode) {
   const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t s = g / kSliceH;
   const int l = static_cast<int>(g % kSliceH);
@@ -234,7 +250,7 @@ __global__ void k_fill(int64_t nslices, const int64_t* __restrict__ slice_ptr, c
     const int64_t idx = base + kSliceH * t + l;
     if (t < len) {
       col[idx] = ci[src + t];
-      val[idx] = df_from_double(va[src + t]);
+      val[idx] = slot_put(round_value(va[src + t], ci[src + t] == r, round_mode), f64);
     } else {
       col[idx] = pad;
       val[idx] = make_float2(0.f, 0.f);
@@ -245,8 +261,8 @@ __global__ void k_fill(int64_t nslices, const int64_t* __restrict__ slice_ptr, c
 }  // namespace
 
 cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t ncols,
-                              const std::vector<int64_t>& seg, int64_t chunk_cols, cudaStream_t s,
-                              const DeviceAlloc& alloc, SellDeviceLayout& out) {
+                              const std::vector<int64_t>& seg, int64_t chunk_cols, bool f64, int round_mode,
+                              cudaStream_t s, const DeviceAlloc& alloc, SellDeviceLayout& out) {
   const int64_t C = (chunk_cols > 0 && chunk_cols < ncols) ? chunk_cols : ncols;
   const int nch = static_cast<int>((ncols + C - 1) / C);
   out.nchunks = nch;
@@ -376,7 +392,7 @@ cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* c
   if (e == cudaSuccess && ns > 0) {
     const int64_t threads = ns * kSliceH;
     k_fill<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(ns, slice_ptr, slice_rows, slice_q, rp, ci, va,
-                                                                         off, nch, C, ncols, col, val);
+                                                                         off, nch, C, ncols, col, val, f64, round_mode);
     count_launch();
     chk(cudaGetLastError());
   }
@@ -406,6 +422,101 @@ cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* c
   out.first_d = first;
   out.last_d = last;
   return cudaStreamSynchronize(s);
+}
+
+// ---- checks and extracts on a CSR that stays on the device
+
+namespace {
+
+// flags |= 2 (column out of range), 4 (columns not strictly increasing), 8 (NaN/Inf)
+__global__ void k_csr_validate(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ va, int* flags) {
+  int bad = 0;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t b = rp[r], e = rp[r + 1];
+    for (int64_t t = b; t < e; ++t) {
+      const int32_t c = ci[t];
+      if (c < 0 || c >= n) bad |= 2;
+      if (t > b && c <= ci[t - 1]) bad |= 4;
+      if (!isfinite(va[t])) bad |= 8;
+    }
+  }
+  if (bad) atomicOr(flags, bad);
+}
+
+// flags |= 1 when some stored (r, c, v) has no (c, r, v) with the same bits
+__global__ void k_csr_symmetry(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ va, int* flags) {
+  int bad = 0;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t t = rp[r]; t < rp[r + 1]; ++t) {
+      const int32_t c = ci[t];
+      int64_t lo = rp[c], hi = rp[c + 1];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ci[mid] < r) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= rp[c + 1] || ci[lo] != r || __double_as_longlong(va[lo]) != __double_as_longlong(va[t])) bad = 1;
+    }
+  }
+  if (bad) atomicOr(flags, bad);
+}
+
+// diag[r] = H_rr (rounded as round_mode says) as a value slot, 0 if not stored
+__global__ void k_csr_diag(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ va, int round_mode, bool f64, float2* __restrict__ diag) {
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t lo = rp[r], hi = rp[r + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ci[mid] < r) lo = mid + 1;
+      else hi = mid;
+    }
+    const bool has = lo < rp[r + 1] && ci[lo] == r;
+    diag[r] = has ? slot_put(round_value(va[lo], true, round_mode), f64) : make_float2(0.f, 0.f);
+  }
+}
+
+unsigned grid_for(int64_t n) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t g = (n + 255) / 256;
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(g, static_cast<int64_t>(sms > 0 ? sms : 1) * 32)));
+}
+
+}  // namespace
+
+cudaError_t csr_check_device(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, bool symmetry,
+                             int* flags_host, cudaStream_t s) {
+  int* flags = nullptr;
+  cudaError_t e = cudaMallocAsync(&flags, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_csr_validate<<<grid_for(n), 256, 0, s>>>(n, rp, ci, va, flags);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && symmetry) {
+    k_csr_symmetry<<<grid_for(n), 256, 0, s>>>(n, rp, ci, va, flags);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flags_host, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (flags) cudaFreeAsync(flags, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+cudaError_t csr_diag_device(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, int round_mode,
+                            bool f64, float2* diag, cudaStream_t s) {
+  k_csr_diag<<<grid_for(n), 256, 0, s>>>(n, rp, ci, va, round_mode, f64, diag);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace sppc

@@ -1,8 +1,8 @@
 // Per-slice row sums of the SELL-16 SpMM, shared by the SpMM kernel and the
 // persistent MINRES kernel.
 #pragma once
-#include "df.cuh"
 #include "sppc_internal.h"
+#include "val.cuh"
 
 namespace sppc {
 
@@ -60,25 +60,26 @@ __device__ __forceinline__ float2 ld_stream(const float2* p) {
 }
 
 // Row sums of slice s: lane pair (2*r, 2*r+1) owns row r of the slice, lane h
-// of the pair accumulates columns [h*kp/2, (h+1)*kp/2) into (ah, al).  Software
-// pipeline of depth 2 per lane: the X half rows of entries t+1 and t+2 are in
-// flight while entry t is accumulated; the loop is unrolled by three so the
-// three buffers rotate without register copies.  Entries are accumulated in
-// order and renormalised after every 16th, whatever the unrolling; column pairs
-// use the packed form (acc_mac2), an odd last column the scalar one.
-template <int KP>
+// of the pair accumulates columns [h*kp/2, (h+1)*kp/2) and returns them in out.
+// Software pipeline of depth 2 per lane: the X half rows of entries t+1 and t+2
+// are in flight while entry t is accumulated; the loop is unrolled by three so
+// the three buffers rotate without register copies.  Entries are accumulated in
+// order (double-float: renormalised after every 16th, whatever the unrolling);
+// column pairs use the packed form (mac2), an odd last column the scalar one.
+template <int KP, bool F64>
 __device__ __forceinline__ void slice_rowsum(const SellDev& A, int64_t s, int rl, int off,
-                                             const float2* __restrict__ X, uint64_t pol, float (&ah)[KP / 2],
-                                             float (&al)[KP / 2]) {
+                                             const float2* __restrict__ X, uint64_t pol, float2 (&out)[KP / 2]) {
+  using V = Ar<F64>;
   constexpr int CPL = KP / 2;
   constexpr int NP = CPL / 2;  // column pairs
   constexpr int H = kSliceH;
   const int64_t end = A.slice_ptr[s + 1];
   int64_t e = A.slice_ptr[s] + rl;
-  float2 ph[NP > 0 ? NP : 1], pl[NP > 0 ? NP : 1];
+  typename V::Acc2 pa[NP > 0 ? NP : 1];
 #pragma unroll
-  for (int c = 0; c < NP; ++c) ph[c] = pl[c] = make_float2(0.f, 0.f);
-  float oh = 0.f, ol = 0.f;  // odd last column
+  for (int c = 0; c < NP; ++c) V::zero(pa[c]);
+  typename V::Acc oa;  // odd last column
+  V::zero(oa);
   float2 x0[CPL], x1[CPL], x2[CPL];
   float2 v0 = make_float2(0.f, 0.f), v1 = v0, v2 = v0;
   auto fetch = [&](int64_t ee, float2 (&x)[CPL], float2& v) {
@@ -91,15 +92,12 @@ __device__ __forceinline__ void slice_rowsum(const SellDev& A, int64_t s, int rl
   int cnt = 0;
   auto mac = [&](const float2 (&x)[CPL], float2 v) {
 #pragma unroll
-    for (int c = 0; c < NP; ++c) acc_mac2(ph[c], pl[c], v, x[2 * c], x[2 * c + 1]);
-    if constexpr (CPL % 2 == 1) acc_mac(oh, ol, v, x[CPL - 1]);
-    if (((++cnt) & 15) == 0) {
+    for (int c = 0; c < NP; ++c) V::mac2(pa[c], v, x[2 * c], x[2 * c + 1]);
+    if constexpr (CPL % 2 == 1) V::mac(oa, v, x[CPL - 1]);
+    if (!F64 && ((++cnt) & 15) == 0) {
 #pragma unroll
-      for (int c = 0; c < NP; ++c) {
-        acc_norm(ph[c].x, pl[c].x);
-        acc_norm(ph[c].y, pl[c].y);
-      }
-      if constexpr (CPL % 2 == 1) acc_norm(oh, ol);
+      for (int c = 0; c < NP; ++c) V::norm(pa[c]);
+      if constexpr (CPL % 2 == 1) V::norm(oa);
     }
   };
   fetch(e, x0, v0);
@@ -116,15 +114,10 @@ __device__ __forceinline__ void slice_rowsum(const SellDev& A, int64_t s, int rl
   }
 #pragma unroll
   for (int c = 0; c < NP; ++c) {
-    ah[2 * c] = ph[c].x;
-    al[2 * c] = pl[c].x;
-    ah[2 * c + 1] = ph[c].y;
-    al[2 * c + 1] = pl[c].y;
+    out[2 * c] = V::get0(pa[c]);
+    out[2 * c + 1] = V::get1(pa[c]);
   }
-  if constexpr (CPL % 2 == 1) {
-    ah[CPL - 1] = oh;
-    al[CPL - 1] = ol;
-  }
+  if constexpr (CPL % 2 == 1) out[CPL - 1] = V::get(oa);
 }
 
 }  // namespace sppc

@@ -35,7 +35,10 @@ struct SellDev {
   const float2* val = nullptr;  // double-float values
   const uint8_t* row_first = nullptr;
   const uint8_t* row_last = nullptr;
-  int tma = 0;  // 1: 8-column products use the TMA-gather kernel (k_spmm_tma.cu)
+  bool f64 = false;  // value format of val and of the vectors it multiplies: IEEE double (true) or double-float
+  int tma = 0;  // 1: 8-column products use the TMA-gather kernel (k_spmm_tma.cu; double-float only)
+  int* tma_flag = nullptr;  // device word the TMA kernel sets when an mbarrier wait gives up
+  unsigned spin_limit = 0;  // TMA kernel: polls before a wait gives up (0 = about a second of clock)
 };
 
 // CSR matrix on the device with double-float values (rowptr has nrows + 1
@@ -45,6 +48,7 @@ struct CsrDev {
   const int64_t* rowptr = nullptr;
   const int32_t* col = nullptr;
   const float2* val = nullptr;
+  bool f64 = false;  // value format (see SellDev)
 };
 
 // SpMM epilogue: Y[r][c] = alpha[c] * (A X)[r][c] + beta[c] * X[r][c] + gamma[c] * Z[r][c].
@@ -64,7 +68,8 @@ struct BlockList {
 };
 
 // ---- sell_build.cu: the SELL-16 layout of H built on the GPU from its CSR on the
-// device (rp, ci, va), bit-identical to the host builder.  Persistent arrays come
+// device (rp, ci, va), bit-identical to the host builder; values stored as slots
+// of the given format (f64: IEEE double bits, else double-float pairs).  Persistent arrays come
 // from `alloc` (bytes); temporaries are stream-ordered allocations freed before
 // return.  Synchronises the stream.
 using DeviceAlloc = std::function<cudaError_t(void**, size_t)>;
@@ -80,9 +85,19 @@ struct SellDeviceLayout {
   uint8_t* first_d = nullptr;
   uint8_t* last_d = nullptr;
 };
+// round_mode: the values as opts.precision stores them (0 as given, 1 FP32,
+// 2 FP32 diagonal and BF16 off-diagonal entries).
 cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t ncols,
-                              const std::vector<int64_t>& seg, int64_t chunk_cols, cudaStream_t s,
-                              const DeviceAlloc& alloc, SellDeviceLayout& out);
+                              const std::vector<int64_t>& seg, int64_t chunk_cols, bool f64, int round_mode,
+                              cudaStream_t s, const DeviceAlloc& alloc, SellDeviceLayout& out);
+// Checks of a CSR that stays on the device: *flags_host gets 2 (column out of
+// range), 4 (columns not strictly increasing), 8 (NaN/Inf) and, with symmetry,
+// 1 (H != H^T bit for bit).  Synchronises the stream.
+cudaError_t csr_check_device(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, bool symmetry,
+                             int* flags_host, cudaStream_t s);
+// diag[r] = H_rr of a device CSR (0 when not stored), rounded per round_mode, as a slot
+cudaError_t csr_diag_device(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, int round_mode,
+                            bool f64, float2* diag, cudaStream_t s);
 
 // ---- k_spmm.cu
 cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
@@ -159,25 +174,25 @@ cudaError_t standardize(const float* F, int64_t count, const float* mu, const fl
 // ---- k_spmm_tma.cu (kp = 8; X 16-byte aligned)
 bool spmm_tma_available();
 cudaError_t spmm_tma8(const SellDev& A, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
-// Copies the kernel's sticky time-out flag (nonzero after an mbarrier wait gave
-// up) to host memory; valid after the stream synchronises.
-cudaError_t spmm_tma_read_timeout(int* flag, cudaStream_t s);
+// Copies A's time-out flag (nonzero after an mbarrier wait of the TMA kernel gave
+// up) to host memory, valid after the stream synchronises (0 without a flag).
+cudaError_t spmm_tma_read_timeout(const SellDev& A, int* flag, cudaStream_t s);
 
 // ---- k_dense.cu
 // Gram: out[(a*kp+i)*kp + j] = sum_{r in [r0,r1)} A_a[r][i] * B[r][j]  (FP64 out)
 cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_t r1, double* out,
-                 float2* partials, int64_t partial_cap, cudaStream_t s);
+                 float2* partials, int64_t partial_cap, bool f64, cudaStream_t s);
 // Update: Y[r][j] = alpha[j] X[r][j] + sum_a sum_i A_a[r][i] coef[(a*kp+i)*kp + j]
 // (coef double-float on device; X may be null; Y may alias X but no block of A).
 cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef,
-                   int kp, int64_t r0, int64_t r1, cudaStream_t s);
+                   int kp, int64_t r0, int64_t r1, bool f64, cudaStream_t s);
 // Diagonal combine: Y[r][j] = alpha[j] X[r][j] + sum_b coef[b*8 + j] A_b[r][j]
 // (coefficients of block b at stride 8 whatever kp is)
 cudaError_t combine_diag(float2* Y, const float2* X, const float2* alpha, const BlockList& A,
-                         const float2* coef, int kp, int64_t r0, int64_t r1, cudaStream_t s);
+                         const float2* coef, int kp, int64_t r0, int64_t r1, bool f64, cudaStream_t s);
 // Column dots: out[q*kp + j] = sum_r A_q[r][j] * B_q[r][j], q < nq <= 4 (FP64 out)
 cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int kp, int64_t r0, int64_t r1,
-                    double* out, float2* partials, int64_t partial_cap, cudaStream_t s);
+                    double* out, float2* partials, int64_t partial_cap, bool f64, cudaStream_t s);
 // Ritz residual: for every row, z = sum_a Q_a[r] Y_a, hz = sum_a W_a[r] Y_a (Y: (na*kp) x kp
 // double-float), accumulate (hz - theta*z)^2 per column -> out[j] (FP64); optionally
 // write z (FP64, leading dim ldz, first ncols columns) to Zout; optionally write
@@ -187,11 +202,13 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
 // nlead x kp) to Zlead and Rlead.
 cudaError_t ritz_resid(const BlockList& Q, const BlockList& Wb, const float2* Y, const float2* theta, int kp,
                        int64_t n, double* out, float2* partials, int64_t partial_cap, double* Zout, int64_t ldz,
-                       int ncols, float2* Tout, const float2* diag, float clamp, cudaStream_t s,
+                       int ncols, float2* Tout, const float2* diag, float clamp, bool f64, cudaStream_t s,
                        float2* Zlead = nullptr, float2* Rlead = nullptr, int64_t nlead = 0);
-cudaError_t f64_to_df(const double* X, int64_t ldx, int ncols, float2* Y, int kp, int64_t r0, int64_t r1,
+// FP64 (leading dimension ldx, ncols columns) <-> value slots (kp columns, padding
+// columns written as 0); f64 selects the slot format (val.cuh)
+cudaError_t f64_to_df(const double* X, int64_t ldx, int ncols, float2* Y, int kp, int64_t r0, int64_t r1, bool f64,
                       cudaStream_t s);
-cudaError_t df_to_f64(const float2* X, int kp, double* Y, int64_t ldy, int ncols, int64_t r0, int64_t r1,
+cudaError_t df_to_f64(const float2* X, int kp, double* Y, int64_t ldy, int ncols, int64_t r0, int64_t r1, bool f64,
                       cudaStream_t s);
 cudaError_t fill_zero(float2* Y, int64_t count, cudaStream_t s);
 
@@ -208,13 +225,13 @@ cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE
 // writes R (upper, kk x kk, ld kp, FP64), Rinv as double-float coefficient matrix
 // (kp x kp, identity on padding), and status[0] = 0 ok / j+1 breakdown at pivot j.
 cudaError_t chol_rinv(const double* G, int ldg, int kk, int kp, double shift_rel, double* R, float2* Rinv_df,
-                      int* status, cudaStream_t s);
+                      int* status, bool f64, cudaStream_t s);
 // Symmetric eigensolve: S (m x m, ld lds), nev lowest eigenpairs -> theta[nev],
 // V (m x nev, ld ldv) FP64; ascending.  m <= 160.
-cudaError_t syev_lowest(const double* S, int lds, int m, int nev, double* theta, double* V, int ldv,
+cudaError_t syev_lowest(const double* S, int lds, int m, int nev, double* theta, double* V, int ldv, bool f64,
                         cudaStream_t s);
 // Generic small-array FP64 kernels used by the driver.
-cudaError_t to_df(const double* x, float2* y, int count, double scale, cudaStream_t s);
-cudaError_t negate_to_df(const double* x, float2* y, int count, cudaStream_t s);
+// y[i] = scale * x[i] as value slots (f64: the slot format)
+cudaError_t to_df(const double* x, float2* y, int count, double scale, bool f64, cudaStream_t s);
 
 }  // namespace sppc

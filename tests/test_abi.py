@@ -41,7 +41,7 @@ def _small():
     ("n1_not_level", 3), ("k_zero", 1), ("k_nine", 1), ("levels_bad", 3), ("unsorted", 1), ("col_range", 1),
     ("nan", 11), ("asym", 2), ("rowptr", 1), ("spmm_kernel", 1), ("reorth", 1), ("precond", 1), ("precision", 1),
     ("precision_k", 1), ("precond_levels", 1), ("switch_stall", 1), ("hybrid", 1), ("rmm_mixed", 1),
-    ("spin_cap", 1),
+    ("spin_cap", 1), ("precision_neg", 1), ("f64_rmm", 1), ("f64_proposal", 1),
 ])
 def test_create_rejects_bad_input(case, status):
     import paper_2407_08901_gb300 as S
@@ -50,10 +50,13 @@ def test_create_rejects_bad_input(case, status):
     n1, k = w.small_dim, w.k
     opts = S.sppc_default_opts(check_symmetry=1, spmm_kernel=2 if case == "spmm_kernel" else 1,
                                reorth=-1 if case == "reorth" else 0, precond=3 if case == "precond" else 1,
-                               precision={"precision": 3, "precision_k": 2}.get(case, 0),
+                               precision={"precision": 3, "precision_k": 2, "precision_neg": -2, "f64_rmm": -1,
+                                          "f64_proposal": -1}.get(case, 0),
                                precond_levels=99 if case == "precond_levels" else 1,
                                switch_stall=-0.5 if case == "switch_stall" else 0.0,
-                               hybrid={"hybrid": 3, "rmm_mixed": 2}.get(case, 0))
+                               hybrid={"hybrid": 3, "rmm_mixed": 2, "f64_rmm": 2, "f64_proposal": 1}.get(case, 0))
+    if case == "f64_proposal":
+        opts.proposal = 1
     if case == "rmm_mixed":
         opts.precision = 1
         k = 8

@@ -19,14 +19,16 @@ torch = pytest.importorskip("torch")
                                                             ("c1", 2, 6, 1, 1), ("small", 3, 5, 2, 1),
                                                             ("c1", 2, 6, 2, 1), ("c1", 2, 6, 2, 3),
                                                             ("small", 3, 5, 2, 2), ("c1", 2, 6, 2, 4)])
-def test_hybrid_matches_oracle(name, switch, pmax, precond, levels):
+@pytest.mark.parametrize("prec", [0, -1])
+def test_hybrid_matches_oracle(name, switch, pmax, precond, levels, prec):
+    """prec: the value format (0 double-float, -1 native FP64)."""
     import paper_2407_08901_gb300 as S
     w, rp, c, v = make_matrix(name)
     tol = 1e-9 if precond else 1e-7
     # both settings of the continuation's second projection are covered
     reorth = 0 if precond else 1
     opts = S.sppc_default_opts(p_max=pmax, hybrid=1, switch_order=switch, precond=precond, hybrid_maxit=400,
-                               reorth=reorth, precond_levels=levels)
+                               reorth=reorth, precond_levels=levels, precision=prec)
     # the oracle restarts when a block would not fit in max_blocks = p_max + 1
     h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, w.k, opts)
     try:
