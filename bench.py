@@ -176,27 +176,58 @@ def spmm_algorithmic_bytes(n: int, nnz: int, kp: int) -> int:
     return nnz * (8 + 4) + (n + 1) * 8 + 2 * n * kp * 8
 
 
-def cpu_oracle_sample(w, rp, c, v, orders: int = 3):
-    """The CPU oracle (as it stands) on a bounded part of the same workload:
-    the k+8 lowest small-space eigenpairs (ARPACK), then `orders` SPPC orders
-    in its MINRES mode.  Returns (seconds, H-vector products done, threads)."""
+def _small_start(w, rp, c, v):
+    """The oracle's small-space start: the k + 8 lowest eigenpairs of H0_hat by
+    ARPACK (all that its MINRES mode needs)."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as sla
-
-    import oracle
-    from oracle import spmm as ospmm
-    threads = os.cpu_count() or 1
-    ospmm.set_threads(threads)
     n1 = w.small_dim
-    t0 = time.perf_counter()
     rows = np.repeat(np.arange(n1), np.diff(rp[: n1 + 1]))
     cc = c[: rp[n1]]
     m = cc < n1
     H11 = sp.csr_matrix((v[: rp[n1]][m], (rows[m], cc[m])), shape=(n1, n1))
     ev, U = sla.eigsh(H11, k=w.k + 8, which="SA", tol=1e-13)
     o = np.argsort(ev)
-    r = oracle.sppc(rp, c, v, n1, w.k, fixed_orders=orders, solver="minres", small_eig=(ev[o], U[:, o]))
-    return time.perf_counter() - t0, r.spmv, threads
+    return ev[o], U[:, o]
+
+
+def cpu_oracle_method(w, rp, c, v, switch_order: int = SWITCH_ORDER, max_steps: int = 1000):
+    """The timed method on the CPU oracle, as it stands: ARPACK start, SPPC
+    (Algorithm 2, MINRES small solves) for switch_order orders, then the
+    continuation preconditioned by the shifted diagonal and the deflated
+    leading-block MINRES (oracle.hybrid) until every scaled residual is <= TOL
+    or max_steps steps.  Returns (seconds, phases, theta, converged, records,
+    threads); phases holds the start and the end time of every order and step,
+    records the Ritz values of every order and step."""
+    import oracle
+    from oracle import spmm as ospmm
+    threads = os.cpu_count() or 1
+    ospmm.set_threads(threads)
+    t0 = time.perf_counter()
+    small = _small_start(w, rp, c, v)
+    marks = [("start", 0, time.perf_counter() - t0)]
+    th, rs, conv, rec = oracle.sppc_hybrid(
+        rp, c, v, w.small_dim, w.k, switch_order=switch_order, tol=TOL, max_blocks=switch_order + 1,
+        maxit=max_steps, precond="lead", solver="minres", lead_iters=PRECOND_ITERS,
+        lead_rows=int(w.level_offsets[min(PRECOND_LEVELS, len(w.level_sizes) - 1)]), small_eig=small,
+        on_step=lambda ph, i: marks.append((ph, i, time.perf_counter() - t0)))
+    return time.perf_counter() - t0, marks, np.asarray(th), bool(conv), rec, threads
+
+
+def cpu_oracle_modelled(w, rp, c, v, orders: int, steps: int):
+    """A bounded sample of the oracle's method: ARPACK start, SPPC orders 0..2,
+    one continuation step.  The solve's time is modelled from its pieces: the
+    start, orders 0 and 1 (order 1 has no small solve, Eq. first_PC), order 2's
+    time for each of the other orders, and the continuation step's time for
+    each step.  Returns (modelled seconds, sample seconds, pieces, threads)."""
+    t, marks, _, _, _, threads = cpu_oracle_method(w, rp, c, v, switch_order=2, max_steps=1)
+    at = {(ph, i): x for ph, i, x in marks}
+    pieces = {"start": at[("start", 0)], "order0": at[("sppc", 0)] - at[("start", 0)],
+              "order1": at[("sppc", 1)] - at[("sppc", 0)], "order2": at[("sppc", 2)] - at[("sppc", 1)],
+              "step1": at[("davidson", 1)] - at[("sppc", 2)]}
+    model = (pieces["start"] + pieces["order0"] + pieces["order1"] + (orders - 1) * pieces["order2"]
+             + steps * pieces["step1"])
+    return model, t, pieces, threads
 
 
 def slowest_rank(value: float, dist=None, device: str = "cuda") -> float:
@@ -210,6 +241,12 @@ def slowest_rank(value: float, dist=None, device: str = "cuda") -> float:
     return float(t.item())
 
 
+# The counts of the timed method on c2 (the GPU solve: 15 SPPC orders, then 11
+# continuation steps), used by the reference arm, which runs without a GPU.
+METHOD_ORDERS = SWITCH_ORDER
+METHOD_STEPS = int(os.environ.get("SPPC_BENCH_STEPS", "11"))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -217,24 +254,22 @@ def run_reference(args):
     import workloads as W
     w = W.config(args.workload)
     rp, c, v = W.generate(w)
-    orders = 2
-    times = []
-    spmv = 0
+    models, samples, pieces = [], [], None
+    threads = os.cpu_count() or 1
     for it in range(args.warmup + args.steps):
-        t, spmv, threads = cpu_oracle_sample(w, rp, c, v, orders=orders)
+        model, t, pieces, threads = cpu_oracle_modelled(w, rp, c, v, METHOD_ORDERS, METHOD_STEPS)
         if it >= args.warmup:
-            times.append(t)
-    # scale the sample to one whole solve by products with H (the GPU solve of this
-    # workload needs 216 H-vector products: 15 orders + 11 continuation steps)
-    gpu_products = int(os.environ.get("SPPC_BENCH_PRODUCTS", "216"))
-    per_step = float(np.mean(times))
-    value = per_step * gpu_products / spmv
-    sample = (f"{args.workload}: ARPACK small-space start + {orders} SPPC orders of the FP64 oracle (MINRES mode), "
-              f"{spmv} H-vector products in {per_step:.2f} s, scaled to {gpu_products} products")
+            models.append(model)
+            samples.append(t)
+    value = float(np.mean(models))
+    sample = (f"{w.name}: per step, the oracle's method (ARPACK start, SPPC in MINRES mode, lead-preconditioned "
+              f"continuation) run to order 2 and one continuation step ({np.mean(samples):.2f} s); the solve "
+              f"modelled as start + orders 0-1 + {METHOD_ORDERS - 1} x order 2 + {METHOD_STEPS} x the step "
+              f"(last sample's pieces, s: " + ", ".join(f"{k} {x:.2f}" for k, x in pieces.items()) + ")")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "k": w.k},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(samples)) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": bench_config(w, int(c.shape[0])),
             "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -299,8 +334,10 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms_step = slowest_rank(float(np.mean(times)), dist, "cuda")
-    # plain SPPC's own result: the largest scaled residual after its last order
+    # plain SPPC's own result: the largest scaled residual after its last order;
+    # the Ritz values of every SPPC order (parity with the oracle below)
     plain_resid = float(np.max(S.sppc_order_info(h, int(st["switched_at"]), k)["resid"]))
+    order_theta = [np.asarray(S.sppc_order_info(h, p, k)["theta"]) for p in range(int(st["switched_at"]) + 1)]
     S.sppc_destroy(h)
 
     # end to end through the C ABI from host buffers
@@ -596,12 +633,30 @@ def run_ours(args):
                                                                  / np.abs(np.asarray(th_last))))}
         S.sppc_destroy(hc)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, spmv, threads = cpu_oracle_sample(w, rp, c, v)
-        value = t * st["spmv_h"] / spmv
+        # the oracle's whole method, once, on the host cores; its eigenvalues
+        # against the GPU's FP64 solve; and the reference arm's bounded-sample
+        # model of the same solve, to show how far the two agree
+        t, marks, cth_, cconv_, crec, threads = cpu_oracle_method(w, rp, c, v)
+        sppc_rel = [float(np.max(np.abs(order_theta[r.step] - r.theta) / np.abs(r.theta)))
+                    for r in crec if r.phase == "sppc" and r.step < len(order_theta)]
+        at = {(ph, i): x for ph, i, x in marks}
+        t_sppc = at.get(("sppc", SWITCH_ORDER), t) - at[("start", 0)]
+        model, tsample, pieces, _ = cpu_oracle_modelled(w, rp, c, v, SWITCH_ORDER, int(st["refine_steps"]))
         line["cpu_baseline"] = {
-            "value": value, "unit": "s", "cores": threads, "kind": "oracle",
-            "sample": f"{w.name}: ARPACK small-space start + 3 SPPC orders of the FP64 oracle (MINRES mode), "
-                      f"{spmv} H-vector products in {t:.2f} s, scaled to the GPU solve's {st['spmv_h']} products"}
+            "value": t, "unit": "s", "cores": threads, "kind": "oracle",
+            "sample": f"{w.name}: full solve, the oracle's method as it stands (ARPACK start, SPPC {SWITCH_ORDER} "
+                      f"orders in MINRES mode, lead-preconditioned continuation to {TOL:g}), one timed run",
+            "phases_s": {"start": at[("start", 0)], "sppc_orders": t_sppc,
+                         "continuation": t - at[("start", 0)] - t_sppc},
+            "converged": cconv_, "spmv_h": int(crec[-1].spmv),
+            "max_rel_theta_diff_vs_gpu_f64": float(np.max(np.abs(cth_ - th_last) / np.abs(th_last))),
+            "reference_arm_model_s": model, "reference_arm_sample_s": tsample}
+        # parity of the timed FP64 solve with the oracle, order by order over the
+        # SPPC phase (the continuation's trajectories part at rounding level)
+        line["parity_vs_oracle"] = {
+            "what": "max relative difference of the k Ritz values, GPU FP64 solve vs the CPU oracle, per SPPC order",
+            "orders": len(sppc_rel), "max_rel_theta_per_order": sppc_rel, "max_rel_theta": max(sppc_rel),
+            "bound": 1e-10, "ok": bool(max(sppc_rel) <= 1e-10)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -149,10 +149,14 @@ typedef struct {
                               a tiny value forces that path, for tests).  With spmm_kernel = 0 it
                               also bounds each mbarrier wait of the TMA-gather SpMM to spin_cap - 1
                               non-blocking tests (1 = give up at the first wait; 0 = about a second
-                              of clock): the warp gives up,
-                              waits for its copies in flight, raises the handle's flag, and
-                              sppc_spmm_host (or the next correction order) returns
-                              SPPC_ERR_TIMEOUT */
+                              of clock): the warp gives up, waits for its copies in flight, raises
+                              the handle's flag, and sppc_spmm_host (or the next correction order)
+                              returns SPPC_ERR_TIMEOUT */
+  int32_t value_rounding;  /* with precision 0 or -1: 1 rounds H's values to FP32, 2 rounds them as
+                              precision 2 does (diagonal FP32, other entries BF16), before anything
+                              else; the solve then runs on that matrix in the chosen format (the
+                              reference of the mixed-precision runs).  0 (default): as given;
+                              ignored with precision 1 or 2, which round this way themselves */
 } sppc_opts;
 
 typedef struct {

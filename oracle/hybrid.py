@@ -87,7 +87,7 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
                 max_blocks: int = 16, maxit: int = 500, precond: str = "jacobi", clamp: float = 1e-2,
                 solver: str = "pinv", minres_tol: float = 1e-12, reorth: str = "cond",
                 perturb: float = 0.0, perturb_seed: int = 0, lead_iters: int = 20, lead_rows: int | None = None,
-                small_eig=None):
+                small_eig=None, on_step=None):
     """Run SPPC (Algorithm 2) for up to `switch_order` orders (stopping early if
     every scaled residual is below tol), then the block continuation above.
     Returns (theta, resid, converged, records).
@@ -97,10 +97,13 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
     along the trajectory.  lead_rows (default n1): rows of the leading block that
     precond="lead" solves with MINRES (a level boundary; more levels than the
     small space make a stronger preconditioner).  small_eig: optional eigenpairs of
-    H0_hat passed to the SPPC phase (see sppc)."""
+    H0_hat passed to the SPPC phase (see sppc).  on_step: optional timing hook,
+    callable(phase, index), called after each SPPC order ("sppc", p) and each
+    continuation step ("davidson", it); it does not change the result."""
     n = row_ptr.shape[0] - 1
     r = sppc(row_ptr, col, val, n1, k, p_max=switch_order, tol=tol, solver=solver, minres_tol=minres_tol,
-             keep=True, small_eig=small_eig)
+             keep=True, small_eig=small_eig,
+             on_order=None if on_step is None else (lambda p: on_step("sppc", p)))
     records = [HybridRecord("sppc", o.p, o.theta, o.resid, o.spmv, k * (o.p + 1)) for o in r.orders]
     spmv = r.spmv
     if r.converged:
@@ -154,6 +157,8 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
         Z = Q @ Y
         res = np.linalg.norm(W @ Y - Z * th, axis=0) / np.abs(th)
         records.append(HybridRecord("davidson", it, th, res, spmv, Q.shape[1]))
+        if on_step is not None:
+            on_step("davidson", it)
         if np.all(res <= tol):
             return th, res, True, records
     return th, res, False, records

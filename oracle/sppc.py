@@ -100,7 +100,7 @@ def _ritz(Ht: np.ndarray, Q: np.ndarray, W: np.ndarray, k: int):
 def sppc(row_ptr, col, val, n1: int, k: int, *, p_max: int = 15, tol: float = 1e-6,
          fixed_orders: int | None = None, solver: str = "pinv", minres_tol: float = 1e-12,
          minres_maxit: int | None = None, vpsi: str = "recycled", degeneracy_tol: float = 1e-10,
-         keep: bool = False, small_eig=None) -> SPPCResult:
+         keep: bool = False, small_eig=None, on_order=None) -> SPPCResult:
     """Run Algorithm 2 on the CSR matrix (row_ptr, col, val).
 
     solver: "pinv" (exact spectral solve) or "minres" for Eq. (sm_lin_proj).
@@ -109,6 +109,8 @@ def sppc(row_ptr, col, val, n1: int, k: int, *, p_max: int = 15, tol: float = 1e
     fixed_orders: run exactly this many correction orders (no early stop).
     small_eig: optional (eigenvalues, eigenvectors) of H0_hat, ascending; "pinv"
             needs all of them, "minres" only those the deflation rule can touch.
+    on_order: optional callable(p), called after the Rayleigh-Ritz step of each
+            order p (0 included); a timing hook, it does not change the result.
     """
     n = row_ptr.shape[0] - 1
     P = fixed_orders if fixed_orders is not None else p_max
@@ -145,6 +147,8 @@ def sppc(row_ptr, col, val, n1: int, k: int, *, p_max: int = 15, tol: float = 1e
     th, Y, Z, res = _ritz(Ht, Qbuf[:, :m], Wbuf[:, :m], k)
     orders = [OrderRecord(0, th, res, E0.copy(), None, None, spmv)]
     result = SPPCResult(orders, E0, psi_hat, False)
+    if on_order is not None:
+        on_order(0)
     if fixed_orders is None and np.all(res < tol):
         result.converged = True
         result.E = [E0.copy()]
@@ -241,6 +245,8 @@ def sppc(row_ptr, col, val, n1: int, k: int, *, p_max: int = 15, tol: float = 1e
         m += k
         th, Y, Z, res = _ritz(Ht, Qbuf[:, :m], Wbuf[:, :m], k)
         orders.append(OrderRecord(p, th, res, Ep.copy(), angle, its, spmv))
+        if on_order is not None:
+            on_order(p)
         if fixed_orders is None and np.all(res < tol):
             result.converged = True
             break

@@ -1628,6 +1628,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->switch_stall = 0.0;
   o->minres_ctas = 0;
   o->spin_cap = 0;
+  o->value_rounding = 0;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1709,6 +1710,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "opts.switch_stall must be in [0, 1]");
   if (opt.minres_ctas < 0) return fail(nullptr, SPPC_ERR_ARG, "opts.minres_ctas must be >= 0");
   if (opt.spin_cap < 0) return fail(nullptr, SPPC_ERR_ARG, "opts.spin_cap must be >= 0");
+  if (opt.value_rounding < 0 || opt.value_rounding > 2)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.value_rounding must be 0, 1 or 2");
   if (opt.precision > 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
@@ -1747,7 +1750,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   const int32_t* ci = Hc->col;
   const double* va = Hc->val;
   const int64_t rows_h = dev_in ? std::max<int64_t>(n1, h->n_lead) : n;  // rows readable on the host
-  const int round_mode = opt.precision > 0 ? opt.precision : 0;
+  const int round_mode = opt.precision > 0 ? opt.precision : opt.value_rounding;
   if (dev_in) {
     rp_h.resize(n + 1);
     if (cudaMemcpy(rp_h.data(), rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -1767,7 +1770,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     ci = ci_h.data();
     va = va_h.data();
   }
-  if (opt.precision == 1) {
+  if (round_mode == 1) {
     // mixed precision: the matrix is H rounded to FP32, everywhere (SpMM, leading
     // block, diagonal); the solver's error is measured against that matrix
     const int64_t cnt = rp[rows_h];
@@ -1775,7 +1778,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
 #pragma omp parallel for schedule(static)
     for (int64_t t = 0; t < cnt; ++t) va_h[t] = static_cast<double>(static_cast<float>(va_h[t]));
     va = va_h.data();
-  } else if (opt.precision == 2) {
+  } else if (round_mode == 2) {
     // BF16 path: off-diagonal values rounded to FP32 and then to BF16 (round to
     // nearest even), the diagonal to FP32, everywhere; the solver's error is
     // measured against that matrix

@@ -4,7 +4,9 @@ This module holds no eigensolver arithmetic.  It defines the five workloads
 (sizes, level partitions, value law, seeds) and generates
 
 * the symmetric hierarchical Hamiltonian H (CSR, FP64 values, int32 columns,
-  int64 row pointers) through the C generator in ``gen.cpp``;
+  int64 row pointers) through the C generator in ``gen.cpp``, or directly in
+  GPU memory through its bit-identical device form ``gen_device.cu`` (for the
+  matrices whose host CSR would not fit or would take minutes to upload);
 * seeded dense blocks for SpMM and solver inputs.
 
 The paper's test matrices (NCSM Hamiltonians of 6Li, 7Li, 11B, 12C with the
@@ -23,17 +25,36 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_sppcgen.so")
+_SO_DEV = os.path.join(_HERE, "_sppcgen_cuda.so")
 _lib = None
+_lib_dev = None
+
+
+def _nvcc() -> str | None:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    import shutil
+    return shutil.which("nvcc")
 
 
 def build(force: bool = False) -> str:
-    """Compile the generator (portable arithmetic: no FMA contraction)."""
+    """Compile the generator (portable arithmetic: no FMA contraction) and, when
+    the CUDA toolkit is present, its device form (gen_device.cu, explicitly
+    rounded IEEE operations, sm_103a)."""
     src = os.path.join(_HERE, "gen.cpp")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
                "-fPIC", "-shared", "-o", _SO + ".tmp", src]
         subprocess.run(cmd, check=True)
         os.replace(_SO + ".tmp", _SO)
+    src_dev = os.path.join(_HERE, "gen_device.cu")
+    nvcc = _nvcc()
+    if nvcc and (force or not os.path.exists(_SO_DEV) or os.path.getmtime(_SO_DEV) < os.path.getmtime(src_dev)):
+        cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-fmad=false",
+               "-Xcompiler", "-fPIC", "-shared", "-o", _SO_DEV + ".tmp", src_dev]
+        subprocess.run(cmd, check=True)
+        os.replace(_SO_DEV + ".tmp", _SO_DEV)
     return _SO
 
 
@@ -175,6 +196,51 @@ def generate(w: Workload, threads: int = 0):
     finally:
         lib.sppcgen_free(h)
     return row_ptr, col, val
+
+
+def _load_dev():
+    global _lib_dev
+    if _lib_dev is None:
+        build()
+        lib = ctypes.CDLL(_SO_DEV)
+        lib.sppcgen_dev_build.restype = ctypes.c_void_p
+        lib.sppcgen_dev_build.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p]
+        lib.sppcgen_dev_n.restype = ctypes.c_int64
+        lib.sppcgen_dev_n.argtypes = [ctypes.c_void_p]
+        lib.sppcgen_dev_nnz.restype = ctypes.c_int64
+        lib.sppcgen_dev_nnz.argtypes = [ctypes.c_void_p]
+        lib.sppcgen_dev_fill.restype = ctypes.c_int32
+        lib.sppcgen_dev_fill.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_void_p]
+        lib.sppcgen_dev_free.restype = None
+        lib.sppcgen_dev_free.argtypes = [ctypes.c_void_p]
+        _lib_dev = lib
+    return _lib_dev
+
+
+def generate_device(w: Workload):
+    """The matrix of generate(w), built on the current CUDA device without a host
+    copy (bit-identical to the host generator).  Returns torch CUDA tensors
+    (row_ptr int64[n+1], col int32[nnz], val float64[nnz])."""
+    import torch
+    lib = _load_dev()
+    sizes = (ctypes.c_int64 * len(w.level_sizes))(*w.level_sizes)
+    stream = torch.cuda.current_stream().cuda_stream
+    h = lib.sppcgen_dev_build(sizes, len(w.level_sizes), w.draws_per_row, float(w.sigma),
+                              ctypes.c_uint64(w.seed & 0xFFFFFFFFFFFFFFFF), stream)
+    if not h:
+        raise MemoryError("device generator failed (bad sizes, a CUDA error or out of device memory)")
+    try:
+        n = lib.sppcgen_dev_n(h)
+        nnz = lib.sppcgen_dev_nnz(h)
+        row_ptr = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")
+        if lib.sppcgen_dev_fill(h, row_ptr.data_ptr(), col.data_ptr(), val.data_ptr(), stream) != 0:
+            raise RuntimeError("device generator: fill failed")
+    finally:
+        lib.sppcgen_dev_free(h)
+    return row_ptr, col[:nnz], val[:nnz]
 
 
 def random_block(n: int, k: int, seed: int) -> np.ndarray:
