@@ -75,6 +75,9 @@ def parse_args():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision solve")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-matrix workload")
+    ap.add_argument("--no-c3", action="store_true", help="skip the n = 2e7 mixed-precision workload (config 3)")
+    ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0],
+                    help="value format of the --profile spmm / solve / minres runs: -1 native FP64, 0 double-float")
     ap.add_argument("--profile", default="none", choices=["none", "spmm", "spmm32", "spmm16", "solve", "minres", "learned"],
                     help="run the workload's SpMM twice (spmm; spmm32 / spmm16: the FP32- / BF16-value kernels), "
                          "one solve with the bench options (solve), or three plain SPPC orders (minres: two "
@@ -276,6 +279,67 @@ def run_reference(args):
     return 0
 
 
+def run_c3(S, W, torch, stream, flush):
+    """Config 3: n = 2e7 in 9 levels x2.2, ~250 entries per row (5.0e9), k = 8,
+    built on the GPU by the device generator (its host CSR would be 60 GB).  The
+    method with FP32 values, then with BF16 off-diagonal values (FP32
+    accumulation, double-float projection); each eigenvalue's error against an
+    FP64 solve of the same rounded matrix (the solver's error) and against the
+    FP64 solve of the unrounded H (the rounding of H's values)."""
+    w3 = W.config("c3")
+    nlev = len(w3.level_sizes)
+    t0 = time.perf_counter()
+    rp3, c3, v3 = W.generate_device(w3)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    n3, nnz3, k3 = w3.n, int(c3.numel()), w3.k
+    out = {"workload": f"c3: n={n3}, {nlev} levels x2.2, n1={w3.small_dim}, nnz={nnz3}, k={k3}, seed {w3.seed}, "
+                       "generated on the device", "generate_s": t_gen}
+
+    def solve(prec=-1, rounding=0):
+        o = solve_opts(S, nlev, timing=1, precision=prec, value_rounding=rounding)
+        hh = S.sppc_create(rp3, c3, v3, w3.level_offsets, w3.small_dim, k3, o, stream=stream, on_device=True)
+        try:
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                conv_, th_, rs_, st_ = S.sppc_solve(hh, k3, tol=TOL, stream=stream)
+                e1.record(stream)
+            e1.synchronize()
+        finally:
+            S.sppc_destroy(hh)
+        return e0.elapsed_time(e1) / 1e3, bool(conv_), np.asarray(th_), np.asarray(rs_), st_
+
+    t64, cv64, th64, rs64, st64 = solve(-1, 0)
+    out["f64"] = {"value": t64, "unit": "s", "converged": cv64, "spmv_h": st64["spmv_h"],
+                  "max_scaled_resid": float(np.max(rs64)),
+                  "spmm_ms_per_product": st64["spmm_ms"] / max(st64["spmm_launches"], 1)}
+    peak, peak_kind = peaks()
+    for prec, key, bytes_val in ((1, "fp32", 4), (2, "bf16", 2)):
+        tm, cvm, thm, rsm, stm = solve(prec, 0)
+        tr, cvr, thr, rsr, _ = solve(-1, prec)
+        spmm_ms = stm["spmm_ms"] / max(stm["spmm_launches"], 1)
+        alg = nnz3 * (bytes_val + 4) + (n3 + 1) * 8 + n3 * 8 * 4 + n3 * 8 * 8
+        out[key] = {
+            "method": ("H values rounded to FP32" if prec == 1 else "off-diagonal values rounded to BF16 (diagonal "
+                       "FP32)") + "; FP32 products with H until the residual estimates reach 1e-6, then "
+                       "double-float products; Gram, CholeskyQR2, projected eigensolve and MINRES in double-float",
+            "value": tm, "unit": "s", "speedup_vs_f64": t64 / tm, "converged": cvm, "spmv_h": stm["spmv_h"],
+            "max_scaled_resid": float(np.max(rsm)),
+            "max_rel_theta_err_vs_f64_same_rounded_matrix": float(np.max(np.abs(thm - thr) / np.abs(thr))),
+            "f64_same_rounded_matrix": {"value": tr, "converged": cvr, "max_scaled_resid": float(np.max(rsr))},
+            "max_rel_theta_diff_vs_f64_unrounded": float(np.max(np.abs(thm - th64) / np.abs(th64))),
+            "spmm": {"kernel": f"k_spmm_sell_f32r (FP32 X, {'FP32' if prec == 1 else 'BF16'} values)",
+                     "ms_per_product": spmm_ms, "algorithmic_bytes": alg,
+                     "achieved_GBps": alg / (spmm_ms * 1e-3) / 1e9,
+                     "frac": alg / (spmm_ms * 1e-3) / 1e9 / peak, "peak": peak, "peak_kind": peak_kind}}
+    del rp3, c3, v3
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -460,6 +524,28 @@ def run_ours(args):
                 "max_rel_theta_err_vs_fp64_same_rounded_matrix": float(np.max(np.abs(mth - rth) / np.abs(rth))),
                 "max_rel_theta_diff_vs_fp64_unrounded": float(np.max(np.abs(mth - th0) / np.abs(th0)))}
         del rounded
+    if rank == 0 and world == 1 and not args.no_mixed:
+        # the small solves by FP32 MINRES with iterative refinement in double-float,
+        # against the double-float MINRES, in the double-float and FP32-value paths
+        fr = {}
+        for prec, key in ((0, "df64_values"), (1, "fp32_values")):
+            res = {}
+            for fp32 in (0, 1):
+                hf = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k,
+                                   solve_opts(S, timing=1, precision=prec, minres_fp32=fp32), stream=stream)
+                try:
+                    timed_solve(hf)
+                    ms_f, fconv, fth, frs, fst = timed_solve(hf)
+                finally:
+                    S.sppc_destroy(hf)
+                res["fp32_refined" if fp32 else "double_float"] = {
+                    "value": ms_f / 1e3, "unit": "s", "minres_ms": fst["minres_ms"],
+                    "minres_iters": fst["minres_iters"], "converged": bool(fconv),
+                    "max_rel_theta_diff_vs_f64": float(np.max(np.abs(np.asarray(fth) - th_last) / np.abs(th_last)))}
+            fr[key] = res
+        line["minres_fp32_refinement"] = fr
+    if rank == 0 and world == 1 and not args.no_c3:
+        line["c3"] = run_c3(S, W, torch, stream, flush)
     if rank == 0 and world == 1 and not args.no_learned:
         # learned correction proposal: the same solve with the trained network's
         # block in each continuation step (kept iff the largest scaled residual
@@ -498,6 +584,30 @@ def run_ours(args):
                 "plain_sppc_after_15_orders_max_scaled_resid": plain_resid,
                 "max_rel_theta_diff_vs_fp64": float(np.max(np.abs(np.asarray(lth) - np.asarray(th_last))
                                                            / np.abs(np.asarray(th_last))))}
+            # held-out matrices of the same law (seeds 1000-1003, n = 2e6, built on the
+            # device): the method with and without the network, one solve each
+            held = {}
+            for seed in (1000, 1001, 1002, 1003):
+                wt = W.Workload(f"c2_seed{seed}", w.level_sizes, w.nnz_per_row, k, seed=seed)
+                trp, tc, tv = W.generate_device(wt)
+                res = {}
+                for key, kw in (("plain", {}), ("learned", {"proposal": 1})):
+                    ht = S.sppc_create(trp, tc, tv, wt.level_offsets, wt.small_dim, k, solve_opts(S, timing=1, **kw),
+                                       stream=stream, on_device=True)
+                    if kw:
+                        S.sppc_set_proposal(ht, params, mu, sd)
+                    try:
+                        ms_t, tconv, tth, trs, tst = timed_solve(ht)
+                    finally:
+                        S.sppc_destroy(ht)
+                    res[key] = {"value": ms_t / 1e3, "spmv_h": tst["spmv_h"], "steps": tst["refine_steps"],
+                                "converged": bool(tconv)}
+                    if kw:
+                        res[key]["proposals_kept"] = tst["proposals_kept"]
+                        res[key]["proposals_tried"] = tst["proposals_tried"]
+                held[str(seed)] = res
+                del trp, tc, tv
+            line["learned_proposal"]["held_out_seeds"] = held
         else:
             line["learned_proposal"] = {"unavailable": "no trained network at " + os.path.relpath(PR.DEFAULT_NET, ROOT)}
     if rank == 0 and world == 1 and not args.no_batched:
@@ -686,7 +796,8 @@ def run_profile(args):
         torch.cuda.synchronize()
         print(f"profile {args.profile}: {w.name}, 2 products", flush=True)
     elif args.profile == "spmm":
-        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=1))
+        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k,
+                          S.sppc_default_opts(p_max=1, precision=args.precision))
         X = torch.from_numpy(W.random_block(w.n, 8, 1)).cuda()
         Y = torch.empty_like(X)
         for _ in range(2):
@@ -702,12 +813,13 @@ def run_profile(args):
         torch.cuda.synchronize()
         print(f"profile learned: {w.name}, converged {conv}, steps {st['refine_steps']}", flush=True)
     elif args.profile == "minres":
-        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=3))
+        h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k,
+                          S.sppc_default_opts(p_max=3, precision=args.precision))
         conv, th, rs, st = S.sppc_solve(h, k, tol=1e-300, p_max=3)
         torch.cuda.synchronize()
         print(f"profile minres: {w.name}, orders {st['orders']}, MINRES iterations {st['minres_iters']}", flush=True)
     else:
-        opts = solve_opts(S, len(w.level_sizes))
+        opts = solve_opts(S, len(w.level_sizes), precision=args.precision)
         h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts)
         conv, th, rs, st = S.sppc_solve(h, k, tol=TOL)
         torch.cuda.synchronize()

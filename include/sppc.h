@@ -157,6 +157,13 @@ typedef struct {
                               else; the solve then runs on that matrix in the chosen format (the
                               reference of the mixed-precision runs).  0 (default): as given;
                               ignored with precision 1 or 2, which round this way themselves */
+  int32_t minres_fp32;     /* 1: the small solves of Eq. sm_lin_proj by iterative refinement: each sweep
+                              runs MINRES in FP32 (to minres_fp32_tol relative, or 2,000 iterations)
+                              on the current residual, adds its solution and recomputes the residual
+                              b1 - (H0_hat - E) x in double-float, until ||r|| <= minres_tol ||b1||
+                              (at most 8 sweeps).  Not with precision -1.  0 (default): MINRES in the
+                              value format */
+  double minres_fp32_tol;  /* FP32 MINRES stopping tolerance of one refinement sweep (default 1e-6) */
 } sppc_opts;
 
 typedef struct {

@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("proposal", ctypes.c_int32), ("precond_levels", ctypes.c_int32),
                 ("minres_deflate", ctypes.c_int32), ("small_degree", ctypes.c_int32),
                 ("switch_stall", ctypes.c_double), ("minres_ctas", ctypes.c_int32),
-                ("spin_cap", ctypes.c_int32), ("value_rounding", ctypes.c_int32)]
+                ("spin_cap", ctypes.c_int32), ("value_rounding", ctypes.c_int32), ("minres_fp32", ctypes.c_int32),
+                ("minres_fp32_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

@@ -96,6 +96,7 @@ struct sppc_ctx {
   float2 *zlead = nullptr, *rlead = nullptr;  // leading rows of the Ritz vectors / residuals (precond 2)
   float2 *mv = nullptr, *mvprev = nullptr, *mp = nullptr, *my = nullptr, *mw1 = nullptr, *mw2 = nullptr,
          *mx = nullptr;
+  float2 *mref = nullptr, *mres = nullptr, *mdx = nullptr;  // refined FP32 MINRES: b, residual, correction
   // small eigensolve (n1 x 8 blocks, up to 2 per set; 3 filter sets + X + AX + tmp)
   float2* se[12] = {nullptr};
   // the small eigensolve's b lowest eigenpairs (two blocks of n1 x 8; values
@@ -958,6 +959,76 @@ sppc_status small_eigensolve(sppc_ctx* h) {
 // psi_hat_k (Eq. sm_lin_proj) with the persistent kernel of k_minres.cu (one
 // cooperative launch); the right-hand side is already deflated.  x0 = 0; stop at
 // ||r|| <= minres_tol ||b1||.  Afterwards x is re-projected onto the complement.
+// Iterative refinement of the small solves with FP32 MINRES: the right-hand side
+// b (h->b1, on the complement of psi_hat) is kept in mref; each sweep runs the
+// persistent MINRES in FP32 on the current residual r (relative tolerance
+// minres_fp32_tol, at most 2,000 iterations), adds its solution to x (h->mx) and
+// recomputes r = b - (H0_hat - E) x in the value format, projected off psi_hat,
+// until every ||r_j|| <= minres_tol ||b_j|| (at most 8 sweeps, else
+// SPPC_ERR_MINRES).  iters gets each column's FP32 iterations over the sweeps.
+sppc_status minres_refined(sppc_ctx* h, int maxit, std::vector<int32_t>& iters) {
+  cudaStream_t s = h->stream;
+  const int k = h->k, kp = h->kp;
+  const int64_t n1 = h->n1;
+  float2* c = h->dCoef;
+  int* dstat = h->dStatus + 32;
+  const size_t bytes = sizeof(float2) * (size_t)n1 * kp;
+  CK(cudaMemcpyAsync(h->mref, h->b1, bytes, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->mres, h->b1, bytes, cudaMemcpyDeviceToDevice, s));
+  CK(fill_zero(h->mx, (int64_t)n1 * kp, s));
+  std::vector<double> bn2(kp), rn2(kp);
+  {
+    const float2* A[1] = {h->mref};
+    const float2* B[1] = {h->mref};
+    CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    CK(cudaMemcpyAsync(bn2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+  }
+  const int inner = std::min(maxit, 2000);
+  for (int sweep = 0;; ++sweep) {
+    if (sweep == 8) return fail(h, SPPC_ERR_MINRES, "refined MINRES: no convergence in 8 sweeps");
+    // dx: FP32 MINRES on the residual (its right-hand-side buffer is overwritten)
+    CK(cudaMemcpyAsync(h->b1, h->mres, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(minres_persistent(h->H11c, k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
+                         h->mw2, h->mdx, h->opt.minres_fp32_tol, inner, h->partials, h->partial_cap, h->dBar, dstat,
+                         s, h->opt.minres_ctas, h->opt.spin_cap, true));
+    int st[10] = {0};
+    CK(cudaMemcpyAsync(st, dstat, sizeof(int) * 10, cudaMemcpyDeviceToHost, s));
+    // x += dx; r = b - (H0_hat - E) x, projected off psi_hat
+    CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->mdx), c + kOnes, kp, 0, n1, h->f64, s));
+    Epi e;
+    e.alpha = c + kNegOnes;
+    e.beta = c + kPosE0;
+    e.gamma = c + kOnes;
+    e.Z = h->mref;
+    CK(spmm11(h, kp, h->mx, h->mres, e, s));
+    {
+      const float2* A[1] = {h->psi_hat};
+      const float2* B[1] = {h->mres};
+      CK(coldots(A, B, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+      k_neg_dots_to_coef<<<1, 32, 0, s>>>(h->dDots, k, kp, c + kDefl, h->f64); count_launch();
+      CK(cudaGetLastError());
+      CK(combine_diag(h->mres, h->mres, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, h->f64, s));
+      const float2* R[1] = {h->mres};
+      CK(coldots(R, R, 1, kp, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+      CK(cudaMemcpyAsync(rn2.data(), h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    if (st[0]) return fail(h, SPPC_ERR_TIMEOUT, "MINRES: a grid barrier timed out");
+    int mxit = 0;
+    for (int j = 0; j < k; ++j) {
+      iters[j] += st[2 + j];
+      mxit = std::max(mxit, st[2 + j]);
+    }
+    h->stats.minres_iters += mxit;
+    h->stats.spmv_h11 += (int64_t)k * (std::abs(st[1]) + 1);
+    bool done = true;
+    for (int j = 0; j < k; ++j)
+      done = done && std::sqrt(std::max(rn2[j], 0.0)) <= h->opt.minres_tol * std::sqrt(std::max(bn2[j], 0.0));
+    if (done) break;
+  }
+  return SPPC_OK;
+}
+
 sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
   PhaseRange nvtx_range("minres");
   cudaStream_t s = h->stream;
@@ -998,9 +1069,14 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
     CK(cudaGetLastError());
     CK(combine_diag(h->b1, h->T1, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, h->f64, s));
   }
-  CK(minres_persistent(h->H11c, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
-                       h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s,
-                       h->opt.minres_ctas, h->opt.spin_cap));
+  iters.assign(h->k, 0);
+  if (h->opt.minres_fp32) {
+    CKS(minres_refined(h, maxit, iters));
+  } else {
+    CK(minres_persistent(h->H11c, h->k, kp, c + kShiftNegE, h->psi_hat, h->b1, h->mv, h->mvprev, h->my, h->mw1,
+                         h->mw2, h->mx, h->opt.minres_tol, maxit, h->partials, h->partial_cap, h->dBar, dstat, s,
+                         h->opt.minres_ctas, h->opt.spin_cap));
+  }
   if (defl) CK(combine_diag(h->mx, h->mx, c + kOnes, one(h->T2), c + kOnes, kp, 0, n1, h->f64, s));  // + x_defl
   // x -= psi_hat (psi_hat^T x): keep the solution on the complement of psi_hat_k
   float2* x = h->mx;
@@ -1012,11 +1088,11 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
     CK(cudaGetLastError());
     CK(combine_diag(x, x, c + kOnes, one(h->psi_hat), c + kDefl, kp, 0, n1, h->f64, s));
   }
+  if (h->opt.minres_fp32) return SPPC_OK;  // statistics kept by minres_refined
   int st[10] = {0};
   CK(cudaMemcpyAsync(st, dstat, sizeof(int) * 10, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (st[0]) return fail(h, SPPC_ERR_TIMEOUT, "MINRES: a grid barrier timed out");
-  iters.assign(h->k, 0);
   int mx = 0;
   for (int j = 0; j < h->k; ++j) {
     iters[j] = st[2 + j];
@@ -1629,6 +1705,8 @@ void sppc_default_opts(sppc_opts* o) {
   o->minres_ctas = 0;
   o->spin_cap = 0;
   o->value_rounding = 0;
+  o->minres_fp32 = 0;
+  o->minres_fp32_tol = 1e-6;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1712,6 +1790,11 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.spin_cap < 0) return fail(nullptr, SPPC_ERR_ARG, "opts.spin_cap must be >= 0");
   if (opt.value_rounding < 0 || opt.value_rounding > 2)
     return fail(nullptr, SPPC_ERR_ARG, "opts.value_rounding must be 0, 1 or 2");
+  if (opt.minres_fp32 != 0 && opt.minres_fp32 != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.minres_fp32 must be 0 or 1");
+  if (opt.minres_fp32 && opt.precision == -1)
+    return fail(nullptr, SPPC_ERR_ARG, "opts.minres_fp32 needs double-float slots (precision 0, 1 or 2)");
+  if (opt.minres_fp32 && !(opt.minres_fp32_tol > 0.0 && opt.minres_fp32_tol < 1.0))
+    return fail(nullptr, SPPC_ERR_ARG, "opts.minres_fp32_tol must be in (0, 1)");
   if (opt.precision > 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
@@ -2026,6 +2109,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     // MINRES vectors: the small-space solves (n1 rows) and the precond 2 solve (n_lead rows)
     for (float2** q : {&h->b1, &h->mv, &h->mvprev, &h->mp, &h->my, &h->mw1, &h->mw2, &h->mx})
       A(q, (size_t)std::max(n1, h->n_lead) * kp);
+    if (h->opt.minres_fp32)
+      for (float2** q : {&h->mref, &h->mres, &h->mdx}) A(q, (size_t)n1 * kp);
     for (int i = 0; i < 12; ++i) A(&h->se[i], (size_t)n1 * 8);
     A(&h->psib[0], (size_t)n1 * 8);
     A(&h->psib[1], (size_t)n1 * 8);

@@ -122,9 +122,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned l
 // the 16 lane sums are combined by a fixed shuffle tree.  Every CTA computes the
 // same result; it lands in red_out (shared).
 constexpr int kMaxPartialsPerWarp = 16;  // gridDim.x <= 16 * kMinresWarps
-template <bool F64>
+template <class V>
 __device__ void reduce_partials(const float2* partials, int nout, float2* red_out) {
-  using V = Ar<F64>;
   const int t = threadIdx.x;
   const int o = t >> 4, part = t & 15;
   const int G = static_cast<int>(gridDim.x);
@@ -186,10 +185,9 @@ __device__ __forceinline__ void gather_p(const float2* X, int cidx, int off, flo
 // Row sums of H0_hat p for one row: this lane's segment (entries seg, seg+4, ...),
 // columns [off, off + CPL), in batches of 4 independent gathers, then the
 // segment sums combined across the 4 lanes of the half (all 32 lanes call it).
-template <int KP, bool F64>
+template <int KP, class V>
 __device__ __forceinline__ void row_product(const CsrDev& A, int64_t row, bool valid, int seg, int off,
                                             const float2* P, uint64_t pol, float2 (&out)[KP / 2]) {
-  using V = Ar<F64>;
   constexpr int CPL = KP / 2;
   typename V::Acc acc[CPL];
 #pragma unroll
@@ -232,9 +230,8 @@ __device__ __forceinline__ void row_product(const CsrDev& A, int64_t row, bool v
   }
 }
 
-template <int KP, bool F64>
+template <int KP, class V>
 __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a) {
-  using V = Ar<F64>;
   using Acc = typename V::Acc;
   constexpr int CPL = KP / 2;
   constexpr int kRowsPerWarp = 4;
@@ -316,7 +313,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
   }
   flush(dd, 1, pbuf[1]);
   if (!grid_barrier(a.bar, err, a.spin_limit)) return;
-  reduce_partials<F64>(pbuf[1], 8, sdot);
+  reduce_partials<V>(pbuf[1], 8, sdot);
   if (threadIdx.x < 8) {
     const int jj = threadIdx.x;
     const double b1 = (jj < a.k) ? sqrt(fmax(V::to_d(sdot[jj]), 0.0)) : 0.0;
@@ -345,7 +342,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
       const int64_t row = r0 + rq;
       const bool valid = row < n;
       float2 hp[CPL];
-      if (!finish) row_product<KP, F64>(a.A, row, valid, seg, off, P, pol, hp);
+      if (!finish) row_product<KP, V>(a.A, row, valid, seg, off, P, pol, hp);
       if (!valid || !has_col) continue;
       const int64_t b = row * KP + j;
       const float2 vold = Vv[b];
@@ -391,7 +388,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
     flush(dd, 4, pbuf[0]);
     if (!grid_barrier(a.bar, err, a.spin_limit)) return;
     // ---- phase B
-    reduce_partials<F64>(pbuf[0], 32, sdot);
+    reduce_partials<V>(pbuf[0], 32, sdot);
     if (threadIdx.x < 8) {
       const int jj = threadIdx.x;
       double s = 0.0, al = 0.0;
@@ -421,7 +418,7 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
     flush(dd, 1, pbuf[1]);
     if (!grid_barrier(a.bar, err, a.spin_limit)) return;
     // ---- phase C
-    reduce_partials<F64>(pbuf[1], 8, sdot);
+    reduce_partials<V>(pbuf[1], 8, sdot);
     ++it;
     if (threadIdx.x < 8) {
       const int jj = threadIdx.x;
@@ -479,28 +476,36 @@ __global__ void __launch_bounds__(kMinresThreads, 1) k_minres(MinresKernelArgs a
 }  // namespace
 
 // Buffers: P holds b1 on entry (overwritten); V, VP, Y, W1, W2 are scratch;
-// X receives the solution.  All n1 x kp value slots in A's format.  status (host-visible via
+// X receives the solution.  All n1 x kp value slots in A's format; with fp32 the
+// iteration runs in FP32 on the slots' leading words and writes FP32 values
+// (a double-float slot with a zero low word).  status (host-visible via
 // a copy): [0] time-out flag, [1] iterations (negative: limit reached),
 // [2+j] iterations of column j.  bar: two zeroed unsigned words.
 cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
                               float2* V, float2* VP, float2* Y, float2* W1, float2* W2, float2* X, double tol,
                               int maxit, float2* partials, int64_t partial_cap, unsigned* bar, int* status,
-                              cudaStream_t s, int max_ctas, int spin_cap) {
+                              cudaStream_t s, int max_ctas, int spin_cap, bool fp32) {
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (!coop) return cudaErrorNotSupported;
   const void* fn = nullptr;
-  switch (kp * 2 + (A.f64 ? 1 : 0)) {
-    case 4: fn = reinterpret_cast<const void*>(k_minres<2, false>); break;
-    case 5: fn = reinterpret_cast<const void*>(k_minres<2, true>); break;
-    case 8: fn = reinterpret_cast<const void*>(k_minres<4, false>); break;
-    case 9: fn = reinterpret_cast<const void*>(k_minres<4, true>); break;
-    case 12: fn = reinterpret_cast<const void*>(k_minres<6, false>); break;
-    case 13: fn = reinterpret_cast<const void*>(k_minres<6, true>); break;
-    case 16: fn = reinterpret_cast<const void*>(k_minres<8, false>); break;
-    case 17: fn = reinterpret_cast<const void*>(k_minres<8, true>); break;
+  // arithmetic: FP32 on request, else the matrix's slot format
+  const int fmt = fp32 ? 2 : (A.f64 ? 1 : 0);
+  switch (kp * 4 + fmt) {
+    case 8: fn = reinterpret_cast<const void*>(k_minres<2, Ar<false>>); break;
+    case 9: fn = reinterpret_cast<const void*>(k_minres<2, Ar<true>>); break;
+    case 10: fn = reinterpret_cast<const void*>(k_minres<2, ArF32>); break;
+    case 16: fn = reinterpret_cast<const void*>(k_minres<4, Ar<false>>); break;
+    case 17: fn = reinterpret_cast<const void*>(k_minres<4, Ar<true>>); break;
+    case 18: fn = reinterpret_cast<const void*>(k_minres<4, ArF32>); break;
+    case 24: fn = reinterpret_cast<const void*>(k_minres<6, Ar<false>>); break;
+    case 25: fn = reinterpret_cast<const void*>(k_minres<6, Ar<true>>); break;
+    case 26: fn = reinterpret_cast<const void*>(k_minres<6, ArF32>); break;
+    case 32: fn = reinterpret_cast<const void*>(k_minres<8, Ar<false>>); break;
+    case 33: fn = reinterpret_cast<const void*>(k_minres<8, Ar<true>>); break;
+    case 34: fn = reinterpret_cast<const void*>(k_minres<8, ArF32>); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMinresThreads, 0);

@@ -218,7 +218,7 @@ cudaError_t fill_zero(float2* Y, int64_t count, cudaStream_t s);
 cudaError_t minres_persistent(const CsrDev& A, int k, int kp, const float2* negE, const float2* psi, float2* P,
                               float2* V, float2* VP, float2* Y, float2* W1, float2* W2, float2* X, double tol,
                               int maxit, float2* partials, int64_t partial_cap, unsigned* bar, int* status,
-                              cudaStream_t s, int max_ctas = 0, int spin_cap = 0);
+                              cudaStream_t s, int max_ctas = 0, int spin_cap = 0, bool fp32 = false);
 
 // ---- k_small.cu (single-CTA FP64 kernels on small matrices)
 // Cholesky of the leading kk x kk part of G (ld = ldg) plus `shift` on the diagonal;

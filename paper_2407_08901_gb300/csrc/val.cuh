@@ -109,6 +109,30 @@ struct Ar<true> {
   }
 };
 
+// FP32 arithmetic on double-float slots: reads the leading word (the value
+// rounded to FP32), writes (value, 0), a valid double-float slot.  Used by the
+// FP32 small-space MINRES whose result iterative refinement corrects in
+// double-float (or FP64).
+struct ArF32 {
+  struct Acc {
+    float s;
+  };
+  static __device__ __forceinline__ void zero(Acc& a) { a.s = 0.f; }
+  static __device__ __forceinline__ void set(Acc& a, float2 v) { a.s = v.x; }
+  static __device__ __forceinline__ void mac(Acc& a, float2 x, float2 y) { a.s = __fmaf_rn(x.x, y.x, a.s); }
+  static __device__ __forceinline__ void acc(Acc& a, float2 x) { a.s = __fadd_rn(a.s, x.x); }
+  static __device__ __forceinline__ void norm(Acc&) {}
+  static __device__ __forceinline__ float2 get(const Acc& a) { return make_float2(a.s, 0.f); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), 0.f); }
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return make_float2(__fsub_rn(a.x, b.x), 0.f); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), 0.f); }
+  static __device__ __forceinline__ float2 div(float2 a, float2 b) { return make_float2(__fdiv_rn(a.x, b.x), 0.f); }
+  static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, 0.f); }
+  static __device__ __forceinline__ double to_d(float2 a) { return (double)a.x; }
+  static __device__ __forceinline__ float2 from_d(double x) { return make_float2(__double2float_rn(x), 0.f); }
+  static __device__ __forceinline__ double lead(float2 a) { return (double)a.x; }
+};
+
 // Butterfly sum over the 32 lanes (fixed order).
 template <bool F64>
 __device__ __forceinline__ float2 warp_sum(float2 v) {
