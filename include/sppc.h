@@ -164,6 +164,13 @@ typedef struct {
                               (at most 8 sweeps).  Not with precision -1.  0 (default): MINRES in the
                               value format */
   double minres_fp32_tol;  /* FP32 MINRES stopping tolerance of one refinement sweep (default 1e-6) */
+  int32_t tensor_gram;     /* 1: the Gram products against the orthonormal basis (the projections of
+                              Eq. blkGS and the border Q^T W of Eq. proj) run on the tensor cores:
+                              entries cut into 62-bit fixed point, eight 8-bit digits each, exact
+                              FP16 digit products summed exactly, combined in FP64 (error below one
+                              FP64 rounding of the largest terms; see sppc_block_gram).  Used where
+                              the block width is 8 (k = 7 or 8); a basis entry that is not finite
+                              makes the solve return SPPC_ERR_NAN.  0 (default): CUDA cores */
 } sppc_opts;
 
 typedef struct {
@@ -322,6 +329,31 @@ sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr
  * on `stream`; SPPC_ERR_ARG on bad sizes.  All buffers are caller-owned. */
 sppc_status sppc_small_syev(const double* S, int32_t m, int32_t lds, int32_t nev, double* theta, double* V,
                             int32_t ldv, void* stream);
+
+/* The block Gram product of block Gram-Schmidt (Eq. blkGS) and of the border of
+ * the projected matrix (Eq. proj), as the solve computes it:
+ *   G[(8a + i) * 8 + j] = sum_{r < n} A_a[r][i] B[r][j],
+ * A: device, nblocks (1 .. 40) blocks of n x 8 row-major FP64, block a at A + 8 a n;
+ * B: device, n x 8 row-major FP64 (A and B may be NULL when n = 0); G: device,
+ * 8 nblocks x 8 row-major FP64.
+ * flags bit 0 (SPPC_GRAM_TENSOR): on the tensor cores.  Every entry of A must have
+ *   |a| < 2 (columns of an orthonormal basis); a = sign X 2^-61 with X < 2^62 an
+ *   integer, b = sign X' 2^(f_j - 61) with 2^f_j above |b| in column j (per group
+ *   of rows), X and X' cut into eight 8-bit digits; every digit product with
+ *   digit levels s + t <= 8 is formed exactly in FP16 x FP16 -> FP32 (sums of 256
+ *   rows stay below 2^24) and summed in 64-bit integers; the result is one FP64
+ *   rounding per row group away from the exact Gram of the rounded inputs, whose
+ *   rounding and dropped levels add at most about 2^-60 |b|_max per row.
+ *   Otherwise (bit 0 clear): FP64 or double-float fused multiply-adds.
+ * flags bit 1 (SPPC_GRAM_DF): the values are first converted to double-float pairs
+ *   and the product runs in that format (FP64 slots otherwise).
+ * Synchronises `stream`; temporaries are allocated and freed per call.  SPPC_ERR_ARG
+ * on bad sizes, SPPC_ERR_NAN if (tensor cores) an entry of A has |a| >= 2 or a value
+ * is not finite, SPPC_ERR_TIMEOUT if a device-side wait gave up. */
+#define SPPC_GRAM_TENSOR 1
+#define SPPC_GRAM_DF 2
+sppc_status sppc_block_gram(const double* A, int32_t nblocks, const double* B, int64_t n, int32_t flags, double* G,
+                            void* stream);
 
 /* ---- Learned correction proposal (not in the paper; the continuation of
  * Sec. 5-6 extended by a network's block).  Network: per (row i, Ritz pair j),

@@ -18,7 +18,7 @@ from .build import LIB
 __all__ = [
     "SppcError", "sppc_default_opts", "sppc_create", "sppc_spmm", "sppc_spmm_noalloc", "sppc_spmm_host", "sppc_start", "sppc_correct",
     "sppc_rayleigh_ritz", "sppc_refine_step", "sppc_solve", "sppc_order_info", "sppc_get_stats", "sppc_get_state", "sppc_get_layout",
-    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "sppc_small_syev", "EXPORTED_SYMBOLS", "STATUS",
+    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "sppc_small_syev", "sppc_block_gram", "EXPORTED_SYMBOLS", "STATUS",
 ]
 
 STATUS = {0: "SPPC_OK", 1: "SPPC_ERR_ARG", 2: "SPPC_ERR_NOT_SYMMETRIC", 3: "SPPC_ERR_LEVELS", 4: "SPPC_ERR_OOM",
@@ -52,7 +52,7 @@ class Opts(ctypes.Structure):
                 ("minres_deflate", ctypes.c_int32), ("small_degree", ctypes.c_int32),
                 ("switch_stall", ctypes.c_double), ("minres_ctas", ctypes.c_int32),
                 ("spin_cap", ctypes.c_int32), ("value_rounding", ctypes.c_int32), ("minres_fp32", ctypes.c_int32),
-                ("minres_fp32_tol", ctypes.c_double)]
+                ("minres_fp32_tol", ctypes.c_double), ("tensor_gram", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -91,6 +91,7 @@ _SIGS = {
     "sppc_last_error": (ctypes.c_char_p, [_VP]),
     "sppc_kernel_launches": (_I64, []),
     "sppc_small_syev": (_I32, [_VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP]),
+    "sppc_block_gram": (_I32, [_VP, _I32, _VP, _I64, _I32, _VP, _VP]),
     "sppc_set_proposal": (_I32, [_VP, _VP, _VP, _VP]),
     "sppc_proposal_samples": (_I32, [_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
     "sppc_mlp_forward": (_I32, [_VP, _VP, _I64, _I32, _VP, _VP]),
@@ -287,6 +288,22 @@ def sppc_small_syev(S, nev: int, stream=None):
     _check(None, _lib.sppc_small_syev(S.data_ptr(), m, m, int(nev), theta.data_ptr(), V.data_ptr(), int(nev),
                                       _stream(stream)))
     return theta, V
+
+
+def sppc_block_gram(A, B, tensor: bool = False, df: bool = False, stream=None):
+    """G = A^T B for A a torch CUDA float64 tensor (nblocks, n, 8) and B (n, 8):
+    returns G (8 nblocks, 8).  tensor: on the tensor cores (|A| < 2 required);
+    df: in double-float slots.  Synchronises the stream."""
+    import torch
+    A = A.contiguous()
+    B = B.contiguous()
+    nb, n = int(A.shape[0]), int(A.shape[1])
+    assert A.dtype == torch.float64 and B.dtype == torch.float64 and A.is_cuda and B.is_cuda
+    assert tuple(A.shape) == (nb, n, 8) and tuple(B.shape) == (n, 8)
+    G = torch.empty(8 * nb, 8, dtype=torch.float64, device=A.device)
+    flags = (1 if tensor else 0) | (2 if df else 0)
+    _check(None, _lib.sppc_block_gram(A.data_ptr(), nb, B.data_ptr(), n, flags, G.data_ptr(), _stream(stream)))
+    return G
 
 
 def _f32_dev(t, n=None):

@@ -1104,6 +1104,15 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
   return SPPC_OK;
 }
 
+// Gram product Q^T B against basis blocks (Eq. blkGS, Eq. proj): on the tensor
+// cores with opts.tensor_gram and 8-column blocks (error flag in dStatus[8],
+// read with the orthogonalisation's status), else on the CUDA cores.
+cudaError_t qgram(sppc_ctx* h, const BlockList& Qs, const float2* B, double* out, cudaStream_t s) {
+  if (h->opt.tensor_gram && h->kp == 8)
+    return gram_tc(Qs, B, 0, h->n, out, h->partials, h->partial_cap, h->f64, h->dStatus + 8, s);
+  return gram(Qs, B, h->kp, 0, h->n, out, h->partials, h->partial_cap, h->f64, s);
+}
+
 // ------------------------------------------------------- Rayleigh-Ritz core
 // Rayleigh-Ritz on blocks 0..p: border the projected matrix with Q^T W_p (Eq.
 // proj), its nev = min(2k, m) lowest eigenpairs (the first k are the Ritz pairs;
@@ -1115,7 +1124,7 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
-  CK(gram(blocks(h->Q, n, kp, 0, p + 1), blk(h->W, n, kp, p), kp, 0, n, h->dGram, h->partials, h->partial_cap, h->f64, s));
+  CK(qgram(h, blocks(h->Q, n, kp, 0, p + 1), blk(h->W, n, kp, p), h->dGram, s));
   k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, p, k, kp, h->dHt, h->mmax); count_launch();
   CK(cudaGetLastError());
   const int m = (p + 1) * k;
@@ -1174,7 +1183,7 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   float2* c = h->dCoef;
   BlockList Qs = blocks(h->Q, n, kp, 0, p);
   const int nc = p * kp * kp;
-  CK(gram(Qs, src, kp, 0, n, h->dC1, h->partials, h->partial_cap, h->f64, s));
+  CK(qgram(h, Qs, src, h->dC1, s));
   k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig, h->f64); count_launch();
   CK(cudaGetLastError());
   CK(update(h->T1, src, c + kOnes, Qs, h->dCoefBig, kp, 0, n, h->f64, s));
@@ -1189,7 +1198,7 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   for (int j = 0; j < k; ++j) again |= !(dd[kp + j] >= 0.25 * dd[j]);  // ||Phi_j|| < ||src_j|| / 2
   h->stats.reorth_passes += again ? 1 : 0;
   if (again) {
-    CK(gram(Qs, h->T1, kp, 0, n, h->dC2, h->partials, h->partial_cap, h->f64, s));
+    CK(qgram(h, Qs, h->T1, h->dC2, s));
     k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig, h->f64); count_launch();
     CK(cudaGetLastError());
     CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, h->f64, s));
@@ -1209,11 +1218,15 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   CK(update(q, nullptr, nullptr, one(h->T2), h->dRinv, kp, 0, n, h->f64, s));
   k_recycle_coefs<<<1, 256, 0, s>>>(h->dC1, p, kp, h->dR2, h->dR1, h->dRecycle, h->f64); count_launch();
   CK(cudaGetLastError());
-  int st[2] = {0, 0}, tmo = 0;
+  int st[2] = {0, 0}, tmo = 0, tcf = 0;
   CK(cudaMemcpyAsync(st, h->dStatus, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
   CK(spmm_tma_read_timeout(h->H, &tmo, s));
+  if (h->opt.tensor_gram) CK(cudaMemcpyAsync(&tcf, h->dStatus + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (tmo) return fail(h, SPPC_ERR_TIMEOUT, "SpMM: a shared-memory pipeline wait timed out");
+  if (tcf) CK(cudaMemsetAsync(h->dStatus + 8, 0, sizeof(int), s));  // reported once
+  if (tcf & 2) return fail(h, SPPC_ERR_TIMEOUT, "tensor-core Gram: a pipeline wait timed out");
+  if (tcf & 1) return fail(h, SPPC_ERR_NAN, "tensor-core Gram: a basis entry is not finite (or |q| >= 2)");
   if (st[0] || st[1])
     return fail(h, SPPC_ERR_BREAKDOWN, "CholeskyQR breakdown appending block %d (rank-deficient block)", p);
   return SPPC_OK;
@@ -1243,8 +1256,7 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
     CK(cudaMemcpyAsync(h->W, blk(h->Psi, n, kp, 2), sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
   }
   for (int b = 0; b < 2; ++b) {
-    CK(gram(blocks(h->Q, n, kp, 0, b + 1), blk(h->W, n, kp, b), kp, 0, n, h->dGram, h->partials, h->partial_cap, h->f64,
-            s));
+    CK(qgram(h, blocks(h->Q, n, kp, 0, b + 1), blk(h->W, n, kp, b), h->dGram, s));
     k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, b, k, kp, h->dHt, h->mmax); count_launch();
     CK(cudaGetLastError());
   }
@@ -1707,6 +1719,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->value_rounding = 0;
   o->minres_fp32 = 0;
   o->minres_fp32_tol = 1e-6;
+  o->tensor_gram = 0;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -1722,6 +1735,48 @@ sppc_status sppc_small_syev(const double* S, int32_t m, int32_t lds, int32_t nev
     return fail(nullptr, SPPC_ERR_ARG, "sppc_small_syev: bad arguments (1 <= m <= 144, 1 <= nev <= min(16, m))");
   const cudaError_t e = syev_lowest(S, lds, m, nev, theta, V, ldv, false, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_small_syev: %s", cudaGetErrorString(e));
+  return SPPC_OK;
+}
+
+sppc_status sppc_block_gram(const double* A, int32_t nblocks, const double* B, int64_t n, int32_t flags, double* G,
+                            void* stream) {
+  if (((!A || !B) && n > 0) || !G || nblocks < 1 || nblocks > kMaxBlocks || n < 0 || n >= ((int64_t)1 << 40) ||
+      (flags & ~3))
+    return fail(nullptr, SPPC_ERR_ARG, "sppc_block_gram: bad arguments (1 <= nblocks <= %d, flags in 0..3)",
+                kMaxBlocks);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool tc = (flags & 1) != 0, df = (flags & 2) != 0;
+  // partial sums: the CUDA-core Gram cuts at >= 2048 rows when its finer cut does not fit
+  const int64_t cap = ((n + 1023) / 1024 + 1) * (int64_t)nblocks * 64;
+  float2* partials = nullptr;
+  float2* Adf = nullptr;
+  int* err = nullptr;
+  cudaError_t e = cudaMalloc(&partials, sizeof(float2) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess && df) e = cudaMalloc(&Adf, sizeof(float2) * ((size_t)nblocks + 1) * (size_t)(n ? n : 1) * 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  BlockList L;
+  L.n = nblocks;
+  const float2* Bs = reinterpret_cast<const float2*>(B);
+  if (e == cudaSuccess && df) {
+    for (int a = 0; a <= nblocks && e == cudaSuccess; ++a)
+      e = f64_to_df(a < nblocks ? A + (int64_t)a * n * 8 : B, 8, 8, Adf + (int64_t)a * n * 8, 8, 0, n, false, s);
+    Bs = Adf + (int64_t)nblocks * n * 8;
+  }
+  for (int a = 0; a < nblocks; ++a)
+    L.p[a] = df ? Adf + (int64_t)a * n * 8 : reinterpret_cast<const float2*>(A + (int64_t)a * n * 8);
+  if (e == cudaSuccess)
+    e = tc ? gram_tc(L, Bs, 0, n, G, partials, cap, !df, err, s) : gram(L, Bs, 8, 0, n, G, partials, cap, !df, s);
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(partials);
+  cudaFree(err);
+  cudaFree(Adf);
+  if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_block_gram: %s", cudaGetErrorString(e));
+  if (flag & 2) return fail(nullptr, SPPC_ERR_TIMEOUT, "sppc_block_gram: a tensor-core pipeline wait timed out");
+  if (flag & 1)
+    return fail(nullptr, SPPC_ERR_NAN, "sppc_block_gram: an entry of A has |a| >= 2, or a value is not finite");
   return SPPC_OK;
 }
 
@@ -1795,6 +1850,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     return fail(nullptr, SPPC_ERR_ARG, "opts.minres_fp32 needs double-float slots (precision 0, 1 or 2)");
   if (opt.minres_fp32 && !(opt.minres_fp32_tol > 0.0 && opt.minres_fp32_tol < 1.0))
     return fail(nullptr, SPPC_ERR_ARG, "opts.minres_fp32_tol must be in (0, 1)");
+  if (opt.tensor_gram != 0 && opt.tensor_gram != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.tensor_gram must be 0 or 1");
   if (opt.precision > 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
@@ -2137,6 +2193,7 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     if (h->opt.hybrid == 1) A(&h->Tspare, (size_t)n * kp);
     A(&h->dCoefBig, (size_t)kMaxBlocks * 64);
     if (e == cudaSuccess) e = dalloc(h, &h->dStatus, 64);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dStatus, 0, sizeof(int) * 64, h->stream);
     if (e == cudaSuccess) e = dalloc(h, &h->dBar, 4);
     h->partial_cap = ((n + 2047) / 2048 + 1) * (int64_t)kMaxBlocks * 64;
     A(&h->partials, (size_t)h->partial_cap);

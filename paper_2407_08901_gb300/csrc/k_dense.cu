@@ -437,6 +437,12 @@ cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_
   return finish(partials, nchunks, nout, out, f64, s);
 }
 
+// The finishing sum of gram() for partial results written by another kernel
+// (k_gram_tc.cu): out[o] = sum over c of partials[c * nout + o], fixed order.
+cudaError_t gram_finish(const float2* partials, int64_t nchunks, int nout, double* out, bool f64, cudaStream_t s) {
+  return finish(partials, nchunks, nout, out, f64, s);
+}
+
 cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef, int kp,
                    int64_t r0, int64_t r1, bool f64, cudaStream_t s) {
   if (r1 <= r0) return cudaSuccess;

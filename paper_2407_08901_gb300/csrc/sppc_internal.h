@@ -182,6 +182,18 @@ cudaError_t spmm_tma_read_timeout(const SellDev& A, int* flag, cudaStream_t s);
 // Gram: out[(a*kp+i)*kp + j] = sum_{r in [r0,r1)} A_a[r][i] * B[r][j]  (FP64 out)
 cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_t r1, double* out,
                  float2* partials, int64_t partial_cap, bool f64, cudaStream_t s);
+// Fixed-order sum of per-CTA partial results (nchunks x nout slots) into FP64 out.
+cudaError_t gram_finish(const float2* partials, int64_t nchunks, int nout, double* out, bool f64, cudaStream_t s);
+
+// ---- k_gram_tc.cu: gram() for kp = 8 on the tensor cores, for A with entries
+// |a| < 2 (the orthonormal basis): exact FP16 digit products of a 62-bit fixed
+// point split, FP64-grade result.  *err (device, sticky) gets bit 0 when an entry
+// of A is out of range or a value is not finite, bit 1 when a wait timed out.
+// partials needs ceil(rows / per) * 64 * min(A.n, 16) slots (gram_tc_geometry).
+cudaError_t gram_tc(const BlockList& A, const float2* B, int64_t r0, int64_t r1, double* out, float2* partials,
+                    int64_t partial_cap, bool f64, int* err, cudaStream_t s);
+void gram_tc_geometry(int64_t rows, int sms, int64_t* per, int64_t* ctas);
+
 // Update: Y[r][j] = alpha[j] X[r][j] + sum_a sum_i A_a[r][i] coef[(a*kp+i)*kp + j]
 // (coef double-float on device; X may be null; Y may alias X but no block of A).
 cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef,
