@@ -76,6 +76,8 @@ def parse_args():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-matrix workload")
     ap.add_argument("--no-c3", action="store_true", help="skip the n = 2e7 mixed-precision workload (config 3)")
+    ap.add_argument("--tensor-gram", type=int, default=0, choices=[0, 1],
+                    help="Gram products against the basis on the tensor cores (opts.tensor_gram)")
     ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0],
                     help="value format of the --profile spmm / solve / minres runs: -1 native FP64, 0 double-float")
     ap.add_argument("--profile", default="none", choices=["none", "spmm", "spmm32", "spmm16", "solve", "minres", "learned"],
@@ -380,7 +382,7 @@ def run_ours(args):
         return (e0.elapsed_time(e1),) + tuple(out)
 
     # the headline: the method in native FP64 (every value an IEEE double, DFMA)
-    opts = solve_opts(S, len(w.level_sizes), timing=1, precision=-1)
+    opts = solve_opts(S, len(w.level_sizes), timing=1, precision=-1, tensor_gram=args.tensor_gram)
     h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts, stream=stream)
     for _ in range(args.warmup):
         timed_solve(h)
@@ -457,8 +459,8 @@ def run_ours(args):
     if rank == 0 and world == 1:
         # the same method in double-float (two fp32 words, ~48 bits, on the FP32
         # pipes): time, agreement with the FP64 run, and its SpMM against HBM
-        hd = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, solve_opts(S, len(w.level_sizes), timing=1),
-                           stream=stream)
+        hd = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k,
+                           solve_opts(S, len(w.level_sizes), timing=1, tensor_gram=args.tensor_gram), stream=stream)
         timed_solve(hd)
         dts, dstats = [], []
         for _ in range(3):
@@ -819,7 +821,7 @@ def run_profile(args):
         torch.cuda.synchronize()
         print(f"profile minres: {w.name}, orders {st['orders']}, MINRES iterations {st['minres_iters']}", flush=True)
     else:
-        opts = solve_opts(S, len(w.level_sizes), precision=args.precision)
+        opts = solve_opts(S, len(w.level_sizes), precision=args.precision, tensor_gram=args.tensor_gram)
         h = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, opts)
         conv, th, rs, st = S.sppc_solve(h, k, tol=TOL)
         torch.cuda.synchronize()

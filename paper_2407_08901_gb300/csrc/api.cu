@@ -109,6 +109,8 @@ struct sppc_ctx {
          *dR2 = nullptr, *dTheta = nullptr, *dV = nullptr, *dDots = nullptr, *dS = nullptr;
   float2 *dCoef = nullptr, *dRinv = nullptr, *dRecycle = nullptr, *dY = nullptr, *dCoefBig = nullptr;
   int* dStatus = nullptr;
+  unsigned char* Qd = nullptr;  // opts.tensor_gram: FP16 digit tiles of the basis blocks (k_gram_tc.cu)
+  uint64_t qd_valid = 0;        // bit a: Qd holds the digits of basis block a as it stands
   unsigned* dBar = nullptr;
   float2* partials = nullptr;
   int64_t partial_cap = 0;
@@ -1104,13 +1106,23 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
   return SPPC_OK;
 }
 
-// Gram product Q^T B against basis blocks (Eq. blkGS, Eq. proj): on the tensor
-// cores with opts.tensor_gram and 8-column blocks (error flag in dStatus[8],
-// read with the orthogonalisation's status), else on the CUDA cores.
-cudaError_t qgram(sppc_ctx* h, const BlockList& Qs, const float2* B, double* out, cudaStream_t s) {
-  if (h->opt.tensor_gram && h->kp == 8)
-    return gram_tc(Qs, B, 0, h->n, out, h->partials, h->partial_cap, h->f64, h->dStatus + 8, s);
-  return gram(Qs, B, h->kp, 0, h->n, out, h->partials, h->partial_cap, h->f64, s);
+// Gram product [Q_0 .. Q_{nq-1}]^T B (Eq. blkGS, Eq. proj): on the tensor cores
+// with opts.tensor_gram and 8-column blocks, else on the CUDA cores.  The tensor
+// path reads the blocks' digit tiles, cut here for every block whose tiles are
+// stale (h->qd_valid; every write of a basis block clears its bit).  Error flag
+// in dStatus[8], read with the orthogonalisation's status.
+cudaError_t qgram(sppc_ctx* h, int nq, const float2* B, double* out, cudaStream_t s) {
+  const int64_t n = h->n;
+  if (h->Qd && h->kp == 8) {
+    for (int a = 0; a < nq; ++a) {
+      if ((h->qd_valid >> a) & 1ull) continue;
+      cudaError_t e = qcut(blk(h->Q, n, 8, a), n, qdigits_block(h->Qd, n, a), h->f64, h->dStatus + 8, s);
+      if (e != cudaSuccess) return e;
+      h->qd_valid |= 1ull << a;
+    }
+    return gram_tc(h->Qd, nq, B, n, out, h->partials, h->partial_cap, h->f64, h->dStatus + 8, h->dStatus + 16, s);
+  }
+  return gram(blocks(h->Q, n, h->kp, 0, nq), B, h->kp, 0, n, out, h->partials, h->partial_cap, h->f64, s);
 }
 
 // ------------------------------------------------------- Rayleigh-Ritz core
@@ -1124,7 +1136,7 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
   cudaStream_t s = h->stream;
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
-  CK(qgram(h, blocks(h->Q, n, kp, 0, p + 1), blk(h->W, n, kp, p), h->dGram, s));
+  CK(qgram(h, p + 1, blk(h->W, n, kp, p), h->dGram, s));
   k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, p, k, kp, h->dHt, h->mmax); count_launch();
   CK(cudaGetLastError());
   const int m = (p + 1) * k;
@@ -1183,7 +1195,7 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   float2* c = h->dCoef;
   BlockList Qs = blocks(h->Q, n, kp, 0, p);
   const int nc = p * kp * kp;
-  CK(qgram(h, Qs, src, h->dC1, s));
+  CK(qgram(h, p, src, h->dC1, s));
   k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig, h->f64); count_launch();
   CK(cudaGetLastError());
   CK(update(h->T1, src, c + kOnes, Qs, h->dCoefBig, kp, 0, n, h->f64, s));
@@ -1198,7 +1210,7 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   for (int j = 0; j < k; ++j) again |= !(dd[kp + j] >= 0.25 * dd[j]);  // ||Phi_j|| < ||src_j|| / 2
   h->stats.reorth_passes += again ? 1 : 0;
   if (again) {
-    CK(qgram(h, Qs, h->T1, h->dC2, s));
+    CK(qgram(h, p, h->T1, h->dC2, s));
     k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig, h->f64); count_launch();
     CK(cudaGetLastError());
     CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, h->f64, s));
@@ -1210,6 +1222,7 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
     CK(cudaMemcpyAsync(dd + kp, h->dDots, sizeof(double) * kp, cudaMemcpyDeviceToHost, s));
   }
   float2* q = blk(h->Q, n, kp, p);
+  h->qd_valid &= ~(1ull << p);  // block p is rewritten below
   CK(gram(one(h->T1), h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, h->f64, s));
   CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR1, h->dRinv, h->dStatus, h->f64, s));
   CK(update(h->T2, nullptr, nullptr, one(h->T1), h->dRinv, kp, 0, n, h->f64, s));
@@ -1248,6 +1261,7 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
               s));
   }
   CK(cudaMemcpyAsync(h->Q, h->Psi, sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
+  h->qd_valid = 0;
   if (fresh_products) {
     // W = H Q recomputed (mixed precision: replaces products made in FP32)
     for (int b = 0; b < 2; ++b) CKS(big_spmm(h, blk(h->Q, n, kp, b), blk(h->W, n, kp, b), kp));
@@ -1256,7 +1270,7 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
     CK(cudaMemcpyAsync(h->W, blk(h->Psi, n, kp, 2), sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
   }
   for (int b = 0; b < 2; ++b) {
-    CK(qgram(h, blocks(h->Q, n, kp, 0, b + 1), blk(h->W, n, kp, b), h->dGram, s));
+    CK(qgram(h, b + 1, blk(h->W, n, kp, b), h->dGram, s));
     k_assemble_ht<<<1, 256, 0, s>>>(h->dGram, b, k, kp, h->dHt, h->mmax); count_launch();
     CK(cudaGetLastError());
   }
@@ -1487,6 +1501,7 @@ sppc_status rmm_run(sppc_ctx* h, double tol) {
   Lx.n = Lr.n = d;
   float2* hx[8];
   float2* hr[8];
+  h->qd_valid = 0;  // the RMM-DIIS history overwrites the basis blocks
   for (int a = 0; a < d; ++a) {
     hx[a] = blk(h->Q, n, kp, a);
     hr[a] = blk(h->W, n, kp, a);
@@ -1752,7 +1767,7 @@ sppc_status sppc_block_gram(const double* A, int32_t nblocks, const double* B, i
   float2* Adf = nullptr;
   int* err = nullptr;
   cudaError_t e = cudaMalloc(&partials, sizeof(float2) * cap);
-  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int) * 16);  // flag, then B's column exponents
   if (e == cudaSuccess && df) e = cudaMalloc(&Adf, sizeof(float2) * ((size_t)nblocks + 1) * (size_t)(n ? n : 1) * 8);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
   BlockList L;
@@ -1765,14 +1780,20 @@ sppc_status sppc_block_gram(const double* A, int32_t nblocks, const double* B, i
   }
   for (int a = 0; a < nblocks; ++a)
     L.p[a] = df ? Adf + (int64_t)a * n * 8 : reinterpret_cast<const float2*>(A + (int64_t)a * n * 8);
+  unsigned char* Ad = nullptr;
+  if (e == cudaSuccess && tc)
+    e = cudaMalloc(&Ad, (size_t)((nblocks + 15) / 16) * (size_t)qdigits_group_bytes(n) + 16);
+  for (int a = 0; a < nblocks && tc && e == cudaSuccess; ++a) e = qcut(L.p[a], n, qdigits_block(Ad, n, a), !df, err, s);
   if (e == cudaSuccess)
-    e = tc ? gram_tc(L, Bs, 0, n, G, partials, cap, !df, err, s) : gram(L, Bs, 8, 0, n, G, partials, cap, !df, s);
+    e = tc ? gram_tc(Ad, nblocks, Bs, n, G, partials, cap, !df, err, err + 8, s)
+           : gram(L, Bs, 8, 0, n, G, partials, cap, !df, s);
   int flag = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(partials);
   cudaFree(err);
   cudaFree(Adf);
+  cudaFree(Ad);
   if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_block_gram: %s", cudaGetErrorString(e));
   if (flag & 2) return fail(nullptr, SPPC_ERR_TIMEOUT, "sppc_block_gram: a tensor-core pipeline wait timed out");
   if (flag & 1)
@@ -2155,6 +2176,8 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       if (e == cudaSuccess) e = dalloc(h, p, c);
     };
     A(&h->Q, nb);
+    if (h->opt.tensor_gram && kp == 8 && e == cudaSuccess)
+      e = dalloc(h, &h->Qd, (size_t)((h->pmax + 1 + 15) / 16) * (size_t)qdigits_group_bytes(n));
     A(&h->W, nb);
     A(&h->Psi, nb);
     A(&h->HPsi, (size_t)n * kp);
@@ -2286,6 +2309,7 @@ sppc_status sppc_start(sppc_handle h, double* theta, double* resid, void* stream
   const int kp = h->kp;
   const int64_t n = h->n;
   // Q^(0) = Psi^(0) = [psi_hat; 0] (Eq. EP_small), W_0 = H Q^(0)
+  h->qd_valid = 0;
   CK(fill_zero(h->Q, n * kp, s));
   CK(cudaMemcpyAsync(h->Q, h->psi_hat, sizeof(float2) * h->n1 * kp, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->Psi, h->Q, sizeof(float2) * n * kp, cudaMemcpyDeviceToDevice, s));

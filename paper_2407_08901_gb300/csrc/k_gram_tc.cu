@@ -3,33 +3,49 @@
 //
 // The projections of block Gram-Schmidt (Eq. blkGS) and the border of the
 // projected matrix (Eq. proj) are Gram products G = A^T B with A = the basis
-// blocks [Q_0 ... Q_{na-1}] (n x M, M = 8 na <= 128, entries |a| < 2 because the
-// columns are orthonormal) and B one n x 8 block.  Both come as value slots
-// (double-float pairs or IEEE doubles).  Scheme (the splitting of Ozaki et al.
-// into exact integer products):
-//   - a -> sign * X_a, X_a = round(|a| 2^61) < 2^62 (fixed point, one scale for
-//     all of A); b in column j -> sign * X_b, X_b = round(|b| 2^(61 - f_j)) with
-//     2^f_j > max |b_j| over the CTA's rows;
-//   - X = sum_s d_s 256^(7 - s) with bytes d_0 (top) .. d_7, so that
-//     a b = sum_{s,t} (+-d_s)(+-c_t) 2^(f_j - 10 - 8 (s + t));
-//   - each byte is exact in FP16, each byte product exact in the FP32
-//     accumulator, and a sum of 256 of them (< 2^24) exact as well;
-//   - levels L = s + t <= 8 are kept: the dropped part of a product is below
-//     2^(f_j - 63), against the 2^-53 |a| |b| of one FP64 rounding.
-// Per CTA (one per SM, 256 threads, rows [c0, c1)) and per 32-row chunk: the
-// threads cut A's and B's values into FP16 digits written to shared memory in
-// the canonical K-major no-swizzle layout (8-row x 16-byte core matrices); one
-// thread issues, for each byte s of A, D_s (+)= A_s^T [B_0 .. B_{8-s}] (M = 128,
-// N = 8 (9 - s) rounded up to 16, two K = 16 steps) into tensor memory and
-// commits to the stage's mbarrier.  Two stages alternate, so the digits of one
-// chunk are cut while the MMAs of the previous one run.  Every 256 rows the
-// accumulators are read back (tcgen05.ld) and added into 64-bit integers, three
-// levels to a word (exact); the next MMA overwrites them.  At the end each
-// column's words are scaled and added in FP64 and written as the CTA's partial
-// result for the fixed-order cross-CTA sum of k_dense.cu.
-// Errors: an entry of A with |a| >= 2 (or a non-finite value) sets bit 0 of
-// *err, a timed-out wait (about a second) bit 1; after a time-out the kernel
-// still waits (bounded) for its committed MMAs and frees its tensor memory.
+// blocks [Q_0 ... Q_{na-1}] (n x 8 na, entries |q| < 2 because the columns are
+// orthonormal) and B one n x 8 block, both in value slots (double-float pairs or
+// IEEE doubles).  Scheme (the splitting of Ozaki et al. into exact integer
+// products):
+//   - q -> sign * X_q, X_q = round(|q| 2^61) < 2^62 (fixed point, one scale for
+//     all of Q); b in column j -> sign * X_b, X_b = round(|b| 2^(61 - f_j)) with
+//     2^f_j > max |b_j| over all rows;
+//   - X = sum_s d_s 256^(7 - s) with balanced digits d_s in [-128, 127] (the
+//     bytes of X + 0x80...80, each minus 128), so that
+//     q b = sum_{s,t} (+-d_s)(+-c_t) 2^(f_j - 10 - 8 (s + t));
+//   - each digit is exact in FP16 and each digit product (|.| <= 2^14) exact in
+//     the FP32 accumulator; the sum over one level L = s + t (at most 8 pairs)
+//     and 64 rows stays below 2^23, exact as well;
+//   - levels L <= 9 are kept: the dropped part of a product is below
+//     2^(f_j - 71), far under the 2^-53 |q| |b| of one FP64 rounding.
+//
+// All MMAs of a chunk accumulate into one tensor-memory region D (128 lanes =
+// basis columns, 80 columns = (level L, B column j)): with C the tile of B's
+// digits padded by zero tiles, C[7 + t] = digit t of the chunk's B rows, the
+// window of C starting at tile 7 - s holds, at level L, B's digit L - s, so
+// D += Q_s^T window_s over the Q digits s gives every level at once.  (An MMA
+// into a different region than the previous one costs several hundred cycles
+// on this part; consecutive MMAs into one region issue back to back.)
+//
+// The basis is cut once per block (k_qcut, when a Gram first needs the block):
+// its digits are stored as FP16 in exactly the shared-memory order the MMA
+// reads.  Per group of 16 blocks and 16-row chunk c, block a's 2 KB lie at
+// (c * 16 + a) * 2048: digit plane s at + 256 s, one 32-byte-swizzled 8 x 16
+// core-matrix atom (row i = basis column at 32 i, its two 16-byte halves = rows
+// 0-7 and 8-15 of the chunk, swapped when i >= 4).  A Gram needs no
+// per-element work on Q: per chunk one bulk copy (cp.async.bulk) brings the na
+// blocks' 2 KB pieces, another the chunk's 16 x 8 slots of B.  Per CTA (one per
+// SM, 256 threads) six stages rotate: the copies of chunks k + 1 .. k + 4 fly
+// while 128 threads cut B's values of chunk k (in shared memory) into C and one
+// thread issues the chunk's eight MMAs (M = 128, N = 80, K = 16), committed to
+// the stage's mbarrier.  B's column exponents f_j come from a separate pass over
+// B (k_colexp).  Every 64 rows D is read back (tcgen05.ld) and added into 64-bit
+// integers, three levels to a word (exact).  At the end each column's words are
+// scaled and added in FP64 and written as the CTA's partial result for the
+// fixed-order cross-CTA sum of k_dense.cu.
+// Errors: |q| >= 2 or a non-finite value sets bit 0 of *err, a timed-out wait
+// (about a second) bit 1; after a time-out the kernel still waits (bounded) for
+// its copies and MMAs in flight and frees its tensor memory.
 #include <cstdint>
 
 #include "sppc_internal.h"
@@ -40,42 +56,43 @@ namespace sppc {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int kTcRows = 32;                      // rows (K) per chunk
-constexpr int kTcGroupChunks = 8;                // chunks summed in tensor memory before a read-back
-constexpr int kATile = 128 * kTcRows * 2;        // one digit plane of A: 128 (M) x 32 (K) FP16
-constexpr int kBTile = 64 * kTcRows * 2;         // B: 64 (8 digits x 8 columns) x 32 FP16
-constexpr int kStage = 8 * kATile + kBTile;      // 69,632 bytes
-constexpr int kTcSmem = 2 * kStage;              // 139,264 bytes: one CTA per SM
-constexpr int kTmemCols = 512;
-constexpr int kMaxLevel = 8;
-constexpr int kAShift = 61;                      // X_a = round(|a| 2^61)
+constexpr int kTcRows = 16;                      // rows (K) per chunk: one K = 16 MMA step
+constexpr int kTcGroupChunks = 4;                // chunks summed in tensor memory before a read-back (64 rows)
+constexpr int kAtom = 256;                       // one 8 x 16 FP16 tile (a 32-byte-swizzled atom)
+constexpr int kBlockChunk = 8 * kAtom;           // one block's digits of one chunk: 8 planes
+constexpr int kGroupChunk = 16 * kBlockChunk;    // a 16-block group's digits of one chunk: 32 KB
+constexpr int kABytes = kGroupChunk;             // A tiles of a stage
+constexpr int kBRaw = kTcRows * 8 * 8;           // B's 16 x 8 slots of a chunk: 1 KB
+constexpr int kCTiles = 17;                      // C: tiles 0-6 and 15-16 zero, 7 + t = B's digit t
+constexpr int kStageBytes = kABytes + kBRaw + kCTiles * kAtom;  // 38,144
+constexpr int kStages = 6;                       // copies run kStages - 2 chunks ahead
+constexpr int kTcSmem = kStages * kStageBytes + 1024;   // + alignment slack: one CTA per SM
+constexpr int kLevels = 10;                      // digit levels L = s + t kept (0 .. 9)
+constexpr int kDCols = 8 * kLevels;              // D columns (L, j): the MMA's N
+constexpr int kTmemCols = 128;
+constexpr int kQShift = 61;                      // X_q = round(|q| 2^61)
 constexpr long long kWaitClocks = 1ll << 31;     // about a second
-
-// N of the MMA for A's digit s (B columns t * 8 + j with s + t <= 8, rounded up
-// to a multiple of 16) and its first tensor-memory column.
-__host__ __device__ constexpr int tc_n(int s) {
-  return (8 * (9 - s < 8 ? 9 - s : 8) + 15) / 16 * 16;
-}
-__host__ __device__ constexpr int tc_col(int s) { return s == 0 ? 0 : tc_col(s - 1) + tc_n(s - 1); }
-static_assert(tc_col(8) <= kTmemCols, "tensor-memory columns");
+static_assert(kDCols % 16 == 0 && kDCols <= kTmemCols, "D columns");
+static_assert(7 + kLevels <= kCTiles, "C windows");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Byte offset of element (row, k) in a K-major tile of 32 K columns: core
-// matrices of 8 rows x 8 elements (16 bytes a row, 128 bytes a core), cores
-// adjacent in K 128 bytes apart, 8-row groups 512 bytes apart.
-__host__ __device__ constexpr uint32_t kmajor_off(int row, int k) {
-  return static_cast<uint32_t>(((row >> 3) * 4 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+// Byte offset of element (row i, k) in a 32-byte-swizzled 8 x 16 FP16 atom:
+// rows 32 bytes apart, 16-byte halves k / 8 swapped for rows 4-7 (address bit 4
+// XOR bit 7, the 32-byte swizzle pattern; atoms are 256-byte aligned).
+__host__ __device__ constexpr uint32_t atom_off(int i, int k) {
+  return static_cast<uint32_t>(i * 32 + (((k >> 3) ^ (i >> 2)) & 1) * 16 + (k & 7) * 2);
 }
 
-// Shared-memory matrix descriptor (tcgen05): start address, leading byte offset
-// (cores adjacent in K) 128, stride byte offset (8-row groups) 512, descriptor
-// version 1, base offset 0, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(128 >> 4) << 16) |
-         (static_cast<uint64_t>(512 >> 4) << 32) | (1ull << 46);
+// Shared-memory matrix descriptor (tcgen05) of a K-major operand made of
+// 32-byte-swizzled atoms `sbo` bytes apart along M/N: start address, leading
+// byte offset 16 (unused by swizzled K-major layouts), stride byte offset,
+// descriptor version 1, base offset 0, swizzle mode 6 (32 bytes).
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr, uint32_t sbo) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (1ull << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (6ull << 61);
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), FP16 A
@@ -100,7 +117,7 @@ __device__ __forceinline__ bool mbar_done(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t"
       "}"
       : "=r"(ok)
@@ -112,6 +129,7 @@ __device__ __forceinline__ bool mbar_done(uint32_t bar, uint32_t parity) {
 // Waits for the completion of the mbarrier phase of the given parity; false
 // after about a second.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_done(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_done(bar, parity)) {
     if (clock64() - t0 > kWaitClocks) return false;
@@ -119,8 +137,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
   return true;
 }
 
-// round(|w| 2^shift) for one FP32 word, as a signed 64-bit integer; false if
-// |w| 2^shift >= 2^62 or w is not finite.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// round(|w| 2^shift) for one FP32 word, signed; false if |w| 2^shift >= 2^62 or
+// w is not finite.
 __device__ __forceinline__ bool f32_fixed(float w, int shift, long long& x) {
   const uint32_t bits = __float_as_uint(w);
   const int ex = static_cast<int>((bits >> 23) & 0xFF);
@@ -149,7 +173,7 @@ __device__ __forceinline__ bool f32_fixed(float w, int shift, long long& x) {
 template <bool F64>
 __device__ __forceinline__ bool to_fixed(float2 v, int shift, uint64_t& x, bool& neg) {
   if constexpr (F64) {
-    const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(slot_d(v)));
+    const uint64_t bits = (static_cast<uint64_t>(__float_as_uint(v.y)) << 32) | __float_as_uint(v.x);
     neg = (bits >> 63) != 0;
     const int ex = static_cast<int>((bits >> 52) & 0x7FF);
     if (ex == 0x7FF) return false;
@@ -183,9 +207,9 @@ __device__ __forceinline__ bool to_fixed(float2 v, int shift, uint64_t& x, bool&
 template <bool F64>
 __device__ __forceinline__ int exp_bound(float2 v) {
   if constexpr (F64) {
-    const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(slot_d(v)));
-    const int ex = static_cast<int>((bits >> 52) & 0x7FF);
-    if (ex == 0) return (bits << 1) == 0 ? -100000 : -1022;
+    const uint32_t hi = __float_as_uint(v.y);
+    const int ex = static_cast<int>((hi >> 20) & 0x7FF);
+    if (ex == 0) return ((hi << 1) | __float_as_uint(v.x)) == 0 ? -100000 : -1022;
     return ex - 1022;
   } else {
     // |hi + lo| < 2^e whenever |hi| < 2^e (|lo| <= ulp(hi) / 2)
@@ -196,14 +220,16 @@ __device__ __forceinline__ int exp_bound(float2 v) {
   }
 }
 
-// The eight FP16 digits of X (bytes d_0 .. d_7) as four words whose halves hold
-// 1024 + d: E_hi = (d_3, d_1), O_hi = (d_2, d_0), E_lo = (d_7, d_5), O_lo = (d_6, d_4)
-// (low half first).  fma(v, +-1, -+1024) then gives +-d exactly.
+// The eight balanced digits of X as FP16 material: the bytes b_s of
+// X + 0x8080808080808080 (d_s = b_s - 128) in four words whose halves hold
+// 1024 + b: E_hi = (b_3, b_1), O_hi = (b_2, b_0), E_lo = (b_7, b_5),
+// O_lo = (b_6, b_4) (low half first).  fma(v, +-1, -+1152) then gives +-d exactly.
 struct Digits {
   uint32_t w[4];  // E_hi, O_hi, E_lo, O_lo
 };
-__device__ __forceinline__ Digits spread(uint64_t x) {
-  const uint32_t hi = static_cast<uint32_t>(x >> 32), lo = static_cast<uint32_t>(x);
+__device__ __forceinline__ Digits spread_balanced(uint64_t x) {
+  const uint64_t y = x + 0x8080808080808080ull;  // X < 2^62: no carry out of the top byte
+  const uint32_t hi = static_cast<uint32_t>(y >> 32), lo = static_cast<uint32_t>(y);
   Digits d;
   d.w[0] = (hi & 0x00FF00FFu) | 0x64006400u;
   d.w[1] = ((hi >> 8) & 0x00FF00FFu) | 0x64006400u;
@@ -222,12 +248,77 @@ __device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
   return r;
 }
 
-// sign factors of a pair of rows: S = (+-1, +-1), T = (-+1024, -+1024) in FP16
+// sign factors of a pair of values: S = (+-1, +-1), T = (-+1152, -+1152) in FP16
 __device__ __forceinline__ uint32_t sign_s(bool n0, bool n1) {
   return (n0 ? 0xBC00u : 0x3C00u) | ((n1 ? 0xBC00u : 0x3C00u) << 16);
 }
 __device__ __forceinline__ uint32_t sign_t(bool n0, bool n1) {
-  return (n0 ? 0x6400u : 0xE400u) | ((n1 ? 0x6400u : 0xE400u) << 16);
+  return (n0 ? 0x6480u : 0xE480u) | ((n1 ? 0x6480u : 0xE480u) << 16);
+}
+
+// One basis block (n rows x 8 columns of slots) cut into its digit tiles at
+// out (= the group's digits + 2048 a for block a of the group): thread u handles
+// chunk u / 16, rows 8 ((u / 8) % 2) .. + 7 of the chunk, column i = u % 8, and
+// writes 16 bytes (the half (u / 8) % 2 of atom row i) per digit plane.  Rows
+// >= n get zero digits.
+template <bool F64>
+__global__ void __launch_bounds__(256) k_qcut(const float2* __restrict__ Q, int64_t n, int64_t nchunks,
+                                              unsigned char* __restrict__ out, int* __restrict__ err) {
+  const int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (u >= nchunks * 16) return;
+  const int64_t c = u >> 4;
+  const int kq = static_cast<int>((u >> 3) & 1), i = static_cast<int>(u & 7);
+  uint64_t x[8];
+  bool ng[8];
+  bool bad = false;
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr) {
+    const int64_t r = c * kTcRows + kq * 8 + rr;
+    const float2 v = r < n ? Q[r * 8 + i] : make_float2(0.f, 0.f);
+    if (!to_fixed<F64>(v, kQShift, x[rr], ng[rr])) {
+      bad = true;
+      x[rr] = 0;
+    }
+  }
+  Digits dg[8];
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr) dg[rr] = spread_balanced(x[rr]);
+  uint32_t S2[4], T2[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    S2[q] = sign_s(ng[2 * q], ng[2 * q + 1]);
+    T2[q] = sign_t(ng[2 * q], ng[2 * q + 1]);
+  }
+  unsigned char* dst = out + c * kGroupChunk + atom_off(i, kq * 8);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int w = digit_word(s);
+    const uint32_t sel = digit_high(s) ? 0x7632u : 0x5410u;
+    uint4 o;
+    o.x = hfma2(__byte_perm(dg[0].w[w], dg[1].w[w], sel), S2[0], T2[0]);
+    o.y = hfma2(__byte_perm(dg[2].w[w], dg[3].w[w], sel), S2[1], T2[1]);
+    o.z = hfma2(__byte_perm(dg[4].w[w], dg[5].w[w], sel), S2[2], T2[2]);
+    o.w = hfma2(__byte_perm(dg[6].w[w], dg[7].w[w], sel), S2[3], T2[3]);
+    *reinterpret_cast<uint4*>(dst + s * kAtom) = o;
+  }
+  if (bad) atomicOr(err, 1);
+}
+
+// Column exponents of B (n x 8 slots): fexp[j] = max over rows of e with
+// |b| < 2^e (fexp preset to a very negative value).
+template <bool F64>
+__global__ void __launch_bounds__(256) k_colexp(const float2* __restrict__ B, int64_t n, int* __restrict__ fexp) {
+  __shared__ int red[8];
+  if (threadIdx.x < 8) red[threadIdx.x] = -100000;
+  __syncthreads();
+  int e = -100000;
+  const int j = threadIdx.x & 7;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 3);
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 3) + (threadIdx.x >> 3); r < n; r += stride)
+    e = max(e, exp_bound<F64>(B[r * 8 + j]));
+  atomicMax(&red[j], e);
+  __syncthreads();
+  if (threadIdx.x < 8) atomicMax(&fexp[threadIdx.x], red[threadIdx.x]);
 }
 
 // Waits for this thread's tensor-memory loads; the four registers pass through
@@ -236,21 +327,18 @@ __device__ __forceinline__ void tmem_wait4(uint32_t (&v)[4]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3])::"memory");
 }
 
-// Reads back the accumulators of A's digit S for the 32 tensor-memory lanes and
-// the four B columns j0 .. j0 + 3 at taddr (= lane base + tc_col(S) + j0) and
-// adds them, level L = S + t, into acc[j - j0][L / 3] with weight 256^(2 - L % 3).
-template <int S>
-__device__ __forceinline__ void read_digit(uint32_t taddr, long long (&acc)[4][3]) {
-  constexpr int NT = 9 - S < 8 ? 9 - S : 8;  // B digits t with S + t <= 8
+// Reads back D for the 32 tensor-memory lanes and the four B columns j0 .. j0 + 3
+// at taddr (= lane base + j0), every level L, and adds level L into
+// acc[j - j0][L / 3] with weight 256^(2 - L % 3).
+__device__ __forceinline__ void read_levels(uint32_t taddr, long long (&acc)[4][4]) {
 #pragma unroll
-  for (int t = 0; t < NT; ++t) {
+  for (int L = 0; L < kLevels; ++L) {
     uint32_t v[4];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(taddr + static_cast<uint32_t>(t * 8))
+                 : "r"(taddr + static_cast<uint32_t>(8 * L))
                  : "memory");
     tmem_wait4(v);
-    const int L = S + t;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const long long q = static_cast<long long>(__float2int_rn(__uint_as_float(v[e])));
@@ -259,27 +347,41 @@ __device__ __forceinline__ void read_digit(uint32_t taddr, long long (&acc)[4][3
   }
 }
 
+// Qd: the digits of a group of 16 blocks (the first na <= 16 used); B: n x 8
+// slots; fexp: B's column exponents (k_colexp); rows [0, n), CTA x takes rows
+// [x rows_per_cta, ...), rows_per_cta a multiple of 16.
 template <bool F64>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_gram_tc(BlockList A, const float2* __restrict__ B, int64_t r0, int64_t r1, int64_t rows_per_cta,
-              float2* __restrict__ partials, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+    k_gram_tc(const unsigned char* __restrict__ Qd, int na, const float2* __restrict__ B,
+              const int* __restrict__ fexp, int64_t n, int64_t rows_per_cta, float2* __restrict__ partials,
+              int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t mma_bar[kStages];
   __shared__ uint32_t tmem_base;
-  __shared__ int fexp[8];
+  // stages from a 1024-byte boundary (the swizzle atoms need 256-byte alignment)
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int na = A.n;
   const int M = na * 8;
-  const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * rows_per_cta;
-  const int64_t c1 = min(c0 + rows_per_cta, r1);
-  const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta;
+  const int64_t c1 = min(c0 + rows_per_cta, n);
+  const int64_t nck = (c1 - c0 + kTcRows - 1) / kTcRows;
+  const int64_t gc0 = c0 / kTcRows;  // first global chunk
 
-  // both stages zeroed once: tile rows >= M stay zero
-  for (int i = tid; i < 2 * kStage / 16; i += kTcThreads) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
-  if (tid < 8) fexp[tid] = -100000;
+  // the zero tiles of C (0-6 and 15-16) in every stage; A rows >= M are never
+  // read back, so A needs no clearing
+  for (int st = 0; st < kStages; ++st) {
+    uint4* z = reinterpret_cast<uint4*>(smem + st * kStageBytes + kABytes + kBRaw);
+    for (int i = tid; i < kCTiles * kAtom / 16; i += kTcThreads) {
+      const int tile = i / (kAtom / 16);
+      if (tile < 7 || tile >= 15) z[i] = make_uint4(0, 0, 0, 0);
+    }
+  }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+    for (int st = 0; st < kStages; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[st])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[st])) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -290,132 +392,94 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
   __syncthreads();
-  // B's column exponents over this CTA's rows
-  {
-    int emax = -100000;
-    const int j = tid & 7;
-    int64_t r = c0 + (tid >> 3);
-    for (; r + 96 < c1; r += 128) {
-      const float2 v0 = B[r * 8 + j], v1 = B[(r + 32) * 8 + j], v2 = B[(r + 64) * 8 + j], v3 = B[(r + 96) * 8 + j];
-      emax = max(max(emax, max(exp_bound<F64>(v0), exp_bound<F64>(v1))), max(exp_bound<F64>(v2), exp_bound<F64>(v3)));
-    }
-    for (; r < c1; r += 32) emax = max(emax, exp_bound<F64>(B[r * 8 + j]));
-    atomicMax(&fexp[j], emax);
-  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
   const uint32_t tmem = tmem_base;
   const int jb = tid & 7;  // this thread's B column
-  const int fb_mine = fexp[jb] > -100000 ? fexp[jb] : 0;
+  int fb_mine = fexp[jb];
+  if (fb_mine < -5000) fb_mine = 0;  // an all-zero column
+  const uint32_t idesc = instr_desc(kDCols);
+
+  // chunk k's copies: the na blocks' digit pieces, and B's rows
+  auto issue = [&](int64_t k) {
+    const int st = static_cast<int>(k % kStages);
+    const uint32_t bar = smem_u32(&full_bar[st]);
+    const int64_t base = c0 + k * kTcRows;
+    const int rows = static_cast<int>(c1 - base < kTcRows ? c1 - base : kTcRows);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(static_cast<uint32_t>(na * kBlockChunk + rows * 64))
+                 : "memory");
+    const uint32_t dst = smem_u32(smem + st * kStageBytes);
+    bulk_g2s(dst, Qd + (gc0 + k) * kGroupChunk, na * kBlockChunk, bar);
+    bulk_g2s(dst + kABytes, B + base * 8, rows * 64, bar);
+  };
+  // bit st: stage st has copies (tma_pend) or committed MMAs (mma_pend) not yet
+  // waited for; fph / mph: parity of that barrier's next phase
+  uint32_t tma_pend = 0u, mma_pend = 0u, fph = 0u, mph = 0u;
+  constexpr int kAhead = kStages - 2;  // chunks whose copies fly ahead of the one in use
+  for (int64_t k = 0; k < kAhead && k < nck; ++k) {
+    if (tid == 0) issue(k);
+    tma_pend |= 1u << k;
+  }
+  auto wait_full = [&](int st) -> bool {
+    if (!((tma_pend >> st) & 1u)) return true;
+    tma_pend &= ~(1u << st);
+    const bool ok = mbar_wait_bounded(smem_u32(&full_bar[st]), (fph >> st) & 1u);
+    fph ^= 1u << st;
+    return ok;
+  };
+  auto wait_mma = [&](int st) -> bool {
+    if (!((mma_pend >> st) & 1u)) return true;
+    mma_pend &= ~(1u << st);
+    const bool ok = mbar_wait_bounded(smem_u32(&mma_bar[st]), (mph >> st) & 1u);
+    mph ^= 1u << st;
+    return ok;
+  };
 
   // read-back split: warp w takes tensor-memory lanes 32 (w % 4) .. (A columns)
-  // and B columns 4 (w / 4) .. 4 (w / 4) + 3, all digits
-  long long acc[4][3];
+  // and B columns 4 (w / 4) .. 4 (w / 4) + 3, all levels
+  long long acc[4][4];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[e][c] = 0;
-
-  // this thread's A units: blocks a = warp and warp + 8, column ic, rows 8 g .. 8 g + 7
-  const int ic = lane & 7, g = lane >> 3;
-  const bool u0 = warp < na, u1 = warp + 8 < na;
-  const float2* __restrict__ A0 = u0 ? A.p[warp] : nullptr;
-  const float2* __restrict__ A1 = u1 ? A.p[warp + 8] : nullptr;
-  // values of the chunk being cut; a unit's next-chunk values are loaded as soon
-  // as its current ones are converted, so the loads overlap the digit stores
-  float2 pa[2][8], pb;
-  auto load_unit = [&](int u, int64_t base) {
-    const float2* __restrict__ Au = u ? A1 : A0;
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-      const int64_t r = base + g * 8 + rr;
-      pa[u][rr] = r < c1 ? Au[r * 8 + ic] : make_float2(0.f, 0.f);
-    }
-  };
-  auto load_b = [&](int64_t base) {
-    const int64_t rb = base + (tid >> 3);
-    pb = rb < c1 ? B[rb * 8 + jb] : make_float2(0.f, 0.f);
-  };
-
-  // bit st of pend: stage st has committed MMAs not yet waited for; bit st of
-  // ph: parity of the stage barrier's next phase
-  uint32_t pend = 0u, ph = 0u;
-  auto wait_stage = [&](int st) -> bool {
-    if (!((pend >> st) & 1u)) return true;
-    pend &= ~(1u << st);
-    const bool okw = mbar_wait_bounded(st ? bar1 : bar0, (ph >> st) & 1u);
-    ph ^= 1u << st;
-    return okw;
-  };
+    for (int c = 0; c < 4; ++c) acc[e][c] = 0;
 
   bool bad = false, timed_out = false;
-  int in_group = 0, chunk = 0;
-  if (c0 < c1) {
-    if (u0) load_unit(0, c0);
-    if (u1) load_unit(1, c0);
-    load_b(c0);
-  }
-  for (int64_t base = c0; base < c1; base += kTcRows, ++chunk) {
-    const int st = chunk & 1;
-    const bool more = base + kTcRows < c1;
-    const bool late = !wait_stage(st);
-    unsigned char* sA = smem + st * kStage;
-    // ---- A: one 16-byte store per digit plane and unit
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      if (u == 0 ? !u0 : !u1) continue;
-      uint64_t x[8];
-      bool ng[8];
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
-        if (!to_fixed<F64>(pa[u][rr], kAShift, x[rr], ng[rr])) {
-          bad = true;
-          x[rr] = 0;
-        }
-      }
-      if (more) load_unit(u, base + kTcRows);
-      Digits dg[8];
-      uint32_t S2[4], T2[4];
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) dg[rr] = spread(x[rr]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        S2[q] = sign_s(ng[2 * q], ng[2 * q + 1]);
-        T2[q] = sign_t(ng[2 * q], ng[2 * q + 1]);
-      }
-      const int a = warp + 8 * u;
-      unsigned char* dst = sA + ((a * 4 + g) * 128 + ic * 16);
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const int w = digit_word(s);
-        const uint32_t sel = digit_high(s) ? 0x7632u : 0x5410u;
-        uint4 o;
-        o.x = hfma2(__byte_perm(dg[0].w[w], dg[1].w[w], sel), S2[0], T2[0]);
-        o.y = hfma2(__byte_perm(dg[2].w[w], dg[3].w[w], sel), S2[1], T2[1]);
-        o.z = hfma2(__byte_perm(dg[4].w[w], dg[5].w[w], sel), S2[2], T2[2]);
-        o.w = hfma2(__byte_perm(dg[6].w[w], dg[7].w[w], sel), S2[3], T2[3]);
-        *reinterpret_cast<uint4*>(dst + s * kATile) = o;
-      }
+  int in_group = 0;
+  for (int64_t k = 0; k < nck; ++k) {
+    const int st = static_cast<int>(k % kStages);
+    const int64_t base = c0 + k * kTcRows;
+    unsigned char* sg = smem + st * kStageBytes;
+    // the stage of chunk k + kAhead (last used by chunk k - 2) is free once its
+    // MMAs are done
+    bool late = false;
+    if (k + kAhead < nck) {
+      const int sa = static_cast<int>((k + kAhead) % kStages);
+      late = !wait_mma(sa);
+      if (tid == 0 && !late) issue(k + kAhead);
+      tma_pend |= 1u << sa;
     }
-    // ---- B: one value per thread (row tid / 8, column tid % 8), eight 2-byte stores
-    {
+    late |= !wait_full(st);
+    // ---- B: threads 0 .. 127 cut one value each (row tid / 8, column tid % 8)
+    // into C's tiles 7 .. 14
+    if (tid < 8 * kTcRows) {
+      const int kr = tid >> 3;
+      const float2 v = base + kr < c1 ? reinterpret_cast<const float2*>(sg + kABytes)[tid] : make_float2(0.f, 0.f);
       uint64_t x;
       bool ng;
-      if (!to_fixed<F64>(pb, kAShift - fb_mine, x, ng)) {
+      if (!to_fixed<F64>(v, kQShift - fb_mine, x, ng)) {
         bad = true;
         x = 0;
       }
-      if (more) load_b(base + kTcRows);
-      const Digits dg = spread(x);
+      const Digits dg = spread_balanced(x);
       const uint32_t S1 = sign_s(ng, ng), T1 = sign_t(ng, ng);
       uint32_t h[4];
 #pragma unroll
       for (int w = 0; w < 4; ++w) h[w] = hfma2(dg.w[w], S1, T1);
-      unsigned char* dst = sA + 8 * kATile + kmajor_off(jb, tid >> 3);
+      unsigned char* dst = sg + kABytes + kBRaw + 7 * kAtom + atom_off(jb, kr);
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const uint32_t word = h[digit_word(t)];
-        *reinterpret_cast<uint16_t*>(dst + t * 512) =
+        *reinterpret_cast<uint16_t*>(dst + t * kAtom) =
             static_cast<uint16_t>(digit_high(t) ? (word >> 16) : (word & 0xFFFFu));
       }
     }
@@ -424,52 +488,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       timed_out = true;
       break;
     }
-    // ---- MMAs of this chunk, committed to the stage's barrier
-    if (tid == 0) {
+    // ---- the chunk's eight MMAs into D, committed to the stage's barrier
+    if (warp == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sA + 8 * kATile);
+      uint32_t leader;
+      asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}" : "=r"(leader));
+      if (leader) {
+        const uint32_t a0 = smem_u32(sg), cb = a0 + kABytes + kBRaw;
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          mma_f16(tmem + static_cast<uint32_t>(tc_col(s)), smem_desc(a0 + s * kATile + kk * 256),
-                  smem_desc(b0 + kk * 256), instr_desc(tc_n(s)), (in_group > 0 || kk > 0) ? 1u : 0u);
-        }
+        for (int s = 0; s < 8; ++s)
+          mma_f16(tmem, smem_desc_sw32(a0 + s * kAtom, kBlockChunk), smem_desc_sw32(cb + (7 - s) * kAtom, kAtom), idesc,
+                  (in_group > 0 || s > 0) ? 1u : 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&mma_bar[st]))
+                     : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       st ? bar1 : bar0)
-                   : "memory");
+      __syncwarp();
     }
-    pend |= 1u << st;
+    mma_pend |= 1u << st;
     ++in_group;
-    if (in_group == kTcGroupChunks || base + kTcRows >= c1) {
-      bool late2 = !wait_stage(0);
-      late2 |= !wait_stage(1);
+    if (in_group == kTcGroupChunks || k + 1 == nck) {
+      bool late2 = false;
+      for (int q = 0; q < kStages; ++q) late2 |= !wait_mma(q);
       if (__syncthreads_or(late2)) {
         timed_out = true;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int q = warp & 3;
-      if (32 * q < M) {
-        const uint32_t tl = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(4 * (warp >> 2));
-        read_digit<0>(tl + tc_col(0), acc);
-        read_digit<1>(tl + tc_col(1), acc);
-        read_digit<2>(tl + tc_col(2), acc);
-        read_digit<3>(tl + tc_col(3), acc);
-        read_digit<4>(tl + tc_col(4), acc);
-        read_digit<5>(tl + tc_col(5), acc);
-        read_digit<6>(tl + tc_col(6), acc);
-        read_digit<7>(tl + tc_col(7), acc);
-      }
+      if (32 * q < M)
+        read_levels(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(4 * (warp >> 2)), acc);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       in_group = 0;
     }
   }
   if (timed_out) {
-    // let committed MMAs finish (bounded) before the tensor memory is freed
-    wait_stage(0);
-    wait_stage(1);
+    // copies and MMAs in flight end (bounded) before the CTA leaves
+    for (int q = 0; q < kStages; ++q) {
+      wait_full(q);
+      wait_mma(q);
+    }
   }
   // A column i = 32 (warp % 4) + lane, B columns 4 (warp / 4) + e: scaled in FP64
   const int i = 32 * (warp & 3) + lane;
@@ -478,10 +536,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int j = 4 * (warp >> 2) + e;
-      const int fj = fexp[j] > -100000 ? fexp[j] : 0;
+      int fj = fexp[j];
+      if (fj < -5000) fj = 0;
       double gsum = 0.0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) gsum += ldexp(static_cast<double>(acc[e][c]), fj - 10 - 8 * (3 * c + 2));
+      for (int c = 3; c >= 0; --c) gsum += ldexp(static_cast<double>(acc[e][c]), fj - 10 - 8 * (3 * c + 2));
       partials[static_cast<int64_t>(blockIdx.x) * nout + i * 8 + j] = Ar<F64>::from_d(gsum);
     }
   }
@@ -493,10 +552,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+int sm_count() {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    return n > 0 ? n : 1;
+  }();
+  return sms;
+}
+
 }  // namespace
 
+int64_t qdigits_group_bytes(int64_t n) { return (n + kTcRows - 1) / kTcRows * kGroupChunk; }
+
+unsigned char* qdigits_block(unsigned char* Qd, int64_t n, int a) {
+  return Qd + (a / 16) * qdigits_group_bytes(n) + (a % 16) * kBlockChunk;
+}
+
+cudaError_t qcut(const float2* Q, int64_t n, unsigned char* out, bool f64, int* err, cudaStream_t s) {
+  const int64_t nch = (n + kTcRows - 1) / kTcRows;
+  if (nch == 0) return cudaSuccess;
+  const unsigned g = static_cast<unsigned>((nch * 16 + 255) / 256);
+  if (f64)
+    k_qcut<true><<<g, 256, 0, s>>>(Q, n, nch, out, err);
+  else
+    k_qcut<false><<<g, 256, 0, s>>>(Q, n, nch, out, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // Rows per CTA and CTA count of a launch over `rows` rows: one CTA per SM, at
-// least 1024 rows a CTA, a multiple of 32 rows, at most 2^22 rows (the 64-bit
+// least 1024 rows a CTA, a multiple of 16 rows, at most 2^22 rows (the 64-bit
 // level words cannot overflow).
 void gram_tc_geometry(int64_t rows, int sms, int64_t* per, int64_t* ctas) {
   int64_t c = (rows + 1023) / 1024;
@@ -509,37 +598,41 @@ void gram_tc_geometry(int64_t rows, int sms, int64_t* per, int64_t* ctas) {
   *ctas = (rows + p - 1) / p;
 }
 
-cudaError_t gram_tc(const BlockList& A, const float2* B, int64_t r0, int64_t r1, double* out, float2* partials,
-                    int64_t partial_cap, bool f64, int* err, cudaStream_t s) {
-  if (A.n < 0 || A.n > kMaxBlocks) return cudaErrorInvalidValue;
-  if (r1 <= r0 || A.n == 0) return cudaMemsetAsync(out, 0, sizeof(double) * A.n * 64, s);
-  static const int sms = [] {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    return n > 0 ? n : 1;
-  }();
+cudaError_t gram_tc(const unsigned char* Qd, int nblocks, const float2* B, int64_t n, double* out, float2* partials,
+                    int64_t partial_cap, bool f64, int* err, int* fexp, cudaStream_t s) {
+  if (nblocks < 0 || nblocks > kMaxBlocks) return cudaErrorInvalidValue;
+  if (n <= 0 || nblocks == 0) return cudaMemsetAsync(out, 0, sizeof(double) * nblocks * 64, s);
+  const int sms = sm_count();
+  // B's column exponents (preset to 0x80808080, below any exponent)
+  cudaError_t e = cudaMemsetAsync(fexp, 0x80, sizeof(int) * 8, s);
+  if (e != cudaSuccess) return e;
+  {
+    int64_t g = (n + 31) / 32;
+    if (g > 4 * sms) g = 4 * sms;
+    if (f64)
+      k_colexp<true><<<static_cast<unsigned>(g), 256, 0, s>>>(B, n, fexp);
+    else
+      k_colexp<false><<<static_cast<unsigned>(g), 256, 0, s>>>(B, n, fexp);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   int64_t per = 0, ctas = 0;
-  gram_tc_geometry(r1 - r0, sms, &per, &ctas);
+  gram_tc_geometry(n, sms, &per, &ctas);
+  const int64_t gb = qdigits_group_bytes(n);
   // groups of at most 16 blocks (M <= 128), each a launch and a finishing sum
-  for (int a0 = 0; a0 < A.n; a0 += 16) {
-    BlockList G;
-    G.n = A.n - a0 < 16 ? A.n - a0 : 16;
-    for (int a = 0; a < G.n; ++a) G.p[a] = A.p[a0 + a];
-    const int nout = G.n * 64;
+  for (int a0 = 0; a0 < nblocks; a0 += 16) {
+    const int na = nblocks - a0 < 16 ? nblocks - a0 : 16;
+    const int nout = na * 64;
     if (ctas * nout > partial_cap) return cudaErrorInvalidValue;
     const unsigned gdim = static_cast<unsigned>(ctas);
+    const unsigned char* q = Qd + (a0 / 16) * gb;
     if (f64)
-      k_gram_tc<true><<<gdim, kTcThreads, kTcSmem, s>>>(G, B, r0, r1, per, partials, err);
+      k_gram_tc<true><<<gdim, kTcThreads, kTcSmem, s>>>(q, na, B, fexp, n, per, partials, err);
     else
-      k_gram_tc<false><<<gdim, kTcThreads, kTcSmem, s>>>(G, B, r0, r1, per, partials, err);
+      k_gram_tc<false><<<gdim, kTcThreads, kTcSmem, s>>>(q, na, B, fexp, n, per, partials, err);
     count_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = gram_finish(partials, ctas, nout, out + a0 * 64, f64, s);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = gram_finish(partials, ctas, nout, out + a0 * 64, f64, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -185,13 +185,19 @@ cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_
 // Fixed-order sum of per-CTA partial results (nchunks x nout slots) into FP64 out.
 cudaError_t gram_finish(const float2* partials, int64_t nchunks, int nout, double* out, bool f64, cudaStream_t s);
 
-// ---- k_gram_tc.cu: gram() for kp = 8 on the tensor cores, for A with entries
-// |a| < 2 (the orthonormal basis): exact FP16 digit products of a 62-bit fixed
-// point split, FP64-grade result.  *err (device, sticky) gets bit 0 when an entry
-// of A is out of range or a value is not finite, bit 1 when a wait timed out.
-// partials needs ceil(rows / per) * 64 * min(A.n, 16) slots (gram_tc_geometry).
-cudaError_t gram_tc(const BlockList& A, const float2* B, int64_t r0, int64_t r1, double* out, float2* partials,
-                    int64_t partial_cap, bool f64, int* err, cudaStream_t s);
+// ---- k_gram_tc.cu: gram() for kp = 8 on the tensor cores against basis blocks
+// (entries |q| < 2) pre-cut into FP16 digit tiles (a 62-bit fixed-point split,
+// exact digit products, FP64-grade result).  The tiles of blocks 16 g .. 16 g + 15
+// form group g (qdigits_group_bytes(n) bytes); qcut writes block a's tiles at
+// qdigits_block(Qd, n, a); gram_tc reads blocks 0 .. nblocks - 1 and B (n x 8
+// slots), rows [0, n).  *err (device, sticky): bit 0 when a value is out of range
+// or not finite, bit 1 when a wait timed out.  fexp: device scratch, 8 ints.
+// partials needs ceil(n / per) * 64 * min(nblocks, 16) slots (gram_tc_geometry).
+int64_t qdigits_group_bytes(int64_t n);
+unsigned char* qdigits_block(unsigned char* Qd, int64_t n, int a);
+cudaError_t qcut(const float2* Q, int64_t n, unsigned char* out, bool f64, int* err, cudaStream_t s);
+cudaError_t gram_tc(const unsigned char* Qd, int nblocks, const float2* B, int64_t n, double* out, float2* partials,
+                    int64_t partial_cap, bool f64, int* err, int* fexp, cudaStream_t s);
 void gram_tc_geometry(int64_t rows, int sms, int64_t* per, int64_t* ctas);
 
 // Update: Y[r][j] = alpha[j] X[r][j] + sum_a sum_i A_a[r][i] coef[(a*kp+i)*kp + j]
