@@ -1107,13 +1107,16 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
 }
 
 // Gram product [Q_0 .. Q_{nq-1}]^T B (Eq. blkGS, Eq. proj): on the tensor cores
-// with opts.tensor_gram and 8-column blocks, else on the CUDA cores.  The tensor
-// path reads the blocks' digit tiles, cut here for every block whose tiles are
-// stale (h->qd_valid; every write of a basis block clears its bit).  Error flag
-// in dStatus[8], read with the orthogonalisation's status.
+// with opts.tensor_gram and 8-column blocks from the block count where they beat
+// the CUDA cores (measured on c2: 2 blocks in FP64, where one DFMA Gram block
+// costs as much as the tensor kernel's fixed part; 5 in double-float), else on
+// the CUDA cores.  The tensor path reads the blocks' digit tiles, cut here for
+// every block whose tiles are stale (h->qd_valid; every write of a basis block
+// clears its bit).  Error flag in dStatus[8], read with the orthogonalisation's
+// status.
 cudaError_t qgram(sppc_ctx* h, int nq, const float2* B, double* out, cudaStream_t s) {
   const int64_t n = h->n;
-  if (h->Qd && h->kp == 8) {
+  if (h->Qd && h->kp == 8 && nq >= (h->f64 ? 2 : 5)) {
     for (int a = 0; a < nq; ++a) {
       if ((h->qd_valid >> a) & 1ull) continue;
       cudaError_t e = qcut(blk(h->Q, n, 8, a), n, qdigits_block(h->Qd, n, a), h->f64, h->dStatus + 8, s);

@@ -55,7 +55,7 @@ namespace sppc {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 384;                 // 12 warps: MMA, copies, 4 cutters, 4 read-back
 constexpr int kTcRows = 16;                      // rows (K) per chunk: one K = 16 MMA step
 constexpr int kTcGroupChunks = 4;                // chunks summed in tensor memory before a read-back (64 rows)
 constexpr int kAtom = 256;                       // one 8 x 16 FP16 tile (a 32-byte-swizzled atom)
@@ -69,10 +69,10 @@ constexpr int kStages = 6;                       // copies run kStages - 2 chunk
 constexpr int kTcSmem = kStages * kStageBytes + 1024;   // + alignment slack: one CTA per SM
 constexpr int kLevels = 10;                      // digit levels L = s + t kept (0 .. 9)
 constexpr int kDCols = 8 * kLevels;              // D columns (L, j): the MMA's N
-constexpr int kTmemCols = 128;
+constexpr int kTmemCols = 256;                  // two D regions of 128 columns
 constexpr int kQShift = 61;                      // X_q = round(|q| 2^61)
 constexpr long long kWaitClocks = 1ll << 31;     // about a second
-static_assert(kDCols % 16 == 0 && kDCols <= kTmemCols, "D columns");
+static_assert(kDCols % 16 == 0 && 2 * 128 <= kTmemCols && kDCols <= 128, "D columns");
 static_assert(7 + kLevels <= kCTiles, "C windows");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -126,10 +126,23 @@ __device__ __forceinline__ bool mbar_done(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t"
+      "}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for the completion of the mbarrier phase of the given parity; false
 // after about a second.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  if (mbar_done(bar, parity)) return true;
+  if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_done(bar, parity)) {
     if (clock64() - t0 > kWaitClocks) return false;
@@ -314,51 +327,89 @@ __global__ void __launch_bounds__(256) k_colexp(const float2* __restrict__ B, in
   int e = -100000;
   const int j = threadIdx.x & 7;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 3);
-  for (int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 3) + (threadIdx.x >> 3); r < n; r += stride)
-    e = max(e, exp_bound<F64>(B[r * 8 + j]));
+  int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 3) + (threadIdx.x >> 3);
+  for (; r + 3 * stride < n; r += 4 * stride) {  // four loads in flight
+    const float2 v0 = B[r * 8 + j], v1 = B[(r + stride) * 8 + j], v2 = B[(r + 2 * stride) * 8 + j],
+                 v3 = B[(r + 3 * stride) * 8 + j];
+    e = max(max(e, max(exp_bound<F64>(v0), exp_bound<F64>(v1))), max(exp_bound<F64>(v2), exp_bound<F64>(v3)));
+  }
+  for (; r < n; r += stride) e = max(e, exp_bound<F64>(B[r * 8 + j]));
   atomicMax(&red[j], e);
   __syncthreads();
   if (threadIdx.x < 8) atomicMax(&fexp[threadIdx.x], red[threadIdx.x]);
 }
 
-// Waits for this thread's tensor-memory loads; the four registers pass through
+// Waits for this thread's tensor-memory loads; the eight registers pass through
 // the wait so that no use of them is scheduled before it.
-__device__ __forceinline__ void tmem_wait4(uint32_t (&v)[4]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3])::"memory");
+__device__ __forceinline__ void tmem_wait8(uint32_t (&v)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])::"memory");
 }
 
-// Reads back D for the 32 tensor-memory lanes and the four B columns j0 .. j0 + 3
-// at taddr (= lane base + j0), every level L, and adds level L into
-// acc[j - j0][L / 3] with weight 256^(2 - L % 3).
-__device__ __forceinline__ void read_levels(uint32_t taddr, long long (&acc)[4][4]) {
+// Reads back D (one region) for the warp's 32 tensor-memory lanes at taddr, all
+// eight B columns and every level L, adding level L into acc[j][L / 3] with
+// weight 256^(2 - L % 3).
+__device__ __forceinline__ void read_levels(uint32_t taddr, long long (&acc)[8][4]) {
 #pragma unroll
   for (int L = 0; L < kLevels; ++L) {
-    uint32_t v[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+    uint32_t v[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                  : "r"(taddr + static_cast<uint32_t>(8 * L))
                  : "memory");
-    tmem_wait4(v);
+    tmem_wait8(v);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const long long q = static_cast<long long>(__float2int_rn(__uint_as_float(v[e])));
-      acc[e][L / 3] += q * (1ll << (8 * (2 - L % 3)));
+    for (int j = 0; j < 8; ++j) {
+      const long long q = static_cast<long long>(__float2int_rn(__uint_as_float(v[j])));
+      acc[j][L / 3] += q * (1ll << (8 * (2 - L % 3)));
     }
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// A role's wait for the mbarrier phase of the given parity: false when another
+// role has given up (*abort set) or after about a second (then sets *abort).
+__device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_done(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitClocks) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool elect_one() {
+  uint32_t leader;
+  asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}" : "=r"(leader));
+  return leader != 0;
+}
+
 // Qd: the digits of a group of 16 blocks (the first na <= 16 used); B: n x 8
 // slots; fexp: B's column exponents (k_colexp); rows [0, n), CTA x takes rows
-// [x rows_per_cta, ...), rows_per_cta a multiple of 16.
+// [x rows_per_cta, ...), rows_per_cta a multiple of 16.  Roles: warp 0 issues
+// the MMAs, warp 1 the copies, warps 4-7 cut B's values, warps 8-11 read D back
+// (warp 8 + q: tensor-memory lanes 32 q ..); chunk k uses stage k % kStages,
+// 64-row group g the D region g % 2.  Handshakes (mbarriers): full (copies
+// landed) -> cut (128 cutter arrivals) -> mma (MMAs done: the stage is free
+// again) and, per group, acc (its MMAs done) -> free (128 read-back arrivals:
+// the region may be overwritten).
 template <bool F64>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gram_tc(const unsigned char* __restrict__ Qd, int na, const float2* __restrict__ B,
               const int* __restrict__ fexp, int64_t n, int64_t rows_per_cta, float2* __restrict__ partials,
               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[kStages];
-  __shared__ __align__(8) uint64_t mma_bar[kStages];
+  __shared__ __align__(8) uint64_t full_bar[kStages], cut_bar[kStages], mma_bar[kStages], acc_bar[2], free_bar[2];
   __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag, bad_flag;
+  __shared__ int armed[kStages], committed[kStages];  // phases started, for the error path
   // stages from a 1024-byte boundary (the swizzle atoms need 256-byte alignment)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -366,7 +417,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta;
   const int64_t c1 = min(c0 + rows_per_cta, n);
   const int64_t nck = (c1 - c0 + kTcRows - 1) / kTcRows;
+  const int64_t ngroups = (nck + kTcGroupChunks - 1) / kTcGroupChunks;
   const int64_t gc0 = c0 / kTcRows;  // first global chunk
+  volatile int* abort = &abort_flag;
 
   // the zero tiles of C (0-6 and 15-16) in every stage; A rows >= M are never
   // read back, so A needs no clearing
@@ -380,8 +433,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0) {
     for (int st = 0; st < kStages; ++st) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[st])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&cut_bar[st])), "r"(8 * kTcRows)
+                   : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[st])) : "memory");
+      armed[st] = committed[st] = 0;
     }
+    for (int r = 0; r < 2; ++r) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_bar[r])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&free_bar[r])) : "memory");
+    }
+    abort_flag = 0;
+    bad_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -394,79 +456,77 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const int jb = tid & 7;  // this thread's B column
-  int fb_mine = fexp[jb];
-  if (fb_mine < -5000) fb_mine = 0;  // an all-zero column
-  const uint32_t idesc = instr_desc(kDCols);
-
-  // chunk k's copies: the na blocks' digit pieces, and B's rows
-  auto issue = [&](int64_t k) {
-    const int st = static_cast<int>(k % kStages);
-    const uint32_t bar = smem_u32(&full_bar[st]);
-    const int64_t base = c0 + k * kTcRows;
-    const int rows = static_cast<int>(c1 - base < kTcRows ? c1 - base : kTcRows);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"(static_cast<uint32_t>(na * kBlockChunk + rows * 64))
-                 : "memory");
-    const uint32_t dst = smem_u32(smem + st * kStageBytes);
-    bulk_g2s(dst, Qd + (gc0 + k) * kGroupChunk, na * kBlockChunk, bar);
-    bulk_g2s(dst + kABytes, B + base * 8, rows * 64, bar);
-  };
-  // bit st: stage st has copies (tma_pend) or committed MMAs (mma_pend) not yet
-  // waited for; fph / mph: parity of that barrier's next phase
-  uint32_t tma_pend = 0u, mma_pend = 0u, fph = 0u, mph = 0u;
-  constexpr int kAhead = kStages - 2;  // chunks whose copies fly ahead of the one in use
-  for (int64_t k = 0; k < kAhead && k < nck; ++k) {
-    if (tid == 0) issue(k);
-    tma_pend |= 1u << k;
-  }
-  auto wait_full = [&](int st) -> bool {
-    if (!((tma_pend >> st) & 1u)) return true;
-    tma_pend &= ~(1u << st);
-    const bool ok = mbar_wait_bounded(smem_u32(&full_bar[st]), (fph >> st) & 1u);
-    fph ^= 1u << st;
-    return ok;
-  };
-  auto wait_mma = [&](int st) -> bool {
-    if (!((mma_pend >> st) & 1u)) return true;
-    mma_pend &= ~(1u << st);
-    const bool ok = mbar_wait_bounded(smem_u32(&mma_bar[st]), (mph >> st) & 1u);
-    mph ^= 1u << st;
-    return ok;
-  };
-
-  // read-back split: warp w takes tensor-memory lanes 32 (w % 4) .. (A columns)
-  // and B columns 4 (w / 4) .. 4 (w / 4) + 3, all levels
-  long long acc[4][4];
+  long long acc[8][4];  // read-back warps: A column 32 (warp - 8) + lane, all B columns
 #pragma unroll
-  for (int e = 0; e < 4; ++e)
+  for (int j = 0; j < 8; ++j)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[e][c] = 0;
+    for (int c = 0; c < 4; ++c) acc[j][c] = 0;
 
-  bool bad = false, timed_out = false;
-  int in_group = 0;
-  for (int64_t k = 0; k < nck; ++k) {
-    const int st = static_cast<int>(k % kStages);
-    const int64_t base = c0 + k * kTcRows;
-    unsigned char* sg = smem + st * kStageBytes;
-    // the stage of chunk k + kAhead (last used by chunk k - 2) is free once its
-    // MMAs are done
-    bool late = false;
-    if (k + kAhead < nck) {
-      const int sa = static_cast<int>((k + kAhead) % kStages);
-      late = !wait_mma(sa);
-      if (tid == 0 && !late) issue(k + kAhead);
-      tma_pend |= 1u << sa;
+  if (warp == 1) {
+    // ---- copies: chunk k into stage k % kStages once the MMAs of chunk k - kStages are done
+    if (elect_one()) {
+      for (int64_t k = 0; k < nck; ++k) {
+        const int st = static_cast<int>(k % kStages);
+        const int64_t use = k / kStages;
+        if (use > 0 && !role_wait(smem_u32(&mma_bar[st]), static_cast<uint32_t>((use - 1) & 1), abort)) break;
+        const uint32_t bar = smem_u32(&full_bar[st]);
+        const int64_t base = c0 + k * kTcRows;
+        const int rows = static_cast<int>(c1 - base < kTcRows ? c1 - base : kTcRows);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(static_cast<uint32_t>(na * kBlockChunk + rows * 64))
+                     : "memory");
+        const uint32_t dst = smem_u32(smem + st * kStageBytes);
+        bulk_g2s(dst, Qd + (gc0 + k) * kGroupChunk, na * kBlockChunk, bar);
+        bulk_g2s(dst + kABytes, B + base * 8, rows * 64, bar);
+        armed[st] += 1;
+      }
     }
-    late |= !wait_full(st);
-    // ---- B: threads 0 .. 127 cut one value each (row tid / 8, column tid % 8)
-    // into C's tiles 7 .. 14
-    if (tid < 8 * kTcRows) {
-      const int kr = tid >> 3;
-      const float2 v = base + kr < c1 ? reinterpret_cast<const float2*>(sg + kABytes)[tid] : make_float2(0.f, 0.f);
+    __syncwarp();
+  } else if (warp == 0) {
+    // ---- MMAs: chunk k's eight into its group's region once it is cut (and,
+    // for a group's first chunk, once the region's previous group is read back)
+    if (elect_one()) {
+      const uint32_t idesc = instr_desc(kDCols);
+      for (int64_t k = 0; k < nck; ++k) {
+        const int st = static_cast<int>(k % kStages);
+        const int64_t g = k / kTcGroupChunks;
+        const int r = static_cast<int>(g & 1);
+        const bool first = k % kTcGroupChunks == 0;
+        if (first && g >= 2 && !role_wait(smem_u32(&free_bar[r]), static_cast<uint32_t>(((g >> 1) - 1) & 1), abort))
+          break;
+        if (!role_wait(smem_u32(&cut_bar[st]), static_cast<uint32_t>((k / kStages) & 1), abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(smem + st * kStageBytes), cb = a0 + kABytes + kBRaw;
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+          mma_f16(tmem + static_cast<uint32_t>(r * 128), smem_desc_sw32(a0 + s * kAtom, kBlockChunk),
+                  smem_desc_sw32(cb + (7 - s) * kAtom, kAtom), idesc, (!first || s > 0) ? 1u : 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&mma_bar[st]))
+                     : "memory");
+        committed[st] += 1;
+        if (k % kTcGroupChunks == kTcGroupChunks - 1 || k + 1 == nck)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&acc_bar[r]))
+                       : "memory");
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // ---- cutters: value (row ct / 8, column ct % 8) of each chunk into C's tiles 7 .. 14
+    const int ct = tid - 128, kr = ct >> 3, jb = ct & 7;
+    int fb = fexp[jb];
+    if (fb < -5000) fb = 0;  // an all-zero column
+    bool bad = false;
+    for (int64_t k = 0; k < nck; ++k) {
+      const int st = static_cast<int>(k % kStages);
+      if (!role_wait(smem_u32(&full_bar[st]), static_cast<uint32_t>((k / kStages) & 1), abort)) break;
+      unsigned char* sg = smem + st * kStageBytes;
+      const float2 v = c0 + k * kTcRows + kr < c1 ? reinterpret_cast<const float2*>(sg + kABytes)[ct]
+                                                   : make_float2(0.f, 0.f);
       uint64_t x;
       bool ng;
-      if (!to_fixed<F64>(v, kQShift - fb_mine, x, ng)) {
+      if (!to_fixed<F64>(v, kQShift - fb, x, ng)) {
         bad = true;
         x = 0;
       }
@@ -482,70 +542,58 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         *reinterpret_cast<uint16_t*>(dst + t * kAtom) =
             static_cast<uint16_t>(digit_high(t) ? (word >> 16) : (word & 0xFFFFu));
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&cut_bar[st]));
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (__syncthreads_or(late)) {
-      timed_out = true;
-      break;
-    }
-    // ---- the chunk's eight MMAs into D, committed to the stage's barrier
-    if (warp == 0) {
+    if (bad) atomicOr(&bad_flag, 1);
+  } else if (warp >= 8) {
+    // ---- read-back: group g's region once its MMAs are done
+    const int q = warp - 8;
+    const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * q) << 16);
+    for (int64_t g = 0; g < ngroups; ++g) {
+      const int r = static_cast<int>(g & 1);
+      if (!role_wait(smem_u32(&acc_bar[r]), static_cast<uint32_t>((g >> 1) & 1), abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t leader;
-      asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}" : "=r"(leader));
-      if (leader) {
-        const uint32_t a0 = smem_u32(sg), cb = a0 + kABytes + kBRaw;
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-          mma_f16(tmem, smem_desc_sw32(a0 + s * kAtom, kBlockChunk), smem_desc_sw32(cb + (7 - s) * kAtom, kAtom), idesc,
-                  (in_group > 0 || s > 0) ? 1u : 0u);
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&mma_bar[st]))
-                     : "memory");
-      }
-      __syncwarp();
-    }
-    mma_pend |= 1u << st;
-    ++in_group;
-    if (in_group == kTcGroupChunks || k + 1 == nck) {
-      bool late2 = false;
-      for (int q = 0; q < kStages; ++q) late2 |= !wait_mma(q);
-      if (__syncthreads_or(late2)) {
-        timed_out = true;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int q = warp & 3;
-      if (32 * q < M)
-        read_levels(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(4 * (warp >> 2)), acc);
+      if (32 * q < M) read_levels(taddr + static_cast<uint32_t>(r * 128), acc);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      in_group = 0;
+      mbar_arrive(smem_u32(&free_bar[r]));
     }
   }
-  if (timed_out) {
-    // copies and MMAs in flight end (bounded) before the CTA leaves
-    for (int q = 0; q < kStages; ++q) {
-      wait_full(q);
-      wait_mma(q);
+  __syncthreads();
+  if (abort_flag) {
+    // copies and MMAs in flight end (bounded) before the tensor memory is freed
+    // and the CTA leaves
+    if (tid == 0) {
+      for (int st = 0; st < kStages; ++st) {
+        const int a = armed[st], c = committed[st];
+        volatile int never = 0;
+        if (a > 0) role_wait(smem_u32(&full_bar[st]), static_cast<uint32_t>((a - 1) & 1), &never);
+        never = 0;
+        if (c > 0) role_wait(smem_u32(&mma_bar[st]), static_cast<uint32_t>((c - 1) & 1), &never);
+      }
     }
+    __syncthreads();
   }
-  // A column i = 32 (warp % 4) + lane, B columns 4 (warp / 4) + e: scaled in FP64
-  const int i = 32 * (warp & 3) + lane;
-  if (i < M) {
-    const int nout = M * 8;
+  // read-back warps: A column i = 32 (warp - 8) + lane, every B column, scaled in FP64
+  if (warp >= 8) {
+    const int i = 32 * (warp - 8) + lane;
+    if (i < M) {
+      const int nout = M * 8;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int j = 4 * (warp >> 2) + e;
-      int fj = fexp[j];
-      if (fj < -5000) fj = 0;
-      double gsum = 0.0;
+      for (int j = 0; j < 8; ++j) {
+        int fj = fexp[j];
+        if (fj < -5000) fj = 0;
+        double gsum = 0.0;
 #pragma unroll
-      for (int c = 3; c >= 0; --c) gsum += ldexp(static_cast<double>(acc[e][c]), fj - 10 - 8 * (3 * c + 2));
-      partials[static_cast<int64_t>(blockIdx.x) * nout + i * 8 + j] = Ar<F64>::from_d(gsum);
+        for (int c = 3; c >= 0; --c) gsum += ldexp(static_cast<double>(acc[j][c]), fj - 10 - 8 * (3 * c + 2));
+        partials[static_cast<int64_t>(blockIdx.x) * nout + i * 8 + j] = Ar<F64>::from_d(gsum);
+      }
     }
   }
-  if (__syncthreads_or(bad) && tid == 0) atomicOr(err, 1);
-  if (timed_out && tid == 0) atomicOr(err, 2);
+  if (tid == 0) {
+    if (bad_flag) atomicOr(err, 1);
+    if (abort_flag) atomicOr(err, 2);
+  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
