@@ -355,6 +355,23 @@ sppc_status sppc_small_syev(const double* S, int32_t m, int32_t lds, int32_t nev
 sppc_status sppc_block_gram(const double* A, int32_t nblocks, const double* B, int64_t n, int32_t flags, double* G,
                             void* stream);
 
+/* The block update of block Gram-Schmidt (Eq. blkGS: T = S - Q C) and of the
+ * restart's Q Y, as the solve computes it:
+ *   Y[r][j] = alpha[j] X[r][j] + sum_a sum_i A_a[r][i] C[(8a + i) * 8 + j],
+ * A: device, nblocks (1 .. 40) blocks of n x 8 row-major FP64, block a at A + 8 a n;
+ * C: device, 8 nblocks x 8 row-major FP64; alpha: device, 8 FP64 or NULL (1);
+ * X: device, n x 8 FP64 or NULL (the term is absent); Y: device, n x 8 FP64, may
+ * be X.  flags as for sppc_block_gram: bit 0 (SPPC_GRAM_TENSOR) on the tensor
+ * cores (needs |A| < 2; the basis digits of sppc_block_gram, C cut into
+ * balanced 8-bit digits with one power of two per column, levels s + t <= 9 of
+ * the digit products summed exactly, each output rounded once to FP64), bit 1
+ * (SPPC_GRAM_DF) in double-float slots.  Synchronises `stream`; temporaries are
+ * allocated per call; SPPC_ERR_ARG on bad sizes, SPPC_ERR_NAN if (tensor cores)
+ * an entry of A has |a| >= 2 or a value is not finite, SPPC_ERR_TIMEOUT if a
+ * device-side wait gave up. */
+sppc_status sppc_block_update(const double* A, int32_t nblocks, const double* C, const double* alpha, const double* X,
+                              double* Y, int64_t n, int32_t flags, void* stream);
+
 /* ---- Learned correction proposal (not in the paper; the continuation of
  * Sec. 5-6 extended by a network's block).  Network: per (row i, Ritz pair j),
  * features f = (H_ii, level(i), ||H_i,:||_2, rhat_ij = r_ij sqrt(n)/||r_j||, theta_j,

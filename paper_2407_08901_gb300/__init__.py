@@ -18,7 +18,7 @@ from .build import LIB
 __all__ = [
     "SppcError", "sppc_default_opts", "sppc_create", "sppc_spmm", "sppc_spmm_noalloc", "sppc_spmm_host", "sppc_start", "sppc_correct",
     "sppc_rayleigh_ritz", "sppc_refine_step", "sppc_solve", "sppc_order_info", "sppc_get_stats", "sppc_get_state", "sppc_get_layout",
-    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "sppc_small_syev", "sppc_block_gram", "EXPORTED_SYMBOLS", "STATUS",
+    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "sppc_small_syev", "sppc_block_gram", "sppc_block_update", "EXPORTED_SYMBOLS", "STATUS",
 ]
 
 STATUS = {0: "SPPC_OK", 1: "SPPC_ERR_ARG", 2: "SPPC_ERR_NOT_SYMMETRIC", 3: "SPPC_ERR_LEVELS", 4: "SPPC_ERR_OOM",
@@ -92,6 +92,7 @@ _SIGS = {
     "sppc_kernel_launches": (_I64, []),
     "sppc_small_syev": (_I32, [_VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP]),
     "sppc_block_gram": (_I32, [_VP, _I32, _VP, _I64, _I32, _VP, _VP]),
+    "sppc_block_update": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP, _I64, _I32, _VP]),
     "sppc_set_proposal": (_I32, [_VP, _VP, _VP, _VP]),
     "sppc_proposal_samples": (_I32, [_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
     "sppc_mlp_forward": (_I32, [_VP, _VP, _I64, _I32, _VP, _VP]),
@@ -304,6 +305,25 @@ def sppc_block_gram(A, B, tensor: bool = False, df: bool = False, stream=None):
     flags = (1 if tensor else 0) | (2 if df else 0)
     _check(None, _lib.sppc_block_gram(A.data_ptr(), nb, B.data_ptr(), n, flags, G.data_ptr(), _stream(stream)))
     return G
+
+
+def sppc_block_update(A, C, alpha=None, X=None, Y=None, tensor: bool = False, df: bool = False, stream=None):
+    """Y = alpha X + sum_a A_a C_a for A a torch CUDA float64 tensor (nblocks, n, 8),
+    C (8 nblocks, 8), alpha (8,) or None, X (n, 8) or None; Y (n, 8) is
+    allocated when None (it may be X).  Returns Y.  tensor: on the tensor cores
+    (|A| < 2 required); df: in double-float slots.  Synchronises the stream."""
+    import torch
+    A = A.contiguous()
+    nb, n = int(A.shape[0]), int(A.shape[1])
+    C = C.contiguous()
+    assert A.dtype == torch.float64 and C.dtype == torch.float64 and tuple(C.shape) == (8 * nb, 8)
+    if Y is None:
+        Y = torch.empty(n, 8, dtype=torch.float64, device=A.device)
+    flags = (1 if tensor else 0) | (2 if df else 0)
+    _check(None, _lib.sppc_block_update(A.data_ptr(), nb, C.data_ptr(), alpha.data_ptr() if alpha is not None else None,
+                                        X.data_ptr() if X is not None else None, Y.data_ptr(), n, flags,
+                                        _stream(stream)))
+    return Y
 
 
 def _f32_dev(t, n=None):

@@ -1804,6 +1804,74 @@ sppc_status sppc_block_gram(const double* A, int32_t nblocks, const double* B, i
   return SPPC_OK;
 }
 
+sppc_status sppc_block_update(const double* A, int32_t nblocks, const double* C, const double* alpha, const double* X,
+                              double* Y, int64_t n, int32_t flags, void* stream) {
+  if (((!A || !Y) && n > 0) || !C || nblocks < 1 || nblocks > kMaxBlocks || n < 0 || n >= ((int64_t)1 << 40) ||
+      (flags & ~3))
+    return fail(nullptr, SPPC_ERR_ARG, "sppc_block_update: bad arguments (1 <= nblocks <= %d, flags in 0..3)",
+                kMaxBlocks);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool tc = (flags & 1) != 0, df = (flags & 2) != 0;
+  const int64_t nn = n ? n : 1;
+  float2* buf = nullptr;  // double-float copies: A blocks, X, Y, then C and alpha
+  int* err = nullptr;
+  unsigned char* Ad = nullptr;
+  cudaError_t e = cudaMalloc(&err, sizeof(int) * 16);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int) * 16, s);
+  if (e == cudaSuccess && df) e = cudaMalloc(&buf, sizeof(float2) * (((size_t)nblocks + 2) * nn * 8 + 64 * nblocks + 8));
+  const float2* Ls[kMaxBlocks];
+  const float2 *Cs = reinterpret_cast<const float2*>(C), *as = reinterpret_cast<const float2*>(alpha),
+               *Xs = reinterpret_cast<const float2*>(X);
+  float2* Ys = reinterpret_cast<float2*>(Y);
+  for (int a = 0; a < nblocks; ++a) Ls[a] = reinterpret_cast<const float2*>(A + (int64_t)a * n * 8);
+  if (e == cudaSuccess && df) {
+    float2* Xd = buf + (int64_t)nblocks * nn * 8;
+    float2* Yd = Xd + nn * 8;
+    float2* Cd = Yd + nn * 8;
+    float2* ad = Cd + 64 * nblocks;
+    for (int a = 0; a < nblocks && e == cudaSuccess; ++a) {
+      float2* d = buf + (int64_t)a * nn * 8;
+      e = f64_to_df(A + (int64_t)a * n * 8, 8, 8, d, 8, 0, n, false, s);
+      Ls[a] = d;
+    }
+    if (e == cudaSuccess) e = f64_to_df(C, 8, 8, Cd, 8, 0, 8 * nblocks, false, s);
+    if (e == cudaSuccess && alpha) e = f64_to_df(alpha, 8, 8, ad, 8, 0, 1, false, s);
+    if (e == cudaSuccess && X) e = f64_to_df(X, 8, 8, Xd, 8, 0, n, false, s);
+    Cs = Cd;
+    as = alpha ? ad : nullptr;
+    Xs = X ? Xd : nullptr;
+    Ys = Yd;
+  }
+  if (e == cudaSuccess && tc) {
+    const size_t bytes = (size_t)((nblocks + 15) / 16) * (size_t)qdigits_group_bytes(n) + 16;
+    e = cudaMalloc(&Ad, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Ad, 0, bytes, s);
+    for (int a = 0; a < nblocks && e == cudaSuccess; ++a) e = qcut(Ls[a], n, qdigits_block(Ad, n, a), !df, err, s);
+  }
+  if (e == cudaSuccess) {
+    if (tc) {
+      e = update_tc(Ad, nblocks, Cs, as, Xs, Ys, n, !df, err, s);
+    } else {
+      BlockList L;
+      L.n = nblocks;
+      for (int a = 0; a < nblocks; ++a) L.p[a] = Ls[a];
+      e = update(Ys, Xs, as, L, Cs, 8, 0, n, !df, s);
+    }
+  }
+  if (e == cudaSuccess && df) e = df_to_f64(Ys, 8, Y, 8, 8, 0, n, false, s);
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  cudaFree(err);
+  cudaFree(Ad);
+  if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_block_update: %s", cudaGetErrorString(e));
+  if (flag & 2) return fail(nullptr, SPPC_ERR_TIMEOUT, "sppc_block_update: a tensor-core pipeline wait timed out");
+  if (flag & 1)
+    return fail(nullptr, SPPC_ERR_NAN, "sppc_block_update: an entry of A has |a| >= 2, or a value is not finite");
+  return SPPC_OK;
+}
+
 sppc_status sppc_destroy(sppc_handle h) {
   if (!h) return SPPC_OK;
   if (h->stream2) cudaStreamSynchronize(h->stream2);
