@@ -1106,26 +1106,47 @@ sppc_status minres(sppc_ctx* h, std::vector<int32_t>& iters) {
   return SPPC_OK;
 }
 
+// Digit tiles of basis blocks 0 .. nq - 1 for the tensor-core kernels, cut for
+// every block whose tiles are stale (h->qd_valid; every write of a basis block
+// clears its bit).  Error flag in dStatus[8], read with the orthogonalisation's
+// status.
+cudaError_t ensure_qdigits(sppc_ctx* h, int nq, cudaStream_t s) {
+  for (int a = 0; a < nq; ++a) {
+    if ((h->qd_valid >> a) & 1ull) continue;
+    cudaError_t e = qcut(blk(h->Q, h->n, 8, a), h->n, qdigits_block(h->Qd, h->n, a), h->f64, h->dStatus + 8, s);
+    if (e != cudaSuccess) return e;
+    h->qd_valid |= 1ull << a;
+  }
+  return cudaSuccess;
+}
+
 // Gram product [Q_0 .. Q_{nq-1}]^T B (Eq. blkGS, Eq. proj): on the tensor cores
 // with opts.tensor_gram and 8-column blocks from the block count where they beat
 // the CUDA cores (measured on c2: 2 blocks in FP64, where one DFMA Gram block
 // costs as much as the tensor kernel's fixed part; 5 in double-float), else on
-// the CUDA cores.  The tensor path reads the blocks' digit tiles, cut here for
-// every block whose tiles are stale (h->qd_valid; every write of a basis block
-// clears its bit).  Error flag in dStatus[8], read with the orthogonalisation's
-// status.
+// the CUDA cores.
 cudaError_t qgram(sppc_ctx* h, int nq, const float2* B, double* out, cudaStream_t s) {
   const int64_t n = h->n;
   if (h->Qd && h->kp == 8 && nq >= (h->f64 ? 2 : 5)) {
-    for (int a = 0; a < nq; ++a) {
-      if ((h->qd_valid >> a) & 1ull) continue;
-      cudaError_t e = qcut(blk(h->Q, n, 8, a), n, qdigits_block(h->Qd, n, a), h->f64, h->dStatus + 8, s);
-      if (e != cudaSuccess) return e;
-      h->qd_valid |= 1ull << a;
-    }
+    cudaError_t e = ensure_qdigits(h, nq, s);
+    if (e != cudaSuccess) return e;
     return gram_tc(h->Qd, nq, B, n, out, h->partials, h->partial_cap, h->f64, h->dStatus + 8, h->dStatus + 16, s);
   }
   return gram(blocks(h->Q, n, h->kp, 0, nq), B, h->kp, 0, n, out, h->partials, h->partial_cap, h->f64, s);
+}
+
+// Block update Y = alpha X + [Q_0 .. Q_{nq-1}] coef (Eq. blkGS, the restart's
+// Q Y): on the tensor cores under the same conditions as qgram, from 2 blocks
+// in FP64 and 10 in double-float (measured on c2), else on the CUDA cores.
+cudaError_t qupdate(sppc_ctx* h, int nq, float2* Y, const float2* X, const float2* alpha, const float2* coef,
+                    cudaStream_t s) {
+  const int64_t n = h->n;
+  if (h->Qd && h->kp == 8 && nq >= (h->f64 ? 2 : 10)) {
+    cudaError_t e = ensure_qdigits(h, nq, s);
+    if (e != cudaSuccess) return e;
+    return update_tc(h->Qd, nq, coef, alpha, X, Y, n, h->f64, h->dStatus + 8, s);
+  }
+  return update(Y, X, alpha, blocks(h->Q, n, h->kp, 0, nq), coef, h->kp, 0, n, h->f64, s);
 }
 
 // ------------------------------------------------------- Rayleigh-Ritz core
@@ -1196,12 +1217,11 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   const int k = h->k, kp = h->kp;
   const int64_t n = h->n;
   float2* c = h->dCoef;
-  BlockList Qs = blocks(h->Q, n, kp, 0, p);
   const int nc = p * kp * kp;
   CK(qgram(h, p, src, h->dC1, s));
   k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, nc, h->dCoefBig, h->f64); count_launch();
   CK(cudaGetLastError());
-  CK(update(h->T1, src, c + kOnes, Qs, h->dCoefBig, kp, 0, n, h->f64, s));
+  CK(qupdate(h, p, h->T1, src, c + kOnes, h->dCoefBig, s));
   {
     const float2* A[2] = {src, h->T1};
     const float2* B[2] = {src, h->T1};
@@ -1216,7 +1236,7 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
     CK(qgram(h, p, h->T1, h->dC2, s));
     k_negmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC2, nc, h->dCoefBig, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(update(h->T1, h->T1, c + kOnes, Qs, h->dCoefBig, kp, 0, n, h->f64, s));
+    CK(qupdate(h, p, h->T1, h->T1, c + kOnes, h->dCoefBig, s));
     k_addmat<<<(nc + 255) / 256, 256, 0, s>>>(h->dC1, h->dC2, nc, h->dC1); count_launch();  // C = C1 + C2
     CK(cudaGetLastError());
     const float2* A[1] = {h->T1};
@@ -1259,7 +1279,7 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
   for (int b = 0; b < 2; ++b) {
     k_restart_coef<<<1, 256, 0, s>>>(h->dV, h->nev, p, k, kp, b, h->dCoefBig, h->f64); count_launch();
     CK(cudaGetLastError());
-    CK(update(blk(h->Psi, n, kp, b), nullptr, nullptr, blocks(h->Q, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n, h->f64, s));
+    CK(qupdate(h, p + 1, blk(h->Psi, n, kp, b), nullptr, nullptr, h->dCoefBig, s));
     CK(update(blk(h->Psi, n, kp, 2 + b), nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n, h->f64,
               s));
   }
@@ -1816,8 +1836,16 @@ sppc_status sppc_block_update(const double* A, int32_t nblocks, const double* C,
   float2* buf = nullptr;  // double-float copies: A blocks, X, Y, then C and alpha
   int* err = nullptr;
   unsigned char* Ad = nullptr;
+  double* ones = nullptr;  // alpha = 1 when X comes without alpha
   cudaError_t e = cudaMalloc(&err, sizeof(int) * 16);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int) * 16, s);
+  if (e == cudaSuccess && X && !alpha) {
+    const double h1[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    e = cudaMalloc(&ones, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ones, h1, sizeof(h1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    alpha = ones;
+  }
   if (e == cudaSuccess && df) e = cudaMalloc(&buf, sizeof(float2) * (((size_t)nblocks + 2) * nn * 8 + 64 * nblocks + 8));
   const float2* Ls[kMaxBlocks];
   const float2 *Cs = reinterpret_cast<const float2*>(C), *as = reinterpret_cast<const float2*>(alpha),
@@ -1865,6 +1893,7 @@ sppc_status sppc_block_update(const double* A, int32_t nblocks, const double* C,
   cudaFree(buf);
   cudaFree(err);
   cudaFree(Ad);
+  cudaFree(ones);
   if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_block_update: %s", cudaGetErrorString(e));
   if (flag & 2) return fail(nullptr, SPPC_ERR_TIMEOUT, "sppc_block_update: a tensor-core pipeline wait timed out");
   if (flag & 1)

@@ -21,8 +21,9 @@
 // step's eight 16-row chunks (cp.async.bulk, the two blocks' 4 KB of a chunk
 // each), warp 0 issues its eight MMAs into the tile's region (two regions
 // alternate between tiles), warps 4-7 read a finished tile back (tcgen05.ld, one
-// row per thread), scale each column's level sums in FP64, add alpha X and store
-// Y.  Y may alias X (a row is read and written by one thread).  Errors: a
+// row per thread), turn each column's level sums into one value by integer
+// arithmetic (tc_digits.cuh: an exact 128-bit sum, rounded once), add alpha X
+// (when X and alpha are given, as update() does) and store Y.  Y may alias X (a row is read and written by one thread).  Errors: a
 // non-finite coefficient sets bit 0 of *err, a timed-out wait (about a second)
 // bit 1; after a time-out the kernel waits (bounded) for its copies and MMAs in
 // flight and frees its tensor memory.
@@ -58,12 +59,12 @@ __device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
 }
 
 // Qd: digits of blocks 0 .. na - 1 (na <= 16) of one group; coef: 8 na x 8 slots,
-// row (8 a + i); alpha: 8 slots or null (1); X: n x 8 slots or null (absent).
+// row (8 a + i); xmode 0: no X term, 1: alpha X (alpha: 8 slots), 2: X.
 template <bool F64>
 __global__ void __launch_bounds__(kUThreads, 1)
     k_update_tc(const unsigned char* __restrict__ Qd, int na, const float2* __restrict__ coef,
-                const float2* __restrict__ alpha, const float2* X, float2* Y, int64_t n, int64_t rows_per_cta,
-                int* __restrict__ err) {
+                const float2* __restrict__ alpha, const float2* X, int xmode, float2* Y, int64_t n,
+                int64_t rows_per_cta, int* __restrict__ err) {
   using V = Ar<F64>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kUStages], mma_bar[kUStages], acc_bar[2], free_bar[2];
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
     for (int j = 0; j < 8; ++j) g[j] = gexp[j] < -5000 ? 0 : gexp[j];
     float2 al[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) al[j] = alpha ? alpha[j] : V::from_d(1.0);
+    for (int j = 0; j < 8; ++j) al[j] = xmode == 1 ? alpha[j] : V::from_d(1.0);
     for (int64_t tile = 0; tile < ntiles; ++tile) {
       const int r = static_cast<int>(tile & 1);
       if (!role_wait(smem_u32(&acc_bar[r]), static_cast<uint32_t>((tile >> 1) & 1), abort)) break;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
       const int64_t row = c0 + tile * kTileRows + 32 * q + lane;
       if (row < c1) {
         float2 x[8];
-        if (X) {
+        if (xmode) {
           const float4* xp = reinterpret_cast<const float4*>(X + row * 8);
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
@@ -238,11 +239,8 @@ __global__ void __launch_bounds__(kUThreads, 1)
         float2 y[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          double v = 0.0;
-#pragma unroll
-          for (int c = 3; c >= 0; --c) v += ldexp(static_cast<double>(acc[j][c]), g[j] - 10 - 8 * (3 * c + 2));
-          float2 t = V::from_d(v);
-          if (X) t = V::add(V::mul(al[j], x[j]), t);
+          float2 t = levels_to_slot<F64>(acc[j], g[j]);
+          if (xmode) t = V::add(V::mul(al[j], x[j]), t);
           y[j] = t;
         }
         float4* yp = reinterpret_cast<float4*>(Y + row * 8);
@@ -301,17 +299,17 @@ cudaError_t update_tc(const unsigned char* Qd, int nblocks, const float2* coef, 
     BlockList none;
     return update(Y, X, alpha, none, coef, 8, 0, n, f64, s);
   }
-  // groups of at most 16 blocks; later groups add onto Y (X = Y, alpha = 1)
+  // groups of at most 16 blocks; later groups add onto Y
   for (int a0 = 0; a0 < nblocks; a0 += 16) {
     const int na = nblocks - a0 < 16 ? nblocks - a0 : 16;
     const float2* x = a0 == 0 ? X : Y;
-    const float2* al = a0 == 0 ? alpha : nullptr;
+    const int xmode = a0 == 0 ? (X && alpha ? 1 : 0) : 2;
     const unsigned char* q = Qd + (a0 / 16) * gb;
     const unsigned g = static_cast<unsigned>(ctas);
     if (f64)
-      k_update_tc<true><<<g, kUThreads, kUSmem, s>>>(q, na, coef + a0 * 64, al, x, Y, n, per, err);
+      k_update_tc<true><<<g, kUThreads, kUSmem, s>>>(q, na, coef + a0 * 64, alpha, x, xmode, Y, n, per, err);
     else
-      k_update_tc<false><<<g, kUThreads, kUSmem, s>>>(q, na, coef + a0 * 64, al, x, Y, n, per, err);
+      k_update_tc<false><<<g, kUThreads, kUSmem, s>>>(q, na, coef + a0 * 64, alpha, x, xmode, Y, n, per, err);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

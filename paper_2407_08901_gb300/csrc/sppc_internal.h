@@ -202,8 +202,9 @@ void gram_tc_geometry(int64_t rows, int sms, int64_t* per, int64_t* ctas);
 
 // ---- k_update_tc.cu: update() for kp = 8 on the tensor cores against basis
 // blocks 0 .. nblocks - 1 of Qd (the tiles gram_tc reads): Y = alpha X + sum_a
-// Q_a coef_a, coef[(8 a + i) * 8 + j], alpha null = 1, X null = absent, Y may
-// alias X.  *err as for gram_tc (bit 0: a coefficient not finite).
+// Q_a coef_a, coef[(8 a + i) * 8 + j], the X term present when X and alpha are
+// both given (as in update()), Y may alias X.  *err as for gram_tc (bit 0: a
+// coefficient not finite).
 cudaError_t update_tc(const unsigned char* Qd, int nblocks, const float2* coef, const float2* alpha, const float2* X,
                       float2* Y, int64_t n, bool f64, int* err, cudaStream_t s);
 

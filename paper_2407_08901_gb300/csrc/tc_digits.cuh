@@ -277,5 +277,77 @@ __device__ __forceinline__ bool elect_one() {
   return leader != 0;
 }
 
+// W 2^e2 for a signed 128-bit integer W, as the nearest double (ties to even),
+// from integer operations only (no FP64 arithmetic).  Results below the normal
+// range are flushed to zero; they lie far under the values the kernels meet.
+__device__ __forceinline__ double i128_scaled_to_double(__int128 W, int e2) {
+  if (W == 0) return 0.0;
+  const bool neg = W < 0;
+  unsigned __int128 U = neg ? static_cast<unsigned __int128>(-W) : static_cast<unsigned __int128>(W);
+  const uint64_t uh = static_cast<uint64_t>(U >> 64), ul = static_cast<uint64_t>(U);
+  const int msb = uh ? 127 - __clzll(static_cast<long long>(uh)) : 63 - __clzll(static_cast<long long>(ul));
+  uint64_t mant;
+  int ex = msb + e2;  // value = 1.mant * 2^ex
+  if (msb > 52) {
+    const int sh = msb - 52;
+    mant = static_cast<uint64_t>(U >> sh);
+    const unsigned __int128 rem = U & ((static_cast<unsigned __int128>(1) << sh) - 1);
+    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++ex;
+      }
+    }
+  } else {
+    mant = ul << (52 - msb);
+  }
+  if (ex < -1022) return 0.0;
+  const uint64_t bits = (neg ? (1ull << 63) : 0ull) | (static_cast<uint64_t>(ex + 1023) << 52) |
+                        (mant & ((1ull << 52) - 1));
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// The same value as a double-float pair hi + lo (the top 24 bits and the next
+// 24, both truncated, then renormalised by an exact fast two-sum), from integer
+// operations and FP32 bit patterns.
+__device__ __forceinline__ float2 i128_scaled_to_df(__int128 W, int e2) {
+  if (W == 0) return make_float2(0.f, 0.f);
+  const bool neg = W < 0;
+  unsigned __int128 U = neg ? static_cast<unsigned __int128>(-W) : static_cast<unsigned __int128>(W);
+  const uint64_t uh = static_cast<uint64_t>(U >> 64), ul = static_cast<uint64_t>(U);
+  const int msb = uh ? 127 - __clzll(static_cast<long long>(uh)) : 63 - __clzll(static_cast<long long>(ul));
+  auto word = [&](int top) -> float {  // the 24 bits from bit `top` down, as a float of the right scale
+    const int sh = top - 23;
+    const uint32_t m = static_cast<uint32_t>((sh >= 0 ? (U >> sh) : (U << -sh)) & 0xFFFFFFu);
+    if (m == 0) return 0.f;
+    const int lead = 31 - __clz(static_cast<int>(m));  // m's top set bit (<= 23)
+    const int ex = top - (23 - lead) + e2;             // exponent of m's leading bit
+    if (ex < -126) return 0.f;
+    if (ex > 127) return neg ? -__int_as_float(0x7F800000) : __int_as_float(0x7F800000);
+    const uint32_t frac = (m << (23 - lead)) & 0x7FFFFFu;
+    return __uint_as_float((neg ? 0x80000000u : 0u) | (static_cast<uint32_t>(ex + 127) << 23) | frac);
+  };
+  const float hi = word(msb), lo = msb >= 24 ? word(msb - 24) : 0.f;
+  const float sum = __fadd_rn(hi, lo);  // renormalised: |lo| <= ulp(hi) / 2
+  return make_float2(sum, __fsub_rn(lo, __fsub_rn(sum, hi)));
+}
+
+// The FP64 value of D's level words for one output: acc[c] holds levels 3c ..
+// 3c + 2 with weight 256^(2 - L % 3), so the exact sum is W = sum_c acc[c]
+// 2^(24 (3 - c)) times 2^(scale - 98), scale = the column's exponent g.
+template <bool F64>
+__device__ __forceinline__ float2 levels_to_slot(const long long (&w)[4], int scale) {
+  __int128 W = static_cast<__int128>(w[0]);
+  W = (W << 24) + w[1];
+  W = (W << 24) + w[2];
+  W = (W << 24) + w[3];
+  if constexpr (F64)
+    return d_slot(i128_scaled_to_double(W, scale - 98));
+  else
+    return i128_scaled_to_df(W, scale - 98);
+}
+
 }  // namespace tc
 }  // namespace sppc

@@ -143,6 +143,26 @@ def test_in_place_and_without_x(df):
     assert np.all(np.abs(Y - ref) <= _tol(Ah, Ch, None, None, df))
 
 
+@pytest.mark.parametrize("df", [False, True])
+def test_tensor_and_cuda_cores_agree_at_scale(df):
+    # 2e5 rows: every CTA runs several 128-row tiles through the pipeline
+    S = _S()
+    nb, n = 6, 200_003
+    Q = _orthonormal(nb, n, seed=21).cuda()
+    g = torch.Generator(device="cuda").manual_seed(4)
+    C = torch.randn(8 * nb, 8, generator=g, dtype=torch.float64, device="cuda")
+    X = torch.randn(n, 8, generator=g, dtype=torch.float64, device="cuda")
+    for alpha in (None, torch.randn(8, generator=g, dtype=torch.float64, device="cuda")):
+        Y1 = S.sppc_block_update(Q, C, alpha, X, tensor=True, df=df)
+        Y0 = S.sppc_block_update(Q, C, alpha, X, tensor=False, df=df)
+        # the CUDA-core update rounds once per multiply-add (8 nb of them, on top
+        # of alpha X); the tensor path rounds the exact sum once
+        a = torch.ones(8, dtype=torch.float64, device="cuda") if alpha is None else alpha.abs()
+        mag = X.abs() * a + Q.abs().permute(1, 0, 2).reshape(n, -1) @ C.abs()
+        u = 2.0 ** -46 if df else 2.0 ** -53
+        assert bool(((Y1 - Y0).abs() <= (8 * nb + 4) * u * mag).all())
+
+
 def test_non_finite_coefficient_is_reported():
     S = _S()
     Q = _orthonormal(2, 3000, seed=2).cuda()
