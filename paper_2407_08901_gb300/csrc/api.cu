@@ -63,7 +63,8 @@ enum CoefSlot : int {
   kPosE0 = 864,      // 8: +E0 per column (right-hand side after deflation)
   kRmmNegTh = 872,   // 8: -theta_j of the RMM-DIIS iterate
   kRmmScale = 880,   // 8: 1 / ||x_j|| (RMM-DIIS normalisation)
-  kCoefEnd = 888
+  kRitzNegTh = 888,  // 8: -theta_j (tensor-core Ritz residuals)
+  kCoefEnd = 896
 };
 
 }  // namespace
@@ -111,6 +112,11 @@ struct sppc_ctx {
   int* dStatus = nullptr;
   unsigned char* Qd = nullptr;  // opts.tensor_gram: FP16 digit tiles of the basis blocks (k_gram_tc.cu)
   uint64_t qd_valid = 0;        // bit a: Qd holds the digits of basis block a as it stands
+  unsigned char* Wd = nullptr;  // the same for the blocks of W = H Q, cut per column at 2^(61 - wexp)
+  int* wexp = nullptr;          // W blocks' column exponents, 8 per block (device)
+  uint64_t wd_valid = 0;
+  float2* Zt = nullptr;         // tensor-core Ritz pass: Ritz vectors Q Y and residuals W Y - Z theta
+  float2* Dt = nullptr;
   unsigned* dBar = nullptr;
   float2* partials = nullptr;
   int64_t partial_cap = 0;
@@ -701,6 +707,8 @@ sppc_status collect_timing(sppc_ctx* h) {
 
 // The big SpMM W_p = H q^(p) (k SpMVs of the order), timed when opts.timing.
 sppc_status big_spmm(sppc_ctx* h, const float2* X, float2* Y, int kp) {
+  if (h->Wd && Y >= h->W && Y < h->W + (int64_t)(h->pmax + 1) * h->n * kp)
+    h->wd_valid &= ~(1ull << ((Y - h->W) / (h->n * kp)));  // this W block is rewritten
   cudaEvent_t a = nullptr, b = nullptr;
   if (h->opt.timing) {
     a = next_event(h);
@@ -1149,6 +1157,81 @@ cudaError_t qupdate(sppc_ctx* h, int nq, float2* Y, const float2* X, const float
   return update(Y, X, alpha, blocks(h->Q, n, h->kp, 0, nq), coef, h->kp, 0, n, h->f64, s);
 }
 
+// Digit tiles of W blocks 0 .. nq - 1 (W = H Q, not orthonormal): column
+// exponents, then the cut at 2^(61 - e) per column.
+cudaError_t ensure_wdigits(sppc_ctx* h, int nq, cudaStream_t s) {
+  for (int a = 0; a < nq; ++a) {
+    if ((h->wd_valid >> a) & 1ull) continue;
+    const float2* w = blk(h->W, h->n, 8, a);
+    cudaError_t e = colexp(w, h->n, h->wexp + 8 * a, h->f64, s);
+    if (e == cudaSuccess)
+      e = qcut(w, h->n, qdigits_block(h->Wd, h->n, a), h->f64, h->dStatus + 8, s, h->wexp + 8 * a);
+    if (e != cudaSuccess) return e;
+    h->wd_valid |= 1ull << a;
+  }
+  return cudaSuccess;
+}
+
+bool tensor_dense(const sppc_ctx* h, int nq, bool update_kind) {
+  if (!h->Qd || h->kp != 8) return false;
+  return nq >= (h->f64 ? 2 : (update_kind ? 10 : 5));
+}
+
+// Update against W blocks 0 .. nq - 1 (the restart's W Y, the recycled H Psi of
+// Eq. HPsip): tensor cores under qupdate's conditions, else CUDA cores.
+cudaError_t wupdate(sppc_ctx* h, int nq, float2* Y, const float2* X, const float2* alpha, const float2* coef,
+                    cudaStream_t s) {
+  if (tensor_dense(h, nq, true)) {
+    cudaError_t e = ensure_wdigits(h, nq, s);
+    if (e != cudaSuccess) return e;
+    return update_tc(h->Wd, nq, coef, alpha, X, Y, h->n, h->f64, h->dStatus + 8, s, h->wexp);
+  }
+  return update(Y, X, alpha, blocks(h->W, h->n, h->kp, 0, nq), coef, h->kp, 0, h->n, h->f64, s);
+}
+
+__global__ void k_neg_slots(const float2* in, float2* out, int count, bool f64) {
+  const int i = threadIdx.x;
+  if (i < count) out[i] = f64 ? make_float2(in[i].x, -in[i].y) : make_float2(-in[i].x, -in[i].y);
+}
+
+// The Ritz pass over blocks 0 .. np1 - 1 (Eq. rrn): ritz_resid's outputs (dDots =
+// squared residual norms; optional Z, T, leading rows).  On the tensor cores:
+// Zt = Q Y, Dt = W Y - Z theta (two tensor-core updates), then the norms, the
+// preconditioned block and the copies from Zt and Dt.
+cudaError_t qritz(sppc_ctx* h, int np1, double* Zout, int64_t ldz, int ncols, float2* Tout, const float2* diag,
+                  float clamp, float2* Zlead, float2* Rlead, int64_t nlead, cudaStream_t s) {
+  const int kp = h->kp;
+  const int64_t n = h->n;
+  if (!tensor_dense(h, np1, true))
+    return ritz_resid(blocks(h->Q, n, kp, 0, np1), blocks(h->W, n, kp, 0, np1), h->dY, h->dCoef + kTheta, kp, n,
+                      h->dDots, h->partials, h->partial_cap, Zout, ldz, ncols, Tout, diag, clamp, h->f64, s, Zlead,
+                      Rlead, nlead);
+  cudaError_t e = ensure_qdigits(h, np1, s);
+  if (e == cudaSuccess) e = ensure_wdigits(h, np1, s);
+  if (e != cudaSuccess) return e;
+  k_neg_slots<<<1, 32, 0, s>>>(h->dCoef + kTheta, h->dCoef + kRitzNegTh, kp, h->f64);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = update_tc(h->Qd, np1, h->dY, nullptr, nullptr, h->Zt, n, h->f64, h->dStatus + 8, s)) != cudaSuccess) return e;
+  if ((e = update_tc(h->Wd, np1, h->dY, h->dCoef + kRitzNegTh, h->Zt, h->Dt, n, h->f64, h->dStatus + 8, s, h->wexp)) !=
+      cudaSuccess)
+    return e;
+  {
+    const float2* A[1] = {h->Dt};
+    const float2* B[1] = {h->Dt};
+    if ((e = coldots(A, B, 1, kp, 0, n, h->dDots, h->partials, h->partial_cap, h->f64, s)) != cudaSuccess) return e;
+  }
+  if (Zout && (e = df_to_f64(h->Zt, kp, Zout, ldz, ncols, 0, n, h->f64, s)) != cudaSuccess) return e;
+  if (nlead > 0 && Zlead) {
+    if ((e = cudaMemcpyAsync(Zlead, h->Zt, sizeof(float2) * nlead * kp, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(Rlead, h->Dt, sizeof(float2) * nlead * kp, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return e;
+  }
+  if (Tout) e = ritz_precond(h->Dt, h->dCoef + kTheta, diag, clamp, Tout, kp, n, h->f64, s);
+  return e;
+}
+
 // ------------------------------------------------------- Rayleigh-Ritz core
 // Rayleigh-Ritz on blocks 0..p: border the projected matrix with Q^T W_p (Eq.
 // proj), its nev = min(2k, m) lowest eigenpairs (the first k are the Ritz pairs;
@@ -1170,10 +1253,8 @@ sppc_status rr_core(sppc_ctx* h, int p, bool want_z, double* Z, int64_t ldz, flo
   k_expand_y<<<1, 256, 0, s>>>(h->dV, nev, p, k, kp, h->dTheta, h->dY, h->dCoef + kTheta, h->f64); count_launch();
   CK(cudaGetLastError());
   const bool lead = T != nullptr && h->opt.precond == 2;
-  CK(ritz_resid(blocks(h->Q, n, kp, 0, p + 1), blocks(h->W, n, kp, 0, p + 1), h->dY, h->dCoef + kTheta, kp, n,
-                h->dDots, h->partials, h->partial_cap, want_z ? Z : nullptr, ldz, k, T, diag,
-                (float)h->opt.precond_clamp, h->f64, s, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
-                lead ? h->n_lead : 0));
+  CK(qritz(h, p + 1, want_z ? Z : nullptr, ldz, k, T, diag, (float)h->opt.precond_clamp, lead ? h->zlead : nullptr,
+           lead ? h->rlead : nullptr, lead ? h->n_lead : 0, s));
   if (defer) {
     // results land in pinned host memory; rr_finish() reads them after a sync
     CK(cudaMemcpyAsync(h->pinned, h->dTheta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
@@ -1280,8 +1361,7 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
     k_restart_coef<<<1, 256, 0, s>>>(h->dV, h->nev, p, k, kp, b, h->dCoefBig, h->f64); count_launch();
     CK(cudaGetLastError());
     CK(qupdate(h, p + 1, blk(h->Psi, n, kp, b), nullptr, nullptr, h->dCoefBig, s));
-    CK(update(blk(h->Psi, n, kp, 2 + b), nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dCoefBig, kp, 0, n, h->f64,
-              s));
+    CK(wupdate(h, p + 1, blk(h->Psi, n, kp, 2 + b), nullptr, nullptr, h->dCoefBig, s));
   }
   CK(cudaMemcpyAsync(h->Q, h->Psi, sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
   h->qd_valid = 0;
@@ -1291,6 +1371,7 @@ sppc_status restart(sppc_ctx* h, bool fresh_products = false) {
     h->stats.spmv_h += 2 * h->k;
   } else {
     CK(cudaMemcpyAsync(h->W, blk(h->Psi, n, kp, 2), sizeof(float2) * 2 * n * kp, cudaMemcpyDeviceToDevice, s));
+    h->wd_valid = 0;
   }
   for (int b = 0; b < 2; ++b) {
     CK(qgram(h, b + 1, blk(h->W, n, kp, b), h->dGram, s));
@@ -1433,10 +1514,8 @@ sppc_status refine_step(sppc_ctx* h) {
   // T from the current Ritz pairs: written by the previous Rayleigh-Ritz pass when
   // it already ran in continuation mode, else one extra pass over Q and W
   if (!h->t_ready) {
-    CK(ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
-                  n, h->dDots, h->partials, h->partial_cap, nullptr, 0, 0, h->HPsi, t_diag(h),
-                  (float)h->opt.precond_clamp, h->f64, h->stream, lead ? h->zlead : nullptr, lead ? h->rlead : nullptr,
-                  lead ? h->n_lead : 0));
+    CK(qritz(h, h->p + 1, nullptr, 0, 0, h->HPsi, t_diag(h), (float)h->opt.precond_clamp, lead ? h->zlead : nullptr,
+             lead ? h->rlead : nullptr, lead ? h->n_lead : 0, h->stream));
   }
   h->t_ready = false;
   float2* T = h->HPsi;
@@ -1524,7 +1603,8 @@ sppc_status rmm_run(sppc_ctx* h, double tol) {
   Lx.n = Lr.n = d;
   float2* hx[8];
   float2* hr[8];
-  h->qd_valid = 0;  // the RMM-DIIS history overwrites the basis blocks
+  h->qd_valid = 0;  // the RMM-DIIS history overwrites the basis blocks and W
+  h->wd_valid = 0;
   for (int a = 0; a < d; ++a) {
     hx[a] = blk(h->Q, n, kp, a);
     hr[a] = blk(h->W, n, kp, a);
@@ -2276,8 +2356,18 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       if (e == cudaSuccess) e = dalloc(h, p, c);
     };
     A(&h->Q, nb);
-    if (h->opt.tensor_gram && kp == 8 && e == cudaSuccess)
-      e = dalloc(h, &h->Qd, (size_t)((h->pmax + 1 + 15) / 16) * (size_t)qdigits_group_bytes(n));
+    if (h->opt.tensor_gram && kp == 8) {
+      const size_t dbytes = (size_t)((h->pmax + 1 + 15) / 16) * (size_t)qdigits_group_bytes(n);
+      if (e == cudaSuccess) e = dalloc(h, &h->Qd, dbytes);
+      if (e == cudaSuccess) e = dalloc(h, &h->Wd, dbytes);
+      if (e == cudaSuccess) e = dalloc(h, &h->wexp, (size_t)(h->pmax + 1) * 8);
+      // stale tiles hold finite digits (blocks beyond a Gram's or update's count meet
+      // zero coefficients)
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->Qd, 0, dbytes, h->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->Wd, 0, dbytes, h->stream);
+      A(&h->Zt, (size_t)n * 8);
+      A(&h->Dt, (size_t)n * 8);
+    }
     A(&h->W, nb);
     A(&h->Psi, nb);
     A(&h->HPsi, (size_t)n * kp);
@@ -2535,7 +2625,7 @@ sppc_status sppc_rayleigh_ritz(sppc_handle h, double* theta, double* resid, void
   h->stats.spmv_h += h->k;
   CKS(rr_core(h, p, false, nullptr, 0));
   // H Psi^(p) = W_{0..p-1} C + W_p R (Eq. HPsip)
-  CK(update(h->HPsi, nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dRecycle, kp, 0, n, h->f64, s));
+  CK(wupdate(h, p + 1, h->HPsi, nullptr, nullptr, h->dRecycle, s));
   OrderRec& r = h->rec.back();
   r.theta = h->theta;
   r.resid = h->resid;
@@ -2617,7 +2707,7 @@ static sppc_status overlap_order(sppc_ctx* h, bool next, bool* pre) {
   // next correction needs
   CKS(big_spmm(h, blk(h->Q, n, kp, p), blk(h->W, n, kp, p), kp));
   h->stats.spmv_h += h->k;
-  CK(update(h->HPsi, nullptr, nullptr, blocks(h->W, n, kp, 0, p + 1), h->dRecycle, kp, 0, n, h->f64, s));
+  CK(wupdate(h, p + 1, h->HPsi, nullptr, nullptr, h->dRecycle, s));
   if (next) CK(cudaEventRecord(h->ev_a, s));  // the correction waits for H Psi^(p) only
   CKS(rr_core(h, p, false, nullptr, 0, nullptr, nullptr, next));
   const size_t rec_p = h->rec.size() - 1;
@@ -2919,9 +3009,7 @@ sppc_status sppc_proposal_samples(sppc_handle h, const double* psi, int64_t ldps
   cudaError_t e = cudaMallocAsync(&scr, sizeof(double) * prop_samples_scratch_doubles(), s);
   // Ritz vectors and raw residuals (into Tplain) of the current subspace
   if (e == cudaSuccess)
-    e = ritz_resid(blocks(h->Q, n, kp, 0, h->p + 1), blocks(h->W, n, kp, 0, h->p + 1), h->dY, h->dCoef + kTheta, kp,
-                   n, h->dDots, h->partials, h->partial_cap, Zd, k, k, h->Tplain, nullptr, (float)h->opt.precond_clamp, h->f64,
-                   s, nullptr, nullptr, 0);
+    e = qritz(h, h->p + 1, Zd, k, k, h->Tplain, nullptr, (float)h->opt.precond_clamp, nullptr, nullptr, 0, s);
   if (e == cudaSuccess) e = prop_prep(h->Tplain, kp, k, h->dDots, n, h->rhat32, h->X32, s);
   if (e == cudaSuccess) e = spmm_abs_f32(h->H, h->val32, h->val16, h->diag32, h->X32, h->T2, s);
   if (e == cudaSuccess)

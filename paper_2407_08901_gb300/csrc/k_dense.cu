@@ -443,6 +443,36 @@ cudaError_t gram_finish(const float2* partials, int64_t nchunks, int nout, doubl
   return finish(partials, nchunks, nout, out, f64, s);
 }
 
+namespace {
+template <bool F64>
+__global__ void k_ritz_precond(const float2* __restrict__ D, const float2* __restrict__ theta,
+                               const float2* __restrict__ diag, float clamp, float2* __restrict__ T, int kp,
+                               int64_t n) {
+  using V = Ar<F64>;
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n * kp) return;
+  const int64_t r = e / kp;
+  const int j = static_cast<int>(e - r * kp);
+  float2 t = D[e];
+  if (diag) t = V::div(t, V::clamp_den(V::sub(diag[r], theta[j]), clamp));
+  T[e] = t;
+}
+}  // namespace
+
+// The preconditioned residual block of the Ritz pass (the division k_ritz_resid
+// applies), from a residual block computed elsewhere.
+cudaError_t ritz_precond(const float2* D, const float2* theta, const float2* diag, float clamp, float2* T, int kp,
+                         int64_t n, bool f64, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned g = nblk(n * kp, 256);
+  if (f64)
+    k_ritz_precond<true><<<g, 256, 0, s>>>(D, theta, diag, clamp, T, kp, n);
+  else
+    k_ritz_precond<false><<<g, 256, 0, s>>>(D, theta, diag, clamp, T, kp, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef, int kp,
                    int64_t r0, int64_t r1, bool f64, cudaStream_t s) {
   if (r1 <= r0) return cudaSuccess;

@@ -69,17 +69,22 @@ static_assert(2 * 128 <= kTmemCols, "two accumulator regions");
 static_assert(7 + kLevels <= kCTiles, "C windows");
 
 // One basis block (n rows x 8 columns of slots) cut into its digit tiles at
-// out (= the group's digits + 2048 a for block a of the group): thread u handles
+// out (= the group's digits + 2048 a for block a of the group), in fixed point
+// 2^61 (colexp null: |v| < 2) or 2^(61 - colexp[i]) per column i (|v| <
+// 2^colexp[i], the column exponents of a block of H Q): thread u handles
 // chunk u / 16, rows 8 ((u / 8) % 2) .. + 7 of the chunk, column i = u % 8, and
 // writes 16 bytes (the half (u / 8) % 2 of atom row i) per digit plane.  Rows
 // >= n get zero digits.
 template <bool F64>
 __global__ void __launch_bounds__(256) k_qcut(const float2* __restrict__ Q, int64_t n, int64_t nchunks,
-                                              unsigned char* __restrict__ out, int* __restrict__ err) {
+                                              const int* __restrict__ colexp, unsigned char* __restrict__ out,
+                                              int* __restrict__ err) {
   const int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (u >= nchunks * 16) return;
   const int64_t c = u >> 4;
   const int kq = static_cast<int>((u >> 3) & 1), i = static_cast<int>(u & 7);
+  int shift = kQShift;  // per column: X = round(|v| 2^(61 - e_i)) when |v| < 2^e_i
+  if (colexp) shift -= colexp[i] < -5000 ? 0 : colexp[i];
   uint64_t x[8];
   bool ng[8];
   bool bad = false;
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(256) k_qcut(const float2* __restrict__ Q, int6
   for (int rr = 0; rr < 8; ++rr) {
     const int64_t r = c * kTcRows + kq * 8 + rr;
     const float2 v = r < n ? Q[r * 8 + i] : make_float2(0.f, 0.f);
-    if (!to_fixed<F64>(v, kQShift, x[rr], ng[rr])) {
+    if (!to_fixed<F64>(v, shift, x[rr], ng[rr])) {
       bad = true;
       x[rr] = 0;
     }
@@ -367,14 +372,28 @@ unsigned char* qdigits_block(unsigned char* Qd, int64_t n, int a) {
   return Qd + (a / 16) * qdigits_group_bytes(n) + (a % 16) * kBlockChunk;
 }
 
-cudaError_t qcut(const float2* Q, int64_t n, unsigned char* out, bool f64, int* err, cudaStream_t s) {
+cudaError_t qcut(const float2* Q, int64_t n, unsigned char* out, bool f64, int* err, cudaStream_t s,
+                 const int* colexp_dev) {
   const int64_t nch = (n + kTcRows - 1) / kTcRows;
   if (nch == 0) return cudaSuccess;
   const unsigned g = static_cast<unsigned>((nch * 16 + 255) / 256);
   if (f64)
-    k_qcut<true><<<g, 256, 0, s>>>(Q, n, nch, out, err);
+    k_qcut<true><<<g, 256, 0, s>>>(Q, n, nch, colexp_dev, out, err);
   else
-    k_qcut<false><<<g, 256, 0, s>>>(Q, n, nch, out, err);
+    k_qcut<false><<<g, 256, 0, s>>>(Q, n, nch, colexp_dev, out, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t colexp(const float2* B, int64_t n, int* fexp, bool f64, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(fexp, 0x80, sizeof(int) * 8, s);  // below any exponent
+  if (e != cudaSuccess || n <= 0) return e;
+  int64_t g = (n + 31) / 32;
+  if (g > 4 * sm_count()) g = 4 * sm_count();
+  if (f64)
+    k_colexp<true><<<static_cast<unsigned>(g), 256, 0, s>>>(B, n, fexp);
+  else
+    k_colexp<false><<<static_cast<unsigned>(g), 256, 0, s>>>(B, n, fexp);
   count_launch();
   return cudaGetLastError();
 }
@@ -398,19 +417,8 @@ cudaError_t gram_tc(const unsigned char* Qd, int nblocks, const float2* B, int64
   if (nblocks < 0 || nblocks > kMaxBlocks) return cudaErrorInvalidValue;
   if (n <= 0 || nblocks == 0) return cudaMemsetAsync(out, 0, sizeof(double) * nblocks * 64, s);
   const int sms = sm_count();
-  // B's column exponents (preset to 0x80808080, below any exponent)
-  cudaError_t e = cudaMemsetAsync(fexp, 0x80, sizeof(int) * 8, s);
+  cudaError_t e = colexp(B, n, fexp, f64, s);  // B's column exponents
   if (e != cudaSuccess) return e;
-  {
-    int64_t g = (n + 31) / 32;
-    if (g > 4 * sms) g = 4 * sms;
-    if (f64)
-      k_colexp<true><<<static_cast<unsigned>(g), 256, 0, s>>>(B, n, fexp);
-    else
-      k_colexp<false><<<static_cast<unsigned>(g), 256, 0, s>>>(B, n, fexp);
-    count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
   int64_t per = 0, ctas = 0;
   gram_tc_geometry(n, sms, &per, &ctas);
   const int64_t gb = qdigits_group_bytes(n);

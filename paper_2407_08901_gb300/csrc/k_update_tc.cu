@@ -59,12 +59,14 @@ __device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
 }
 
 // Qd: digits of blocks 0 .. na - 1 (na <= 16) of one group; coef: 8 na x 8 slots,
-// row (8 a + i); xmode 0: no X term, 1: alpha X (alpha: 8 slots), 2: X.
+// row (8 a + i); rowexp: null (blocks cut at 2^61) or the blocks' column
+// exponents e (cut at 2^(61 - e)), one per coefficient row, folded into the
+// coefficients; xmode 0: no X term, 1: alpha X (alpha: 8 slots), 2: X.
 template <bool F64>
 __global__ void __launch_bounds__(kUThreads, 1)
     k_update_tc(const unsigned char* __restrict__ Qd, int na, const float2* __restrict__ coef,
-                const float2* __restrict__ alpha, const float2* X, int xmode, float2* Y, int64_t n,
-                int64_t rows_per_cta, int* __restrict__ err) {
+                const int* __restrict__ rowexp, const float2* __restrict__ alpha, const float2* X, int xmode,
+                float2* Y, int64_t n, int64_t rows_per_cta, int* __restrict__ err) {
   using V = Ar<F64>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kUStages], mma_bar[kUStages], acc_bar[2], free_bar[2];
@@ -113,7 +115,11 @@ __global__ void __launch_bounds__(kUThreads, 1)
   __syncthreads();
   // C's column exponents, then its digits into the window tiles of each K step
   const int ncoef = 64 * na;
-  for (int e = tid; e < ncoef; e += kUThreads) atomicMax(&gexp[e & 7], exp_bound<F64>(coef[e]));
+  auto row_e = [&](int i) -> int { return rowexp ? (rowexp[i] < -5000 ? 0 : rowexp[i]) : 0; };
+  for (int e = tid; e < ncoef; e += kUThreads) {
+    const int eb = exp_bound<F64>(coef[e]);
+    atomicMax(&gexp[e & 7], eb < -5000 ? eb : eb + row_e(e >> 3));
+  }
   __syncthreads();
   {
     bool bad = false;
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
       const int g = gexp[j] < -5000 ? 0 : gexp[j];
       uint64_t x;
       bool ng;
-      if (!to_fixed<F64>(coef[e], kQShift - g, x, ng)) {
+      if (!to_fixed<F64>(coef[e], kQShift - g + row_e(i), x, ng)) {
         bad = true;
         x = 0;
       }
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
 
 // Rows per CTA: one CTA per SM, multiples of the 128-row tile.
 cudaError_t update_tc(const unsigned char* Qd, int nblocks, const float2* coef, const float2* alpha, const float2* X,
-                      float2* Y, int64_t n, bool f64, int* err, cudaStream_t s) {
+                      float2* Y, int64_t n, bool f64, int* err, cudaStream_t s, const int* rowexp) {
   if (nblocks < 0 || nblocks > kMaxBlocks) return cudaErrorInvalidValue;
   if (n <= 0) return cudaSuccess;
   static const int sms = [] {
@@ -306,10 +312,11 @@ cudaError_t update_tc(const unsigned char* Qd, int nblocks, const float2* coef, 
     const int xmode = a0 == 0 ? (X && alpha ? 1 : 0) : 2;
     const unsigned char* q = Qd + (a0 / 16) * gb;
     const unsigned g = static_cast<unsigned>(ctas);
+    const int* re = rowexp ? rowexp + a0 * 8 : nullptr;
     if (f64)
-      k_update_tc<true><<<g, kUThreads, kUSmem, s>>>(q, na, coef + a0 * 64, alpha, x, xmode, Y, n, per, err);
+      k_update_tc<true><<<g, kUThreads, kUSmem, s>>>(q, na, coef + a0 * 64, re, alpha, x, xmode, Y, n, per, err);
     else
-      k_update_tc<false><<<g, kUThreads, kUSmem, s>>>(q, na, coef + a0 * 64, alpha, x, xmode, Y, n, per, err);
+      k_update_tc<false><<<g, kUThreads, kUSmem, s>>>(q, na, coef + a0 * 64, re, alpha, x, xmode, Y, n, per, err);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

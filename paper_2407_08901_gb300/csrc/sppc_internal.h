@@ -195,7 +195,13 @@ cudaError_t gram_finish(const float2* partials, int64_t nchunks, int nout, doubl
 // partials needs ceil(n / per) * 64 * min(nblocks, 16) slots (gram_tc_geometry).
 int64_t qdigits_group_bytes(int64_t n);
 unsigned char* qdigits_block(unsigned char* Qd, int64_t n, int a);
-cudaError_t qcut(const float2* Q, int64_t n, unsigned char* out, bool f64, int* err, cudaStream_t s);
+// colexp_dev (device, 8 ints, optional): column exponents e_i (|v| < 2^e_i) for
+// blocks that are not orthonormal (H Q); the tiles are then cut at 2^(61 - e_i).
+cudaError_t qcut(const float2* Q, int64_t n, unsigned char* out, bool f64, int* err, cudaStream_t s,
+                 const int* colexp_dev = nullptr);
+// fexp[j] (device, 8 ints) = max over rows of e with |B[r][j]| < 2^e (a very
+// negative value for an all-zero column).
+cudaError_t colexp(const float2* B, int64_t n, int* fexp, bool f64, cudaStream_t s);
 cudaError_t gram_tc(const unsigned char* Qd, int nblocks, const float2* B, int64_t n, double* out, float2* partials,
                     int64_t partial_cap, bool f64, int* err, int* fexp, cudaStream_t s);
 void gram_tc_geometry(int64_t rows, int sms, int64_t* per, int64_t* ctas);
@@ -205,8 +211,14 @@ void gram_tc_geometry(int64_t rows, int sms, int64_t* per, int64_t* ctas);
 // Q_a coef_a, coef[(8 a + i) * 8 + j], the X term present when X and alpha are
 // both given (as in update()), Y may alias X.  *err as for gram_tc (bit 0: a
 // coefficient not finite).
+// rowexp (device, 8 nblocks ints, optional): the blocks' column exponents when
+// their tiles were cut with colexp_dev (blocks of H Q).
 cudaError_t update_tc(const unsigned char* Qd, int nblocks, const float2* coef, const float2* alpha, const float2* X,
-                      float2* Y, int64_t n, bool f64, int* err, cudaStream_t s);
+                      float2* Y, int64_t n, bool f64, int* err, cudaStream_t s, const int* rowexp = nullptr);
+// Preconditioned residual block T[r][j] = D[r][j] / clamp(diag[r] - theta_j)
+// (|denominator| >= clamp), or T = D without diag; theta: kp slots.
+cudaError_t ritz_precond(const float2* D, const float2* theta, const float2* diag, float clamp, float2* T, int kp,
+                         int64_t n, bool f64, cudaStream_t s);
 
 // Update: Y[r][j] = alpha[j] X[r][j] + sum_a sum_i A_a[r][i] coef[(a*kp+i)*kp + j]
 // (coef double-float on device; X may be null; Y may alias X but no block of A).
