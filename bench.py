@@ -76,11 +76,12 @@ def parse_args():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 64-matrix workload")
     ap.add_argument("--no-c3", action="store_true", help="skip the n = 2e7 mixed-precision workload (config 3)")
-    ap.add_argument("--tensor-gram", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--tensor-gram", type=int, default=1, choices=[0, 1],
                     help="Gram products against the basis on the tensor cores (opts.tensor_gram)")
     ap.add_argument("--precision", type=int, default=-1, choices=[-1, 0],
                     help="value format of the --profile spmm / solve / minres runs: -1 native FP64, 0 double-float")
-    ap.add_argument("--profile", default="none", choices=["none", "spmm", "spmm32", "spmm16", "solve", "minres", "learned"],
+    ap.add_argument("--profile", default="none",
+                    choices=["none", "spmm", "spmm32", "spmm16", "solve", "minres", "learned", "dense"],
                     help="run the workload's SpMM twice (spmm; spmm32 / spmm16: the FP32- / BF16-value kernels), "
                          "one solve with the bench options (solve), or three plain SPPC orders (minres: two "
                          "small-space MINRES solves, few GB held) or one solve with the learned proposal (learned) "
@@ -785,6 +786,20 @@ def run_profile(args):
     import paper_2407_08901_gb300 as S
     import workloads as W
 
+    if args.profile == "dense":
+        # the tensor-core Gram and update kernels alone on n = 5e5 rows (A = 512 MB
+        # of FP64 values, 1 GB of digit tiles at 16 blocks), 1 and 16 blocks
+        n = 500_000
+        g = torch.Generator(device="cuda").manual_seed(1)
+        A = torch.randn(16, n, 8, device="cuda", dtype=torch.float64, generator=g) / n ** 0.5
+        B = torch.randn(n, 8, device="cuda", dtype=torch.float64, generator=g)
+        for nb in (1, 16):
+            C = torch.randn(8 * nb, 8, device="cuda", dtype=torch.float64, generator=g)
+            S.sppc_block_gram(A[:nb].contiguous(), B, tensor=True, df=args.precision == 0)
+            S.sppc_block_update(A[:nb].contiguous(), C, None, B, tensor=True, df=args.precision == 0)
+        torch.cuda.synchronize()
+        print(f"profile dense: n {n}, blocks 1 and 16, precision {args.precision}", flush=True)
+        return 0
     w = W.config(args.workload)
     rp, c, v = W.generate(w)
     k = w.k
