@@ -38,7 +38,11 @@
 // SM, 256 threads) six stages rotate: the copies of chunks k + 1 .. k + 4 fly
 // while 128 threads cut B's values of chunk k (in shared memory) into C and one
 // thread issues the chunk's eight MMAs (M = 128, N = 80, K = 16), committed to
-// the stage's mbarrier.  B's column exponents f_j come from a separate pass over
+// the stage's mbarrier.  With at most 8 blocks (64 basis columns) the A tile's
+// upper half is idle, so a second copy of the pieces, shifted by one digit plane,
+// fills it: one MMA then takes digit 2p in lanes 0-63 and digit 2p + 1 in lanes
+// 64-127 against digit 2p's window (the upper lanes land one level higher and
+// are read back as such), four MMAs a chunk instead of eight.  B's column exponents f_j come from a separate pass over
 // B (k_colexp).  Every 64 rows D is read back (tcgen05.ld) and added into 64-bit
 // integers, three levels to a word (exact).  At the end each column's words are
 // scaled and added in FP64 and written as the CTA's partial result for the
@@ -65,6 +69,10 @@ constexpr int kStageBytes = kABytes + kBRaw + kCTiles * kAtom;  // 38,144
 constexpr int kStages = 6;                       // copies run kStages - 2 chunks ahead
 constexpr int kTcSmem = kStages * kStageBytes + 1024;   // + alignment slack: one CTA per SM
 constexpr int kTmemCols = 256;                  // two D regions of 128 columns
+// Stacked mode (na <= 8): a second copy of a chunk's digit pieces, without its
+// first plane (block 0's digit 0, never read there), lands at A row group 8 so
+// that row group 8 + a reads block a one digit plane further on.
+constexpr int kStackCopy = 8 * kBlockChunk;
 static_assert(2 * 128 <= kTmemCols, "two accumulator regions");
 static_assert(7 + kLevels <= kCTiles, "C windows");
 
@@ -166,6 +174,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int M = na * 8;
+  // up to 8 blocks: digits 2p and 2p + 1 share an MMA (A rows 0-63 and 64-127)
+  const bool stack = na <= 8;
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta;
   const int64_t c1 = min(c0 + rows_per_cta, n);
   const int64_t nck = (c1 - c0 + kTcRows - 1) / kTcRows;
@@ -225,10 +235,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int64_t base = c0 + k * kTcRows;
         const int rows = static_cast<int>(c1 - base < kTcRows ? c1 - base : kTcRows);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"(static_cast<uint32_t>(na * kBlockChunk + rows * 64))
+                     "r"(static_cast<uint32_t>((stack ? 2 * na * kBlockChunk - kAtom : na * kBlockChunk) + rows * 64))
                      : "memory");
         const uint32_t dst = smem_u32(smem + st * kStageBytes);
-        bulk_g2s(dst, Qd + (gc0 + k) * kGroupChunk, na * kBlockChunk, bar);
+        const unsigned char* src = Qd + (gc0 + k) * kGroupChunk;
+        bulk_g2s(dst, src, na * kBlockChunk, bar);
+        if (stack) bulk_g2s(dst + kStackCopy, src + kAtom, na * kBlockChunk - kAtom, bar);
         bulk_g2s(dst + kABytes, B + base * 8, rows * 64, bar);
         armed[st] += 1;
       }
@@ -249,10 +261,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!role_wait(smem_u32(&cut_bar[st]), static_cast<uint32_t>((k / kStages) & 1), abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = smem_u32(smem + st * kStageBytes), cb = a0 + kABytes + kBRaw;
+        if (stack) {
+          // digits 2p (rows 0-63 of A) and 2p + 1 (rows 64-127, from the second
+          // copy) in one MMA, both against digit 2p's window
 #pragma unroll
-        for (int s = 0; s < 8; ++s)
-          mma_f16(tmem + static_cast<uint32_t>(r * 128), smem_desc_sw32(a0 + s * kAtom, kBlockChunk),
-                  smem_desc_sw32(cb + (7 - s) * kAtom, kAtom), idesc, (!first || s > 0) ? 1u : 0u);
+          for (int p = 0; p < 4; ++p)
+            mma_f16(tmem + static_cast<uint32_t>(r * 128), smem_desc_sw32(a0 + 2 * p * kAtom, kBlockChunk),
+                    smem_desc_sw32(cb + (7 - 2 * p) * kAtom, kAtom), idesc, (!first || p > 0) ? 1u : 0u);
+        } else {
+#pragma unroll
+          for (int s = 0; s < 8; ++s)
+            mma_f16(tmem + static_cast<uint32_t>(r * 128), smem_desc_sw32(a0 + s * kAtom, kBlockChunk),
+                    smem_desc_sw32(cb + (7 - s) * kAtom, kAtom), idesc, (!first || s > 0) ? 1u : 0u);
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mma_bar[st]))
                      : "memory");
@@ -306,7 +327,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int r = static_cast<int>(g & 1);
       if (!role_wait(smem_u32(&acc_bar[r]), static_cast<uint32_t>((g >> 1) & 1), abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (32 * q < M) read_levels(taddr + static_cast<uint32_t>(r * 128), acc);
+      if (!stack) {
+        if (32 * q < M) read_levels<0>(taddr + static_cast<uint32_t>(r * 128), acc);
+      } else if (q < 2) {
+        if (32 * q < M) read_levels<0>(taddr + static_cast<uint32_t>(r * 128), acc);
+      } else {
+        // digit 2p + 1 against digit 2p's window: one level up (up to level 10)
+        if (32 * (q - 2) < M) read_levels<1>(taddr + static_cast<uint32_t>(r * 128), acc);
+      }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&free_bar[r]));
     }
@@ -326,8 +354,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     __syncthreads();
   }
+  // stacked: lanes 64 + i hold basis column i's odd digits; fold them onto lane i
+  long long* fold = reinterpret_cast<long long*>(smem);  // the stages are idle now
+  if (stack && warp >= 10) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) fold[((32 * (warp - 10) + lane) * 8 + j) * 4 + c] = acc[j][c];
+  }
+  __syncthreads();
+  if (stack && warp >= 8 && warp < 10) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[j][c] += fold[((32 * (warp - 8) + lane) * 8 + j) * 4 + c];
+  }
   // read-back warps: A column i = 32 (warp - 8) + lane, every B column, scaled in FP64
-  if (warp >= 8) {
+  if (warp >= 8 && !(stack && warp >= 10)) {
     const int i = 32 * (warp - 8) + lane;
     if (i < M) {
       const int nout = M * 8;

@@ -20,10 +20,13 @@
 // (two blocks each) stream through five shared-memory stages: warp 1 copies a
 // step's eight 16-row chunks (cp.async.bulk, the two blocks' 4 KB of a chunk
 // each), warp 0 issues its eight MMAs into the tile's region (two regions
-// alternate between tiles), warps 4-7 read a finished tile back (tcgen05.ld, one
-// row per thread), turn each column's level sums into one value by integer
-// arithmetic (tc_digits.cuh: an exact 128-bit sum, rounded once), add alpha X
-// (when X and alpha are given, as update() does) and store Y.  Y may alias X (a row is read and written by one thread).  Errors: a
+// alternate between tiles), and two groups of four warps (4-7 for the even
+// tiles, 8-11 for the odd ones, so that two tiles' epilogues overlap) read a
+// finished tile back (tcgen05.ld, one row per thread), turn each column's level
+// sums into one value by integer arithmetic (tc_digits.cuh: an exact 128-bit
+// sum, rounded once), add alpha X (when X and alpha are given, as update() does;
+// the X row is loaded before the tile's MMAs are waited for) and store Y.  Y may
+// alias X (a row is read and written by one thread).  Errors: a
 // non-finite coefficient sets bit 0 of *err, a timed-out wait (about a second)
 // bit 1; after a time-out the kernel waits (bounded) for its copies and MMAs in
 // flight and frees its tensor memory.
@@ -37,7 +40,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kUThreads = 256;                          // warps: 0 MMA, 1 copies, 4-7 read-back
+constexpr int kUThreads = 384;                          // warps: 0 MMA, 1 copies, 4-7 and 8-11 read-back
 constexpr int kTileRows = 128;                          // rows per tile: the MMA's M
 constexpr int kTileChunks = kTileRows / kTcRows;        // 8 digit chunks per tile
 constexpr int kChunkStride = 2 * kBlockChunk;           // a chunk's two blocks of one K step in a stage
@@ -209,17 +212,25 @@ __global__ void __launch_bounds__(kUThreads, 1)
     }
     __syncwarp();
   } else if (warp >= 4) {
-    // ---- read-back and epilogue: row 32 (warp - 4) + lane of each tile
-    const int q = warp - 4;
-    const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * q) << 16);
+    // ---- read-back and epilogue: group r = (warp - 4) / 4 takes the tiles of
+    // region r, row 32 q + lane of each (tensor-memory lanes 32 q .., q = warp % 4)
+    const int q = warp & 3, r = (warp - 4) >> 2;
+    const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(r * 128);
     int g[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) g[j] = gexp[j] < -5000 ? 0 : gexp[j];
     float2 al[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) al[j] = xmode == 1 ? alpha[j] : V::from_d(1.0);
-    for (int64_t tile = 0; tile < ntiles; ++tile) {
-      const int r = static_cast<int>(tile & 1);
+    for (int64_t tile = r; tile < ntiles; tile += 2) {
+      const int64_t row = c0 + tile * kTileRows + 32 * q + lane;
+      // X's row first: its load flies while the tile's MMAs finish
+      float4 xr[4];
+      if (xmode && row < c1) {
+        const float4* xp = reinterpret_cast<const float4*>(X + row * 8);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) xr[h] = xp[h];
+      }
       if (!role_wait(smem_u32(&acc_bar[r]), static_cast<uint32_t>((tile >> 1) & 1), abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       long long acc[8][4];
@@ -227,19 +238,16 @@ __global__ void __launch_bounds__(kUThreads, 1)
       for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[j][c] = 0;
-      read_levels(taddr + static_cast<uint32_t>(r * 128), acc);
+      read_levels<0>(taddr, acc);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&free_bar[r]));
-      const int64_t row = c0 + tile * kTileRows + 32 * q + lane;
       if (row < c1) {
         float2 x[8];
         if (xmode) {
-          const float4* xp = reinterpret_cast<const float4*>(X + row * 8);
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            const float4 t = xp[h];
-            x[2 * h] = make_float2(t.x, t.y);
-            x[2 * h + 1] = make_float2(t.z, t.w);
+            x[2 * h] = make_float2(xr[h].x, xr[h].y);
+            x[2 * h + 1] = make_float2(xr[h].z, xr[h].w);
           }
         }
         float2 y[8];

@@ -233,8 +233,10 @@ __device__ __forceinline__ void tmem_wait8(uint32_t (&v)[8]) {
 }
 
 // Reads back D (one region) for the warp's 32 tensor-memory lanes at taddr, all
-// eight B columns and every level L, adding level L into acc[j][L / 3] with
-// weight 256^(2 - L % 3).
+// eight B columns and every level L, adding level L + UP into acc[j][(L + UP) / 3]
+// with weight 256^(2 - (L + UP) % 3) (UP = 1: lanes whose digits sit one level
+// higher than the columns' index says).
+template <int UP>
 __device__ __forceinline__ void read_levels(uint32_t taddr, long long (&acc)[8][4]) {
 #pragma unroll
   for (int L = 0; L < kLevels; ++L) {
@@ -247,7 +249,7 @@ __device__ __forceinline__ void read_levels(uint32_t taddr, long long (&acc)[8][
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const long long q = static_cast<long long>(__float2int_rn(__uint_as_float(v[j])));
-      acc[j][L / 3] += q * (1ll << (8 * (2 - L % 3)));
+      acc[j][(L + UP) / 3] += q * (1ll << (8 * (2 - (L + UP) % 3)));
     }
   }
 }
