@@ -319,16 +319,18 @@ sppc_status sppc_get_layout(sppc_handle h, int64_t* n_slices, int64_t* slice_ptr
                             int64_t* chunk_slice);
 
 /* The nev lowest eigenpairs of a small dense symmetric matrix: the projected
- * eigensolve of the Rayleigh-Ritz step (Alg. 2; Eqs. tilde_H, rrn) on its own
- * (the default path's double-float form).
+ * eigensolve of the Rayleigh-Ritz step (Alg. 2; Eqs. tilde_H, rrn) on its own.
  * S: device, m x m row-major with leading dimension lds (symmetrised as
  * (S + S^T)/2), 1 <= m <= 144; theta: device, nev values ascending; V: device,
  * m x nev row-major with leading dimension ldv >= nev, orthonormal columns.
- * 1 <= nev <= min(16, m).  Householder tridiagonalisation in double-float,
- * Sturm-count brackets, inverse iteration (FP32 steps, then FP64).  Asynchronous
- * on `stream`; SPPC_ERR_ARG on bad sizes.  All buffers are caller-owned. */
+ * 1 <= nev <= min(16, m).  flags: 0 = Householder tridiagonalisation and
+ * back-transformation in double-float (the default path's form), 1 = in FP64
+ * (the native FP64 path's); other bits SPPC_ERR_ARG.  One launch of a cluster
+ * of 8 CTAs; Sturm-count brackets, inverse iteration (FP32 steps, then FP64).
+ * Asynchronous on `stream`; SPPC_ERR_ARG on bad sizes.  All buffers are
+ * caller-owned. */
 sppc_status sppc_small_syev(const double* S, int32_t m, int32_t lds, int32_t nev, double* theta, double* V,
-                            int32_t ldv, void* stream);
+                            int32_t ldv, int32_t flags, void* stream);
 
 /* The block Gram product of block Gram-Schmidt (Eq. blkGS) and of the border of
  * the projected matrix (Eq. proj), as the solve computes it:

@@ -90,7 +90,7 @@ _SIGS = {
     "sppc_destroy": (_I32, [_VP]),
     "sppc_last_error": (ctypes.c_char_p, [_VP]),
     "sppc_kernel_launches": (_I64, []),
-    "sppc_small_syev": (_I32, [_VP, _I32, _I32, _I32, _VP, _VP, _I32, _VP]),
+    "sppc_small_syev": (_I32, [_VP, _I32, _I32, _I32, _VP, _VP, _I32, _I32, _VP]),
     "sppc_block_gram": (_I32, [_VP, _I32, _VP, _I64, _I32, _VP, _VP]),
     "sppc_block_update": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP, _I64, _I32, _VP]),
     "sppc_set_proposal": (_I32, [_VP, _VP, _VP, _VP]),
@@ -278,16 +278,17 @@ def sppc_kernel_launches() -> int:
     return int(_lib.sppc_kernel_launches())
 
 
-def sppc_small_syev(S, nev: int, stream=None):
+def sppc_small_syev(S, nev: int, f64: bool = False, stream=None):
     """nev lowest eigenpairs of the symmetric m x m torch CUDA float64 tensor S
-    (m <= 144, nev <= 16); returns (theta, V) as CUDA tensors (V: m x nev)."""
+    (m <= 144, nev <= 16); returns (theta, V) as CUDA tensors (V: m x nev).
+    f64: Householder steps in FP64 instead of double-float."""
     import torch
     S = S.contiguous()
     m = int(S.shape[0])
     theta = torch.empty(nev, dtype=torch.float64, device=S.device)
     V = torch.empty(m, nev, dtype=torch.float64, device=S.device)
     _check(None, _lib.sppc_small_syev(S.data_ptr(), m, m, int(nev), theta.data_ptr(), V.data_ptr(), int(nev),
-                                      _stream(stream)))
+                                      1 if f64 else 0, _stream(stream)))
     return theta, V
 
 

@@ -1848,10 +1848,13 @@ const char* sppc_last_error(sppc_handle h) { return h ? h->err.c_str() : g_creat
 int64_t sppc_kernel_launches(void) { return (int64_t)launch_count(); }
 
 sppc_status sppc_small_syev(const double* S, int32_t m, int32_t lds, int32_t nev, double* theta, double* V,
-                            int32_t ldv, void* stream) {
-  if (!S || !theta || !V || m < 1 || m > 144 || nev < 1 || nev > 16 || nev > m || lds < m || ldv < nev)
-    return fail(nullptr, SPPC_ERR_ARG, "sppc_small_syev: bad arguments (1 <= m <= 144, 1 <= nev <= min(16, m))");
-  const cudaError_t e = syev_lowest(S, lds, m, nev, theta, V, ldv, false, static_cast<cudaStream_t>(stream));
+                            int32_t ldv, int32_t flags, void* stream) {
+  if (!S || !theta || !V || m < 1 || m > 144 || nev < 1 || nev > 16 || nev > m || lds < m || ldv < nev ||
+      (flags & ~1))
+    return fail(nullptr, SPPC_ERR_ARG,
+                "sppc_small_syev: bad arguments (1 <= m <= 144, 1 <= nev <= min(16, m), flags 0 or 1)");
+  const cudaError_t e =
+      syev_lowest(S, lds, m, nev, theta, V, ldv, (flags & 1) != 0, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail(nullptr, SPPC_ERR_CUDA, "sppc_small_syev: %s", cudaGetErrorString(e));
   return SPPC_OK;
 }

@@ -120,21 +120,59 @@ __device__ void multisect(const T* d, const T* e2, int m, int w, T pivmin, T rel
   hi_io = static_cast<double>(hi);
 }
 
-// Narrow [lo, hi] for index w by 4-section in FP64: three Sturm counts per round
-// (lanes 0-2 of the warp; FP64 throughput, not latency, is the scarce resource).
+// Eigenvalues of the symmetric tridiagonal T (diagonal d, squared
+// off-diagonal e2) below x: the sign changes along the leading principal
+// minors p_0 = 1, p_1, ..., p_m of T - x I (Sturm sequence property), from
+// p_{i+1} = (d_i - x) p_i - e2_{i-1} p_{i-1}: three FP64 operations a step and
+// no division (on this GPU every FP64 instruction is expensive, so the
+// division of the ratio form dominates it).  Rounding perturbs d_i - x and
+// e2_i by a few ulps, as in the ratio form.  A minor that is exactly zero is
+// replaced by a tiny one of the sign opposite to its predecessor's (a
+// perturbation of d_i far below its rounding); the pair is rescaled by a power
+// of two (exact) when the larger magnitude leaves [2^-256, 2^256].  Signs,
+// zeros and exponents are read from the high words with integer operations.
+__device__ int sturm_count_minors(const double* d, const double* e2, int m, double x) {
+  double pm = 1.0, p = __dsub_rn(d[0], x);
+  int hm = __double2hiint(pm), cnt = 0;
+#pragma unroll 2
+  for (int i = 0;; ++i) {
+    const double dn = i + 1 < m ? d[i + 1] : 0.0, en = i + 1 < m ? e2[i] : 0.0;
+    int hi = __double2hiint(p);
+    if (((hi & 0x7FFFFFFF) | __double2loint(p)) == 0) {
+      p = __dmul_rn(pm, -0x1p-300);
+      hi = __double2hiint(p);
+    }
+    cnt += ((hi ^ hm) < 0) ? 1 : 0;
+    if (i + 1 >= m) break;
+    const int ep = (hi >> 20) & 0x7FF, em = (hm >> 20) & 0x7FF, mx = ep > em ? ep : em;
+    if (mx > 1023 + 256 || mx < 1023 - 256) {
+      const double sc = __hiloint2double((2046 - mx) << 20, 0);
+      p = __dmul_rn(p, sc);
+      pm = __dmul_rn(pm, sc);
+    }
+    const double pn = __fma_rn(__dsub_rn(dn, x), p, -__dmul_rn(en, pm));
+    pm = p;
+    p = pn;
+    hm = __double2hiint(pm);
+  }
+  return cnt;
+}
+
+// Narrow [lo, hi] for index w by 33-section in FP64: 32 Sturm counts per round
+// (one per lane, at the same cost as one), every lane takes the same decision.
 // Stops when hi - lo <= rel * max(|lo|,|hi|) + abs_tol.
-__device__ void quadsect64(const double* d, const double* e2, int m, int w, double pivmin, double rel,
-                           double abs_tol, int max_rounds, double& lo_io, double& hi_io) {
+__device__ void multisect64(const double* d, const double* e2, int m, int w, double rel, double abs_tol,
+                            int max_rounds, double& lo_io, double& hi_io) {
   const int lane = threadIdx.x & 31;
   double lo = lo_io, hi = hi_io;
   for (int it = 0; it < max_rounds; ++it) {
     if (hi - lo <= rel * fmax(fabs(lo), fabs(hi)) + abs_tol) break;
-    const double h = hi - lo;
-    const int c = (lane < 3) ? sturm_count<double>(d, e2, m, lo + h * 0.25 * (double)(lane + 1), pivmin) : m + 1;
-    const unsigned ball = __ballot_sync(0xffffffffu, c > w) & 0x7u;
-    const int f = ball ? __ffs(ball) - 1 : 3;  // first quarter point above index w
-    const double nlo = (f > 0) ? lo + h * 0.25 * (double)f : lo;
-    const double nhi = (f < 3) ? lo + h * 0.25 * (double)(f + 1) : hi;
+    const double h = (hi - lo) * (1.0 / 33.0);
+    const int c = sturm_count_minors(d, e2, m, lo + h * static_cast<double>(lane + 1));
+    const unsigned ball = __ballot_sync(0xffffffffu, c > w);
+    const int f = ball ? __ffs(ball) - 1 : 32;  // first section point above index w
+    const double nlo = f > 0 ? lo + h * static_cast<double>(f) : lo;
+    const double nhi = f < 32 ? lo + h * static_cast<double>(f + 1) : hi;
     lo = nlo;
     hi = nhi;
   }
@@ -181,11 +219,46 @@ __device__ float2 block_sum(float2 v, float2* red) {
   return r;
 }
 
-// Solve (T - sigma I) y = y in place for the tridiagonal (d, e), FP64, with
-// partial pivoting; returns false on an exactly zero pivot set to eps.
+// On this GPU an FP64 division or square root costs about ten times a
+// dependent FP64 multiply-add, so the serial chains below take 1/x and
+// 1/sqrt(x) from the hardware approximations (about 2^-22 relative) and two
+// Newton steps, each of which squares the relative error: r <- r + r (1 - x r)
+// and y <- y + y (1 - x y^2) / 2.  Within a few ulps, not correctly rounded;
+// for finite x of normal magnitude (x > 0 for the square root).
+__device__ __forceinline__ bool mid_range64(double x) {  // exponent away from both ends
+  const int ex = (__double2hiint(x) >> 20) & 0x7FF;
+  return ex > 64 && ex < 2046 - 64;
+}
+__device__ __forceinline__ double recip64(double x) {
+  if (!mid_range64(x)) return 1.0 / x;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = __fma_rn(-x, r, 1.0);
+  r = __fma_rn(r, e, r);
+  e = __fma_rn(-x, r, 1.0);
+  return __fma_rn(r, e, r);
+}
+__device__ __forceinline__ double rsqrt64(double x) {
+  if (!mid_range64(x)) return 1.0 / sqrt(x);
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+#pragma unroll
+  for (int s = 0; s < 2; ++s) y = __fma_rn(__dmul_rn(0.5, y), __fma_rn(-x, __dmul_rn(y, y), 1.0), y);
+  return y;
+}
+__device__ __forceinline__ float recip_of(float x) { return 1.f / x; }
+__device__ __forceinline__ double recip_of(double x) { return recip64(x); }
+
+// Solve (T - sigma I) y = y in place for the tridiagonal (d, e), with partial
+// pivoting; an exactly zero pivot is set to eps_piv.  One reciprocal per row
+// (of the pivot), used by the elimination and kept (rdu) for the
+// back-substitution.
 template <typename T>
-__device__ void tri_shift_solve(const T* d, const T* e, int m, T sigma, T eps_piv, T* y, T* du, T* u1, T* u2, T* lm,
+__device__ void tri_shift_solve(const T* d, const T* e, int m, T sigma, T eps_piv, T* y, T* rdu, T* u1, T* u2, T* lm,
                                 unsigned char* piv) {
+  const T reps = recip_of(eps_piv);
+  // 1 / the back-substitution's divisor: the pivot, or +-eps_piv below that
+  auto rback = [&](T pv, T r) { return fabs(pv) < eps_piv ? (pv < T(0) ? -reps : reps) : r; };
   T a0 = d[0] - sigma, b0 = (m > 1) ? e[0] : T(0);
   for (int i = 0; i + 1 < m; ++i) {
     const T c = e[i];
@@ -193,26 +266,31 @@ __device__ void tri_shift_solve(const T* d, const T* e, int m, T sigma, T eps_pi
     const T b1 = (i + 2 < m) ? e[i + 1] : T(0);
     if (fabs(c) > fabs(a0)) {
       piv[i] = 1;
-      du[i] = c;
+      const T r = recip_of(c);
+      rdu[i] = rback(c, r);
       u1[i] = a1;
       u2[i] = b1;
-      const T l = a0 / c;
+      const T l = a0 * r;
       lm[i] = l;
       a0 = b0 - l * a1;
       b0 = -l * b1;
     } else {
       piv[i] = 0;
       if (a0 == T(0)) a0 = eps_piv;
-      du[i] = a0;
+      const T r = recip_of(a0);
+      rdu[i] = rback(a0, r);
       u1[i] = b0;
       u2[i] = T(0);
-      const T l = c / a0;
+      const T l = c * r;
       lm[i] = l;
       a0 = a1 - l * b0;
       b0 = b1;
     }
   }
-  du[m - 1] = (a0 == T(0)) ? eps_piv : a0;
+  {
+    const T pv = (a0 == T(0)) ? eps_piv : a0;
+    rdu[m - 1] = rback(pv, recip_of(pv));
+  }
   for (int i = 0; i + 1 < m; ++i) {
     if (piv[i]) {
       const T tmp = y[i];
@@ -226,9 +304,7 @@ __device__ void tri_shift_solve(const T* d, const T* e, int m, T sigma, T eps_pi
     T sv = y[i];
     if (i + 1 < m) sv -= u1[i] * y[i + 1];
     if (i + 2 < m) sv -= u2[i] * y[i + 2];
-    T di = du[i];
-    if (fabs(di) < eps_piv) di = (di < 0 ? -eps_piv : eps_piv);
-    y[i] = sv / di;
+    y[i] = sv * rdu[i];
   }
 }
 
@@ -245,153 +321,295 @@ __device__ T rayleigh_tri(const T* d, const T* e, int m, const T* y) {
   return num / den;
 }
 
+// ---- the projected eigensolve on a cluster of kSyC CTAs (one per SM)
+//
+// The FP64 pipe of this GPU issues one warp instruction in tens of cycles, so a
+// single SM spends most of an m = 128 eigensolve in the O(m^3) Householder
+// steps.  Here they run over a thread-block cluster: CTA r holds rows r, r + C,
+// r + 2C, ... of the matrix, each step's reflector and matrix-vector products
+// travel through distributed shared memory, two cluster barriers a step.
+constexpr int kSyC = 8;
+constexpr int kSyThreads = 512;
+constexpr int kSyWarps = kSyThreads / 32;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the shared::cluster address of `p` (in this CTA's shared memory) in CTA `rank`
+__device__ __forceinline__ uint32_t at_rank(const void* p, unsigned rank) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
+// Shared-memory layout of one CTA (byte offsets), the same in every CTA.
+struct SyevLayout {
+  int al, vb, pb, wb, kb, red, tau, refl, yd, d, e, e2, y, lo, hi, ev, d32, e232, crowd, total;
+  __host__ __device__ explicit SyevLayout(int m) {
+    const int rows = (m + kSyC - 1) / kSyC;
+    int o = 0;
+    auto take = [&](int bytes) {
+      const int at = o;
+      o += (bytes + 15) & ~15;
+      return at;
+    };
+    al = take(8 * rows * m);           // this CTA's rows
+    vb = take(8 * 2 * kMaxM);          // the step's reflector, two buffers
+    pb = take(8 * kMaxM);              // p = tau A v, all trailing rows
+    wb = take(8 * kMaxM);              // w = p - K v
+    kb = take(8 * kSyC);               // the CTAs' parts of p . v
+    red = take(8 * 40);
+    tau = take(8 * kMaxM);
+    refl = take(8 * (m * (m - 1) / 2 + 1));  // reflector j: m - 1 - j slots
+    yd = take(8 * kMaxNev * m);
+    d = take(8 * m);
+    e = take(8 * m);
+    e2 = take(8 * m);
+    y = take(8 * kMaxNev * m);
+    lo = take(8 * kMaxNev);
+    hi = take(8 * kMaxNev);
+    ev = take(8 * kMaxNev);
+    d32 = take(4 * m);
+    e232 = take(4 * m);
+    crowd = take(4 * kMaxNev);
+    total = o;
+  }
+};
+
+__host__ __device__ inline int refl_off(int j, int m) { return j * (m - 1) - j * (j - 1) / 2; }
+
 // Symmetric eigensolve of the projected matrix, nev lowest pairs.
 //  1. Householder tridiagonalisation (Golub and Van Loan, Alg. 8.3.1) in the
-//     slot format (double-float, or FP64 for the native FP64 path), matrix in
-//     shared memory with leading dimension m+1.
+//     slot format (double-float, or FP64 for the native FP64 path), distributed
+//     over the cluster by rows; every CTA then gathers all reflectors.
 //  2. Eigenvalue brackets by Sturm-count multisection in FP32 to ~1e-5; indices
-//     whose brackets crowd a neighbour are narrowed further in FP64.
+//     whose brackets crowd a neighbour are narrowed further in FP64
+//     (division-free counts, 33-section).
 //  3. Eigenvectors of the tridiagonal matrix by inverse iteration, one thread
-//     per vector: three FP32 steps, then FP64 steps (the FP64 pipe is ~1/64 of
-//     FP32 here, so FP64 is kept to the last steps).  Isolated eigenvalues: FP32
+//     per vector: three FP32 steps, then FP64 steps.  Isolated eigenvalues: FP32
 //     Rayleigh-quotient shifts, one FP64 step at the FP64 Rayleigh quotient.
 //     Crowded groups: shifts at the bracket midpoints (FP64 brackets ~1e-13
-//     wide), two FP64 steps, then modified Gram-Schmidt in the group.  The
-//     eigenvalue is the final Rayleigh quotient.
-//  4. Back-transformation through the stored reflectors in the slot format.
+//     wide), two FP64 steps, then modified Gram-Schmidt over the crowded
+//     vectors.  The eigenvalue is the final Rayleigh quotient.  Every CTA that
+//     owns a wanted vector computes all of them (lanes of one warp: the same
+//     time as one).
+//  4. Back-transformation through the reflectors in the slot format: CTA r
+//     takes the vectors c = r (mod C), a warp each.
 template <bool F64>
-__global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ S, int lds, int m, int nev,
-                                                     double* __restrict__ theta, double* __restrict__ V, int ldv) {
+__global__ void __cluster_dims__(kSyC, 1, 1) __launch_bounds__(kSyThreads, 1)
+    k_syev_lowest(const double* __restrict__ S, int lds, int m, int nev, double* __restrict__ theta,
+                  double* __restrict__ V, int ldv) {
   using AR = Ar<F64>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int ld = m + 1;
-  float2* A = reinterpret_cast<float2*>(smraw);  // m x ld, reflectors below the diagonal
-  float2* vec = A + m * ld;                        // m
-  float2* pw = vec + m;                            // m
-  float2* tau = pw + m;                            // m
-  float2* red = tau + m;                           // 33
-  float2* Yd = red + 40;                           // nev x m (double-float eigenvectors)
-  double* d = reinterpret_cast<double*>(Yd + kMaxNev * m);  // m
-  double* e = d + m;                                         // m
-  double* e2 = e + m;                                        // m
-  double* Y = e2 + m;                                        // nev x m (FP64 eigenvectors of T)
-  double* lo = Y + kMaxNev * m;                              // nev
-  double* hi = lo + kMaxNev;                                 // nev
-  double* ev = hi + kMaxNev;                                 // nev
-  float* d32 = reinterpret_cast<float*>(ev + kMaxNev);       // m
-  float* e232 = d32 + m;                                     // m
-  int* crowd = reinterpret_cast<int*>(e232 + m);             // nev
-  const int t = threadIdx.x, nt = blockDim.x;
-  const int lane = t & 31, warp = t >> 5, nwarp = nt >> 5;
-  for (int x = t; x < m * m; x += nt) {
-    const int i = x / m, j = x % m;
-    A[i * ld + j] = AR::from_d(0.5 * (S[i * lds + j] + S[j * lds + i]));
+  const SyevLayout L(m);
+  float2* Al = reinterpret_cast<float2*>(smraw + L.al);
+  float2* vb = reinterpret_cast<float2*>(smraw + L.vb);
+  float2* pb = reinterpret_cast<float2*>(smraw + L.pb);
+  float2* wb = reinterpret_cast<float2*>(smraw + L.wb);
+  float2* kb = reinterpret_cast<float2*>(smraw + L.kb);
+  float2* red = reinterpret_cast<float2*>(smraw + L.red);
+  float2* tau = reinterpret_cast<float2*>(smraw + L.tau);
+  float2* refl = reinterpret_cast<float2*>(smraw + L.refl);
+  float2* Yd = reinterpret_cast<float2*>(smraw + L.yd);
+  double* d = reinterpret_cast<double*>(smraw + L.d);
+  double* e = reinterpret_cast<double*>(smraw + L.e);
+  double* e2 = reinterpret_cast<double*>(smraw + L.e2);
+  double* Y = reinterpret_cast<double*>(smraw + L.y);
+  double* lo = reinterpret_cast<double*>(smraw + L.lo);
+  double* hi = reinterpret_cast<double*>(smraw + L.hi);
+  double* ev = reinterpret_cast<double*>(smraw + L.ev);
+  float* d32 = reinterpret_cast<float*>(smraw + L.d32);
+  float* e232 = reinterpret_cast<float*>(smraw + L.e232);
+  int* crowd = reinterpret_cast<int*>(smraw + L.crowd);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int rank = static_cast<int>(cluster_rank());
+  const int nloc = rank < m ? (m - rank + kSyC - 1) / kSyC : 0;  // rows rank + C li, li < nloc
+  for (int x = t; x < nloc * m; x += kSyThreads) {
+    const int li = x / m, l = x % m, i = rank + kSyC * li;
+    Al[x] = AR::from_d(0.5 * (S[static_cast<int64_t>(i) * lds + l] + S[static_cast<int64_t>(l) * lds + i]));
   }
   __syncthreads();
-  // ---- 1. Householder tridiagonalisation (slot format)
+  // ---- 1. Householder tridiagonalisation over the cluster
   for (int j = 0; j + 2 < m; ++j) {
     const int len = m - j - 1;
-    typename AR::Acc sa;
-    AR::zero(sa);
-    for (int i = t; i < len; i += nt) {
-      const float2 xv = A[(j + 1 + i) * ld + j];
-      AR::mac(sa, xv, xv);
-    }
-    const float2 s2 = block_sum<F64>(AR::get(sa), red);
-    if (t == 0) {
-      const float2 x0 = A[(j + 1) * ld + j];
-      const float2 nrm = slot_sqrt<F64>(s2);
-      if (AR::lead(nrm) == 0.0) {
-        tau[j] = make_float2(0.f, 0.f);
-        e[j] = 0.0;
-        red[34] = make_float2(0.f, 0.f);
-      } else {
-        const float2 alpha = (AR::lead(x0) >= 0.0) ? AR::neg(nrm) : nrm;
-        const float2 v0 = AR::sub(x0, alpha);
-        const float2 vtv = AR::add(AR::sub(s2, AR::mul(x0, x0)), AR::mul(v0, v0));
-        tau[j] = AR::div(AR::from_d(2.0), vtv);
-        e[j] = AR::to_d(alpha);
-        red[34] = v0;
+    float2* vcur = vb + (j & 1) * kMaxM;
+    if (rank == j % kSyC) {
+      // the reflector from row j (= column j below the diagonal); it stays in
+      // row j, columns j + 1 .., for the back-transformation
+      float2* row = Al + (j / kSyC) * m;
+      if (warp == 0) {
+        typename AR::Acc sa;
+        AR::zero(sa);
+        for (int l = lane; l < len; l += 32) AR::mac(sa, row[j + 1 + l], row[j + 1 + l]);
+        const float2 s2 = warp_sum<F64>(AR::get(sa));
+        if (lane == 0) {
+          const float2 x0 = row[j + 1];
+          float2 tj = make_float2(0.f, 0.f), v0 = x0;
+          double ej = 0.0;
+          if constexpr (F64) {
+            // |v|^2 = 2 (s2 + |x0| ||x||), so tau = 2 / |v|^2 = 1 / (s2 + |x0| ||x||)
+            const double s2d = slot_d(s2), x0d = slot_d(x0);
+            if (s2d > 0.0) {
+              const double nr = s2d * rsqrt64(s2d);
+              const double al = x0d >= 0.0 ? -nr : nr;
+              v0 = d_slot(x0d - al);
+              tj = d_slot(recip64(__fma_rn(fabs(x0d), nr, s2d)));
+              ej = al;
+            }
+          } else {
+            const float2 nrm = slot_sqrt<F64>(s2);
+            if (AR::lead(nrm) != 0.0) {
+              const float2 alpha = (AR::lead(x0) >= 0.0) ? AR::neg(nrm) : nrm;
+              v0 = AR::sub(x0, alpha);
+              const float2 vtv = AR::add(AR::sub(s2, AR::mul(x0, x0)), AR::mul(v0, v0));
+              tj = AR::div(AR::from_d(2.0), vtv);
+              ej = AR::to_d(alpha);
+            }
+          }
+          row[j + 1] = v0;
+          red[34] = tj;
+          red[35] = d_slot(ej);
+          red[36] = d_slot(AR::to_d(row[j]));
+        }
+      }
+      __syncthreads();
+      for (int x = t; x < kSyC * len; x += kSyThreads) {
+        const int q = x / len, l = x % len;
+        st_cluster(at_rank(vcur + l, q), row[j + 1 + l]);
+      }
+      if (t < kSyC) {
+        st_cluster(at_rank(tau + j, t), red[34]);
+        st_cluster(at_rank(e + j, t), slot_d(red[35]));
+        st_cluster(at_rank(d + j, t), slot_d(red[36]));
       }
     }
-    __syncthreads();
+    cluster_sync();  // the reflector, tau_j, d_j, e_j everywhere
     const float2 tj = tau[j];
-    for (int i = t; i < len; i += nt) vec[i] = (i == 0) ? red[34] : A[(j + 1 + i) * ld + j];
-    __syncthreads();
-    if (AR::lead(tj) != 0.0) {
-      // p = tau A v: four threads per row (entries sub, sub+4, ...), combined by shuffles
-      for (int i0 = 0; i0 < len; i0 += nt / 4) {
-        const int i = i0 + (t >> 2), sub = t & 3;
+    const bool active = AR::lead(tj) != 0.0;
+    const int li0 = j + 1 <= rank ? 0 : (j + 1 - rank + kSyC - 1) / kSyC;  // this CTA's trailing rows
+    if (active) {
+      // p_i = tau_j (A v)_i, a warp per row, sent to every CTA; this CTA's part of p . v
+      typename AR::Acc kd;
+      AR::zero(kd);
+      for (int li = li0 + warp; li < nloc; li += kSyWarps) {
+        const int ii = rank + kSyC * li - j - 1;
+        const float2* row = Al + li * m + (j + 1);
         typename AR::Acc pa;
         AR::zero(pa);
-        if (i < len) {
-          const float2* row = A + (j + 1 + i) * ld + (j + 1);
-          int c = 0;
-          for (int l = sub; l < len; l += 4) {
-            AR::mac(pa, row[l], vec[l]);
-            if (((++c) & 15) == 0) AR::norm(pa);
-          }
+        for (int l = lane; l < len; l += 32) AR::mac(pa, row[l], vcur[l]);
+        const float2 pr = AR::mul(tj, warp_sum<F64>(AR::get(pa)));
+        if (lane < kSyC) st_cluster(at_rank(pb + ii, lane), pr);
+        AR::mac(kd, pr, vcur[ii]);
+      }
+      if (lane == 0) red[warp] = AR::get(kd);
+      __syncthreads();
+      if (warp == 0) {  // the warps' parts summed by a butterfly over lanes 0-15
+        float2 k = lane < kSyWarps ? red[lane] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int o = kSyWarps / 2; o > 0; o >>= 1) k = AR::add(k, shfl_xor_df(k, o));
+        if (lane < kSyC) st_cluster(at_rank(kb + rank, lane), k);
+      }
+    }
+    cluster_sync();  // p and the parts of p . v everywhere
+    if (active) {
+      if (warp == 0) {
+        float2 k = lane < kSyC ? kb[lane] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int o = kSyC / 2; o > 0; o >>= 1) k = AR::add(k, shfl_xor_df(k, o));
+        if (lane == 0) red[37] = AR::mul(AR::mul(AR::from_d(0.5), tj), k);
+      }
+      __syncthreads();
+      const float2 K = red[37];
+      for (int l = t; l < len; l += kSyThreads) wb[l] = AR::sub(pb[l], AR::mul(K, vcur[l]));  // w
+      __syncthreads();
+      // A -= v w^T + w v^T on this CTA's trailing rows
+      for (int li = li0 + warp; li < nloc; li += kSyWarps) {
+        const int ii = rank + kSyC * li - j - 1;
+        const float2 vi = vcur[ii], wi = wb[ii];
+        float2* row = Al + li * m + (j + 1);
+        for (int l = lane; l < len; l += 32) {
+          if constexpr (F64)
+            row[l] = d_slot(__fma_rn(-slot_d(wi), slot_d(vcur[l]), __fma_rn(-slot_d(vi), slot_d(wb[l]), slot_d(row[l]))));
+          else
+            row[l] = AR::sub(row[l], AR::add(AR::mul(vi, wb[l]), AR::mul(wi, vcur[l])));
         }
-        float2 pr = AR::get(pa);
-        pr = AR::add(pr, shfl_xor_df(pr, 1));
-        pr = AR::add(pr, shfl_xor_df(pr, 2));
-        if (i < len && sub == 0) pw[i] = AR::mul(tj, pr);
-      }
-      __syncthreads();
-      typename AR::Acc ka;
-      AR::zero(ka);
-      for (int i = t; i < len; i += nt) AR::mac(ka, pw[i], vec[i]);
-      const float2 pv = block_sum<F64>(AR::get(ka), red);
-      const float2 K = AR::mul(AR::mul(AR::from_d(0.5), tj), pv);
-      for (int i = t; i < len; i += nt) pw[i] = AR::sub(pw[i], AR::mul(K, vec[i]));  // w
-      __syncthreads();
-      // A -= v w^T + w v^T: a warp per row, lanes along the row
-      for (int i = warp; i < len; i += nwarp) {
-        const float2 vi = vec[i], wi = pw[i];
-        float2* arow = A + (j + 1 + i) * ld + (j + 1);
-        for (int l = lane; l < len; l += 32)
-          arow[l] = AR::sub(arow[l], AR::add(AR::mul(vi, pw[l]), AR::mul(wi, vec[l])));
       }
     }
     __syncthreads();
-    for (int i = t; i < len; i += nt) A[(j + 1 + i) * ld + j] = vec[i];
-    if (t == 0) d[j] = AR::to_d(A[j * ld + j]);
-    __syncthreads();
   }
-  if (t == 0) {
-    if (m >= 2) {
-      d[m - 2] = AR::to_d(A[(m - 2) * ld + (m - 2)]);
-      d[m - 1] = AR::to_d(A[(m - 1) * ld + (m - 1)]);
-      e[m - 2] = AR::to_d(A[(m - 1) * ld + (m - 2)]);
-      tau[m - 2] = make_float2(0.f, 0.f);
-    } else {
-      d[0] = AR::to_d(A[0]);
+  // the last diagonal entries and off-diagonal from their rows' owners
+  if (m >= 2) {
+    if (rank == (m - 2) % kSyC && t < kSyC) {
+      const float2* row = Al + ((m - 2) / kSyC) * m;
+      st_cluster(at_rank(d + (m - 2), t), AR::to_d(row[m - 2]));
+      st_cluster(at_rank(e + (m - 2), t), AR::to_d(row[m - 1]));
+      st_cluster(at_rank(tau + (m - 2), t), make_float2(0.f, 0.f));
     }
-    if (m >= 1) tau[m - 1] = make_float2(0.f, 0.f);
+    if (rank == (m - 1) % kSyC && t < kSyC) {
+      const float2* row = Al + ((m - 1) / kSyC) * m;
+      st_cluster(at_rank(d + (m - 1), t), AR::to_d(row[m - 1]));
+      st_cluster(at_rank(tau + (m - 1), t), make_float2(0.f, 0.f));
+    }
+  } else if (rank == 0 && t == 0) {
+    d[0] = AR::to_d(Al[0]);
+    tau[0] = make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  for (int i = t; i < m; i += nt) {
+  cluster_sync();
+  // every CTA gathers the reflectors (row j, columns j + 1 .., of CTA j mod C)
+  for (int j = warp; j + 2 < m; j += kSyWarps) {
+    const uint32_t src = at_rank(Al + (j / kSyC) * m + (j + 1), j % kSyC);
+    const int len = m - j - 1, o = refl_off(j, m);
+    for (int l = lane; l < len; l += 32) refl[o + l] = ld_cluster(src + 8u * l);
+  }
+  cluster_sync();  // no CTA leaves while another reads its rows
+  if (rank >= nev) return;  // no vector to back-transform here
+
+  for (int i = t; i < m; i += kSyThreads) {
     e2[i] = (i + 1 < m) ? e[i] * e[i] : 0.0;
     d32[i] = static_cast<float>(d[i]);
     e232[i] = static_cast<float>(e2[i]);
   }
   __shared__ double gl, gu, tnorm;
-  if (t == 0) {
+  if (warp == 0) {  // Gershgorin bounds and ||T||: lanes over rows, then a butterfly
     double l0 = 1e300, h0 = -1e300, mx = 0.0;
-    for (int i = 0; i < m; ++i) {
+    for (int i = lane; i < m; i += 32) {
       const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
       l0 = fmin(l0, d[i] - r);
       h0 = fmax(h0, d[i] + r);
       mx = fmax(mx, fabs(d[i]) + r);
     }
-    tnorm = fmax(mx, 1e-300);
-    const double pad = 1e-6 * tnorm + 1e-300;
-    gl = l0 - pad;
-    gu = h0 + pad;
+    for (int o = 16; o > 0; o >>= 1) {
+      l0 = fmin(l0, __shfl_xor_sync(0xffffffffu, l0, o));
+      h0 = fmax(h0, __shfl_xor_sync(0xffffffffu, h0, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+      tnorm = fmax(mx, 1e-300);
+      const double pad = 1e-6 * tnorm + 1e-300;
+      gl = l0 - pad;
+      gu = h0 + pad;
+    }
   }
   __syncthreads();
   // ---- 2. brackets: FP32 multisection, then FP64 for crowded indices
-  for (int w = warp; w < nev; w += nwarp) {
+  for (int w = warp; w < nev; w += kSyWarps) {
     double l0 = gl, h0 = gu;
     multisect<float>(d32, e232, m, w, 1e-30f, 2e-6f, static_cast<float>(1e-7 * tnorm), 12, l0, h0);
     if (lane == 0) {
@@ -410,20 +628,18 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
     crowd[t] = c;
   }
   __syncthreads();
-  for (int w = warp; w < nev; w += nwarp) {
+  for (int w = warp; w < nev; w += kSyWarps) {
     if (!crowd[w]) continue;
     // start from the FP32 bracket widened well past the FP32 Sturm error
     // (about m * 2^-24 * ||T||); if the FP64 counts disagree, from the whole interval
     double l0 = lo[w] - 4e-5 * tnorm, h0 = hi[w] + 4e-5 * tnorm;
-    int c = 0;
-    if (lane == 0) c = sturm_count<double>(d, e2, m, l0, 1e-280);
-    if (lane == 1) c = sturm_count<double>(d, e2, m, h0, 1e-280);
+    const int c = sturm_count_minors(d, e2, m, lane == 0 ? l0 : h0);
     const int cl = __shfl_sync(0xffffffffu, c, 0), ch = __shfl_sync(0xffffffffu, c, 1);
     if (!(cl <= w && ch > w)) {
       l0 = gl;
       h0 = gu;
     }
-    quadsect64(d, e2, m, w, 1e-280, 1e-13, 1e-15 * tnorm, 80, l0, h0);
+    multisect64(d, e2, m, w, 1e-13, 1e-15 * tnorm, 24, l0, h0);
     if (lane == 0) {
       lo[w] = l0;
       hi[w] = h0;
@@ -439,7 +655,7 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
     // three FP32 steps (isolated: Rayleigh-quotient shifts; crowded: the bracket
     // midpoint), then FP64 steps: one at the FP64 Rayleigh quotient (isolated) or
     // two at the FP64 bracket midpoint, ~1e-13 wide (crowded; orthogonalised in
-    // the group below).  The FP64 pipe is ~1/64 of FP32 here.
+    // the group below).
     float yf[kMaxM], duf[kMaxM], u1f[kMaxM], u2f[kMaxM], lmf[kMaxM], ef[kMaxM];
     for (int i = 0; i < m; ++i) {
       yf[i] = 1.f + 0.1f * (float)((i * 7 + t * 3) % 11);
@@ -474,55 +690,70 @@ __global__ void __launch_bounds__(512) k_syev_lowest(const double* __restrict__ 
     }
   }
   __syncthreads();
-  // crowded groups: modified Gram-Schmidt in index order (thread 0, rare)
-  if (t == 0) {
+  // crowded vectors: modified Gram-Schmidt in index order (warp 0, lanes over rows)
+  if (warp == 0) {
     for (int c = 0; c < nev; ++c) {
+      if (!crowd[c]) continue;
       double* yc = Y + c * m;
-      if (crowd[c]) {
-        for (int b = 0; b < c; ++b) {
-          if (!crowd[b]) continue;
-          const double* yb = Y + b * m;
-          double dot = 0.0, nb = 0.0;
-          for (int i = 0; i < m; ++i) {
-            dot += yb[i] * yc[i];
-            nb += yb[i] * yb[i];
-          }
-          for (int i = 0; i < m; ++i) yc[i] -= (dot / nb) * yb[i];
+      for (int b = 0; b < c; ++b) {
+        if (!crowd[b]) continue;
+        const double* yb = Y + b * m;
+        double dot = 0.0, nb = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          dot = fma(yb[i], yc[i], dot);
+          nb = fma(yb[i], yb[i], nb);
         }
+        for (int o = 16; o > 0; o >>= 1) {
+          dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        }
+        const double f = dot / nb;
+        for (int i = lane; i < m; i += 32) yc[i] -= f * yb[i];
+        __syncwarp();
       }
     }
   }
   __syncthreads();
-  if (t < nev) {
-    double* y = Y + t * m;
-    double nrm = 0.0;
-    for (int i = 0; i < m; ++i) nrm += y[i] * y[i];
-    nrm = 1.0 / sqrt(nrm);
-    for (int i = 0; i < m; ++i) y[i] *= nrm;
-    ev[t] = rayleigh_tri<double>(d, e, m, y);
-    for (int i = 0; i < m; ++i) Yd[t * m + i] = AR::from_d(y[i]);
+  // normalise, Rayleigh quotient on T (the eigenvalue): a warp per vector
+  for (int c = warp; c < nev; c += kSyWarps) {
+    double* y = Y + c * m;
+    double nn = 0.0;
+    for (int i = lane; i < m; i += 32) nn = fma(y[i], y[i], nn);
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    const double inv = 1.0 / sqrt(nn);
+    double num = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      double ty = d[i] * y[i];
+      if (i > 0) ty = fma(e[i - 1], y[i - 1], ty);
+      if (i + 1 < m) ty = fma(e[i], y[i + 1], ty);
+      num = fma(y[i], ty, num);
+    }
+    for (int o = 16; o > 0; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) Yd[c * m + i] = AR::from_d(y[i] * inv);
+    if (lane == 0) ev[c] = num / nn;
   }
   __syncthreads();
-  // ---- 4. back-transform y <- H_0 H_1 ... H_{m-3} y (slot format), warp per vector
-  for (int j = m - 3; j >= 0; --j) {
-    const float2 tj = tau[j];
-    if (AR::lead(tj) == 0.0) continue;
-    const int len = m - j - 1;
-    for (int c = warp; c < nev; c += nwarp) {
+  // ---- 4. back-transform y <- H_0 H_1 ... H_{m-3} y (slot format): vectors
+  // c = rank (mod C), a warp each, no block barrier (the reflectors are read only)
+  const int c = rank + kSyC * warp;
+  if (c < nev) {
+    float2* yv = Yd + c * m;
+    for (int j = m - 3; j >= 0; --j) {
+      const float2 tj = tau[j];
+      if (AR::lead(tj) == 0.0) continue;
+      const int len = m - j - 1;
+      const float2* v = refl + refl_off(j, m);
       typename AR::Acc pa;
       AR::zero(pa);
-      for (int i = lane; i < len; i += 32) AR::mac(pa, A[(j + 1 + i) * ld + j], Yd[c * m + j + 1 + i]);
+      for (int i = lane; i < len; i += 32) AR::mac(pa, v[i], yv[j + 1 + i]);
       const float2 sdot = AR::mul(tj, warp_sum<F64>(AR::get(pa)));
-      for (int i = lane; i < len; i += 32)
-        Yd[c * m + j + 1 + i] = AR::sub(Yd[c * m + j + 1 + i], AR::mul(sdot, A[(j + 1 + i) * ld + j]));
+      for (int i = lane; i < len; i += 32) yv[j + 1 + i] = AR::sub(yv[j + 1 + i], AR::mul(sdot, v[i]));
+      __syncwarp();
     }
-    __syncthreads();
+    for (int i = lane; i < m; i += 32) V[static_cast<int64_t>(i) * ldv + c] = AR::to_d(yv[i]);
+    if (lane == 0) theta[c] = ev[c];
   }
-  for (int x = t; x < m * nev; x += nt) {
-    const int i = x / nev, c = x % nev;
-    V[i * ldv + c] = AR::to_d(Yd[c * m + i]);
-  }
-  if (t < nev) theta[t] = ev[t];
 }
 
 __global__ void k_to_df(const double* __restrict__ x, float2* __restrict__ y, int count, double scale, bool f64) {
@@ -539,30 +770,22 @@ cudaError_t chol_rinv(const double* G, int ldg, int kk, int kp, double shift_rel
   return cudaGetLastError();
 }
 
-static size_t syev_smem(int m) {
-  const size_t f2 = (size_t)m * (m + 1) + 3 * (size_t)m + 40 + (size_t)kMaxNev * m;   // float2 entries
-  const size_t db = 3 * (size_t)m + (size_t)kMaxNev * m + 3 * kMaxNev;               // doubles
-  const size_t fl = 2 * (size_t)m;                                                   // floats
-  return f2 * sizeof(float2) + db * sizeof(double) + fl * sizeof(float) + kMaxNev * sizeof(int) + 256;
-}
-
 cudaError_t syev_lowest(const double* S, int lds, int m, int nev, double* theta, double* V, int ldv, bool f64,
                         cudaStream_t s) {
   if (m < 1 || m > kMaxM || nev < 1 || nev > kMaxNev || nev > m) return cudaErrorInvalidValue;
-  const size_t smem = syev_smem(m);
+  const int smem = SyevLayout(m).total;
   static const cudaError_t attr = [] {
-    cudaError_t e = cudaFuncSetAttribute(k_syev_lowest<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)syev_smem(kMaxM));
+    const int most = SyevLayout(kMaxM).total;
+    cudaError_t e = cudaFuncSetAttribute(k_syev_lowest<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_syev_lowest<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)syev_smem(kMaxM));
+      e = cudaFuncSetAttribute(k_syev_lowest<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     return e;
   }();
   if (attr != cudaSuccess) return attr;
   if (f64)
-    k_syev_lowest<true><<<1, 512, smem, s>>>(S, lds, m, nev, theta, V, ldv);
+    k_syev_lowest<true><<<kSyC, kSyThreads, smem, s>>>(S, lds, m, nev, theta, V, ldv);
   else
-    k_syev_lowest<false><<<1, 512, smem, s>>>(S, lds, m, nev, theta, V, ldv);
+    k_syev_lowest<false><<<kSyC, kSyThreads, smem, s>>>(S, lds, m, nev, theta, V, ldv);
   count_launch();
   return cudaGetLastError();
 }

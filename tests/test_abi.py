@@ -95,8 +95,10 @@ def test_small_syev_rejects_bad_sizes_before_any_device_call():
     lib = ctypes.CDLL(S.LIB)
     lib.sppc_small_syev.restype = ctypes.c_int32
     lib.sppc_small_syev.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_void_p]
     buf = ctypes.c_void_p(1)  # never dereferenced: the size check fails first
-    assert lib.sppc_small_syev(buf, 200, 200, 8, buf, buf, 8, None) == 1
-    assert lib.sppc_small_syev(buf, 10, 10, 0, buf, buf, 8, None) == 1
-    assert lib.sppc_small_syev(None, 10, 10, 4, buf, buf, 4, None) == 1
+    assert lib.sppc_small_syev(buf, 200, 200, 8, buf, buf, 8, 0, None) == 1
+    assert lib.sppc_small_syev(buf, 10, 10, 0, buf, buf, 8, 0, None) == 1
+    assert lib.sppc_small_syev(None, 10, 10, 4, buf, buf, 4, 0, None) == 1
+    assert lib.sppc_small_syev(buf, 10, 10, 4, buf, buf, 4, 2, None) == 1  # unknown flag bit
