@@ -1327,12 +1327,12 @@ sppc_status orth_append(sppc_ctx* h, const float2* src, int p, double* dd, bool 
   }
   float2* q = blk(h->Q, n, kp, p);
   h->qd_valid &= ~(1ull << p);  // block p is rewritten below
-  CK(gram(one(h->T1), h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, h->f64, s));
+  CK(gram_sym(h->T1, kp, 0, n, h->dS, h->partials, h->partial_cap, h->f64, s));
   CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR1, h->dRinv, h->dStatus, h->f64, s));
-  CK(update(h->T2, nullptr, nullptr, one(h->T1), h->dRinv, kp, 0, n, h->f64, s));
-  CK(gram(one(h->T2), h->T2, kp, 0, n, h->dS, h->partials, h->partial_cap, h->f64, s));
+  CK(update_tri(h->T2, h->T1, h->dRinv, kp, 0, n, h->f64, s));
+  CK(gram_sym(h->T2, kp, 0, n, h->dS, h->partials, h->partial_cap, h->f64, s));
   CK(chol_rinv(h->dS, kp, k, kp, 0.0, h->dR2, h->dRinv, h->dStatus + 1, h->f64, s));
-  CK(update(q, nullptr, nullptr, one(h->T2), h->dRinv, kp, 0, n, h->f64, s));
+  CK(update_tri(q, h->T2, h->dRinv, kp, 0, n, h->f64, s));
   k_recycle_coefs<<<1, 256, 0, s>>>(h->dC1, p, kp, h->dR2, h->dR1, h->dRecycle, h->f64); count_launch();
   CK(cudaGetLastError());
   int st[2] = {0, 0}, tmo = 0, tcf = 0;

@@ -135,7 +135,75 @@ __global__ void __launch_bounds__(256) k_gram(BlockList A, const float2* __restr
   }
 }
 
-template <int KP, bool F64>
+// Symmetric Gram A^T A of one n x 8 block (CholeskyQR, Eq. QR): the 36 pairs
+// i <= j instead of all 64 products.  Lane (rho, c) = (lane / 4, lane % 4)
+// takes row rho of the warp's 8 and holds the row rotated by c, b[k] =
+// a[(k + c) mod 8], so that its nine pairs are fixed positions of b: (b[0],
+// b[d]) and (b[4], b[4 + d]) for d = 0 .. 3, i.e. (c, c + d) and (c + 4, c + 4 +
+// d), and (b[0], b[4]) = (c, c + 4); the four classes c cover the 36 pairs once.
+// Lanes of one class are combined by shuffles, the 8 warps in shared memory;
+// the CTA writes all 64 entries (mirrored) as its partial.
+template <bool F64>
+__global__ void __launch_bounds__(256) k_gram_sym8(const float2* __restrict__ A, int64_t r0, int64_t r1,
+                                                   int64_t chunk, float2* __restrict__ partials) {
+  using V = Ar<F64>;
+  __shared__ float2 red[8][4][9];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rho = lane >> 2, c = lane & 3;
+  const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t c1 = min(c0 + chunk, r1);
+  typename V::Acc acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) V::zero(acc[q]);
+  int cnt = 0;
+  for (int64_t r = c0 + warp * 8 + rho; r < c1; r += 64) {
+    float2 b[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b[k] = A[r * 8 + ((k + c) & 7)];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      V::mac(acc[2 * d], b[0], b[d]);
+      V::mac(acc[2 * d + 1], b[4], b[(4 + d) & 7]);
+    }
+    V::mac(acc[8], b[0], b[4]);
+    if (((++cnt) & 7) == 0) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) V::norm(acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    float2 v = V::get(acc[q]);
+#pragma unroll
+    for (int m = 4; m < 32; m <<= 1) v = V::add(v, shfl_xor_df(v, m));
+    if (rho == 0) red[warp][c][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int i = threadIdx.x >> 3, j = threadIdx.x & 7;
+    // the class and slot holding pair (min, max): (cc, cc + dd) with dd = j - i mod 8
+    const int lo = i < j ? i : j, hi = i < j ? j : i, dd = hi - lo;
+    int cc, q;
+    if (dd == 4) {
+      cc = lo;
+      q = 8;
+    } else if (dd < 4) {  // (cc, cc + dd) or (cc + 4, cc + 4 + dd) with cc < 4
+      cc = lo & 3;
+      q = 2 * dd + (lo >= 4 ? 1 : 0);
+    } else {  // hi + (8 - dd) = lo (mod 8): the pair read from hi
+      const int e = 8 - dd;
+      cc = hi & 3;
+      q = 2 * e + (hi >= 4 ? 1 : 0);
+    }
+    float2 t = red[0][cc][q];
+    for (int w = 1; w < 8; ++w) t = V::add(t, red[w][cc][q]);
+    partials[static_cast<int64_t>(blockIdx.x) * 64 + threadIdx.x] = t;
+  }
+}
+
+// TRI: one block and an upper triangular coef (CholeskyQR's R^-1): the products
+// with its zero entries (i > j) are skipped, which leaves every sum unchanged.
+template <int KP, bool F64, bool TRI = false>
 __global__ void __launch_bounds__(256) k_update(float2* Y, const float2* X, const float2* __restrict__ alpha,
                                                 BlockList A, const float2* __restrict__ coef, int64_t r0, int64_t r1) {
   using V = Ar<F64>;
@@ -167,7 +235,8 @@ __global__ void __launch_bounds__(256) k_update(float2* Y, const float2* X, cons
 #pragma unroll
     for (int i = 0; i < KP; ++i) {
 #pragma unroll
-      for (int j = 0; j < KP; ++j) V::mac(acc[j], av[i], ca[i * KP + j]);
+      for (int j = 0; j < KP; ++j)
+        if (!TRI || i <= j) V::mac(acc[j], av[i], ca[i * KP + j]);
     }
 #pragma unroll
     for (int j = 0; j < KP; ++j) V::norm(acc[j]);
@@ -178,7 +247,7 @@ __global__ void __launch_bounds__(256) k_update(float2* Y, const float2* X, cons
 
 // Short blocks: one thread per element (row r, column j) instead of per row,
 // the same sum in the same order as k_update.
-template <int KP, bool F64>
+template <int KP, bool F64, bool TRI = false>
 __global__ void __launch_bounds__(256) k_update_el(float2* Y, const float2* X, const float2* __restrict__ alpha,
                                                    BlockList A, const float2* __restrict__ coef, int64_t r0,
                                                    int64_t r1) {
@@ -198,7 +267,8 @@ __global__ void __launch_bounds__(256) k_update_el(float2* Y, const float2* X, c
     const float2* ar = A.p[a] + r * KP;
     const float2* ca = scoef + a * KP * KP + j;
 #pragma unroll
-    for (int i = 0; i < KP; ++i) V::mac(acc, ar[i], ca[i * KP]);
+    for (int i = 0; i < KP; ++i)
+      if (!TRI || i <= j) V::mac(acc, ar[i], ca[i * KP]);
     V::norm(acc);
   }
   __syncwarp();
@@ -437,6 +507,33 @@ cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_
   return finish(partials, nchunks, nout, out, f64, s);
 }
 
+// A^T A for one n x kp block, the same contract as gram(one block, A); kp = 8
+// takes the symmetric kernel (36 pairs), other kp the general one.
+cudaError_t gram_sym(const float2* A, int kp, int64_t r0, int64_t r1, double* out, float2* partials,
+                     int64_t partial_cap, bool f64, cudaStream_t s) {
+  BlockList L;
+  L.p[0] = A;
+  L.n = 1;
+  if (kp != 8) return gram(L, A, kp, r0, r1, out, partials, partial_cap, f64, s);
+  if (r1 <= r0) return cudaMemsetAsync(out, 0, sizeof(double) * 64, s);
+  int64_t chunk = chunk_rows(r1 - r0);
+  int64_t nchunks = (r1 - r0 + chunk - 1) / chunk;
+  if (nchunks * 64 > partial_cap) {
+    chunk = kChunk;
+    nchunks = (r1 - r0 + chunk - 1) / chunk;
+  }
+  if (nchunks * 64 > partial_cap) return cudaErrorInvalidValue;
+  const unsigned g = static_cast<unsigned>(nchunks);
+  if (f64)
+    k_gram_sym8<true><<<g, 256, 0, s>>>(A, r0, r1, chunk, partials);
+  else
+    k_gram_sym8<false><<<g, 256, 0, s>>>(A, r0, r1, chunk, partials);
+  count_launch();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return finish(partials, nchunks, 64, out, f64, s);
+}
+
 // The finishing sum of gram() for partial results written by another kernel
 // (k_gram_tc.cu): out[o] = sum over c of partials[c * nout + o], fixed order.
 cudaError_t gram_finish(const float2* partials, int64_t nchunks, int nout, double* out, bool f64, cudaStream_t s) {
@@ -485,6 +582,27 @@ cudaError_t update(float2* Y, const float2* X, const float2* alpha, const BlockL
   }
   const unsigned g = nblk(r1 - r0, 256);
   return dispatch(kp, f64, [&]<int KP, bool F>() { k_update<KP, F><<<g, 256, smem, s>>>(Y, X, alpha, A, coef, r0, r1); });
+}
+
+// Y = A coef for one block A and an upper triangular kp x kp coef (CholeskyQR's
+// T R^-1): update() without the products with coef's zero lower entries.
+cudaError_t update_tri(float2* Y, const float2* A, const float2* coef, int kp, int64_t r0, int64_t r1, bool f64,
+                       cudaStream_t s) {
+  if (r1 <= r0) return cudaSuccess;
+  BlockList L;
+  L.p[0] = A;
+  L.n = 1;
+  const size_t smem = sizeof(float2) * kp * kp;
+  if (r1 - r0 < static_cast<int64_t>(kChunk) * 64) {
+    const unsigned ge = nblk((r1 - r0) * kp, 256);
+    return dispatch(kp, f64, [&]<int KP, bool F>() {
+      k_update_el<KP, F, true><<<ge, 256, smem, s>>>(Y, nullptr, nullptr, L, coef, r0, r1);
+    });
+  }
+  const unsigned g = nblk(r1 - r0, 256);
+  return dispatch(kp, f64, [&]<int KP, bool F>() {
+    k_update<KP, F, true><<<g, 256, smem, s>>>(Y, nullptr, nullptr, L, coef, r0, r1);
+  });
 }
 
 cudaError_t combine_diag(float2* Y, const float2* X, const float2* alpha, const BlockList& A, const float2* coef,

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "sppc_internal.h"
+#include "fp64_fast.cuh"
 #include "val.cuh"
 
 namespace sppc {
@@ -219,33 +220,6 @@ __device__ float2 block_sum(float2 v, float2* red) {
   return r;
 }
 
-// On this GPU an FP64 division or square root costs about ten times a
-// dependent FP64 multiply-add, so the serial chains below take 1/x and
-// 1/sqrt(x) from the hardware approximations (about 2^-22 relative) and two
-// Newton steps, each of which squares the relative error: r <- r + r (1 - x r)
-// and y <- y + y (1 - x y^2) / 2.  Within a few ulps, not correctly rounded;
-// for finite x of normal magnitude (x > 0 for the square root).
-__device__ __forceinline__ bool mid_range64(double x) {  // exponent away from both ends
-  const int ex = (__double2hiint(x) >> 20) & 0x7FF;
-  return ex > 64 && ex < 2046 - 64;
-}
-__device__ __forceinline__ double recip64(double x) {
-  if (!mid_range64(x)) return 1.0 / x;
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = __fma_rn(-x, r, 1.0);
-  r = __fma_rn(r, e, r);
-  e = __fma_rn(-x, r, 1.0);
-  return __fma_rn(r, e, r);
-}
-__device__ __forceinline__ double rsqrt64(double x) {
-  if (!mid_range64(x)) return 1.0 / sqrt(x);
-  double y;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-#pragma unroll
-  for (int s = 0; s < 2; ++s) y = __fma_rn(__dmul_rn(0.5, y), __fma_rn(-x, __dmul_rn(y, y), 1.0), y);
-  return y;
-}
 __device__ __forceinline__ float recip_of(float x) { return 1.f / x; }
 __device__ __forceinline__ double recip_of(double x) { return recip64(x); }
 

@@ -183,6 +183,13 @@ cudaError_t spmm_tma_read_timeout(const SellDev& A, int* flag, cudaStream_t s);
 cudaError_t gram(const BlockList& A, const float2* B, int kp, int64_t r0, int64_t r1, double* out,
                  float2* partials, int64_t partial_cap, bool f64, cudaStream_t s);
 // Fixed-order sum of per-CTA partial results (nchunks x nout slots) into FP64 out.
+// A^T A for one block (symmetric: 36 of the 64 products when kp = 8); out: kp x kp.
+cudaError_t gram_sym(const float2* A, int kp, int64_t r0, int64_t r1, double* out, float2* partials,
+                     int64_t partial_cap, bool f64, cudaStream_t s);
+// Y = A coef for one block and an upper triangular coef (zero entries below the
+// diagonal are skipped).
+cudaError_t update_tri(float2* Y, const float2* A, const float2* coef, int kp, int64_t r0, int64_t r1, bool f64,
+                       cudaStream_t s);
 cudaError_t gram_finish(const float2* partials, int64_t nchunks, int nout, double* out, bool f64, cudaStream_t s);
 
 // ---- k_gram_tc.cu: gram() for kp = 8 on the tensor cores against basis blocks
