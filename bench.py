@@ -672,15 +672,24 @@ def run_ours(args):
             "graph_algorithmic_GBps": (nnz_all * 12 + sum(wb.n * 4 * 8 * 2 for wb in ws)) / t_graph / 1e9}
         del mats
     if rank == 0 and world == 1 and not args.no_comparator:
-        # the SpMM column tile chosen by the library's autotuner (spmm_chunk_cols = -2)
-        ht = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k, S.sppc_default_opts(p_max=1, spmm_chunk_cols=-2),
-                           stream=stream)
-        tc, tms = S.sppc_spmm_tiling(ht)
-        S.sppc_destroy(ht)
-        line["spmm_tile_autotune"] = {
-            "chosen_columns_per_tile": tc,
-            "ms_per_product": {name: float(x) for name, x in zip(("untiled", "2621440", "1310720", "655360",
-                                                                  "327680"), tms) if x > 0}}
+        # the SpMM layout chosen by the library's autotuners: the column tile
+        # (spmm_chunk_cols = -2), then the SELL sort window at that tile
+        # (sell_sigma = -2), in both value formats
+        tune = {}
+        for prec, key in ((0, "double_float"), (-1, "f64")):
+            ht = S.sppc_create(rp, c, v, w.level_offsets, w.small_dim, k,
+                               S.sppc_default_opts(p_max=1, spmm_chunk_cols=-2, sell_sigma=-2, precision=prec),
+                               stream=stream)
+            tc, tms = S.sppc_spmm_tiling(ht)
+            sg, sms = S.sppc_sell_sigma(ht)
+            S.sppc_destroy(ht)
+            tune[key] = {
+                "chosen_columns_per_tile": tc,
+                "ms_per_product": {name: float(x) for name, x in zip(("untiled", "2621440", "1310720", "655360",
+                                                                      "327680"), tms) if x > 0},
+                "chosen_sigma": sg,
+                "ms_per_product_by_sigma": {str(s_): float(x) for s_, x in zip((64, 256, 1024), sms)}}
+        line["spmm_tile_autotune"] = tune
     if rank == 0 and world == 1 and not args.no_comparator:
         # the paper's own hybrid: SPPC for 15 orders, then per-pair RMM-DIIS
         # (Jacobi preconditioner, DIIS depth 8), capped at 600 iterations

@@ -171,6 +171,12 @@ typedef struct {
                               FP64 rounding of the largest terms; see sppc_block_gram).  Used where
                               the block width is 8 (k = 7 or 8); a basis entry that is not finite
                               makes the solve return SPPC_ERR_NAN.  0 (default): CUDA cores */
+  int32_t sell_sigma;      /* rows of the windows inside which H's SELL-16 layout sorts the rows of a
+                              level by decreasing entry count (less padding against more reordering of
+                              the X gathers): a multiple of 16 in [16, 1024]; 0 (default) = 1024; -2 =
+                              autotuned at create (64, 256 and 1024 built and timed on two 8-column
+                              products each at the column tile in use, the fastest kept; see
+                              sppc_sell_sigma) */
 } sppc_opts;
 
 typedef struct {
@@ -456,6 +462,12 @@ sppc_status sppc_solve_batch(sppc_handle* handles, int32_t count, double tol, in
  * 8-column product of each candidate, in the order untiled, 2.6M, 1.31M, 655k,
  * 328k columns (0 for a candidate not tried; candidate_ms[5], may be NULL). */
 sppc_status sppc_spmm_tiling(sppc_handle h, int64_t* chunk_cols, double* candidate_ms);
+
+/* The sort window (opts.sell_sigma) of H's SELL-16 layout: *sigma gets the rows
+ * of the window in use; with sell_sigma = -2, candidate_ms[3] (may be NULL) the
+ * autotuner's ms per 8-column product at windows 64, 256 and 1024 (zeros
+ * otherwise).  Host pointers; SPPC_ERR_ARG for a null handle. */
+sppc_status sppc_sell_sigma(sppc_handle h, int32_t* sigma, double* candidate_ms);
 
 /* ---- Batched SpMM: Y_i = H_i X_i for `count` handles (1..1024, untiled layouts,
  * i.e. at most 1,310,720 columns each by default) in one persistent launch: the

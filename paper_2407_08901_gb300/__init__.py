@@ -52,7 +52,8 @@ class Opts(ctypes.Structure):
                 ("minres_deflate", ctypes.c_int32), ("small_degree", ctypes.c_int32),
                 ("switch_stall", ctypes.c_double), ("minres_ctas", ctypes.c_int32),
                 ("spin_cap", ctypes.c_int32), ("value_rounding", ctypes.c_int32), ("minres_fp32", ctypes.c_int32),
-                ("minres_fp32_tol", ctypes.c_double), ("tensor_gram", ctypes.c_int32)]
+                ("minres_fp32_tol", ctypes.c_double), ("tensor_gram", ctypes.c_int32),
+                ("sell_sigma", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -105,6 +106,7 @@ _SIGS = {
     "sppc_standardize": (_I32, [_VP, _I64, _VP, _VP, _VP, _VP]),
     "sppc_solve_batch": (_I32, [_VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
     "sppc_spmm_tiling": (_I32, [_VP, _VP, _VP]),
+    "sppc_sell_sigma": (_I32, [_VP, _VP, _VP]),
     "sppc_spmm_batch_plan": (_I32, [_VP, _I32, _VP, _VP, _I32, ctypes.POINTER(_VP)]),
     "sppc_spmm_batch_run": (_I32, [_VP, _VP]),
     "sppc_spmm_batch_destroy": (_I32, [_VP]),
@@ -428,6 +430,14 @@ def sppc_spmm_tiling(h):
     ms = np.zeros(5)
     _check(h, _lib.sppc_spmm_tiling(h, ctypes.byref(cc), ms.ctypes.data))
     return int(cc.value), ms
+
+
+def sppc_sell_sigma(h):
+    """(sort window of H's layout; autotuner's ms per product at windows 64, 256, 1024, zeros if not tuned)."""
+    sg = ctypes.c_int32()
+    ms = np.zeros(3)
+    _check(h, _lib.sppc_sell_sigma(h, ctypes.byref(sg), ms.ctypes.data))
+    return int(sg.value), ms
 
 
 def sppc_spmm_batch_plan(handles, Xs, Ys):

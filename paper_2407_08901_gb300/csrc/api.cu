@@ -151,6 +151,8 @@ struct sppc_ctx {
   float2* rmm_x = nullptr;
   int64_t chunk_cols_used = 0;                    // SpMM column tile of H's layout (-1: untiled)
   double tuned_ms[8] = {0};                       // autotuner: ms per product of each candidate
+  int sigma_used = 1024;                          // sort window of H's layout
+  double sigma_ms[4] = {0};                       // sigma autotuner: ms per product of 64, 256, 1024
 
   // state
   bool started = false, corrected = false, in_refine = false, t_ready = false;
@@ -1709,10 +1711,84 @@ bool all_converged(const sppc_ctx* h, double tol) {
 
 namespace {
 
+// ms per 8-column product of H's layout with column tile c and sort window
+// sigma: built with a temporary allocator, timed on two products after a
+// warm-up (register-gather kernel, X = 0: the gather pattern, not the values,
+// sets the time) and freed.
+cudaError_t time_layout(int64_t n, const int64_t* d_rp, const int32_t* d_ci, const double* d_va,
+                        const std::vector<int64_t>& seg, bool f64, int64_t c, int sigma, const float2* X, float2* Y,
+                        cudaEvent_t a, cudaEvent_t b, cudaStream_t s, double* ms_out) {
+  std::vector<void*> mine;
+  const DeviceAlloc tmp = [&mine](void** p, size_t bytes) {
+    const cudaError_t x = cudaMalloc(p, bytes ? bytes : 1);
+    if (x == cudaSuccess) mine.push_back(*p);
+    return x;
+  };
+  SellDeviceLayout T;
+  cudaError_t e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, c, f64, 0, s, tmp, T, sigma);
+  if (e == cudaSuccess) {
+    SellDev A;
+    A.nslices = T.nslices;
+    A.nrows = n;
+    A.nchunks = T.nchunks;
+    A.chunk_cols = T.chunk_cols;
+    A.chunk_slice = T.chunk_slice.data();
+    A.slice_ptr = T.slice_ptr_d;
+    A.slice_rows = T.rows_d;
+    A.col = T.col_d;
+    A.val = T.val_d;
+    A.row_first = T.first_d;
+    A.row_last = T.last_d;
+    A.f64 = f64;
+    e = spmm(A, 8, X, Y, Epi{}, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = spmm(A, 8, X, Y, Epi{}, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess) *ms_out = ms / 2.0;
+  }
+  const cudaError_t se = cudaStreamSynchronize(s);
+  for (void* p : mine) cudaFree(p);
+  return e != cudaSuccess ? e : se;
+}
+
+// Candidates of the SELL sort window: 1024, 256 and 64 rows at column tile c.
+cudaError_t tune_sigma(int64_t n, const int64_t* d_rp, const int32_t* d_ci, const double* d_va,
+                       const std::vector<int64_t>& seg, bool f64, int64_t c, cudaStream_t s, int* best,
+                       double* ms_out) {
+  const int cand[3] = {1024, 256, 64};  // reported as 64, 256, 1024
+  float2 *X = nullptr, *Y = nullptr;
+  cudaError_t e = cudaMallocAsync(&X, sizeof(float2) * n * 8, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&Y, sizeof(float2) * n * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(float2) * n * 8, s);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  double best_ms = 1e300;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    double ms = 0.0;
+    e = time_layout(n, d_rp, d_ci, d_va, seg, f64, c, cand[i], X, Y, a, b, s, &ms);
+    if (e == cudaSuccess) {
+      ms_out[2 - i] = ms;
+      if (ms < 0.98 * best_ms) {  // a narrower window must win by 2%
+        best_ms = ms;
+        *best = cand[i];
+      }
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (X) cudaFreeAsync(X, s);
+  if (Y) cudaFreeAsync(Y, s);
+  const cudaError_t se = cudaStreamSynchronize(s);
+  return e != cudaSuccess ? e : se;
+}
+
 // Candidates of the SpMM column tile: untiled, then 2.6M, 1.31M, 655k and
-// 328k columns (at most 255 tiles).  Each layout is built with a temporary
-// allocator, timed on two 8-column products (register-gather kernel, X = 0;
-// the gather pattern, not the values, sets the time) and freed.
+// 328k columns (at most 255 tiles), each timed as time_layout does at the
+// default sort window.
 cudaError_t tune_chunk_cols(int64_t n, const int64_t* d_rp, const int32_t* d_ci, const double* d_va,
                             const std::vector<int64_t>& seg, bool f64, cudaStream_t s, int64_t* best, double* ms_out) {
   const int64_t cand[5] = {-1, 2621440, 1310720, 655360, 327680};
@@ -1727,45 +1803,15 @@ cudaError_t tune_chunk_cols(int64_t n, const int64_t* d_rp, const int32_t* d_ci,
   for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
     const int64_t c = cand[ci];
     if (c > 0 && (c >= n || (n + c - 1) / c > 255)) continue;
-    std::vector<void*> mine;
-    const DeviceAlloc tmp = [&mine](void** p, size_t bytes) {
-      const cudaError_t x = cudaMalloc(p, bytes ? bytes : 1);
-      if (x == cudaSuccess) mine.push_back(*p);
-      return x;
-    };
-    SellDeviceLayout T;
-    e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, c, f64, 0, s, tmp, T);
+    double ms = 0.0;
+    e = time_layout(n, d_rp, d_ci, d_va, seg, f64, c, 1024, X, Y, a, b, s, &ms);
     if (e == cudaSuccess) {
-      SellDev A;
-      A.nslices = T.nslices;
-      A.nrows = n;
-      A.nchunks = T.nchunks;
-      A.chunk_cols = T.chunk_cols;
-      A.chunk_slice = T.chunk_slice.data();
-      A.slice_ptr = T.slice_ptr_d;
-      A.slice_rows = T.rows_d;
-      A.col = T.col_d;
-      A.val = T.val_d;
-      A.row_first = T.first_d;
-      A.row_last = T.last_d;
-      A.f64 = f64;
-      e = spmm(A, 8, X, Y, Epi{}, s);  // warm-up
-      if (e == cudaSuccess) e = cudaEventRecord(a, s);
-      for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = spmm(A, 8, X, Y, Epi{}, s);
-      if (e == cudaSuccess) e = cudaEventRecord(b, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(b);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-      if (e == cudaSuccess) {
-        ms_out[ci] = ms / 2.0;
-        if (ms / 2.0 < 0.98 * best_ms) {  // a finer tile must win by 2%
-          best_ms = ms / 2.0;
-          *best = c;
-        }
+      ms_out[ci] = ms;
+      if (ms < 0.98 * best_ms) {  // a finer tile must win by 2%
+        best_ms = ms;
+        *best = c;
       }
     }
-    cudaStreamSynchronize(s);
-    for (void* p : mine) cudaFree(p);
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
@@ -1838,6 +1884,7 @@ void sppc_default_opts(sppc_opts* o) {
   o->minres_fp32 = 0;
   o->minres_fp32_tol = 1e-6;
   o->tensor_gram = 0;
+  o->sell_sigma = 0;
   o->hybrid_blocks = 0;
   o->spmm_kernel = 1;
   o->reorth = 0;
@@ -2055,6 +2102,9 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
   if (opt.minres_fp32 && !(opt.minres_fp32_tol > 0.0 && opt.minres_fp32_tol < 1.0))
     return fail(nullptr, SPPC_ERR_ARG, "opts.minres_fp32_tol must be in (0, 1)");
   if (opt.tensor_gram != 0 && opt.tensor_gram != 1) return fail(nullptr, SPPC_ERR_ARG, "opts.tensor_gram must be 0 or 1");
+  if (!(opt.sell_sigma == 0 || opt.sell_sigma == -2 ||
+        (opt.sell_sigma >= 16 && opt.sell_sigma <= 1024 && opt.sell_sigma % 16 == 0)))
+    return fail(nullptr, SPPC_ERR_ARG, "opts.sell_sigma must be 0, -2 or a multiple of 16 in [16, 1024]");
   if (opt.precision > 0 && (k + 1) / 2 * 2 != 8 && (k + 1) / 2 * 2 != 4)
     return fail(nullptr, SPPC_ERR_ARG, "opts.precision 1 or 2 needs k in {3, 4, 7, 8} (4- or 8-column FP32 products)");
   if (opt.precond_iters < 0 || opt.precond_iters > 10000)
@@ -2240,8 +2290,13 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
       e = tune_chunk_cols(n, d_rp, d_ci, d_va, seg, h->f64, s, &chunk, h->tuned_ms);
     }
     h->chunk_cols_used = chunk;
+    int sigma = opt.sell_sigma > 0 ? opt.sell_sigma : 1024;
+    if (e == cudaSuccess && opt.sell_sigma == -2)
+      e = tune_sigma(n, d_rp, d_ci, d_va, seg, h->f64, chunk, s, &sigma, h->sigma_ms);
+    h->sigma_used = sigma;
     if (e == cudaSuccess)
-      e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, chunk, h->f64, dev_in ? round_mode : 0, s, alloc, L);
+      e = build_sell_device(n, d_rp, d_ci, d_va, n, seg, chunk, h->f64, dev_in ? round_mode : 0, s, alloc, L,
+                            sigma);
     if (e == cudaSuccess) {
       // per-row constants of the learned proposal's features
       int64_t* d_lev = nullptr;
@@ -3129,6 +3184,13 @@ sppc_status sppc_spmm_tiling(sppc_handle h, int64_t* chunk_cols, double* candida
   if (!h) return fail(nullptr, SPPC_ERR_ARG, "NULL handle");
   if (chunk_cols) *chunk_cols = h->chunk_cols_used;
   if (candidate_ms) std::copy(h->tuned_ms, h->tuned_ms + 5, candidate_ms);
+  return SPPC_OK;
+}
+
+sppc_status sppc_sell_sigma(sppc_handle h, int32_t* sigma, double* candidate_ms) {
+  if (!h) return fail(nullptr, SPPC_ERR_ARG, "sppc_sell_sigma: null handle");
+  if (sigma) *sigma = h->sigma_used;
+  if (candidate_ms) std::copy(h->sigma_ms, h->sigma_ms + 3, candidate_ms);
   return SPPC_OK;
 }
 

@@ -8,7 +8,8 @@
 // padding entries take the chunk's first column and value 0.  Steps:
 //   1. per row, the offsets of the chunk boundaries (binary search in the row);
 //   2. per chunk, the listed rows by an exclusive scan of their flags;
-//   3. per window (<= 1024 rows), a bitonic sort on (decreasing count, position);
+//   3. per window (sigma rows, a multiple of 16 up to 1024), a bitonic sort on
+//      (decreasing count, position);
 //   4. per slice, its rows and width; slice_ptr by an exclusive scan of 16 x width;
 //   5. the entries, one half-warp per slice, values split into double-float.
 // On c2 (4e8 entries) this replaces ~0.42 s of host work.
@@ -262,7 +263,8 @@ __global__ void k_fill(int64_t nslices, const int64_t* __restrict__ slice_ptr, c
 
 cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t ncols,
                               const std::vector<int64_t>& seg, int64_t chunk_cols, bool f64, int round_mode,
-                              cudaStream_t s, const DeviceAlloc& alloc, SellDeviceLayout& out) {
+                              cudaStream_t s, const DeviceAlloc& alloc, SellDeviceLayout& out, int sigma) {
+  if (sigma < kSliceH || sigma > kWindow || sigma % kSliceH) return cudaErrorInvalidValue;
   const int64_t C = (chunk_cols > 0 && chunk_cols < ncols) ? chunk_cols : ncols;
   const int nch = static_cast<int>((ncols + C - 1) / C);
   out.nchunks = nch;
@@ -328,10 +330,10 @@ cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* c
       p.slice_base = slice_base;
       p.q = q;
       parts.push_back(p);
-      for (int64_t w0 = 0; w0 < cnt; w0 += kWindow) {
+      for (int64_t w0 = 0; w0 < cnt; w0 += sigma) {
         Window w;
         w.start = p.list_off + w0;
-        w.size = static_cast<int32_t>(std::min<int64_t>(kWindow, cnt - w0));
+        w.size = static_cast<int32_t>(std::min<int64_t>(sigma, cnt - w0));
         w.q = q;
         wins.push_back(w);
       }

@@ -89,7 +89,7 @@ struct SellDeviceLayout {
 // 2 FP32 diagonal and BF16 off-diagonal entries).
 cudaError_t build_sell_device(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* va, int64_t ncols,
                               const std::vector<int64_t>& seg, int64_t chunk_cols, bool f64, int round_mode,
-                              cudaStream_t s, const DeviceAlloc& alloc, SellDeviceLayout& out);
+                              cudaStream_t s, const DeviceAlloc& alloc, SellDeviceLayout& out, int sigma = 1024);
 // Checks of a CSR that stays on the device: *flags_host gets 2 (column out of
 // range), 4 (columns not strictly increasing), 8 (NaN/Inf) and, with symmetry,
 // 1 (H != H^T bit for bit).  Synchronises the stream.

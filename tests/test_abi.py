@@ -42,6 +42,7 @@ def _small():
     ("nan", 11), ("asym", 2), ("rowptr", 1), ("spmm_kernel", 1), ("reorth", 1), ("precond", 1), ("precision", 1),
     ("precision_k", 1), ("precond_levels", 1), ("switch_stall", 1), ("hybrid", 1), ("rmm_mixed", 1),
     ("spin_cap", 1), ("precision_neg", 1), ("f64_rmm", 1), ("f64_proposal", 1),
+    ("sigma_odd", 1), ("sigma_big", 1), ("sigma_neg", 1),
 ])
 def test_create_rejects_bad_input(case, status):
     import paper_2407_08901_gb300 as S
@@ -62,6 +63,8 @@ def test_create_rejects_bad_input(case, status):
         k = 8
     if case == "spin_cap":
         opts.spin_cap = -1
+    if case.startswith("sigma_"):
+        opts.sell_sigma = {"sigma_odd": 24, "sigma_big": 2048, "sigma_neg": -1}[case]
     if case == "n1_not_level":
         n1 = n1 + 1
     elif case == "k_zero":

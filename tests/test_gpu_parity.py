@@ -107,7 +107,7 @@ def test_spmm_empty_and_ragged_rows(ncols, kernel):
 def _sell_reference(rp, c, ncols, seg, chunk_cols=0, sigma=1024, sh=16):
     """The SELL-16 layout: columns cut into chunks; per chunk and per level the
     rows with entries in the chunk (plus, in chunk 0, rows with no entry at all)
-    are sorted by decreasing count inside windows of 1024 rows (stable) and cut
+    are sorted by decreasing count inside windows of sigma rows (stable) and cut
     into slices of 16 rows."""
     nrows = seg[-1]
     C = chunk_cols if 0 < chunk_cols < ncols else ncols
@@ -137,19 +137,42 @@ def _sell_reference(rp, c, ncols, seg, chunk_cols=0, sigma=1024, sh=16):
             np.array(chunk_slice, dtype=np.int64))
 
 
-@pytest.mark.parametrize("name,chunk", [("small", -1), ("small", 700), ("c1", -1), ("c1", 4096)])
-def test_layout_is_bit_exact(name, chunk):
-    S, w, rp, c, v, h = _create(name, spmm_chunk_cols=chunk)
+@pytest.mark.parametrize("name,chunk,sigma", [("small", -1, 0), ("small", 700, 0), ("c1", -1, 0), ("c1", 4096, 0),
+                                              ("small", 700, 16), ("c1", -1, 64), ("c1", 4096, 256)])
+def test_layout_is_bit_exact(name, chunk, sigma):
+    S, w, rp, c, v, h = _create(name, spmm_chunk_cols=chunk, sell_sigma=sigma)
     try:
         L = S.sppc_get_layout(h)
+        assert S.sppc_sell_sigma(h)[0] == (sigma or 1024)
     finally:
         S.sppc_destroy(h)
-    sp, sr, cs = _sell_reference(rp, c, w.n, list(w.level_offsets), chunk)
+    sp, sr, cs = _sell_reference(rp, c, w.n, list(w.level_offsets), chunk, sigma=sigma or 1024)
     assert L["n_chunks"] == len(cs) - 1
     assert np.array_equal(L["chunk_slice"], cs)
     assert np.array_equal(L["slice_ptr"], sp) and np.array_equal(L["slice_rows"], sr)
     sp11, sr11, _ = _sell_reference(rp, c, w.small_dim, [0, w.small_dim])
     assert np.array_equal(L["h11_slice_ptr"], sp11) and np.array_equal(L["h11_slice_rows"], sr11)
+
+
+def test_sigma_autotune_picks_a_candidate_and_stays_exact():
+    """opts.sell_sigma = -2: the three windows are timed, one of them is kept,
+    and the layout (and so the product) is the one of that window."""
+    S, w, rp, c, v, h = _create("c1", sell_sigma=-2)
+    try:
+        sigma, ms = S.sppc_sell_sigma(h)
+        assert sigma in (64, 256, 1024) and np.all(ms > 0)
+        L = S.sppc_get_layout(h)
+        X = W.random_block(w.n, 8, 4)
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.empty_like(Xd)
+        S.sppc_spmm(h, Xd, Yd)
+        Y = Yd.cpu().numpy()
+    finally:
+        S.sppc_destroy(h)
+    sp, sr, _ = _sell_reference(rp, c, w.n, list(w.level_offsets), 0, sigma=sigma)
+    assert np.array_equal(L["slice_ptr"], sp) and np.array_equal(L["slice_rows"], sr)
+    ref = csr_spmm(rp, c, v, X)
+    assert np.all(np.abs(Y - ref) <= SPMM_TOL[0] * _abs_spmm(rp, c, v, X))
 
 
 @pytest.mark.parametrize("prec", [0, -1])
