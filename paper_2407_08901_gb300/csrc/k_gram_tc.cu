@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t full_bar[kStages], cut_bar[kStages], mma_bar[kStages], acc_bar[2], free_bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, bad_flag;
-  __shared__ int armed[kStages], committed[kStages];  // phases started, for the error path
+  __shared__ int armed[kStages], committed[kStages];  // [0]: chunks armed / committed, for the error path
   // stages from a 1024-byte boundary (the swizzle atoms need 256-byte alignment)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -227,10 +227,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 1) {
     // ---- copies: chunk k into stage k % kStages once the MMAs of chunk k - kStages are done
     if (elect_one()) {
-      for (int64_t k = 0; k < nck; ++k) {
-        const int st = static_cast<int>(k % kStages);
-        const int64_t use = k / kStages;
-        if (use > 0 && !role_wait(smem_u32(&mma_bar[st]), static_cast<uint32_t>((use - 1) & 1), abort)) break;
+      // stage st, used for the wraps-th time (32-bit counters stepped per chunk)
+      int st = 0, armed_total = 0;
+      uint32_t wraps = 0;
+      for (int k = 0; k < static_cast<int>(nck); ++k) {
+        if (wraps > 0 && !role_wait(smem_u32(&mma_bar[st]), (wraps - 1) & 1u, abort)) break;
         const uint32_t bar = smem_u32(&full_bar[st]);
         const int64_t base = c0 + k * kTcRows;
         const int rows = static_cast<int>(c1 - base < kTcRows ? c1 - base : kTcRows);
@@ -242,8 +243,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bulk_g2s(dst, src, na * kBlockChunk, bar);
         if (stack) bulk_g2s(dst + kStackCopy, src + kAtom, na * kBlockChunk - kAtom, bar);
         bulk_g2s(dst + kABytes, B + base * 8, rows * 64, bar);
-        armed[st] += 1;
+        ++armed_total;
+        if (++st == kStages) {
+          st = 0;
+          ++wraps;
+        }
       }
+      armed[0] = armed_total;
     }
     __syncwarp();
   } else if (warp == 0) {
@@ -251,14 +257,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // for a group's first chunk, once the region's previous group is read back)
     if (elect_one()) {
       const uint32_t idesc = instr_desc(kDCols);
-      for (int64_t k = 0; k < nck; ++k) {
-        const int st = static_cast<int>(k % kStages);
-        const int64_t g = k / kTcGroupChunks;
-        const int r = static_cast<int>(g & 1);
-        const bool first = k % kTcGroupChunks == 0;
-        if (first && g >= 2 && !role_wait(smem_u32(&free_bar[r]), static_cast<uint32_t>(((g >> 1) - 1) & 1), abort))
+      // stage st and its phase parity, group g and the chunk's place gi in it
+      int st = 0, gi = 0, g = 0, committed_total = 0;
+      uint32_t ph = 0;
+      for (int k = 0; k < static_cast<int>(nck); ++k) {
+        const int r = g & 1;
+        const bool first = gi == 0;
+        if (first && g >= 2 && !role_wait(smem_u32(&free_bar[r]), static_cast<uint32_t>((g >> 1) - 1) & 1u, abort))
           break;
-        if (!role_wait(smem_u32(&cut_bar[st]), static_cast<uint32_t>((k / kStages) & 1), abort)) break;
+        if (!role_wait(smem_u32(&cut_bar[st]), ph, abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = smem_u32(smem + st * kStageBytes), cb = a0 + kABytes + kBRaw;
         if (stack) {
@@ -277,12 +284,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mma_bar[st]))
                      : "memory");
-        committed[st] += 1;
-        if (k % kTcGroupChunks == kTcGroupChunks - 1 || k + 1 == nck)
+        ++committed_total;
+        if (gi == kTcGroupChunks - 1 || k + 1 == static_cast<int>(nck))
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&acc_bar[r]))
                        : "memory");
+        if (++st == kStages) {
+          st = 0;
+          ph ^= 1u;
+        }
+        if (++gi == kTcGroupChunks) {
+          gi = 0;
+          ++g;
+        }
       }
+      committed[0] = committed_total;
     }
     __syncwarp();
   } else if (warp >= 4 && warp < 8) {
@@ -291,12 +307,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int fb = fexp[jb];
     if (fb < -5000) fb = 0;  // an all-zero column
     bool bad = false;
-    for (int64_t k = 0; k < nck; ++k) {
-      const int st = static_cast<int>(k % kStages);
-      if (!role_wait(smem_u32(&full_bar[st]), static_cast<uint32_t>((k / kStages) & 1), abort)) break;
+    // value of chunk k (stage st) into its C tiles
+    auto cut = [&](int k, int st) {
       unsigned char* sg = smem + st * kStageBytes;
-      const float2 v = c0 + k * kTcRows + kr < c1 ? reinterpret_cast<const float2*>(sg + kABytes)[ct]
-                                                   : make_float2(0.f, 0.f);
+      const float2 v = c0 + static_cast<int64_t>(k) * kTcRows + kr < c1
+                           ? reinterpret_cast<const float2*>(sg + kABytes)[ct]
+                           : make_float2(0.f, 0.f);
       uint64_t x;
       bool ng;
       if (!to_fixed<F64>(v, kQShift - fb, x, ng)) {
@@ -315,8 +331,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         *reinterpret_cast<uint16_t*>(dst + t * kAtom) =
             static_cast<uint16_t>(digit_high(t) ? (word >> 16) : (word & 0xFFFFu));
       }
+    };
+    int st = 0;
+    uint32_t ph = 0;
+    for (int k = 0; k < static_cast<int>(nck); ++k) {
+      if (!role_wait(smem_u32(&full_bar[st]), ph, abort)) break;
+      cut(k, st);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&cut_bar[st]));
+      if (++st == kStages) {
+        st = 0;
+        ph ^= 1u;
+      }
     }
     if (bad) atomicOr(&bad_flag, 1);
   } else if (warp >= 8) {
@@ -345,7 +371,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // and the CTA leaves
     if (tid == 0) {
       for (int st = 0; st < kStages; ++st) {
-        const int a = armed[st], c = committed[st];
+        // phases of stage st started: the chunks k < total with k % kStages == st
+        const int a = armed[0] / kStages + (st < armed[0] % kStages ? 1 : 0);
+        const int c = committed[0] / kStages + (st < committed[0] % kStages ? 1 : 0);
         volatile int never = 0;
         if (a > 0) role_wait(smem_u32(&full_bar[st]), static_cast<uint32_t>((a - 1) & 1), &never);
         never = 0;

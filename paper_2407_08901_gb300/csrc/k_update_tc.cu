@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
   __shared__ uint32_t tmem_base;
   __shared__ int gexp[8];
   __shared__ int abort_flag, bad_flag;
-  __shared__ int armed[kUStages], committed[kUStages];  // phases started, for the error path
+  __shared__ int armed[kUStages], committed[kUStages];  // [0]: units armed / committed, for the error path
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* ctiles = smem + kUStages * kStepBytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -158,13 +158,12 @@ __global__ void __launch_bounds__(kUThreads, 1)
   if (warp == 1) {
     // ---- copies: unit u = (tile u / ksteps, K step u % ksteps) into stage u % kUStages
     if (elect_one()) {
-      for (int64_t u = 0; u < nunits; ++u) {
-        const int st = static_cast<int>(u % kUStages);
-        const int64_t use = u / kUStages;
-        if (use > 0 && !role_wait(smem_u32(&mma_bar[st]), static_cast<uint32_t>((use - 1) & 1), abort)) break;
-        const int64_t tile = u / ksteps;
-        const int ks = static_cast<int>(u % ksteps);
-        const int64_t ch0 = tile * kTileChunks;
+      // stage st used for the wraps-th time; unit = (tile, K step ks) (32-bit counters)
+      int st = 0, ks = 0, tile = 0, armed_total = 0;
+      uint32_t wraps = 0;
+      for (int u = 0; u < static_cast<int>(nunits); ++u) {
+        if (wraps > 0 && !role_wait(smem_u32(&mma_bar[st]), (wraps - 1) & 1u, abort)) break;
+        const int64_t ch0 = static_cast<int64_t>(tile) * kTileChunks;
         const int nch = static_cast<int>(nck - ch0 < kTileChunks ? nck - ch0 : kTileChunks);
         const int nb = na - 2 * ks < 2 ? na - 2 * ks : 2;
         const uint32_t bar = smem_u32(&full_bar[st]);
@@ -175,8 +174,17 @@ __global__ void __launch_bounds__(kUThreads, 1)
         const unsigned char* src = Qd + (gc0 + ch0) * kGroupChunk + 2 * ks * kBlockChunk;
         for (int c = 0; c < nch; ++c)
           bulk_g2s(dst + c * kChunkStride, src + static_cast<int64_t>(c) * kGroupChunk, nb * kBlockChunk, bar);
-        armed[st] += 1;
+        ++armed_total;
+        if (++st == kUStages) {
+          st = 0;
+          ++wraps;
+        }
+        if (++ks == ksteps) {
+          ks = 0;
+          ++tile;
+        }
       }
+      armed[0] = armed_total;
     }
     __syncwarp();
   } else if (warp == 0) {
@@ -184,15 +192,14 @@ __global__ void __launch_bounds__(kUThreads, 1)
     // until the region's previous tile is read back
     if (elect_one()) {
       const uint32_t idesc = instr_desc(kDCols, true);
-      for (int64_t u = 0; u < nunits; ++u) {
-        const int st = static_cast<int>(u % kUStages);
-        const int64_t tile = u / ksteps;
-        const int ks = static_cast<int>(u % ksteps);
-        const int r = static_cast<int>(tile & 1);
+      int st = 0, ks = 0, tile = 0, committed_total = 0;
+      uint32_t ph = 0;
+      for (int u = 0; u < static_cast<int>(nunits); ++u) {
+        const int r = tile & 1;
         if (ks == 0 && tile >= 2 &&
-            !role_wait(smem_u32(&free_bar[r]), static_cast<uint32_t>(((tile >> 1) - 1) & 1), abort))
+            !role_wait(smem_u32(&free_bar[r]), static_cast<uint32_t>((tile >> 1) - 1) & 1u, abort))
           break;
-        if (!role_wait(smem_u32(&full_bar[st]), static_cast<uint32_t>((u / kUStages) & 1), abort)) break;
+        if (!role_wait(smem_u32(&full_bar[st]), ph, abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = smem_u32(smem + st * kStepBytes);
         const uint32_t cb = smem_u32(ctiles + ks * kCoefTiles * kAtom);
@@ -203,12 +210,21 @@ __global__ void __launch_bounds__(kUThreads, 1)
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mma_bar[st]))
                      : "memory");
-        committed[st] += 1;
+        ++committed_total;
         if (ks == ksteps - 1)
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&acc_bar[r]))
                        : "memory");
+        if (++st == kUStages) {
+          st = 0;
+          ph ^= 1u;
+        }
+        if (++ks == ksteps) {
+          ks = 0;
+          ++tile;
+        }
       }
+      committed[0] = committed_total;
     }
     __syncwarp();
   } else if (warp >= 4) {
@@ -267,7 +283,9 @@ __global__ void __launch_bounds__(kUThreads, 1)
   if (abort_flag) {
     if (tid == 0) {
       for (int st = 0; st < kUStages; ++st) {
-        const int a = armed[st], c = committed[st];
+        // phases of stage st started: the units u < total with u % kUStages == st
+        const int a = armed[0] / kUStages + (st < armed[0] % kUStages ? 1 : 0);
+        const int c = committed[0] / kUStages + (st < committed[0] % kUStages ? 1 : 0);
         volatile int never = 0;
         if (a > 0) role_wait(smem_u32(&full_bar[st]), static_cast<uint32_t>((a - 1) & 1), &never);
         never = 0;
