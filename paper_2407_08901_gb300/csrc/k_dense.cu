@@ -8,6 +8,7 @@
 // partial sums, a finishing kernel adds the partials in a fixed order.  Every
 // kernel is instantiated for both slot formats (val.cuh): double-float (F64 =
 // false) and native FP64 (F64 = true); the host wrappers take the format.
+#include "fp64_fast.cuh"
 #include "sppc_internal.h"
 #include "val.cuh"
 
@@ -16,6 +17,18 @@ namespace sppc {
 namespace {
 
 constexpr int kChunk = 2048;  // rows per CTA in the reductions over long blocks
+
+// The preconditioned residual r / (diag(H) - theta) of the Ritz pass: one
+// division per element.  In FP64 a division costs about ten FP64 operations on
+// this GPU, which made the elementwise pass DFMA-bound (n x 8 divisions); the
+// fast reciprocal (fp64_fast.cuh, within a few ulps) and a product take four.
+template <bool F64>
+__device__ __forceinline__ float2 precond_div(float2 num, float2 den) {
+  if constexpr (F64)
+    return d_slot(slot_d(num) * recip64(slot_d(den)));
+  else
+    return Ar<false>::div(num, den);
+}
 
 // Rows per CTA of a reduction over `rows` rows: about eight CTAs per SM (so
 // that four resident CTAs of 8 warps run two full waves), in multiples of 32
@@ -411,7 +424,7 @@ __global__ void __launch_bounds__(256) k_ritz_resid(BlockList Q, BlockList Wb, c
       if (Tout) {
         // preconditioned residual d / (H_rr - theta_j), denominator clamped to |.| >= clamp
         float2 t = d;
-        if (diag) t = V::div(d, V::clamp_den(V::sub(diag[r], sth[j]), clamp));
+        if (diag) t = precond_div<F64>(d, V::clamp_den(V::sub(diag[r], sth[j]), clamp));
         Tout[r * KP + j] = t;
       }
     }
@@ -551,7 +564,7 @@ __global__ void k_ritz_precond(const float2* __restrict__ D, const float2* __res
   const int64_t r = e / kp;
   const int j = static_cast<int>(e - r * kp);
   float2 t = D[e];
-  if (diag) t = V::div(t, V::clamp_den(V::sub(diag[r], theta[j]), clamp));
+  if (diag) t = precond_div<F64>(t, V::clamp_den(V::sub(diag[r], theta[j]), clamp));
   T[e] = t;
 }
 }  // namespace

@@ -25,6 +25,7 @@ __global__ void k_chol_rinv(const double* __restrict__ G, int ldg, int kk, int k
                             double* __restrict__ R, float2* __restrict__ Rinv_df, int* status, bool f64) {
   __shared__ double A[16][17];
   __shared__ double Ri[16][17];
+  __shared__ double rdiag[16];  // 1 / R_jj (fast reciprocal: a few ulps)
   __shared__ int bad;
   const int t = threadIdx.x;
   if (t == 0) bad = 0;
@@ -42,19 +43,24 @@ __global__ void k_chol_rinv(const double* __restrict__ G, int ldg, int kk, int k
     }
     __syncthreads();
   }
-  // right-looking Cholesky A = R^T R, R upper; thread i owns column i
+  // right-looking Cholesky A = R^T R, R upper; thread i owns column i.  The
+  // square roots and reciprocals take the fast FP64 forms (fp64_fast.cuh): this
+  // serial chain runs twice per appended block
   for (int j = 0; j < kk; ++j) {
     if (t == 0) {
       const double d = A[j][j];
       if (!(d > 0.0)) {
         if (!bad) bad = j + 1;
         A[j][j] = 1.0;
+        rdiag[j] = 1.0;
       } else {
-        A[j][j] = sqrt(d);
+        const double rs = rsqrt64(d);
+        A[j][j] = d * rs;
+        rdiag[j] = recip64(A[j][j]);
       }
     }
     __syncthreads();
-    if (t > j && t < kk) A[j][t] /= A[j][j];
+    if (t > j && t < kk) A[j][t] *= rdiag[j];
     __syncthreads();
     if (t > j && t < kk) {
       for (int i = j + 1; i <= t; ++i) A[i][t] -= A[j][i] * A[j][t];
@@ -66,7 +72,7 @@ __global__ void k_chol_rinv(const double* __restrict__ G, int ldg, int kk, int k
     for (int i = t; i >= 0; --i) {
       double s = (i == t) ? 1.0 : 0.0;
       for (int l = i + 1; l <= t; ++l) s -= A[i][l] * Ri[l][t];
-      Ri[i][t] = s / A[i][i];
+      Ri[i][t] = s * rdiag[i];
     }
   }
   __syncthreads();
