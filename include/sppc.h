@@ -79,7 +79,8 @@ typedef struct {
   int32_t timing;         /* 1: time kernels with CUDA events into sppc_stats (default 0) */
   int64_t spmm_chunk_cols; /* SpMM column tile: 0 (default) = 1310720 columns, 80 MB of an 8-column
                               double-float block (keeps the gathered rows of X in L2), untiled with
-                              precision -1 (the FP64 product is DFMA-bound), -1 = untiled, > 0 = that many
+                              precision -1 when an 8-column X fits in L2 (the FP64 product is then
+                              DFMA-bound), -1 = untiled, > 0 = that many
                               columns (at most 255 tiles), -2 = autotuned at create (untiled and
                               2.6M/1.31M/655k/328k-column tiles timed on two 8-column products each;
                               the fastest kept, see sppc_spmm_tiling) */

@@ -2255,9 +2255,16 @@ sppc_status sppc_create(const sppc_csr* Hc, const int64_t* level_offsets, int32_
     int64_t chunk = opt.spmm_chunk_cols;
     const bool tune = chunk == -2;
     // default: 80 MB of an 8-column double-float block keeps X's gathered rows
-    // in L2; the native FP64 product is DFMA-bound, where tiles only add passes
-    // (c2: 6.13 ms untiled against 6.43 ms in 1.31M-column tiles)
-    if (chunk == 0) chunk = h->f64 ? -1 : 1310720;
+    // in L2.  The native FP64 product is DFMA-bound as long as X itself fits in
+    // L2, and then tiles only add passes (c2, X 128 MB: 6.12 ms untiled against
+    // 6.43 ms in 1.31M-column tiles); beyond that the gathers miss L2 and the
+    // tiles win again (c3, X 1.28 GB: 107 ms untiled against 90 ms)
+    if (chunk == 0) {
+      int dev = 0, l2 = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+      chunk = (h->f64 && n * 8 * (int64_t)sizeof(float2) <= (int64_t)l2) ? -1 : 1310720;
+    }
     if (chunk > 0 && (n + chunk - 1) / chunk > 255) chunk = (n + 254) / 255;
     cudaStream_t s = h->stream;
     int64_t* d_rp = nullptr;
