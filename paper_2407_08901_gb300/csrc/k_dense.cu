@@ -320,33 +320,38 @@ struct Pairs {
   const float2* b[4];
 };
 
-template <int KP, bool F64>
-__global__ void __launch_bounds__(256) k_coldots(Pairs P, int nq, int64_t r0, int64_t r1, int64_t chunk,
+// NQ pairs: only NQ * KP accumulators live (more resident warps for the
+// one-pair calls); rows read as 16-byte vectors.  The same sums in the same
+// order for every NQ.
+template <int KP, bool F64, int NQ>
+__global__ void __launch_bounds__(256) k_coldots(Pairs P, int64_t r0, int64_t r1, int64_t chunk,
                                                  float2* partials) {
   using V = Ar<F64>;
-  __shared__ float2 red[8][4 * 8];
+  __shared__ float2 red[8][NQ * KP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = r0 + static_cast<int64_t>(blockIdx.x) * chunk;
   const int64_t c1 = min(c0 + chunk, r1);
-  typename V::Acc acc[4 * KP];
+  typename V::Acc acc[NQ * KP];
 #pragma unroll
-  for (int t = 0; t < 4 * KP; ++t) V::zero(acc[t]);
+  for (int t = 0; t < NQ * KP; ++t) V::zero(acc[t]);
   for (int64_t r = c0 + threadIdx.x; r < c1; r += blockDim.x) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q < nq) {
+    for (int q = 0; q < NQ; ++q) {
+      const float4* ar = reinterpret_cast<const float4*>(P.a[q] + r * KP);
+      const float4* br = reinterpret_cast<const float4*>(P.b[q] + r * KP);
 #pragma unroll
-        for (int j = 0; j < KP; ++j) V::mac(acc[q * KP + j], P.a[q][r * KP + j], P.b[q][r * KP + j]);
+      for (int h = 0; h < KP / 2; ++h) {
+        const float4 x = ar[h], y = br[h];
+        V::mac(acc[q * KP + 2 * h], make_float2(x.x, x.y), make_float2(y.x, y.y));
+        V::mac(acc[q * KP + 2 * h + 1], make_float2(x.z, x.w), make_float2(y.z, y.w));
       }
     }
   }
-  const int nout = nq * KP;
+  constexpr int nout = NQ * KP;
 #pragma unroll
-  for (int t = 0; t < 4 * KP; ++t) {
-    if (t < nout) {
-      const float2 v = warp_sum<F64>(V::get(acc[t]));
-      if (lane == 0) red[warp][t] = v;
-    }
+  for (int t = 0; t < nout; ++t) {
+    const float2 v = warp_sum<F64>(V::get(acc[t]));
+    if (lane == 0) red[warp][t] = v;
   }
   __syncthreads();
   if (threadIdx.x < nout) {
@@ -644,8 +649,14 @@ cudaError_t coldots(const float2* const* A, const float2* const* B, int nq, int 
   }
   if (nchunks * nout > partial_cap) return cudaErrorInvalidValue;
   const unsigned g = static_cast<unsigned>(nchunks);
-  cudaError_t e =
-      dispatch(kp, f64, [&]<int KP, bool F>() { k_coldots<KP, F><<<g, 256, 0, s>>>(P, nq, r0, r1, chunk, partials); });
+  cudaError_t e = dispatch(kp, f64, [&]<int KP, bool F>() {
+    switch (nq) {
+      case 1: k_coldots<KP, F, 1><<<g, 256, 0, s>>>(P, r0, r1, chunk, partials); break;
+      case 2: k_coldots<KP, F, 2><<<g, 256, 0, s>>>(P, r0, r1, chunk, partials); break;
+      case 3: k_coldots<KP, F, 3><<<g, 256, 0, s>>>(P, r0, r1, chunk, partials); break;
+      default: k_coldots<KP, F, 4><<<g, 256, 0, s>>>(P, r0, r1, chunk, partials); break;
+    }
+  });
   if (e != cudaSuccess) return e;
   return finish(partials, nchunks, nout, out, f64, s);
 }
