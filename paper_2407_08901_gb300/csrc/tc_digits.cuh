@@ -279,60 +279,76 @@ __device__ __forceinline__ bool elect_one() {
   return leader != 0;
 }
 
-// W 2^e2 for a signed 128-bit integer W, as the nearest double (ties to even),
-// from integer operations only (no FP64 arithmetic).  Results below the normal
-// range are flushed to zero; they lie far under the values the kernels meet.
-__device__ __forceinline__ double i128_scaled_to_double(__int128 W, int e2) {
-  if (W == 0) return 0.0;
-  const bool neg = W < 0;
-  unsigned __int128 U = neg ? static_cast<unsigned __int128>(-W) : static_cast<unsigned __int128>(W);
-  const uint64_t uh = static_cast<uint64_t>(U >> 64), ul = static_cast<uint64_t>(U);
-  const int msb = uh ? 127 - __clzll(static_cast<long long>(uh)) : 63 - __clzll(static_cast<long long>(ul));
-  uint64_t mant;
-  int ex = msb + e2;  // value = 1.mant * 2^ex
-  if (msb > 52) {
-    const int sh = msb - 52;
-    mant = static_cast<uint64_t>(U >> sh);
-    const unsigned __int128 rem = U & ((static_cast<unsigned __int128>(1) << sh) - 1);
-    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant == (1ull << 53)) {
-        mant >>= 1;
-        ++ex;
-      }
-    }
-  } else {
-    mant = ul << (52 - msb);
-  }
+// The level words' exact sum W = w0 2^72 + w1 2^48 + w2 2^24 + w3 (|w_c| <
+// 2^41) as its sign and magnitude left-aligned in 128 bits: V = |W| 2^lz with
+// bit 127 set (lz = leading zeros of |W|), in two 64-bit halves.  Integer
+// operations with selects instead of branches, so that the eight outputs of a
+// thread interleave.  Returns false for W = 0.
+__device__ __forceinline__ bool words_aligned(const long long (&w)[4], uint64_t& vh, uint64_t& vl, int& msb,
+                                              bool& neg) {
+  // two's-complement 128-bit sum of the shifted words
+  uint64_t lo = static_cast<uint64_t>(w[3]), hi = static_cast<uint64_t>(w[3] >> 63);
+  auto add = [&](uint64_t l2, uint64_t h2) {
+    const uint64_t nl = lo + l2;
+    hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  };
+  add(static_cast<uint64_t>(w[2]) << 24, static_cast<uint64_t>(w[2] >> 40));
+  add(static_cast<uint64_t>(w[1]) << 48, static_cast<uint64_t>(w[1] >> 16));
+  hi += static_cast<uint64_t>(w[0]) << 8;
+  neg = static_cast<long long>(hi) < 0;
+  const uint64_t nlo = ~lo + 1ull, nhi = ~hi + (nlo == 0 ? 1ull : 0ull);
+  const uint64_t ul = neg ? nlo : lo, uh = neg ? nhi : hi;
+  if ((ul | uh) == 0) return false;
+  const int lz = uh ? __clzll(static_cast<long long>(uh)) : 64 + __clzll(static_cast<long long>(ul));
+  const int sa = lz & 63;                       // shift within the word
+  const uint64_t a_hi = sa ? (uh << sa) | (ul >> (64 - sa)) : uh, a_lo = ul << sa;
+  vh = lz >= 64 ? (ul << sa) : a_hi;
+  vl = lz >= 64 ? 0ull : a_lo;
+  msb = 127 - lz;
+  return true;
+}
+
+// The nearest double (ties to even) of W 2^e2, W the level words' sum; results
+// below the normal range are flushed to zero (they lie far under the values
+// the kernels meet).
+__device__ __forceinline__ double words_to_double(const long long (&w)[4], int e2) {
+  uint64_t vh, vl;
+  int msb;
+  bool neg;
+  if (!words_aligned(w, vh, vl, msb, neg)) return 0.0;
+  uint64_t mant = vh >> 11;                     // 53 bits, leading one at bit 52
+  const uint64_t rnd = (vh >> 10) & 1ull;
+  const uint64_t sticky = ((vh & 0x3FFull) | vl) != 0 ? 1ull : 0ull;
+  mant += rnd & (sticky | (mant & 1ull));
+  const bool carry = (mant >> 53) != 0;
+  mant = carry ? mant >> 1 : mant;
+  const int ex = msb + (carry ? 1 : 0) + e2;   // value = 1.mant * 2^ex
   if (ex < -1022) return 0.0;
   const uint64_t bits = (neg ? (1ull << 63) : 0ull) | (static_cast<uint64_t>(ex + 1023) << 52) |
                         (mant & ((1ull << 52) - 1));
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
-// The same value as a double-float pair hi + lo (the top 24 bits and the next
-// 24, both truncated, then renormalised by an exact fast two-sum), from integer
-// operations and FP32 bit patterns.
-__device__ __forceinline__ float2 i128_scaled_to_df(__int128 W, int e2) {
-  if (W == 0) return make_float2(0.f, 0.f);
-  const bool neg = W < 0;
-  unsigned __int128 U = neg ? static_cast<unsigned __int128>(-W) : static_cast<unsigned __int128>(W);
-  const uint64_t uh = static_cast<uint64_t>(U >> 64), ul = static_cast<uint64_t>(U);
-  const int msb = uh ? 127 - __clzll(static_cast<long long>(uh)) : 63 - __clzll(static_cast<long long>(ul));
-  auto word = [&](int top) -> float {  // the 24 bits from bit `top` down, as a float of the right scale
-    const int sh = top - 23;
-    const uint32_t m = static_cast<uint32_t>((sh >= 0 ? (U >> sh) : (U << -sh)) & 0xFFFFFFu);
+// The double-float pair of W 2^e2: the top 24 bits and the next 24, both
+// truncated, as FP32 bit patterns, then renormalised by an exact fast two-sum.
+__device__ __forceinline__ float2 words_to_df(const long long (&w)[4], int e2) {
+  uint64_t vh, vl;
+  int msb;
+  bool neg;
+  if (!words_aligned(w, vh, vl, msb, neg)) return make_float2(0.f, 0.f);
+  const uint32_t sgn = neg ? 0x80000000u : 0u;
+  auto word = [&](uint32_t m, int top) -> float {  // 24-bit chunk m whose bit 23 sits at bit `top`
     if (m == 0) return 0.f;
-    const int lead = 31 - __clz(static_cast<int>(m));  // m's top set bit (<= 23)
-    const int ex = top - (23 - lead) + e2;             // exponent of m's leading bit
+    const int lead = 31 - __clz(static_cast<int>(m));
+    const int ex = top - (23 - lead) + e2;
     if (ex < -126) return 0.f;
-    if (ex > 127) return neg ? -__int_as_float(0x7F800000) : __int_as_float(0x7F800000);
-    const uint32_t frac = (m << (23 - lead)) & 0x7FFFFFu;
-    return __uint_as_float((neg ? 0x80000000u : 0u) | (static_cast<uint32_t>(ex + 127) << 23) | frac);
+    if (ex > 127) return __uint_as_float(sgn | 0x7F800000u);
+    return __uint_as_float(sgn | (static_cast<uint32_t>(ex + 127) << 23) | ((m << (23 - lead)) & 0x7FFFFFu));
   };
-  const float hi = word(msb), lo = msb >= 24 ? word(msb - 24) : 0.f;
-  const float sum = __fadd_rn(hi, lo);  // renormalised: |lo| <= ulp(hi) / 2
+  const float hi = word(static_cast<uint32_t>(vh >> 40), msb);
+  const float lo = word(static_cast<uint32_t>(vh >> 16) & 0xFFFFFFu, msb - 24);
+  const float sum = __fadd_rn(hi, lo);
   return make_float2(sum, __fsub_rn(lo, __fsub_rn(sum, hi)));
 }
 
@@ -341,14 +357,10 @@ __device__ __forceinline__ float2 i128_scaled_to_df(__int128 W, int e2) {
 // 2^(24 (3 - c)) times 2^(scale - 98), scale = the column's exponent g.
 template <bool F64>
 __device__ __forceinline__ float2 levels_to_slot(const long long (&w)[4], int scale) {
-  __int128 W = static_cast<__int128>(w[0]);
-  W = (W << 24) + w[1];
-  W = (W << 24) + w[2];
-  W = (W << 24) + w[3];
   if constexpr (F64)
-    return d_slot(i128_scaled_to_double(W, scale - 98));
+    return d_slot(words_to_double(w, scale - 98));
   else
-    return i128_scaled_to_df(W, scale - 98);
+    return words_to_df(w, scale - 98);
 }
 
 }  // namespace tc
