@@ -1147,11 +1147,12 @@ cudaError_t qgram(sppc_ctx* h, int nq, const float2* B, double* out, cudaStream_
 
 // Block update Y = alpha X + [Q_0 .. Q_{nq-1}] coef (Eq. blkGS, the restart's
 // Q Y): on the tensor cores under the same conditions as qgram, from 2 blocks
-// in FP64 and 10 in double-float (measured on c2), else on the CUDA cores.
+// in FP64 and 4 in double-float (measured on 2e6 rows: 214 against 237 us at 4
+// blocks, 200 against 144 us at 2), else on the CUDA cores.
 cudaError_t qupdate(sppc_ctx* h, int nq, float2* Y, const float2* X, const float2* alpha, const float2* coef,
                     cudaStream_t s) {
   const int64_t n = h->n;
-  if (h->Qd && h->kp == 8 && nq >= (h->f64 ? 2 : 10)) {
+  if (h->Qd && h->kp == 8 && nq >= (h->f64 ? 2 : 4)) {
     cudaError_t e = ensure_qdigits(h, nq, s);
     if (e != cudaSuccess) return e;
     return update_tc(h->Qd, nq, coef, alpha, X, Y, n, h->f64, h->dStatus + 8, s);
@@ -1174,16 +1175,20 @@ cudaError_t ensure_wdigits(sppc_ctx* h, int nq, cudaStream_t s) {
   return cudaSuccess;
 }
 
-bool tensor_dense(const sppc_ctx* h, int nq, bool update_kind) {
+// Whether a product over nq basis blocks takes the tensor cores: from 2 blocks
+// in FP64; in double-float from 4 for block updates and 10 for the Ritz pass
+// (two tensor-core updates against one fused CUDA-core pass over Q and W).
+enum class DenseKind { update, ritz };
+bool tensor_dense(const sppc_ctx* h, int nq, DenseKind kind) {
   if (!h->Qd || h->kp != 8) return false;
-  return nq >= (h->f64 ? 2 : (update_kind ? 10 : 5));
+  return nq >= (h->f64 ? 2 : (kind == DenseKind::update ? 4 : 10));
 }
 
 // Update against W blocks 0 .. nq - 1 (the restart's W Y, the recycled H Psi of
 // Eq. HPsip): tensor cores under qupdate's conditions, else CUDA cores.
 cudaError_t wupdate(sppc_ctx* h, int nq, float2* Y, const float2* X, const float2* alpha, const float2* coef,
                     cudaStream_t s) {
-  if (tensor_dense(h, nq, true)) {
+  if (tensor_dense(h, nq, DenseKind::update)) {
     cudaError_t e = ensure_wdigits(h, nq, s);
     if (e != cudaSuccess) return e;
     return update_tc(h->Wd, nq, coef, alpha, X, Y, h->n, h->f64, h->dStatus + 8, s, h->wexp);
@@ -1204,7 +1209,7 @@ cudaError_t qritz(sppc_ctx* h, int np1, double* Zout, int64_t ldz, int ncols, fl
                   float clamp, float2* Zlead, float2* Rlead, int64_t nlead, cudaStream_t s) {
   const int kp = h->kp;
   const int64_t n = h->n;
-  if (!tensor_dense(h, np1, true))
+  if (!tensor_dense(h, np1, DenseKind::ritz))
     return ritz_resid(blocks(h->Q, n, kp, 0, np1), blocks(h->W, n, kp, 0, np1), h->dY, h->dCoef + kTheta, kp, n,
                       h->dDots, h->partials, h->partial_cap, Zout, ldz, ncols, Tout, diag, clamp, h->f64, s, Zlead,
                       Rlead, nlead);
