@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsppc.so")
-SOURCES = ["k_spmm.cu", "k_spmm_tma.cu", "k_spmm_f32.cu", "sell_build.cu", "k_dense.cu", "k_gram_tc.cu", "k_update_tc.cu", "k_small.cu", "k_minres.cu", "k_learned.cu", "api.cu", "noalloc.cu", "batch.cu", "k_spmm_batch.cu"]
+SOURCES = ["k_spmm.cu", "k_spmm_tma.cu", "k_spmm_f32.cu", "sell_build.cu", "k_dense.cu", "k_gram_tc.cu", "k_update_tc.cu", "k_small.cu", "k_minres.cu", "k_learned.cu", "api.cu", "api_create.cu", "drv_host.cu", "drv_solver.cu", "noalloc.cu", "batch.cu", "k_spmm_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
