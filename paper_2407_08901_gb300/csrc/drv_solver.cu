@@ -46,18 +46,23 @@ sppc_status rotate_set(sppc_ctx* h, float2** X, float2** Y, int nb, const float2
 }
 
 sppc_status ortho_set(sppc_ctx* h, float2** X, float2** Tmp, int nb, int b) {
-  // shifted CholeskyQR, then CholeskyQR twice (result back in X)
+  // shifted CholeskyQR, then CholeskyQR twice (result back in X).  A breakdown
+  // leaves a finite factor (the pivot set to 1), so the three passes run and
+  // their statuses (dStatus[2..4]) are read once at the end; the caller
+  // discards the block on a breakdown.
   for (int pass = 0; pass < 3; ++pass) {
     CKS(gram_set(h, X, X, nb, h->dS));
     const double shift = (pass == 0) ? 1e-12 : 0.0;
-    CK(chol_rinv(h->dS, 16, b, 16, shift, h->dR1, h->dRinv, h->dStatus, h->f64, h->stream));
-    int st = 0;
-    CK(cudaMemcpyAsync(&st, h->dStatus, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    if (st != 0) return fail(h, SPPC_ERR_BREAKDOWN, "small eigensolve: Cholesky breakdown at column %d", st - 1);
+    CK(chol_rinv(h->dS, 16, b, 16, shift, h->dR1, h->dRinv, h->dStatus + 2 + pass, h->f64, h->stream));
     CKS(rotate_set(h, X, Tmp, nb, h->dRinv));
     for (int a = 0; a < nb; ++a) std::swap(X[a], Tmp[a]);
   }
+  int st[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(st, h->dStatus + 2, sizeof(int) * 3, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int pass = 0; pass < 3; ++pass)
+    if (st[pass] != 0)
+      return fail(h, SPPC_ERR_BREAKDOWN, "small eigensolve: Cholesky breakdown at column %d", st[pass] - 1);
   return SPPC_OK;
 }
 
