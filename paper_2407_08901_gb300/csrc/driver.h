@@ -262,6 +262,7 @@ __global__ void k_expand_y(const double* V, int ldv, int p, int k, int kp, const
                            float2* thdf, bool f64);
 __global__ void k_restart_coef(const double* V, int ldv, int p, int k, int kp, int b, float2* out, bool f64);
 __global__ void k_subblock(const float2* src, int lds, int na, int ob, float2* out);
+__global__ void k_neg_theta(const double* th, int b, float2* out, bool f64);
 __global__ void k_vmat_df(const double* V, int m, int nev, int ldv, float2* out, bool f64);
 void split_df(double x, float2& out);
 void put_slot(double x, float2& out, bool f64);

@@ -251,6 +251,12 @@ __global__ void k_subblock(const float2* src, int lds, int na, int ob, float2* o
 }
 
 // V (m x nev FP64, ld nev) -> double-float rotation coefficients (m x m padded to 16x16 ld 16)
+// -theta_c (c < b, else 0) of the small eigensolve's residual columns
+__global__ void k_neg_theta(const double* th, int b, float2* out, bool f64) {
+  const int c = threadIdx.x;
+  if (c < 8) out[c] = slot_put(c < b ? -th[c] : 0.0, f64);
+}
+
 __global__ void k_vmat_df(const double* V, int m, int nev, int ldv, float2* out, bool f64) {
   const int t = threadIdx.x;
   for (int e = t; e < 256; e += blockDim.x) {

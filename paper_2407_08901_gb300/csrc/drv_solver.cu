@@ -113,16 +113,15 @@ sppc_status small_eigensolve(sppc_ctx* h) {
     for (int a = 0; a < nb; ++a) std::swap(X[a], Tmp[a]);
     CKS(rotate_set(h, AX, Tmp, nb, h->dRinv));
     for (int a = 0; a < nb; ++a) std::swap(AX[a], Tmp[a]);
-    CK(cudaMemcpyAsync(th.data(), h->dTheta, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    // residuals of the k lowest: D = AX - X theta (block 0 holds columns 0..7)
-    std::vector<float2> thdf(8);
-    for (int c = 0; c < 8; ++c) put_slot((c < b) ? -th[c] : 0.0, thdf[c], h->f64);
-    CK(cudaMemcpyAsync(h->dCoef + kTheta, thdf.data(), sizeof(float2) * 8, cudaMemcpyHostToDevice, s));
+    // residuals of the k lowest: D = AX - X theta (block 0 holds columns 0..7);
+    // theta and the residual norms come back in one synchronisation
+    k_neg_theta<<<1, 32, 0, s>>>(h->dTheta, b, h->dCoef + kTheta, h->f64); count_launch();
+    CK(cudaGetLastError());
     CK(combine_diag(Tmp[0], AX[0], h->dCoef + kOnes, one(X[0]), h->dCoef + kTheta, 8, 0, n1, h->f64, s));
     const float2* A1[1] = {Tmp[0]};
     const float2* B1[1] = {Tmp[0]};
     CK(coldots(A1, B1, 1, 8, 0, n1, h->dDots, h->partials, h->partial_cap, h->f64, s));
+    CK(cudaMemcpyAsync(th.data(), h->dTheta, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(res.data(), h->dDots, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     double worst = 0.0;
