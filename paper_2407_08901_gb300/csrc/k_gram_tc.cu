@@ -35,7 +35,7 @@
 // 0-7 and 8-15 of the chunk, swapped when i >= 4).  A Gram needs no
 // per-element work on Q: per chunk one bulk copy (cp.async.bulk) brings the na
 // blocks' 2 KB pieces, another the chunk's 16 x 8 slots of B.  Per CTA (one per
-// SM, 256 threads) six stages rotate: the copies of chunks k + 1 .. k + 4 fly
+// SM, 384 threads) six stages rotate: the copies of chunks k + 1 .. k + 4 fly
 // while 128 threads cut B's values of chunk k (in shared memory) into C and one
 // thread issues the chunk's eight MMAs (M = 128, N = 80, K = 16), committed to
 // the stage's mbarrier.  With at most 8 blocks (64 basis columns) the A tile's

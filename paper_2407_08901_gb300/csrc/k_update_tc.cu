@@ -16,7 +16,7 @@
 // level L = s + t <= 9 in one tensor-memory region.  A level's sum over at most
 // 128 basis columns and 8 digit pairs stays within 2^24, exact in FP32.
 //
-// Per CTA (one per SM, 256 threads), tiles of 128 rows; per tile the K steps
+// Per CTA (one per SM, 384 threads), tiles of 128 rows; per tile the K steps
 // (two blocks each) stream through five shared-memory stages: warp 1 copies a
 // step's eight 16-row chunks (cp.async.bulk, the two blocks' 4 KB of a chunk
 // each), warp 0 issues its eight MMAs into the tile's region (two regions
