@@ -10,7 +10,8 @@ Pins:
   scales and a zero column, ragged row counts, more than 16 blocks (two
   launches), Y written over X, X absent: within the fixed-point bound plus one
   FP64 rounding, in both slot formats;
-* a non-finite coefficient is reported as SPPC_ERR_NAN.
+* a non-finite coefficient is reported as SPPC_ERR_NAN;
+* ties: Y = 2^12 + t 2^-41 rounds to nearest, ties to even, on both cores.
 """
 import numpy as np
 import pytest
@@ -171,3 +172,24 @@ def test_non_finite_coefficient_is_reported():
     with pytest.raises(S.SppcError) as err:
         S.sppc_block_update(Q, C, tensor=True)
     assert err.value.status == 11
+
+
+def test_rounding_ties_to_even():
+    """The exact sum is rounded once, to nearest with ties to even: Y = 2^12 +
+    t 2^-41 (half an ulp of 2^12 per unit of t) from q = 1 against c = 2^12 and
+    q = t 2^-30 against c = 2^-11, on the tensor and the CUDA cores."""
+    from fractions import Fraction
+    S = _S()
+    ts = [1, 2, 3, 5, -1, -3, 0, 7]
+    n = len(ts)
+    A = np.zeros((1, n, 8))
+    A[0, :, 0] = 1.0
+    A[0, :, 1] = np.ldexp(np.array(ts, dtype=np.float64), -30)
+    C = np.zeros((8, 8))
+    C[0, 0] = 2.0 ** 12
+    C[1, 0] = 2.0 ** -11
+    want = np.array([float(Fraction(2) ** 12 + t * Fraction(1, 2 ** 41)) for t in ts])  # Fraction -> nearest double
+    for tc in (True, False):
+        Y = S.sppc_block_update(torch.from_numpy(A).cuda(), torch.from_numpy(C).cuda(), tensor=tc).cpu().numpy()
+        assert np.array_equal(Y[:, 0], want), (tc, Y[:, 0] - want)
+        assert np.all(Y[:, 1:] == 0.0)
