@@ -18,7 +18,11 @@ from .build import LIB
 __all__ = [
     "SppcError", "sppc_default_opts", "sppc_create", "sppc_spmm", "sppc_spmm_noalloc", "sppc_spmm_host", "sppc_start", "sppc_correct",
     "sppc_rayleigh_ritz", "sppc_refine_step", "sppc_solve", "sppc_order_info", "sppc_get_stats", "sppc_get_state", "sppc_get_layout",
-    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "sppc_small_syev", "sppc_block_gram", "sppc_block_update", "EXPORTED_SYMBOLS", "STATUS",
+    "sppc_destroy", "sppc_last_error", "sppc_kernel_launches", "sppc_small_syev", "sppc_block_gram", "sppc_block_update",
+    "sppc_set_proposal", "sppc_proposal_samples", "sppc_mlp_forward", "sppc_mlp_loss_grad", "sppc_mlp_adam",
+    "sppc_mlp_train_epoch", "sppc_feature_moments", "sppc_standardize", "sppc_solve_batch", "sppc_spmm_tiling",
+    "sppc_sell_sigma", "sppc_spmm_batch_plan", "sppc_spmm_batch_run", "sppc_spmm_batch_destroy",
+    "EXPORTED_SYMBOLS", "STATUS",
 ]
 
 STATUS = {0: "SPPC_OK", 1: "SPPC_ERR_ARG", 2: "SPPC_ERR_NOT_SYMMETRIC", 3: "SPPC_ERR_LEVELS", 4: "SPPC_ERR_OOM",
