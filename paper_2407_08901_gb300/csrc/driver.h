@@ -271,6 +271,10 @@ void build_sell(int64_t nrows, const int64_t* rp, const int32_t* ci, const doubl
                 const std::vector<int64_t>& seg, int64_t sigma, int64_t chunk_cols, bool f64, SellHost& S);
 sppc_status upload_sell(sppc_ctx* h, SellHost& S, SellDev& D, int64_t nrows, std::vector<int64_t>& chunk_store);
 cudaError_t spmm11(const sppc_ctx* h, int kp, const float2* X, float2* Y, const Epi& e, cudaStream_t s);
+// spmm11 on nb blocks (Y[a] = epilogue(H0_hat X[a]), Z[a] as the epilogue's Z when
+// Z is given); two CSR blocks go in one launch.
+cudaError_t spmm11_set(const sppc_ctx* h, int kp, const float2* const* X, float2* const* Y, const float2* const* Z,
+                       int nb, Epi e, cudaStream_t s);
 sppc_status upload_csr11(sppc_ctx* h, int64_t n1, const int64_t* rp, const int32_t* ci, const double* va,
                          CsrDev& out);
 cudaEvent_t next_event(sppc_ctx* h);

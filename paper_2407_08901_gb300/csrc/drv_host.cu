@@ -425,6 +425,17 @@ cudaError_t spmm11(const sppc_ctx* h, int kp, const float2* X, float2* Y, const 
   return spmm(h->H11, kp, X, Y, e, s);
 }
 
+cudaError_t spmm11_set(const sppc_ctx* h, int kp, const float2* const* X, float2* const* Y, const float2* const* Z,
+                       int nb, Epi e, cudaStream_t s) {
+  if (nb == 2 && h->H11c.rowptr && h->H11c.nrows <= kCsrRowsMax) return spmm_csr2(h->H11c, kp, X, Y, Z, e, s);
+  for (int a = 0; a < nb; ++a) {
+    if (Z) e.Z = Z[a];
+    const cudaError_t r = spmm11(h, kp, X[a], Y[a], e, s);
+    if (r != cudaSuccess) return r;
+  }
+  return cudaSuccess;
+}
+
 // H0_hat (rows and columns < n1 of H) as CSR with double-float values.
 // Leading block H[:n1, :n1] as a double-float CSR on the device (columns sorted
 // within each row, so a row's block entries are its first ones).

@@ -103,7 +103,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
   int outer = 0;
   for (; outer < 400; ++outer) {
     // Rayleigh-Ritz on the block
-    for (int a = 0; a < nb; ++a) CK(spmm11(h, 8, X[a], AX[a], Epi{}, s));
+    CK(spmm11_set(h, 8, X, AX, nullptr, nb, Epi{}, s));
     h->stats.spmv_h11 += 8 * nb;
     CKS(gram_set(h, X, AX, nb, h->dS));
     CK(syev_lowest(h->dS, 16, b, b, h->dTheta, h->dV, b, h->f64, s));
@@ -153,7 +153,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
       Epi e1;
       e1.alpha = h->dCoef + kCheb;
       e1.beta = h->dCoef + kCheb + 16;
-      for (int a = 0; a < nb; ++a) CK(spmm11(h, 8, X[a], Y1[a], e1, s));
+      CK(spmm11_set(h, 8, X, Y1, nullptr, nb, e1, s));
       CKS(put3(2.0 / e, -2.0 * c / e, -1.0));
       float2* setA[2] = {X[0], X[1]};
       float2* setB[2] = {Y1[0], Y1[1]};
@@ -163,10 +163,7 @@ sppc_status small_eigensolve(sppc_ctx* h) {
         e2.alpha = h->dCoef + kCheb;
         e2.beta = h->dCoef + kCheb + 16;
         e2.gamma = h->dCoef + kCheb + 32;
-        for (int a = 0; a < nb; ++a) {
-          e2.Z = setA[a];
-          CK(spmm11(h, 8, setB[a], setC[a], e2, s));
-        }
+        CK(spmm11_set(h, 8, setB, setC, setA, nb, e2, s));
         for (int a = 0; a < nb; ++a) {
           float2* t0 = setA[a];
           setA[a] = setB[a];

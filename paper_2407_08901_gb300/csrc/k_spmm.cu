@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(128, 7) k_spmm_sell(SellDev A, int64_t s0, int
 // product over a few thousand rows.  The segment sums combine by shuffles in a
 // fixed order; lane (half, seg) then owns element (row, half * KP/2 + seg).
 template <int KP, bool EPI, bool F64>
-__global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __restrict__ X, float2* __restrict__ Y,
-                                                  Epi epi) {
+__device__ __forceinline__ void csr_rows(const CsrDev& A, const float2* __restrict__ X, float2* __restrict__ Y,
+                                         const Epi& epi) {
   using V = Ar<F64>;
   constexpr int CPL = KP / 2;
   constexpr int NP = CPL / 2;
@@ -142,6 +142,27 @@ __global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __rest
   Y[b] = r;
 }
 
+template <int KP, bool EPI, bool F64>
+__global__ void __launch_bounds__(128) k_spmm_csr(CsrDev A, const float2* __restrict__ X, float2* __restrict__ Y,
+                                                  Epi epi) {
+  csr_rows<KP, EPI, F64>(A, X, Y, epi);
+}
+
+// Two blocks in one launch (blockIdx.y picks the block): the same rows and sums
+// as two k_spmm_csr launches, with twice the warps in flight for these
+// latency-bound products.
+struct CsrPair {
+  const float2* X[2];
+  float2* Y[2];
+  const float2* Z[2];
+};
+template <int KP, bool EPI, bool F64>
+__global__ void __launch_bounds__(128) k_spmm_csr2(CsrDev A, CsrPair P, Epi epi) {
+  const int b = blockIdx.y;
+  epi.Z = P.Z[b];
+  csr_rows<KP, EPI, F64>(A, P.X[b], P.Y[b], epi);
+}
+
 std::atomic<long long> g_launches{0};
 
 // Calls f.template operator()<KP, EPI, F64>() for the run-time column count,
@@ -207,6 +228,20 @@ cudaError_t spmm(const SellDev& A, int kp, const float2* X, float2* Y, const Epi
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t spmm_csr2(const CsrDev& A, int kp, const float2* const X[2], float2* const Y[2], const float2* const Z[2],
+                      const Epi& epi, cudaStream_t s) {
+  if (A.nrows == 0) return cudaSuccess;
+  const dim3 g(static_cast<unsigned>((A.nrows + 15) / 16), 2);
+  const bool has_epi = epi.alpha || epi.beta || epi.gamma;
+  CsrPair P{{X[0], X[1]}, {Y[0], Y[1]}, {Z ? Z[0] : nullptr, Z ? Z[1] : nullptr}};
+  const cudaError_t e0 = dispatch_spmm(kp, has_epi, A.f64, [&]<int KP, bool EPI, bool F>() {
+    k_spmm_csr2<KP, EPI, F><<<g, 128, 0, s>>>(A, P, epi);
+  });
+  if (e0 != cudaSuccess) return e0;
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t spmm_csr(const CsrDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s) {

@@ -105,6 +105,10 @@ int spmm_default_grid();
 // The same product (and epilogue) for a CSR matrix of few rows: 8 lanes per row
 // (latency of the gather chains, not bandwidth, sets the time there).
 cudaError_t spmm_csr(const CsrDev& A, int kp, const float2* X, float2* Y, const Epi& epi, cudaStream_t s);
+// spmm_csr on two blocks in one launch (Y[b] = epilogue(A X[b]), with Z[b] as the
+// epilogue's Z when Z is given): the same results as two spmm_csr calls.
+cudaError_t spmm_csr2(const CsrDev& A, int kp, const float2* const X[2], float2* const Y[2], const float2* const Z[2],
+                      const Epi& epi, cudaStream_t s);
 
 // ---- k_spmm_f32.cu (mixed precision, kp = 4 or 8 columns): X (double-float)
 // rounded to FP32 into X32 (n x kp floats), Y = H X with FP32 values val32 (same
