@@ -1,8 +1,11 @@
 """Pins for the oracle (CPU only): closed forms, textbook special cases,
 invariants and brute force.  None of these re-types an oracle formula; each
 checks it against something the paper or the mathematics fixes."""
+from fractions import Fraction
+
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import oracle
 import workloads as W
@@ -271,3 +274,69 @@ def test_c_spmm_matches_dense_product(c1_matrix):
     assert np.abs(Yc - Ys).max() <= 1e-13 * np.abs(Ys).max()
     A = dense(rp[:201], c, v, w.n)
     assert np.abs(Yc[:200] - A[:200] @ X).max() <= 1e-13 * np.abs(Ys).max()
+
+
+# ------------------------------------- closed-form correction energies
+def _rs_closed_form(a, b, v, w, V22):
+    """E^(2), E^(3), E^(4) of the lowest state for H0 = diag(a, b, 0, ..., 0)
+    (H0_hat = diag(a, b), a < b, a != 0) and V with V11 = 0, rows v (state a)
+    and w (state b) of V12, lower block V22: Rayleigh-Schroedinger theory
+    worked out by hand, in exact rationals.
+
+    With intermediate normalisation the lower block of H0 is zero, so its
+    resolvent is 1/a; the second state enters through 1/(a - b):
+      Psi1 = (0, 0, v/a)            E2 = s/a,             s = v.v
+      Psi2 = (0, (w.v)/(a(a-b)), V22 v/a^2)   E3 = t/a^2, t = v.V22 v
+      E4 = (w.v)^2/(a^2 (a-b)) + (u - s^2)/a^3,          u = v.V22^2 v
+    """
+    Fr = Fraction
+    v = [Fr(x) for x in v]
+    w = [Fr(x) for x in w]
+    a, b = Fr(a), Fr(b)
+    dot = lambda x, y: sum(p * q for p, q in zip(x, y))
+    mv = lambda M, x: [sum(Fr(M[i][j]) * x[j] for j in range(len(x))) for i in range(len(M))]
+    s = dot(v, v)
+    V22v = mv(V22, v)
+    t = dot(v, V22v)
+    u = dot(V22v, V22v)
+    wv = dot(w, v)
+    return [s / a, t / a ** 2, wv ** 2 / (a ** 2 * (a - b)) + (u - s ** 2) / a ** 3]
+
+
+@pytest.mark.parametrize("solver", ["pinv", "minres"])
+@pytest.mark.parametrize("case", ["one_state", "two_states"])
+def test_correction_energies_match_hand_derived_series(solver, case):
+    """Eq. (exp)'s energies E^(1..4) on small integer matrices against the
+    hand-derived Rayleigh-Schroedinger closed forms (Eqs. split2, sm_lin):
+    E^(1) = 0 because V's leading block is zero; a wrong resolvent sign, a
+    dropped E^(q) Psi^(p-q) term or a missing second state changes E^(3) or
+    E^(4).  For n1 = 1, H = [[-3, 1, 2], [1, 1, 1], [2, 1, -1]] gives
+    E = -3, 0, -5/3, 1/9, 5/9."""
+    if case == "one_state":
+        a, b = -3, None
+        v, w = [1, 2], [0, 0]
+        V22 = [[1, 1], [1, -1]]
+    else:
+        a, b = -3, 2
+        v, w = [1, 2, 0, -1], [2, -1, 1, 1]
+        V22 = [[1, 1, 0, 2], [1, -1, 1, 0], [0, 1, 2, -1], [2, 0, -1, 0]]
+    n1 = 1 if b is None else 2
+    m = len(v)
+    A = np.zeros((n1 + m, n1 + m))
+    A[0, 0] = a
+    A[0, n1:] = A[n1:, 0] = v
+    if b is not None:
+        A[1, 1] = b
+        A[1, n1:] = A[n1:, 1] = w
+    A[n1:, n1:] = V22
+    M = sp.csr_matrix(A)
+    r = oracle.sppc(M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data, n1, 1,
+                    fixed_orders=4, keep=True, solver=solver)
+    want = _rs_closed_form(a, b if b is not None else 0, v, w, V22)
+    if case == "one_state":
+        assert want == [Fraction(-5, 3), Fraction(1, 9), Fraction(5, 9)]
+    assert r.E[0][0] == a and r.E[1][0] == 0.0
+    tol = 1e-13 if solver == "pinv" else 1e-10
+    assert len(r.E) >= 5
+    for p, e in enumerate(want, start=2):
+        assert abs(r.E[p][0] - float(e)) <= tol * max(1.0, abs(float(e))), (p, r.E[p][0], e)
