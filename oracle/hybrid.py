@@ -87,7 +87,7 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
                 max_blocks: int = 16, maxit: int = 500, precond: str = "jacobi", clamp: float = 1e-2,
                 solver: str = "pinv", minres_tol: float = 1e-12, reorth: str = "cond",
                 perturb: float = 0.0, perturb_seed: int = 0, lead_iters: int = 20, lead_rows: int | None = None,
-                small_eig=None, on_step=None):
+                small_eig=None, on_step=None, out: dict | None = None):
     """Run SPPC (Algorithm 2) for up to `switch_order` orders (stopping early if
     every scaled residual is below tol), then the block continuation above.
     Returns (theta, resid, converged, records).
@@ -99,7 +99,8 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
     small space make a stronger preconditioner).  small_eig: optional eigenpairs of
     H0_hat passed to the SPPC phase (see sppc).  on_step: optional timing hook,
     callable(phase, index), called after each SPPC order ("sppc", p) and each
-    continuation step ("davidson", it); it does not change the result."""
+    continuation step ("davidson", it); it does not change the result.  out:
+    optional dict that receives the final Ritz vectors as out["Z"] (n x k)."""
     n = row_ptr.shape[0] - 1
     r = sppc(row_ptr, col, val, n1, k, p_max=switch_order, tol=tol, solver=solver, minres_tol=minres_tol,
              keep=True, small_eig=small_eig,
@@ -107,6 +108,8 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
     records = [HybridRecord("sppc", o.p, o.theta, o.resid, o.spmv, k * (o.p + 1)) for o in r.orders]
     spmv = r.spmv
     if r.converged:
+        if out is not None:
+            out["Z"] = r.Z
         return r.theta, r.resid, True, records
     Q, W = r.Q, r.W
     rng = np.random.Generator(np.random.PCG64(perturb_seed))
@@ -160,5 +163,9 @@ def sppc_hybrid(row_ptr, col, val, n1: int, k: int, *, switch_order: int = 15, t
         if on_step is not None:
             on_step("davidson", it)
         if np.all(res <= tol):
+            if out is not None:
+                out["Z"] = Z
             return th, res, True, records
+    if out is not None:
+        out["Z"] = Z
     return th, res, False, records

@@ -119,3 +119,22 @@ def test_lead_block_over_more_levels_converges_to_the_same_eigenvalues():
     assert cv1 and cv2
     assert np.allclose(th1, th2, rtol=1e-12, atol=0)
     assert len(rec2) <= len(rec1)
+
+
+def test_continuation_residual_and_scale_covariance(small_matrix):
+    """The continuation's reported residuals equal ||H z - theta z|| / |theta|
+    formed with the dense matrix and the final Ritz vectors (Eq. rrn), and
+    H -> 3H scales its Ritz values by 3 and leaves those residuals unchanged
+    (no preconditioner: every step is homogeneous)."""
+    w, rp, c, v = small_matrix
+    kw = dict(switch_order=2, tol=1e-300, max_blocks=8, maxit=5, precond="none")
+    out = {}
+    th, rs, conv, rec = oracle.sppc_hybrid(rp, c, v, w.small_dim, w.k, out=out, **kw)
+    A = dense(rp, c, v)
+    Z = out["Z"]
+    direct = np.linalg.norm(A @ Z - Z * th, axis=0) / np.abs(th)
+    assert np.allclose(rs, direct, rtol=1e-8, atol=1e-13)
+    assert np.allclose(Z.T @ Z, np.eye(w.k), atol=1e-12)
+    th3, rs3, _, _ = oracle.sppc_hybrid(rp, c, 3.0 * v, w.small_dim, w.k, **kw)
+    assert np.allclose(th3, 3.0 * th, rtol=1e-11, atol=0)
+    assert np.allclose(rs3, rs, rtol=1e-6, atol=1e-14)

@@ -340,3 +340,26 @@ def test_correction_energies_match_hand_derived_series(solver, case):
     assert len(r.E) >= 5
     for p, e in enumerate(want, start=2):
         assert abs(r.E[p][0] - float(e)) <= tol * max(1.0, abs(float(e))), (p, r.E[p][0], e)
+
+
+# ------------------------------------------- scale covariance, Eq. (rrn)
+def test_scale_covariance_and_reported_residual(small_run):
+    """H -> 3H scales every energy and Ritz value by 3 and leaves Psi^(p) and the
+    scaled residuals (Eq. rrn) unchanged: every step of Algorithm 2 is
+    homogeneous, so a dropped scale (an unscaled residual, an E^(0) squared, a
+    constant shift) breaks it.  The reported residual equals
+    ||H z - theta z|| / |theta| formed with the dense matrix and the returned
+    Ritz vectors."""
+    w, rp, c, v, r = small_run
+    r3 = oracle.sppc(rp, c, 3.0 * v, w.small_dim, w.k, fixed_orders=6, vpsi="both", keep=True)
+    for o, o3 in zip(r.orders, r3.orders):
+        assert np.allclose(o3.theta, 3.0 * o.theta, rtol=1e-12, atol=0)
+        assert np.allclose(o3.resid, o.resid, rtol=1e-8, atol=1e-14)
+    scale = max(np.abs(e).max() for e in r.E)
+    for e, e3 in zip(r.E, r3.E):
+        assert np.abs(e3 - 3.0 * e).max() <= 1e-10 * 3.0 * scale
+    for ps, ps3 in zip(r.Psi, r3.Psi):
+        assert np.abs(ps3 - ps).max() <= 1e-9 * max(1.0, np.abs(ps).max())
+    A = dense(rp, c, v)
+    direct = np.linalg.norm(A @ r.Z - r.Z * r.theta, axis=0) / np.abs(r.theta)
+    assert np.allclose(r.resid, direct, rtol=1e-8, atol=1e-13)
