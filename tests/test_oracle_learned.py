@@ -167,3 +167,56 @@ def test_training_pairs_zero_unmatched_ritz_vectors():
     rh, y = L.training_pairs(V[:, :3], Z, R, np.diag(A).copy(), theta, 1e-2, rhat)
     assert np.array_equal(rh[:, :2], rhat[:, :2]) and np.all(rh[:, 2] == 0) and np.all(y[:, 2] == 0)
     assert np.array_equal(y[:, :2], L.target(V[:, :3], Z, R, np.diag(A).copy(), theta, 1e-2)[:, :2])
+
+
+def test_clamp_keeps_the_sign_of_the_shift():
+    """|H_ii - theta| below the clamp becomes the clamp with the shift's sign (a
+    zero shift counts as positive); larger shifts pass unchanged."""
+    diag = np.array([-2.005, -1.995, -2.0, -2.5, 3.0])
+    den = L.shifted_diag(diag, np.array([-2.0]), 1e-2)[:, 0]
+    assert np.array_equal(den, np.array([-1e-2, 1e-2, 1e-2, -0.5, 5.0]))
+
+
+def test_bf16_inference_rounds_every_operand_and_activation():
+    """Inputs, weights and both hidden activations pass through BF16 before each
+    product, so perturbations far below half a BF16 step of any of them (here
+    1e-12 relative) leave the result bit-identical, while the unrounded final
+    bias still moves it."""
+    p, X, _, _ = _batch(11, B=256)
+    m0 = L.infer_bf16(p, X)
+    W1, b1, W2, b2, w3, b3 = L.unpack(p)
+    eps = 1e-12
+    cases = {
+        "x": (p, X * (1.0 + eps)),
+        "W1": (L.pack(W1 * (1.0 + eps), b1, W2, b2, w3, b3), X),
+        "b1": (L.pack(W1, b1 + eps, W2, b2, w3, b3), X),
+        "W2": (L.pack(W1, b1, W2 * (1.0 + eps), b2, w3, b3), X),
+        "b2": (L.pack(W1, b1, W2, b2 + eps, w3, b3), X),
+        "w3": (L.pack(W1, b1, W2, b2, w3 * (1.0 + eps), b3), X),
+    }
+    for name, (pp, XX) in cases.items():
+        assert np.array_equal(L.infer_bf16(pp, XX), m0), name
+    assert not np.array_equal(L.infer_bf16(L.pack(W1, b1, W2, b2, w3, b3 + 1e-6), X), m0)
+
+
+def test_bf16_inference_rounds_the_input_and_the_first_activation():
+    """Two one-unit networks whose later stages are exact (gelu(a) = a for a >= 8
+    in FP64, power-of-two weights) expose where BF16 rounding happens.
+    (1) a1 = 1024 (x - 1), a2 = a1 / 8: with x rounded to BF16 (steps of 2^-7
+    on [1, 2)) a1 is a multiple of 8 and the output an integer; unrounded x
+    gives fractions.  (2) a1 = x in gelu's curved range, a2 = 1024 (h1 - 0.5)
+    + 8: with h1 rounded to BF16 (steps of 2^-8 on [0.5, 1)) the output is a
+    multiple of 4 and at least 8."""
+    rng = np.random.default_rng(5)
+    z = np.zeros
+    W1, b1, W2, b2, w3 = z((L.NH, L.NF)), z(L.NH), z((L.NH, L.NH)), z(L.NH), z(L.NH)
+    W1[0, 0], b1[0], W2[0, 0], w3[0] = 1024.0, -1024.0, 0.125, 1.0
+    X = np.zeros((400, L.NF))
+    X[:, 0] = rng.uniform(1.07, 1.9, 400)
+    m = L.infer_bf16(L.pack(W1, b1, W2, b2, w3, 0.0), X)
+    assert np.all(m >= 8) and np.array_equal(m, np.round(m))
+    W1, b1, W2, b2 = z((L.NH, L.NF)), z(L.NH), z((L.NH, L.NH)), z(L.NH)
+    W1[0, 0], W2[0, 0], b2[0] = 1.0, 1024.0, -504.0
+    X[:, 0] = rng.uniform(0.72, 1.1, 400)
+    m = L.infer_bf16(L.pack(W1, b1, W2, b2, w3, 0.0), X)
+    assert np.all(m >= 8) and np.array_equal(m, 4.0 * np.round(m / 4.0))
