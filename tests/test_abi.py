@@ -105,3 +105,21 @@ def test_small_syev_rejects_bad_sizes_before_any_device_call():
     assert lib.sppc_small_syev(buf, 10, 10, 0, buf, buf, 8, 0, None) == 1
     assert lib.sppc_small_syev(None, 10, 10, 4, buf, buf, 4, 0, None) == 1
     assert lib.sppc_small_syev(buf, 10, 10, 4, buf, buf, 4, 2, None) == 1  # unknown flag bit
+
+
+def test_binding_refuses_to_import_without_the_library(tmp_path):
+    """The binding has no fallback: a copy of the package whose libsppc.so was
+    never built raises ImportError on import, naming the missing library."""
+    import shutil
+    import subprocess
+    import sys
+    src = os.path.join(ROOT, "paper_2407_08901_gb300")
+    dst = tmp_path / "paper_2407_08901_gb300"
+    dst.mkdir()
+    for f in os.listdir(src):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(src, f), dst / f)
+    r = subprocess.run([sys.executable, "-c", "import paper_2407_08901_gb300"], cwd=tmp_path,
+                       env={**os.environ, "PYTHONPATH": str(tmp_path)}, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libsppc.so is missing" in r.stderr
