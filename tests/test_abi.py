@@ -123,3 +123,19 @@ def test_binding_refuses_to_import_without_the_library(tmp_path):
                        env={**os.environ, "PYTHONPATH": str(tmp_path)}, capture_output=True, text=True, timeout=300)
     assert r.returncode != 0
     assert "ImportError" in r.stderr and "libsppc.so is missing" in r.stderr
+
+
+def test_product_path_shares_nothing_with_the_oracle():
+    """The package (binding, CUDA sources, header) neither imports, includes nor
+    links anything under oracle/, and the oracle imports nothing from the package."""
+    pat = re.compile(r"^\s*(from\s+oracle\b|import\s+oracle\b|#\s*include\s+[<\"][^>\"]*oracle)", re.M)
+    for d in ("paper_2407_08901_gb300", os.path.join("paper_2407_08901_gb300", "csrc"), "include"):
+        for f in os.listdir(os.path.join(ROOT, d)):
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(ROOT, d, f)).read()
+                assert not pat.search(src), os.path.join(d, f)
+                assert "_oracle_spmm" not in src, os.path.join(d, f)
+    back = re.compile(r"^\s*(from\s+paper_2407_08901_gb300\b|import\s+paper_2407_08901_gb300\b)", re.M)
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c")):
+            assert not back.search(open(os.path.join(ROOT, "oracle", f)).read()), f
